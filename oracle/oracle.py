@@ -1,0 +1,304 @@
+"""ctypes binding of the plain FP64 C oracle (``usp_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the product path.  It shares
+no code with the CUDA library (``paper_2508_05642_gb300``).
+
+Every wrapper below calls one C function of the oracle; the C source states the
+passage of Kim & Jun (arXiv 2508.05642) that the function follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "usp_oracle.c")
+_HDR = os.path.join(_HERE, "usp_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+NMOM = 22
+MOMENT_FIELDS = ["N", "Ux", "Uy", "Uz", "T_tr", "T_rot", "T_vib",
+                 "Pxx", "Pyy", "Pzz", "Pxy", "Pxz", "Pyz",
+                 "qtr_x", "qtr_y", "qtr_z", "qrot_x", "qrot_y", "qrot_z",
+                 "qvib_x", "qvib_y", "qvib_z"]
+
+F_PB_CLAMP = 0x01
+F_CHOL_FAIL_AFTER_FIX = 0x02
+F_NEG_RADICAND = 0x04
+F_VIB_LOOP_CAP = 0x08
+F_TREL_CLAMP = 0x10
+F_SAMPLER_CAP = 0x20
+F_A_NONPOS = 0x40
+F_SAMPLER_UNDERFLOW = 0x80
+F_WALL_CAP = 0x100
+
+C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, \
+    C_INTERP_FALLBACK, C_SKIPPED_CELLS = range(8)
+NCOUNTERS = 8
+
+
+def build(force: bool = False, openmp: bool = True) -> str:
+    """Compile the oracle with gcc into ``oracle/_build/liborc.so``."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH):
+        t = os.path.getmtime(_LIB_PATH)
+        if t >= os.path.getmtime(_SRC) and t >= os.path.getmtime(_HDR):
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+            "-fPIC", "-shared", "-Wall", "-Wno-misleading-indentation",
+            _SRC, "-o", tmp, "-lm"]
+    cmd = base[:1] + (["-fopenmp"] if openmp else []) + base[1:]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0 and openmp:
+        r = subprocess.run(base, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle build failed:\n" + r.stderr)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Species(C.Structure):
+    _fields_ = [("m", C.c_double), ("d_ref", C.c_double), ("omega", C.c_double),
+                ("T_ref", C.c_double), ("c_alpha", C.c_double), ("theta_v", C.c_double),
+                ("Z_rot", C.c_double), ("Z_vib", C.c_double), ("zmodel", C.c_int),
+                ("Zrot_inf", C.c_double), ("T_star", C.c_double), ("C1", C.c_double),
+                ("C2", C.c_double), ("sigma_vib", C.c_double)]
+
+
+class Coeffs(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("n", "dt", "T_tr", "T_rot", "T_vib",
+                 "mu", "p", "mu_p", "tau_c", "Z_rot", "Z_vib", "tau_rot", "tau_vib", "Pr",
+                 "A", "B", "alpha", "nu_ref",
+                 "g_r", "g_v", "cv_T1", "T_check", "gamma_tr_rot", "gamma_tr_vib",
+                 "gamma_rot_vib")] + [("t1_iters", C.c_int)] + \
+               [(n, C.c_double) for n in ("e_tr_tgt", "e_rot_tgt", "e_vib_tgt")]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def species(**kw) -> Species:
+    s = Species()
+    for k, v in kw.items():
+        setattr(s, k, v)
+    return s
+
+
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_U32 = C.POINTER(C.c_uint32)
+_I64 = C.POINTER(C.c_int64)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
+            L.orc_uniform.argtypes = [C.c_uint32, C.c_int]
+            L.orc_uniform.restype = C.c_double
+            for fn in ("orc_e_vib", "orc_cv_vib", "orc_T_vib_from_mean_level", "orc_mu",
+                       "orc_prandtl"):
+                getattr(L, fn).argtypes = [C.POINTER(Species), C.c_double]
+                getattr(L, fn).restype = C.c_double
+            L.orc_R.argtypes = [C.POINTER(Species)]
+            L.orc_R.restype = C.c_double
+            L.orc_tau_c.argtypes = [C.POINTER(Species), C.c_double, C.c_double]
+            L.orc_tau_c.restype = C.c_double
+            L.orc_collision_numbers.argtypes = [C.POINTER(Species), C.c_double, _D, _D]
+            L.orc_cell_coeffs.argtypes = [C.POINTER(Species)] + [C.c_double] * 5 + [C.POINTER(Coeffs)]
+            L.orc_cell_coeffs.restype = C.c_int
+            L.orc_relaxation_temperatures.argtypes = [C.POINTER(Species), C.POINTER(Coeffs), C.c_double,
+                                                      C.c_double, C.c_double, C.c_double, _D, _D, _D, _U32]
+            L.orc_sym3_eig_minmax.argtypes = [_D, _D, _D]
+            L.orc_cholesky3.argtypes = [_D, _D]
+            L.orc_cholesky3.restype = C.c_int
+            L.orc_sample_nb.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, _U32]
+            L.orc_sample_nb.restype = C.c_int
+            L.orc_sample_b.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, _U32]
+            L.orc_sample_b.restype = C.c_int
+            L.orc_collide_particle.argtypes = [C.POINTER(Species), C.c_int, C.POINTER(Coeffs), _D, _D,
+                                               C.c_double, C.c_double, C.c_double, _D, C.c_double,
+                                               C.c_double, _D, _D, _I32, _U32, _I64]
+            L.orc_moments.argtypes = [C.POINTER(Species), C.c_int, _I64, _D, _D, _D, _D, _I32, _D]
+            L.orc_homog_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
+                                         C.c_int, _I64, _D, _D, _D, _D, _D, _D, _I32, _U32, _U32, _I64]
+            L.orc_homog_step.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+# ---- random numbers ---------------------------------------------------------
+def philox(ctr, key) -> tuple:
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(out, C.c_uint32))
+    return tuple(int(x) for x in out)
+
+
+def uniform(x: int, form: int) -> float:
+    return lib().orc_uniform(C.c_uint32(x), form)
+
+
+# ---- closed forms -----------------------------------------------------------
+def R(sp: Species) -> float:
+    return lib().orc_R(C.byref(sp))
+
+
+def e_vib(sp, T):
+    return lib().orc_e_vib(C.byref(sp), T)
+
+
+def cv_vib(sp, T):
+    return lib().orc_cv_vib(C.byref(sp), T)
+
+
+def T_vib_from_mean_level(sp, ebar):
+    return lib().orc_T_vib_from_mean_level(C.byref(sp), ebar)
+
+
+def mu(sp, T):
+    return lib().orc_mu(C.byref(sp), T)
+
+
+def tau_c(sp, n, T):
+    return lib().orc_tau_c(C.byref(sp), n, T)
+
+
+def prandtl(sp, T):
+    return lib().orc_prandtl(C.byref(sp), T)
+
+
+def collision_numbers(sp, T_tr):
+    zr, zv = C.c_double(), C.c_double()
+    lib().orc_collision_numbers(C.byref(sp), T_tr, C.byref(zr), C.byref(zv))
+    return zr.value, zv.value
+
+
+def cell_coeffs(sp, n, dt, T_tr, T_rot, T_vib) -> Coeffs:
+    cc = Coeffs()
+    rc = lib().orc_cell_coeffs(C.byref(sp), n, dt, T_tr, T_rot, T_vib, C.byref(cc))
+    if rc != 0:
+        raise ValueError("time step too large: 2 mu/p - Pr dt <= 0")
+    return cc
+
+
+def relaxation_temperatures(sp, cc: Coeffs, alpha, T_tr, T_rot, T_vib):
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    f = C.c_uint32(0)
+    lib().orc_relaxation_temperatures(C.byref(sp), C.byref(cc), alpha, T_tr, T_rot, T_vib,
+                                      C.byref(a), C.byref(b), C.byref(c), C.byref(f))
+    return a.value, b.value, c.value, f.value
+
+
+def sym3_eig_minmax(P6):
+    P = np.ascontiguousarray(P6, dtype=np.float64)
+    lo, hi = C.c_double(), C.c_double()
+    lib().orc_sym3_eig_minmax(_p(P, C.c_double), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+def cholesky3(M6):
+    M = np.ascontiguousarray(M6, dtype=np.float64)
+    L = np.zeros(6)
+    ok = lib().orc_cholesky3(_p(M, C.c_double), _p(L, C.c_double))
+    return bool(ok), L
+
+
+def sample_nb(r, p, u, form=0):
+    f = C.c_uint32(0)
+    k = lib().orc_sample_nb(r, p, u, form, C.byref(f))
+    return k, f.value
+
+
+def sample_b(n, p, u, form=0):
+    f = C.c_uint32(0)
+    k = lib().orc_sample_b(n, p, u, form, C.byref(f))
+    return k, f.value
+
+
+def collide_particle(sp, form, cc: Coeffs, U, Pi, T_tr, T_rot, T_vib, G, u5, u6, c, erot, lev):
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    Pi = np.ascontiguousarray(Pi, dtype=np.float64)
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    cc_ = np.ascontiguousarray(c, dtype=np.float64).copy()
+    e = C.c_double(erot)
+    lv = C.c_int32(lev)
+    fl = C.c_uint32(0)
+    cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+    lib().orc_collide_particle(C.byref(sp), form, C.byref(cc), _p(U, C.c_double), _p(Pi, C.c_double),
+                               T_tr, T_rot, T_vib, _p(G, C.c_double), u5, u6, _p(cc_, C.c_double),
+                               C.byref(e), C.byref(lv), C.byref(fl), _p(cnt, C.c_int64))
+    return cc_, e.value, lv.value, fl.value, cnt
+
+
+# ---- particle-state operations ------------------------------------------------
+@dataclass
+class State:
+    """Particle state in structure-of-arrays form, FP64 (levels int32)."""
+    cx: np.ndarray
+    cy: np.ndarray
+    cz: np.ndarray
+    erot: np.ndarray
+    lev: np.ndarray
+    pid: np.ndarray
+
+    @classmethod
+    def from_arrays(cls, cx, cy, cz, erot, lev, pid=None):
+        n = len(cx)
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float64).copy()
+        if pid is None:
+            pid = np.arange(n, dtype=np.uint32)
+        return cls(f(cx), f(cy), f(cz), f(erot),
+                   np.ascontiguousarray(lev, dtype=np.int32).copy(),
+                   np.ascontiguousarray(pid, dtype=np.uint32).copy())
+
+    def copy(self):
+        return State(self.cx.copy(), self.cy.copy(), self.cz.copy(), self.erot.copy(),
+                     self.lev.copy(), self.pid.copy())
+
+
+def moments(sp, off, st: State) -> np.ndarray:
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    ncell = len(off) - 1
+    out = np.zeros(NMOM * ncell)
+    lib().orc_moments(C.byref(sp), ncell, _p(off, C.c_int64), _p(st.cx, C.c_double),
+                      _p(st.cy, C.c_double), _p(st.cz, C.c_double), _p(st.erot, C.c_double),
+                      _p(st.lev, C.c_int32), _p(out, C.c_double))
+    return out.reshape(NMOM, ncell)
+
+
+def homog_step(sp, form, seed, step0, nsteps, off, ndens, dt, st: State):
+    """Advance independent homogeneous cells ``nsteps`` steps in place.
+
+    Returns (flags, counters)."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    ndens = np.ascontiguousarray(ndens, dtype=np.float64)
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    fl = C.c_uint32(0)
+    cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+    rc = lib().orc_homog_step(C.byref(sp), form, C.c_uint64(seed), step0, nsteps, len(off) - 1,
+                              _p(off, C.c_int64), _p(ndens, C.c_double), _p(dt, C.c_double),
+                              _p(st.cx, C.c_double), _p(st.cy, C.c_double), _p(st.cz, C.c_double),
+                              _p(st.erot, C.c_double), _p(st.lev, C.c_int32), _p(st.pid, C.c_uint32),
+                              C.byref(fl), _p(cnt, C.c_int64))
+    if rc != 0:
+        raise ValueError("time step too large for the method in some cell")
+    return fl.value, cnt

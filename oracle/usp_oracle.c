@@ -1,0 +1,777 @@
+/*
+ * usp_oracle.c -- plain FP64 CPU oracle of the USP-FPM particle update.
+ *
+ * TEST INFRASTRUCTURE ONLY (see usp_oracle.h).  Written for a reader who has
+ * the paper open: no blocking, no fusion, no reordering beyond what the paper's
+ * algorithm states.  Compile with -ffp-contract=off so that the float-form
+ * inversion is a fixed sequence of IEEE operations.
+ */
+#include "usp_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define KB 1.380649e-23          /* Boltzmann constant [J/K] (SI, exact)      */
+#define PI 3.14159265358979323846
+#define SAMPLER_KCAP 4096        /* search cap of one inversion              */
+
+/* ======================================================================== */
+/* Random numbers.  The paper names no generator; the method only needs      */
+/* independent uniforms and standard normals per particle and per cell.      */
+/* Philox4x32-10 is Salmon, Moraes, Dror & Shaw, "Parallel random numbers:   */
+/* as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64 products with the */
+/* multipliers below, the key bumped by the two Weyl constants between       */
+/* rounds.                                                                   */
+/* ======================================================================== */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Open-interval uniform from one 32-bit word.  Form 0: the midpoint rule on
+ * all 32 bits, exact in double.  Form 1: the midpoint rule on the top 23 bits,
+ * (2k+1) 2^-24, which is exact in float. */
+double orc_uniform(uint32_t x, int form)
+{
+    if (form == 0) return ((double)x + 0.5) * (1.0 / 4294967296.0);
+    float k = (float)((x >> 9) * 2u + 1u);
+    float u = k * (1.0f / 16777216.0f);
+    return (double)u;
+}
+
+static void philox_words(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                         uint64_t seed, uint32_t out[4])
+{
+    uint32_t ctr[4] = { c0, c1, c2, c3 };
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* Box-Muller: two independent standard normals from two uniforms. */
+static void box_muller(double ua, double ub, double* ga, double* gb)
+{
+    double rad = sqrt(-2.0 * log(ua));
+    *ga = rad * cos(2.0 * PI * ub);
+    *gb = rad * sin(2.0 * PI * ub);
+}
+
+/* ======================================================================== */
+/* Closed-form physics                                                       */
+/* ======================================================================== */
+double orc_R(const orc_species* sp) { return KB / sp->m; }
+
+/* Sec. 2.A: e_vib(T) = R Theta / (exp(Theta/T) - 1); the T -> 0 limit is 0. */
+double orc_e_vib(const orc_species* sp, double T)
+{
+    if (T <= 0.0) return 0.0;
+    return orc_R(sp) * sp->theta_v / (exp(sp->theta_v / T) - 1.0);
+}
+
+/* Sec. 2.A: c_v,vib = d e_vib / dT.  The printed formula has sinh without the
+ * square; the derivative of e_vib is R (Theta/2T)^2 / sinh^2(Theta/2T), which
+ * is what is used (the Grad-17 weight of Sec. 5.A.1 carries the square too). */
+double orc_cv_vib(const orc_species* sp, double T)
+{
+    if (T <= 0.0) return 0.0;
+    double h = 0.5 * sp->theta_v / T;
+    double s = sinh(h);
+    return orc_R(sp) * (h * h) / (s * s);
+}
+
+/* Inverse of e_vib for the sample mean level ebar = <I>:
+ * e_vib(T) = R Theta ebar  <=>  T = Theta / ln(1 + 1/ebar); ebar = 0 -> T = 0. */
+double orc_T_vib_from_mean_level(const orc_species* sp, double ebar)
+{
+    if (ebar <= 0.0) return 0.0;
+    return sp->theta_v / log(1.0 + 1.0 / ebar);
+}
+
+/* Sec. 4.A: VSS viscosity mu = mu_ref (T/T_ref)^omega with the Chapman-Enskog
+ * reference viscosity. */
+double orc_mu(const orc_species* sp, double T)
+{
+    double ca = sp->c_alpha, w = sp->omega;
+    double mu_ref = 5.0 * (ca + 1.0) * (ca + 2.0) * sqrt(sp->m * KB * sp->T_ref / PI)
+                  / (4.0 * ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) * sp->d_ref * sp->d_ref);
+    return mu_ref * pow(T / sp->T_ref, w);
+}
+
+/* Eq. tau_c: mean collision time of the VSS model, p = n k_B T. */
+double orc_tau_c(const orc_species* sp, double n, double T)
+{
+    double ca = sp->c_alpha, w = sp->omega;
+    double p = n * KB * T;
+    return ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (ca + 1.0) * (ca + 2.0))
+         * orc_mu(sp, T) / p;
+}
+
+/* Sec. 4.B: Eucken Prandtl number with xi_vib as printed.  The paper does not
+ * say which temperature enters xi_vib; the cell vibrational temperature is
+ * used (T <= 0 gives xi = 0, the limit). */
+double orc_prandtl(const orc_species* sp, double T)
+{
+    double xi = 0.0;
+    if (T > 0.0) {
+        double x = sp->theta_v / T;
+        xi = x / (exp(x) - 1.0);
+    }
+    return (14.0 + 2.0 * xi) / (19.0 + 2.0 * xi);
+}
+
+/* Sec. 2.A (fixed numbers) or Sec. 5.C (Parker rotational number and the
+ * Millikan-White number with the high-temperature term), both at T_tr. */
+void orc_collision_numbers(const orc_species* sp, double T_tr, double* Zrot, double* Zvib)
+{
+    if (sp->zmodel == 0) { *Zrot = sp->Z_rot; *Zvib = sp->Z_vib; return; }
+    double r = sp->T_star / T_tr;
+    *Zrot = sp->Zrot_inf / (1.0 + 0.5 * pow(PI, 1.5) * sqrt(r) + (PI + 0.25 * PI * PI) * r);
+    double zmw = (sp->C1 / pow(T_tr, sp->omega)) * exp(sp->C2 * pow(T_tr, -1.0 / 3.0));
+    double zht = (PI * sp->d_ref * sp->d_ref / sp->sigma_vib) * pow(sp->T_ref / T_tr, sp->omega - 0.5);
+    *Zvib = zmw + zht;
+}
+
+/* Per-cell coefficients of Sec. 3.A.1 and 3.A.2.
+ *   A = (2mu/p - Pr dt)/(2mu/p + Pr dt),  alpha_tr = alpha_rot = alpha_vib = A^(1/3)
+ *   B = (2mu/p - dt)/(2mu/p + dt),        nu = (B - alpha^2)/(1 - alpha^2)
+ *   gamma_tr-rot, gamma_tr-vib, gamma_rot-vib with c_v,vib(T_1) where
+ *   c_v,vib(T_1) = (e_vib(T_check) - e_vib(T_vib)) / (T_check - T_vib) and
+ *   e_tr(T_check) = e_tr(T_tr) + gamma_tr-rot/2 (T_rot - T_tr)
+ *                             + gamma_tr-vib/2 (T_vib - T_tr).
+ * The paper gives no solver for this implicit pair.  Reading: fixed-point
+ * iteration on c_v,vib(T_1), started at c_v,vib(T_tr), until the relative
+ * change is below 1e-14 (at most 50 passes); when T_check is within 1e-9 of
+ * T_vib the secant is replaced by the derivative c_v,vib(T_vib).
+ * Returns 0, or -1 if A <= 0 (the time step is too large for the method). */
+int orc_cell_coeffs(const orc_species* sp, double n, double dt,
+                    double T_tr, double T_rot, double T_vib, orc_coeffs* o)
+{
+    memset(o, 0, sizeof(*o));
+    double R = orc_R(sp);
+    double c_tr = 1.5 * R, c_rot = R;
+    o->n = n; o->dt = dt; o->T_tr = T_tr; o->T_rot = T_rot; o->T_vib = T_vib;
+    o->p = n * KB * T_tr;
+    o->mu = orc_mu(sp, T_tr);
+    o->mu_p = o->mu / o->p;
+    o->tau_c = orc_tau_c(sp, n, T_tr);
+    orc_collision_numbers(sp, T_tr, &o->Z_rot, &o->Z_vib);
+    o->tau_rot = o->Z_rot * o->tau_c;
+    o->tau_vib = o->Z_vib * o->tau_c;
+    o->Pr = orc_prandtl(sp, T_vib);
+
+    o->A = (2.0 * o->mu_p - o->Pr * dt) / (2.0 * o->mu_p + o->Pr * dt);
+    o->B = (2.0 * o->mu_p - dt) / (2.0 * o->mu_p + dt);
+    if (!(o->A > 0.0)) return -1;
+    o->alpha = cbrt(o->A);
+    double a2 = o->alpha * o->alpha;
+    o->nu_ref = (o->B - a2) / (1.0 - a2);
+
+    o->g_r = dt / (dt + 2.0 * o->tau_rot);
+    o->g_v = dt / (dt + 2.0 * o->tau_vib);
+
+    double x = orc_cv_vib(sp, T_tr);
+    double Tc = T_tr;
+    int it = 0;
+    for (it = 1; it <= 50; ++it) {
+        double den = c_tr + o->g_r * c_rot + o->g_v * x;
+        double gtr = 2.0 * o->g_r * c_tr * c_rot / den;
+        double gtv = 2.0 * o->g_v * c_tr * x / den;
+        /* e_tr(Tc) - e_tr(T_tr) = c_tr (Tc - T_tr) */
+        Tc = T_tr + (0.5 * gtr * (T_rot - T_tr) + 0.5 * gtv * (T_vib - T_tr)) / c_tr;
+        double xn;
+        double scale = fabs(Tc) > fabs(T_vib) ? fabs(Tc) : fabs(T_vib);
+        if (fabs(Tc - T_vib) <= 1e-9 * scale)
+            xn = orc_cv_vib(sp, T_vib);
+        else
+            xn = (orc_e_vib(sp, Tc) - orc_e_vib(sp, T_vib)) / (Tc - T_vib);
+        double change = fabs(xn - x);
+        x = xn;
+        if (change <= 1e-14 * fabs(xn)) break;
+    }
+    o->t1_iters = it > 50 ? 50 : it;
+    o->cv_T1 = x;
+    {
+        double den = c_tr + o->g_r * c_rot + o->g_v * x;
+        o->gamma_tr_rot = 2.0 * o->g_r * c_tr * c_rot / den;
+        o->gamma_tr_vib = 2.0 * o->g_v * c_tr * x / den;
+        o->gamma_rot_vib = 2.0 * o->g_r * o->g_v * c_rot * x / den;
+        o->T_check = T_tr + (0.5 * o->gamma_tr_rot * (T_rot - T_tr)
+                           + 0.5 * o->gamma_tr_vib * (T_vib - T_tr)) / c_tr;
+    }
+    /* Eqs. e_tr_relax, e_rot_relax, e_vib_relax */
+    o->e_tr_tgt = c_tr * T_tr - o->gamma_tr_rot * (T_tr - T_rot) - o->gamma_tr_vib * (T_tr - T_vib);
+    o->e_rot_tgt = c_rot * T_rot + o->gamma_tr_rot * (T_tr - T_rot) - o->gamma_rot_vib * (T_rot - T_vib);
+    o->e_vib_tgt = orc_e_vib(sp, T_vib) + o->gamma_tr_vib * (T_tr - T_vib) + o->gamma_rot_vib * (T_rot - T_vib);
+    return 0;
+}
+
+/* Eqs. T_tr_USP, T_rot_USP, T_vib_USP.  The vibrational equation is printed
+ * with 1 - alpha_rot^2; all three alphas are equal (also after the positivity
+ * fix, Eq. alpha_USP_positivity_4), so the one alpha passed in is used.
+ * Negative results (possible only for very large dt) are clamped to zero and
+ * flagged. */
+void orc_relaxation_temperatures(const orc_species* sp, const orc_coeffs* cc, double alpha,
+                                 double T_tr, double T_rot, double T_vib,
+                                 double* T_tr_rel, double* T_rot_rel, double* e_vib_rel,
+                                 uint32_t* flags)
+{
+    double R = orc_R(sp);
+    double oma2 = 1.0 - alpha * alpha;
+    double ttr = T_tr - (cc->gamma_tr_rot * (T_tr - T_rot) + cc->gamma_tr_vib * (T_tr - T_vib))
+                        / (oma2 * 1.5 * R);
+    double tro = T_rot + (cc->gamma_tr_rot * (T_tr - T_rot) - cc->gamma_rot_vib * (T_rot - T_vib))
+                        / (oma2 * R);
+    double evr = orc_e_vib(sp, T_vib)
+               + (cc->gamma_tr_vib * (T_tr - T_vib) + cc->gamma_rot_vib * (T_rot - T_vib)) / oma2;
+    if (ttr < 0.0) { ttr = 0.0; *flags |= ORC_F_TREL_CLAMP; }
+    if (tro < 0.0) { tro = 0.0; *flags |= ORC_F_TREL_CLAMP; }
+    if (evr < 0.0) { evr = 0.0; *flags |= ORC_F_TREL_CLAMP; }
+    *T_tr_rel = ttr; *T_rot_rel = tro; *e_vib_rel = evr;
+}
+
+/* ======================================================================== */
+/* Linear algebra                                                           */
+/* ======================================================================== */
+/* Smallest and largest eigenvalue of a symmetric 3x3 matrix stored as
+ * (xx, yy, zz, xy, xz, yz): the trigonometric closed form of the cubic. */
+void orc_sym3_eig_minmax(const double P[6], double* lmin, double* lmax)
+{
+    double a = P[0], b = P[1], c = P[2], d = P[3], e = P[4], f = P[5];
+    double p1 = d * d + e * e + f * f;
+    if (p1 == 0.0) {
+        double lo = a, hi = a;
+        if (b < lo) lo = b; if (c < lo) lo = c;
+        if (b > hi) hi = b; if (c > hi) hi = c;
+        *lmin = lo; *lmax = hi; return;
+    }
+    double q = (a + b + c) / 3.0;
+    double p2 = (a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + 2.0 * p1;
+    double p = sqrt(p2 / 6.0);
+    double b11 = (a - q) / p, b22 = (b - q) / p, b33 = (c - q) / p;
+    double b12 = d / p, b13 = e / p, b23 = f / p;
+    double det = b11 * (b22 * b33 - b23 * b23) - b12 * (b12 * b33 - b23 * b13)
+               + b13 * (b12 * b23 - b22 * b13);
+    double r = det / 2.0;
+    if (r < -1.0) r = -1.0;
+    if (r > 1.0) r = 1.0;
+    double phi = acos(r) / 3.0;
+    *lmax = q + 2.0 * p * cos(phi);
+    *lmin = q + 2.0 * p * cos(phi + 2.0 * PI / 3.0);
+}
+
+/* Cholesky factor L (l00, l10, l11, l20, l21, l22) of M = (xx, yy, zz, xy, xz,
+ * yz); returns 0 if a pivot is not positive (M not positive definite). */
+int orc_cholesky3(const double M[6], double L[6])
+{
+    double m00 = M[0], m11 = M[1], m22 = M[2], m10 = M[3], m20 = M[4], m21 = M[5];
+    if (!(m00 > 0.0)) return 0;
+    double l00 = sqrt(m00);
+    double l10 = m10 / l00;
+    double l20 = m20 / l00;
+    double d1 = m11 - l10 * l10;
+    if (!(d1 > 0.0)) return 0;
+    double l11 = sqrt(d1);
+    double l21 = (m21 - l20 * l10) / l11;
+    double d2 = m22 - l20 * l20 - l21 * l21;
+    if (!(d2 > 0.0)) return 0;
+    double l22 = sqrt(d2);
+    L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = l22;
+    return 1;
+}
+
+/* ======================================================================== */
+/* Discrete samplers for Eq. update_evib.  The paper fixes the distributions */
+/* (negative binomial for up-jumps, binomial for down-jumps) but no sampler. */
+/* Reading: sequential inversion with one uniform each, the pmf stepped by   */
+/* its ratio recursion; P(0) by square-and-multiply; a binomial with p > 1/2 */
+/* is drawn as n - B(n, 1 - p) with the same uniform.  The search stops when */
+/* the cdf can no longer grow in the working precision.  Form 1 runs the     */
+/* search in float (falling back to double when P(0) is not a normal float). */
+/* ======================================================================== */
+static double powi_d(double x, int e)
+{
+    double r = 1.0, b = x;
+    while (e > 0) { if (e & 1) r = r * b; b = b * b; e >>= 1; }
+    return r;
+}
+static float powi_f(float x, int e)
+{
+    float r = 1.0f, b = x;
+    while (e > 0) { if (e & 1) r = r * b; b = b * b; e >>= 1; }
+    return r;
+}
+
+/* NB(r, p): number of failures before the r-th success, P(0) = p^r,
+ * P(k+1) = P(k) (k + r)/(k + 1) (1 - p). */
+static int nb_d(int r, double p, double u, uint32_t* flags)
+{
+    double q = 1.0 - p;
+    double P = powi_d(p, r);
+    if (P < DBL_MIN) {
+        *flags |= ORC_F_SAMPLER_UNDERFLOW;
+        return (int)floor(r * q / p);
+    }
+    double cdf = P;
+    int k = 0;
+    while (u >= cdf) {
+        if (k >= SAMPLER_KCAP) { *flags |= ORC_F_SAMPLER_CAP; break; }
+        double t = (double)(k + r) / (double)(k + 1);
+        P = P * t;
+        P = P * q;
+        k = k + 1;
+        double nc = cdf + P;
+        if (nc == cdf) break;
+        cdf = nc;
+    }
+    return k;
+}
+static int nb_f(int r, float p, float u, uint32_t* flags)
+{
+    float q = 1.0f - p;
+    float P = powi_f(p, r);
+    if (P < FLT_MIN) return nb_d(r, (double)p, (double)u, flags);
+    float cdf = P;
+    int k = 0;
+    while (u >= cdf) {
+        if (k >= SAMPLER_KCAP) { *flags |= ORC_F_SAMPLER_CAP; break; }
+        float t = (float)(k + r) / (float)(k + 1);
+        P = P * t;
+        P = P * q;
+        k = k + 1;
+        float nc = cdf + P;
+        if (nc == cdf) break;
+        cdf = nc;
+    }
+    return k;
+}
+
+/* B(n, p) for 0 < p <= 1/2: P(0) = (1-p)^n, P(k+1) = P(k) (n-k)/(k+1) p/(1-p). */
+static int binv_d(int n, double p, double u, uint32_t* flags)
+{
+    double q = 1.0 - p;
+    double P = powi_d(q, n);
+    if (P < DBL_MIN) {
+        *flags |= ORC_F_SAMPLER_UNDERFLOW;
+        return (int)floor(n * p);
+    }
+    double pq = p / q;
+    double cdf = P;
+    int k = 0;
+    while (u >= cdf && k < n) {
+        double t = (double)(n - k) / (double)(k + 1);
+        P = P * t;
+        P = P * pq;
+        k = k + 1;
+        double nc = cdf + P;
+        if (nc == cdf) break;
+        cdf = nc;
+    }
+    return k;
+}
+static int binv_f(int n, float p, float u, uint32_t* flags)
+{
+    float q = 1.0f - p;
+    float P = powi_f(q, n);
+    if (P < FLT_MIN) return binv_d(n, (double)p, (double)u, flags);
+    float pq = p / q;
+    float cdf = P;
+    int k = 0;
+    while (u >= cdf && k < n) {
+        float t = (float)(n - k) / (float)(k + 1);
+        P = P * t;
+        P = P * pq;
+        k = k + 1;
+        float nc = cdf + P;
+        if (nc == cdf) break;
+        cdf = nc;
+    }
+    return k;
+}
+
+int orc_sample_nb(int r, double p, double u, int form, uint32_t* flags)
+{
+    if (r <= 0) return 0;
+    if (form == 1) {
+        float pf = (float)p;
+        if (!(pf < 1.0f)) return 0;
+        return nb_f(r, pf, (float)u, flags);
+    }
+    if (!(p < 1.0)) return 0;
+    return nb_d(r, p, u, flags);
+}
+
+int orc_sample_b(int n, double p, double u, int form, uint32_t* flags)
+{
+    if (n <= 0) return 0;
+    if (form == 1) {
+        float pf = (float)p;
+        if (pf >= 1.0f) { if (pf > 1.0f) *flags |= ORC_F_PB_CLAMP; return n; }
+        if (!(pf > 0.0f)) return 0;
+        if (pf > 0.5f) return n - binv_f(n, 1.0f - pf, (float)u, flags);
+        return binv_f(n, pf, (float)u, flags);
+    }
+    if (p >= 1.0) { if (p > 1.0) *flags |= ORC_F_PB_CLAMP; return n; }
+    if (!(p > 0.0)) return 0;
+    if (p > 0.5) return n - binv_d(n, 1.0 - p, u, flags);
+    return binv_d(n, p, u, flags);
+}
+
+/* ======================================================================== */
+/* One particle through the collision step (Sec. 4.D):                      */
+/*   relaxation temperatures (Eqs. T_tr_USP, T_rot_USP, T_vib_USP),         */
+/*   M = tau D_tr = R T_tr^rel I + nu (Pi - R T_tr I)        (Eq. D_tr),     */
+/*   Cholesky test; on failure the nu / alpha adjustment of Sec. 3.A.3,     */
+/*   then Eqs. update_ci, update_erot and update_evib.                      */
+/* U, Pi, T_* are the macroscopic fields at the particle (cell values, or   */
+/* interpolated ones).  G holds four standard normals; u5, u6 the uniforms  */
+/* of the two jump samplers.                                                */
+/* Positivity-fix readings (the paper gives the rule, not these details):   */
+/*  - a bound whose denominator is not positive does not restrict nu;       */
+/*  - the adjusted nu is shrunk by (1 - 1e-6) so M is strictly definite;    */
+/*  - alpha^2 from Eq. alpha_USP_positivity_1 is clamped to [0, 1 - 1e-12]; */
+/*  - of +-sqrt(alpha^2) the one whose Pr (Eq. alpha_USP_positivity_3) is   */
+/*    nearest the target wins, ties to +;                                   */
+/*  - the relaxation temperatures are re-evaluated with the new alpha and   */
+/*    the test repeated; since T_tr^rel depends on alpha, the bound is      */
+/*    re-taken from the new T_tr^rel, at most four passes; if D_tr is still */
+/*    not definite, nu = 0 is used and the failure is flagged.              */
+/* ======================================================================== */
+void orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
+                          const double U[3], const double Pi[6],
+                          double T_tr, double T_rot, double T_vib,
+                          const double G[4], double u5, double u6,
+                          double c[3], double* erot, int32_t* lev,
+                          uint32_t* flags, int64_t* counters)
+{
+    double R = orc_R(sp);
+    double alpha = cc->alpha;
+    double nu = cc->nu_ref;
+    double Ttr_rel, Trot_rel, evib_rel;
+    uint32_t tf = 0;
+    orc_relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, &Ttr_rel, &Trot_rel, &evib_rel, &tf);
+
+    double M[6], L[6];
+    M[0] = R * Ttr_rel + nu * (Pi[0] - R * T_tr);
+    M[1] = R * Ttr_rel + nu * (Pi[1] - R * T_tr);
+    M[2] = R * Ttr_rel + nu * (Pi[2] - R * T_tr);
+    M[3] = nu * Pi[3];
+    M[4] = nu * Pi[4];
+    M[5] = nu * Pi[5];
+    if (!orc_cholesky3(M, L)) {
+        counters[ORC_C_CHOL_FIX] += 1;
+        double lmin, lmax;
+        orc_sym3_eig_minmax(Pi, &lmin, &lmax);
+        int ok = 0;
+        for (int pass = 0; pass < 4 && !ok; ++pass) {
+            /* Eq. nu_USP_positivity with the current T_tr^rel */
+            double nref = cc->nu_ref;
+            nu = nref;
+            if (nref <= 0.0) {
+                if (lmax - R * T_tr > 0.0) {
+                    double bound = -R * Ttr_rel / (lmax - R * T_tr);
+                    if (bound > nu) nu = bound;
+                }
+            } else {
+                if (R * T_tr - lmin > 0.0) {
+                    double bound = R * Ttr_rel / (R * T_tr - lmin);
+                    if (bound < nu) nu = bound;
+                }
+            }
+            nu = nu * (1.0 - 1e-6);
+            /* Eqs. alpha_USP_positivity_1 .. _4 */
+            double a2 = (nu - cc->B) / (nu - 1.0);
+            if (a2 < 0.0) a2 = 0.0;
+            if (a2 > 1.0 - 1e-12) a2 = 1.0 - 1e-12;
+            double ap = sqrt(a2), am = -ap;
+            double prp = 2.0 * cc->mu_p * (1.0 - ap * ap * ap) / (cc->dt * (1.0 + ap * ap * ap));
+            double prm = 2.0 * cc->mu_p * (1.0 - am * am * am) / (cc->dt * (1.0 + am * am * am));
+            alpha = (fabs(prm - cc->Pr) < fabs(prp - cc->Pr)) ? am : ap;
+            orc_relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, &Ttr_rel, &Trot_rel, &evib_rel, &tf);
+            M[0] = R * Ttr_rel + nu * (Pi[0] - R * T_tr);
+            M[1] = R * Ttr_rel + nu * (Pi[1] - R * T_tr);
+            M[2] = R * Ttr_rel + nu * (Pi[2] - R * T_tr);
+            M[3] = nu * Pi[3];
+            M[4] = nu * Pi[4];
+            M[5] = nu * Pi[5];
+            ok = orc_cholesky3(M, L);
+        }
+        if (!ok) {
+            *flags |= ORC_F_CHOL_FAIL_AFTER_FIX;
+            double s = sqrt(R * Ttr_rel);
+            L[0] = s; L[1] = 0.0; L[2] = s; L[3] = 0.0; L[4] = 0.0; L[5] = s;
+        }
+    }
+    if (tf) { *flags |= tf; counters[ORC_C_TREL_CLAMP] += 1; }
+
+    /* Eq. update_ci: C^{n+1} = alpha C^n + sqrt(1 - alpha^2) L G, with
+     * L L^T = tau D_tr (the tau of Eq. update_ci cancels). */
+    double a2 = alpha * alpha;
+    double sq = sqrt(1.0 - a2);
+    double LG0 = L[0] * G[0];
+    double LG1 = L[1] * G[0] + L[2] * G[1];
+    double LG2 = L[3] * G[0] + L[4] * G[1] + L[5] * G[2];
+    c[0] = U[0] + alpha * (c[0] - U[0]) + sq * LG0;
+    c[1] = U[1] + alpha * (c[1] - U[1]) + sq * LG1;
+    c[2] = U[2] + alpha * (c[2] - U[2]) + sq * LG2;
+
+    /* Eq. update_erot */
+    double a = R * Trot_rel * (1.0 - a2) / 2.0;
+    double root = sqrt(*erot) * alpha + sqrt(a) * G[3];
+    *erot = a + root * root;
+
+    /* Eq. update_evib with its parameters r_NB, p_NB, n_B, p_B (the p_N of the
+     * printed p_B equation is p_B).  exp(Theta/T_rel) / (exp(Theta/T_rel) - 1)
+     * = 1 + ebar_rel with ebar_rel = e_vib(T_vib^rel) / (R Theta). */
+    double ebar = evib_rel / (R * sp->theta_v);
+    double p_nb = 1.0 / (1.0 + ebar * (1.0 - a2));
+    double p_b = (1.0 + ebar) * (1.0 - a2);
+    int I = *lev;
+    uint32_t sf = 0;
+    int up = orc_sample_nb(I + 1, p_nb, u5, form, &sf);
+    int dn = orc_sample_b(I, p_b, u6, form, &sf);
+    if (sf & ORC_F_PB_CLAMP) counters[ORC_C_PB_CLAMP] += 1;
+    *flags |= sf;
+    *lev = I + up - dn;
+}
+
+/* ======================================================================== */
+/* Moments of Sec. 2.A per cell, with ensemble averages read as sample      */
+/* means over the particles of the cell (1/N):                              */
+/*   out fields: 0 N | 1-3 U | 4 T_tr | 5 T_rot | 6 T_vib |                */
+/*   7-12 Pi (xx yy zz xy xz yz) | 13-15 q_tr | 16-18 q_rot | 19-21 q_vib   */
+/* with T_tr = tr(Pi) / 3R, T_rot = <eps_rot>/R, T_vib from <I>, and heat   */
+/* fluxes per unit mass: q_tr = <C^2 C>/2, q_rot = <C eps>, q_vib =         */
+/* <C I R Theta>.  Cells with no particle give zeros.                       */
+/* ======================================================================== */
+void orc_moments(const orc_species* sp, int ncell, const int64_t* off,
+                 const double* cx, const double* cy, const double* cz,
+                 const double* erot, const int32_t* lev, double* out)
+{
+    double R = orc_R(sp);
+    for (int f = 0; f < ORC_NMOM * ncell; ++f) out[f] = 0.0;
+    for (int ci = 0; ci < ncell; ++ci) {
+        int64_t b = off[ci], e = off[ci + 1];
+        int64_t N = e - b;
+        if (N <= 0) continue;
+        double U[3] = { 0, 0, 0 }, er = 0.0, lv = 0.0;
+        for (int64_t j = b; j < e; ++j) { U[0] += cx[j]; U[1] += cy[j]; U[2] += cz[j]; er += erot[j]; lv += lev[j]; }
+        U[0] /= N; U[1] /= N; U[2] /= N; er /= N; lv /= N;
+        double P[6] = { 0, 0, 0, 0, 0, 0 }, qt[3] = { 0, 0, 0 }, qr[3] = { 0, 0, 0 }, qv[3] = { 0, 0, 0 };
+        for (int64_t j = b; j < e; ++j) {
+            double C0 = cx[j] - U[0], C1 = cy[j] - U[1], C2 = cz[j] - U[2];
+            double C2s = C0 * C0 + C1 * C1 + C2 * C2;
+            P[0] += C0 * C0; P[1] += C1 * C1; P[2] += C2 * C2;
+            P[3] += C0 * C1; P[4] += C0 * C2; P[5] += C1 * C2;
+            qt[0] += 0.5 * C2s * C0; qt[1] += 0.5 * C2s * C1; qt[2] += 0.5 * C2s * C2;
+            qr[0] += C0 * erot[j]; qr[1] += C1 * erot[j]; qr[2] += C2 * erot[j];
+            double ev = lev[j] * R * sp->theta_v;
+            qv[0] += C0 * ev; qv[1] += C1 * ev; qv[2] += C2 * ev;
+        }
+        for (int k = 0; k < 6; ++k) P[k] /= N;
+        for (int k = 0; k < 3; ++k) { qt[k] /= N; qr[k] /= N; qv[k] /= N; }
+        out[0 * ncell + ci] = (double)N;
+        for (int k = 0; k < 3; ++k) out[(1 + k) * ncell + ci] = U[k];
+        out[4 * ncell + ci] = (P[0] + P[1] + P[2]) / (3.0 * R);
+        out[5 * ncell + ci] = er / R;
+        out[6 * ncell + ci] = orc_T_vib_from_mean_level(sp, lv);
+        for (int k = 0; k < 6; ++k) out[(7 + k) * ncell + ci] = P[k];
+        for (int k = 0; k < 3; ++k) {
+            out[(13 + k) * ncell + ci] = qt[k];
+            out[(16 + k) * ncell + ci] = qr[k];
+            out[(19 + k) * ncell + ci] = qv[k];
+        }
+    }
+}
+
+/* ======================================================================== */
+/* Conservation scheme of Sec. 4.C on the particles [b, e) of one cell.     */
+/* Inputs: the step-n cell energies (e_tr^n, e_rot^n, e_vib^n), the         */
+/* step-n bulk velocity U^n, the targets e_rot(T_rot^{n+1}) and             */
+/* e_vib(T_vib^{n+1}) of Eqs. e_rot_relax and e_vib_relax.                  */
+/* Readings:                                                                 */
+/*  - int() is the floor, so the added uniform gives unbiased rounding;     */
+/*  - "a particle is randomly selected": position k = floor(w N / 2^32) of  */
+/*    the j-th cell draw w, with replacement; a decrement that meets a      */
+/*    level-0 particle draws again; at most 64 N draws;                     */
+/*  - the velocity rescale uses the actual post-correction rotational and   */
+/*    vibrational means; a non-positive radicand leaves the velocities      */
+/*    unchanged and is flagged.                                             */
+/* ======================================================================== */
+#define CELL_TAG(t) (0x80000000u | (uint32_t)(t))
+#define CELL_TAG_IDELTA 0
+#define CELL_TAG_PICK 1
+
+static void conserve_cell(const orc_species* sp, uint64_t seed, uint32_t cell, uint32_t step,
+                          int64_t b, int64_t e,
+                          double e_tr_n, double e_rot_n, double e_vib_n, const double Un[3],
+                          double e_rot_tgt, double e_vib_tgt,
+                          double* cx, double* cy, double* cz, double* erot, int32_t* lev,
+                          uint32_t* flags, int64_t* counters)
+{
+    double R = orc_R(sp);
+    double Rth = R * sp->theta_v;
+    int64_t N = e - b;
+    uint32_t w[4];
+
+    /* vibrational: summation-based correction */
+    int64_t sumI = 0;
+    for (int64_t j = b; j < e; ++j) sumI += lev[j];
+    philox_words(cell, step, CELL_TAG(CELL_TAG_IDELTA), 0u, seed, w);
+    double u = orc_uniform(w[0], 0);
+    int64_t Id = (int64_t)floor((double)N * e_vib_tgt / Rth - (double)sumI + u);
+    int64_t draws = 0, cap = 64 * N;
+    while (Id != 0) {
+        if (draws >= cap) { *flags |= ORC_F_VIB_LOOP_CAP; break; }
+        uint32_t blk = (uint32_t)(draws >> 2);
+        philox_words(cell, step, CELL_TAG(CELL_TAG_PICK), blk, seed, w);
+        uint32_t word = w[draws & 3];
+        draws += 1;
+        int64_t k = (int64_t)(((uint64_t)word * (uint64_t)N) >> 32);
+        if (Id > 0) { lev[b + k] += 1; Id -= 1; }
+        else if (lev[b + k] > 0) { lev[b + k] -= 1; Id += 1; }
+    }
+    counters[ORC_C_VIB_DRAWS] += draws;
+
+    /* rotational: scaling-based correction */
+    double er_star = 0.0;
+    for (int64_t j = b; j < e; ++j) er_star += erot[j];
+    er_star /= N;
+    if (er_star > 0.0) {
+        double r = e_rot_tgt / er_star;
+        for (int64_t j = b; j < e; ++j) erot[j] = r * erot[j];
+    }
+
+    /* translational: momentum and total energy */
+    double e_rot_new = 0.0, lv = 0.0;
+    for (int64_t j = b; j < e; ++j) { e_rot_new += erot[j]; lv += lev[j]; }
+    e_rot_new /= N;
+    double e_vib_new = Rth * lv / N;
+    double Us[3] = { 0, 0, 0 };
+    for (int64_t j = b; j < e; ++j) { Us[0] += cx[j]; Us[1] += cy[j]; Us[2] += cz[j]; }
+    Us[0] /= N; Us[1] /= N; Us[2] /= N;
+    double etr_star = 0.0;
+    for (int64_t j = b; j < e; ++j) {
+        double d0 = cx[j] - Us[0], d1 = cy[j] - Us[1], d2 = cz[j] - Us[2];
+        etr_star += 0.5 * (d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    etr_star /= N;
+    double rad = (e_tr_n + e_rot_n + e_vib_n - e_rot_new - e_vib_new) / etr_star;
+    if (!(etr_star > 0.0) || !(rad > 0.0)) {
+        *flags |= ORC_F_NEG_RADICAND;
+        counters[ORC_C_NEG_RADICAND] += 1;
+        return;
+    }
+    double s = sqrt(rad);
+    for (int64_t j = b; j < e; ++j) {
+        cx[j] = Un[0] + s * (cx[j] - Us[0]);
+        cy[j] = Un[1] + s * (cy[j] - Us[1]);
+        cz[j] = Un[2] + s * (cz[j] - Us[2]);
+    }
+}
+
+/* Collision-stream draws of one particle: counter (pid, step, tag, 0).
+ * Tag 0 -> four normals (two Box-Muller pairs), tag 1 -> the two uniforms of
+ * the jump samplers. */
+#define PTAG_NORMALS 0u
+#define PTAG_JUMPS 1u
+static void particle_draws(uint64_t seed, uint32_t pid, uint32_t step, int form,
+                           double G[4], double* u5, double* u6)
+{
+    uint32_t w[4];
+    philox_words(pid, step, PTAG_NORMALS, 0u, seed, w);
+    box_muller(orc_uniform(w[0], form), orc_uniform(w[1], form), &G[0], &G[1]);
+    box_muller(orc_uniform(w[2], form), orc_uniform(w[3], form), &G[2], &G[3]);
+    philox_words(pid, step, PTAG_JUMPS, 0u, seed, w);
+    *u5 = orc_uniform(w[0], form);
+    *u6 = orc_uniform(w[1], form);
+}
+
+/* ======================================================================== */
+/* Independent homogeneous cells (Sec. 5.A set-up): for every step, every   */
+/* cell runs the collision step of Sec. 4.D with its cell-averaged fields   */
+/* (no reconstruction), then the conservation scheme.  Cells with fewer    */
+/* than two particles are left unchanged (reading: their moments are not    */
+/* defined).  The density of each cell stays fixed (no transport).          */
+/* ======================================================================== */
+int orc_homog_step(const orc_species* sp, int form, uint64_t seed,
+                   int64_t step0, int nsteps, int n_inst, const int64_t* off,
+                   const double* ndens, const double* dt,
+                   double* cx, double* cy, double* cz, double* erot,
+                   int32_t* lev, const uint32_t* pid,
+                   uint32_t* flags, int64_t* counters)
+{
+    double R = orc_R(sp);
+    int status = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        uint32_t step = (uint32_t)(step0 + s);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+        for (int ci = 0; ci < n_inst; ++ci) {
+            uint32_t lflags = 0;
+            int64_t lcnt[ORC_NCOUNTERS] = { 0 };
+            int64_t b = off[ci], e = off[ci + 1];
+            int64_t N = e - b;
+            if (N < 2) { lcnt[ORC_C_SKIPPED_CELLS] += 1; goto merge; }
+            {
+                /* cell moments, Sec. 2.A */
+                double U[3] = { 0, 0, 0 }, er = 0.0, lv = 0.0, P[6] = { 0, 0, 0, 0, 0, 0 };
+                for (int64_t j = b; j < e; ++j) { U[0] += cx[j]; U[1] += cy[j]; U[2] += cz[j]; er += erot[j]; lv += lev[j]; }
+                U[0] /= N; U[1] /= N; U[2] /= N; er /= N; lv /= N;
+                for (int64_t j = b; j < e; ++j) {
+                    double C0 = cx[j] - U[0], C1 = cy[j] - U[1], C2 = cz[j] - U[2];
+                    P[0] += C0 * C0; P[1] += C1 * C1; P[2] += C2 * C2;
+                    P[3] += C0 * C1; P[4] += C0 * C2; P[5] += C1 * C2;
+                }
+                for (int k = 0; k < 6; ++k) P[k] /= N;
+                double T_tr = (P[0] + P[1] + P[2]) / (3.0 * R);
+                double T_rot = er / R;
+                double T_vib = orc_T_vib_from_mean_level(sp, lv);
+
+                orc_coeffs cc;
+                if (orc_cell_coeffs(sp, ndens[ci], dt[ci], T_tr, T_rot, T_vib, &cc) != 0) {
+                    lflags |= ORC_F_A_NONPOS;
+                    goto merge;
+                }
+                for (int64_t j = b; j < e; ++j) {
+                    double G[4], u5, u6, c[3] = { cx[j], cy[j], cz[j] };
+                    uint32_t id = pid ? pid[j] : (uint32_t)j;
+                    particle_draws(seed, id, step, form, G, &u5, &u6);
+                    orc_collide_particle(sp, form, &cc, U, P, T_tr, T_rot, T_vib, G, u5, u6,
+                                         c, &erot[j], &lev[j], &lflags, lcnt);
+                    cx[j] = c[0]; cy[j] = c[1]; cz[j] = c[2];
+                }
+                conserve_cell(sp, seed, (uint32_t)ci, step, b, e,
+                              1.5 * R * T_tr, R * T_rot, orc_e_vib(sp, T_vib), U,
+                              cc.e_rot_tgt, cc.e_vib_tgt, cx, cy, cz, erot, lev, &lflags, lcnt);
+            }
+        merge:
+#ifdef _OPENMP
+#pragma omp critical(orc_merge)
+#endif
+            {
+                *flags |= lflags;
+                for (int k = 0; k < ORC_NCOUNTERS; ++k) counters[k] += lcnt[k];
+            }
+        }
+        if (*flags & ORC_F_A_NONPOS) status = -1;
+    }
+    return status;
+}

@@ -1,0 +1,132 @@
+/*
+ * usp_oracle.h -- plain, slow, FP64 CPU oracle of the USP-FPM particle update.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link or
+ * call this code: only tests/, __graft_entry__.smoke() and bench.py's CPU
+ * baseline leg use it.  It shares no code, header, table or constant with the
+ * CUDA library; the only thing both sides share is the seeded input generator,
+ * which holds none of the method's arithmetic.
+ *
+ * Every function follows one passage of Kim & Jun, "A second-order particle
+ * Fokker-Planck-Master method for diatomic gas flows" (arXiv 2508.05642); the
+ * passage is named next to it.  Where the paper is silent, garbled or
+ * ambiguous the reading taken is stated in the comment of the function.
+ *
+ * Two "forms" exist (argument `form`):
+ *   0  FP64 plain method: uniforms u = (x + 0.5) 2^-32 in double, discrete
+ *      decisions (negative-binomial / binomial inversion) in double.
+ *   1  FP32-state method: particle uniforms u = (2 (x >> 9) + 1) 2^-24, exact
+ *      in float, and the inversion that decides the new vibrational level is
+ *      carried out in float, operation by operation as written below, so that
+ *      an integer outcome is decided in the same precision as the FP32 kernel.
+ *      Everything else in the oracle stays FP64.
+ */
+#ifndef USP_ORACLE_H
+#define USP_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status bits (sticky, OR-ed into *flags) */
+#define ORC_F_PB_CLAMP            0x01u  /* p_B > 1 met: binomial clamped to n   */
+#define ORC_F_CHOL_FAIL_AFTER_FIX 0x02u  /* D_tr still not PD after the nu fix  */
+#define ORC_F_NEG_RADICAND        0x04u  /* velocity rescale radicand <= 0      */
+#define ORC_F_VIB_LOOP_CAP        0x08u  /* +-1 level loop hit its draw cap     */
+#define ORC_F_TREL_CLAMP          0x10u  /* a relaxation temperature was < 0    */
+#define ORC_F_SAMPLER_CAP         0x20u  /* inversion search hit its cap        */
+#define ORC_F_A_NONPOS            0x40u  /* (2mu/p - Pr dt) <= 0: dt too large  */
+#define ORC_F_SAMPLER_UNDERFLOW   0x80u  /* P(0) underflowed even in double     */
+#define ORC_F_WALL_CAP            0x100u /* a particle hit walls too many times */
+
+/* counters[] slots */
+enum { ORC_C_CHOL_FIX = 0, ORC_C_PB_CLAMP = 1, ORC_C_TREL_CLAMP = 2,
+       ORC_C_VIB_DRAWS = 3, ORC_C_NEG_RADICAND = 4, ORC_C_WALL_HITS = 5,
+       ORC_C_INTERP_FALLBACK = 6, ORC_C_SKIPPED_CELLS = 7, ORC_NCOUNTERS = 8 };
+
+/* number of per-cell output moments (field-major: out[f * ncell + cell]) */
+#define ORC_NMOM 22
+
+typedef struct {
+    double m;        /* molecular mass [kg]                                  */
+    double d_ref;    /* VSS/VHS reference diameter [m]                        */
+    double omega;    /* viscosity index c_omega                              */
+    double T_ref;    /* reference temperature [K]                            */
+    double c_alpha;  /* VSS angular scattering parameter (1 for VHS)         */
+    double theta_v;  /* characteristic vibrational temperature [K]           */
+    double Z_rot;    /* fixed rotational collision number (zmodel 0)         */
+    double Z_vib;    /* fixed vibrational collision number (zmodel 0)        */
+    int    zmodel;   /* 0 fixed numbers, 1 Parker + Millikan-White/high-T    */
+    double Zrot_inf, T_star, C1, C2, sigma_vib;   /* zmodel 1 parameters     */
+} orc_species;
+
+typedef struct {
+    /* inputs */
+    double n, dt, T_tr, T_rot, T_vib;
+    /* transport (Sec. 4.A) */
+    double mu, p, mu_p, tau_c, Z_rot, Z_vib, tau_rot, tau_vib, Pr;
+    /* Eqs. USP-FPM_alpha_tr, USP-FPM_nu, sigma_relax */
+    double A, B, alpha, nu_ref;
+    /* gamma coefficients with the implicit T_1 (Sec. 3.A.1) */
+    double g_r, g_v, cv_T1, T_check, gamma_tr_rot, gamma_tr_vib, gamma_rot_vib;
+    int    t1_iters;
+    /* second-order targets, Eqs. e_tr_relax .. e_vib_relax */
+    double e_tr_tgt, e_rot_tgt, e_vib_tgt;
+} orc_coeffs;
+
+/* ---- random numbers ---------------------------------------------------- */
+void   orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_uniform(uint32_t x, int form);
+
+/* ---- closed-form physics ----------------------------------------------- */
+double orc_R(const orc_species* sp);
+double orc_e_vib(const orc_species* sp, double T);
+double orc_cv_vib(const orc_species* sp, double T);
+double orc_T_vib_from_mean_level(const orc_species* sp, double ebar);
+double orc_mu(const orc_species* sp, double T);
+double orc_tau_c(const orc_species* sp, double n, double T);
+double orc_prandtl(const orc_species* sp, double T);
+void   orc_collision_numbers(const orc_species* sp, double T_tr, double* Zrot, double* Zvib);
+int    orc_cell_coeffs(const orc_species* sp, double n, double dt,
+                       double T_tr, double T_rot, double T_vib, orc_coeffs* out);
+void   orc_relaxation_temperatures(const orc_species* sp, const orc_coeffs* cc, double alpha,
+                                   double T_tr, double T_rot, double T_vib,
+                                   double* T_tr_rel, double* T_rot_rel, double* e_vib_rel,
+                                   uint32_t* flags);
+
+/* ---- small linear algebra ---------------------------------------------- */
+void   orc_sym3_eig_minmax(const double P[6], double* lmin, double* lmax);
+int    orc_cholesky3(const double M[6], double L[6]);
+
+/* ---- discrete samplers (inversion with one uniform each) ----------------- */
+int    orc_sample_nb(int r, double p, double u, int form, uint32_t* flags);
+int    orc_sample_b(int n, double p, double u, int form, uint32_t* flags);
+
+/* ---- one particle collision (Sec. 4.D flow, Eqs. update_ci, update_erot,
+ *      update_evib with the positivity fix of Sec. 3.A.3) ------------------ */
+void   orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
+                            const double U[3], const double Pi[6],
+                            double T_tr, double T_rot, double T_vib,
+                            const double G[4], double u5, double u6,
+                            double c[3], double* erot, int32_t* lev,
+                            uint32_t* flags, int64_t* counters);
+
+/* ---- moments (Sec. 2.A) -------------------------------------------------- */
+void   orc_moments(const orc_species* sp, int ncell, const int64_t* off,
+                   const double* cx, const double* cy, const double* cz,
+                   const double* erot, const int32_t* lev, double* out);
+
+/* ---- one or more steps of independent homogeneous cells ("instances") ---- */
+int    orc_homog_step(const orc_species* sp, int form, uint64_t seed,
+                      int64_t step0, int nsteps, int n_inst, const int64_t* off,
+                      const double* ndens, const double* dt,
+                      double* cx, double* cy, double* cz, double* erot,
+                      int32_t* lev, const uint32_t* pid,
+                      uint32_t* flags, int64_t* counters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
