@@ -1,0 +1,199 @@
+/*
+ * usp.h -- C ABI of the GB300 (sm_103a) USP-FPM particle-update library.
+ *
+ * The library advances a population of diatomic (N2-like) simulation
+ * particles with the unified stochastic particle Fokker-Planck-Master method
+ * of Kim & Jun, "A second-order particle Fokker-Planck-Master method for
+ * diatomic gas flows" (arXiv 2508.05642).  One step is the collision step of
+ * the paper's Sec. 4.D for every cell: cell moments (Sec. 2.A), per-cell
+ * coefficients alpha, nu, gamma (Sec. 3.A.1-3.A.2, Eqs. USP-FPM_alpha_tr,
+ * USP-FPM_nu, e_tr_relax .. e_vib_relax), the particle updates of velocity
+ * (Eq. update_ci with Eq. D_tr and the positivity fix of Sec. 3.A.3),
+ * rotational energy (Eq. update_erot) and vibrational level (Eq. update_evib),
+ * then the conservation scheme of Sec. 4.C.
+ *
+ * Conventions shared by every entry point:
+ *  - All particle data is structure-of-arrays.  Velocities c_x, c_y, c_z are
+ *    in m/s, the rotational energy is specific (J/kg), the vibrational level
+ *    is a non-negative int32.
+ *  - A "cell" of the homogeneous problem is an independent relaxation
+ *    instance; its particles are the contiguous range
+ *    [offsets[i], offsets[i+1]) of the caller's arrays.
+ *  - Pointers named h_* are host memory, d_* device memory.  The library
+ *    copies what it needs; it never keeps or frees a caller pointer.
+ *  - Device memory is owned by the context: taken from the caller's
+ *    allocator callback when one is given (released through its free
+ *    callback), else from cudaMalloc.  usp_destroy releases all of it.
+ *  - Work is enqueued on the context's CUDA stream and returns without
+ *    waiting, except where a function says it synchronises.
+ *  - Every function returns USP_OK (0) or a negative usp_err.  A failing CUDA
+ *    call returns USP_ECUDA; invalid arguments return USP_EINVAL and change
+ *    nothing.  Numerical events inside the step do not stop it: they set bits
+ *    of a sticky device status word read by usp_status.
+ */
+#ifndef USP_H
+#define USP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  USP_OK = 0,
+  USP_EINVAL = -1,   /* invalid argument                                   */
+  USP_ENOMEM = -2,   /* allocation failed                                  */
+  USP_ECUDA = -3,    /* a CUDA runtime call failed                         */
+  USP_EDEVICE = -4,  /* the device status word has an error bit set        */
+  USP_ENOTSUP = -5   /* the request is not supported by this context       */
+} usp_err;
+
+/* Device status bits (usp_status).  Bits 0x02, 0x40, 0x80, 0x200 are errors;
+ * the others report clamps the method applies and continues. */
+enum {
+  USP_F_PB_CLAMP = 0x01,            /* p_B > 1 met (Sec. 3.A.2): binomial clamped to n   */
+  USP_F_CHOL_FAIL_AFTER_FIX = 0x02, /* D_tr not positive after the Sec. 3.A.3 fix       */
+  USP_F_NEG_RADICAND = 0x04,        /* velocity rescale of Sec. 4.C impossible; skipped  */
+  USP_F_VIB_LOOP_CAP = 0x08,        /* vibrational +-1 correction hit 64 N draws         */
+  USP_F_TREL_CLAMP = 0x10,          /* a relaxation temperature came out negative        */
+  USP_F_SAMPLER_CAP = 0x20,         /* a jump-sampler search hit 4096 steps              */
+  USP_F_A_NONPOS = 0x40,            /* 2 mu/p <= Pr dt in a cell: dt too large           */
+  USP_F_SAMPLER_UNDERFLOW = 0x80,   /* jump pmf underflowed double                       */
+  USP_F_BOUNDS = 0x200              /* an index check failed (kernel skipped the access) */
+};
+
+/* Counter slots of usp_status. */
+enum {
+  USP_C_CHOL_FIX = 0,      /* positivity fixes applied (per cell and step)       */
+  USP_C_PB_CLAMP = 1,      /* particles whose p_B exceeded 1                      */
+  USP_C_TREL_CLAMP = 2,    /* relaxation-temperature clamps                      */
+  USP_C_VIB_DRAWS = 3,     /* random draws made by the +-1 level correction      */
+  USP_C_NEG_RADICAND = 4,  /* cells whose velocity rescale was skipped           */
+  USP_C_WALL_HITS = 5,
+  USP_C_INTERP_FALLBACK = 6,
+  USP_C_SKIPPED_CELLS = 7, /* cells with fewer than two particles (not collided) */
+  USP_NCOUNTERS = 8
+};
+
+/* Number of per-cell moments written by usp_moments, field-major
+ * (out[f * n_cells + cell]):
+ *   0 N | 1-3 U (m/s) | 4 T_tr | 5 T_rot | 6 T_vib (K) |
+ *   7-12 Pi_ij = <C_i C_j> (xx yy zz xy xz yz, m^2/s^2) |
+ *   13-15 q_tr = <C^2 C>/2 | 16-18 q_rot = <C eps_rot> | 19-21 q_vib = <C I R Theta>
+ * (heat fluxes per unit mass, m^3/s^3; multiply by rho for W/m^2).  These are
+ * the moments of Sec. 2.A with ensemble averages taken as 1/N sample means;
+ * T_vib inverts e_vib of Sec. 2.A at the mean level (0 for no excitation). */
+#define USP_NMOM 22
+
+enum { USP_FP64 = 0, USP_FP32 = 1 };
+
+/* Gas species.  VSS/VHS viscosity parameters of Sec. 4.A; theta_v of the
+ * harmonic vibrational model (Sec. 2.A); zmodel 0 uses the fixed collision
+ * numbers Z_rot, Z_vib (Sec. 2.A), zmodel 1 the Parker and Millikan-White /
+ * high-temperature numbers of Sec. 5.C with their five parameters. */
+typedef struct {
+  double m, d_ref, omega, T_ref, c_alpha, theta_v;
+  double Z_rot, Z_vib;
+  int zmodel;
+  double Zrot_inf, T_star, C1, C2, sigma_vib;
+} usp_species;
+
+/* Device-memory allocator callbacks: alloc(bytes, user) returns a device
+ * pointer aligned to 256 bytes or NULL; free(ptr, user) releases it. */
+typedef void* (*usp_alloc_fn)(size_t bytes, void* user);
+typedef void (*usp_free_fn)(void* ptr, void* user);
+
+typedef struct {
+  int precision;        /* USP_FP64: FP64 state and arithmetic (plain form);
+                           USP_FP32: FP32 particle state and per-particle
+                           arithmetic, FP64 per-cell sums and coefficients  */
+  uint64_t seed;        /* key of the Philox4x32-10 stream                   */
+  int64_t step0;        /* index of the first step (Philox counter word 1)   */
+  void* stream;         /* cudaStream_t to enqueue on; NULL = legacy stream  */
+  int use_graph;        /* 1: replay the step from a captured CUDA graph     */
+  int tile;             /* particles per collide tile (0 = autotune)         */
+  usp_alloc_fn alloc;   /* optional allocator (NULL = cudaMalloc)            */
+  usp_free_fn free_;
+  void* alloc_user;
+} usp_config;
+
+typedef struct usp_ctx usp_ctx;
+
+/* Mean collision time tau_c = K(c_alpha, omega) mu(T) / (n k_B T) of the VSS
+ * model (Eq. tau_c), evaluated on the host.  Callers use it to choose dt as
+ * a multiple of tau_c. */
+double usp_tau_c(const usp_species* sp, double n, double T);
+
+/* Create a context for n_cells independent homogeneous cells (the setting of
+ * the paper's Sec. 5.A) and upload the initial particles.
+ *   h_offsets: n_cells + 1 int64, non-decreasing, h_offsets[0] = 0; the
+ *              particles of cell i are [h_offsets[i], h_offsets[i+1]).
+ *   h_ndens:   number density n of each cell [1/m^3] (constant in time).
+ *   h_dt:      time step of each cell [s]; must satisfy 2 mu/p > Pr dt.
+ *   h_cx, h_cy, h_cz, h_erot (double) and h_lev (int32): the particles.
+ * Particle ids (the Philox counter word 0) are the positions in these
+ * arrays.  Returns USP_EINVAL for inconsistent sizes or a total above 2^31.
+ * Synchronises the stream. */
+int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
+                         int n_cells, const int64_t* h_offsets, const double* h_ndens,
+                         const double* h_dt, const double* h_cx, const double* h_cy,
+                         const double* h_cz, const double* h_erot, const int32_t* h_lev);
+
+/* Enqueue nsteps collision steps (Sec. 4.D + Sec. 4.C) on the stream. */
+int usp_step(usp_ctx* ctx, int nsteps);
+
+/* Enqueue the per-cell moments of the current state into out (USP_NMOM x
+ * n_cells doubles, field-major).  out_is_device = 1: out is device memory
+ * and the call is asynchronous; 0: out is host memory and the call
+ * synchronises the stream. */
+int usp_moments(usp_ctx* ctx, double* out, int out_is_device);
+
+/* Copy the current particle state to host arrays (length = total particles,
+ * positions as given to usp_init_homogeneous).  Synchronises. */
+int usp_get_particles(usp_ctx* ctx, double* h_cx, double* h_cy, double* h_cz, double* h_erot,
+                      int32_t* h_lev);
+
+/* Replace the particle state from host arrays (same layout as init) and
+ * recompute the cell moments; the step counter is kept.  Asynchronous with
+ * respect to the host only if the host arrays are pinned. */
+int usp_set_particles(usp_ctx* ctx, const double* h_cx, const double* h_cy, const double* h_cz,
+                      const double* h_erot, const int32_t* h_lev);
+
+/* End-to-end call on host buffers: upload the state (h_* arrays in the
+ * context's precision: float for USP_FP32, double for USP_FP64; int32
+ * levels), run nsteps steps, download the moments into h_moments (USP_NMOM x
+ * n_cells doubles) and, if h_*_out are not NULL, the resulting state.
+ * Synchronises.  For pinned host buffers the copies overlap nothing else but
+ * run at full link speed. */
+int usp_step_host(usp_ctx* ctx, const void* h_cx, const void* h_cy, const void* h_cz,
+                  const void* h_erot, const int32_t* h_lev, int nsteps, double* h_moments,
+                  void* h_cx_out, void* h_cy_out, void* h_cz_out, void* h_erot_out,
+                  int32_t* h_lev_out);
+
+/* Read (and clear with reset != 0) the sticky status word and counters.
+ * Synchronises.  Returns USP_EDEVICE if an error bit is set. */
+int usp_status(usp_ctx* ctx, uint32_t* flags, int64_t counters[USP_NCOUNTERS], int reset);
+
+/* Wait for all work of the context. */
+int usp_sync(usp_ctx* ctx);
+
+/* Sizes of the context. */
+int usp_info(usp_ctx* ctx, int64_t* n_particles, int* n_cells, int* precision, int64_t* step,
+             int* tile, int64_t* device_bytes);
+
+/* Number of kernel launches the library enqueued since creation (graph
+ * replays count every kernel in the graph). */
+int64_t usp_launch_count(usp_ctx* ctx);
+
+/* Release the context and all its device memory (synchronises). */
+void usp_destroy(usp_ctx* ctx);
+
+/* Static description of an error code. */
+const char* usp_strerror(int err);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -375,6 +375,7 @@ static int binv_d(int n, double p, double u, uint32_t* flags)
     double cdf = P;
     int k = 0;
     while (u >= cdf && k < n) {
+        if (k >= SAMPLER_KCAP) { *flags |= ORC_F_SAMPLER_CAP; break; }
         double t = (double)(n - k) / (double)(k + 1);
         P = P * t;
         P = P * pq;
@@ -394,6 +395,7 @@ static int binv_f(int n, float p, float u, uint32_t* flags)
     float cdf = P;
     int k = 0;
     while (u >= cdf && k < n) {
+        if (k >= SAMPLER_KCAP) { *flags |= ORC_F_SAMPLER_CAP; break; }
         float t = (float)(n - k) / (float)(k + 1);
         P = P * t;
         P = P * pq;

@@ -1,0 +1,457 @@
+// usp_device.cuh -- device building blocks of the USP-FPM particle update on
+// sm_103a: the counter-based random stream, the jump samplers, small linear
+// algebra and the per-cell closed forms of Kim & Jun (arXiv 2508.05642).
+//
+// Precision policy: per-cell work (transport coefficients, gamma fixed point,
+// conservation factors) is FP64; per-particle work is templated on the state
+// type T (float for the FP32-state form, double for the plain FP64 form).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace usp {
+
+constexpr double kB = 1.380649e-23;  // Boltzmann constant [J/K]
+constexpr double kPi = 3.14159265358979323846;
+
+// status bits (sticky device word)
+enum : uint32_t {
+  F_PB_CLAMP = 0x01u,
+  F_CHOL_FAIL_AFTER_FIX = 0x02u,
+  F_NEG_RADICAND = 0x04u,
+  F_VIB_LOOP_CAP = 0x08u,
+  F_TREL_CLAMP = 0x10u,
+  F_SAMPLER_CAP = 0x20u,
+  F_A_NONPOS = 0x40u,
+  F_SAMPLER_UNDERFLOW = 0x80u,
+  F_WALL_CAP = 0x100u,
+  F_BOUNDS = 0x200u,
+};
+enum { C_CHOL_FIX = 0, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND,
+       C_WALL_HITS, C_INTERP_FALLBACK, C_SKIPPED_CELLS, NCOUNTERS };
+
+// Philox stream layout: particle counter (pid, step, tag, 0); cell counter
+// (cell, step, 0x80000000 | tag, block).
+enum : uint32_t { PTAG_NORMALS = 0u, PTAG_JUMPS = 1u };
+enum : uint32_t { CTAG_IDELTA = 0x80000000u, CTAG_PICK = 0x80000001u };
+
+struct Species {
+  double m, d_ref, omega, T_ref, c_alpha, theta_v, Z_rot, Z_vib;
+  int zmodel;
+  double Zrot_inf, T_star, C1, C2, sigma_vib;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds, two 32x32->64 products
+// per round, key bumped by the Weyl constants.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// Open-interval uniforms.  double: (x + 0.5) 2^-32 (exact).
+// float: (2 (x >> 9) + 1) 2^-24 (exact; 23 random bits).
+template <typename T> __device__ __forceinline__ T uniform_open(uint32_t x);
+template <> __device__ __forceinline__ double uniform_open<double>(uint32_t x) {
+  return __dmul_rn(__dadd_rn(__uint2double_rn(x), 0.5), 2.3283064365386963e-10);
+}
+template <> __device__ __forceinline__ float uniform_open<float>(uint32_t x) {
+  return __fmul_rn(__uint2float_rn((x >> 9) * 2u + 1u), 5.9604644775390625e-08f);
+}
+
+// Box-Muller pair.
+__device__ __forceinline__ void box_muller(float ua, float ub, float& ga, float& gb) {
+  const float rad = sqrtf(-2.0f * logf(ua));
+  float s, c;
+  sincospif(2.0f * ub, &s, &c);
+  ga = rad * c;
+  gb = rad * s;
+}
+__device__ __forceinline__ void box_muller(double ua, double ub, double& ga, double& gb) {
+  const double rad = sqrt(-2.0 * log(ua));
+  double s, c;
+  sincospi(2.0 * ub, &s, &c);
+  ga = rad * c;
+  gb = rad * s;
+}
+
+// ---------------------------------------------------------------------------
+// Jump samplers of Eq. update_evib: sequential inversion with one uniform,
+// pmf stepped by its ratio recursion, P(0) by square-and-multiply; a binomial
+// with p > 1/2 is drawn as n - B(n, 1 - p).  Every operation is an explicit
+// round-to-nearest intrinsic so the integer outcome is a fixed function of
+// (r or n, p, u) in the working precision.  The float search falls back to
+// double when P(0) is not a normal float.
+// ---------------------------------------------------------------------------
+constexpr int kSamplerCap = 4096;
+
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rn_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rn_i2f(int a, double) { return __int2double_rn(a); }
+__device__ __forceinline__ float rn_i2f(int a, float) { return __int2float_rn(a); }
+
+template <typename T>
+__device__ __forceinline__ T powi_rn(T x, int e) {
+  T r = T(1), b = x;
+  while (e > 0) {
+    if (e & 1) r = rn_mul(r, b);
+    b = rn_mul(b, b);
+    e >>= 1;
+  }
+  return r;
+}
+
+__device__ __noinline__ int nb_inv_d(int r, double p, double u, uint32_t& fl) {
+  const double q = rn_sub(1.0, p);
+  double P = powi_rn(p, r);
+  if (P < 2.2250738585072014e-308) {
+    fl |= F_SAMPLER_UNDERFLOW;
+    return (int)floor(r * q / p);
+  }
+  double cdf = P;
+  int k = 0;
+  while (u >= cdf) {
+    if (k >= kSamplerCap) { fl |= F_SAMPLER_CAP; break; }
+    const double t = rn_div(rn_i2f(k + r, 0.0), rn_i2f(k + 1, 0.0));
+    P = rn_mul(P, t);
+    P = rn_mul(P, q);
+    k = k + 1;
+    const double nc = rn_add(cdf, P);
+    if (nc == cdf) break;
+    cdf = nc;
+  }
+  return k;
+}
+
+__device__ __noinline__ int binv_d(int n, double p, double u, uint32_t& fl) {
+  const double q = rn_sub(1.0, p);
+  double P = powi_rn(q, n);
+  if (P < 2.2250738585072014e-308) {
+    fl |= F_SAMPLER_UNDERFLOW;
+    return (int)floor(n * p);
+  }
+  const double pq = rn_div(p, q);
+  double cdf = P;
+  int k = 0;
+  while (u >= cdf && k < n) {
+    if (k >= kSamplerCap) { fl |= F_SAMPLER_CAP; break; }
+    const double t = rn_div(rn_i2f(n - k, 0.0), rn_i2f(k + 1, 0.0));
+    P = rn_mul(P, t);
+    P = rn_mul(P, pq);
+    k = k + 1;
+    const double nc = rn_add(cdf, P);
+    if (nc == cdf) break;
+    cdf = nc;
+  }
+  return k;
+}
+
+__device__ __forceinline__ int nb_inv(int r, float p, float u, uint32_t& fl) {
+  const float q = rn_sub(1.0f, p);
+  float P = powi_rn(p, r);
+  if (P < 1.17549435e-38f) return nb_inv_d(r, (double)p, (double)u, fl);
+  float cdf = P;
+  int k = 0;
+  while (u >= cdf) {
+    if (k >= kSamplerCap) { fl |= F_SAMPLER_CAP; break; }
+    const float t = rn_div(rn_i2f(k + r, 0.0f), rn_i2f(k + 1, 0.0f));
+    P = rn_mul(P, t);
+    P = rn_mul(P, q);
+    k = k + 1;
+    const float nc = rn_add(cdf, P);
+    if (nc == cdf) break;
+    cdf = nc;
+  }
+  return k;
+}
+__device__ __forceinline__ int nb_inv(int r, double p, double u, uint32_t& fl) {
+  return nb_inv_d(r, p, u, fl);
+}
+
+__device__ __forceinline__ int binv(int n, float p, float u, uint32_t& fl) {
+  const float q = rn_sub(1.0f, p);
+  float P = powi_rn(q, n);
+  if (P < 1.17549435e-38f) return binv_d(n, (double)p, (double)u, fl);
+  const float pq = rn_div(p, q);
+  float cdf = P;
+  int k = 0;
+  while (u >= cdf && k < n) {
+    if (k >= kSamplerCap) { fl |= F_SAMPLER_CAP; break; }
+    const float t = rn_div(rn_i2f(n - k, 0.0f), rn_i2f(k + 1, 0.0f));
+    P = rn_mul(P, t);
+    P = rn_mul(P, pq);
+    k = k + 1;
+    const float nc = rn_add(cdf, P);
+    if (nc == cdf) break;
+    cdf = nc;
+  }
+  return k;
+}
+__device__ __forceinline__ int binv(int n, double p, double u, uint32_t& fl) {
+  return binv_d(n, p, u, fl);
+}
+
+// NB(r, p): failures before the r-th success.
+template <typename T>
+__device__ __forceinline__ int sample_nb(int r, T p, T u, uint32_t& fl) {
+  if (r <= 0 || !(p < T(1))) return 0;
+  return nb_inv(r, p, u, fl);
+}
+// B(n, p); p >= 1 gives n (and flags p > 1).
+template <typename T>
+__device__ __forceinline__ int sample_b(int n, T p, T u, uint32_t& fl) {
+  if (n <= 0) return 0;
+  if (p >= T(1)) {
+    if (p > T(1)) fl |= F_PB_CLAMP;
+    return n;
+  }
+  if (!(p > T(0))) return 0;
+  if (p > T(0.5)) return n - binv(n, rn_sub(T(1), p), u, fl);
+  return binv(n, p, u, fl);
+}
+
+// ---------------------------------------------------------------------------
+// Closed forms (FP64, per cell).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double gasR(const Species& s) { return kB / s.m; }
+
+// e_vib(T) = R Theta / (exp(Theta/T) - 1) (Sec. 2.A)
+__device__ __forceinline__ double e_vib_T(const Species& s, double T) {
+  if (T <= 0.0) return 0.0;
+  return gasR(s) * s.theta_v / expm1(s.theta_v / T);
+}
+// c_v,vib(T) = R (Theta/2T)^2 / sinh^2(Theta/2T): the derivative of e_vib.
+__device__ __forceinline__ double cv_vib_T(const Species& s, double T) {
+  if (T <= 0.0) return 0.0;
+  const double h = 0.5 * s.theta_v / T;
+  const double sh = sinh(h);
+  return gasR(s) * (h * h) / (sh * sh);
+}
+// temperature whose e_vib is R Theta ebar
+__device__ __forceinline__ double T_vib_of_level(const Species& s, double ebar) {
+  if (ebar <= 0.0) return 0.0;
+  return s.theta_v / log1p(1.0 / ebar);
+}
+// VSS viscosity and the factor tau_c = K mu / p (Sec. 4.A)
+__device__ __forceinline__ double mu_of_T(const Species& s, double T) {
+  const double ca = s.c_alpha, w = s.omega;
+  const double mu_ref = 5.0 * (ca + 1.0) * (ca + 2.0) * sqrt(s.m * kB * s.T_ref / kPi) /
+                        (4.0 * ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) * s.d_ref * s.d_ref);
+  return mu_ref * pow(T / s.T_ref, w);
+}
+__device__ __forceinline__ double tau_c_factor(const Species& s) {
+  const double ca = s.c_alpha, w = s.omega;
+  return ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (ca + 1.0) * (ca + 2.0));
+}
+// Eucken Pr (Sec. 4.B), xi_vib evaluated at the cell vibrational temperature
+__device__ __forceinline__ double prandtl_T(const Species& s, double Tv) {
+  double xi = 0.0;
+  if (Tv > 0.0) {
+    const double x = s.theta_v / Tv;
+    xi = x / expm1(x);
+  }
+  return (14.0 + 2.0 * xi) / (19.0 + 2.0 * xi);
+}
+__device__ __forceinline__ void collision_numbers(const Species& s, double Ttr, double& zr, double& zv) {
+  if (s.zmodel == 0) { zr = s.Z_rot; zv = s.Z_vib; return; }
+  const double r = s.T_star / Ttr;
+  zr = s.Zrot_inf / (1.0 + 0.5 * pow(kPi, 1.5) * sqrt(r) + (kPi + 0.25 * kPi * kPi) * r);
+  zv = (s.C1 / pow(Ttr, s.omega)) * exp(s.C2 * pow(Ttr, -1.0 / 3.0)) +
+       (kPi * s.d_ref * s.d_ref / s.sigma_vib) * pow(s.T_ref / Ttr, s.omega - 0.5);
+}
+
+// Per-cell coefficients of Sec. 3.A: alpha = A^(1/3), nu, the gamma
+// coefficients with the implicit c_v,vib(T_1) (fixed point started at
+// c_v,vib(T_tr), relative tolerance 1e-14, at most 50 passes), and the
+// second-order energy targets.
+struct CellCoeffs {
+  double mu_p, Pr, A, B, alpha, nu_ref;
+  double g_tr_rot, g_tr_vib, g_rot_vib;
+  double e_rot_tgt, e_vib_tgt;
+  bool ok;
+};
+
+__device__ inline CellCoeffs cell_coeffs(const Species& s, double n, double dt,
+                                         double Ttr, double Trot, double Tvib) {
+  CellCoeffs c;
+  const double R = gasR(s);
+  const double ctr = 1.5 * R, crot = R;
+  const double p = n * kB * Ttr;
+  c.mu_p = mu_of_T(s, Ttr) / p;
+  const double tau_c = tau_c_factor(s) * c.mu_p;
+  double zr, zv;
+  collision_numbers(s, Ttr, zr, zv);
+  const double tau_rot = zr * tau_c, tau_vib = zv * tau_c;
+  c.Pr = prandtl_T(s, Tvib);
+  c.A = (2.0 * c.mu_p - c.Pr * dt) / (2.0 * c.mu_p + c.Pr * dt);
+  c.B = (2.0 * c.mu_p - dt) / (2.0 * c.mu_p + dt);
+  c.ok = c.A > 0.0;
+  c.alpha = c.ok ? cbrt(c.A) : 0.0;
+  const double a2 = c.alpha * c.alpha;
+  c.nu_ref = (c.B - a2) / (1.0 - a2);
+  const double gr = dt / (dt + 2.0 * tau_rot);
+  const double gv = dt / (dt + 2.0 * tau_vib);
+  const double evT = e_vib_T(s, Tvib);
+  double x = cv_vib_T(s, Ttr);
+  for (int it = 0; it < 50; ++it) {
+    const double den = ctr + gr * crot + gv * x;
+    const double gtr = 2.0 * gr * ctr * crot / den;
+    const double gtv = 2.0 * gv * ctr * x / den;
+    const double Tc = Ttr + (0.5 * gtr * (Trot - Ttr) + 0.5 * gtv * (Tvib - Ttr)) / ctr;
+    const double scale = fmax(fabs(Tc), fabs(Tvib));
+    const double xn = (fabs(Tc - Tvib) <= 1e-9 * scale) ? cv_vib_T(s, Tvib)
+                                                         : (e_vib_T(s, Tc) - evT) / (Tc - Tvib);
+    const double ch = fabs(xn - x);
+    x = xn;
+    if (ch <= 1e-14 * fabs(xn)) break;
+  }
+  const double den = ctr + gr * crot + gv * x;
+  c.g_tr_rot = 2.0 * gr * ctr * crot / den;
+  c.g_tr_vib = 2.0 * gv * ctr * x / den;
+  c.g_rot_vib = 2.0 * gr * gv * crot * x / den;
+  c.e_rot_tgt = crot * Trot + c.g_tr_rot * (Ttr - Trot) - c.g_rot_vib * (Trot - Tvib);
+  c.e_vib_tgt = evT + c.g_tr_vib * (Ttr - Tvib) + c.g_rot_vib * (Trot - Tvib);
+  return c;
+}
+
+// Relaxation temperatures (Eqs. T_tr_USP, T_rot_USP, T_vib_USP) for a given
+// alpha; negative values are clamped to 0 and reported.
+__device__ __forceinline__ void relax_temps(const Species& s, const CellCoeffs& c, double alpha,
+                                            double Ttr, double Trot, double Tvib, double& ttr,
+                                            double& trot, double& evr, bool& clamped) {
+  const double R = gasR(s);
+  const double oma2 = 1.0 - alpha * alpha;
+  ttr = Ttr - (c.g_tr_rot * (Ttr - Trot) + c.g_tr_vib * (Ttr - Tvib)) / (oma2 * 1.5 * R);
+  trot = Trot + (c.g_tr_rot * (Ttr - Trot) - c.g_rot_vib * (Trot - Tvib)) / (oma2 * R);
+  evr = e_vib_T(s, Tvib) + (c.g_tr_vib * (Ttr - Tvib) + c.g_rot_vib * (Trot - Tvib)) / oma2;
+  clamped = false;
+  if (ttr < 0.0) { ttr = 0.0; clamped = true; }
+  if (trot < 0.0) { trot = 0.0; clamped = true; }
+  if (evr < 0.0) { evr = 0.0; clamped = true; }
+}
+
+// Cholesky factor (l00, l10, l11, l20, l21, l22) of (xx, yy, zz, xy, xz, yz).
+template <typename T>
+__device__ __forceinline__ bool chol3(const T* M, T* L) {
+  if (!(M[0] > T(0))) return false;
+  const T l00 = sqrt(M[0]);
+  const T l10 = M[3] / l00, l20 = M[4] / l00;
+  const T d1 = M[1] - l10 * l10;
+  if (!(d1 > T(0))) return false;
+  const T l11 = sqrt(d1);
+  const T l21 = (M[5] - l20 * l10) / l11;
+  const T d2 = M[2] - l20 * l20 - l21 * l21;
+  if (!(d2 > T(0))) return false;
+  L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = sqrt(d2);
+  return true;
+}
+
+// extreme eigenvalues of a symmetric 3x3 matrix (trigonometric closed form)
+template <typename T>
+__device__ __forceinline__ void sym3_minmax(const T* P, T& lmin, T& lmax) {
+  const T a = P[0], b = P[1], c = P[2], d = P[3], e = P[4], f = P[5];
+  const T p1 = d * d + e * e + f * f;
+  if (p1 == T(0)) {
+    lmin = fmin(a, fmin(b, c));
+    lmax = fmax(a, fmax(b, c));
+    return;
+  }
+  const T q = (a + b + c) / T(3);
+  const T p2 = (a - q) * (a - q) + (b - q) * (b - q) + (c - q) * (c - q) + T(2) * p1;
+  const T p = sqrt(p2 / T(6));
+  const T b11 = (a - q) / p, b22 = (b - q) / p, b33 = (c - q) / p;
+  const T b12 = d / p, b13 = e / p, b23 = f / p;
+  const T det = b11 * (b22 * b33 - b23 * b23) - b12 * (b12 * b33 - b23 * b13) +
+                b13 * (b12 * b23 - b22 * b13);
+  T r = det / T(2);
+  r = fmin(T(1), fmax(T(-1), r));
+  const T phi = acos(r) / T(3);
+  lmax = q + T(2) * p * cos(phi);
+  lmin = q + T(2) * p * cos(phi + T(2.0943951023931954923));
+}
+
+// Drift-diffusion factor for one set of macroscopic fields: returns the
+// alpha actually used and L with L L^T = tau D_tr (Eq. D_tr), applying the
+// positivity adjustment of Sec. 3.A.3 when the Cholesky test fails (nu
+// clamped by Eq. nu_USP_positivity with the current T_tr^rel and shrunk by
+// 1 - 1e-6, alpha^2 from Eq. alpha_USP_positivity_1 clamped to
+// [0, 1 - 1e-12], the sign giving the Pr nearest the target, up to four
+// passes; then nu = 0).  Also returns the relaxation temperatures for that
+// alpha.  chol_fix / fail report what happened.
+struct DriftDiff {
+  double alpha, L[6], Ttr_rel, Trot_rel, evib_rel;
+  bool fixed, failed, clamped;
+};
+
+__device__ inline DriftDiff drift_diffusion(const Species& s, const CellCoeffs& c, double dt,
+                                            const double* Pi, double Ttr, double Trot, double Tvib) {
+  DriftDiff o;
+  const double R = gasR(s);
+  o.alpha = c.alpha;
+  o.fixed = false;
+  o.failed = false;
+  relax_temps(s, c, o.alpha, Ttr, Trot, Tvib, o.Ttr_rel, o.Trot_rel, o.evib_rel, o.clamped);
+  double nu = c.nu_ref;
+  double M[6];
+  auto fill = [&](double nu_) {
+    M[0] = R * o.Ttr_rel + nu_ * (Pi[0] - R * Ttr);
+    M[1] = R * o.Ttr_rel + nu_ * (Pi[1] - R * Ttr);
+    M[2] = R * o.Ttr_rel + nu_ * (Pi[2] - R * Ttr);
+    M[3] = nu_ * Pi[3];
+    M[4] = nu_ * Pi[4];
+    M[5] = nu_ * Pi[5];
+  };
+  fill(nu);
+  if (chol3(M, o.L)) return o;
+  o.fixed = true;
+  double lmin, lmax;
+  sym3_minmax(Pi, lmin, lmax);
+  bool ok = false;
+  for (int pass = 0; pass < 4 && !ok; ++pass) {
+    nu = c.nu_ref;
+    if (c.nu_ref <= 0.0) {
+      if (lmax - R * Ttr > 0.0) nu = fmax(nu, -R * o.Ttr_rel / (lmax - R * Ttr));
+    } else {
+      if (R * Ttr - lmin > 0.0) nu = fmin(nu, R * o.Ttr_rel / (R * Ttr - lmin));
+    }
+    nu = nu * (1.0 - 1e-6);
+    double a2 = (nu - c.B) / (nu - 1.0);
+    a2 = fmin(fmax(a2, 0.0), 1.0 - 1e-12);
+    const double ap = sqrt(a2), am = -ap;
+    const double prp = 2.0 * c.mu_p * (1.0 - ap * ap * ap) / (dt * (1.0 + ap * ap * ap));
+    const double prm = 2.0 * c.mu_p * (1.0 - am * am * am) / (dt * (1.0 + am * am * am));
+    o.alpha = (fabs(prm - c.Pr) < fabs(prp - c.Pr)) ? am : ap;
+    bool cl;
+    relax_temps(s, c, o.alpha, Ttr, Trot, Tvib, o.Ttr_rel, o.Trot_rel, o.evib_rel, cl);
+    o.clamped = o.clamped || cl;
+    fill(nu);
+    ok = chol3(M, o.L);
+  }
+  if (!ok) {
+    o.failed = true;
+    const double sq = sqrt(R * o.Ttr_rel);
+    o.L[0] = sq; o.L[1] = 0.0; o.L[2] = sq; o.L[3] = 0.0; o.L[4] = 0.0; o.L[5] = sq;
+  }
+  return o;
+}
+
+}  // namespace usp

@@ -1,0 +1,1170 @@
+// usp_homog.cu -- kernels and C ABI of the homogeneous (batched-cell) USP-FPM
+// step on sm_103a.
+//
+// Data layout in HBM
+//   particles: SoA arrays cx, cy, cz, erot (T = float or double) and lev
+//   (int32).  Each cell's particles are a contiguous segment whose start is
+//   padded to a multiple of 4 elements, so every 16-byte vector lies inside
+//   one cell and vector loads are aligned.
+//   cells: FP64 CellState (moments of the current step, targets, the pending
+//   conservation rescale), CollideParams<T> (everything the particle kernel
+//   needs, precomputed per cell), CellSums (FP64 post-collision sums).
+//
+// One step = two kernels:
+//   collide_kernel   one pass over the particles (read 1x, write 1x).  It
+//                    applies the previous step's pending conservation rescale
+//                    on load (c = U + s (c* - U*), eps = r eps*), performs the
+//                    particle updates of Eqs. update_ci, update_erot and
+//                    update_evib with per-cell coefficients, stores the
+//                    post-collision state and accumulates per-cell sums.
+//   finalize_kernel  one warp per cell: the vibrational +-1 correction of
+//                    Sec. 4.C (warp-parallel with the sequential semantics),
+//                    the rotational and velocity rescale factors, the
+//                    moments of the next step (exact under the affine
+//                    rescale: U' = U, Pi' = s^2 Pi*, e_rot' = r e_rot*), and
+//                    the next step's coefficients (Sec. 3.A) in FP64.
+// The rescale is never written back as a separate pass: it rides along with
+// the next collide pass, or with usp_moments / usp_get_particles.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/usp.h"
+#include "usp_device.cuh"
+
+using namespace usp;
+
+namespace {
+
+constexpr int kBlock = 256;       // threads of the particle kernels
+constexpr int kAlign = 4;         // segment alignment (elements)
+
+struct CellState {
+  double U[3], Pi[6];        // bulk velocity and temperature tensor of the step
+  double Ttr, Trot, ebar;    // temperatures (T_vib through ebar = <I>)
+  double e_rot_tgt, e_vib_tgt;
+  double Us[3], s, r;        // pending rescale of the stored state
+  double ndens, dt;
+  long long off, N;          // padded segment start, particle count
+  unsigned int pid0, step;   // id of the first particle, step index
+  int active;
+  int pad_;
+};
+
+template <typename T>
+struct CollideParams {
+  T U[3], Us[3];
+  T as, ar;                  // alpha * s, alpha * sqrt(r)
+  T Lp[6];                   // sqrt(1 - alpha^2) L, L L^T = tau D_tr
+  T a_rot, sqrt_a;           // R T_rot^rel (1 - alpha^2) / 2 and its root
+  T p_nb, p_b;
+  unsigned int step, pid0;
+  long long off;
+  int count, active;
+};
+
+struct CellSums {
+  double v[10];              // sum d (3), sum d d^T (6), sum eps
+  unsigned long long I;      // sum of levels
+  unsigned long long pad_;
+};
+
+struct Tile {
+  int cell, start, count, pad_;
+};
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ float4 ld_vec(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ double2 ld_vec(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ int4 ld_vec_i(const int* p) { return *reinterpret_cast<const int4*>(p); }
+__device__ __forceinline__ int2 ld_vec_i2(const int* p) { return *reinterpret_cast<const int2*>(p); }
+__device__ __forceinline__ void st_vec(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void st_vec(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
+
+__device__ __forceinline__ float& el(float4& v, int i) { return (&v.x)[i]; }
+__device__ __forceinline__ double& el(double2& v, int i) { return (&v.x)[i]; }
+
+__device__ __forceinline__ void flag_or(uint32_t* flags, uint32_t f) {
+  if (f) atomicOr(flags, f);
+}
+
+// ---------------------------------------------------------------------------
+// One particle: pending rescale, velocity, rotation, vibration.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t pid, uint32_t k0,
+                                            uint32_t k1, T& cx, T& cy, T& cz, T& er, int& lv,
+                                            T* acc, int& accI, uint32_t& fl) {
+  const U4 w = philox4x32_10(pid, P.step, PTAG_NORMALS, 0u, k0, k1);
+  T g0, g1, g2, g3;
+  box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
+  box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
+  // c^n - U = s (c* - U*);  C' = alpha C^n + sqrt(1 - alpha^2) L G
+  const T d0 = cx - P.Us[0], d1 = cy - P.Us[1], d2 = cz - P.Us[2];
+  const T r0 = P.as * d0 + P.Lp[0] * g0;
+  const T r1 = P.as * d1 + (P.Lp[1] * g0 + P.Lp[2] * g1);
+  const T r2 = P.as * d2 + (P.Lp[3] * g0 + P.Lp[4] * g1 + P.Lp[5] * g2);
+  cx = P.U[0] + r0;
+  cy = P.U[1] + r1;
+  cz = P.U[2] + r2;
+  // eps' = a + (sqrt(eps^n) alpha + sqrt(a) G)^2, eps^n = r eps*
+  const T root = sqrt(er) * P.ar + P.sqrt_a * g3;
+  er = P.a_rot + root * root;
+  // I' = I + NB(I + 1, p_NB) - B(I, p_B)
+  const U4 w2 = philox4x32_10(pid, P.step, PTAG_JUMPS, 0u, k0, k1);
+  const T u5 = uniform_open<T>(w2.x), u6 = uniform_open<T>(w2.y);
+  const int I = lv;
+  const int up = sample_nb<T>(I + 1, P.p_nb, u5, fl);
+  const int dn = sample_b<T>(I, P.p_b, u6, fl);
+  lv = I + up - dn;
+  acc[0] += r0; acc[1] += r1; acc[2] += r2;
+  acc[3] += r0 * r0; acc[4] += r1 * r1; acc[5] += r2 * r2;
+  acc[6] += r0 * r1; acc[7] += r0 * r2; acc[8] += r1 * r2;
+  acc[9] += er;
+  accI += lv;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block reduction of the tile sums and one FP64 atomic per sum.  Partial sums
+// stay in T inside a thread and a warp; warps combine in FP64.
+template <typename T>
+__device__ __forceinline__ void flush_sums(const T* acc, int accI, CellSums* dst) {
+  __shared__ double red[kBlock / 32][11];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const T s = warp_sum(acc[i]);
+    if (lane == 0) red[wid][i] = (double)s;
+  }
+  const int sI = warp_sum(accI);
+  if (lane == 0) red[wid][10] = (double)sI;
+  __syncthreads();
+  if (threadIdx.x < 11) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) t += red[w][threadIdx.x];
+    if (threadIdx.x < 10)
+      atomicAdd(&dst->v[threadIdx.x], t);
+    else
+      atomicAdd(&dst->I, (unsigned long long)(long long)t);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock, 4)
+collide_kernel(const Tile* __restrict__ tiles, int ntiles,
+               const CollideParams<T>* __restrict__ prm, T* __restrict__ cx,
+               T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
+               int* __restrict__ lev, CellSums* __restrict__ sums, uint32_t* flags,
+               unsigned long long* counters, uint32_t k0, uint32_t k1) {
+  constexpr int V = Vec<T>::n;
+  using VT = typename Vec<T>::type;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const CollideParams<T> P = prm[tl.cell];
+    if (!P.active) continue;
+    const long long base = P.off + tl.start;
+    const uint32_t pid0 = P.pid0 + (uint32_t)tl.start;
+    T acc[10];
+#pragma unroll
+    for (int i = 0; i < 10; ++i) acc[i] = T(0);
+    int accI = 0;
+    uint32_t fl = 0;
+    int npb = 0;
+    const int nvec = (tl.count + V - 1) / V;
+    for (int v = threadIdx.x; v < nvec; v += kBlock) {
+      const long long e0 = base + (long long)v * V;
+      VT vx = ld_vec(cx + e0), vy = ld_vec(cy + e0), vz = ld_vec(cz + e0), ve = ld_vec(er + e0);
+      int li[V];
+      if constexpr (V == 4) {
+        const int4 q = ld_vec_i(lev + e0);
+        li[0] = q.x; li[1] = q.y; li[2] = q.z; li[3] = q.w;
+      } else {
+        const int2 q = ld_vec_i2(lev + e0);
+        li[0] = q.x; li[1] = q.y;
+      }
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const int k = v * V + i;
+        if (k < tl.count) {
+          uint32_t f1 = 0;
+          collide_one<T>(P, pid0 + (uint32_t)(v * V + i), k0, k1, el(vx, i), el(vy, i), el(vz, i),
+                         el(ve, i), li[i], acc, accI, f1);
+          if (f1 & F_PB_CLAMP) ++npb;
+          fl |= f1;
+        }
+      }
+      st_vec(cx + e0, vx); st_vec(cy + e0, vy); st_vec(cz + e0, vz); st_vec(er + e0, ve);
+      if constexpr (V == 4) {
+        *reinterpret_cast<int4*>(lev + e0) = make_int4(li[0], li[1], li[2], li[3]);
+      } else {
+        *reinterpret_cast<int2*>(lev + e0) = make_int2(li[0], li[1]);
+      }
+    }
+    flush_sums<T>(acc, accI, &sums[tl.cell]);
+    if (fl) {
+      flag_or(flags, fl);
+      if (npb) atomicAdd(&counters[C_PB_CLAMP], (unsigned long long)npb);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-cell coefficient block: from the step's moments to CollideParams.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void write_params(const Species& sp, CellState& cs, CollideParams<T>& P, uint32_t* flags,
+                             unsigned long long* counters) {
+  const double R = gasR(sp);
+  P.step = cs.step;
+  P.pid0 = cs.pid0;
+  P.off = cs.off;
+  P.count = (int)cs.N;
+  P.active = cs.active;
+  for (int i = 0; i < 3; ++i) { P.U[i] = (T)cs.U[i]; P.Us[i] = (T)cs.Us[i]; }
+  if (!cs.active) return;
+  const double Tvib = T_vib_of_level(sp, cs.ebar);
+  const CellCoeffs c = cell_coeffs(sp, cs.ndens, cs.dt, cs.Ttr, cs.Trot, Tvib);
+  if (!c.ok) {
+    atomicOr(flags, (uint32_t)F_A_NONPOS);
+    cs.active = 0;
+    P.active = 0;
+    return;
+  }
+  cs.e_rot_tgt = c.e_rot_tgt;
+  cs.e_vib_tgt = c.e_vib_tgt;
+  // homogeneous cell: the fields at every particle are the cell values, so
+  // D_tr, its Cholesky factor and the relaxation temperatures are per cell
+  const DriftDiff dd = drift_diffusion(sp, c, cs.dt, cs.Pi, cs.Ttr, cs.Trot, Tvib);
+  if (dd.fixed) atomicAdd(&counters[C_CHOL_FIX], 1ull);
+  if (dd.failed) atomicOr(flags, (uint32_t)F_CHOL_FAIL_AFTER_FIX);
+  if (dd.clamped) {
+    atomicOr(flags, (uint32_t)F_TREL_CLAMP);
+    atomicAdd(&counters[C_TREL_CLAMP], 1ull);
+  }
+  const double a = dd.alpha, oma2 = 1.0 - a * a, sq = sqrt(oma2);
+  P.as = (T)(a * cs.s);
+  P.ar = (T)(a * sqrt(cs.r));
+  for (int i = 0; i < 6; ++i) P.Lp[i] = (T)(sq * dd.L[i]);
+  const double arot = R * dd.Trot_rel * oma2 / 2.0;
+  P.a_rot = (T)arot;
+  P.sqrt_a = (T)sqrt(arot);
+  const double eb = dd.evib_rel / (R * sp.theta_v);
+  P.p_nb = (T)(1.0 / (1.0 + eb * oma2));
+  P.p_b = (T)((1.0 + eb) * oma2);
+}
+
+// Initial coefficients from freshly reduced moments (identity pending rescale).
+// mom: field-major USP_NMOM x ncell as written by assemble_moments.
+template <typename T>
+__global__ void init_params_kernel(Species sp, int ncell, const double* __restrict__ mom,
+                                   CellState* cells, CollideParams<T>* prm, uint32_t* flags,
+                                   unsigned long long* counters) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  CellState cs = cells[c];
+  const double R = gasR(sp);
+  for (int i = 0; i < 3; ++i) { cs.U[i] = mom[(1 + i) * ncell + c]; cs.Us[i] = cs.U[i]; }
+  for (int i = 0; i < 6; ++i) cs.Pi[i] = mom[(7 + i) * ncell + c];
+  cs.Ttr = mom[4 * ncell + c];
+  cs.Trot = mom[5 * ncell + c];
+  cs.ebar = 0.0;
+  cs.s = 1.0;
+  cs.r = 1.0;
+  cs.active = cs.N >= 2;
+  if (!cs.active) atomicAdd(&counters[C_SKIPPED_CELLS], 1ull);
+  cells[c] = cs;  // ebar is filled by the level-sum pass below
+  (void)R;
+  (void)prm;
+  (void)flags;
+}
+
+template <typename T>
+__global__ void init_params_finish(Species sp, int ncell, const double* __restrict__ levsum,
+                                   CellState* cells, CollideParams<T>* prm, uint32_t* flags,
+                                   unsigned long long* counters) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  CellState cs = cells[c];
+  cs.ebar = cs.N > 0 ? levsum[c] / (double)cs.N : 0.0;
+  CollideParams<T> P;
+  write_params<T>(sp, cs, P, flags, counters);
+  cells[c] = cs;
+  prm[c] = P;
+}
+
+// ---------------------------------------------------------------------------
+// finalize: +-1 level correction, rescale factors, next moments and params.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__global__ void finalize_kernel(Species sp, int ncell, CellState* __restrict__ cells,
+                                CollideParams<T>* __restrict__ prm, CellSums* __restrict__ sums,
+                                int* __restrict__ lev, uint32_t* flags,
+                                unsigned long long* counters, uint32_t k0, uint32_t k1) {
+  const int lane = threadIdx.x & 31;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= ncell) return;
+  CellState cs = cells[c];
+  if (!cs.active) return;
+  const double R = gasR(sp);
+  const double Rth = R * sp.theta_v;
+  const long long N = cs.N;
+  const CellSums S = sums[c];
+  // Sec. 4.C: I_Delta = floor(N e_vib^{n+1} / (R Theta) - sum I* + U)
+  long long Id = 0;
+  if (lane == 0) {
+    const U4 w = philox4x32_10((uint32_t)c, cs.step, CTAG_IDELTA, 0u, k0, k1);
+    const double u = uniform_open<double>(w.x);
+    Id = (long long)floor((double)N * cs.e_vib_tgt / Rth - (double)(long long)S.I + u);
+  }
+  Id = __shfl_sync(0xffffffffu, Id, 0);
+  // Random +-1 picks with replacement, k = floor(w N / 2^32), at most 64 N
+  // draws; a decrement meeting level 0 draws again.  32 draws per round; the
+  // acceptance of draw j is decided exactly as in the one-at-a-time loop:
+  // a decrement on particle k is accepted iff fewer than lev[k] earlier
+  // accepted decrements in the round hit k.
+  long long remaining = Id, draws = 0;
+  const long long cap = 64 * N;
+  long long net = 0;
+  int* lv = lev + cs.off;
+  while (remaining != 0 && draws < cap) {
+    const long long j = draws + lane;
+    const U4 w = philox4x32_10((uint32_t)c, cs.step, CTAG_PICK, (uint32_t)(j >> 2), k0, k1);
+    const uint32_t word = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
+    const long long k = (long long)(((unsigned long long)word * (unsigned long long)N) >> 32);
+    const bool valid = j < cap;
+    bool accept;
+    if (remaining > 0) {
+      accept = valid;
+    } else {
+      const int cur = valid ? __ldcg(&lv[k]) : 0;
+      const unsigned grp = __match_any_sync(0xffffffffu, valid ? k : -1ll);
+      const int rank = __popc(grp & lanemask_lt());
+      accept = valid && rank < cur;
+    }
+    const unsigned am = __ballot_sync(0xffffffffu, accept);
+    const long long need = remaining > 0 ? remaining : -remaining;
+    const int nacc = __popc(am);
+    const int take = (int)(nacc < need ? nacc : need);
+    const int order = __popc(am & lanemask_lt());
+    const bool eff = accept && order < take;
+    __syncwarp();
+    if (eff) atomicAdd(&lv[k], remaining > 0 ? 1 : -1);
+    __syncwarp();
+    long long used = 32;
+    if (take == need && take > 0) {
+      // the loop stops at the take-th accepted draw
+      unsigned m = am;
+      for (int i = 1; i < take; ++i) m &= m - 1;
+      used = __ffs((int)m);  // lane index + 1
+    }
+    if (draws + used > cap) used = cap - draws;
+    draws += used;
+    if (remaining > 0) { remaining -= take; net += take; }
+    else { remaining += take; net -= take; }
+  }
+  if (lane != 0) return;
+  if (remaining != 0) atomicOr(flags, (uint32_t)F_VIB_LOOP_CAP);
+  atomicAdd(&counters[C_VIB_DRAWS], (unsigned long long)draws);
+
+  const double invN = 1.0 / (double)N;
+  const double sumI = (double)((long long)S.I + net);
+  // rotational scaling
+  const double er_star = S.v[9] * invN;
+  const double r = er_star > 0.0 ? cs.e_rot_tgt / er_star : 1.0;
+  const double e_rot_new = r * er_star;
+  const double e_vib_new = Rth * sumI * invN;
+  // velocity scaling about the post-collision mean
+  const double m0 = S.v[0] * invN, m1 = S.v[1] * invN, m2 = S.v[2] * invN;
+  double Ps[6];
+  Ps[0] = S.v[3] * invN - m0 * m0;
+  Ps[1] = S.v[4] * invN - m1 * m1;
+  Ps[2] = S.v[5] * invN - m2 * m2;
+  Ps[3] = S.v[6] * invN - m0 * m1;
+  Ps[4] = S.v[7] * invN - m0 * m2;
+  Ps[5] = S.v[8] * invN - m1 * m2;
+  const double etr_star = 0.5 * (Ps[0] + Ps[1] + Ps[2]);
+  const double e_tr_n = 0.5 * (cs.Pi[0] + cs.Pi[1] + cs.Pi[2]);
+  const double e_rot_n = R * cs.Trot;
+  const double e_vib_n = Rth * cs.ebar;
+  const double rad = (e_tr_n + e_rot_n + e_vib_n - e_rot_new - e_vib_new) / etr_star;
+  double s;
+  double Un[3] = {cs.U[0], cs.U[1], cs.U[2]};
+  double Us[3] = {cs.U[0] + m0, cs.U[1] + m1, cs.U[2] + m2};
+  if (!(etr_star > 0.0) || !(rad > 0.0)) {
+    atomicOr(flags, (uint32_t)F_NEG_RADICAND);
+    atomicAdd(&counters[C_NEG_RADICAND], 1ull);
+    s = 1.0;  // velocities stay as collided: c = U* + (c* - U*)
+    for (int i = 0; i < 3; ++i) Un[i] = Us[i];
+  } else {
+    s = sqrt(rad);
+  }
+  // moments of step n+1 (exact under the affine rescale)
+  for (int i = 0; i < 3; ++i) { cs.U[i] = Un[i]; cs.Us[i] = Us[i]; }
+  for (int i = 0; i < 6; ++i) cs.Pi[i] = s * s * Ps[i];
+  cs.Ttr = (cs.Pi[0] + cs.Pi[1] + cs.Pi[2]) / (3.0 * R);
+  cs.Trot = e_rot_new / R;
+  cs.ebar = sumI * invN;
+  cs.s = s;
+  cs.r = r;
+  cs.step += 1;
+  CollideParams<T> P;
+  write_params<T>(sp, cs, P, flags, counters);
+  cells[c] = cs;
+  prm[c] = P;
+  CellSums z;
+  memset(&z, 0, sizeof(z));
+  sums[c] = z;
+}
+
+// ---------------------------------------------------------------------------
+// Moments of the current state (pending rescale applied), FP64 accumulation.
+// pass 0: sum c, sum eps, sum I;  pass 1: central sums about the mean.
+// acc layout per cell: [0..2] sum c, [3] sum eps, [4] sum I,
+// [5..10] sum CC, [11..13] sum C^2 C / 2, [14..16] sum C eps, [17..19] sum C I
+// ---------------------------------------------------------------------------
+constexpr int kMomAcc = 20;
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock)
+moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
+               const CellState* __restrict__ cells, const T* __restrict__ cx,
+               const T* __restrict__ cy, const T* __restrict__ cz, const T* __restrict__ er,
+               const int* __restrict__ lev, double* __restrict__ acc_out) {
+  __shared__ double red[kBlock / 32][15];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const Tile tl = tiles[t];
+    const CellState cs = cells[tl.cell];
+    const long long base = cs.off + tl.start;
+    double a[15];
+    for (int i = 0; i < 15; ++i) a[i] = 0.0;
+    double mean[5] = {0, 0, 0, 0, 0};
+    if (pass == 1 && cs.N > 0) {
+      for (int i = 0; i < 5; ++i) mean[i] = acc_out[(size_t)tl.cell * kMomAcc + i] / (double)cs.N;
+    }
+    for (int k = threadIdx.x; k < tl.count; k += kBlock) {
+      const long long e = base + k;
+      const double c0 = cs.U[0] + cs.s * ((double)cx[e] - cs.Us[0]);
+      const double c1 = cs.U[1] + cs.s * ((double)cy[e] - cs.Us[1]);
+      const double c2 = cs.U[2] + cs.s * ((double)cz[e] - cs.Us[2]);
+      const double ep = cs.r * (double)er[e];
+      const double li = (double)lev[e];
+      if (pass == 0) {
+        a[0] += c0; a[1] += c1; a[2] += c2; a[3] += ep; a[4] += li;
+      } else {
+        const double C0 = c0 - mean[0], C1 = c1 - mean[1], C2 = c2 - mean[2];
+        const double q = 0.5 * (C0 * C0 + C1 * C1 + C2 * C2);
+        a[0] += C0 * C0; a[1] += C1 * C1; a[2] += C2 * C2;
+        a[3] += C0 * C1; a[4] += C0 * C2; a[5] += C1 * C2;
+        a[6] += q * C0; a[7] += q * C1; a[8] += q * C2;
+        a[9] += C0 * ep; a[10] += C1 * ep; a[11] += C2 * ep;
+        a[12] += C0 * li; a[13] += C1 * li; a[14] += C2 * li;
+      }
+    }
+    const int na = pass == 0 ? 5 : 15;
+    for (int i = 0; i < na; ++i) {
+      const double s = warp_sum(a[i]);
+      if (lane == 0) red[wid][i] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < na) {
+      double s = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) s += red[w][threadIdx.x];
+      atomicAdd(&acc_out[(size_t)tl.cell * kMomAcc + (pass == 0 ? 0 : 5) + threadIdx.x], s);
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void assemble_moments(Species sp, int ncell, const CellState* __restrict__ cells,
+                                 const double* __restrict__ acc, double* __restrict__ out,
+                                 double* __restrict__ levsum) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const double R = gasR(sp);
+  const double N = (double)cells[c].N;
+  const double* a = acc + (size_t)c * kMomAcc;
+  if (levsum) levsum[c] = a[4];
+  if (N <= 0.0) {
+    for (int f = 0; f < USP_NMOM; ++f) out[(size_t)f * ncell + c] = 0.0;
+    return;
+  }
+  const double inv = 1.0 / N;
+  out[c] = N;
+  for (int i = 0; i < 3; ++i) out[(size_t)(1 + i) * ncell + c] = a[i] * inv;
+  const double Pxx = a[5] * inv, Pyy = a[6] * inv, Pzz = a[7] * inv;
+  out[(size_t)4 * ncell + c] = (Pxx + Pyy + Pzz) / (3.0 * R);
+  out[(size_t)5 * ncell + c] = a[3] * inv / R;
+  out[(size_t)6 * ncell + c] = T_vib_of_level(sp, a[4] * inv);
+  for (int i = 0; i < 6; ++i) out[(size_t)(7 + i) * ncell + c] = a[5 + i] * inv;
+  for (int i = 0; i < 3; ++i) {
+    out[(size_t)(13 + i) * ncell + c] = a[11 + i] * inv;
+    out[(size_t)(16 + i) * ncell + c] = a[14 + i] * inv;
+    out[(size_t)(19 + i) * ncell + c] = a[17 + i] * inv * R * sp.theta_v;
+  }
+}
+
+// A freshly uploaded state has no pending rescale.
+__global__ void reset_pending(int ncell, CellState* cells, CellSums* sums) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  for (int i = 0; i < 3; ++i) { cells[c].U[i] = 0.0; cells[c].Us[i] = 0.0; }
+  cells[c].s = 1.0;
+  cells[c].r = 1.0;
+  for (int i = 0; i < 10; ++i) sums[c].v[i] = 0.0;
+  sums[c].I = 0ull;
+}
+
+// Scatter an unpadded host-layout state (type S) into the padded device
+// layout (type T), or gather back with the pending rescale applied.
+template <typename S, typename T>
+__global__ void scatter_state(int ncell, const CellState* __restrict__ cells,
+                              const long long* __restrict__ uoff, const S* __restrict__ ix,
+                              const S* __restrict__ iy, const S* __restrict__ iz,
+                              const S* __restrict__ ie, const int* __restrict__ il,
+                              T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ cz,
+                              T* __restrict__ er, int* __restrict__ lev) {
+  for (int c = blockIdx.y; c < ncell; c += gridDim.y) {
+  const long long b = uoff[c], n = uoff[c + 1] - b, o = cells[c].off;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    cx[o + k] = (T)ix[b + k];
+    cy[o + k] = (T)iy[b + k];
+    cz[o + k] = (T)iz[b + k];
+    er[o + k] = (T)ie[b + k];
+    lev[o + k] = il[b + k];
+  }
+  }
+}
+
+template <typename T>
+__global__ void gather_state(int ncell, const CellState* __restrict__ cells,
+                             const long long* __restrict__ uoff, const T* __restrict__ cx,
+                             const T* __restrict__ cy, const T* __restrict__ cz,
+                             const T* __restrict__ er, const int* __restrict__ lev,
+                             double* __restrict__ ox, double* __restrict__ oy,
+                             double* __restrict__ oz, double* __restrict__ oe,
+                             int* __restrict__ ol) {
+  for (int c = blockIdx.y; c < ncell; c += gridDim.y) {
+  const CellState cs = cells[c];
+  const long long b = uoff[c], n = uoff[c + 1] - b, o = cs.off;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    ox[b + k] = cs.U[0] + cs.s * ((double)cx[o + k] - cs.Us[0]);
+    oy[b + k] = cs.U[1] + cs.s * ((double)cy[o + k] - cs.Us[1]);
+    oz[b + k] = cs.U[2] + cs.s * ((double)cz[o + k] - cs.Us[2]);
+    oe[b + k] = cs.r * (double)er[o + k];
+    ol[b + k] = lev[o + k];
+  }
+  }
+}
+
+template <typename T>
+__global__ void gather_state_native(int ncell, const CellState* __restrict__ cells,
+                                    const long long* __restrict__ uoff, const T* __restrict__ cx,
+                                    const T* __restrict__ cy, const T* __restrict__ cz,
+                                    const T* __restrict__ er, const int* __restrict__ lev,
+                                    T* __restrict__ ox, T* __restrict__ oy, T* __restrict__ oz,
+                                    T* __restrict__ oe, int* __restrict__ ol) {
+  for (int c = blockIdx.y; c < ncell; c += gridDim.y) {
+  const CellState cs = cells[c];
+  const long long b = uoff[c], n = uoff[c + 1] - b, o = cs.off;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    ox[b + k] = (T)(cs.U[0] + cs.s * ((double)cx[o + k] - cs.Us[0]));
+    oy[b + k] = (T)(cs.U[1] + cs.s * ((double)cy[o + k] - cs.Us[1]));
+    oz[b + k] = (T)(cs.U[2] + cs.s * ((double)cz[o + k] - cs.Us[2]));
+    oe[b + k] = (T)(cs.r * (double)er[o + k]);
+    ol[b + k] = lev[o + k];
+  }
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// Host side
+// ===========================================================================
+struct usp_ctx {
+  Species sp;
+  usp_config cfg;
+  int precision;
+  int ncell;
+  long long nparticles;     // real particles
+  long long nstore;         // padded storage length
+  cudaStream_t stream;
+  bool own_stream;
+  // device buffers
+  void* cx; void* cy; void* cz; void* er;
+  int* lev;
+  CellState* cells;
+  void* prm;
+  CellSums* sums;
+  Tile* tiles;
+  int ntiles;
+  long long* uoff;          // unpadded offsets (device)
+  double* macc;             // moment accumulators
+  double* mout;             // moment output (device)
+  double* levsum;
+  uint32_t* flags;
+  unsigned long long* counters;
+  std::vector<long long> h_uoff;
+  int tile;
+  int grid_collide;
+  long long step;
+  long long launches;
+  cudaGraphExec_t graph_exec;
+  int graph_steps;
+  cudaGraph_t graph;
+  long long device_bytes;
+  std::vector<void*> owned;
+};
+
+namespace {
+
+int g_last_cuda_error = 0;
+
+#define CK(x)                                            \
+  do {                                                   \
+    cudaError_t e_ = (x);                                \
+    if (e_ != cudaSuccess) {                             \
+      g_last_cuda_error = (int)e_;                       \
+      return USP_ECUDA;                                  \
+    }                                                    \
+  } while (0)
+
+void* dev_alloc(usp_ctx* c, size_t bytes) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (c->cfg.alloc) {
+    p = c->cfg.alloc(bytes, c->cfg.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) {
+    c->owned.push_back(p);
+    c->device_bytes += (long long)bytes;
+  }
+  return p;
+}
+
+void dev_free_all(usp_ctx* c) {
+  for (void* p : c->owned) {
+    if (c->cfg.alloc && c->cfg.free_) c->cfg.free_(p, c->cfg.alloc_user);
+    else if (!c->cfg.alloc) cudaFree(p);
+  }
+  c->owned.clear();
+}
+
+Species to_dev(const usp_species* s) {
+  Species d;
+  d.m = s->m; d.d_ref = s->d_ref; d.omega = s->omega; d.T_ref = s->T_ref;
+  d.c_alpha = s->c_alpha; d.theta_v = s->theta_v; d.Z_rot = s->Z_rot; d.Z_vib = s->Z_vib;
+  d.zmodel = s->zmodel; d.Zrot_inf = s->Zrot_inf; d.T_star = s->T_star; d.C1 = s->C1;
+  d.C2 = s->C2; d.sigma_vib = s->sigma_vib;
+  return d;
+}
+
+uint32_t key0(const usp_ctx* c) { return (uint32_t)(c->cfg.seed & 0xffffffffull); }
+uint32_t key1(const usp_ctx* c) { return (uint32_t)(c->cfg.seed >> 32); }
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+int build_tiles(usp_ctx* c, int tile) {
+  std::vector<Tile> t;
+  for (int i = 0; i < c->ncell; ++i) {
+    const long long n = c->h_uoff[i + 1] - c->h_uoff[i];
+    for (long long s = 0; s < n; s += tile) {
+      Tile x;
+      x.cell = i;
+      x.start = (int)s;
+      x.count = (int)std::min<long long>(tile, n - s);
+      x.pad_ = 0;
+      t.push_back(x);
+    }
+  }
+  if (t.empty()) {
+    Tile x = {0, 0, 0, 0};
+    t.push_back(x);
+  }
+  Tile* d = (Tile*)dev_alloc(c, t.size() * sizeof(Tile));
+  if (!d) return USP_ENOMEM;
+  CK(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->tiles = d;
+  c->ntiles = (int)t.size();
+  c->tile = tile;
+  return USP_OK;
+}
+
+template <typename T>
+int launch_step(usp_ctx* c) {
+  collide_kernel<T><<<c->grid_collide, kBlock, 0, c->stream>>>(
+      c->tiles, c->ntiles, (const CollideParams<T>*)c->prm, (T*)c->cx, (T*)c->cy, (T*)c->cz,
+      (T*)c->er, c->lev, c->sums, c->flags, c->counters, key0(c), key1(c));
+  CK(cudaGetLastError());
+  const int warps_per_block = 4;
+  const int blocks = (c->ncell + warps_per_block - 1) / warps_per_block;
+  finalize_kernel<T><<<blocks, 32 * warps_per_block, 0, c->stream>>>(
+      c->sp, c->ncell, c->cells, (CollideParams<T>*)c->prm, c->sums, c->lev, c->flags,
+      c->counters, key0(c), key1(c));
+  CK(cudaGetLastError());
+  return USP_OK;
+}
+
+int step_once(usp_ctx* c) {
+  return c->precision == USP_FP32 ? launch_step<float>(c) : launch_step<double>(c);
+}
+
+template <typename T>
+int compute_moments(usp_ctx* c, double* levsum) {
+  CK(cudaMemsetAsync(c->macc, 0, sizeof(double) * kMomAcc * c->ncell, c->stream));
+  for (int pass = 0; pass < 2; ++pass) {
+    moments_kernel<T><<<c->grid_collide, kBlock, 0, c->stream>>>(
+        pass, c->tiles, c->ntiles, c->cells, (const T*)c->cx, (const T*)c->cy, (const T*)c->cz,
+        (const T*)c->er, c->lev, c->macc);
+    CK(cudaGetLastError());
+  }
+  assemble_moments<<<(c->ncell + 127) / 128, 128, 0, c->stream>>>(c->sp, c->ncell, c->cells,
+                                                                   c->macc, c->mout, levsum);
+  CK(cudaGetLastError());
+  c->launches += 3;
+  return USP_OK;
+}
+
+template <typename T>
+int init_params(usp_ctx* c) {
+  int rc = compute_moments<T>(c, c->levsum);
+  if (rc) return rc;
+  const int b = (c->ncell + 127) / 128;
+  init_params_kernel<T><<<b, 128, 0, c->stream>>>(c->sp, c->ncell, c->mout, c->cells,
+                                                  (CollideParams<T>*)c->prm, c->flags, c->counters);
+  CK(cudaGetLastError());
+  init_params_finish<T><<<b, 128, 0, c->stream>>>(c->sp, c->ncell, c->levsum, c->cells,
+                                                  (CollideParams<T>*)c->prm, c->flags, c->counters);
+  CK(cudaGetLastError());
+  c->launches += 2;
+  return USP_OK;
+}
+
+int upload_state(usp_ctx* c, const void* hx, const void* hy, const void* hz, const void* he,
+                 const int32_t* hl, bool host_is_native) {
+  const long long n = c->nparticles;
+  const size_t es = host_is_native ? (c->precision == USP_FP32 ? 4 : 8) : 8;
+  // staging buffers (unpadded), reused across calls
+  static_assert(sizeof(int) == 4, "int32");
+  void* st = dev_alloc(c, (size_t)n * (4 * es + 4) + 64);
+  if (!st) return USP_ENOMEM;
+  char* p = (char*)st;
+  void* sx = p; void* sy = p + n * es; void* sz = p + 2 * n * es; void* se = p + 3 * n * es;
+  int* sl = (int*)(p + 4 * n * es);
+  CK(cudaMemcpyAsync(sx, hx, n * es, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(sy, hy, n * es, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(sz, hz, n * es, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(se, he, n * es, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(sl, hl, n * 4, cudaMemcpyHostToDevice, c->stream));
+  reset_pending<<<(c->ncell + 127) / 128, 128, 0, c->stream>>>(c->ncell, c->cells, c->sums);
+  CK(cudaGetLastError());
+  c->launches += 1;
+  dim3 grid(64, std::min(c->ncell, 65535));
+  if (c->precision == USP_FP32) {
+    if (es == 4)
+      scatter_state<float, float><<<grid, 256, 0, c->stream>>>(
+          c->ncell, c->cells, c->uoff, (const float*)sx, (const float*)sy, (const float*)sz,
+          (const float*)se, sl, (float*)c->cx, (float*)c->cy, (float*)c->cz, (float*)c->er, c->lev);
+    else
+      scatter_state<double, float><<<grid, 256, 0, c->stream>>>(
+          c->ncell, c->cells, c->uoff, (const double*)sx, (const double*)sy, (const double*)sz,
+          (const double*)se, sl, (float*)c->cx, (float*)c->cy, (float*)c->cz, (float*)c->er, c->lev);
+  } else {
+    scatter_state<double, double><<<grid, 256, 0, c->stream>>>(
+        c->ncell, c->cells, c->uoff, (const double*)sx, (const double*)sy, (const double*)sz,
+        (const double*)se, sl, (double*)c->cx, (double*)c->cy, (double*)c->cz, (double*)c->er,
+        c->lev);
+  }
+  CK(cudaGetLastError());
+  c->launches += 1;
+  CK(cudaStreamSynchronize(c->stream));
+  // release the staging buffer
+  if (c->cfg.alloc && c->cfg.free_) c->cfg.free_(st, c->cfg.alloc_user);
+  else if (!c->cfg.alloc) cudaFree(st);
+  c->owned.erase(std::find(c->owned.begin(), c->owned.end(), st));
+  c->device_bytes -= (long long)(((size_t)n * (4 * es + 4) + 64 + 255) & ~(size_t)255);
+  return USP_OK;
+}
+
+int build_graph(usp_ctx* c, int steps) {
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+  }
+  CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  int rc = USP_OK;
+  for (int i = 0; i < steps && rc == USP_OK; ++i) rc = step_once(c);
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+  if (rc != USP_OK) return rc;
+  CK(e);
+  CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
+  c->graph = g;
+  c->graph_steps = steps;
+  return USP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+double usp_tau_c(const usp_species* s, double n, double T) {
+  if (!s) return 0.0;
+  const double kPiH = 3.14159265358979323846;
+  const double kBH = 1.380649e-23;
+  const double ca = s->c_alpha, w = s->omega;
+  const double mu_ref = 5.0 * (ca + 1.0) * (ca + 2.0) * std::sqrt(s->m * kBH * s->T_ref / kPiH) /
+                        (4.0 * ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) * s->d_ref * s->d_ref);
+  const double mu = mu_ref * std::pow(T / s->T_ref, w);
+  return ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (ca + 1.0) * (ca + 2.0)) * mu /
+         (n * kBH * T);
+}
+
+const char* usp_strerror(int err) {
+  switch (err) {
+    case USP_OK: return "ok";
+    case USP_EINVAL: return "invalid argument";
+    case USP_ENOMEM: return "device allocation failed";
+    case USP_ECUDA: return "CUDA runtime error";
+    case USP_EDEVICE: return "device status word reports an error";
+    case USP_ENOTSUP: return "not supported";
+    default: return "unknown error";
+  }
+}
+
+int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config* cfg, int n_cells,
+                         const int64_t* h_offsets, const double* h_ndens, const double* h_dt,
+                         const double* h_cx, const double* h_cy, const double* h_cz,
+                         const double* h_erot, const int32_t* h_lev) {
+  if (!out || !sp || !cfg || n_cells <= 0 || !h_offsets || !h_ndens || !h_dt) return USP_EINVAL;
+  if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64) return USP_EINVAL;
+  if (h_offsets[0] != 0) return USP_EINVAL;
+  for (int i = 0; i < n_cells; ++i) {
+    if (h_offsets[i + 1] < h_offsets[i]) return USP_EINVAL;
+    if (!(h_ndens[i] > 0.0) || !(h_dt[i] > 0.0)) return USP_EINVAL;
+  }
+  const long long n = h_offsets[n_cells];
+  if (n > 0x7fffffffll) return USP_EINVAL;
+  if (n > 0 && (!h_cx || !h_cy || !h_cz || !h_erot || !h_lev)) return USP_EINVAL;
+  if (!(sp->m > 0) || !(sp->d_ref > 0) || !(sp->T_ref > 0) || !(sp->c_alpha > 0) ||
+      !(sp->theta_v > 0))
+    return USP_EINVAL;
+  *out = nullptr;
+  usp_ctx* c = new usp_ctx();
+  std::memset((void*)&c->sp, 0, sizeof(c->sp));
+  c->cfg = *cfg;
+  c->sp = to_dev(sp);
+  c->precision = cfg->precision;
+  c->ncell = n_cells;
+  c->nparticles = n;
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  c->graph_steps = 0;
+  c->step = cfg->step0;
+  c->launches = 0;
+  c->device_bytes = 0;
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+    c->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return USP_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  auto fail = [&](int rc) {
+    cudaStreamSynchronize(c->stream);
+    dev_free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return rc;
+  };
+  c->h_uoff.assign(h_offsets, h_offsets + n_cells + 1);
+  std::vector<CellState> hc(n_cells);
+  long long off = 0;
+  for (int i = 0; i < n_cells; ++i) {
+    CellState& s = hc[i];
+    std::memset(&s, 0, sizeof(s));
+    s.off = off;
+    s.N = h_offsets[i + 1] - h_offsets[i];
+    s.pid0 = (unsigned int)h_offsets[i];
+    s.step = (unsigned int)cfg->step0;
+    s.ndens = h_ndens[i];
+    s.dt = h_dt[i];
+    s.s = 1.0;
+    s.r = 1.0;
+    off += (s.N + kAlign - 1) / kAlign * kAlign;
+  }
+  c->nstore = std::max<long long>(off, kAlign);
+  const size_t es = c->precision == USP_FP32 ? 4 : 8;
+  c->cx = dev_alloc(c, c->nstore * es);
+  c->cy = dev_alloc(c, c->nstore * es);
+  c->cz = dev_alloc(c, c->nstore * es);
+  c->er = dev_alloc(c, c->nstore * es);
+  c->lev = (int*)dev_alloc(c, c->nstore * 4);
+  c->cells = (CellState*)dev_alloc(c, sizeof(CellState) * n_cells);
+  c->prm = dev_alloc(c, (c->precision == USP_FP32 ? sizeof(CollideParams<float>)
+                                                  : sizeof(CollideParams<double>)) * n_cells);
+  c->sums = (CellSums*)dev_alloc(c, sizeof(CellSums) * n_cells);
+  c->uoff = (long long*)dev_alloc(c, sizeof(long long) * (n_cells + 1));
+  c->macc = (double*)dev_alloc(c, sizeof(double) * kMomAcc * n_cells);
+  c->mout = (double*)dev_alloc(c, sizeof(double) * USP_NMOM * n_cells);
+  c->levsum = (double*)dev_alloc(c, sizeof(double) * n_cells);
+  c->flags = (uint32_t*)dev_alloc(c, 256);
+  c->counters = (unsigned long long*)dev_alloc(c, 256);
+  if (!c->cx || !c->cy || !c->cz || !c->er || !c->lev || !c->cells || !c->prm || !c->sums ||
+      !c->uoff || !c->macc || !c->mout || !c->levsum || !c->flags || !c->counters)
+    return fail(USP_ENOMEM);
+  if (cudaMemsetAsync(c->cx, 0, c->nstore * es, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->cy, 0, c->nstore * es, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->cz, 0, c->nstore * es, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->er, 0, c->nstore * es, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->lev, 0, c->nstore * 4, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->sums, 0, sizeof(CellSums) * n_cells, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->flags, 0, 256, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->counters, 0, 256, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->cells, hc.data(), sizeof(CellState) * n_cells, cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->uoff, c->h_uoff.data(), sizeof(long long) * (n_cells + 1),
+                      cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return fail(USP_ECUDA);
+  const int tile = cfg->tile > 0 ? (cfg->tile + kAlign - 1) / kAlign * kAlign : 2048;
+  int rc = build_tiles(c, tile);
+  if (rc) return fail(rc);
+  c->grid_collide = std::max(1, std::min(c->ntiles, sm_count() * 4));
+  if (n > 0) {
+    rc = upload_state(c, h_cx, h_cy, h_cz, h_erot, h_lev, false);
+    if (rc) return fail(rc);
+  }
+  rc = c->precision == USP_FP32 ? init_params<float>(c) : init_params<double>(c);
+  if (rc) return fail(rc);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(USP_ECUDA);
+  *out = c;
+  return USP_OK;
+}
+
+int usp_step(usp_ctx* c, int nsteps) {
+  if (!c || nsteps < 0) return USP_EINVAL;
+  if (nsteps == 0) return USP_OK;
+  if (!c->cfg.use_graph) {
+    for (int i = 0; i < nsteps; ++i) {
+      int rc = step_once(c);
+      if (rc) return rc;
+      c->launches += 2;
+    }
+    c->step += nsteps;
+    return USP_OK;
+  }
+  const int G = nsteps >= 16 ? 16 : 1;
+  if (!c->graph_exec || c->graph_steps != G) {
+    int rc = build_graph(c, G);
+    if (rc) return rc;
+  }
+  int done = 0;
+  while (nsteps - done >= c->graph_steps) {
+    CK(cudaGraphLaunch(c->graph_exec, c->stream));
+    c->launches += 2 * c->graph_steps;
+    done += c->graph_steps;
+  }
+  for (; done < nsteps; ++done) {
+    int rc = step_once(c);
+    if (rc) return rc;
+    c->launches += 2;
+  }
+  c->step += nsteps;
+  return USP_OK;
+}
+
+int usp_moments(usp_ctx* c, double* out, int out_is_device) {
+  if (!c || !out) return USP_EINVAL;
+  int rc = c->precision == USP_FP32 ? compute_moments<float>(c, nullptr)
+                                    : compute_moments<double>(c, nullptr);
+  if (rc) return rc;
+  if (out_is_device) {
+    CK(cudaMemcpyAsync(out, c->mout, sizeof(double) * USP_NMOM * c->ncell,
+                       cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(out, c->mout, sizeof(double) * USP_NMOM * c->ncell,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return USP_OK;
+}
+
+int usp_get_particles(usp_ctx* c, double* hx, double* hy, double* hz, double* he, int32_t* hl) {
+  if (!c || !hx || !hy || !hz || !he || !hl) return USP_EINVAL;
+  const long long n = c->nparticles;
+  if (n == 0) return USP_OK;
+  double* st = (double*)dev_alloc(c, (size_t)n * 36 + 64);
+  if (!st) return USP_ENOMEM;
+  double* ox = st; double* oy = st + n; double* oz = st + 2 * n; double* oe = st + 3 * n;
+  int* ol = (int*)(st + 4 * n);
+  dim3 grid(64, std::min(c->ncell, 65535));
+  if (c->precision == USP_FP32)
+    gather_state<float><<<grid, 256, 0, c->stream>>>(c->ncell, c->cells, c->uoff,
+        (const float*)c->cx, (const float*)c->cy, (const float*)c->cz, (const float*)c->er,
+        c->lev, ox, oy, oz, oe, ol);
+  else
+    gather_state<double><<<grid, 256, 0, c->stream>>>(c->ncell, c->cells, c->uoff,
+        (const double*)c->cx, (const double*)c->cy, (const double*)c->cz, (const double*)c->er,
+        c->lev, ox, oy, oz, oe, ol);
+  CK(cudaGetLastError());
+  c->launches += 1;
+  CK(cudaMemcpyAsync(hx, ox, n * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hy, oy, n * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hz, oz, n * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(he, oe, n * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hl, ol, n * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->cfg.alloc && c->cfg.free_) c->cfg.free_(st, c->cfg.alloc_user);
+  else if (!c->cfg.alloc) cudaFree(st);
+  c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void*)st));
+  c->device_bytes -= (long long)(((size_t)n * 36 + 64 + 255) & ~(size_t)255);
+  return USP_OK;
+}
+
+int usp_set_particles(usp_ctx* c, const double* hx, const double* hy, const double* hz,
+                      const double* he, const int32_t* hl) {
+  if (!c || !hx || !hy || !hz || !he || !hl) return USP_EINVAL;
+  int rc = upload_state(c, hx, hy, hz, he, hl, false);
+  if (rc) return rc;
+  return c->precision == USP_FP32 ? init_params<float>(c) : init_params<double>(c);
+}
+
+int usp_step_host(usp_ctx* c, const void* hx, const void* hy, const void* hz, const void* he,
+                  const int32_t* hl, int nsteps, double* h_moments, void* ox, void* oy, void* oz,
+                  void* oe, int32_t* ol) {
+  if (!c || !hx || !hy || !hz || !he || !hl || !h_moments || nsteps < 0) return USP_EINVAL;
+  int rc = upload_state(c, hx, hy, hz, he, hl, true);
+  if (rc) return rc;
+  rc = c->precision == USP_FP32 ? init_params<float>(c) : init_params<double>(c);
+  if (rc) return rc;
+  rc = usp_step(c, nsteps);
+  if (rc) return rc;
+  rc = usp_moments(c, h_moments, 0);
+  if (rc) return rc;
+  if (ox && oy && oz && oe && ol) {
+    const long long n = c->nparticles;
+    const size_t es = c->precision == USP_FP32 ? 4 : 8;
+    void* st = dev_alloc(c, (size_t)n * (4 * es + 4) + 64);
+    if (!st) return USP_ENOMEM;
+    char* p = (char*)st;
+    dim3 grid(64, std::min(c->ncell, 65535));
+    if (c->precision == USP_FP32)
+      gather_state_native<float><<<grid, 256, 0, c->stream>>>(c->ncell, c->cells, c->uoff,
+          (const float*)c->cx, (const float*)c->cy, (const float*)c->cz, (const float*)c->er,
+          c->lev, (float*)p, (float*)(p + n * es), (float*)(p + 2 * n * es),
+          (float*)(p + 3 * n * es), (int*)(p + 4 * n * es));
+    else
+      gather_state_native<double><<<grid, 256, 0, c->stream>>>(c->ncell, c->cells, c->uoff,
+          (const double*)c->cx, (const double*)c->cy, (const double*)c->cz, (const double*)c->er,
+          c->lev, (double*)p, (double*)(p + n * es), (double*)(p + 2 * n * es),
+          (double*)(p + 3 * n * es), (int*)(p + 4 * n * es));
+    CK(cudaGetLastError());
+    c->launches += 1;
+    CK(cudaMemcpyAsync(ox, p, n * es, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(oy, p + n * es, n * es, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(oz, p + 2 * n * es, n * es, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(oe, p + 3 * n * es, n * es, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(ol, p + 4 * n * es, n * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->cfg.alloc && c->cfg.free_) c->cfg.free_(st, c->cfg.alloc_user);
+    else if (!c->cfg.alloc) cudaFree(st);
+    c->owned.erase(std::find(c->owned.begin(), c->owned.end(), st));
+    c->device_bytes -= (long long)(((size_t)n * (4 * es + 4) + 64 + 255) & ~(size_t)255);
+  }
+  return USP_OK;
+}
+
+int usp_status(usp_ctx* c, uint32_t* flags, int64_t* counters, int reset) {
+  if (!c) return USP_EINVAL;
+  uint32_t f = 0;
+  unsigned long long cnt[NCOUNTERS];
+  CK(cudaMemcpyAsync(&f, c->flags, 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (flags) *flags = f;
+  if (counters)
+    for (int i = 0; i < NCOUNTERS; ++i) counters[i] = (int64_t)cnt[i];
+  if (reset) {
+    CK(cudaMemsetAsync(c->flags, 0, 256, c->stream));
+    CK(cudaMemsetAsync(c->counters, 0, 256, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  const uint32_t err = F_CHOL_FAIL_AFTER_FIX | F_A_NONPOS | F_SAMPLER_UNDERFLOW | F_BOUNDS;
+  return (f & err) ? USP_EDEVICE : USP_OK;
+}
+
+int usp_sync(usp_ctx* c) {
+  if (!c) return USP_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  return USP_OK;
+}
+
+int usp_info(usp_ctx* c, int64_t* np, int* nc, int* prec, int64_t* step, int* tile,
+             int64_t* bytes) {
+  if (!c) return USP_EINVAL;
+  if (np) *np = c->nparticles;
+  if (nc) *nc = c->ncell;
+  if (prec) *prec = c->precision;
+  if (step) *step = c->step;
+  if (tile) *tile = c->tile;
+  if (bytes) *bytes = c->device_bytes;
+  return USP_OK;
+}
+
+int64_t usp_launch_count(usp_ctx* c) { return c ? c->launches : -1; }
+
+void usp_destroy(usp_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    cudaGraphDestroy(c->graph);
+  }
+  dev_free_all(c);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

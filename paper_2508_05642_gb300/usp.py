@@ -1,0 +1,278 @@
+"""Thin ctypes binding of ``libusp.so`` (C ABI in ``include/usp.h``).
+
+Argument marshalling only: every step of the particle update runs in the CUDA
+kernels of the library.  The functions keep the C names.  Importing this
+module never falls back to anything: if the library cannot be built or loaded
+the call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+USP_OK, USP_EINVAL, USP_ENOMEM, USP_ECUDA, USP_EDEVICE, USP_ENOTSUP = 0, -1, -2, -3, -4, -5
+USP_FP64, USP_FP32 = 0, 1
+USP_NMOM = 22
+USP_NCOUNTERS = 8
+
+F_PB_CLAMP = 0x01
+F_CHOL_FAIL_AFTER_FIX = 0x02
+F_NEG_RADICAND = 0x04
+F_VIB_LOOP_CAP = 0x08
+F_TREL_CLAMP = 0x10
+F_SAMPLER_CAP = 0x20
+F_A_NONPOS = 0x40
+F_SAMPLER_UNDERFLOW = 0x80
+F_BOUNDS = 0x200
+
+C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, \
+    C_INTERP_FALLBACK, C_SKIPPED_CELLS = range(8)
+
+EXPORTED = ["usp_tau_c", "usp_strerror", "usp_init_homogeneous", "usp_step", "usp_moments",
+            "usp_get_particles", "usp_set_particles", "usp_step_host", "usp_status", "usp_sync",
+            "usp_info", "usp_launch_count", "usp_destroy"]
+
+
+class usp_species(C.Structure):
+    _fields_ = [("m", C.c_double), ("d_ref", C.c_double), ("omega", C.c_double),
+                ("T_ref", C.c_double), ("c_alpha", C.c_double), ("theta_v", C.c_double),
+                ("Z_rot", C.c_double), ("Z_vib", C.c_double), ("zmodel", C.c_int),
+                ("Zrot_inf", C.c_double), ("T_star", C.c_double), ("C1", C.c_double),
+                ("C2", C.c_double), ("sigma_vib", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class usp_config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("seed", C.c_uint64), ("step0", C.c_int64),
+                ("stream", C.c_void_p), ("use_graph", C.c_int), ("tile", C.c_int),
+                ("alloc", ALLOC_FN), ("free_", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+_D = C.POINTER(C.c_double)
+_I32 = C.POINTER(C.c_int32)
+_I64 = C.POINTER(C.c_int64)
+_U32 = C.POINTER(C.c_uint32)
+_CTX = C.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Build (if stale) and load libusp.so; raises if either fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            L.usp_tau_c.argtypes = [C.POINTER(usp_species), C.c_double, C.c_double]
+            L.usp_tau_c.restype = C.c_double
+            L.usp_strerror.argtypes = [C.c_int]
+            L.usp_strerror.restype = C.c_char_p
+            L.usp_init_homogeneous.argtypes = [C.POINTER(_CTX), C.POINTER(usp_species),
+                                               C.POINTER(usp_config), C.c_int, _I64, _D, _D,
+                                               _D, _D, _D, _D, _I32]
+            L.usp_step.argtypes = [_CTX, C.c_int]
+            L.usp_moments.argtypes = [_CTX, C.c_void_p, C.c_int]
+            L.usp_get_particles.argtypes = [_CTX, _D, _D, _D, _D, _I32]
+            L.usp_set_particles.argtypes = [_CTX, _D, _D, _D, _D, _I32]
+            L.usp_step_host.argtypes = [_CTX, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        _I32, C.c_int, _D, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, _I32]
+            L.usp_status.argtypes = [_CTX, _U32, _I64, C.c_int]
+            L.usp_sync.argtypes = [_CTX]
+            L.usp_info.argtypes = [_CTX, _I64, C.POINTER(C.c_int), C.POINTER(C.c_int), _I64,
+                                   C.POINTER(C.c_int), _I64]
+            L.usp_launch_count.argtypes = [_CTX]
+            L.usp_launch_count.restype = C.c_int64
+            L.usp_destroy.argtypes = [_CTX]
+            L.usp_destroy.restype = None
+            _lib = L
+    return _lib
+
+
+class USPError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: {usp_strerror(code)} ({code})")
+        self.code = code
+
+
+def _check(rc, where):
+    if rc != USP_OK:
+        raise USPError(rc, where)
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def usp_strerror(code: int) -> str:
+    return lib().usp_strerror(code).decode()
+
+
+def make_species(d: dict) -> usp_species:
+    s = usp_species()
+    for k, _ in usp_species._fields_:
+        setattr(s, k, d.get(k, 0))
+    return s
+
+
+def usp_tau_c(species: dict, n: float, T: float) -> float:
+    return lib().usp_tau_c(C.byref(make_species(species)), n, T)
+
+
+class Context:
+    """Owns one ``usp_ctx``; methods map 1:1 onto the C entry points."""
+
+    def __init__(self, handle, n_particles, n_cells, precision, keepalive):
+        self.h = handle
+        self.n_particles = n_particles
+        self.n_cells = n_cells
+        self.precision = precision
+        self._keep = keepalive
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            lib().usp_destroy(self.h)
+            self.h = None
+
+
+def usp_init_homogeneous(species: dict, offsets, ndens, dt, cx, cy, cz, erot, lev, *,
+                         precision=USP_FP32, seed=1, step0=0, stream=None, use_graph=True,
+                         tile=0, allocator=None) -> Context:
+    """Create a context for independent homogeneous cells; arrays are host numpy."""
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nd = np.ascontiguousarray(ndens, dtype=np.float64)
+    dtv = np.ascontiguousarray(dt, dtype=np.float64)
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    cx, cy, cz, erot = f(cx), f(cy), f(cz), f(erot)
+    lev = np.ascontiguousarray(lev, dtype=np.int32)
+    cfg = usp_config()
+    cfg.precision = precision
+    cfg.seed = seed
+    cfg.step0 = step0
+    cfg.stream = stream or None
+    cfg.use_graph = 1 if use_graph else 0
+    cfg.tile = tile
+    keep = []
+    if allocator is not None:
+        a_fn, f_fn, user = allocator
+        cfg.alloc = a_fn
+        cfg.free_ = f_fn
+        cfg.alloc_user = user
+        keep += [a_fn, f_fn]
+    sp = make_species(species)
+    h = _CTX()
+    rc = lib().usp_init_homogeneous(C.byref(h), C.byref(sp), C.byref(cfg), len(off) - 1,
+                                    _p(off, C.c_int64), _p(nd, C.c_double), _p(dtv, C.c_double),
+                                    _p(cx, C.c_double), _p(cy, C.c_double), _p(cz, C.c_double),
+                                    _p(erot, C.c_double), _p(lev, C.c_int32))
+    _check(rc, "usp_init_homogeneous")
+    return Context(h, int(off[-1]), len(off) - 1, precision, keep)
+
+
+def usp_step(ctx: Context, nsteps: int):
+    _check(lib().usp_step(ctx.h, nsteps), "usp_step")
+
+
+def usp_moments(ctx: Context, out=None, out_is_device=False) -> np.ndarray:
+    """Per-cell moments (USP_NMOM x n_cells); host numpy unless a device
+    pointer (int) is given with out_is_device=True."""
+    if out_is_device:
+        _check(lib().usp_moments(ctx.h, C.c_void_p(out), 1), "usp_moments")
+        return None
+    o = np.zeros((USP_NMOM, ctx.n_cells), dtype=np.float64)
+    _check(lib().usp_moments(ctx.h, o.ctypes.data_as(C.c_void_p), 0), "usp_moments")
+    return o
+
+
+def usp_get_particles(ctx: Context):
+    n = ctx.n_particles
+    out = [np.zeros(n) for _ in range(4)] + [np.zeros(n, dtype=np.int32)]
+    _check(lib().usp_get_particles(ctx.h, *[_p(a, C.c_double) for a in out[:4]],
+                                   _p(out[4], C.c_int32)), "usp_get_particles")
+    return out
+
+
+def usp_set_particles(ctx: Context, cx, cy, cz, erot, lev):
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    arrs = [f(cx), f(cy), f(cz), f(erot)]
+    lv = np.ascontiguousarray(lev, dtype=np.int32)
+    _check(lib().usp_set_particles(ctx.h, *[_p(a, C.c_double) for a in arrs],
+                                   _p(lv, C.c_int32)), "usp_set_particles")
+
+
+def usp_step_host(ctx: Context, cx, cy, cz, erot, lev, nsteps: int, moments_out: np.ndarray,
+                  out=None):
+    """End-to-end call on host buffers (ideally pinned); arrays in the
+    context's precision.  ``out`` = (cx, cy, cz, erot, lev) host arrays or None."""
+    ptr = lambda a: C.c_void_p(a.ctypes.data) if isinstance(a, np.ndarray) else C.c_void_p(a)
+    lv = lev.ctypes.data_as(_I32) if isinstance(lev, np.ndarray) else C.cast(lev, _I32)
+    o = [None] * 5 if out is None else out
+    olv = None if o[4] is None else (o[4].ctypes.data_as(_I32) if isinstance(o[4], np.ndarray)
+                                     else C.cast(o[4], _I32))
+    rc = lib().usp_step_host(ctx.h, ptr(cx), ptr(cy), ptr(cz), ptr(erot), lv, nsteps,
+                             _p(moments_out, C.c_double),
+                             *(None if a is None else ptr(a) for a in o[:4]), olv)
+    _check(rc, "usp_step_host")
+
+
+def usp_status(ctx: Context, reset=False):
+    f = C.c_uint32(0)
+    cnt = np.zeros(USP_NCOUNTERS, dtype=np.int64)
+    rc = lib().usp_status(ctx.h, C.byref(f), _p(cnt, C.c_int64), 1 if reset else 0)
+    if rc not in (USP_OK, USP_EDEVICE):
+        _check(rc, "usp_status")
+    return f.value, cnt
+
+
+def usp_sync(ctx: Context):
+    _check(lib().usp_sync(ctx.h), "usp_sync")
+
+
+def usp_info(ctx: Context) -> dict:
+    np_, st, b = C.c_int64(), C.c_int64(), C.c_int64()
+    nc, pr, tl = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().usp_info(ctx.h, C.byref(np_), C.byref(nc), C.byref(pr), C.byref(st),
+                          C.byref(tl), C.byref(b)), "usp_info")
+    return dict(n_particles=np_.value, n_cells=nc.value, precision=pr.value, step=st.value,
+                tile=tl.value, device_bytes=b.value)
+
+
+def usp_launch_count(ctx: Context) -> int:
+    return lib().usp_launch_count(ctx.h)
+
+
+def usp_destroy(ctx: Context):
+    ctx.destroy()
+
+
+def torch_allocator():
+    """Allocator callbacks routing the library's device memory through
+    PyTorch's caching allocator on the current device and stream."""
+    import torch
+    dev = torch.cuda.current_device()
+
+    @ALLOC_FN
+    def _alloc(nbytes, user):
+        return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+
+    @FREE_FN
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return _alloc, _free, None

@@ -1,0 +1,234 @@
+"""GPU parity of the homogeneous USP-FPM step (CUDA library via the C ABI)
+against the FP64 CPU oracle on the same seeded inputs.
+
+Bars (from the method's stated accuracy targets): cell moments within 1e-5
+relative (temperatures, Pi) or 1e-5 of the thermal scale (velocities, heat
+fluxes); vibrational levels mismatching in fewer than 1e-5 of the particles;
+per-cell momentum and total energy conserved to 1e-12 relative in the FP64
+form.  In the FP64 form both sides take every discrete decision in double, so
+the states must agree to rounding; in the FP32 form the single-step state is
+compared within FP32 rounding of the particle arithmetic.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2508_05642_gb300 import inputs as I
+from paper_2508_05642_gb300 import usp
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_dt(w):
+    sp = O.species(**w.species)
+    return np.array([w.dt_over_tau_c * O.tau_c(sp, w.ndens[i], w.T_nominal[i, 0])
+                     for i in range(w.n_cells)])
+
+
+def _gpu_dt(w):
+    return np.array([w.dt_over_tau_c * usp.usp_tau_c(w.species, w.ndens[i], w.T_nominal[i, 0])
+                     for i in range(w.n_cells)])
+
+
+def _run_pair(w, steps, precision, tile=0, use_graph=True, particles=None):
+    p = particles if particles is not None else w.particles
+    form = 1 if precision == usp.USP_FP32 else 0
+    if form == 1:
+        p = p.astype_f32_exact()
+    st = O.State.from_arrays(p.cx, p.cy, p.cz, p.erot, p.lev)
+    sp = O.species(**w.species)
+    ofl, ocnt = O.homog_step(sp, form, w.seed, 0, steps, w.offsets, w.ndens, _oracle_dt(w), st)
+    ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, _gpu_dt(w), p.cx, p.cy, p.cz,
+                                   p.erot, p.lev, precision=precision, seed=w.seed, tile=tile,
+                                   use_graph=use_graph)
+    usp.usp_step(ctx, steps)
+    gm = usp.usp_moments(ctx)
+    gs = usp.usp_get_particles(ctx)
+    gfl, gcnt = usp.usp_status(ctx)
+    om = O.moments(sp, w.offsets, st)
+    return dict(ctx=ctx, gm=gm, gs=gs, gfl=gfl, gcnt=gcnt, om=om, ost=st, ofl=ofl, ocnt=ocnt, sp=sp)
+
+
+def _check_moments(om, gm, sp, rel=1e-5, mask=None):
+    R = O.R(sp)
+    ok = om[0] >= 2 if mask is None else mask
+    assert np.array_equal(om[0], gm[0])
+    T = om[4][ok]
+    vth = np.sqrt(R * T)
+    for f in (4, 5):
+        np.testing.assert_allclose(gm[f][ok], om[f][ok], rtol=rel, atol=0)
+    # T_vib: absolute tolerance scaled by theta_v (T_vib -> 0 at low excitation)
+    np.testing.assert_allclose(gm[6][ok], om[6][ok], rtol=rel, atol=rel * 10)
+    for f in (1, 2, 3):
+        assert np.all(np.abs(gm[f][ok] - om[f][ok]) <= rel * vth)
+    for f in range(7, 13):
+        assert np.all(np.abs(gm[f][ok] - om[f][ok]) <= rel * R * T)
+    for f in range(13, 22):
+        scale = vth ** 3 if f < 19 else vth * R * sp.theta_v * max(1.0, 1.0)
+        assert np.all(np.abs(gm[f][ok] - om[f][ok]) <= rel * scale * 10)
+
+
+def test_fp64_single_cell_full_run_matches_oracle():
+    """Config-1 workload (1 cell, 20,000 particles, 200 steps, FP64 plain)."""
+    w = I.homogeneous_single(N=20000, steps=200)
+    r = _run_pair(w, 200, usp.USP_FP64)
+    _check_moments(r["om"], r["gm"], r["sp"])
+    gx, gy, gz, ge, gl = r["gs"]
+    st = r["ost"]
+    R = O.R(r["sp"])
+    vth = math.sqrt(R * r["om"][4, 0])
+    assert np.mean(gl != st.lev) < 1e-5
+    if np.all(gl == st.lev):
+        assert np.max(np.abs(gx - st.cx)) < 1e-8 * vth
+        assert np.max(np.abs(ge - st.erot)) < 1e-8 * R * r["om"][5, 0]
+    assert r["gfl"] == r["ofl"]
+    assert r["gcnt"][usp.C_CHOL_FIX] == r["ocnt"][O.C_CHOL_FIX] // 20000
+
+
+def test_fp64_batched_multi_tile_ragged_matches_oracle():
+    """Many cells of uneven size; small tiles so cells span several tiles
+    with ragged tails; includes cells of 0, 1, 2 and 3 particles."""
+    w = I.batched_instances(seed=7, n_inst=40, nmin=50, nmax=3000, steps=10)
+    counts = np.diff(w.offsets)
+    counts[:4] = [0, 1, 2, 3]
+    off = np.zeros(len(counts) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(counts)
+    rng = np.random.default_rng(8)
+    sp = w.species
+    parts = [I.equilibrium_particles(rng, int(n), sp["m"], sp["theta_v"], T_tr=w.T_nominal[i, 0],
+                                     T_rot=w.T_nominal[i, 1], T_vib=w.T_nominal[i, 2])
+             for i, n in enumerate(counts)]
+    cat = lambda k: np.concatenate([getattr(p, k) for p in parts])
+    w.offsets = off
+    w.particles = I.Particles(cat("cx"), cat("cy"), cat("cz"), cat("erot"), cat("lev"))
+    r = _run_pair(w, 10, usp.USP_FP64, tile=256)
+    _check_moments(r["om"], r["gm"], r["sp"])
+    gl = r["gs"][4]
+    assert np.mean(gl != r["ost"].lev) < 1e-5
+    # cells with fewer than two particles are untouched
+    for i in range(2):
+        b, e = off[i], off[i + 1]
+        assert np.array_equal(r["gs"][0][b:e], w.particles.cx[b:e])
+
+
+def test_fp32_single_step_matches_oracle():
+    """FP32 state form, one step from the identical state (the oracle takes
+    the level decisions in float, as the kernel does)."""
+    w = I.batched_instances(seed=9, n_inst=24, nmin=500, nmax=20000, steps=1)
+    r = _run_pair(w, 1, usp.USP_FP32, tile=1024)
+    _check_moments(r["om"], r["gm"], r["sp"])
+    gx, gy, gz, ge, gl = r["gs"]
+    st = r["ost"]
+    assert np.mean(gl != st.lev) < 1e-5
+    R = O.R(r["sp"])
+    for i in range(w.n_cells):
+        b, e = w.offsets[i], w.offsets[i + 1]
+        vth = math.sqrt(R * r["om"][4, i])
+        assert np.max(np.abs(gx[b:e] - st.cx[b:e])) < 2e-5 * vth
+        assert np.max(np.abs(gz[b:e] - st.cz[b:e])) < 2e-5 * vth
+        eth = R * r["om"][5, i]
+        assert np.max(np.abs(ge[b:e] - st.erot[b:e])) < 2e-5 * eth * 20
+
+
+def test_fp32_multi_step_field_error_is_small():
+    """Over 20 steps the FP32 form's cell temperatures stay within 1e-4 of
+    the FP64 oracle (the stated FP32-form field error; trajectories
+    de-correlate only through rare level flips)."""
+    w = I.batched_instances(seed=10, n_inst=16, nmin=2000, nmax=20000, steps=20)
+    r = _run_pair(w, 20, usp.USP_FP32)
+    om, gm = r["om"], r["gm"]
+    for f in (4, 5):
+        assert np.max(np.abs(gm[f] / om[f] - 1)) < 1e-4
+    assert np.max(np.abs(gm[6] - om[6]) / np.maximum(om[6], 100.0)) < 1e-3
+
+
+def test_conservation_on_gpu_fp64():
+    w = I.batched_instances(seed=11, n_inst=8, nmin=1000, nmax=5000, steps=0)
+    sp = O.species(**w.species)
+    R = O.R(sp)
+    p = w.particles
+    ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, _gpu_dt(w), p.cx, p.cy, p.cz,
+                                   p.erot, p.lev, precision=usp.USP_FP64, seed=3)
+
+    def tot(x, y, z, e, l):
+        out = []
+        for i in range(w.n_cells):
+            b, f = w.offsets[i], w.offsets[i + 1]
+            out.append((np.array([x[b:f].sum(), y[b:f].sum(), z[b:f].sum()]),
+                        (0.5 * (x[b:f] ** 2 + y[b:f] ** 2 + z[b:f] ** 2) + e[b:f]
+                         + R * sp.theta_v * l[b:f]).sum(),
+                        np.sqrt((x[b:f] ** 2).sum())))
+        return out
+
+    t0 = tot(p.cx, p.cy, p.cz, p.erot, p.lev)
+    usp.usp_step(ctx, 25)
+    t1 = tot(*usp.usp_get_particles(ctx))
+    for (m0, e0, v0), (m1, e1, _) in zip(t0, t1):
+        assert np.max(np.abs(m1 - m0)) <= 1e-11 * v0
+        assert e1 == pytest.approx(e0, rel=1e-12)
+
+
+def test_graph_and_eager_paths_agree_and_are_deterministic():
+    w = I.batched_instances(seed=12, n_inst=8, nmin=500, nmax=4000, steps=0)
+    p = w.particles
+    outs = []
+    for g in (True, False, True):
+        ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, _gpu_dt(w), p.cx, p.cy,
+                                       p.cz, p.erot, p.lev, precision=usp.USP_FP32, seed=5,
+                                       use_graph=g)
+        usp.usp_step(ctx, 37)
+        outs.append(usp.usp_get_particles(ctx))
+        assert usp.usp_launch_count(ctx) >= 74
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    for a, b in zip(outs[0], outs[2]):
+        assert np.array_equal(a, b)
+
+
+def test_step_host_matches_device_path():
+    w = I.batched_instances(seed=13, n_inst=6, nmin=500, nmax=3000, steps=0)
+    p = w.particles.astype_f32_exact()
+    dt = _gpu_dt(w)
+    ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, dt, p.cx, p.cy, p.cz, p.erot,
+                                   p.lev, precision=usp.USP_FP32, seed=4)
+    usp.usp_step(ctx, 5)
+    ref = usp.usp_moments(ctx)
+    ctx2 = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, dt, p.cx, p.cy, p.cz, p.erot,
+                                    p.lev, precision=usp.USP_FP32, seed=4)
+    f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    mom = np.zeros((usp.USP_NMOM, w.n_cells))
+    usp.usp_step_host(ctx2, f32(p.cx), f32(p.cy), f32(p.cz), f32(p.erot), p.lev, 5, mom)
+    np.testing.assert_allclose(mom, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_pb_clamp_flag_matches_oracle():
+    """A time step close to the limit 2 mu/p = Pr dt drives alpha to 0 and
+    p_B = (1 + e_rel)(1 - alpha^2) above 1 (Sec. 3.A.2): both sides clamp the
+    binomial and report it."""
+    w = I.homogeneous_single(N=5000, T_tr=6000.0, T_rot=6000.0, T_vib=6000.0, steps=1)
+    sp = O.species(**w.species)
+    T = 6000.0
+    mu_p = O.mu(sp, T) / (1e23 * 1.380649e-23 * T)
+    w.dt_over_tau_c = 0.97 * 2 * mu_p / O.prandtl(sp, T) / O.tau_c(sp, 1e23, T)
+    r = _run_pair(w, 1, usp.USP_FP64)
+    assert r["ofl"] & O.F_PB_CLAMP
+    assert r["gfl"] & usp.F_PB_CLAMP
+    assert r["gcnt"][usp.C_PB_CLAMP] == r["ocnt"][O.C_PB_CLAMP]
+    assert np.mean(r["gs"][4] != r["ost"].lev) < 1e-5
+
+
+def test_torch_allocator_path():
+    torch = pytest.importorskip("torch")
+    w = I.batched_instances(seed=14, n_inst=4, nmin=500, nmax=2000, steps=0)
+    p = w.particles
+    alloc = usp.torch_allocator()
+    ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, _gpu_dt(w), p.cx, p.cy, p.cz,
+                                   p.erot, p.lev, precision=usp.USP_FP32, seed=2,
+                                   allocator=alloc,
+                                   stream=torch.cuda.current_stream().cuda_stream)
+    usp.usp_step(ctx, 3)
+    m = usp.usp_moments(ctx)
+    assert np.all(m[4] > 0)
+    ctx.destroy()
