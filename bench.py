@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched homogeneous USP-FPM step on GB300.
+
+Workload: 4096 independent single-cell N2 relaxation instances, particle
+counts log-uniform in [1e3, 2e5] (~1.5e8 particles), T_tr ~ U[2000, 20000] K,
+T_rot, T_vib ~ U[300, 3000] K, n = 1e23 m^-3, dt_i = 0.5 tau_c, FP32 particle
+state with FP64 cell sums and coefficients.  Synthetic, seeded inputs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line is printed by rank 0.  ``value`` is particle-steps/s of the whole
+job (all ranks; each rank runs its own 4096 instances: weak scaling, no
+collective on the data path), from CUDA events on the library's stream with the
+state resident in HBM.  ``e2e`` repeats the measurement through the C-ABI call
+on pinned host buffers (state uploaded and moments read back every step).
+``roofline`` rates the dominant kernel (the particle collide pass) against the
+measured HBM copy bandwidth; ``cpu_baseline`` times the FP64 CPU oracle on a
+bounded sample of the same workload.  ``--impl reference`` times that oracle
+alone (the comparison arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("particle-steps/s on 1 GB300 and % HBM roofline; FP32-batched vs plain FP64 form "
+          "at stated error")
+UNIT = "particle-steps/s"
+N_INST = 4096
+CPU_SAMPLE_INST = 64          # instances of the bounded oracle sample
+BYTES_PER_PARTICLE_STEP = {"f32": 40, "f64": 72}   # 2 x state (read + write)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink particle counts (debug only; the default is the full workload)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampler running across the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        loaded = [x for x in sm if smax and x > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2508_05642_gb300", "csrc", "*"))):
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n_particles):
+    """DRAM bytes per collide launch from the committed ncu summary, scaled to
+    this launch's particle count; None if the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", "collide_fp32_batched4096.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha256_16") != source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_particle"]) * n_particles
+    except (KeyError, ValueError):
+        return None
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(rank, scale):
+    from paper_2508_05642_gb300 import inputs as I
+    return I.batched_instances(seed=1 + 1000 * rank, n_inst=N_INST, steps=500, scale=scale)
+
+
+def config_of(w, steps, precision="f32"):
+    return {"workload": w.name + (", FP32 state / FP64 cell sums" if precision == "f32"
+                                  else ", FP64 plain"),
+            "instances": w.n_cells, "particles_per_gpu": w.n_particles,
+            "steps_timed": steps, "dt": "0.5 tau_c per instance",
+            "l2": "inputs larger than L2 (state %.1f GB per GPU)" % (w.n_particles * 20 / 1e9),
+            "parallelism": "independent instances per GPU (weak scaling, no collective)"}
+
+
+def cpu_baseline(w, target_s, fixed_steps=None):
+    """Time the FP64 CPU oracle (as it stands) on the first CPU_SAMPLE_INST
+    instances of the workload; returns (rate, cores, sample description)."""
+    import numpy as np
+    from oracle import oracle as O
+    k = min(CPU_SAMPLE_INST, w.n_cells)
+    off = w.offsets[:k + 1].copy()
+    n = int(off[-1])
+    p = w.particles
+    st = O.State.from_arrays(p.cx[:n], p.cy[:n], p.cz[:n], p.erot[:n], p.lev[:n])
+    sp = O.species(**w.species)
+    dt = np.array([w.dt_over_tau_c * O.tau_c(sp, w.ndens[i], w.T_nominal[i, 0]) for i in range(k)])
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    O.homog_step(sp, 1, w.seed, 0, 1, off, w.ndens[:k], dt, st)
+    t1 = time.perf_counter() - t0
+    steps = fixed_steps or max(1, min(500, int(target_s / max(t1, 1e-4))))
+    t0 = time.perf_counter()
+    O.homog_step(sp, 1, w.seed, 1, steps, off, w.ndens[:k], dt, st)
+    el = time.perf_counter() - t0
+    rate = n * steps / el
+    return rate, cores, el, (f"first {k} of {w.n_cells} instances ({n} particles), {steps} steps, "
+                             f"FP64 oracle (float-decision form), {el:.1f} s")
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = workload(0, args.scale)
+    import numpy as np
+    from oracle import oracle as O
+    k = min(CPU_SAMPLE_INST, w.n_cells)
+    off = w.offsets[:k + 1].copy()
+    n = int(off[-1])
+    p = w.particles
+    st = O.State.from_arrays(p.cx[:n], p.cy[:n], p.cz[:n], p.erot[:n], p.lev[:n])
+    sp = O.species(**w.species)
+    dt = np.array([w.dt_over_tau_c * O.tau_c(sp, w.ndens[i], w.T_nominal[i, 0]) for i in range(k)])
+    O.homog_step(sp, 1, w.seed, 0, args.warmup, off, w.ndens[:k], dt, st)
+    t0 = time.perf_counter()
+    O.homog_step(sp, 1, w.seed, args.warmup, args.steps, off, w.ndens[:k], dt, st)
+    el = time.perf_counter() - t0
+    rate = n * args.steps / el
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"first {k} of {w.n_cells} instances ({n} particles) per step"
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, args.steps),
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2508_05642_gb300 import usp
+
+    torch.cuda.set_device(local)
+    usp.usp_select_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    w = workload(rank, args.scale)
+    dt = np.array([w.dt_over_tau_c * usp.usp_tau_c(w.species, w.ndens[i], w.T_nominal[i, 0])
+                   for i in range(w.n_cells)])
+    p = w.particles
+    stream = torch.cuda.Stream()
+    ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, dt, p.cx, p.cy, p.cz, p.erot,
+                                   p.lev, precision=usp.USP_FP32, seed=w.seed,
+                                   stream=stream.cuda_stream, use_graph=True)
+    N = w.n_particles
+    usp.usp_step(ctx, args.warmup)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, graph replay, inputs resident in HBM ------
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = usp.usp_launch_count(ctx)
+    e0.record(stream)
+    usp.usp_step(ctx, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = usp.usp_launch_count(ctx) - l0
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    total_particles = sum_over_ranks(float(N))
+    value = total_particles * args.steps / (ms / 1e3)
+
+    # ---- same K steps with every kernel bracketed by events (roofline) ----
+    usp.usp_profile_enable(ctx, True)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    usp.usp_step(ctx, args.steps)
+    f1.record(stream)
+    kms, kn = usp.usp_profile_read(ctx)
+    usp.usp_profile_enable(ctx, False)
+    ms_prof = f0.elapsed_time(f1)
+    collide_ms = kms[0] / max(1, kn[0])
+    finalize_ms = kms[1] / max(1, kn[1])
+    alg_bytes = BYTES_PER_PARTICLE_STEP["f32"] * N
+    peak, peak_kind = hbm_peak()
+    achieved = alg_bytes / (collide_ms / 1e3) / 1e9
+    flags, counters = usp.usp_status(ctx)
+
+    # ---- end to end through the C ABI on pinned host buffers ---------------
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda a, dt_: torch.from_numpy(np.ascontiguousarray(a, dtype=dt_)).pin_memory()
+        hx, hy, hz, he = (pin(a, np.float32) for a in (p.cx, p.cy, p.cz, p.erot))
+        hl = pin(p.lev, np.int32)
+        mom = np.zeros((usp.USP_NMOM, w.n_cells))
+        args_h = [hx.data_ptr(), hy.data_ptr(), hz.data_ptr(), he.data_ptr(), hl.data_ptr()]
+        usp.usp_step_host(ctx, *args_h, 1, mom)     # warm-up of the path
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            usp.usp_step_host(ctx, *args_h, 1, mom)
+        el = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": total_particles * args.e2e_steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(N * 20), "d2h_bytes_per_step": int(mom.nbytes),
+               "ms_per_step": 1e3 * el / args.e2e_steps}
+    ctx.destroy()
+    del ctx
+
+    # ---- the plain all-FP64 form on the same workload ----------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        c64 = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, dt, p.cx, p.cy, p.cz,
+                                       p.erot, p.lev, precision=usp.USP_FP64, seed=w.seed,
+                                       stream=stream.cuda_stream, use_graph=True)
+        usp.usp_step(c64, 2)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        usp.usp_step(c64, args.fp64_steps)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(g0.elapsed_time(g1))
+        fp64 = {"value": total_particles * args.fp64_steps / (ms64 / 1e3), "unit": UNIT,
+                "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
+        c64.destroy()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, cores, el, sample = cpu_baseline(w, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic", "config": config_of(w, args.steps),
+                "gpu_launches": int(launches),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": peak_kind,
+                             "traffic": profiled_traffic(N), "kernel": "collide_kernel<float>",
+                             "kernel_ms": collide_ms, "alg_bytes_per_launch": alg_bytes,
+                             "finalize_ms": finalize_ms, "ms_per_step_profiled": ms_prof / args.steps},
+                "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "clocks": clk,
+                "status": {"flags": int(flags), "counters": [int(x) for x in counters]}}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

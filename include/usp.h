@@ -121,6 +121,11 @@ typedef struct {
 
 typedef struct usp_ctx usp_ctx;
 
+/* Make device `dev` current for the calling thread (cudaSetDevice) so that
+ * contexts created afterwards live on it.  Returns USP_EINVAL for a device
+ * index out of range. */
+int usp_select_device(int dev);
+
 /* Mean collision time tau_c = K(c_alpha, omega) mu(T) / (n k_B T) of the VSS
  * model (Eq. tau_c), evaluated on the host.  Callers use it to choose dt as
  * a multiple of tau_c. */
@@ -186,6 +191,15 @@ int usp_info(usp_ctx* ctx, int64_t* n_particles, int* n_cells, int* precision, i
 /* Number of kernel launches the library enqueued since creation (graph
  * replays count every kernel in the graph). */
 int64_t usp_launch_count(usp_ctx* ctx);
+
+/* Per-kernel device timing.  While enabled (on = 1), usp_step launches its
+ * kernels one by one (no graph replay) and brackets each launch with a pair
+ * of CUDA events recorded on the context stream; enabling clears the
+ * totals.  usp_profile_read synchronises and returns, per kernel kind
+ * (0 = particle collide pass, 1 = per-cell finalize), the accumulated device
+ * milliseconds and the number of launches timed. */
+int usp_profile_enable(usp_ctx* ctx, int on);
+int usp_profile_read(usp_ctx* ctx, double ms[2], int64_t launches[2]);
 
 /* Release the context and all its device memory (synchronises). */
 void usp_destroy(usp_ctx* ctx);

@@ -777,3 +777,247 @@ int orc_homog_step(const orc_species* sp, int form, uint64_t seed,
     }
     return status;
 }
+
+/* ======================================================================== */
+/* 1D channel between two fully diffuse plates (the Poiseuille set-up of    */
+/* Sec. 5.B, force-driven).  One step, in the order of the host particle    */
+/* framework the paper builds on: move (with wall interaction) -> sort by   */
+/* cell -> collision step of Sec. 4.D per cell -> conservation (Sec. 4.C).  */
+/* ======================================================================== */
+#define PTAG_WALL_A 2u
+#define PTAG_WALL_B 3u
+#define WALL_HIT_CAP 16
+#define NFIELD 13   /* U(3), T_tr, T_rot, T_vib, Pi(6) */
+
+/* Fully diffuse wall at T_w (Sec. 5.B: "fully diffusive" walls; reading:
+ * full accommodation of velocity, rotational energy and vibrational level).
+ * Normal speed from the flux-weighted half-range Maxwellian (Rayleigh with
+ * variance R T_w), tangential components Maxwellian, eps_rot exponential with
+ * mean R T_w, level geometric at T_w.  Draws: counters (pid, step, 2, hit)
+ * and (pid, step, 3, hit). */
+static void diffuse_reemit(const orc_species* sp, int form, uint64_t seed, uint32_t pid,
+                           uint32_t step, int hit, double Tw, int into_positive_y,
+                           double* cx, double* cy, double* cz, double* erot, int32_t* lev)
+{
+    double R = orc_R(sp);
+    uint32_t w[4], v[4];
+    philox_words(pid, step, PTAG_WALL_A, (uint32_t)hit, seed, w);
+    philox_words(pid, step, PTAG_WALL_B, (uint32_t)hit, seed, v);
+    double vn = sqrt(-2.0 * R * Tw * log(orc_uniform(w[0], form)));
+    *cy = into_positive_y ? vn : -vn;
+    double g1, g2;
+    box_muller(orc_uniform(w[1], form), orc_uniform(w[2], form), &g1, &g2);
+    double s = sqrt(R * Tw);
+    *cx = s * g1;
+    *cz = s * g2;
+    *erot = -R * Tw * log(orc_uniform(w[3], form));
+    /* P(I >= k) = exp(-k Theta / T_w)  ->  I = floor(-ln(u) T_w / Theta) */
+    *lev = (int32_t)floor(-log(orc_uniform(v[0], form)) * Tw / sp->theta_v);
+}
+
+/* Ballistic flight over dt with the body force along x, reflecting off the
+ * diffuse plates at y = 0 and y = L; a hit re-emits the particle and the
+ * flight continues for the rest of the step.  Returns the x-momentum (per
+ * unit mass) handed to the walls. */
+static double advect_channel(const orc_species* sp, int form, uint64_t seed, uint32_t step,
+                             const orc_channel* ch, double dt, double* y, double* cx, double* cy,
+                             double* cz, double* erot, int32_t* lev, uint32_t pid,
+                             uint32_t* flags, int64_t* counters)
+{
+    double t_left = dt, mom = 0.0;
+    int hits = 0;
+    for (;;) {
+        double yn = *y + *cy * t_left;
+        if (yn >= 0.0 && yn <= ch->L) {
+            *y = yn;
+            *cx += ch->g * t_left;
+            break;
+        }
+        if (hits >= WALL_HIT_CAP) {
+            *flags |= ORC_F_WALL_CAP;
+            *y = yn < 0.0 ? 0.0 : ch->L;
+            *cx += ch->g * t_left;
+            break;
+        }
+        double wall = yn < 0.0 ? 0.0 : ch->L;
+        double t_hit = (wall - *y) / *cy;
+        if (t_hit < 0.0) t_hit = 0.0;
+        if (t_hit > t_left) t_hit = t_left;
+        *cx += ch->g * t_hit;
+        mom += *cx;
+        *y = wall;
+        t_left -= t_hit;
+        diffuse_reemit(sp, form, seed, pid, step, hits, ch->T_wall, wall == 0.0,
+                       cx, cy, cz, erot, lev);
+        mom -= *cx;
+        hits += 1;
+        counters[ORC_C_WALL_HITS] += 1;
+    }
+    return mom;
+}
+
+static int channel_cell(const orc_channel* ch, double y)
+{
+    double dy = ch->L / ch->ny;
+    int c = (int)floor(y / dy);
+    if (c < 0) c = 0;
+    if (c >= ch->ny) c = ch->ny - 1;
+    return c;
+}
+
+/* First-order reconstruction of Sec. 3.B in one dimension: of the quadrant
+ * stencils only the part along y remains, a straight line through the cell
+ * average at the centroid and the neighbour's average at its centroid, the
+ * neighbour being on the particle's side of the centroid (ties to +), or on
+ * the opposite side when that neighbour is a wall or holds fewer than two
+ * particles; with neither neighbour usable the cell value is used. */
+void orc_channel_reconstruct(const orc_channel* ch, const int64_t* counts, const double* F,
+                             int cell, double y, double* out)
+{
+    double dy = ch->L / ch->ny;
+    double yc = (cell + 0.5) * dy;
+    int s = (y >= yc) ? 1 : -1;
+    int nb = cell + s;
+    if (nb < 0 || nb >= ch->ny || counts[nb] < 2) {
+        nb = cell - s;
+        if (nb < 0 || nb >= ch->ny || counts[nb] < 2) nb = -1;
+    }
+    for (int f = 0; f < NFIELD; ++f) {
+        double fc = F[cell * NFIELD + f];
+        if (nb < 0) { out[f] = fc; continue; }
+        double fn = F[nb * NFIELD + f];
+        out[f] = fc + (fn - fc) * (y - yc) / ((nb - cell) * dy);
+    }
+}
+
+/* stable reorder of all particle arrays by cell index */
+static void sort_by_cell(const orc_channel* ch, int64_t n, double* y, double* cx, double* cy,
+                         double* cz, double* erot, int32_t* lev, uint32_t* pid, int64_t* off)
+{
+    int ny = ch->ny;
+    int* cell = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    int64_t* pos = (int64_t*)calloc(ny + 1, sizeof(int64_t));
+    for (int64_t j = 0; j < n; ++j) { cell[j] = channel_cell(ch, y[j]); pos[cell[j] + 1] += 1; }
+    for (int c = 0; c < ny; ++c) pos[c + 1] += pos[c];
+    for (int c = 0; c <= ny; ++c) off[c] = pos[c];
+    double* tmp = (double*)malloc(sizeof(double) * 5 * (n > 0 ? n : 1));
+    int32_t* tl = (int32_t*)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    uint32_t* tp = (uint32_t*)malloc(sizeof(uint32_t) * (n > 0 ? n : 1));
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t k = pos[cell[j]]++;
+        tmp[k] = y[j]; tmp[n + k] = cx[j]; tmp[2 * n + k] = cy[j]; tmp[3 * n + k] = cz[j];
+        tmp[4 * n + k] = erot[j]; tl[k] = lev[j]; tp[k] = pid[j];
+    }
+    memcpy(y, tmp, sizeof(double) * n); memcpy(cx, tmp + n, sizeof(double) * n);
+    memcpy(cy, tmp + 2 * n, sizeof(double) * n); memcpy(cz, tmp + 3 * n, sizeof(double) * n);
+    memcpy(erot, tmp + 4 * n, sizeof(double) * n);
+    memcpy(lev, tl, sizeof(int32_t) * n); memcpy(pid, tp, sizeof(uint32_t) * n);
+    free(tmp); free(tl); free(tp); free(cell); free(pos);
+}
+
+int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t step0,
+                     int nsteps, const orc_channel* ch, double dt, int64_t n,
+                     double* y, double* cx, double* cy, double* cz, double* erot,
+                     int32_t* lev, uint32_t* pid, int64_t* cell_off, double* acc,
+                     uint32_t* flags, int64_t* counters)
+{
+    double R = orc_R(sp);
+    int ny = ch->ny;
+    double dy = ch->L / ny;
+    double vol = ch->area * dy;
+    double* F = (double*)malloc(sizeof(double) * NFIELD * ny);
+    double* cellT = (double*)malloc(sizeof(double) * 3 * ny);
+    int64_t* counts = (int64_t*)malloc(sizeof(int64_t) * ny);
+    orc_coeffs* cc = (orc_coeffs*)malloc(sizeof(orc_coeffs) * ny);
+    int* ok = (int*)malloc(sizeof(int) * ny);
+    int status = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        uint32_t step = (uint32_t)(step0 + s);
+        /* 1. move */
+        double wall_mom = 0.0;
+        for (int64_t j = 0; j < n; ++j)
+            wall_mom += advect_channel(sp, form, seed, step, ch, dt, &y[j], &cx[j], &cy[j], &cz[j],
+                                       &erot[j], &lev[j], pid[j], flags, counters);
+        /* 2. sort */
+        sort_by_cell(ch, n, y, cx, cy, cz, erot, lev, pid, cell_off);
+        /* 3. cell moments and coefficients */
+        for (int c = 0; c < ny; ++c) {
+            int64_t b = cell_off[c], e = cell_off[c + 1], N = e - b;
+            counts[c] = N;
+            ok[c] = 0;
+            for (int f = 0; f < NFIELD; ++f) F[c * NFIELD + f] = 0.0;
+            if (N < 2) { counters[ORC_C_SKIPPED_CELLS] += 1; continue; }
+            double U[3] = { 0, 0, 0 }, er = 0.0, lv = 0.0, P[6] = { 0, 0, 0, 0, 0, 0 };
+            for (int64_t j = b; j < e; ++j) { U[0] += cx[j]; U[1] += cy[j]; U[2] += cz[j]; er += erot[j]; lv += lev[j]; }
+            U[0] /= N; U[1] /= N; U[2] /= N; er /= N; lv /= N;
+            for (int64_t j = b; j < e; ++j) {
+                double C0 = cx[j] - U[0], C1 = cy[j] - U[1], C2 = cz[j] - U[2];
+                P[0] += C0 * C0; P[1] += C1 * C1; P[2] += C2 * C2;
+                P[3] += C0 * C1; P[4] += C0 * C2; P[5] += C1 * C2;
+            }
+            for (int k = 0; k < 6; ++k) P[k] /= N;
+            double T_tr = (P[0] + P[1] + P[2]) / (3.0 * R);
+            double T_rot = er / R;
+            double T_vib = orc_T_vib_from_mean_level(sp, lv);
+            double* Fc = &F[c * NFIELD];
+            Fc[0] = U[0]; Fc[1] = U[1]; Fc[2] = U[2];
+            Fc[3] = T_tr; Fc[4] = T_rot; Fc[5] = T_vib;
+            for (int k = 0; k < 6; ++k) Fc[6 + k] = P[k];
+            cellT[3 * c] = T_tr; cellT[3 * c + 1] = T_rot; cellT[3 * c + 2] = T_vib;
+            double nd = N * ch->F_num / vol;
+            if (orc_cell_coeffs(sp, nd, dt, T_tr, T_rot, T_vib, &cc[c]) != 0) {
+                *flags |= ORC_F_A_NONPOS;
+                status = -1;
+                continue;
+            }
+            ok[c] = 1;
+        }
+        /* 4. particles: reconstruction (Sec. 3.B) and collision (Sec. 4.D) */
+        for (int c = 0; c < ny; ++c) {
+            if (!ok[c]) continue;
+            const double* Fc = &F[c * NFIELD];
+            for (int64_t j = cell_off[c]; j < cell_off[c + 1]; ++j) {
+                double f[NFIELD];
+                if (ch->reconstruct) {
+                    orc_channel_reconstruct(ch, counts, F, c, y[j], f);
+                    if (!(f[3] > 0.0) || !(f[4] > 0.0) || !(f[5] >= 0.0)) {
+                        counters[ORC_C_INTERP_FALLBACK] += 1;
+                        memcpy(f, Fc, sizeof(f));
+                    }
+                } else {
+                    memcpy(f, Fc, sizeof(f));
+                }
+                double G[4], u5, u6, cv[3] = { cx[j], cy[j], cz[j] };
+                particle_draws(seed, pid[j], step, form, G, &u5, &u6);
+                orc_collide_particle(sp, form, &cc[c], f, f + 6, f[3], f[4], f[5], G, u5, u6,
+                                     cv, &erot[j], &lev[j], flags, counters);
+                cx[j] = cv[0]; cy[j] = cv[1]; cz[j] = cv[2];
+            }
+        }
+        /* 5. conservation per cell with the cell-averaged step-n values */
+        for (int c = 0; c < ny; ++c) {
+            if (!ok[c]) continue;
+            const double* Fc = &F[c * NFIELD];
+            conserve_cell(sp, seed, (uint32_t)c, step, cell_off[c], cell_off[c + 1],
+                          1.5 * R * cellT[3 * c], R * cellT[3 * c + 1], orc_e_vib(sp, cellT[3 * c + 2]),
+                          Fc, cc[c].e_rot_tgt, cc[c].e_vib_tgt, cx, cy, cz, erot, lev, flags, counters);
+        }
+        /* 6. time-average sums */
+        if (acc) {
+            for (int c = 0; c < ny; ++c) {
+                double* a = &acc[c * ORC_NACC];
+                for (int64_t j = cell_off[c]; j < cell_off[c + 1]; ++j) {
+                    a[0] += 1.0;
+                    a[1] += cx[j]; a[2] += cy[j]; a[3] += cz[j];
+                    a[4] += cx[j] * cx[j]; a[5] += cy[j] * cy[j]; a[6] += cz[j] * cz[j];
+                    a[7] += cx[j] * cy[j]; a[8] += cx[j] * cz[j]; a[9] += cy[j] * cz[j];
+                    a[10] += erot[j]; a[11] += lev[j];
+                }
+            }
+            acc[ny * ORC_NACC] += 1.0;
+            acc[ny * ORC_NACC + 1] += wall_mom;
+        }
+    }
+    free(F); free(cellT); free(counts); free(cc); free(ok);
+    return status;
+}

@@ -126,6 +126,32 @@ int    orc_homog_step(const orc_species* sp, int form, uint64_t seed,
                       int32_t* lev, const uint32_t* pid,
                       uint32_t* flags, int64_t* counters);
 
+/* ---- 1D channel between two diffuse plates (Sec. 5.B set-up) ------------ */
+typedef struct {
+    int    ny;        /* cells along y                                        */
+    double L;         /* plate gap [m]; walls at y = 0 and y = L              */
+    double T_wall;    /* temperature of both fully diffuse walls [K]          */
+    double g;         /* uniform body force along x [m/s^2]                   */
+    double F_num;     /* real molecules per simulation particle               */
+    double area;      /* cross-section normal to y [m^2]; V_cell = area * dy  */
+    int    reconstruct; /* 1: first-order reconstruction (Sec. 3.B), 0: cell values */
+} orc_channel;
+
+/* Per-cell accumulator layout of orc_channel_step (time-average sums, FP64):
+ * [c * ORC_NACC + k], k: 0 N, 1-3 sum c, 4-9 sum c c (xx yy zz xy xz yz),
+ * 10 sum eps, 11 sum I; slot [ny * ORC_NACC] counts sampled steps and
+ * [ny * ORC_NACC + 1] the x-momentum (per unit particle mass) given to the
+ * walls. */
+#define ORC_NACC 12
+
+int    orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t step0,
+                        int nsteps, const orc_channel* ch, double dt, int64_t n,
+                        double* y, double* cx, double* cy, double* cz, double* erot,
+                        int32_t* lev, uint32_t* pid, int64_t* cell_off, double* acc,
+                        uint32_t* flags, int64_t* counters);
+void   orc_channel_reconstruct(const orc_channel* ch, const int64_t* counts, const double* F,
+                               int cell, double y, double* out);
+
 #ifdef __cplusplus
 }
 #endif

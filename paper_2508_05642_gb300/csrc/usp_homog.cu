@@ -640,6 +640,11 @@ struct usp_ctx {
   cudaGraph_t graph;
   long long device_bytes;
   std::vector<void*> owned;
+  // per-kernel event timing
+  int profiling;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;   // kind of pair i (events 2i, 2i+1)
+  size_t ev_used;
 };
 
 namespace {
@@ -725,19 +730,46 @@ int build_tiles(usp_ctx* c, int tile) {
   return USP_OK;
 }
 
+// Event pair for one timed launch (profiling mode only).
+int prof_begin(usp_ctx* c, int kind, cudaEvent_t* e1) {
+  if (!c->profiling) return USP_OK;
+  if (c->ev_used + 2 > c->ev_pool.size()) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      CK(cudaEventCreate(&e));
+      c->ev_pool.push_back(e);
+    }
+  }
+  CK(cudaEventRecord(c->ev_pool[c->ev_used], c->stream));
+  *e1 = c->ev_pool[c->ev_used + 1];
+  c->ev_kind.push_back(kind);
+  c->ev_used += 2;
+  return USP_OK;
+}
+int prof_end(usp_ctx* c, cudaEvent_t e1) {
+  if (!c->profiling) return USP_OK;
+  CK(cudaEventRecord(e1, c->stream));
+  return USP_OK;
+}
+
 template <typename T>
 int launch_step(usp_ctx* c) {
+  cudaEvent_t e1 = nullptr;
+  int rc = prof_begin(c, 0, &e1);
+  if (rc) return rc;
   collide_kernel<T><<<c->grid_collide, kBlock, 0, c->stream>>>(
       c->tiles, c->ntiles, (const CollideParams<T>*)c->prm, (T*)c->cx, (T*)c->cy, (T*)c->cz,
       (T*)c->er, c->lev, c->sums, c->flags, c->counters, key0(c), key1(c));
   CK(cudaGetLastError());
+  if ((rc = prof_end(c, e1))) return rc;
+  if ((rc = prof_begin(c, 1, &e1))) return rc;
   const int warps_per_block = 4;
   const int blocks = (c->ncell + warps_per_block - 1) / warps_per_block;
   finalize_kernel<T><<<blocks, 32 * warps_per_block, 0, c->stream>>>(
       c->sp, c->ncell, c->cells, (CollideParams<T>*)c->prm, c->sums, c->lev, c->flags,
       c->counters, key0(c), key1(c));
   CK(cudaGetLastError());
-  return USP_OK;
+  return prof_end(c, e1);
 }
 
 int step_once(usp_ctx* c) {
@@ -847,6 +879,14 @@ int build_graph(usp_ctx* c, int steps) {
 // ===========================================================================
 extern "C" {
 
+int usp_select_device(int dev) {
+  int n = 0;
+  CK(cudaGetDeviceCount(&n));
+  if (dev < 0 || dev >= n) return USP_EINVAL;
+  CK(cudaSetDevice(dev));
+  return USP_OK;
+}
+
 double usp_tau_c(const usp_species* s, double n, double T) {
   if (!s) return 0.0;
   const double kPiH = 3.14159265358979323846;
@@ -902,6 +942,8 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   c->step = cfg->step0;
   c->launches = 0;
   c->device_bytes = 0;
+  c->profiling = 0;
+  c->ev_used = 0;
   if (cfg->stream) {
     c->stream = (cudaStream_t)cfg->stream;
     c->own_stream = false;
@@ -986,7 +1028,7 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
 int usp_step(usp_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return USP_EINVAL;
   if (nsteps == 0) return USP_OK;
-  if (!c->cfg.use_graph) {
+  if (!c->cfg.use_graph || c->profiling) {
     for (int i = 0; i < nsteps; ++i) {
       int rc = step_once(c);
       if (rc) return rc;
@@ -1155,6 +1197,32 @@ int usp_info(usp_ctx* c, int64_t* np, int* nc, int* prec, int64_t* step, int* ti
 
 int64_t usp_launch_count(usp_ctx* c) { return c ? c->launches : -1; }
 
+int usp_profile_enable(usp_ctx* c, int on) {
+  if (!c) return USP_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  c->profiling = on ? 1 : 0;
+  c->ev_used = 0;
+  c->ev_kind.clear();
+  return USP_OK;
+}
+
+int usp_profile_read(usp_ctx* c, double* ms, int64_t* launches) {
+  if (!c || !ms || !launches) return USP_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  ms[0] = ms[1] = 0.0;
+  launches[0] = launches[1] = 0;
+  for (size_t i = 0; i < c->ev_kind.size(); ++i) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]));
+    const int k = c->ev_kind[i];
+    if (k >= 0 && k < 2) {
+      ms[k] += t;
+      launches[k] += 1;
+    }
+  }
+  return USP_OK;
+}
+
 void usp_destroy(usp_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
@@ -1162,6 +1230,7 @@ void usp_destroy(usp_ctx* c) {
     cudaGraphExecDestroy(c->graph_exec);
     cudaGraphDestroy(c->graph);
   }
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   dev_free_all(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

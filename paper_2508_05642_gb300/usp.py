@@ -33,9 +33,10 @@ F_BOUNDS = 0x200
 C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, \
     C_INTERP_FALLBACK, C_SKIPPED_CELLS = range(8)
 
-EXPORTED = ["usp_tau_c", "usp_strerror", "usp_init_homogeneous", "usp_step", "usp_moments",
+EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogeneous", "usp_step", "usp_moments",
             "usp_get_particles", "usp_set_particles", "usp_step_host", "usp_status", "usp_sync",
-            "usp_info", "usp_launch_count", "usp_destroy"]
+            "usp_info", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
+            "usp_destroy"]
 
 
 class usp_species(C.Structure):
@@ -76,6 +77,7 @@ def lib():
         if _lib is None:
             path = _build.build()
             L = C.CDLL(path)
+            L.usp_select_device.argtypes = [C.c_int]
             L.usp_tau_c.argtypes = [C.POINTER(usp_species), C.c_double, C.c_double]
             L.usp_tau_c.restype = C.c_double
             L.usp_strerror.argtypes = [C.c_int]
@@ -96,6 +98,8 @@ def lib():
                                    C.POINTER(C.c_int), _I64]
             L.usp_launch_count.argtypes = [_CTX]
             L.usp_launch_count.restype = C.c_int64
+            L.usp_profile_enable.argtypes = [_CTX, C.c_int]
+            L.usp_profile_read.argtypes = [_CTX, _D, _I64]
             L.usp_destroy.argtypes = [_CTX]
             L.usp_destroy.restype = None
             _lib = L
@@ -126,6 +130,10 @@ def make_species(d: dict) -> usp_species:
     for k, _ in usp_species._fields_:
         setattr(s, k, d.get(k, 0))
     return s
+
+
+def usp_select_device(dev: int):
+    _check(lib().usp_select_device(dev), "usp_select_device")
 
 
 def usp_tau_c(species: dict, n: float, T: float) -> float:
@@ -255,6 +263,18 @@ def usp_info(ctx: Context) -> dict:
 
 def usp_launch_count(ctx: Context) -> int:
     return lib().usp_launch_count(ctx.h)
+
+
+def usp_profile_enable(ctx: Context, on: bool = True):
+    _check(lib().usp_profile_enable(ctx.h, 1 if on else 0), "usp_profile_enable")
+
+
+def usp_profile_read(ctx: Context):
+    """(ms[2], launches[2]) accumulated per kernel kind: 0 collide, 1 finalize."""
+    ms = np.zeros(2)
+    n = np.zeros(2, dtype=np.int64)
+    _check(lib().usp_profile_read(ctx.h, _p(ms, C.c_double), _p(n, C.c_int64)), "usp_profile_read")
+    return ms, n
 
 
 def usp_destroy(ctx: Context):
