@@ -201,6 +201,39 @@ int64_t usp_launch_count(usp_ctx* ctx);
 int usp_profile_enable(usp_ctx* ctx, int on);
 int usp_profile_read(usp_ctx* ctx, double ms[2], int64_t launches[2]);
 
+/* Largest n_cells accepted by usp_moments_noalloc. */
+#define USP_NOALLOC_MAX_CELLS 8192
+
+/* Per-cell moments (same fields and layout as usp_moments) of a particle
+ * state the caller holds in device memory, computed without allocating any
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that may not allocate, such as frameworks that reserve all device
+ * memory in their own pool at start-up and forbid later cudaMalloc, or time
+ * loops that must not risk the implicit synchronisation of cudaMalloc and
+ * cudaFree.
+ *   sp:        gas species (only m and theta_v are used).
+ *   n_cells:   1 .. USP_NOALLOC_MAX_CELLS; a larger value returns USP_EINVAL
+ *              and launches nothing.
+ *   d_offsets: device int64[n_cells + 1], cell i holds particles
+ *              [d_offsets[i], d_offsets[i+1]).
+ *   d_cx, d_cy, d_cz, d_erot (device double) and d_lev (device int32): the
+ *              particles, indexed by those offsets.
+ *   d_out:     device double[USP_NMOM * n_cells], field-major, written.
+ *   stream:    cudaStream_t the work is enqueued on (NULL: legacy stream);
+ *              the call returns without waiting.
+ * Working space is one fixed device array of 20 * USP_NOALLOC_MAX_CELLS
+ * doubles (1.25 MiB) that every device loading the library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents: each call clears it on its stream first, and
+ * calls whose work overlaps on the GPU race on it.  No cudaMalloc, cudaFree
+ * or other allocating routine is called. */
+int usp_moments_noalloc(const usp_species* sp, int n_cells, const int64_t* d_offsets,
+                        const double* d_cx, const double* d_cy, const double* d_cz,
+                        const double* d_erot, const int32_t* d_lev, double* d_out,
+                        void* stream);
+
 /* Release the context and all its device memory (synchronises). */
 void usp_destroy(usp_ctx* ctx);
 

@@ -36,7 +36,8 @@ C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, 
 EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogeneous", "usp_step", "usp_moments",
             "usp_get_particles", "usp_set_particles", "usp_step_host", "usp_status", "usp_sync",
             "usp_info", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
-            "usp_destroy"]
+            "usp_moments_noalloc", "usp_destroy"]
+USP_NOALLOC_MAX_CELLS = 8192
 
 
 class usp_species(C.Structure):
@@ -100,6 +101,9 @@ def lib():
             L.usp_launch_count.restype = C.c_int64
             L.usp_profile_enable.argtypes = [_CTX, C.c_int]
             L.usp_profile_read.argtypes = [_CTX, _D, _I64]
+            L.usp_moments_noalloc.argtypes = [C.POINTER(usp_species), C.c_int, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_void_p, C.c_void_p]
             L.usp_destroy.argtypes = [_CTX]
             L.usp_destroy.restype = None
             _lib = L
@@ -275,6 +279,18 @@ def usp_profile_read(ctx: Context):
     n = np.zeros(2, dtype=np.int64)
     _check(lib().usp_profile_read(ctx.h, _p(ms, C.c_double), _p(n, C.c_int64)), "usp_profile_read")
     return ms, n
+
+
+def usp_moments_noalloc(species: dict, n_cells: int, d_offsets: int, d_cx: int, d_cy: int,
+                        d_cz: int, d_erot: int, d_lev: int, d_out: int, stream: int = 0):
+    """Per-cell moments of a device-resident state, without any device
+    allocation (for callers whose memory is owned by their own pool).  All
+    pointers are device addresses (ints); returns without waiting."""
+    sp = make_species(species)
+    rc = lib().usp_moments_noalloc(C.byref(sp), n_cells, *[C.c_void_p(x) for x in
+                                   (d_offsets, d_cx, d_cy, d_cz, d_erot, d_lev, d_out)],
+                                   C.c_void_p(stream or None))
+    _check(rc, "usp_moments_noalloc")
 
 
 def usp_destroy(ctx: Context):
