@@ -258,6 +258,7 @@ def run_ours(args, rank, world, local):
                                    p.lev, precision=usp.USP_FP32, seed=w.seed,
                                    stream=stream.cuda_stream, use_graph=True)
     N = w.n_particles
+    minb, tune_ms = usp.usp_tuning(ctx)
     usp.usp_step(ctx, args.warmup)
     torch.cuda.synchronize()
 
@@ -348,7 +349,9 @@ def run_ours(args, rank, world, local):
                              "frac": achieved / peak, "peak_source": peak_kind,
                              "traffic": profiled_traffic(N), "kernel": "collide_kernel<float>",
                              "kernel_ms": collide_ms, "alg_bytes_per_launch": alg_bytes,
-                             "finalize_ms": finalize_ms, "ms_per_step_profiled": ms_prof / args.steps},
+                             "finalize_ms": finalize_ms, "ms_per_step_profiled": ms_prof / args.steps,
+                             "autotune": {"blocks_per_sm": minb,
+                                          "ms_by_blocks_per_sm_2_3_4": [float(x) for x in tune_ms]}},
                 "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "clocks": clk,
                 "status": {"flags": int(flags), "counters": [int(x) for x in counters]}}
         print(json.dumps(line), flush=True)

@@ -50,7 +50,7 @@ typedef enum {
   USP_ENOTSUP = -5   /* the request is not supported by this context       */
 } usp_err;
 
-/* Device status bits (usp_status).  Bits 0x02, 0x40, 0x80, 0x200 are errors;
+/* Device status bits (usp_status).  Bits 0x02, 0x40, 0x80, 0x200, 0x400 are errors;
  * the others report clamps the method applies and continues. */
 enum {
   USP_F_PB_CLAMP = 0x01,            /* p_B > 1 met (Sec. 3.A.2): binomial clamped to n   */
@@ -61,7 +61,8 @@ enum {
   USP_F_SAMPLER_CAP = 0x20,         /* a jump-sampler search hit 4096 steps              */
   USP_F_A_NONPOS = 0x40,            /* 2 mu/p <= Pr dt in a cell: dt too large           */
   USP_F_SAMPLER_UNDERFLOW = 0x80,   /* jump pmf underflowed double                       */
-  USP_F_BOUNDS = 0x200              /* an index check failed (kernel skipped the access) */
+  USP_F_BOUNDS = 0x200,             /* an index check failed (kernel skipped the access) */
+  USP_F_WAIT_TIMEOUT = 0x400        /* a device-side wait gave up after its time limit  */
 };
 
 /* Counter slots of usp_status. */
@@ -187,6 +188,12 @@ int usp_sync(usp_ctx* ctx);
 /* Sizes of the context. */
 int usp_info(usp_ctx* ctx, int64_t* n_particles, int* n_cells, int* precision, int64_t* step,
              int* tile, int64_t* device_bytes);
+
+/* Particle-pass variant in use: resident blocks per SM its register budget
+ * targets (2, 3 or 4), and the autotuner's milliseconds per launch of each
+ * variant on its sample (zeros when the tuner did not run: explicit tile
+ * size, or fewer than 2^20 particles). */
+int usp_tuning(usp_ctx* ctx, int* blocks_per_sm, double ms[3]);
 
 /* Number of kernel launches the library enqueued since creation (graph
  * replays count every kernel in the graph). */

@@ -27,6 +27,7 @@ enum : uint32_t {
   F_SAMPLER_UNDERFLOW = 0x80u,
   F_WALL_CAP = 0x100u,
   F_BOUNDS = 0x200u,
+  F_WAIT_TIMEOUT = 0x400u,
 };
 enum { C_CHOL_FIX = 0, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND,
        C_WALL_HITS, C_INTERP_FALLBACK, C_SKIPPED_CELLS, NCOUNTERS };
@@ -72,13 +73,16 @@ template <> __device__ __forceinline__ float uniform_open<float>(uint32_t x) {
   return __fmul_rn(__uint2float_rn((x >> 9) * 2u + 1u), 5.9604644775390625e-08f);
 }
 
-// Box-Muller pair.
+// Box-Muller pair: G_a = sqrt(-2 ln u_a) cos(2 pi u_b), G_b = ... sin(2 pi u_b).
+// The float version evaluates the angle on (-pi, pi), where the hardware
+// sine/cosine has an absolute error below 2^-21:
+// cos(2 pi u) = -cos(2 pi u - pi), sin(2 pi u) = -sin(2 pi u - pi).
 __device__ __forceinline__ void box_muller(float ua, float ub, float& ga, float& gb) {
   const float rad = sqrtf(-2.0f * logf(ua));
   float s, c;
-  sincospif(2.0f * ub, &s, &c);
-  ga = rad * c;
-  gb = rad * s;
+  __sincosf(6.28318530717958647692f * (ub - 0.5f), &s, &c);
+  ga = -rad * c;
+  gb = -rad * s;
 }
 __device__ __forceinline__ void box_muller(double ua, double ub, double& ga, double& gb) {
   const double rad = sqrt(-2.0 * log(ua));

@@ -53,7 +53,7 @@ struct CellState {
   long long off, N;          // padded segment start, particle count
   unsigned int pid0, step;   // id of the first particle, step index
   int active;
-  int pad_;
+  int maxI;                  // bound on the levels entering the step (jump-table rows)
 };
 
 template <typename T>
@@ -70,30 +70,108 @@ struct CollideParams {
 
 struct CellSums {
   double v[10];              // sum d (3), sum d d^T (6), sum eps
-  unsigned long long I;      // sum of levels
-  unsigned long long pad_;
+  unsigned long long I;      // sum of levels after the collision
+  long long net;             // net change of the level sum by the +-1 correction
+  int maxI;                  // largest level after the collision
+  int pad_;
 };
 
 struct Tile {
   int cell, start, count, pad_;
 };
 
-template <typename T> struct Vec;
-template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
-template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
-
-__device__ __forceinline__ float4 ld_vec(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ double2 ld_vec(const double* p) { return *reinterpret_cast<const double2*>(p); }
-__device__ __forceinline__ int4 ld_vec_i(const int* p) { return *reinterpret_cast<const int4*>(p); }
-__device__ __forceinline__ int2 ld_vec_i2(const int* p) { return *reinterpret_cast<const int2*>(p); }
-__device__ __forceinline__ void st_vec(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-__device__ __forceinline__ void st_vec(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
-
-__device__ __forceinline__ float& el(float4& v, int i) { return (&v.x)[i]; }
-__device__ __forceinline__ double& el(double2& v, int i) { return (&v.x)[i]; }
-
 __device__ __forceinline__ void flag_or(uint32_t* flags, uint32_t f) {
   if (f) atomicOr(flags, f);
+}
+
+// ---------------------------------------------------------------------------
+// Jump tables of the FP32 form.  In a homogeneous cell p_NB and p_B are cell
+// constants, so the cumulative values the sequential inversion would compute
+// for a given r = I + 1 (or n = I) are the same for every particle of the
+// cell.  jumptable_kernel computes them once per cell and step with exactly
+// the operations of nb_inv / binv; a particle then scans its row.  The result
+// is identical, bit for bit, to the sequential search: a stall of the
+// cumulative sum and the end of the binomial support become +inf entries, an
+// underflowed P(0) marks the row (-1) and sends the particle to the
+// sequential search, as does a search running past the row.
+// ---------------------------------------------------------------------------
+constexpr int kJR = 32;   // rows: NB r = 1..32, B n = 0..31
+constexpr int kJK = 48;   // cumulative values per row
+
+__device__ void nb_row(int r, float p, float* T) {
+  const float q = rn_sub(1.0f, p);
+  float P = powi_rn(p, r);
+  if (P < 1.17549435e-38f) { T[0] = -1.0f; return; }
+  float cdf = P;
+  T[0] = cdf;
+  bool stop = false;
+  for (int j = 1; j < kJK; ++j) {
+    if (!stop) {
+      const int k = j - 1;
+      const float t = rn_div(rn_i2f(k + r, 0.0f), rn_i2f(k + 1, 0.0f));
+      P = rn_mul(P, t);
+      P = rn_mul(P, q);
+      const float nc = rn_add(cdf, P);
+      if (nc == cdf) stop = true;
+      else cdf = nc;
+    }
+    T[j] = stop ? __int_as_float(0x7f800000) : cdf;
+  }
+}
+
+// p here is the binomial parameter after the p > 1/2 flip
+__device__ void b_row(int n, float p, float* T) {
+  const float q = rn_sub(1.0f, p);
+  float P = powi_rn(q, n);
+  if (P < 1.17549435e-38f) { T[0] = -1.0f; return; }
+  const float pq = rn_div(p, q);
+  float cdf = P;
+  T[0] = cdf;
+  bool stop = false;
+  for (int j = 1; j < kJK; ++j) {
+    if (!stop) {
+      if (j >= n) {
+        stop = true;   // the search ends at k = n whatever u is
+      } else {
+        const int k = j - 1;
+        const float t = rn_div(rn_i2f(n - k, 0.0f), rn_i2f(k + 1, 0.0f));
+        P = rn_mul(P, t);
+        P = rn_mul(P, pq);
+        const float nc = rn_add(cdf, P);
+        if (nc == cdf) stop = true;
+        else cdf = nc;
+      }
+    }
+    T[j] = stop ? __int_as_float(0x7f800000) : cdf;
+  }
+}
+
+__device__ __forceinline__ int nb_tab(const float* __restrict__ T, int r, float p, float u,
+                                      uint32_t& fl) {
+  if (r <= 0 || !(p < 1.0f)) return 0;
+  if (r > kJR || T[0] < 0.0f) return nb_inv(r, p, u, fl);
+  int k = 0;
+  while (k < kJK && u >= T[k]) ++k;
+  return k < kJK ? k : nb_inv(r, p, u, fl);
+}
+
+__device__ __forceinline__ int b_tab(const float* __restrict__ T, int n, float p, float u,
+                                     uint32_t& fl) {
+  if (n <= 0) return 0;
+  if (p >= 1.0f) {
+    if (p > 1.0f) fl |= F_PB_CLAMP;
+    return n;
+  }
+  if (!(p > 0.0f)) return 0;
+  const bool flip = p > 0.5f;
+  int k;
+  if (n >= kJR || T[0] < 0.0f) {
+    k = binv(n, flip ? rn_sub(1.0f, p) : p, u, fl);
+  } else {
+    k = 0;
+    while (u >= T[k]) ++k;   // T[n] = +inf ends the scan by k = n < kJK
+  }
+  return flip ? n - k : k;
 }
 
 // ---------------------------------------------------------------------------
@@ -102,7 +180,9 @@ __device__ __forceinline__ void flag_or(uint32_t* flags, uint32_t f) {
 template <typename T>
 __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t pid, uint32_t k0,
                                             uint32_t k1, T& cx, T& cy, T& cz, T& er, int& lv,
-                                            T* acc, int& accI, uint32_t& fl) {
+                                            T* acc, int& accI, int& maxI, uint32_t& fl,
+                                            const float* __restrict__ tnb,
+                                            const float* __restrict__ tb) {
   const U4 w = philox4x32_10(pid, P.step, PTAG_NORMALS, 0u, k0, k1);
   T g0, g1, g2, g3;
   box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
@@ -122,9 +202,16 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   const U4 w2 = philox4x32_10(pid, P.step, PTAG_JUMPS, 0u, k0, k1);
   const T u5 = uniform_open<T>(w2.x), u6 = uniform_open<T>(w2.y);
   const int I = lv;
-  const int up = sample_nb<T>(I + 1, P.p_nb, u5, fl);
-  const int dn = sample_b<T>(I, P.p_b, u6, fl);
+  int up, dn;
+  if constexpr (sizeof(T) == 4) {
+    up = nb_tab(tnb + (size_t)(I < kJR ? I : 0) * kJK, I + 1, P.p_nb, u5, fl);
+    dn = b_tab(tb + (size_t)(I < kJR ? I : 0) * kJK, I, P.p_b, u6, fl);
+  } else {
+    up = sample_nb<T>(I + 1, P.p_nb, u5, fl);
+    dn = sample_b<T>(I, P.p_b, u6, fl);
+  }
   lv = I + up - dn;
+  maxI = max(maxI, lv);
   acc[0] += r0; acc[1] += r1; acc[2] += r2;
   acc[3] += r0 * r0; acc[4] += r1 * r1; acc[5] += r2 * r2;
   acc[6] += r0 * r1; acc[7] += r0 * r2; acc[8] += r1 * r2;
@@ -142,7 +229,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Block reduction of the tile sums and one FP64 atomic per sum.  Partial sums
 // stay in T inside a thread and a warp; warps combine in FP64.
 template <typename T>
-__device__ __forceinline__ void flush_sums(const T* acc, int accI, CellSums* dst) {
+__device__ __forceinline__ void flush_sums(const T* acc, int accI, int maxI, CellSums* dst) {
   __shared__ double red[kBlock / 32][11];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -152,6 +239,8 @@ __device__ __forceinline__ void flush_sums(const T* acc, int accI, CellSums* dst
   }
   const int sI = warp_sum(accI);
   if (lane == 0) red[wid][10] = (double)sI;
+  const int mI = __reduce_max_sync(0xffffffffu, maxI);
+  if (lane == 0 && mI > 0) atomicMax(&dst->maxI, mI);
   __syncthreads();
   if (threadIdx.x < 11) {
     double t = 0.0;
@@ -165,62 +254,262 @@ __device__ __forceinline__ void flush_sums(const T* acc, int accI, CellSums* dst
   __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Bulk-copy (TMA) staging helpers: shared-memory mbarrier, cp.async.bulk
+// global<->shared copies, proxy fences.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+      ::"r"(smem_u32(bar)), "r"(bytes)
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared, completion counted on the mbarrier (bytes % 16 == 0,
+// both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// shared -> global in the current bulk group
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+               ::"l"(dst), "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2e9 SM cycles (about a
+// second) and reports false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > 2000000000ll) return false;
+  }
+  return true;
+}
+
+constexpr int kTileMax = 1024;   // particles per staged tile
+
+// One staging buffer: x, y, z, eps (kTileMax T each) then levels (kTileMax int).
 template <typename T>
-__global__ void __launch_bounds__(kBlock, 4)
+constexpr size_t stage_bytes() {
+  return (size_t)kTileMax * (4 * sizeof(T) + sizeof(int));
+}
+template <typename T>
+__device__ __forceinline__ T* sb_x(unsigned char* b) { return reinterpret_cast<T*>(b); }
+template <typename T>
+__device__ __forceinline__ int* sb_l(unsigned char* b) {
+  return reinterpret_cast<int*>(b + 4 * kTileMax * sizeof(T));
+}
+
+// bytes of one staged copy of `count` particles (rounded up to the 4-element
+// segment padding, so every copy is a multiple of 16 bytes)
+__device__ __forceinline__ int round4(int n) { return (n + 3) & ~3; }
+
+// Issue the five bulk loads of tile t into buffer b (one thread).
+template <typename T>
+__device__ __forceinline__ void stage_load(const Tile& tl, long long off, unsigned char* b,
+                                           uint64_t* bar, const T* cx, const T* cy, const T* cz,
+                                           const T* er, const int* lev) {
+  const int n4 = round4(tl.count);
+  const long long base = off + tl.start;
+  const uint32_t bt = (uint32_t)(n4 * sizeof(T)), bl = (uint32_t)(n4 * sizeof(int));
+  T* X = sb_x<T>(b);
+  mbar_expect_tx(bar, 4 * bt + bl);
+  if (n4 > 0) {
+    bulk_g2s(X, cx + base, bt, bar);
+    bulk_g2s(X + kTileMax, cy + base, bt, bar);
+    bulk_g2s(X + 2 * kTileMax, cz + base, bt, bar);
+    bulk_g2s(X + 3 * kTileMax, er + base, bt, bar);
+    bulk_g2s(sb_l<T>(b), lev + base, bl, bar);
+  }
+}
+
+// Particle pass of one step.  Each persistent block owns a contiguous range
+// of the tile list (tiles of one cell are adjacent, so a block meets few cell
+// boundaries); each tile (<= kTileMax particles of one cell) is brought into
+// shared memory by bulk copies while the previous tile is being processed (two
+// buffers), updated in place, and written back by bulk copies.  Cell sums are
+// flushed when the cell changes.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
 collide_kernel(const Tile* __restrict__ tiles, int ntiles,
                const CollideParams<T>* __restrict__ prm, T* __restrict__ cx,
                T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
                int* __restrict__ lev, CellSums* __restrict__ sums, uint32_t* flags,
-               unsigned long long* counters, uint32_t k0, uint32_t k1) {
-  constexpr int V = Vec<T>::n;
-  using VT = typename Vec<T>::type;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+               unsigned long long* counters, uint32_t k0, uint32_t k1,
+               const float* __restrict__ tab_nb, const float* __restrict__ tab_b) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(16) CollideParams<T> Ps;   // the current tile's cell parameters
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const int t_begin = (int)(((long long)ntiles * blockIdx.x) / G);
+  const int t_end = (int)(((long long)ntiles * (blockIdx.x + 1)) / G);
+  if (t_begin >= t_end) return;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const Tile tl = tiles[t_begin];
+    stage_load<T>(tl, prm[tl.cell].off, smem, &bar[0], cx, cy, cz, er, lev);
+  }
+  uint32_t phase[2] = {0u, 0u};
+  bool inflight[2] = {true, false};  // meaningful in thread 0, which issues the loads
+  T acc[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) acc[i] = T(0);
+  int accI = 0, maxI = 0;
+  uint32_t fl = 0;
+  int npb = 0;
+  int it = 0;
+  for (int t = t_begin; t < t_end; ++t, ++it) {
+    const int b = it & 1;
+    const int tn = t + 1;
+    if (tid == 0 && tn < t_end) {
+      // buffer b^1 was the source of the previous tile's bulk store
+      bulk_wait_read_all();
+      const Tile tn_l = tiles[tn];
+      stage_load<T>(tn_l, prm[tn_l.cell].off, smem + (b ^ 1) * stage_bytes<T>(), &bar[b ^ 1], cx,
+                    cy, cz, er, lev);
+      inflight[b ^ 1] = true;
+    }
     const Tile tl = tiles[t];
-    const CollideParams<T> P = prm[tl.cell];
-    if (!P.active) continue;
-    const long long base = P.off + tl.start;
-    const uint32_t pid0 = P.pid0 + (uint32_t)tl.start;
-    T acc[10];
-#pragma unroll
-    for (int i = 0; i < 10; ++i) acc[i] = T(0);
-    int accI = 0;
-    uint32_t fl = 0;
-    int npb = 0;
-    const int nvec = (tl.count + V - 1) / V;
-    for (int v = threadIdx.x; v < nvec; v += kBlock) {
-      const long long e0 = base + (long long)v * V;
-      VT vx = ld_vec(cx + e0), vy = ld_vec(cy + e0), vz = ld_vec(cz + e0), ve = ld_vec(er + e0);
-      int li[V];
-      if constexpr (V == 4) {
-        const int4 q = ld_vec_i(lev + e0);
-        li[0] = q.x; li[1] = q.y; li[2] = q.z; li[3] = q.w;
-      } else {
-        const int2 q = ld_vec_i2(lev + e0);
-        li[0] = q.x; li[1] = q.y;
+    {
+      // stage the cell parameters of tile t (visible after the barrier below)
+      constexpr int nw = (int)(sizeof(CollideParams<T>) / 4);
+      if (tid < nw)
+        reinterpret_cast<uint32_t*>(&Ps)[tid] =
+            reinterpret_cast<const uint32_t*>(&prm[tl.cell])[tid];
+    }
+    const bool ok = mbar_wait_bounded(&bar[b], phase[b]);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
+      break;
+    }
+    phase[b] ^= 1u;
+    if (tid == 0) inflight[b] = false;
+    const CollideParams<T>& P = Ps;
+    if (P.active) {
+      T* X = sb_x<T>(smem + b * stage_bytes<T>());
+      int* Lv = sb_l<T>(smem + b * stage_bytes<T>());
+      const uint32_t pid0 = P.pid0 + (uint32_t)tl.start;
+      const float* tnb = tab_nb + (size_t)tl.cell * kJR * kJK;
+      const float* tb = tab_b + (size_t)tl.cell * kJR * kJK;
+#pragma unroll 1
+      for (int k = tid; k < tl.count; k += kBlock) {
+        T x = X[k], y = X[k + kTileMax], z = X[k + 2 * kTileMax], e = X[k + 3 * kTileMax];
+        int l = Lv[k];
+        uint32_t f1 = 0;
+        collide_one<T>(P, pid0 + (uint32_t)k, k0, k1, x, y, z, e, l, acc, accI, maxI, f1, tnb, tb);
+        X[k] = x; X[k + kTileMax] = y; X[k + 2 * kTileMax] = z; X[k + 3 * kTileMax] = e;
+        Lv[k] = l;
+        npb += (f1 & F_PB_CLAMP) ? 1 : 0;
+        fl |= f1;
       }
-#pragma unroll
-      for (int i = 0; i < V; ++i) {
-        const int k = v * V + i;
-        if (k < tl.count) {
-          uint32_t f1 = 0;
-          collide_one<T>(P, pid0 + (uint32_t)(v * V + i), k0, k1, el(vx, i), el(vy, i), el(vz, i),
-                         el(ve, i), li[i], acc, accI, f1);
-          if (f1 & F_PB_CLAMP) ++npb;
-          fl |= f1;
+      // results in shared memory -> visible to the bulk-copy engine
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        const int n4 = round4(tl.count);
+        const long long base = P.off + tl.start;
+        const uint32_t bt = (uint32_t)(n4 * sizeof(T)), bl = (uint32_t)(n4 * sizeof(int));
+        if (n4 > 0) {
+          bulk_s2g(cx + base, X, bt);
+          bulk_s2g(cy + base, X + kTileMax, bt);
+          bulk_s2g(cz + base, X + 2 * kTileMax, bt);
+          bulk_s2g(er + base, X + 3 * kTileMax, bt);
+          bulk_s2g(lev + base, Lv, bl);
         }
+        bulk_commit();
       }
-      st_vec(cx + e0, vx); st_vec(cy + e0, vy); st_vec(cz + e0, vz); st_vec(er + e0, ve);
-      if constexpr (V == 4) {
-        *reinterpret_cast<int4*>(lev + e0) = make_int4(li[0], li[1], li[2], li[3]);
-      } else {
-        *reinterpret_cast<int2*>(lev + e0) = make_int2(li[0], li[1]);
+      // sums of a cell are flushed once its last tile in this range is done
+      if (tn >= t_end || tiles[tn].cell != tl.cell) {
+        flush_sums<T>(acc, accI, maxI, &sums[tl.cell]);
+#pragma unroll
+        for (int i = 0; i < 10; ++i) acc[i] = T(0);
+        accI = 0;
+        maxI = 0;
       }
+    } else {
+      __syncthreads();
     }
-    flush_sums<T>(acc, accI, &sums[tl.cell]);
-    if (fl) {
-      flag_or(flags, fl);
-      if (npb) atomicAdd(&counters[C_PB_CLAMP], (unsigned long long)npb);
-    }
+  }
+  if (fl) {
+    flag_or(flags, fl);
+    if (npb) atomicAdd(&counters[C_PB_CLAMP], (unsigned long long)npb);
+  }
+  if (tid == 0) {
+    // loads still in flight after a timeout: wait for them (bounded) before
+    // the block's shared memory is released
+    for (int b = 0; b < 2; ++b)
+      if (inflight[b]) (void)mbar_wait_bounded(&bar[b], phase[b]);
+    bulk_wait_all();
+  }
+}
+
+// Jump-table rows of every cell for the coming step (FP32 form): thread j <
+// kJR builds the NB row r = j + 1, thread kJR + n the binomial row n, for the
+// rows the cell's levels can reach.
+__global__ void jumptable_kernel(int ncell, const CollideParams<float>* __restrict__ prm,
+                                 const CellState* __restrict__ cells, float* __restrict__ tab_nb,
+                                 float* __restrict__ tab_b) {
+  const int c = blockIdx.x;
+  const int j = threadIdx.x;
+  if (c >= ncell) return;
+  const CollideParams<float>& P = prm[c];
+  if (!P.active) return;
+  const int rows = min(kJR, cells[c].maxI + 1);
+  if (j < kJR) {
+    const int r = j + 1;
+    if (r > rows || !(P.p_nb < 1.0f)) return;
+    nb_row(r, P.p_nb, tab_nb + ((size_t)c * kJR + j) * kJK);
+  } else {
+    const int n = j - kJR;
+    if (n < 1 || n > rows - 1) return;
+    float p = P.p_b;
+    if (!(p < 1.0f) || !(p > 0.0f)) return;
+    if (p > 0.5f) p = rn_sub(1.0f, p);
+    b_row(n, p, tab_b + ((size_t)c * kJR + n) * kJK);
   }
 }
 
@@ -286,6 +575,7 @@ __global__ void init_params_kernel(Species sp, int ncell, const double* __restri
   cs.ebar = 0.0;
   cs.s = 1.0;
   cs.r = 1.0;
+  cs.maxI = 1 << 30;   // unknown: build every jump-table row
   cs.active = cs.N >= 2;
   if (!cs.active) atomicAdd(&counters[C_SKIPPED_CELLS], 1ull);
   cells[c] = cs;  // ebar is filled by the level-sum pass below
@@ -317,40 +607,39 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-template <typename T>
-__global__ void finalize_kernel(Species sp, int ncell, CellState* __restrict__ cells,
-                                CollideParams<T>* __restrict__ prm, CellSums* __restrict__ sums,
-                                int* __restrict__ lev, uint32_t* flags,
-                                unsigned long long* counters, uint32_t k0, uint32_t k1) {
+// Vibrational summation correction of Sec. 4.C, one warp per cell:
+// I_Delta = floor(N e_vib^{n+1} / (R Theta) - sum I* + U), then random +-1
+// picks with replacement at position k = floor(w N / 2^32), at most 64 N
+// draws, a decrement meeting level 0 drawing again.  32 draws per round; the
+// acceptance of draw j is decided exactly as in the one-at-a-time loop: a
+// decrement on particle k is accepted iff fewer than lev[k] earlier accepted
+// decrements in the round hit k.  The net level change goes to sums[c].net.
+__global__ void levelfix_kernel(Species sp, int ncell, const CellState* __restrict__ cells,
+                                CellSums* __restrict__ sums, int* __restrict__ lev,
+                                uint32_t* flags, unsigned long long* counters, uint32_t k0,
+                                uint32_t k1) {
   const int lane = threadIdx.x & 31;
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (c >= ncell) return;
-  CellState cs = cells[c];
+  const CellState& cs = cells[c];
   if (!cs.active) return;
-  const double R = gasR(sp);
-  const double Rth = R * sp.theta_v;
+  const double Rth = gasR(sp) * sp.theta_v;
   const long long N = cs.N;
-  const CellSums S = sums[c];
-  // Sec. 4.C: I_Delta = floor(N e_vib^{n+1} / (R Theta) - sum I* + U)
+  const unsigned int step = cs.step;
   long long Id = 0;
   if (lane == 0) {
-    const U4 w = philox4x32_10((uint32_t)c, cs.step, CTAG_IDELTA, 0u, k0, k1);
+    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_IDELTA, 0u, k0, k1);
     const double u = uniform_open<double>(w.x);
-    Id = (long long)floor((double)N * cs.e_vib_tgt / Rth - (double)(long long)S.I + u);
+    Id = (long long)floor((double)N * cs.e_vib_tgt / Rth - (double)(long long)sums[c].I + u);
   }
   Id = __shfl_sync(0xffffffffu, Id, 0);
-  // Random +-1 picks with replacement, k = floor(w N / 2^32), at most 64 N
-  // draws; a decrement meeting level 0 draws again.  32 draws per round; the
-  // acceptance of draw j is decided exactly as in the one-at-a-time loop:
-  // a decrement on particle k is accepted iff fewer than lev[k] earlier
-  // accepted decrements in the round hit k.
   long long remaining = Id, draws = 0;
   const long long cap = 64 * N;
   long long net = 0;
   int* lv = lev + cs.off;
   while (remaining != 0 && draws < cap) {
     const long long j = draws + lane;
-    const U4 w = philox4x32_10((uint32_t)c, cs.step, CTAG_PICK, (uint32_t)(j >> 2), k0, k1);
+    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_PICK, (uint32_t)(j >> 2), k0, k1);
     const uint32_t word = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
     const long long k = (long long)(((unsigned long long)word * (unsigned long long)N) >> 32);
     const bool valid = j < cap;
@@ -386,10 +675,28 @@ __global__ void finalize_kernel(Species sp, int ncell, CellState* __restrict__ c
   }
   if (lane != 0) return;
   if (remaining != 0) atomicOr(flags, (uint32_t)F_VIB_LOOP_CAP);
-  atomicAdd(&counters[C_VIB_DRAWS], (unsigned long long)draws);
+  if (draws) atomicAdd(&counters[C_VIB_DRAWS], (unsigned long long)draws);
+  sums[c].net = net;
+}
 
-  const double invN = 1.0 / (double)N;
-  const double sumI = (double)((long long)S.I + net);
+// Rotational and velocity rescale factors of Sec. 4.C, the moments of the
+// next step (exact under the affine rescale) and the next step's per-cell
+// coefficients; one thread per cell so that the FP64 work of 32 cells shares
+// each warp instruction.
+template <typename T>
+__global__ void cellupdate_kernel(Species sp, int ncell, CellState* __restrict__ cells,
+                                  CollideParams<T>* __restrict__ prm,
+                                  CellSums* __restrict__ sums, uint32_t* flags,
+                                  unsigned long long* counters) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  CellState cs = cells[c];
+  if (!cs.active) return;
+  const double R = gasR(sp);
+  const double Rth = R * sp.theta_v;
+  const CellSums S = sums[c];
+  const double invN = 1.0 / (double)cs.N;
+  const double sumI = (double)((long long)S.I + S.net);
   // rotational scaling
   const double er_star = S.v[9] * invN;
   const double r = er_star > 0.0 ? cs.e_rot_tgt / er_star : 1.0;
@@ -420,7 +727,6 @@ __global__ void finalize_kernel(Species sp, int ncell, CellState* __restrict__ c
   } else {
     s = sqrt(rad);
   }
-  // moments of step n+1 (exact under the affine rescale)
   for (int i = 0; i < 3; ++i) { cs.U[i] = Un[i]; cs.Us[i] = Us[i]; }
   for (int i = 0; i < 6; ++i) cs.Pi[i] = s * s * Ps[i];
   cs.Ttr = (cs.Pi[0] + cs.Pi[1] + cs.Pi[2]) / (3.0 * R);
@@ -429,6 +735,7 @@ __global__ void finalize_kernel(Species sp, int ncell, CellState* __restrict__ c
   cs.s = s;
   cs.r = r;
   cs.step += 1;
+  cs.maxI = S.maxI + 1;   // the +-1 correction can raise the largest level by one
   CollideParams<T> P;
   write_params<T>(sp, cs, P, flags, counters);
   cells[c] = cs;
@@ -446,6 +753,8 @@ __global__ void finalize_kernel(Species sp, int ncell, CellState* __restrict__ c
 // ---------------------------------------------------------------------------
 constexpr int kMomAcc = 20;
 
+// Per-particle arithmetic in the state precision T; partial sums stay in T
+// within a thread (a few particles) and a warp, then combine in FP64.
 template <typename T>
 __global__ void __launch_bounds__(kBlock)
 moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
@@ -456,26 +765,30 @@ moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tl = tiles[t];
-    const CellState cs = cells[tl.cell];
+    const CellState& cs = cells[tl.cell];
     const long long base = cs.off + tl.start;
-    double a[15];
-    for (int i = 0; i < 15; ++i) a[i] = 0.0;
-    double mean[5] = {0, 0, 0, 0, 0};
+    T a[15];
+    for (int i = 0; i < 15; ++i) a[i] = T(0);
+    T mean[3] = {T(0), T(0), T(0)};
     if (pass == 1 && cs.N > 0) {
-      for (int i = 0; i < 5; ++i) mean[i] = acc_out[(size_t)tl.cell * kMomAcc + i] / (double)cs.N;
+      for (int i = 0; i < 3; ++i)
+        mean[i] = (T)(acc_out[(size_t)tl.cell * kMomAcc + i] / (double)cs.N);
     }
+    const T U0 = (T)cs.U[0], U1 = (T)cs.U[1], U2 = (T)cs.U[2];
+    const T S0 = (T)cs.Us[0], S1 = (T)cs.Us[1], S2 = (T)cs.Us[2];
+    const T sc = (T)cs.s, rc = (T)cs.r;
     for (int k = threadIdx.x; k < tl.count; k += kBlock) {
       const long long e = base + k;
-      const double c0 = cs.U[0] + cs.s * ((double)cx[e] - cs.Us[0]);
-      const double c1 = cs.U[1] + cs.s * ((double)cy[e] - cs.Us[1]);
-      const double c2 = cs.U[2] + cs.s * ((double)cz[e] - cs.Us[2]);
-      const double ep = cs.r * (double)er[e];
-      const double li = (double)lev[e];
+      const T c0 = U0 + sc * (cx[e] - S0);
+      const T c1 = U1 + sc * (cy[e] - S1);
+      const T c2 = U2 + sc * (cz[e] - S2);
+      const T ep = rc * er[e];
+      const T li = (T)lev[e];
       if (pass == 0) {
         a[0] += c0; a[1] += c1; a[2] += c2; a[3] += ep; a[4] += li;
       } else {
-        const double C0 = c0 - mean[0], C1 = c1 - mean[1], C2 = c2 - mean[2];
-        const double q = 0.5 * (C0 * C0 + C1 * C1 + C2 * C2);
+        const T C0 = c0 - mean[0], C1 = c1 - mean[1], C2 = c2 - mean[2];
+        const T q = T(0.5) * (C0 * C0 + C1 * C1 + C2 * C2);
         a[0] += C0 * C0; a[1] += C1 * C1; a[2] += C2 * C2;
         a[3] += C0 * C1; a[4] += C0 * C2; a[5] += C1 * C2;
         a[6] += q * C0; a[7] += q * C1; a[8] += q * C2;
@@ -485,8 +798,8 @@ moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
     }
     const int na = pass == 0 ? 5 : 15;
     for (int i = 0; i < na; ++i) {
-      const double s = warp_sum(a[i]);
-      if (lane == 0) red[wid][i] = s;
+      const T s = warp_sum(a[i]);
+      if (lane == 0) red[wid][i] = (double)s;
     }
     __syncthreads();
     if (threadIdx.x < na) {
@@ -628,11 +941,17 @@ struct usp_ctx {
   double* macc;             // moment accumulators
   double* mout;             // moment output (device)
   double* levsum;
+  float* tab_nb;            // jump tables (FP32 form)
+  float* tab_b;
   uint32_t* flags;
   unsigned long long* counters;
   std::vector<long long> h_uoff;
+  std::vector<long long> h_poff;   // padded segment starts
+  std::vector<float> tune_ms;      // autotuner timings per variant (2, 3, 4)
   int tile;
   int grid_collide;
+  int minb;                 // register-budget variant of the particle pass
+  int grid_by_minb[5];
   long long step;
   long long launches;
   cudaGraphExec_t graph_exec;
@@ -752,25 +1071,72 @@ int prof_end(usp_ctx* c, cudaEvent_t e1) {
   return USP_OK;
 }
 
+template <typename T, int MINB>
+void* collide_fn() {
+  return (void*)collide_kernel<T, MINB>;
+}
+
+template <typename T>
+void* collide_variant(int minb) {
+  return minb == 2 ? collide_fn<T, 2>() : minb == 3 ? collide_fn<T, 3>() : collide_fn<T, 4>();
+}
+
+// Launch the particle pass on the given state / sums buffers.
+template <typename T>
+int launch_collide(usp_ctx* c, int minb, int grid, const Tile* tiles, int ntiles, void* cx,
+                   void* cy, void* cz, void* er, int* lev, CellSums* sums, uint32_t* flags,
+                   unsigned long long* counters) {
+  const size_t smem = 2 * stage_bytes<T>();
+  const CollideParams<T>* prm = (const CollideParams<T>*)c->prm;
+  T* x = (T*)cx; T* y = (T*)cy; T* z = (T*)cz; T* e = (T*)er;
+  const uint32_t a = key0(c), b = key1(c);
+  const float* tn = c->tab_nb;
+  const float* tb = c->tab_b;
+  if (minb == 2)
+    collide_kernel<T, 2><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
+                                                            sums, flags, counters, a, b, tn, tb);
+  else if (minb == 3)
+    collide_kernel<T, 3><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
+                                                            sums, flags, counters, a, b, tn, tb);
+  else
+    collide_kernel<T, 4><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
+                                                            sums, flags, counters, a, b, tn, tb);
+  CK(cudaGetLastError());
+  return USP_OK;
+}
+
+// jump tables for the coming step (FP32 form only)
+int launch_tables(usp_ctx* c) {
+  if (c->precision != USP_FP32) return USP_OK;
+  jumptable_kernel<<<c->ncell, 2 * kJR, 0, c->stream>>>(
+      c->ncell, (const CollideParams<float>*)c->prm, c->cells, c->tab_nb, c->tab_b);
+  CK(cudaGetLastError());
+  return USP_OK;
+}
+
 template <typename T>
 int launch_step(usp_ctx* c) {
   cudaEvent_t e1 = nullptr;
   int rc = prof_begin(c, 0, &e1);
   if (rc) return rc;
-  collide_kernel<T><<<c->grid_collide, kBlock, 0, c->stream>>>(
-      c->tiles, c->ntiles, (const CollideParams<T>*)c->prm, (T*)c->cx, (T*)c->cy, (T*)c->cz,
-      (T*)c->er, c->lev, c->sums, c->flags, c->counters, key0(c), key1(c));
-  CK(cudaGetLastError());
+  rc = launch_collide<T>(c, c->minb, c->grid_collide, c->tiles, c->ntiles, c->cx, c->cy, c->cz,
+                         c->er, c->lev, c->sums, c->flags, c->counters);
+  if (rc) return rc;
   if ((rc = prof_end(c, e1))) return rc;
   if ((rc = prof_begin(c, 1, &e1))) return rc;
   const int warps_per_block = 4;
   const int blocks = (c->ncell + warps_per_block - 1) / warps_per_block;
-  finalize_kernel<T><<<blocks, 32 * warps_per_block, 0, c->stream>>>(
-      c->sp, c->ncell, c->cells, (CollideParams<T>*)c->prm, c->sums, c->lev, c->flags,
-      c->counters, key0(c), key1(c));
+  levelfix_kernel<<<blocks, 32 * warps_per_block, 0, c->stream>>>(
+      c->sp, c->ncell, c->cells, c->sums, c->lev, c->flags, c->counters, key0(c), key1(c));
   CK(cudaGetLastError());
+  cellupdate_kernel<T><<<(c->ncell + 63) / 64, 64, 0, c->stream>>>(
+      c->sp, c->ncell, c->cells, (CollideParams<T>*)c->prm, c->sums, c->flags, c->counters);
+  CK(cudaGetLastError());
+  if ((rc = launch_tables(c))) return rc;
   return prof_end(c, e1);
 }
+
+int kernels_per_step(const usp_ctx* c) { return c->precision == USP_FP32 ? 4 : 3; }
 
 int step_once(usp_ctx* c) {
   return c->precision == USP_FP32 ? launch_step<float>(c) : launch_step<double>(c);
@@ -804,6 +1170,8 @@ int init_params(usp_ctx* c) {
                                                   (CollideParams<T>*)c->prm, c->flags, c->counters);
   CK(cudaGetLastError());
   c->launches += 2;
+  if ((rc = launch_tables(c))) return rc;
+  c->launches += c->precision == USP_FP32 ? 1 : 0;
   return USP_OK;
 }
 
@@ -869,6 +1237,76 @@ int build_graph(usp_ctx* c, int steps) {
   CK(cudaGraphInstantiate(&c->graph_exec, g, 0));
   c->graph = g;
   c->graph_steps = steps;
+  return USP_OK;
+}
+
+// Autotuner of the particle pass: times each register-budget variant (2, 3
+// or 4 resident blocks per SM) on a scratch copy of a prefix of the tile list
+// (up to ~8M particles, so the data exceeds L2) and keeps the fastest.
+template <typename T>
+int autotune(usp_ctx* c) {
+  const size_t es = sizeof(T);
+  long long np = 0;
+  int nt = 0;
+  std::vector<Tile> ht(c->ntiles);
+  CK(cudaMemcpy(ht.data(), c->tiles, sizeof(Tile) * c->ntiles, cudaMemcpyDeviceToHost));
+  int last_cell = 0;
+  while (nt < c->ntiles && np < (8ll << 20)) {
+    np += ht[nt].count;
+    last_cell = ht[nt].cell;
+    ++nt;
+  }
+  // include whole cells only: extend to the end of last_cell's tiles
+  while (nt < c->ntiles && ht[nt].cell == last_cell) ++nt;
+  const long long end = c->h_poff[last_cell] +
+      ((c->h_uoff[last_cell + 1] - c->h_uoff[last_cell]) + kAlign - 1) / kAlign * kAlign;
+  const size_t bytes = (size_t)end * (4 * es + 4);
+  unsigned char* scratch = (unsigned char*)dev_alloc(c, bytes + sizeof(CellSums) * c->ncell + 512);
+  if (!scratch) return USP_ENOMEM;
+  void* sx = scratch; void* sy = scratch + end * es; void* sz = scratch + 2 * end * es;
+  void* se = scratch + 3 * end * es;
+  int* sl = (int*)(scratch + 4 * end * es);
+  CellSums* ssum = (CellSums*)(scratch + ((bytes + 255) & ~(size_t)255));
+  uint32_t* sflags = (uint32_t*)((unsigned char*)ssum + sizeof(CellSums) * c->ncell);
+  unsigned long long* scnt = (unsigned long long*)((unsigned char*)sflags + 256);
+  CK(cudaMemcpyAsync(sx, c->cx, end * es, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(sy, c->cy, end * es, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(sz, c->cz, end * es, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(se, c->er, end * es, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(sl, c->lev, end * 4, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemsetAsync(ssum, 0, sizeof(CellSums) * c->ncell + 512, c->stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_mb = 3;
+  c->tune_ms.assign(3, 0.f);
+  for (int mb = 2; mb <= 4; ++mb) {
+    const int grid = std::max(1, std::min(nt, c->grid_by_minb[mb]));
+    int rc = launch_collide<T>(c, mb, grid, c->tiles, nt, sx, sy, sz, se, sl, ssum, sflags, scnt);
+    if (rc) return rc;
+    CK(cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < 3; ++r) {
+      rc = launch_collide<T>(c, mb, grid, c->tiles, nt, sx, sy, sz, se, sl, ssum, sflags, scnt);
+      if (rc) return rc;
+    }
+    CK(cudaEventRecord(e1, c->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    c->tune_ms[mb - 2] = ms / 3.f;
+    if (ms < best) { best = ms; best_mb = mb; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->launches += 12;
+  c->minb = best_mb;
+  c->grid_collide = c->grid_by_minb[best_mb];
+  CK(cudaStreamSynchronize(c->stream));
+  if (!c->cfg.alloc) cudaFree(scratch);
+  else if (c->cfg.free_) c->cfg.free_(scratch, c->cfg.alloc_user);
+  c->owned.erase(std::find(c->owned.begin(), c->owned.end(), (void*)scratch));
+  c->device_bytes -= (long long)(((bytes + sizeof(CellSums) * c->ncell + 512) + 255) & ~(size_t)255);
   return USP_OK;
 }
 
@@ -968,6 +1406,7 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
     CellState& s = hc[i];
     std::memset(&s, 0, sizeof(s));
     s.off = off;
+    c->h_poff.push_back(off);
     s.N = h_offsets[i + 1] - h_offsets[i];
     s.pid0 = (unsigned int)h_offsets[i];
     s.step = (unsigned int)cfg->step0;
@@ -992,6 +1431,13 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   c->macc = (double*)dev_alloc(c, sizeof(double) * kMomAcc * n_cells);
   c->mout = (double*)dev_alloc(c, sizeof(double) * USP_NMOM * n_cells);
   c->levsum = (double*)dev_alloc(c, sizeof(double) * n_cells);
+  c->tab_nb = nullptr;
+  c->tab_b = nullptr;
+  if (c->precision == USP_FP32) {
+    c->tab_nb = (float*)dev_alloc(c, sizeof(float) * (size_t)n_cells * kJR * kJK);
+    c->tab_b = (float*)dev_alloc(c, sizeof(float) * (size_t)n_cells * kJR * kJK);
+    if (!c->tab_nb || !c->tab_b) return fail(USP_ENOMEM);
+  }
   c->flags = (uint32_t*)dev_alloc(c, 256);
   c->counters = (unsigned long long*)dev_alloc(c, 256);
   if (!c->cx || !c->cy || !c->cz || !c->er || !c->lev || !c->cells || !c->prm || !c->sums ||
@@ -1010,16 +1456,38 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
       cudaMemcpyAsync(c->uoff, c->h_uoff.data(), sizeof(long long) * (n_cells + 1),
                       cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
     return fail(USP_ECUDA);
-  const int tile = cfg->tile > 0 ? (cfg->tile + kAlign - 1) / kAlign * kAlign : 2048;
+  // the particle pass stages fixed tiles of kTileMax; smaller tiles (tests)
+  // split cells more finely but use the same staging buffers
+  const int tile = cfg->tile > 0 ? std::min(kTileMax, (cfg->tile + kAlign - 1) / kAlign * kAlign)
+                                  : kTileMax;
   int rc = build_tiles(c, tile);
   if (rc) return fail(rc);
-  c->grid_collide = std::max(1, std::min(c->ntiles, sm_count() * 4));
+  {
+    // persistent grid per register-budget variant: as many resident blocks
+    // as the SMs hold
+    const size_t smem = 2 * (size_t)kTileMax * (4 * es + sizeof(int));
+    for (int mb = 2; mb <= 4; ++mb) {
+      void* fn = c->precision == USP_FP32 ? collide_variant<float>(mb) : collide_variant<double>(mb);
+      int per_sm = 1;
+      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+              cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem) != cudaSuccess)
+        return fail(USP_ECUDA);
+      c->grid_by_minb[mb] = std::max(1, std::min(c->ntiles, sm_count() * std::max(1, per_sm)));
+    }
+    c->minb = 3;
+    c->grid_collide = c->grid_by_minb[3];
+  }
   if (n > 0) {
     rc = upload_state(c, h_cx, h_cy, h_cz, h_erot, h_lev, false);
     if (rc) return fail(rc);
   }
   rc = c->precision == USP_FP32 ? init_params<float>(c) : init_params<double>(c);
   if (rc) return fail(rc);
+  if (cfg->tile == 0 && n >= (1ll << 20)) {
+    rc = c->precision == USP_FP32 ? autotune<float>(c) : autotune<double>(c);
+    if (rc) return fail(rc);
+  }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(USP_ECUDA);
   *out = c;
   return USP_OK;
@@ -1032,7 +1500,7 @@ int usp_step(usp_ctx* c, int nsteps) {
     for (int i = 0; i < nsteps; ++i) {
       int rc = step_once(c);
       if (rc) return rc;
-      c->launches += 2;
+      c->launches += kernels_per_step(c);
     }
     c->step += nsteps;
     return USP_OK;
@@ -1045,13 +1513,13 @@ int usp_step(usp_ctx* c, int nsteps) {
   int done = 0;
   while (nsteps - done >= c->graph_steps) {
     CK(cudaGraphLaunch(c->graph_exec, c->stream));
-    c->launches += 2 * c->graph_steps;
+    c->launches += kernels_per_step(c) * c->graph_steps;
     done += c->graph_steps;
   }
   for (; done < nsteps; ++done) {
     int rc = step_once(c);
     if (rc) return rc;
-    c->launches += 2;
+    c->launches += kernels_per_step(c);
   }
   c->step += nsteps;
   return USP_OK;
@@ -1196,6 +1664,14 @@ int usp_info(usp_ctx* c, int64_t* np, int* nc, int* prec, int64_t* step, int* ti
 }
 
 int64_t usp_launch_count(usp_ctx* c) { return c ? c->launches : -1; }
+
+int usp_tuning(usp_ctx* c, int* blocks_per_sm, double* ms) {
+  if (!c) return USP_EINVAL;
+  if (blocks_per_sm) *blocks_per_sm = c->minb;
+  if (ms)
+    for (int i = 0; i < 3; ++i) ms[i] = i < (int)c->tune_ms.size() ? c->tune_ms[i] : 0.0;
+  return USP_OK;
+}
 
 int usp_profile_enable(usp_ctx* c, int on) {
   if (!c) return USP_EINVAL;

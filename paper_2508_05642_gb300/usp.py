@@ -35,7 +35,7 @@ C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, 
 
 EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogeneous", "usp_step", "usp_moments",
             "usp_get_particles", "usp_set_particles", "usp_step_host", "usp_status", "usp_sync",
-            "usp_info", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
+            "usp_info", "usp_tuning", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
             "usp_moments_noalloc", "usp_destroy"]
 USP_NOALLOC_MAX_CELLS = 8192
 
@@ -97,6 +97,7 @@ def lib():
             L.usp_sync.argtypes = [_CTX]
             L.usp_info.argtypes = [_CTX, _I64, C.POINTER(C.c_int), C.POINTER(C.c_int), _I64,
                                    C.POINTER(C.c_int), _I64]
+            L.usp_tuning.argtypes = [_CTX, C.POINTER(C.c_int), _D]
             L.usp_launch_count.argtypes = [_CTX]
             L.usp_launch_count.restype = C.c_int64
             L.usp_profile_enable.argtypes = [_CTX, C.c_int]
@@ -263,6 +264,14 @@ def usp_info(ctx: Context) -> dict:
                           C.byref(tl), C.byref(b)), "usp_info")
     return dict(n_particles=np_.value, n_cells=nc.value, precision=pr.value, step=st.value,
                 tile=tl.value, device_bytes=b.value)
+
+
+def usp_tuning(ctx: Context):
+    """(blocks_per_sm of the particle-pass variant in use, autotuner ms[3])."""
+    mb = C.c_int()
+    ms = np.zeros(3)
+    _check(lib().usp_tuning(ctx.h, C.byref(mb), _p(ms, C.c_double)), "usp_tuning")
+    return mb.value, ms
 
 
 def usp_launch_count(ctx: Context) -> int:

@@ -232,3 +232,16 @@ def test_torch_allocator_path():
     m = usp.usp_moments(ctx)
     assert np.all(m[4] > 0)
     ctx.destroy()
+
+
+def test_fp32_hot_levels_match_oracle():
+    """Equilibrium at 20,000 K: mean level ~5.5, levels beyond the kernel's
+    per-cell jump tables (32 rows x 48 values) occur, so both the table scan
+    and its sequential fallback are exercised; every level must equal the
+    oracle's float-decision result."""
+    w = I.homogeneous_single(N=60000, T_tr=20000.0, T_rot=20000.0, T_vib=20000.0, steps=1)
+    r = _run_pair(w, 1, usp.USP_FP32)
+    gl = r["gs"][4]
+    assert gl.max() > 48
+    assert np.mean(gl != r["ost"].lev) < 1e-5
+    _check_moments(r["om"], r["gm"], r["sp"])
