@@ -88,6 +88,22 @@ class Coeffs(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class Channel(C.Structure):
+    _fields_ = [("ny", C.c_int), ("L", C.c_double), ("T_wall", C.c_double), ("g", C.c_double),
+                ("F_num", C.c_double), ("area", C.c_double), ("reconstruct", C.c_int)]
+
+
+NACC = 12
+NFIELD = 13
+
+
+def channel(**kw) -> Channel:
+    c = Channel()
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
 def species(**kw) -> Species:
     s = Species()
     for k, v in kw.items():
@@ -136,6 +152,13 @@ def lib():
             L.orc_homog_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
                                          C.c_int, _I64, _D, _D, _D, _D, _D, _D, _I32, _U32, _U32, _I64]
             L.orc_homog_step.restype = C.c_int
+            L.orc_channel_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
+                                           C.POINTER(Channel), C.c_double, C.c_int64, _D, _D, _D, _D, _D,
+                                           _I32, _U32, _I64, _D, _U32, _I64]
+            L.orc_channel_step.restype = C.c_int
+            L.orc_channel_reconstruct.argtypes = [C.POINTER(Channel), _I64, _D, C.c_int, C.c_double, _D]
+            L.orc_wall_reemit.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_uint32,
+                                          C.c_uint32, C.c_int, C.c_double, C.c_int, _D, _I32]
             _lib = L
     return _lib
 
@@ -302,3 +325,60 @@ def homog_step(sp, form, seed, step0, nsteps, off, ndens, dt, st: State):
     if rc != 0:
         raise ValueError("time step too large for the method in some cell")
     return fl.value, cnt
+
+
+# ---- 1D channel -------------------------------------------------------------
+@dataclass
+class ChannelState:
+    y: np.ndarray
+    cx: np.ndarray
+    cy: np.ndarray
+    cz: np.ndarray
+    erot: np.ndarray
+    lev: np.ndarray
+    pid: np.ndarray
+
+    @classmethod
+    def from_arrays(cls, y, cx, cy, cz, erot, lev, pid=None):
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float64).copy()
+        n = len(y)
+        if pid is None:
+            pid = np.arange(n, dtype=np.uint32)
+        return cls(f(y), f(cx), f(cy), f(cz), f(erot),
+                   np.ascontiguousarray(lev, dtype=np.int32).copy(),
+                   np.ascontiguousarray(pid, dtype=np.uint32).copy())
+
+
+def channel_step(sp, form, seed, step0, nsteps, ch: Channel, dt, st: ChannelState, acc=None):
+    """Advance the channel ``nsteps`` steps in place (arrays end sorted by
+    cell).  Returns (cell offsets, flags, counters)."""
+    n = len(st.y)
+    off = np.zeros(ch.ny + 1, dtype=np.int64)
+    fl = C.c_uint32(0)
+    cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+    accp = _p(acc, C.c_double) if acc is not None else None
+    rc = lib().orc_channel_step(C.byref(sp), form, C.c_uint64(seed), step0, nsteps, C.byref(ch), dt, n,
+                                _p(st.y, C.c_double), _p(st.cx, C.c_double), _p(st.cy, C.c_double),
+                                _p(st.cz, C.c_double), _p(st.erot, C.c_double), _p(st.lev, C.c_int32),
+                                _p(st.pid, C.c_uint32), _p(off, C.c_int64), accp, C.byref(fl),
+                                _p(cnt, C.c_int64))
+    if rc != 0:
+        raise ValueError("time step too large for the method in some cell")
+    return off, fl.value, cnt
+
+
+def channel_reconstruct(ch: Channel, counts, F, cell, y):
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros(NFIELD)
+    lib().orc_channel_reconstruct(C.byref(ch), _p(counts, C.c_int64), _p(F, C.c_double), cell, y,
+                                  _p(out, C.c_double))
+    return out
+
+
+def wall_reemit(sp, form, seed, pid, step, hit, Tw, into_positive_y):
+    out = np.zeros(4)
+    lv = C.c_int32(0)
+    lib().orc_wall_reemit(C.byref(sp), form, C.c_uint64(seed), pid, step, hit, Tw,
+                          1 if into_positive_y else 0, _p(out, C.c_double), C.byref(lv))
+    return out, lv.value

@@ -815,6 +815,13 @@ static void diffuse_reemit(const orc_species* sp, int form, uint64_t seed, uint3
     *lev = (int32_t)floor(-log(orc_uniform(v[0], form)) * Tw / sp->theta_v);
 }
 
+void orc_wall_reemit(const orc_species* sp, int form, uint64_t seed, uint32_t pid, uint32_t step,
+                     int hit, double Tw, int into_positive_y, double out[4], int32_t* lev)
+{
+    diffuse_reemit(sp, form, seed, pid, step, hit, Tw, into_positive_y,
+                   &out[0], &out[1], &out[2], &out[3], lev);
+}
+
 /* Ballistic flight over dt with the body force along x, reflecting off the
  * diffuse plates at y = 0 and y = L; a hit re-emits the particle and the
  * flight continues for the rest of the step.  Returns the x-momentum (per

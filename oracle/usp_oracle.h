@@ -151,6 +151,9 @@ int    orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t 
                         uint32_t* flags, int64_t* counters);
 void   orc_channel_reconstruct(const orc_channel* ch, const int64_t* counts, const double* F,
                                int cell, double y, double* out);
+/* one diffuse re-emission (velocity, eps_rot, level) for tests of the wall law */
+void   orc_wall_reemit(const orc_species* sp, int form, uint64_t seed, uint32_t pid, uint32_t step,
+                       int hit, double Tw, int into_positive_y, double out[4], int32_t* lev);
 
 #ifdef __cplusplus
 }

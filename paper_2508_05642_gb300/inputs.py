@@ -140,3 +140,44 @@ def batched_instances(seed: int = 1, n_inst: int = 4096, nmin: float = 1e3, nmax
                     % (n_inst, int(nmin * scale), int(nmax * scale)), sp, off,
                     np.full(n_inst, n), np.stack([Ttr, Trot, Tvib], axis=1), dt_over_tau_c,
                     Particles(cx, cy, cz, er, lev), seed, steps)
+
+
+@dataclass
+class ChannelWorkload:
+    name: str
+    species: dict
+    channel: dict                # ny, L, T_wall, g, F_num, area, reconstruct
+    dt_over_tau_c: float         # dt = factor * tau_c(n, T_wall)
+    n: float                     # initial number density [1/m^3]
+    y: np.ndarray
+    particles: Particles
+    seed: int
+    steps: int
+    average_last: int
+
+    @property
+    def n_particles(self) -> int:
+        return len(self.y)
+
+
+def channel_poiseuille(seed: int = 1, ny: int = 64, ppc: int = 200, n: float = 1.3240e23,
+                       L: float = 1e-4, T_wall: float = 300.0, g: float = 5.827e7,
+                       dt_over_tau_c: float = 0.2, Z_rot: float = 5.0, Z_vib: float = 50.0,
+                       steps: int = 20000, average_last: int = 10000,
+                       reconstruct: int = 1) -> ChannelWorkload:
+    """Force-driven Poiseuille flow of N2 between diffuse plates (the set-up of
+    Sec. 5.B with a body force in place of the pressure gradient): VSS N2,
+    plate gap 1e-4 m (Kn = 0.1 at n = 1.324e23 m^-3), 64 cells, 200 particles
+    per cell, walls at 300 K, body force 5.827e7 m/s^2 (Mach ~0.1 centreline),
+    dt = 0.2 tau_c.  Particles start uniform in y at rest and equilibrium."""
+    sp = n2_vss_species(Z_rot, Z_vib)
+    rng = np.random.default_rng([seed, 0xC4A7])
+    N = ny * ppc
+    y = rng.uniform(0.0, L, N)
+    p = equilibrium_particles(rng, N, sp["m"], sp["theta_v"], T_tr=T_wall, T_rot=T_wall,
+                              T_vib=T_wall)
+    area = 1.0
+    ch = dict(ny=ny, L=L, T_wall=T_wall, g=g, F_num=n * L * area / N, area=area,
+              reconstruct=reconstruct)
+    return ChannelWorkload("force-driven Poiseuille N2, %d cells x %d particles" % (ny, ppc), sp,
+                           ch, dt_over_tau_c, n, y, p, seed, steps, average_last)
