@@ -52,6 +52,7 @@ def parse():
                     help="shrink particle counts (debug only; the default is the full workload)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--channel-steps", type=int, default=2000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -334,6 +335,30 @@ def run_ours(args, rank, world, local):
                 "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
         c64.destroy()
 
+    # ---- the spatial path: force-driven Poiseuille channel (64 x 200) -----
+    chan = None
+    if args.channel_steps > 0:
+        from paper_2508_05642_gb300 import inputs as I
+        cw = I.channel_poiseuille(seed=1 + 1000 * rank)
+        cdt = cw.dt_over_tau_c * usp.usp_tau_c(cw.species, cw.n, cw.channel["T_wall"])
+        cp = cw.particles
+        cctx = usp.usp_init_channel(cw.species, cw.channel, cdt, cw.y, cp.cx, cp.cy, cp.cz, cp.erot,
+                                    cp.lev, precision=usp.USP_FP32, seed=cw.seed,
+                                    stream=stream.cuda_stream, use_graph=True)
+        usp.usp_step(cctx, 64)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        usp.usp_step(cctx, args.channel_steps)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        cms = max_over_ranks(h0.elapsed_time(h1))
+        chan = {"workload": cw.name + ", FP32 state, reconstruction on",
+                "value": sum_over_ranks(float(cw.n_particles)) * args.channel_steps / (cms / 1e3),
+                "unit": UNIT, "ms_per_step": cms / args.channel_steps,
+                "steps": args.channel_steps}
+        cctx.destroy()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, el, sample = cpu_baseline(w, args.cpu_seconds)
@@ -352,7 +377,8 @@ def run_ours(args, rank, world, local):
                              "finalize_ms": finalize_ms, "ms_per_step_profiled": ms_prof / args.steps,
                              "autotune": {"blocks_per_sm": minb,
                                           "ms_by_blocks_per_sm_2_3_4": [float(x) for x in tune_ms]}},
-                "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "clocks": clk,
+                "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "poiseuille_channel": chan,
+                "clocks": clk,
                 "status": {"flags": int(flags), "counters": [int(x) for x in counters]}}
         print(json.dumps(line), flush=True)
     if dist is not None:

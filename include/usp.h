@@ -120,6 +120,17 @@ typedef struct {
   void* alloc_user;
 } usp_config;
 
+/* 1D channel between two fully diffuse plates at y = 0 and y = L (the
+ * Poiseuille set-up of the paper's Sec. 5.B, driven by a uniform body force
+ * g along x): ny cells of width L / ny, particle weight F_num (real
+ * molecules per simulation particle), cross-section `area` normal to y,
+ * reconstruct = 1 for the first-order reconstruction of Sec. 3.B. */
+typedef struct {
+  int ny;
+  double L, T_wall, g, F_num, area;
+  int reconstruct;
+} usp_channel;
+
 typedef struct usp_ctx usp_ctx;
 
 /* Make device `dev` current for the calling thread (cudaSetDevice) so that
@@ -146,6 +157,35 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
                          int n_cells, const int64_t* h_offsets, const double* h_ndens,
                          const double* h_dt, const double* h_cx, const double* h_cy,
                          const double* h_cz, const double* h_erot, const int32_t* h_lev);
+
+/* Create a context for the 1D channel (usp_channel) holding n particles:
+ * positions h_y in [0, L], velocities, specific rotational energies and
+ * levels as in usp_init_homogeneous, and the particle ids h_pid (the Philox
+ * counter word 0; NULL: ids 0..n-1).  dt is the time step [s].  One step is:
+ * ballistic move with the body force and diffuse-wall re-emission (full
+ * accommodation at T_wall, flight continued for the rest of the step), a
+ * stable sort of the particles by cell, then the collision step of Sec. 4.D
+ * in every cell with the fields interpolated to each particle (Sec. 3.B),
+ * then the conservation scheme of Sec. 4.C.  Particle order after a step is
+ * the cell order (stable).  Returns USP_EINVAL for a particle outside [0, L],
+ * a negative level or invalid sizes.  Synchronises. */
+int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
+                     const usp_channel* ch, double dt, int64_t n, const double* h_y,
+                     const double* h_cx, const double* h_cy, const double* h_cz,
+                     const double* h_erot, const int32_t* h_lev, const uint32_t* h_pid);
+
+/* Channel time averages: while on (1), every step adds, per cell of its
+ * post-step state, N, sum c (3), sum c c (xx yy zz xy xz yz), sum eps, sum I
+ * (12 doubles per cell), plus one to the sampled-step count and the step's
+ * x-momentum (per unit mass) taken by the walls.  usp_channel_read copies
+ * the ny * 12 + 2 doubles to h_acc (synchronises) and clears them if reset. */
+int usp_channel_sample(usp_ctx* ctx, int on);
+int usp_channel_read(usp_ctx* ctx, double* h_acc, int reset);
+
+/* Current channel particles (cell order, conservation rescale applied) to
+ * host arrays of length n; y and pid may be NULL.  Synchronises. */
+int usp_channel_get_particles(usp_ctx* ctx, double* h_y, double* h_cx, double* h_cy,
+                              double* h_cz, double* h_erot, int32_t* h_lev, uint32_t* h_pid);
 
 /* Enqueue nsteps collision steps (Sec. 4.D + Sec. 4.C) on the stream. */
 int usp_step(usp_ctx* ctx, int nsteps);

@@ -1,0 +1,1067 @@
+// usp_channel.cu -- the spatial USP-FPM step in a 1D channel between two
+// fully diffuse plates (the Poiseuille set-up of Kim & Jun, arXiv 2508.05642,
+// Sec. 5.B, force-driven), on sm_103a.
+//
+// One step, in the order of the particle framework the method is built into
+// (move -> sort -> collide per cell, Sec. 4.D):
+//   ch_advect      pending conservation rescale of the previous step, ballistic
+//                  flight with the body force, diffuse-wall re-emission
+//                  (full accommodation at T_wall, flight continued for the
+//                  rest of the step), new cell key
+//   radix passes   stable LSD radix sort of (cell key, index), 8-bit digits
+//   ch_gather      state permuted into cell order
+//   ch_offsets     cell segment starts from the sorted keys
+//   ch_moments     per-cell moments (Sec. 2.A), one warp per cell
+//   ch_coeffs      per-cell coefficients alpha, nu, gamma, targets (Sec. 3.A)
+//   ch_recon       first-order reconstruction of Sec. 3.B: per cell the field
+//                  values and the slopes used on each side of the centroid
+//   ch_collide     per particle: interpolated fields, relaxation temperatures,
+//                  tau D_tr and its Cholesky factor with the Sec. 3.A.3 fix,
+//                  Eqs. update_ci / update_erot / update_evib; cell sums
+//   ch_levelfix    vibrational +-1 correction of Sec. 4.C (warp per cell)
+//   ch_update      rescale factors of Sec. 4.C, kept pending for the next move
+//   ch_sample      (while sampling) time-average sums of the post-step state
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "usp_channel.h"
+
+using namespace usp;
+
+namespace {
+
+constexpr int kNF = 13;            // U(3), T_tr, T_rot, T_vib, Pi(6)
+constexpr int kRB = 256;           // radix block
+constexpr int kRPT = 16;           // keys per thread per radix block
+constexpr int kChunk = kRB * kRPT;
+constexpr int kNAcc = 12;          // time-average sums per cell
+constexpr int kWallHitCap = 16;
+constexpr uint32_t PTAG_WALL_A = 2u, PTAG_WALL_B = 3u;
+
+struct ChCell {
+  double U[3], Pi[6];
+  double Ttr, Trot, Tvib, ebar;
+  double n;
+  double alpha, nu_ref, B, mu_p, Pr, gtr, gtv, grv;
+  double e_rot_tgt, e_vib_tgt;
+  double Un[3], Us[3], s, r;   // pending rescale: c = Un + s (c* - Us), eps = r eps*
+  long long off, N;
+  int active, maxI;
+};
+
+template <typename T>
+struct ChParams {
+  T alpha, nu_ref, B, mu_p, Pr, gtr, gtv, grv;
+  T R, theta, dt, yc;
+  T F[kNF], Sm[kNF], Sp[kNF];   // cell values; slopes used below / above the centroid
+  int active, pad;
+};
+
+struct ChSums {
+  double v[10];
+  unsigned long long I;
+  long long net;
+  int maxI, pad;
+};
+
+__device__ __forceinline__ unsigned lane_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// e_vib in the working precision
+__device__ __forceinline__ float evib_t(float Rth, float theta, float T) {
+  return T > 0.0f ? Rth / expm1f(theta / T) : 0.0f;
+}
+__device__ __forceinline__ double evib_t(double Rth, double theta, double T) {
+  return T > 0.0 ? Rth / expm1(theta / T) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// move
+// ---------------------------------------------------------------------------
+// Diffuse re-emission at T_w (double): Rayleigh normal speed into the gas,
+// Maxwellian tangential components, exponential eps_rot, geometric level.
+template <typename T>
+__device__ void wall_emit(const Species& sp, uint32_t pid, uint32_t step, int hit, double Tw,
+                          bool into_pos, uint32_t k0, uint32_t k1, double& vx, double& vy,
+                          double& vz, double& e, int& l) {
+  const double R = gasR(sp);
+  const U4 w = philox4x32_10(pid, step, PTAG_WALL_A, (uint32_t)hit, k0, k1);
+  const U4 v = philox4x32_10(pid, step, PTAG_WALL_B, (uint32_t)hit, k0, k1);
+  const double vn = sqrt(-2.0 * R * Tw * log((double)uniform_open<T>(w.x)));
+  vy = into_pos ? vn : -vn;
+  double g1, g2;
+  box_muller((double)uniform_open<T>(w.y), (double)uniform_open<T>(w.z), g1, g2);
+  const double s = sqrt(R * Tw);
+  vx = s * g1;
+  vz = s * g2;
+  e = -R * Tw * log((double)uniform_open<T>(w.w));
+  l = (int)floor(-log((double)uniform_open<T>(v.x)) * Tw / sp.theta_v);
+}
+
+template <typename T>
+__global__ void ch_advect(long long n, int ny, double L, double dy, double Tw, double g, double dt,
+                          const int* __restrict__ keycell, const ChCell* __restrict__ cells,
+                          T* __restrict__ y, T* __restrict__ cx, T* __restrict__ cy,
+                          T* __restrict__ cz, T* __restrict__ er, int* __restrict__ lev,
+                          const uint32_t* __restrict__ pid, int* __restrict__ keyout,
+                          int* __restrict__ idxout, const long long* __restrict__ dstep, Species sp,
+                          uint32_t k0, uint32_t k1, double* wallmom, uint32_t* flags,
+                          unsigned long long* counters) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint32_t step = (uint32_t)*dstep;
+  const ChCell& cc = cells[keycell[j]];
+  // pending conservation rescale of the previous step
+  T vx = (T)cc.Un[0] + (T)cc.s * (cx[j] - (T)cc.Us[0]);
+  T vy = (T)cc.Un[1] + (T)cc.s * (cy[j] - (T)cc.Us[1]);
+  T vz = (T)cc.Un[2] + (T)cc.s * (cz[j] - (T)cc.Us[2]);
+  T e = (T)cc.r * er[j];
+  int l = lev[j];
+  T yy = y[j];
+  T t_left = (T)dt;
+  double mom = 0.0;
+  int hits = 0;
+  for (;;) {
+    const T yn = yy + vy * t_left;
+    if (yn >= T(0) && yn <= (T)L) {
+      yy = yn;
+      vx += (T)g * t_left;
+      break;
+    }
+    if (hits >= kWallHitCap) {
+      atomicOr(flags, (uint32_t)F_WALL_CAP);
+      yy = yn < T(0) ? T(0) : (T)L;
+      vx += (T)g * t_left;
+      break;
+    }
+    const T wall = yn < T(0) ? T(0) : (T)L;
+    T t_hit = (wall - yy) / vy;
+    t_hit = t_hit < T(0) ? T(0) : (t_hit > t_left ? t_left : t_hit);
+    vx += (T)g * t_hit;
+    mom += (double)vx;
+    yy = wall;
+    t_left -= t_hit;
+    double ox, oy, oz, oe;
+    int ol;
+    wall_emit<T>(sp, pid[j], step, hits, Tw, wall == T(0), k0, k1, ox, oy, oz, oe, ol);
+    vx = (T)ox; vy = (T)oy; vz = (T)oz; e = (T)oe; l = ol;
+    mom -= (double)vx;
+    hits += 1;
+  }
+  if (hits) {
+    atomicAdd(wallmom, mom);
+    atomicAdd(&counters[C_WALL_HITS], (unsigned long long)hits);
+  }
+  y[j] = yy; cx[j] = vx; cy[j] = vy; cz[j] = vz; er[j] = e; lev[j] = l;
+  int k = (int)floor(yy / (T)dy);
+  k = k < 0 ? 0 : (k >= ny ? ny - 1 : k);
+  keyout[j] = k;
+  idxout[j] = (int)j;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (key, index), 8-bit digits
+// ---------------------------------------------------------------------------
+__global__ void rad_hist(const int* __restrict__ key, long long n, int shift, int* __restrict__ bh) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const long long b = (long long)blockIdx.x * kChunk;
+  for (int r = 0; r < kRPT; ++r) {
+    const long long i = b + (long long)r * kRB + threadIdx.x;
+    if (i < n) atomicAdd(&h[(key[i] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  bh[(size_t)blockIdx.x * 256 + threadIdx.x] = h[threadIdx.x];
+}
+
+// digit-major exclusive scan of the block histograms, in place (one block)
+__global__ void rad_scan(int* __restrict__ bh, int nblk) {
+  __shared__ long long base[256];
+  const int d = threadIdx.x;
+  long long tot = 0;
+  for (int b = 0; b < nblk; ++b) tot += bh[(size_t)b * 256 + d];
+  base[d] = tot;
+  __syncthreads();
+  if (d == 0) {
+    long long run = 0;
+    for (int i = 0; i < 256; ++i) {
+      const long long t = base[i];
+      base[i] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+  long long run = base[d];
+  for (int b = 0; b < nblk; ++b) {
+    const int v = bh[(size_t)b * 256 + d];
+    bh[(size_t)b * 256 + d] = (int)run;
+    run += v;
+  }
+}
+
+__global__ void rad_scatter(const int* __restrict__ kin, const int* __restrict__ iin,
+                            int* __restrict__ kout, int* __restrict__ iout, long long n, int shift,
+                            const int* __restrict__ bh) {
+  __shared__ int cnt[kRB / 32][256];
+  __shared__ int run[256];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  run[t] = bh[(size_t)blockIdx.x * 256 + t];
+  const long long b = (long long)blockIdx.x * kChunk;
+  for (int r = 0; r < kRPT; ++r) {
+    for (int q = 0; q < kRB / 32; ++q) cnt[q][t] = 0;
+    __syncthreads();
+    const long long i = b + (long long)r * kRB + t;
+    const bool valid = i < n;
+    const int kk = valid ? kin[i] : 0;
+    const int d = valid ? ((kk >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lane_lt());
+    if (valid && rank == 0) cnt[w][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int pre = 0;
+      for (int q = 0; q < w; ++q) pre += cnt[q][d];
+      const int pos = run[d] + pre + rank;
+      kout[pos] = kk;
+      iout[pos] = iin[i];
+    }
+    __syncthreads();
+    int tot = 0;
+    for (int q = 0; q < kRB / 32; ++q) tot += cnt[q][t];
+    run[t] += tot;
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void ch_gather(long long n, const int* __restrict__ idx, const T* __restrict__ y0,
+                          const T* __restrict__ x0, const T* __restrict__ vy0,
+                          const T* __restrict__ z0, const T* __restrict__ e0,
+                          const int* __restrict__ l0, const uint32_t* __restrict__ p0,
+                          T* __restrict__ y1, T* __restrict__ x1, T* __restrict__ vy1,
+                          T* __restrict__ z1, T* __restrict__ e1, int* __restrict__ l1,
+                          uint32_t* __restrict__ p1) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int s = idx[j];
+  y1[j] = y0[s]; x1[j] = x0[s]; vy1[j] = vy0[s]; z1[j] = z0[s]; e1[j] = e0[s];
+  l1[j] = l0[s]; p1[j] = p0[s];
+}
+
+__global__ void ch_offsets(long long n, int ny, const int* __restrict__ key,
+                           long long* __restrict__ off) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n == 0) {
+    if (j <= ny) off[j] = 0;
+    return;
+  }
+  if (j >= n) return;
+  const int k = key[j];
+  const int prev = j > 0 ? key[j - 1] : -1;
+  for (int c = prev + 1; c <= k; ++c) off[c] = j;
+  if (j == n - 1)
+    for (int c = k + 1; c <= ny; ++c) off[c] = n;
+}
+
+// ---------------------------------------------------------------------------
+// per-cell moments, coefficients, reconstruction
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void ch_moments(int ny, const long long* __restrict__ off, const T* __restrict__ cx,
+                           const T* __restrict__ cy, const T* __restrict__ cz,
+                           const T* __restrict__ er, const int* __restrict__ lev,
+                           ChCell* __restrict__ cells, Species sp, unsigned long long* counters) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= ny) return;
+  const long long b = off[c], e = off[c + 1], N = e - b;
+  T a0 = 0, a1 = 0, a2 = 0, ae = 0, al = 0;
+  for (long long j = b + lane; j < e; j += 32) {
+    a0 += cx[j]; a1 += cy[j]; a2 += cz[j]; ae += er[j]; al += (T)lev[j];
+  }
+  const double s0 = (double)wsum(a0), s1 = (double)wsum(a1), s2 = (double)wsum(a2);
+  const double se = (double)wsum(ae), sl = (double)wsum(al);
+  const double inv = N > 0 ? 1.0 / (double)N : 0.0;
+  const T m0 = (T)(s0 * inv), m1 = (T)(s1 * inv), m2 = (T)(s2 * inv);
+  T p[6] = {0, 0, 0, 0, 0, 0};
+  for (long long j = b + lane; j < e; j += 32) {
+    const T C0 = cx[j] - m0, C1 = cy[j] - m1, C2 = cz[j] - m2;
+    p[0] += C0 * C0; p[1] += C1 * C1; p[2] += C2 * C2;
+    p[3] += C0 * C1; p[4] += C0 * C2; p[5] += C1 * C2;
+  }
+  double P[6];
+  for (int i = 0; i < 6; ++i) P[i] = (double)wsum(p[i]) * inv;
+  if (lane != 0) return;
+  ChCell& cs = cells[c];
+  const double R = gasR(sp);
+  cs.off = b;
+  cs.N = N;
+  cs.active = N >= 2;
+  cs.U[0] = s0 * inv; cs.U[1] = s1 * inv; cs.U[2] = s2 * inv;
+  // identity pending rescale until the cell is updated
+  for (int i = 0; i < 3; ++i) { cs.Un[i] = 0.0; cs.Us[i] = 0.0; }
+  cs.s = 1.0;
+  cs.r = 1.0;
+  if (!cs.active) {
+    atomicAdd(&counters[C_SKIPPED_CELLS], 1ull);
+    return;
+  }
+  for (int i = 0; i < 6; ++i) cs.Pi[i] = P[i];
+  cs.Ttr = (P[0] + P[1] + P[2]) / (3.0 * R);
+  cs.Trot = se * inv / R;
+  cs.ebar = sl * inv;
+  cs.Tvib = T_vib_of_level(sp, cs.ebar);
+}
+
+__global__ void ch_coeffs(int ny, double F_num, double vol, double dt, ChCell* __restrict__ cells,
+                          Species sp, uint32_t* flags) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ny) return;
+  ChCell& cs = cells[c];
+  if (!cs.active) return;
+  cs.n = (double)cs.N * F_num / vol;
+  const CellCoeffs k = cell_coeffs(sp, cs.n, dt, cs.Ttr, cs.Trot, cs.Tvib);
+  if (!k.ok) {
+    atomicOr(flags, (uint32_t)F_A_NONPOS);
+    cs.active = 0;
+    return;
+  }
+  cs.alpha = k.alpha; cs.nu_ref = k.nu_ref; cs.B = k.B; cs.mu_p = k.mu_p; cs.Pr = k.Pr;
+  cs.gtr = k.g_tr_rot; cs.gtv = k.g_tr_vib; cs.grv = k.g_rot_vib;
+  cs.e_rot_tgt = k.e_rot_tgt;
+  cs.e_vib_tgt = k.e_vib_tgt;
+}
+
+__device__ __forceinline__ void cell_fields(const ChCell& c, double* f) {
+  f[0] = c.U[0]; f[1] = c.U[1]; f[2] = c.U[2];
+  f[3] = c.Ttr; f[4] = c.Trot; f[5] = c.Tvib;
+  for (int i = 0; i < 6; ++i) f[6 + i] = c.Pi[i];
+}
+
+// Sec. 3.B in one dimension: the line through the cell average at the
+// centroid and the neighbour's average at its centroid, the neighbour on the
+// particle's side, or on the other side when that one is a wall or holds
+// fewer than two particles.
+template <typename T>
+__global__ void ch_recon(int ny, double dy, int recon, double dt, const ChCell* __restrict__ cells,
+                         ChParams<T>* __restrict__ prm, Species sp) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ny) return;
+  const ChCell& cs = cells[c];
+  ChParams<T> P;
+  P.active = cs.active;
+  P.pad = 0;
+  P.alpha = (T)cs.alpha; P.nu_ref = (T)cs.nu_ref; P.B = (T)cs.B; P.mu_p = (T)cs.mu_p;
+  P.Pr = (T)cs.Pr; P.gtr = (T)cs.gtr; P.gtv = (T)cs.gtv; P.grv = (T)cs.grv;
+  P.R = (T)gasR(sp); P.theta = (T)sp.theta_v; P.dt = (T)dt;
+  P.yc = (T)((c + 0.5) * dy);
+  double f[kNF];
+  cell_fields(cs, f);
+  auto valid = [&](int k) { return k >= 0 && k < ny && cells[k].active; };
+  const int up = valid(c + 1) ? c + 1 : (valid(c - 1) ? c - 1 : -1);
+  const int dn = valid(c - 1) ? c - 1 : (valid(c + 1) ? c + 1 : -1);
+  double fu[kNF], fd[kNF];
+  if (up >= 0) cell_fields(cells[up], fu);
+  if (dn >= 0) cell_fields(cells[dn], fd);
+  for (int i = 0; i < kNF; ++i) {
+    P.F[i] = (T)f[i];
+    P.Sp[i] = (recon && up >= 0) ? (T)((fu[i] - f[i]) / ((up - c) * dy)) : T(0);
+    P.Sm[i] = (recon && dn >= 0) ? (T)((fd[i] - f[i]) / ((dn - c) * dy)) : T(0);
+  }
+  prm[c] = P;
+}
+
+// ---------------------------------------------------------------------------
+// per-particle collision with interpolated fields (working precision T)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ bool chol3_t(const T* M, T* L) {
+  if (!(M[0] > T(0))) return false;
+  const T l00 = sqrt(M[0]);
+  const T l10 = M[3] / l00, l20 = M[4] / l00;
+  const T d1 = M[1] - l10 * l10;
+  if (!(d1 > T(0))) return false;
+  const T l11 = sqrt(d1);
+  const T l21 = (M[5] - l20 * l10) / l11;
+  const T d2 = M[2] - l20 * l20 - l21 * l21;
+  if (!(d2 > T(0))) return false;
+  L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = sqrt(d2);
+  return true;
+}
+
+template <typename T>
+__device__ __forceinline__ void relax_t(const ChParams<T>& P, T alpha, const T* f, T& ttr, T& trot,
+                                        T& evr, bool& cl) {
+  const T oma2 = T(1) - alpha * alpha;
+  ttr = f[3] - (P.gtr * (f[3] - f[4]) + P.gtv * (f[3] - f[5])) / (oma2 * T(1.5) * P.R);
+  trot = f[4] + (P.gtr * (f[3] - f[4]) - P.grv * (f[4] - f[5])) / (oma2 * P.R);
+  evr = evib_t(P.R * P.theta, P.theta, f[5]) + (P.gtv * (f[3] - f[5]) + P.grv * (f[4] - f[5])) / oma2;
+  cl = false;
+  if (ttr < T(0)) { ttr = T(0); cl = true; }
+  if (trot < T(0)) { trot = T(0); cl = true; }
+  if (evr < T(0)) { evr = T(0); cl = true; }
+}
+
+template <typename T>
+__global__ void ch_collide(int ny, const ChCell* __restrict__ cells, const ChParams<T>* __restrict__ prm,
+                           const T* __restrict__ y, T* __restrict__ cx, T* __restrict__ cy,
+                           T* __restrict__ cz, T* __restrict__ er, int* __restrict__ lev,
+                           const uint32_t* __restrict__ pid, ChSums* __restrict__ sums,
+                           const long long* __restrict__ dstep, uint32_t k0, uint32_t k1,
+                           uint32_t* flags, unsigned long long* counters) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= ny) return;
+  const ChCell& cs = cells[c];
+  if (!cs.active) return;
+  const ChParams<T>& P = prm[c];
+  const uint32_t step = (uint32_t)*dstep;
+  const T Uc0 = (T)cs.U[0], Uc1 = (T)cs.U[1], Uc2 = (T)cs.U[2];
+  T acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  T accI = 0;
+  int maxI = 0;
+  uint32_t fl = 0;
+  unsigned long long nfix = 0, nfb = 0, ncl = 0, npb = 0;
+  for (long long j = cs.off + lane; j < cs.off + cs.N; j += 32) {
+    // interpolated fields at the particle
+    const T dyv = y[j] - P.yc;
+    const bool above = dyv >= T(0);
+    T f[kNF];
+#pragma unroll
+    for (int i = 0; i < kNF; ++i) f[i] = P.F[i] + (above ? P.Sp[i] : P.Sm[i]) * dyv;
+    if (!(f[3] > T(0)) || !(f[4] > T(0)) || !(f[5] >= T(0))) {
+#pragma unroll
+      for (int i = 0; i < kNF; ++i) f[i] = P.F[i];
+      ++nfb;
+    }
+    // relaxation temperatures and tau D_tr
+    T alpha = P.alpha, nu = P.nu_ref, ttr, trot, evr;
+    bool cl;
+    relax_t(P, alpha, f, ttr, trot, evr, cl);
+    const T RT = P.R * f[3];
+    T M[6], L[6];
+    auto fill = [&](T nu_) {
+      M[0] = P.R * ttr + nu_ * (f[6] - RT);
+      M[1] = P.R * ttr + nu_ * (f[7] - RT);
+      M[2] = P.R * ttr + nu_ * (f[8] - RT);
+      M[3] = nu_ * f[9]; M[4] = nu_ * f[10]; M[5] = nu_ * f[11];
+    };
+    fill(nu);
+    if (!chol3_t(M, L)) {
+      ++nfix;
+      T lmin, lmax;
+      sym3_minmax(f + 6, lmin, lmax);
+      bool ok = false;
+      for (int pass = 0; pass < 4 && !ok; ++pass) {
+        nu = P.nu_ref;
+        if (P.nu_ref <= T(0)) {
+          if (lmax - RT > T(0)) nu = fmax(nu, -P.R * ttr / (lmax - RT));
+        } else {
+          if (RT - lmin > T(0)) nu = fmin(nu, P.R * ttr / (RT - lmin));
+        }
+        nu = nu * (T(1) - T(1e-6));
+        T a2 = (nu - P.B) / (nu - T(1));
+        a2 = fmin(fmax(a2, T(0)), T(1) - (sizeof(T) == 4 ? T(1e-7) : T(1e-12)));
+        const T ap = sqrt(a2), am = -ap;
+        const T prp = T(2) * P.mu_p * (T(1) - ap * ap * ap) / (P.dt * (T(1) + ap * ap * ap));
+        const T prm_ = T(2) * P.mu_p * (T(1) - am * am * am) / (P.dt * (T(1) + am * am * am));
+        alpha = (fabs(prm_ - P.Pr) < fabs(prp - P.Pr)) ? am : ap;
+        bool cl2;
+        relax_t(P, alpha, f, ttr, trot, evr, cl2);
+        cl = cl || cl2;
+        fill(nu);
+        ok = chol3_t(M, L);
+      }
+      if (!ok) {
+        fl |= F_CHOL_FAIL_AFTER_FIX;
+        const T sq = sqrt(P.R * ttr);
+        L[0] = sq; L[1] = 0; L[2] = sq; L[3] = 0; L[4] = 0; L[5] = sq;
+      }
+    }
+    if (cl) { fl |= F_TREL_CLAMP; ++ncl; }
+    // draws
+    const uint32_t id = pid[j];
+    const U4 w = philox4x32_10(id, step, PTAG_NORMALS, 0u, k0, k1);
+    T g0, g1, g2, g3;
+    box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
+    box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
+    const U4 w2 = philox4x32_10(id, step, PTAG_JUMPS, 0u, k0, k1);
+    // Eq. update_ci about the interpolated bulk velocity
+    const T a2 = alpha * alpha, sq = sqrt(T(1) - a2);
+    const T v0 = f[0] + alpha * (cx[j] - f[0]) + sq * (L[0] * g0);
+    const T v1 = f[1] + alpha * (cy[j] - f[1]) + sq * (L[1] * g0 + L[2] * g1);
+    const T v2 = f[2] + alpha * (cz[j] - f[2]) + sq * (L[3] * g0 + L[4] * g1 + L[5] * g2);
+    cx[j] = v0; cy[j] = v1; cz[j] = v2;
+    // Eq. update_erot
+    const T a = P.R * trot * (T(1) - a2) / T(2);
+    const T root = sqrt(er[j]) * alpha + sqrt(a) * g3;
+    const T en = a + root * root;
+    er[j] = en;
+    // Eq. update_evib
+    const T eb = evr / (P.R * P.theta);
+    const T p_nb = T(1) / (T(1) + eb * (T(1) - a2));
+    const T p_b = (T(1) + eb) * (T(1) - a2);
+    const int I = lev[j];
+    uint32_t f1 = 0;
+    const int up = sample_nb<T>(I + 1, p_nb, uniform_open<T>(w2.x), f1);
+    const int dn = sample_b<T>(I, p_b, uniform_open<T>(w2.y), f1);
+    if (f1 & F_PB_CLAMP) ++npb;
+    fl |= f1;
+    const int ln = I + up - dn;
+    lev[j] = ln;
+    maxI = max(maxI, ln);
+    const T d0 = v0 - Uc0, d1 = v1 - Uc1, d2 = v2 - Uc2;
+    acc[0] += d0; acc[1] += d1; acc[2] += d2;
+    acc[3] += d0 * d0; acc[4] += d1 * d1; acc[5] += d2 * d2;
+    acc[6] += d0 * d1; acc[7] += d0 * d2; acc[8] += d1 * d2;
+    acc[9] += en;
+    accI += (T)ln;
+  }
+  double s[11];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) s[i] = (double)wsum(acc[i]);
+  s[10] = (double)wsum(accI);
+  const unsigned long long fix = wsum(nfix), fb = wsum(nfb), ncl2 = wsum(ncl), pb = wsum(npb);
+  const int mI = __reduce_max_sync(0xffffffffu, maxI);
+  const uint32_t fla = __reduce_or_sync(0xffffffffu, fl);
+  if (lane != 0) return;
+  ChSums& S = sums[c];
+  for (int i = 0; i < 10; ++i) S.v[i] = s[i];
+  S.I = (unsigned long long)(long long)llrint(s[10]);
+  S.net = 0;
+  S.maxI = mI;
+  if (fla) atomicOr(flags, fla);
+  if (fix) atomicAdd(&counters[C_CHOL_FIX], fix);
+  if (fb) atomicAdd(&counters[C_INTERP_FALLBACK], fb);
+  if (ncl2) atomicAdd(&counters[C_TREL_CLAMP], ncl2);
+  if (pb) atomicAdd(&counters[C_PB_CLAMP], pb);
+}
+
+// vibrational +-1 correction (Sec. 4.C), one warp per cell; same acceptance
+// rule as the one-at-a-time loop (see the homogeneous path)
+__global__ void ch_levelfix(int ny, const ChCell* __restrict__ cells, ChSums* __restrict__ sums,
+                            int* __restrict__ lev, const long long* __restrict__ dstep, Species sp,
+                            uint32_t k0, uint32_t k1, uint32_t* flags,
+                            unsigned long long* counters) {
+  const int lane = threadIdx.x & 31;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= ny) return;
+  const ChCell& cs = cells[c];
+  if (!cs.active) return;
+  const uint32_t step = (uint32_t)*dstep;
+  const double Rth = gasR(sp) * sp.theta_v;
+  const long long N = cs.N;
+  long long Id = 0;
+  if (lane == 0) {
+    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_IDELTA, 0u, k0, k1);
+    const double u = uniform_open<double>(w.x);
+    Id = (long long)floor((double)N * cs.e_vib_tgt / Rth - (double)(long long)sums[c].I + u);
+  }
+  Id = __shfl_sync(0xffffffffu, Id, 0);
+  long long remaining = Id, draws = 0, net = 0;
+  const long long cap = 64 * N;
+  int* lv = lev + cs.off;
+  while (remaining != 0 && draws < cap) {
+    const long long j = draws + lane;
+    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_PICK, (uint32_t)(j >> 2), k0, k1);
+    const uint32_t word = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
+    const long long k = (long long)(((unsigned long long)word * (unsigned long long)N) >> 32);
+    const bool valid = j < cap;
+    bool accept;
+    if (remaining > 0) {
+      accept = valid;
+    } else {
+      const int cur = valid ? __ldcg(&lv[k]) : 0;
+      const unsigned grp = __match_any_sync(0xffffffffu, valid ? k : -1ll);
+      accept = valid && __popc(grp & lane_lt()) < cur;
+    }
+    const unsigned am = __ballot_sync(0xffffffffu, accept);
+    const long long need = remaining > 0 ? remaining : -remaining;
+    const int nacc = __popc(am);
+    const int take = (int)(nacc < need ? nacc : need);
+    const bool eff = accept && __popc(am & lane_lt()) < take;
+    __syncwarp();
+    if (eff) atomicAdd(&lv[k], remaining > 0 ? 1 : -1);
+    __syncwarp();
+    long long used = 32;
+    if (take == need && take > 0) {
+      unsigned m = am;
+      for (int i = 1; i < take; ++i) m &= m - 1;
+      used = __ffs((int)m);
+    }
+    if (draws + used > cap) used = cap - draws;
+    draws += used;
+    if (remaining > 0) { remaining -= take; net += take; }
+    else { remaining += take; net -= take; }
+  }
+  if (lane != 0) return;
+  if (remaining != 0) atomicOr(flags, (uint32_t)F_VIB_LOOP_CAP);
+  if (draws) atomicAdd(&counters[C_VIB_DRAWS], (unsigned long long)draws);
+  sums[c].net = net;
+}
+
+// rescale factors of Sec. 4.C, kept pending for the next move; the step
+// counter advances after the last reader of this step
+__global__ void ch_update(int ny, ChCell* __restrict__ cells, const ChSums* __restrict__ sums,
+                          long long* dstep, Species sp, uint32_t* flags,
+                          unsigned long long* counters) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ny) {
+    ChCell& cs = cells[c];
+    if (cs.active) {
+      const double R = gasR(sp), Rth = R * sp.theta_v;
+      const ChSums& S = sums[c];
+      const double invN = 1.0 / (double)cs.N;
+      const double sumI = (double)((long long)S.I + S.net);
+      const double er_star = S.v[9] * invN;
+      const double r = er_star > 0.0 ? cs.e_rot_tgt / er_star : 1.0;
+      const double e_rot_new = r * er_star;
+      const double e_vib_new = Rth * sumI * invN;
+      const double m0 = S.v[0] * invN, m1 = S.v[1] * invN, m2 = S.v[2] * invN;
+      const double etr_star =
+          0.5 * (S.v[3] * invN - m0 * m0 + S.v[4] * invN - m1 * m1 + S.v[5] * invN - m2 * m2);
+      const double e_tr_n = 0.5 * (cs.Pi[0] + cs.Pi[1] + cs.Pi[2]);
+      const double rad =
+          (e_tr_n + R * cs.Trot + Rth * cs.ebar - e_rot_new - e_vib_new) / etr_star;
+      double Us[3] = {cs.U[0] + m0, cs.U[1] + m1, cs.U[2] + m2};
+      if (!(etr_star > 0.0) || !(rad > 0.0)) {
+        atomicOr(flags, (uint32_t)F_NEG_RADICAND);
+        atomicAdd(&counters[C_NEG_RADICAND], 1ull);
+        for (int i = 0; i < 3; ++i) { cs.Un[i] = Us[i]; cs.Us[i] = Us[i]; }
+        cs.s = 1.0;
+      } else {
+        for (int i = 0; i < 3; ++i) { cs.Un[i] = cs.U[i]; cs.Us[i] = Us[i]; }
+        cs.s = sqrt(rad);
+      }
+      cs.r = r;
+      cs.maxI = S.maxI + 1;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dstep += 1;
+}
+
+// time-average sums of the post-step state, binned by its cell
+template <typename T>
+__global__ void ch_sample(long long n, int ny, const int* __restrict__ keycell,
+                          const ChCell* __restrict__ cells, const T* __restrict__ cx,
+                          const T* __restrict__ cy, const T* __restrict__ cz,
+                          const T* __restrict__ er, const int* __restrict__ lev,
+                          double* __restrict__ acc, const double* __restrict__ wallmom) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j == 0) {
+    atomicAdd(&acc[(size_t)ny * kNAcc], 1.0);
+    atomicAdd(&acc[(size_t)ny * kNAcc + 1], *wallmom);
+  }
+  if (j >= n) return;
+  const int k = keycell[j];
+  const ChCell& cc = cells[k];
+  const double v0 = cc.Un[0] + cc.s * ((double)cx[j] - cc.Us[0]);
+  const double v1 = cc.Un[1] + cc.s * ((double)cy[j] - cc.Us[1]);
+  const double v2 = cc.Un[2] + cc.s * ((double)cz[j] - cc.Us[2]);
+  const double e = cc.r * (double)er[j];
+  double* a = acc + (size_t)k * kNAcc;
+  atomicAdd(&a[0], 1.0);
+  atomicAdd(&a[1], v0); atomicAdd(&a[2], v1); atomicAdd(&a[3], v2);
+  atomicAdd(&a[4], v0 * v0); atomicAdd(&a[5], v1 * v1); atomicAdd(&a[6], v2 * v2);
+  atomicAdd(&a[7], v0 * v1); atomicAdd(&a[8], v0 * v2); atomicAdd(&a[9], v1 * v2);
+  atomicAdd(&a[10], e); atomicAdd(&a[11], (double)lev[j]);
+}
+
+// on-demand moments (USP_NMOM fields) of the current state by cell key:
+// pass 0 raw sums, pass 1 central sums (FP64 atomics; not on the step path)
+template <typename T>
+__global__ void ch_mom_pass(int pass, long long n, const int* __restrict__ keycell,
+                            const ChCell* __restrict__ cells, const T* __restrict__ cx,
+                            const T* __restrict__ cy, const T* __restrict__ cz,
+                            const T* __restrict__ er, const int* __restrict__ lev,
+                            double* __restrict__ a) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int k = keycell[j];
+  const ChCell& cc = cells[k];
+  const double v0 = cc.Un[0] + cc.s * ((double)cx[j] - cc.Us[0]);
+  const double v1 = cc.Un[1] + cc.s * ((double)cy[j] - cc.Us[1]);
+  const double v2 = cc.Un[2] + cc.s * ((double)cz[j] - cc.Us[2]);
+  const double ep = cc.r * (double)er[j];
+  const double li = (double)lev[j];
+  double* A = a + (size_t)k * 21;
+  if (pass == 0) {
+    atomicAdd(&A[0], 1.0);
+    atomicAdd(&A[1], v0); atomicAdd(&A[2], v1); atomicAdd(&A[3], v2);
+    atomicAdd(&A[4], ep); atomicAdd(&A[5], li);
+    return;
+  }
+  const double N = A[0];
+  const double C0 = v0 - A[1] / N, C1 = v1 - A[2] / N, C2 = v2 - A[3] / N;
+  const double q = 0.5 * (C0 * C0 + C1 * C1 + C2 * C2);
+  atomicAdd(&A[6], C0 * C0); atomicAdd(&A[7], C1 * C1); atomicAdd(&A[8], C2 * C2);
+  atomicAdd(&A[9], C0 * C1); atomicAdd(&A[10], C0 * C2); atomicAdd(&A[11], C1 * C2);
+  atomicAdd(&A[12], q * C0); atomicAdd(&A[13], q * C1); atomicAdd(&A[14], q * C2);
+  atomicAdd(&A[15], C0 * ep); atomicAdd(&A[16], C1 * ep); atomicAdd(&A[17], C2 * ep);
+  atomicAdd(&A[18], C0 * li); atomicAdd(&A[19], C1 * li); atomicAdd(&A[20], C2 * li);
+}
+
+__global__ void ch_mom_out(int ny, const double* __restrict__ a, double* __restrict__ out,
+                           Species sp) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ny) return;
+  const double* A = a + (size_t)c * 21;
+  const double N = A[0];
+  if (!(N > 0.0)) {
+    for (int f = 0; f < USP_NMOM; ++f) out[(size_t)f * ny + c] = 0.0;
+    return;
+  }
+  const double R = gasR(sp), inv = 1.0 / N;
+  out[c] = N;
+  for (int i = 0; i < 3; ++i) out[(size_t)(1 + i) * ny + c] = A[1 + i] * inv;
+  out[(size_t)4 * ny + c] = (A[6] + A[7] + A[8]) * inv / (3.0 * R);
+  out[(size_t)5 * ny + c] = A[4] * inv / R;
+  out[(size_t)6 * ny + c] = T_vib_of_level(sp, A[5] * inv);
+  for (int i = 0; i < 6; ++i) out[(size_t)(7 + i) * ny + c] = A[6 + i] * inv;
+  for (int i = 0; i < 3; ++i) {
+    out[(size_t)(13 + i) * ny + c] = A[12 + i] * inv;
+    out[(size_t)(16 + i) * ny + c] = A[15 + i] * inv;
+    out[(size_t)(19 + i) * ny + c] = A[18 + i] * inv * R * sp.theta_v;
+  }
+}
+
+template <typename T>
+__global__ void ch_to_host_layout(long long n, const int* __restrict__ keycell,
+                                  const ChCell* __restrict__ cells, const T* __restrict__ y,
+                                  const T* __restrict__ cx, const T* __restrict__ cy,
+                                  const T* __restrict__ cz, const T* __restrict__ er,
+                                  double* __restrict__ out) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const ChCell& cc = cells[keycell[j]];
+  out[j] = (double)y[j];
+  out[n + j] = cc.Un[0] + cc.s * ((double)cx[j] - cc.Us[0]);
+  out[2 * n + j] = cc.Un[1] + cc.s * ((double)cy[j] - cc.Us[1]);
+  out[3 * n + j] = cc.Un[2] + cc.s * ((double)cz[j] - cc.Us[2]);
+  out[4 * n + j] = cc.r * (double)er[j];
+}
+
+template <typename T>
+__global__ void ch_from_host_layout(long long n, const double* __restrict__ in, T* __restrict__ y,
+                                    T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ cz,
+                                    T* __restrict__ er) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  y[j] = (T)in[j]; cx[j] = (T)in[n + j]; cy[j] = (T)in[2 * n + j]; cz[j] = (T)in[3 * n + j];
+  er[j] = (T)in[4 * n + j];
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side
+// ===========================================================================
+struct ChannelCtx {
+  int ny, recon, passes, nblk;
+  double L, dy, Tw, g, Fnum, area, dt;
+  long long n;
+  size_t es;
+  void* st[2][5];           // y, cx, cy, cz, eps (ping-pong)
+  int* lv[2];
+  uint32_t* pd[2];
+  int cur;
+  int* kbuf[2];
+  int* ibuf[2];
+  int* keycell;
+  int* bh;
+  long long* off;
+  ChCell* cells;
+  void* prm;
+  ChSums* sums;
+  double* acc;
+  double* wallmom;
+  double* macc;
+  double* mout;
+  long long* dstep;
+  int sampling;
+};
+
+namespace {
+
+#define CHK(x)                                 \
+  do {                                         \
+    if ((x) != cudaSuccess) return USP_ECUDA;  \
+  } while (0)
+
+template <typename T>
+int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
+  cudaStream_t s = env.stream;
+  const long long n = h->n;
+  const int nb = (int)((n + 255) / 256) > 0 ? (int)((n + 255) / 256) : 1;
+  const int a = h->cur, b = a ^ 1;
+  T* y = (T*)h->st[a][0]; T* cx = (T*)h->st[a][1]; T* cy = (T*)h->st[a][2];
+  T* cz = (T*)h->st[a][3]; T* er = (T*)h->st[a][4];
+  if (prof) prof(env.owner, 0, 1);
+  CHK(cudaMemsetAsync(h->wallmom, 0, sizeof(double), s));
+  ch_advect<T><<<nb, 256, 0, s>>>(n, h->ny, h->L, h->dy, h->Tw, h->g, h->dt, h->keycell, h->cells,
+                                   y, cx, cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0], h->ibuf[0],
+                                   h->dstep, env.sp, env.k0, env.k1, h->wallmom, env.flags,
+                                   env.counters);
+  CHK(cudaGetLastError());
+  int src = 0;
+  for (int p = 0; p < h->passes; ++p) {
+    rad_hist<<<h->nblk, kRB, 0, s>>>(h->kbuf[src], n, 8 * p, h->bh);
+    rad_scan<<<1, 256, 0, s>>>(h->bh, h->nblk);
+    rad_scatter<<<h->nblk, kRB, 0, s>>>(h->kbuf[src], h->ibuf[src], h->kbuf[src ^ 1],
+                                        h->ibuf[src ^ 1], n, 8 * p, h->bh);
+    CHK(cudaGetLastError());
+    src ^= 1;
+  }
+  ch_gather<T><<<nb, 256, 0, s>>>(n, h->ibuf[src], y, cx, cy, cz, er, h->lv[a], h->pd[a],
+                                  (T*)h->st[b][0], (T*)h->st[b][1], (T*)h->st[b][2],
+                                  (T*)h->st[b][3], (T*)h->st[b][4], h->lv[b], h->pd[b]);
+  CHK(cudaMemcpyAsync(h->keycell, h->kbuf[src], sizeof(int) * (n > 0 ? n : 1),
+                      cudaMemcpyDeviceToDevice, s));
+  ch_offsets<<<std::max(nb, (h->ny + 256) / 256), 256, 0, s>>>(n, h->ny, h->keycell, h->off);
+  CHK(cudaGetLastError());
+  h->cur = b;
+  y = (T*)h->st[b][0]; cx = (T*)h->st[b][1]; cy = (T*)h->st[b][2]; cz = (T*)h->st[b][3];
+  er = (T*)h->st[b][4];
+  if (prof) prof(env.owner, 0, 0);
+  if (prof) prof(env.owner, 1, 1);
+  const int wb = (h->ny * 32 + 127) / 128;
+  const int cb = (h->ny + 127) / 128;
+  ch_moments<T><<<wb, 128, 0, s>>>(h->ny, h->off, cx, cy, cz, er, h->lv[b], h->cells, env.sp,
+                                   env.counters);
+  ch_coeffs<<<cb, 128, 0, s>>>(h->ny, h->Fnum, h->area * h->dy, h->dt, h->cells, env.sp,
+                               env.flags);
+  ch_recon<T><<<cb, 128, 0, s>>>(h->ny, h->dy, h->recon, h->dt, h->cells, (ChParams<T>*)h->prm,
+                                 env.sp);
+  CHK(cudaGetLastError());
+  if (prof) prof(env.owner, 1, 0);
+  if (prof) prof(env.owner, 0, 1);
+  ch_collide<T><<<wb, 128, 0, s>>>(h->ny, h->cells, (const ChParams<T>*)h->prm, y, cx, cy, cz, er,
+                                   h->lv[b], h->pd[b], h->sums, h->dstep, env.k0, env.k1,
+                                   env.flags, env.counters);
+  CHK(cudaGetLastError());
+  if (prof) prof(env.owner, 0, 0);
+  if (prof) prof(env.owner, 1, 1);
+  ch_levelfix<<<wb, 128, 0, s>>>(h->ny, h->cells, h->sums, h->lv[b], h->dstep, env.sp, env.k0,
+                                 env.k1, env.flags, env.counters);
+  ch_update<<<cb, 128, 0, s>>>(h->ny, h->cells, h->sums, h->dstep, env.sp, env.flags,
+                               env.counters);
+  CHK(cudaGetLastError());
+  if (h->sampling) {
+    ch_sample<T><<<nb, 256, 0, s>>>(n, h->ny, h->keycell, h->cells, cx, cy, cz, er, h->lv[b],
+                                    h->acc, h->wallmom);
+    CHK(cudaGetLastError());
+  }
+  if (prof) prof(env.owner, 1, 0);
+  return USP_OK;
+}
+
+}  // namespace
+
+int ch_kernels_per_step(const ChannelCtx* h) {
+  return 2 + 3 * h->passes + 8 + (h->sampling ? 1 : 0);
+}
+
+int ch_launch_step(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
+  return env.precision == USP_FP32 ? ch_step_t<float>(h, env, prof)
+                                   : ch_step_t<double>(h, env, prof);
+}
+
+int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double dt, int64_t n,
+              int64_t step0, const double* y, const double* cx, const double* cy,
+              const double* cz, const double* erot, const int32_t* lev, const uint32_t* pid) {
+  if (!chp || chp->ny <= 0 || chp->ny > (1 << 24) || !(chp->L > 0) || !(chp->T_wall > 0) ||
+      !(chp->F_num > 0) || !(chp->area > 0) || !(dt > 0) || n < 0 || n > 0x7fffffffll)
+    return USP_EINVAL;
+  if (n > 0 && (!y || !cx || !cy || !cz || !erot || !lev))
+    return USP_EINVAL;
+  for (int64_t j = 0; j < n; ++j)
+    if (!(y[j] >= 0.0 && y[j] <= chp->L) || lev[j] < 0) return USP_EINVAL;
+  ChannelCtx* h = new ChannelCtx();
+  h->ny = chp->ny; h->L = chp->L; h->dy = chp->L / chp->ny; h->Tw = chp->T_wall; h->g = chp->g;
+  h->Fnum = chp->F_num; h->area = chp->area; h->recon = chp->reconstruct ? 1 : 0; h->dt = dt;
+  h->n = n;
+  h->es = env.precision == USP_FP32 ? 4 : 8;
+  h->cur = 0;
+  h->sampling = 0;
+  int bits = 1;
+  while ((1 << bits) < h->ny) ++bits;
+  h->passes = (bits + 7) / 8;
+  h->nblk = (int)std::max<long long>(1, (n + kChunk - 1) / kChunk);
+  const size_t nn = (size_t)std::max<long long>(n, 1);
+  auto A = [&](size_t bytes) { return env.alloc(env.owner, bytes); };
+  for (int k = 0; k < 2; ++k) {
+    for (int f = 0; f < 5; ++f) h->st[k][f] = A(nn * h->es);
+    h->lv[k] = (int*)A(nn * 4);
+    h->pd[k] = (uint32_t*)A(nn * 4);
+    h->kbuf[k] = (int*)A(nn * 4);
+    h->ibuf[k] = (int*)A(nn * 4);
+  }
+  h->keycell = (int*)A(nn * 4);
+  h->bh = (int*)A((size_t)h->nblk * 256 * 4);
+  h->off = (long long*)A(sizeof(long long) * (h->ny + 1));
+  h->cells = (ChCell*)A(sizeof(ChCell) * h->ny);
+  h->prm = A((env.precision == USP_FP32 ? sizeof(ChParams<float>) : sizeof(ChParams<double>)) *
+             h->ny);
+  h->sums = (ChSums*)A(sizeof(ChSums) * h->ny);
+  h->acc = (double*)A(sizeof(double) * ((size_t)h->ny * kNAcc + 2));
+  h->wallmom = (double*)A(sizeof(double));
+  h->macc = (double*)A(sizeof(double) * 21 * h->ny);
+  h->mout = (double*)A(sizeof(double) * USP_NMOM * h->ny);
+  h->dstep = (long long*)A(sizeof(long long));
+  bool ok = h->keycell && h->bh && h->off && h->cells && h->prm && h->sums && h->acc &&
+            h->wallmom && h->macc && h->mout && h->dstep;
+  for (int k = 0; k < 2; ++k) {
+    for (int f = 0; f < 5; ++f) ok = ok && h->st[k][f];
+    ok = ok && h->lv[k] && h->pd[k] && h->kbuf[k] && h->ibuf[k];
+  }
+  if (!ok) {
+    delete h;
+    return USP_ENOMEM;
+  }
+  cudaStream_t s = env.stream;
+  // upload: doubles in host layout, converted on the device
+  std::vector<double> hl(5 * nn, 0.0);
+  std::vector<int> key(nn, 0);
+  std::vector<uint32_t> hp(nn, 0);
+  for (int64_t j = 0; j < n; ++j) {
+    hl[j] = y[j]; hl[n + j] = cx[j]; hl[2 * n + j] = cy[j]; hl[3 * n + j] = cz[j];
+    hl[4 * n + j] = erot[j];
+    int k = (int)std::floor(y[j] / h->dy);
+    key[j] = std::min(std::max(k, 0), h->ny - 1);
+    hp[j] = pid ? pid[j] : (uint32_t)j;
+  }
+  double* stage = nullptr;
+  void* tmp = nullptr;
+  if (n > 0) {
+    tmp = env.alloc(env.owner, 5 * nn * sizeof(double));
+    if (!tmp) {
+      delete h;
+      return USP_ENOMEM;
+    }
+    stage = (double*)tmp;
+  }
+  const long long dstep0 = step0;
+  bool cok = n == 0 || cudaMemcpyAsync(h->lv[0], lev, n * 4, cudaMemcpyHostToDevice, s) ==
+                           cudaSuccess;
+  cok = cok && cudaMemcpyAsync(h->pd[0], hp.data(), nn * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  cok = cok && cudaMemcpyAsync(h->keycell, key.data(), nn * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  cok = cok && cudaMemsetAsync(h->cells, 0, sizeof(ChCell) * h->ny, s) == cudaSuccess;
+  cok = cok && cudaMemsetAsync(h->sums, 0, sizeof(ChSums) * h->ny, s) == cudaSuccess;
+  cok = cok && cudaMemsetAsync(h->acc, 0, sizeof(double) * ((size_t)h->ny * kNAcc + 2), s) == cudaSuccess;
+  cok = cok && cudaMemcpyAsync(h->dstep, &dstep0, sizeof(long long), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  if (n > 0) {
+    cok = cok && cudaMemcpyAsync(stage, hl.data(), 5 * nn * sizeof(double), cudaMemcpyHostToDevice,
+                                 s) == cudaSuccess;
+    const int nb = (int)((n + 255) / 256);
+    if (env.precision == USP_FP32)
+      ch_from_host_layout<float><<<nb, 256, 0, s>>>(n, stage, (float*)h->st[0][0],
+          (float*)h->st[0][1], (float*)h->st[0][2], (float*)h->st[0][3], (float*)h->st[0][4]);
+    else
+      ch_from_host_layout<double><<<nb, 256, 0, s>>>(n, stage, (double*)h->st[0][0],
+          (double*)h->st[0][1], (double*)h->st[0][2], (double*)h->st[0][3], (double*)h->st[0][4]);
+    cok = cok && cudaGetLastError() == cudaSuccess;
+  }
+  // every cell starts with an identity pending rescale (s = r = 1, Un = Us = 0)
+  std::vector<ChCell> hc(h->ny);
+  std::memset(hc.data(), 0, sizeof(ChCell) * h->ny);
+  for (auto& c : hc) { c.s = 1.0; c.r = 1.0; }
+  cok = cok && cudaMemcpyAsync(h->cells, hc.data(), sizeof(ChCell) * h->ny, cudaMemcpyHostToDevice,
+                               s) == cudaSuccess;
+  cok = cok && cudaStreamSynchronize(s) == cudaSuccess;
+  if (tmp) env.release(env.owner, tmp);
+  if (!cok) {
+    delete h;
+    return USP_ECUDA;
+  }
+  *out = h;
+  return USP_OK;
+}
+
+int ch_sample(ChannelCtx* h, int on) {
+  h->sampling = on ? 1 : 0;
+  return USP_OK;
+}
+
+int ch_read(ChannelCtx* h, const ChEnv& env, double* h_acc, int reset) {
+  const size_t bytes = sizeof(double) * ((size_t)h->ny * kNAcc + 2);
+  CHK(cudaMemcpyAsync(h_acc, h->acc, bytes, cudaMemcpyDeviceToHost, env.stream));
+  if (reset) CHK(cudaMemsetAsync(h->acc, 0, bytes, env.stream));
+  CHK(cudaStreamSynchronize(env.stream));
+  return USP_OK;
+}
+
+int ch_moments(ChannelCtx* h, const ChEnv& env, double* out, int out_is_device) {
+  cudaStream_t s = env.stream;
+  const long long n = h->n;
+  const int nb = (int)std::max<long long>(1, (n + 255) / 256);
+  const int b = h->cur;
+  CHK(cudaMemsetAsync(h->macc, 0, sizeof(double) * 21 * h->ny, s));
+  for (int pass = 0; pass < 2; ++pass) {
+    if (env.precision == USP_FP32)
+      ch_mom_pass<float><<<nb, 256, 0, s>>>(pass, n, h->keycell, h->cells, (float*)h->st[b][1],
+          (float*)h->st[b][2], (float*)h->st[b][3], (float*)h->st[b][4], h->lv[b], h->macc);
+    else
+      ch_mom_pass<double><<<nb, 256, 0, s>>>(pass, n, h->keycell, h->cells, (double*)h->st[b][1],
+          (double*)h->st[b][2], (double*)h->st[b][3], (double*)h->st[b][4], h->lv[b], h->macc);
+    CHK(cudaGetLastError());
+  }
+  ch_mom_out<<<(h->ny + 127) / 128, 128, 0, s>>>(h->ny, h->macc, h->mout, env.sp);
+  CHK(cudaGetLastError());
+  CHK(cudaMemcpyAsync(out, h->mout, sizeof(double) * USP_NMOM * h->ny,
+                      out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!out_is_device) CHK(cudaStreamSynchronize(s));
+  return USP_OK;
+}
+
+int ch_get_particles(ChannelCtx* h, const ChEnv& env, double* y, double* cx, double* cy,
+                     double* cz, double* erot, int32_t* lev, uint32_t* pid) {
+  const long long n = h->n;
+  if (n == 0) return USP_OK;
+  cudaStream_t s = env.stream;
+  double* tmp = (double*)env.alloc(env.owner, 5 * n * sizeof(double));
+  if (!tmp) return USP_ENOMEM;
+  const int b = h->cur;
+  const int nb = (int)((n + 255) / 256);
+  if (env.precision == USP_FP32)
+    ch_to_host_layout<float><<<nb, 256, 0, s>>>(n, h->keycell, h->cells, (float*)h->st[b][0],
+        (float*)h->st[b][1], (float*)h->st[b][2], (float*)h->st[b][3], (float*)h->st[b][4], tmp);
+  else
+    ch_to_host_layout<double><<<nb, 256, 0, s>>>(n, h->keycell, h->cells, (double*)h->st[b][0],
+        (double*)h->st[b][1], (double*)h->st[b][2], (double*)h->st[b][3], (double*)h->st[b][4],
+        tmp);
+  std::vector<double> hl(5 * n);
+  bool ok = cudaGetLastError() == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(hl.data(), tmp, 5 * n * sizeof(double), cudaMemcpyDeviceToHost, s) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpyAsync(lev, h->lv[b], n * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  if (pid)
+    ok = ok && cudaMemcpyAsync(pid, h->pd[b], n * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+  env.release(env.owner, tmp);
+  if (!ok) return USP_ECUDA;
+  for (long long j = 0; j < n; ++j) {
+    if (y) y[j] = hl[j];
+    cx[j] = hl[n + j]; cy[j] = hl[2 * n + j]; cz[j] = hl[3 * n + j]; erot[j] = hl[4 * n + j];
+  }
+  return USP_OK;
+}
+
+int ch_ncell(const ChannelCtx* h) { return h->ny; }
+int ch_parity(const ChannelCtx* h) { return h->cur; }
+long long ch_nparticles(const ChannelCtx* h) { return h->n; }
+void ch_destroy(ChannelCtx* h) { delete h; }

@@ -124,7 +124,7 @@ __device__ __forceinline__ T powi_rn(T x, int e) {
   return r;
 }
 
-__device__ __noinline__ int nb_inv_d(int r, double p, double u, uint32_t& fl) {
+static __device__ __noinline__ int nb_inv_d(int r, double p, double u, uint32_t& fl) {
   const double q = rn_sub(1.0, p);
   double P = powi_rn(p, r);
   if (P < 2.2250738585072014e-308) {
@@ -146,7 +146,7 @@ __device__ __noinline__ int nb_inv_d(int r, double p, double u, uint32_t& fl) {
   return k;
 }
 
-__device__ __noinline__ int binv_d(int n, double p, double u, uint32_t& fl) {
+static __device__ __noinline__ int binv_d(int n, double p, double u, uint32_t& fl) {
   const double q = rn_sub(1.0, p);
   double P = powi_rn(q, n);
   if (P < 2.2250738585072014e-308) {

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "../../include/usp.h"
+#include "usp_channel.h"
 #include "usp_device.cuh"
 
 using namespace usp;
@@ -921,6 +922,9 @@ __global__ void gather_state_native(int ncell, const CellState* __restrict__ cel
 // Host side
 // ===========================================================================
 struct usp_ctx {
+  int kind;                 // 0 homogeneous cells, 1 channel
+  ChannelCtx* ch;
+  cudaEvent_t prof_pending;
   Species sp;
   usp_config cfg;
   int precision;
@@ -956,6 +960,7 @@ struct usp_ctx {
   long long launches;
   cudaGraphExec_t graph_exec;
   int graph_steps;
+  int graph_parity;          // channel buffer parity the graph was captured at
   cudaGraph_t graph;
   long long device_bytes;
   std::vector<void*> owned;
@@ -1015,6 +1020,32 @@ Species to_dev(const usp_species* s) {
 uint32_t key0(const usp_ctx* c) { return (uint32_t)(c->cfg.seed & 0xffffffffull); }
 uint32_t key1(const usp_ctx* c) { return (uint32_t)(c->cfg.seed >> 32); }
 
+void dev_release(usp_ctx* c, void* p) {
+  auto it = std::find(c->owned.begin(), c->owned.end(), p);
+  if (it == c->owned.end()) return;
+  c->owned.erase(it);
+  if (c->cfg.alloc && c->cfg.free_) c->cfg.free_(p, c->cfg.alloc_user);
+  else if (!c->cfg.alloc) cudaFree(p);
+}
+
+void* env_alloc(void* owner, size_t bytes) { return dev_alloc((usp_ctx*)owner, bytes); }
+void env_release(void* owner, void* p) { dev_release((usp_ctx*)owner, p); }
+
+ChEnv make_env(usp_ctx* c) {
+  ChEnv e;
+  e.stream = c->stream;
+  e.flags = c->flags;
+  e.counters = c->counters;
+  e.sp = c->sp;
+  e.k0 = key0(c);
+  e.k1 = key1(c);
+  e.precision = c->precision;
+  e.alloc = env_alloc;
+  e.release = env_release;
+  e.owner = c;
+  return e;
+}
+
 int sm_count() {
   int dev = 0, n = 0;
   cudaGetDevice(&dev);
@@ -1069,6 +1100,12 @@ int prof_end(usp_ctx* c, cudaEvent_t e1) {
   if (!c->profiling) return USP_OK;
   CK(cudaEventRecord(e1, c->stream));
   return USP_OK;
+}
+
+int prof_cb(void* owner, int kind, int begin) {
+  usp_ctx* c = (usp_ctx*)owner;
+  if (begin) return prof_begin(c, kind, &c->prof_pending);
+  return prof_end(c, c->prof_pending);
 }
 
 template <typename T, int MINB>
@@ -1136,9 +1173,13 @@ int launch_step(usp_ctx* c) {
   return prof_end(c, e1);
 }
 
-int kernels_per_step(const usp_ctx* c) { return c->precision == USP_FP32 ? 4 : 3; }
+int kernels_per_step(const usp_ctx* c) {
+  if (c->kind == 1) return ch_kernels_per_step(c->ch);
+  return c->precision == USP_FP32 ? 4 : 3;
+}
 
 int step_once(usp_ctx* c) {
+  if (c->kind == 1) return ch_launch_step(c->ch, make_env(c), c->profiling ? prof_cb : nullptr);
   return c->precision == USP_FP32 ? launch_step<float>(c) : launch_step<double>(c);
 }
 
@@ -1368,6 +1409,8 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
     return USP_EINVAL;
   *out = nullptr;
   usp_ctx* c = new usp_ctx();
+  c->kind = 0;
+  c->ch = nullptr;
   std::memset((void*)&c->sp, 0, sizeof(c->sp));
   c->cfg = *cfg;
   c->sp = to_dev(sp);
@@ -1377,6 +1420,7 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   c->graph_exec = nullptr;
   c->graph = nullptr;
   c->graph_steps = 0;
+  c->graph_parity = 0;
   c->step = cfg->step0;
   c->launches = 0;
   c->device_bytes = 0;
@@ -1493,6 +1537,88 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   return USP_OK;
 }
 
+int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
+                     const usp_channel* ch, double dt, int64_t n, const double* h_y,
+                     const double* h_cx, const double* h_cy, const double* h_cz,
+                     const double* h_erot, const int32_t* h_lev, const uint32_t* h_pid) {
+  if (!out || !sp || !cfg || !ch) return USP_EINVAL;
+  if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64) return USP_EINVAL;
+  if (!(sp->m > 0) || !(sp->d_ref > 0) || !(sp->T_ref > 0) || !(sp->c_alpha > 0) ||
+      !(sp->theta_v > 0))
+    return USP_EINVAL;
+  *out = nullptr;
+  usp_ctx* c = new usp_ctx();
+  c->kind = 1;
+  c->ch = nullptr;
+  c->cfg = *cfg;
+  c->sp = to_dev(sp);
+  c->precision = cfg->precision;
+  c->ncell = 0;
+  c->nparticles = 0;
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  c->graph_steps = 0;
+  c->graph_parity = 0;
+  c->step = cfg->step0;
+  c->launches = 0;
+  c->device_bytes = 0;
+  c->profiling = 0;
+  c->ev_used = 0;
+  c->minb = 0;
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+    c->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return USP_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  auto fail = [&](int rc) {
+    cudaStreamSynchronize(c->stream);
+    if (c->ch) ch_destroy(c->ch);
+    dev_free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return rc;
+  };
+  c->flags = (uint32_t*)dev_alloc(c, 256);
+  c->counters = (unsigned long long*)dev_alloc(c, 256);
+  if (!c->flags || !c->counters) return fail(USP_ENOMEM);
+  if (cudaMemsetAsync(c->flags, 0, 256, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->counters, 0, 256, c->stream) != cudaSuccess)
+    return fail(USP_ECUDA);
+  const int rc = ch_create(&c->ch, make_env(c), ch, dt, n, cfg->step0, h_y, h_cx, h_cy, h_cz,
+                           h_erot, h_lev, h_pid);
+  if (rc != USP_OK) return fail(rc);
+  c->nparticles = ch_nparticles(c->ch);
+  c->ncell = ch_ncell(c->ch);
+  *out = c;
+  return USP_OK;
+}
+
+int usp_channel_sample(usp_ctx* c, int on) {
+  if (!c || c->kind != 1) return USP_EINVAL;
+  if (c->graph_exec) {  // the captured step depends on the sampling switch
+    cudaGraphExecDestroy(c->graph_exec);
+    cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+  }
+  return ch_sample(c->ch, on);
+}
+
+int usp_channel_read(usp_ctx* c, double* h_acc, int reset) {
+  if (!c || c->kind != 1 || !h_acc) return USP_EINVAL;
+  return ch_read(c->ch, make_env(c), h_acc, reset);
+}
+
+int usp_channel_get_particles(usp_ctx* c, double* y, double* cx, double* cy, double* cz,
+                              double* erot, int32_t* lev, uint32_t* pid) {
+  if (!c || c->kind != 1 || !cx || !cy || !cz || !erot || !lev) return USP_EINVAL;
+  return ch_get_particles(c->ch, make_env(c), y, cx, cy, cz, erot, lev, pid);
+}
+
 int usp_step(usp_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return USP_EINVAL;
   if (nsteps == 0) return USP_OK;
@@ -1505,10 +1631,23 @@ int usp_step(usp_ctx* c, int nsteps) {
     c->step += nsteps;
     return USP_OK;
   }
-  const int G = nsteps >= 16 ? 16 : 1;
-  if (!c->graph_exec || c->graph_steps != G) {
+  // The channel path alternates two particle buffers chosen on the host, so
+  // its graphs hold an even number of steps and are captured at the current
+  // buffer parity; an odd remainder runs eagerly.
+  int G = nsteps >= 16 ? 16 : 1;
+  if (c->kind == 1) G = nsteps >= 16 ? 16 : (nsteps >= 2 ? 2 : 0);
+  if (G == 0) {
+    int rc = step_once(c);
+    if (rc) return rc;
+    c->launches += kernels_per_step(c);
+    c->step += nsteps;
+    return USP_OK;
+  }
+  const int parity = c->kind == 1 ? ch_parity(c->ch) : 0;
+  if (!c->graph_exec || c->graph_steps != G || c->graph_parity != parity) {
     int rc = build_graph(c, G);
     if (rc) return rc;
+    c->graph_parity = parity;
   }
   int done = 0;
   while (nsteps - done >= c->graph_steps) {
@@ -1527,6 +1666,7 @@ int usp_step(usp_ctx* c, int nsteps) {
 
 int usp_moments(usp_ctx* c, double* out, int out_is_device) {
   if (!c || !out) return USP_EINVAL;
+  if (c->kind == 1) return ch_moments(c->ch, make_env(c), out, out_is_device);
   int rc = c->precision == USP_FP32 ? compute_moments<float>(c, nullptr)
                                     : compute_moments<double>(c, nullptr);
   if (rc) return rc;
@@ -1543,6 +1683,7 @@ int usp_moments(usp_ctx* c, double* out, int out_is_device) {
 
 int usp_get_particles(usp_ctx* c, double* hx, double* hy, double* hz, double* he, int32_t* hl) {
   if (!c || !hx || !hy || !hz || !he || !hl) return USP_EINVAL;
+  if (c->kind != 0) return USP_ENOTSUP;
   const long long n = c->nparticles;
   if (n == 0) return USP_OK;
   double* st = (double*)dev_alloc(c, (size_t)n * 36 + 64);
@@ -1576,6 +1717,7 @@ int usp_get_particles(usp_ctx* c, double* hx, double* hy, double* hz, double* he
 int usp_set_particles(usp_ctx* c, const double* hx, const double* hy, const double* hz,
                       const double* he, const int32_t* hl) {
   if (!c || !hx || !hy || !hz || !he || !hl) return USP_EINVAL;
+  if (c->kind != 0) return USP_ENOTSUP;
   int rc = upload_state(c, hx, hy, hz, he, hl, false);
   if (rc) return rc;
   return c->precision == USP_FP32 ? init_params<float>(c) : init_params<double>(c);
@@ -1585,6 +1727,7 @@ int usp_step_host(usp_ctx* c, const void* hx, const void* hy, const void* hz, co
                   const int32_t* hl, int nsteps, double* h_moments, void* ox, void* oy, void* oz,
                   void* oe, int32_t* ol) {
   if (!c || !hx || !hy || !hz || !he || !hl || !h_moments || nsteps < 0) return USP_EINVAL;
+  if (c->kind != 0) return USP_ENOTSUP;
   int rc = upload_state(c, hx, hy, hz, he, hl, true);
   if (rc) return rc;
   rc = c->precision == USP_FP32 ? init_params<float>(c) : init_params<double>(c);
@@ -1654,8 +1797,8 @@ int usp_sync(usp_ctx* c) {
 int usp_info(usp_ctx* c, int64_t* np, int* nc, int* prec, int64_t* step, int* tile,
              int64_t* bytes) {
   if (!c) return USP_EINVAL;
-  if (np) *np = c->nparticles;
-  if (nc) *nc = c->ncell;
+  if (np) *np = c->kind == 1 ? ch_nparticles(c->ch) : c->nparticles;
+  if (nc) *nc = c->kind == 1 ? ch_ncell(c->ch) : c->ncell;
   if (prec) *prec = c->precision;
   if (step) *step = c->step;
   if (tile) *tile = c->tile;
@@ -1667,6 +1810,11 @@ int64_t usp_launch_count(usp_ctx* c) { return c ? c->launches : -1; }
 
 int usp_tuning(usp_ctx* c, int* blocks_per_sm, double* ms) {
   if (!c) return USP_EINVAL;
+  if (c->kind != 0) {
+    if (blocks_per_sm) *blocks_per_sm = 0;
+    if (ms) ms[0] = ms[1] = ms[2] = 0.0;
+    return USP_OK;
+  }
   if (blocks_per_sm) *blocks_per_sm = c->minb;
   if (ms)
     for (int i = 0; i < 3; ++i) ms[i] = i < (int)c->tune_ms.size() ? c->tune_ms[i] : 0.0;
@@ -1707,6 +1855,7 @@ void usp_destroy(usp_ctx* c) {
     cudaGraphDestroy(c->graph);
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->ch) ch_destroy(c->ch);
   dev_free_all(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

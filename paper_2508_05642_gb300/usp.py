@@ -29,6 +29,8 @@ F_SAMPLER_CAP = 0x20
 F_A_NONPOS = 0x40
 F_SAMPLER_UNDERFLOW = 0x80
 F_BOUNDS = 0x200
+F_WAIT_TIMEOUT = 0x400
+ERROR_FLAGS = F_CHOL_FAIL_AFTER_FIX | F_A_NONPOS | F_SAMPLER_UNDERFLOW | F_BOUNDS | F_WAIT_TIMEOUT
 
 C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, \
     C_INTERP_FALLBACK, C_SKIPPED_CELLS = range(8)
@@ -36,7 +38,8 @@ C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, 
 EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogeneous", "usp_step", "usp_moments",
             "usp_get_particles", "usp_set_particles", "usp_step_host", "usp_status", "usp_sync",
             "usp_info", "usp_tuning", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
-            "usp_moments_noalloc", "usp_destroy"]
+            "usp_moments_noalloc", "usp_init_channel", "usp_channel_sample",
+            "usp_channel_read", "usp_channel_get_particles", "usp_destroy"]
 USP_NOALLOC_MAX_CELLS = 8192
 
 
@@ -46,6 +49,11 @@ class usp_species(C.Structure):
                 ("Z_rot", C.c_double), ("Z_vib", C.c_double), ("zmodel", C.c_int),
                 ("Zrot_inf", C.c_double), ("T_star", C.c_double), ("C1", C.c_double),
                 ("C2", C.c_double), ("sigma_vib", C.c_double)]
+
+
+class usp_channel(C.Structure):
+    _fields_ = [("ny", C.c_int), ("L", C.c_double), ("T_wall", C.c_double), ("g", C.c_double),
+                ("F_num", C.c_double), ("area", C.c_double), ("reconstruct", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -105,6 +113,12 @@ def lib():
             L.usp_moments_noalloc.argtypes = [C.POINTER(usp_species), C.c_int, C.c_void_p,
                                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_void_p, C.c_void_p]
+            L.usp_init_channel.argtypes = [C.POINTER(_CTX), C.POINTER(usp_species),
+                                           C.POINTER(usp_config), C.POINTER(usp_channel),
+                                           C.c_double, C.c_int64, _D, _D, _D, _D, _D, _I32, _U32]
+            L.usp_channel_sample.argtypes = [_CTX, C.c_int]
+            L.usp_channel_read.argtypes = [_CTX, _D, C.c_int]
+            L.usp_channel_get_particles.argtypes = [_CTX, _D, _D, _D, _D, _D, _I32, _U32]
             L.usp_destroy.argtypes = [_CTX]
             L.usp_destroy.restype = None
             _lib = L
@@ -196,6 +210,64 @@ def usp_init_homogeneous(species: dict, offsets, ndens, dt, cx, cy, cz, erot, le
                                     _p(erot, C.c_double), _p(lev, C.c_int32))
     _check(rc, "usp_init_homogeneous")
     return Context(h, int(off[-1]), len(off) - 1, precision, keep)
+
+
+def usp_init_channel(species: dict, channel: dict, dt: float, y, cx, cy, cz, erot, lev, pid=None,
+                     *, precision=USP_FP32, seed=1, step0=0, stream=None, use_graph=True,
+                     allocator=None) -> Context:
+    """Create a 1D-channel context (host numpy inputs)."""
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    y, cx, cy, cz, erot = f(y), f(cx), f(cy), f(cz), f(erot)
+    lev = np.ascontiguousarray(lev, dtype=np.int32)
+    pidp = None
+    if pid is not None:
+        pid = np.ascontiguousarray(pid, dtype=np.uint32)
+        pidp = _p(pid, C.c_uint32)
+    cfg = usp_config()
+    cfg.precision = precision
+    cfg.seed = seed
+    cfg.step0 = step0
+    cfg.stream = stream or None
+    cfg.use_graph = 1 if use_graph else 0
+    keep = []
+    if allocator is not None:
+        a_fn, f_fn, user = allocator
+        cfg.alloc, cfg.free_, cfg.alloc_user = a_fn, f_fn, user
+        keep += [a_fn, f_fn]
+    ch = usp_channel()
+    for k, _ in usp_channel._fields_:
+        setattr(ch, k, channel[k])
+    sp = make_species(species)
+    h = _CTX()
+    n = len(y)
+    rc = lib().usp_init_channel(C.byref(h), C.byref(sp), C.byref(cfg), C.byref(ch), dt, n,
+                                _p(y, C.c_double), _p(cx, C.c_double), _p(cy, C.c_double),
+                                _p(cz, C.c_double), _p(erot, C.c_double), _p(lev, C.c_int32), pidp)
+    _check(rc, "usp_init_channel")
+    return Context(h, n, int(channel["ny"]), precision, keep)
+
+
+def usp_channel_sample(ctx: Context, on: bool = True):
+    _check(lib().usp_channel_sample(ctx.h, 1 if on else 0), "usp_channel_sample")
+
+
+def usp_channel_read(ctx: Context, reset: bool = False) -> np.ndarray:
+    """ny * 12 + 2 doubles: per-cell time-average sums, step count, wall momentum."""
+    out = np.zeros(ctx.n_cells * 12 + 2)
+    _check(lib().usp_channel_read(ctx.h, _p(out, C.c_double), 1 if reset else 0),
+           "usp_channel_read")
+    return out
+
+
+def usp_channel_get_particles(ctx: Context):
+    n = ctx.n_particles
+    y, cx, cy, cz, er = (np.zeros(n) for _ in range(5))
+    lev = np.zeros(n, dtype=np.int32)
+    pid = np.zeros(n, dtype=np.uint32)
+    _check(lib().usp_channel_get_particles(ctx.h, *[_p(a, C.c_double) for a in (y, cx, cy, cz, er)],
+                                           _p(lev, C.c_int32), _p(pid, C.c_uint32)),
+           "usp_channel_get_particles")
+    return y, cx, cy, cz, er, lev, pid
 
 
 def usp_step(ctx: Context, nsteps: int):
