@@ -88,7 +88,13 @@ enum {
  * T_vib inverts e_vib of Sec. 2.A at the mean level (0 for no excitation). */
 #define USP_NMOM 22
 
-enum { USP_FP64 = 0, USP_FP32 = 1 };
+/* Forms: USP_FP64 plain FP64 state and arithmetic; USP_FP32 FP32 particle
+ * state and per-particle arithmetic with FP64 cell sums and coefficients;
+ * USP_FP64_TANGENT (channel contexts only) the FP64 form carrying, for every
+ * continuous quantity, its derivatives with respect to Z_rot, the viscosity
+ * index omega and T_wall (forward-mode pathwise derivatives under common
+ * random numbers; discrete outcomes held fixed). */
+enum { USP_FP64 = 0, USP_FP32 = 1, USP_FP64_TANGENT = 2 };
 
 /* Gas species.  VSS/VHS viscosity parameters of Sec. 4.A; theta_v of the
  * harmonic vibrational model (Sec. 2.A); zmodel 0 uses the fixed collision
@@ -178,7 +184,11 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
  * post-step state, N, sum c (3), sum c c (xx yy zz xy xz yz), sum eps, sum I
  * (12 doubles per cell), plus one to the sampled-step count and the step's
  * x-momentum (per unit mass) taken by the walls.  usp_channel_read copies
- * the ny * 12 + 2 doubles to h_acc (synchronises) and clears them if reset. */
+ * the ny * 12 + 2 doubles to h_acc (synchronises) and clears them if reset.
+ * In the USP_FP64_TANGENT form h_acc holds 4 such blocks: the sums, then
+ * their derivatives with respect to Z_rot, omega and T_wall (entries that
+ * carry no derivative -- counts, levels, step count, wall momentum -- are 0
+ * in blocks 1-3). */
 int usp_channel_sample(usp_ctx* ctx, int on);
 int usp_channel_read(usp_ctx* ctx, double* h_acc, int reset);
 

@@ -29,8 +29,32 @@
 #include <vector>
 
 #include "usp_channel.h"
+#include "usp_dual.cuh"
 
 using namespace usp;
+
+// The gradient form runs the same kernels on derivative numbers: random
+// numbers and discrete outcomes carry no derivative.
+namespace usp {
+template <>
+__device__ __forceinline__ D3 uniform_open<D3>(uint32_t x) {
+  return D3(uniform_open<double>(x));
+}
+__device__ __forceinline__ void box_muller(D3 ua, D3 ub, D3& ga, D3& gb) {
+  double a, b;
+  box_muller(ua.v, ub.v, a, b);
+  ga = D3(a);
+  gb = D3(b);
+}
+template <>
+__device__ __forceinline__ int sample_nb<D3>(int r, D3 p, D3 u, uint32_t& fl) {
+  return sample_nb<double>(r, p.v, u.v, fl);
+}
+template <>
+__device__ __forceinline__ int sample_b<D3>(int n, D3 p, D3 u, uint32_t& fl) {
+  return sample_b<double>(n, p.v, u.v, fl);
+}
+}  // namespace usp
 
 namespace {
 
@@ -42,13 +66,16 @@ constexpr int kNAcc = 12;          // time-average sums per cell
 constexpr int kWallHitCap = 16;
 constexpr uint32_t PTAG_WALL_A = 2u, PTAG_WALL_B = 3u;
 
-struct ChCell {
-  double U[3], Pi[6];
-  double Ttr, Trot, Tvib, ebar;
-  double n;
-  double alpha, nu_ref, B, mu_p, Pr, gtr, gtv, grv;
-  double e_rot_tgt, e_vib_tgt;
-  double Un[3], Us[3], s, r;   // pending rescale: c = Un + s (c* - Us), eps = r eps*
+// Per-cell state; S = double (plain forms) or a derivative number.  T_vib
+// comes from the mean level alone (levels carry no derivative).
+template <typename S>
+struct ChCellT {
+  S U[3], Pi[6];
+  S Ttr, Trot;
+  double Tvib, ebar, n;
+  S alpha, nu_ref, B, mu_p, Pr, gtr, gtv, grv;
+  S e_rot_tgt, e_vib_tgt;
+  S Un[3], Us[3], s, r;   // pending rescale: c = Un + s (c* - Us), eps = r eps*
   long long off, N;
   int active, maxI;
 };
@@ -61,8 +88,9 @@ struct ChParams {
   int active, pad;
 };
 
-struct ChSums {
-  double v[10];
+template <typename S>
+struct ChSumsT {
+  S v[10];
   unsigned long long I;
   long long net;
   int maxI, pad;
@@ -81,12 +109,29 @@ __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
-// e_vib in the working precision
-__device__ __forceinline__ float evib_t(float Rth, float theta, float T) {
-  return T > 0.0f ? Rth / expm1f(theta / T) : 0.0f;
+__device__ __forceinline__ D3 wsum(D3 v) {
+  v.v = wsum(v.v);
+  for (int k = 0; k < kND; ++k) v.d[k] = wsum(v.d[k]);
+  return v;
 }
-__device__ __forceinline__ double evib_t(double Rth, double theta, double T) {
-  return T > 0.0 ? Rth / expm1(theta / T) : 0.0;
+
+// e_vib in the working precision
+template <typename T>
+__device__ __forceinline__ T evib_t(const T& Rth, const T& theta, const T& Tv) {
+  return Tv > T(0) ? Rth / expm1(theta / Tv) : T(0);
+}
+
+// cell index of a position, in the precision of the position
+__device__ __forceinline__ int cell_index(float y, double dy) { return (int)floorf(y / (float)dy); }
+__device__ __forceinline__ int cell_index(double y, double dy) { return (int)floor(y / dy); }
+__device__ __forceinline__ int cell_index(const D3& y, double dy) { return (int)floor(y.v / dy); }
+
+// add a quantity to block 0 of an accumulator and, for derivative numbers,
+// its derivatives to blocks 1..3 (stride blk)
+__device__ __forceinline__ void acc_add(double* a, size_t, double q) { atomicAdd(a, q); }
+__device__ __forceinline__ void acc_add(double* a, size_t blk, const D3& q) {
+  atomicAdd(a, q.v);
+  for (int k = 0; k < kND; ++k) atomicAdd(a + (k + 1) * blk, q.d[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -94,27 +139,32 @@ __device__ __forceinline__ double evib_t(double Rth, double theta, double T) {
 // ---------------------------------------------------------------------------
 // Diffuse re-emission at T_w (double): Rayleigh normal speed into the gas,
 // Maxwellian tangential components, exponential eps_rot, geometric level.
-template <typename T>
-__device__ void wall_emit(const Species& sp, uint32_t pid, uint32_t step, int hit, double Tw,
-                          bool into_pos, uint32_t k0, uint32_t k1, double& vx, double& vy,
-                          double& vz, double& e, int& l) {
+template <typename T, typename S>
+__device__ void wall_emit(const Species& sp, uint32_t pid, uint32_t step, int hit, const S& Tw,
+                          bool into_pos, uint32_t k0, uint32_t k1, S& vx, S& vy, S& vz, S& e,
+                          int& l) {
   const double R = gasR(sp);
   const U4 w = philox4x32_10(pid, step, PTAG_WALL_A, (uint32_t)hit, k0, k1);
   const U4 v = philox4x32_10(pid, step, PTAG_WALL_B, (uint32_t)hit, k0, k1);
-  const double vn = sqrt(-2.0 * R * Tw * log((double)uniform_open<T>(w.x)));
+  const double u0 = (double)value(uniform_open<T>(w.x));
+  const double u1 = (double)value(uniform_open<T>(w.y));
+  const double u2 = (double)value(uniform_open<T>(w.z));
+  const double u3 = (double)value(uniform_open<T>(w.w));
+  const double u4 = (double)value(uniform_open<T>(v.x));
+  const S vn = sqrt(-2.0 * R * Tw * log(u0));
   vy = into_pos ? vn : -vn;
   double g1, g2;
-  box_muller((double)uniform_open<T>(w.y), (double)uniform_open<T>(w.z), g1, g2);
-  const double s = sqrt(R * Tw);
+  box_muller(u1, u2, g1, g2);
+  const S s = sqrt(R * Tw);
   vx = s * g1;
   vz = s * g2;
-  e = -R * Tw * log((double)uniform_open<T>(w.w));
-  l = (int)floor(-log((double)uniform_open<T>(v.x)) * Tw / sp.theta_v);
+  e = -R * Tw * log(u3);
+  l = (int)floor(-log(u4) * value(Tw) / sp.theta_v);
 }
 
-template <typename T>
-__global__ void ch_advect(long long n, int ny, double L, double dy, double Tw, double g, double dt,
-                          const int* __restrict__ keycell, const ChCell* __restrict__ cells,
+template <typename T, typename S>
+__global__ void ch_advect(long long n, int ny, double L, double dy, S Tw, double g, double dt,
+                          const int* __restrict__ keycell, const ChCellT<S>* __restrict__ cells,
                           T* __restrict__ y, T* __restrict__ cx, T* __restrict__ cy,
                           T* __restrict__ cz, T* __restrict__ er, int* __restrict__ lev,
                           const uint32_t* __restrict__ pid, int* __restrict__ keyout,
@@ -124,7 +174,7 @@ __global__ void ch_advect(long long n, int ny, double L, double dy, double Tw, d
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const uint32_t step = (uint32_t)*dstep;
-  const ChCell& cc = cells[keycell[j]];
+  const ChCellT<S>& cc = cells[keycell[j]];
   // pending conservation rescale of the previous step
   T vx = (T)cc.Un[0] + (T)cc.s * (cx[j] - (T)cc.Us[0]);
   T vy = (T)cc.Un[1] + (T)cc.s * (cy[j] - (T)cc.Us[1]);
@@ -155,9 +205,9 @@ __global__ void ch_advect(long long n, int ny, double L, double dy, double Tw, d
     mom += (double)vx;
     yy = wall;
     t_left -= t_hit;
-    double ox, oy, oz, oe;
+    S ox, oy, oz, oe;
     int ol;
-    wall_emit<T>(sp, pid[j], step, hits, Tw, wall == T(0), k0, k1, ox, oy, oz, oe, ol);
+    wall_emit<T, S>(sp, pid[j], step, hits, Tw, wall == T(0), k0, k1, ox, oy, oz, oe, ol);
     vx = (T)ox; vy = (T)oy; vz = (T)oz; e = (T)oe; l = ol;
     mom -= (double)vx;
     hits += 1;
@@ -167,7 +217,7 @@ __global__ void ch_advect(long long n, int ny, double L, double dy, double Tw, d
     atomicAdd(&counters[C_WALL_HITS], (unsigned long long)hits);
   }
   y[j] = yy; cx[j] = vx; cy[j] = vy; cz[j] = vz; er[j] = e; lev[j] = l;
-  int k = (int)floor(yy / (T)dy);
+  int k = cell_index(yy, dy);
   k = k < 0 ? 0 : (k >= ny ? ny - 1 : k);
   keyout[j] = k;
   idxout[j] = (int)j;
@@ -219,7 +269,7 @@ __global__ void rad_scatter(const int* __restrict__ kin, const int* __restrict__
                             const int* __restrict__ bh) {
   __shared__ int cnt[kRB / 32][256];
   __shared__ int run[256];
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int t = threadIdx.x, w = t >> 5;
   run[t] = bh[(size_t)blockIdx.x * 256 + t];
   const long long b = (long long)blockIdx.x * kChunk;
   for (int r = 0; r < kRPT; ++r) {
@@ -281,42 +331,44 @@ __global__ void ch_offsets(long long n, int ny, const int* __restrict__ key,
 // ---------------------------------------------------------------------------
 // per-cell moments, coefficients, reconstruction
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename S>
 __global__ void ch_moments(int ny, const long long* __restrict__ off, const T* __restrict__ cx,
                            const T* __restrict__ cy, const T* __restrict__ cz,
                            const T* __restrict__ er, const int* __restrict__ lev,
-                           ChCell* __restrict__ cells, Species sp, unsigned long long* counters) {
+                           ChCellT<S>* __restrict__ cells, Species sp,
+                           unsigned long long* counters) {
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= ny) return;
   const long long b = off[c], e = off[c + 1], N = e - b;
-  T a0 = 0, a1 = 0, a2 = 0, ae = 0, al = 0;
+  T a0 = T(0), a1 = T(0), a2 = T(0), ae = T(0);
+  double al = 0.0;
   for (long long j = b + lane; j < e; j += 32) {
-    a0 += cx[j]; a1 += cy[j]; a2 += cz[j]; ae += er[j]; al += (T)lev[j];
+    a0 += cx[j]; a1 += cy[j]; a2 += cz[j]; ae += er[j]; al += (double)lev[j];
   }
-  const double s0 = (double)wsum(a0), s1 = (double)wsum(a1), s2 = (double)wsum(a2);
-  const double se = (double)wsum(ae), sl = (double)wsum(al);
+  const S s0 = S(wsum(a0)), s1 = S(wsum(a1)), s2 = S(wsum(a2)), se = S(wsum(ae));
+  const double sl = wsum(al);
   const double inv = N > 0 ? 1.0 / (double)N : 0.0;
   const T m0 = (T)(s0 * inv), m1 = (T)(s1 * inv), m2 = (T)(s2 * inv);
-  T p[6] = {0, 0, 0, 0, 0, 0};
+  T p[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
   for (long long j = b + lane; j < e; j += 32) {
     const T C0 = cx[j] - m0, C1 = cy[j] - m1, C2 = cz[j] - m2;
     p[0] += C0 * C0; p[1] += C1 * C1; p[2] += C2 * C2;
     p[3] += C0 * C1; p[4] += C0 * C2; p[5] += C1 * C2;
   }
-  double P[6];
-  for (int i = 0; i < 6; ++i) P[i] = (double)wsum(p[i]) * inv;
+  S P[6];
+  for (int i = 0; i < 6; ++i) P[i] = S(wsum(p[i])) * inv;
   if (lane != 0) return;
-  ChCell& cs = cells[c];
+  ChCellT<S>& cs = cells[c];
   const double R = gasR(sp);
   cs.off = b;
   cs.N = N;
   cs.active = N >= 2;
   cs.U[0] = s0 * inv; cs.U[1] = s1 * inv; cs.U[2] = s2 * inv;
   // identity pending rescale until the cell is updated
-  for (int i = 0; i < 3; ++i) { cs.Un[i] = 0.0; cs.Us[i] = 0.0; }
-  cs.s = 1.0;
-  cs.r = 1.0;
+  for (int i = 0; i < 3; ++i) { cs.Un[i] = S(0.0); cs.Us[i] = S(0.0); }
+  cs.s = S(1.0);
+  cs.r = S(1.0);
   if (!cs.active) {
     atomicAdd(&counters[C_SKIPPED_CELLS], 1ull);
     return;
@@ -325,17 +377,20 @@ __global__ void ch_moments(int ny, const long long* __restrict__ off, const T* _
   cs.Ttr = (P[0] + P[1] + P[2]) / (3.0 * R);
   cs.Trot = se * inv / R;
   cs.ebar = sl * inv;
-  cs.Tvib = T_vib_of_level(sp, cs.ebar);
+  cs.Tvib = T_vib_of_level<double>(sp, cs.ebar);
 }
 
-__global__ void ch_coeffs(int ny, double F_num, double vol, double dt, ChCell* __restrict__ cells,
-                          Species sp, uint32_t* flags) {
+template <typename S>
+__global__ void ch_coeffs(int ny, double F_num, double vol, double dt,
+                          ChCellT<S>* __restrict__ cells, Species sp, S omega, S zrot,
+                          uint32_t* flags) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ny) return;
-  ChCell& cs = cells[c];
+  ChCellT<S>& cs = cells[c];
   if (!cs.active) return;
   cs.n = (double)cs.N * F_num / vol;
-  const CellCoeffs k = cell_coeffs(sp, cs.n, dt, cs.Ttr, cs.Trot, cs.Tvib);
+  const CellCoeffsT<S> k =
+      cell_coeffs_t<S>(sp, omega, zrot, cs.n, dt, cs.Ttr, cs.Trot, S(cs.Tvib));
   if (!k.ok) {
     atomicOr(flags, (uint32_t)F_A_NONPOS);
     cs.active = 0;
@@ -347,9 +402,10 @@ __global__ void ch_coeffs(int ny, double F_num, double vol, double dt, ChCell* _
   cs.e_vib_tgt = k.e_vib_tgt;
 }
 
-__device__ __forceinline__ void cell_fields(const ChCell& c, double* f) {
+template <typename S>
+__device__ __forceinline__ void cell_fields(const ChCellT<S>& c, S* f) {
   f[0] = c.U[0]; f[1] = c.U[1]; f[2] = c.U[2];
-  f[3] = c.Ttr; f[4] = c.Trot; f[5] = c.Tvib;
+  f[3] = c.Ttr; f[4] = c.Trot; f[5] = S(c.Tvib);
   for (int i = 0; i < 6; ++i) f[6 + i] = c.Pi[i];
 }
 
@@ -357,12 +413,13 @@ __device__ __forceinline__ void cell_fields(const ChCell& c, double* f) {
 // centroid and the neighbour's average at its centroid, the neighbour on the
 // particle's side, or on the other side when that one is a wall or holds
 // fewer than two particles.
-template <typename T>
-__global__ void ch_recon(int ny, double dy, int recon, double dt, const ChCell* __restrict__ cells,
-                         ChParams<T>* __restrict__ prm, Species sp) {
+template <typename T, typename S>
+__global__ void ch_recon(int ny, double dy, int recon, double dt,
+                         const ChCellT<S>* __restrict__ cells, ChParams<T>* __restrict__ prm,
+                         Species sp) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ny) return;
-  const ChCell& cs = cells[c];
+  const ChCellT<S>& cs = cells[c];
   ChParams<T> P;
   P.active = cs.active;
   P.pad = 0;
@@ -370,12 +427,12 @@ __global__ void ch_recon(int ny, double dy, int recon, double dt, const ChCell* 
   P.Pr = (T)cs.Pr; P.gtr = (T)cs.gtr; P.gtv = (T)cs.gtv; P.grv = (T)cs.grv;
   P.R = (T)gasR(sp); P.theta = (T)sp.theta_v; P.dt = (T)dt;
   P.yc = (T)((c + 0.5) * dy);
-  double f[kNF];
+  S f[kNF];
   cell_fields(cs, f);
   auto valid = [&](int k) { return k >= 0 && k < ny && cells[k].active; };
   const int up = valid(c + 1) ? c + 1 : (valid(c - 1) ? c - 1 : -1);
   const int dn = valid(c - 1) ? c - 1 : (valid(c + 1) ? c + 1 : -1);
-  double fu[kNF], fd[kNF];
+  S fu[kNF], fd[kNF];
   if (up >= 0) cell_fields(cells[up], fu);
   if (dn >= 0) cell_fields(cells[dn], fd);
   for (int i = 0; i < kNF; ++i) {
@@ -417,23 +474,25 @@ __device__ __forceinline__ void relax_t(const ChParams<T>& P, T alpha, const T* 
   if (evr < T(0)) { evr = T(0); cl = true; }
 }
 
-template <typename T>
-__global__ void ch_collide(int ny, const ChCell* __restrict__ cells, const ChParams<T>* __restrict__ prm,
+template <typename T, typename S>
+__global__ void ch_collide(int ny, const ChCellT<S>* __restrict__ cells,
+                           const ChParams<T>* __restrict__ prm,
                            const T* __restrict__ y, T* __restrict__ cx, T* __restrict__ cy,
                            T* __restrict__ cz, T* __restrict__ er, int* __restrict__ lev,
-                           const uint32_t* __restrict__ pid, ChSums* __restrict__ sums,
+                           const uint32_t* __restrict__ pid, ChSumsT<S>* __restrict__ sums,
                            const long long* __restrict__ dstep, uint32_t k0, uint32_t k1,
                            uint32_t* flags, unsigned long long* counters) {
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (c >= ny) return;
-  const ChCell& cs = cells[c];
+  const ChCellT<S>& cs = cells[c];
   if (!cs.active) return;
   const ChParams<T>& P = prm[c];
   const uint32_t step = (uint32_t)*dstep;
   const T Uc0 = (T)cs.U[0], Uc1 = (T)cs.U[1], Uc2 = (T)cs.U[2];
-  T acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  T accI = 0;
+  T acc[10];
+  for (int i = 0; i < 10; ++i) acc[i] = T(0);
+  double accI = 0.0;
   int maxI = 0;
   uint32_t fl = 0;
   unsigned long long nfix = 0, nfb = 0, ncl = 0, npb = 0;
@@ -490,7 +549,7 @@ __global__ void ch_collide(int ny, const ChCell* __restrict__ cells, const ChPar
       if (!ok) {
         fl |= F_CHOL_FAIL_AFTER_FIX;
         const T sq = sqrt(P.R * ttr);
-        L[0] = sq; L[1] = 0; L[2] = sq; L[3] = 0; L[4] = 0; L[5] = sq;
+        L[0] = sq; L[1] = T(0); L[2] = sq; L[3] = T(0); L[4] = T(0); L[5] = sq;
       }
     }
     if (cl) { fl |= F_TREL_CLAMP; ++ncl; }
@@ -530,21 +589,21 @@ __global__ void ch_collide(int ny, const ChCell* __restrict__ cells, const ChPar
     acc[3] += d0 * d0; acc[4] += d1 * d1; acc[5] += d2 * d2;
     acc[6] += d0 * d1; acc[7] += d0 * d2; acc[8] += d1 * d2;
     acc[9] += en;
-    accI += (T)ln;
+    accI += (double)ln;
   }
-  double s[11];
+  S s[10];
 #pragma unroll
-  for (int i = 0; i < 10; ++i) s[i] = (double)wsum(acc[i]);
-  s[10] = (double)wsum(accI);
+  for (int i = 0; i < 10; ++i) s[i] = S(wsum(acc[i]));
+  const double sI = wsum(accI);
   const unsigned long long fix = wsum(nfix), fb = wsum(nfb), ncl2 = wsum(ncl), pb = wsum(npb);
   const int mI = __reduce_max_sync(0xffffffffu, maxI);
   const uint32_t fla = __reduce_or_sync(0xffffffffu, fl);
   if (lane != 0) return;
-  ChSums& S = sums[c];
-  for (int i = 0; i < 10; ++i) S.v[i] = s[i];
-  S.I = (unsigned long long)(long long)llrint(s[10]);
-  S.net = 0;
-  S.maxI = mI;
+  ChSumsT<S>& sm = sums[c];
+  for (int i = 0; i < 10; ++i) sm.v[i] = s[i];
+  sm.I = (unsigned long long)(long long)llrint(sI);
+  sm.net = 0;
+  sm.maxI = mI;
   if (fla) atomicOr(flags, fla);
   if (fix) atomicAdd(&counters[C_CHOL_FIX], fix);
   if (fb) atomicAdd(&counters[C_INTERP_FALLBACK], fb);
@@ -554,14 +613,16 @@ __global__ void ch_collide(int ny, const ChCell* __restrict__ cells, const ChPar
 
 // vibrational +-1 correction (Sec. 4.C), one warp per cell; same acceptance
 // rule as the one-at-a-time loop (see the homogeneous path)
-__global__ void ch_levelfix(int ny, const ChCell* __restrict__ cells, ChSums* __restrict__ sums,
+template <typename S>
+__global__ void ch_levelfix(int ny, const ChCellT<S>* __restrict__ cells,
+                            ChSumsT<S>* __restrict__ sums,
                             int* __restrict__ lev, const long long* __restrict__ dstep, Species sp,
                             uint32_t k0, uint32_t k1, uint32_t* flags,
                             unsigned long long* counters) {
   const int lane = threadIdx.x & 31;
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (c >= ny) return;
-  const ChCell& cs = cells[c];
+  const ChCellT<S>& cs = cells[c];
   if (!cs.active) return;
   const uint32_t step = (uint32_t)*dstep;
   const double Rth = gasR(sp) * sp.theta_v;
@@ -570,7 +631,7 @@ __global__ void ch_levelfix(int ny, const ChCell* __restrict__ cells, ChSums* __
   if (lane == 0) {
     const U4 w = philox4x32_10((uint32_t)c, step, CTAG_IDELTA, 0u, k0, k1);
     const double u = uniform_open<double>(w.x);
-    Id = (long long)floor((double)N * cs.e_vib_tgt / Rth - (double)(long long)sums[c].I + u);
+    Id = (long long)floor((double)N * value(cs.e_vib_tgt) / Rth - (double)(long long)sums[c].I + u);
   }
   Id = __shfl_sync(0xffffffffu, Id, 0);
   long long remaining = Id, draws = 0, net = 0;
@@ -617,87 +678,91 @@ __global__ void ch_levelfix(int ny, const ChCell* __restrict__ cells, ChSums* __
 
 // rescale factors of Sec. 4.C, kept pending for the next move; the step
 // counter advances after the last reader of this step
-__global__ void ch_update(int ny, ChCell* __restrict__ cells, const ChSums* __restrict__ sums,
-                          long long* dstep, Species sp, uint32_t* flags,
-                          unsigned long long* counters) {
+template <typename S>
+__global__ void ch_update(int ny, ChCellT<S>* __restrict__ cells,
+                          const ChSumsT<S>* __restrict__ sums, long long* dstep, Species sp,
+                          uint32_t* flags, unsigned long long* counters) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c < ny) {
-    ChCell& cs = cells[c];
+    ChCellT<S>& cs = cells[c];
     if (cs.active) {
       const double R = gasR(sp), Rth = R * sp.theta_v;
-      const ChSums& S = sums[c];
+      const ChSumsT<S>& sm = sums[c];
       const double invN = 1.0 / (double)cs.N;
-      const double sumI = (double)((long long)S.I + S.net);
-      const double er_star = S.v[9] * invN;
-      const double r = er_star > 0.0 ? cs.e_rot_tgt / er_star : 1.0;
-      const double e_rot_new = r * er_star;
+      const double sumI = (double)((long long)sm.I + sm.net);
+      const S er_star = sm.v[9] * invN;
+      const S r = er_star > 0.0 ? cs.e_rot_tgt / er_star : S(1.0);
+      const S e_rot_new = r * er_star;
       const double e_vib_new = Rth * sumI * invN;
-      const double m0 = S.v[0] * invN, m1 = S.v[1] * invN, m2 = S.v[2] * invN;
-      const double etr_star =
-          0.5 * (S.v[3] * invN - m0 * m0 + S.v[4] * invN - m1 * m1 + S.v[5] * invN - m2 * m2);
-      const double e_tr_n = 0.5 * (cs.Pi[0] + cs.Pi[1] + cs.Pi[2]);
-      const double rad =
-          (e_tr_n + R * cs.Trot + Rth * cs.ebar - e_rot_new - e_vib_new) / etr_star;
-      double Us[3] = {cs.U[0] + m0, cs.U[1] + m1, cs.U[2] + m2};
+      const S m0 = sm.v[0] * invN, m1 = sm.v[1] * invN, m2 = sm.v[2] * invN;
+      const S etr_star = 0.5 * (sm.v[3] * invN - m0 * m0 + sm.v[4] * invN - m1 * m1 +
+                                sm.v[5] * invN - m2 * m2);
+      const S e_tr_n = 0.5 * (cs.Pi[0] + cs.Pi[1] + cs.Pi[2]);
+      const S rad = (e_tr_n + R * cs.Trot + Rth * cs.ebar - e_rot_new - e_vib_new) / etr_star;
+      S Us[3] = {cs.U[0] + m0, cs.U[1] + m1, cs.U[2] + m2};
       if (!(etr_star > 0.0) || !(rad > 0.0)) {
         atomicOr(flags, (uint32_t)F_NEG_RADICAND);
         atomicAdd(&counters[C_NEG_RADICAND], 1ull);
         for (int i = 0; i < 3; ++i) { cs.Un[i] = Us[i]; cs.Us[i] = Us[i]; }
-        cs.s = 1.0;
+        cs.s = S(1.0);
       } else {
         for (int i = 0; i < 3; ++i) { cs.Un[i] = cs.U[i]; cs.Us[i] = Us[i]; }
         cs.s = sqrt(rad);
       }
       cs.r = r;
-      cs.maxI = S.maxI + 1;
+      cs.maxI = sm.maxI + 1;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *dstep += 1;
 }
 
 // time-average sums of the post-step state, binned by its cell
-template <typename T>
+// (gradient form: block 0 holds the sums, blocks 1..3 their derivatives)
+template <typename T, typename S>
 __global__ void ch_sample(long long n, int ny, const int* __restrict__ keycell,
-                          const ChCell* __restrict__ cells, const T* __restrict__ cx,
+                          const ChCellT<S>* __restrict__ cells, const T* __restrict__ cx,
                           const T* __restrict__ cy, const T* __restrict__ cz,
                           const T* __restrict__ er, const int* __restrict__ lev,
                           double* __restrict__ acc, const double* __restrict__ wallmom) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t blk = (size_t)ny * kNAcc + 2;
   if (j == 0) {
     atomicAdd(&acc[(size_t)ny * kNAcc], 1.0);
     atomicAdd(&acc[(size_t)ny * kNAcc + 1], *wallmom);
   }
   if (j >= n) return;
   const int k = keycell[j];
-  const ChCell& cc = cells[k];
-  const double v0 = cc.Un[0] + cc.s * ((double)cx[j] - cc.Us[0]);
-  const double v1 = cc.Un[1] + cc.s * ((double)cy[j] - cc.Us[1]);
-  const double v2 = cc.Un[2] + cc.s * ((double)cz[j] - cc.Us[2]);
-  const double e = cc.r * (double)er[j];
+  const ChCellT<S>& cc = cells[k];
+  const S v0 = cc.Un[0] + cc.s * (S(cx[j]) - cc.Us[0]);
+  const S v1 = cc.Un[1] + cc.s * (S(cy[j]) - cc.Us[1]);
+  const S v2 = cc.Un[2] + cc.s * (S(cz[j]) - cc.Us[2]);
+  const S e = cc.r * S(er[j]);
   double* a = acc + (size_t)k * kNAcc;
   atomicAdd(&a[0], 1.0);
-  atomicAdd(&a[1], v0); atomicAdd(&a[2], v1); atomicAdd(&a[3], v2);
-  atomicAdd(&a[4], v0 * v0); atomicAdd(&a[5], v1 * v1); atomicAdd(&a[6], v2 * v2);
-  atomicAdd(&a[7], v0 * v1); atomicAdd(&a[8], v0 * v2); atomicAdd(&a[9], v1 * v2);
-  atomicAdd(&a[10], e); atomicAdd(&a[11], (double)lev[j]);
+  acc_add(&a[1], blk, v0); acc_add(&a[2], blk, v1); acc_add(&a[3], blk, v2);
+  acc_add(&a[4], blk, v0 * v0); acc_add(&a[5], blk, v1 * v1); acc_add(&a[6], blk, v2 * v2);
+  acc_add(&a[7], blk, v0 * v1); acc_add(&a[8], blk, v0 * v2); acc_add(&a[9], blk, v1 * v2);
+  acc_add(&a[10], blk, e);
+  atomicAdd(&a[11], (double)lev[j]);
 }
 
 // on-demand moments (USP_NMOM fields) of the current state by cell key:
 // pass 0 raw sums, pass 1 central sums (FP64 atomics; not on the step path)
-template <typename T>
+template <typename T, typename S>
 __global__ void ch_mom_pass(int pass, long long n, const int* __restrict__ keycell,
-                            const ChCell* __restrict__ cells, const T* __restrict__ cx,
+                            const ChCellT<S>* __restrict__ cells, const T* __restrict__ cx,
                             const T* __restrict__ cy, const T* __restrict__ cz,
                             const T* __restrict__ er, const int* __restrict__ lev,
                             double* __restrict__ a) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const int k = keycell[j];
-  const ChCell& cc = cells[k];
-  const double v0 = cc.Un[0] + cc.s * ((double)cx[j] - cc.Us[0]);
-  const double v1 = cc.Un[1] + cc.s * ((double)cy[j] - cc.Us[1]);
-  const double v2 = cc.Un[2] + cc.s * ((double)cz[j] - cc.Us[2]);
-  const double ep = cc.r * (double)er[j];
+  const ChCellT<S>& cc = cells[k];
+  const double sc = value(cc.s);
+  const double v0 = value(cc.Un[0]) + sc * ((double)value(cx[j]) - value(cc.Us[0]));
+  const double v1 = value(cc.Un[1]) + sc * ((double)value(cy[j]) - value(cc.Us[1]));
+  const double v2 = value(cc.Un[2]) + sc * ((double)value(cz[j]) - value(cc.Us[2]));
+  const double ep = value(cc.r) * (double)value(er[j]);
   const double li = (double)lev[j];
   double* A = a + (size_t)k * 21;
   if (pass == 0) {
@@ -740,20 +805,21 @@ __global__ void ch_mom_out(int ny, const double* __restrict__ a, double* __restr
   }
 }
 
-template <typename T>
+template <typename T, typename S>
 __global__ void ch_to_host_layout(long long n, const int* __restrict__ keycell,
-                                  const ChCell* __restrict__ cells, const T* __restrict__ y,
+                                  const ChCellT<S>* __restrict__ cells, const T* __restrict__ y,
                                   const T* __restrict__ cx, const T* __restrict__ cy,
                                   const T* __restrict__ cz, const T* __restrict__ er,
                                   double* __restrict__ out) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const ChCell& cc = cells[keycell[j]];
-  out[j] = (double)y[j];
-  out[n + j] = cc.Un[0] + cc.s * ((double)cx[j] - cc.Us[0]);
-  out[2 * n + j] = cc.Un[1] + cc.s * ((double)cy[j] - cc.Us[1]);
-  out[3 * n + j] = cc.Un[2] + cc.s * ((double)cz[j] - cc.Us[2]);
-  out[4 * n + j] = cc.r * (double)er[j];
+  const ChCellT<S>& cc = cells[keycell[j]];
+  const double sc = value(cc.s);
+  out[j] = (double)value(y[j]);
+  out[n + j] = value(cc.Un[0]) + sc * ((double)value(cx[j]) - value(cc.Us[0]));
+  out[2 * n + j] = value(cc.Un[1]) + sc * ((double)value(cy[j]) - value(cc.Us[1]));
+  out[3 * n + j] = value(cc.Un[2]) + sc * ((double)value(cz[j]) - value(cc.Us[2]));
+  out[4 * n + j] = value(cc.r) * (double)value(er[j]);
 }
 
 template <typename T>
@@ -785,9 +851,10 @@ struct ChannelCtx {
   int* keycell;
   int* bh;
   long long* off;
-  ChCell* cells;
-  void* prm;
-  ChSums* sums;
+  void* cells;              // ChCellT<S>
+  void* prm;                // ChParams<T>
+  void* sums;               // ChSumsT<S>
+  int blocks;               // accumulator blocks: 1, or 4 in the gradient form
   double* acc;
   double* wallmom;
   double* macc;
@@ -803,9 +870,24 @@ namespace {
     if ((x) != cudaSuccess) return USP_ECUDA;  \
   } while (0)
 
-template <typename T>
+// parameter values of the gradient form: Z_rot, omega, T_wall are the three
+// independent variables (derivative slots 0, 1, 2)
+template <typename S> S param(double v, int slot);
+template <> double param<double>(double v, int) { return v; }
+template <> D3 param<D3>(double v, int slot) {
+  D3 r(v);
+  r.d[slot] = 1.0;
+  return r;
+}
+
+template <typename T, typename S>
 int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
   cudaStream_t s = env.stream;
+  ChCellT<S>* cells = (ChCellT<S>*)h->cells;
+  ChSumsT<S>* sums = (ChSumsT<S>*)h->sums;
+  const S Tw = param<S>(h->Tw, 2);
+  const S omega = param<S>(env.sp.omega, 1);
+  const S zrot = param<S>(env.sp.Z_rot, 0);
   const long long n = h->n;
   const int nb = (int)((n + 255) / 256) > 0 ? (int)((n + 255) / 256) : 1;
   const int a = h->cur, b = a ^ 1;
@@ -813,7 +895,7 @@ int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
   T* cz = (T*)h->st[a][3]; T* er = (T*)h->st[a][4];
   if (prof) prof(env.owner, 0, 1);
   CHK(cudaMemsetAsync(h->wallmom, 0, sizeof(double), s));
-  ch_advect<T><<<nb, 256, 0, s>>>(n, h->ny, h->L, h->dy, h->Tw, h->g, h->dt, h->keycell, h->cells,
+  ch_advect<T, S><<<nb, 256, 0, s>>>(n, h->ny, h->L, h->dy, Tw, h->g, h->dt, h->keycell, cells,
                                    y, cx, cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0], h->ibuf[0],
                                    h->dstep, env.sp, env.k0, env.k1, h->wallmom, env.flags,
                                    env.counters);
@@ -841,29 +923,28 @@ int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
   if (prof) prof(env.owner, 1, 1);
   const int wb = (h->ny * 32 + 127) / 128;
   const int cb = (h->ny + 127) / 128;
-  ch_moments<T><<<wb, 128, 0, s>>>(h->ny, h->off, cx, cy, cz, er, h->lv[b], h->cells, env.sp,
-                                   env.counters);
-  ch_coeffs<<<cb, 128, 0, s>>>(h->ny, h->Fnum, h->area * h->dy, h->dt, h->cells, env.sp,
-                               env.flags);
-  ch_recon<T><<<cb, 128, 0, s>>>(h->ny, h->dy, h->recon, h->dt, h->cells, (ChParams<T>*)h->prm,
-                                 env.sp);
+  ch_moments<T, S><<<wb, 128, 0, s>>>(h->ny, h->off, cx, cy, cz, er, h->lv[b], cells, env.sp,
+                                      env.counters);
+  ch_coeffs<S><<<cb, 128, 0, s>>>(h->ny, h->Fnum, h->area * h->dy, h->dt, cells, env.sp, omega,
+                                  zrot, env.flags);
+  ch_recon<T, S><<<cb, 128, 0, s>>>(h->ny, h->dy, h->recon, h->dt, cells, (ChParams<T>*)h->prm,
+                                    env.sp);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 1, 0);
   if (prof) prof(env.owner, 0, 1);
-  ch_collide<T><<<wb, 128, 0, s>>>(h->ny, h->cells, (const ChParams<T>*)h->prm, y, cx, cy, cz, er,
-                                   h->lv[b], h->pd[b], h->sums, h->dstep, env.k0, env.k1,
-                                   env.flags, env.counters);
+  ch_collide<T, S><<<wb, 128, 0, s>>>(h->ny, cells, (const ChParams<T>*)h->prm, y, cx, cy, cz,
+                                      er, h->lv[b], h->pd[b], sums, h->dstep, env.k0, env.k1,
+                                      env.flags, env.counters);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 0, 0);
   if (prof) prof(env.owner, 1, 1);
-  ch_levelfix<<<wb, 128, 0, s>>>(h->ny, h->cells, h->sums, h->lv[b], h->dstep, env.sp, env.k0,
-                                 env.k1, env.flags, env.counters);
-  ch_update<<<cb, 128, 0, s>>>(h->ny, h->cells, h->sums, h->dstep, env.sp, env.flags,
-                               env.counters);
+  ch_levelfix<S><<<wb, 128, 0, s>>>(h->ny, cells, sums, h->lv[b], h->dstep, env.sp, env.k0,
+                                    env.k1, env.flags, env.counters);
+  ch_update<S><<<cb, 128, 0, s>>>(h->ny, cells, sums, h->dstep, env.sp, env.flags, env.counters);
   CHK(cudaGetLastError());
   if (h->sampling) {
-    ch_sample<T><<<nb, 256, 0, s>>>(n, h->ny, h->keycell, h->cells, cx, cy, cz, er, h->lv[b],
-                                    h->acc, h->wallmom);
+    ch_sample<T, S><<<nb, 256, 0, s>>>(n, h->ny, h->keycell, cells, cx, cy, cz, er, h->lv[b],
+                                       h->acc, h->wallmom);
     CHK(cudaGetLastError());
   }
   if (prof) prof(env.owner, 1, 0);
@@ -877,8 +958,9 @@ int ch_kernels_per_step(const ChannelCtx* h) {
 }
 
 int ch_launch_step(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
-  return env.precision == USP_FP32 ? ch_step_t<float>(h, env, prof)
-                                   : ch_step_t<double>(h, env, prof);
+  if (env.precision == USP_FP32) return ch_step_t<float, double>(h, env, prof);
+  if (env.precision == USP_FP64_TANGENT) return ch_step_t<D3, D3>(h, env, prof);
+  return ch_step_t<double, double>(h, env, prof);
 }
 
 int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double dt, int64_t n,
@@ -895,7 +977,12 @@ int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double
   h->ny = chp->ny; h->L = chp->L; h->dy = chp->L / chp->ny; h->Tw = chp->T_wall; h->g = chp->g;
   h->Fnum = chp->F_num; h->area = chp->area; h->recon = chp->reconstruct ? 1 : 0; h->dt = dt;
   h->n = n;
-  h->es = env.precision == USP_FP32 ? 4 : 8;
+  const bool grad = env.precision == USP_FP64_TANGENT;
+  h->es = env.precision == USP_FP32 ? 4 : (grad ? sizeof(D3) : 8);
+  h->blocks = grad ? 1 + kND : 1;
+  const size_t cell_bytes = grad ? sizeof(ChCellT<D3>) : sizeof(ChCellT<double>);
+  const size_t sums_bytes = grad ? sizeof(ChSumsT<D3>) : sizeof(ChSumsT<double>);
+  const size_t acc_bytes = sizeof(double) * ((size_t)chp->ny * kNAcc + 2) * h->blocks;
   h->cur = 0;
   h->sampling = 0;
   int bits = 1;
@@ -914,11 +1001,12 @@ int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double
   h->keycell = (int*)A(nn * 4);
   h->bh = (int*)A((size_t)h->nblk * 256 * 4);
   h->off = (long long*)A(sizeof(long long) * (h->ny + 1));
-  h->cells = (ChCell*)A(sizeof(ChCell) * h->ny);
-  h->prm = A((env.precision == USP_FP32 ? sizeof(ChParams<float>) : sizeof(ChParams<double>)) *
+  h->cells = A(cell_bytes * h->ny);
+  h->prm = A((env.precision == USP_FP32 ? sizeof(ChParams<float>)
+                                        : (grad ? sizeof(ChParams<D3>) : sizeof(ChParams<double>))) *
              h->ny);
-  h->sums = (ChSums*)A(sizeof(ChSums) * h->ny);
-  h->acc = (double*)A(sizeof(double) * ((size_t)h->ny * kNAcc + 2));
+  h->sums = A(sums_bytes * h->ny);
+  h->acc = (double*)A(acc_bytes);
   h->wallmom = (double*)A(sizeof(double));
   h->macc = (double*)A(sizeof(double) * 21 * h->ny);
   h->mout = (double*)A(sizeof(double) * USP_NMOM * h->ny);
@@ -960,9 +1048,9 @@ int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double
                            cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->pd[0], hp.data(), nn * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->keycell, key.data(), nn * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
-  cok = cok && cudaMemsetAsync(h->cells, 0, sizeof(ChCell) * h->ny, s) == cudaSuccess;
-  cok = cok && cudaMemsetAsync(h->sums, 0, sizeof(ChSums) * h->ny, s) == cudaSuccess;
-  cok = cok && cudaMemsetAsync(h->acc, 0, sizeof(double) * ((size_t)h->ny * kNAcc + 2), s) == cudaSuccess;
+  cok = cok && cudaMemsetAsync(h->cells, 0, cell_bytes * h->ny, s) == cudaSuccess;
+  cok = cok && cudaMemsetAsync(h->sums, 0, sums_bytes * h->ny, s) == cudaSuccess;
+  cok = cok && cudaMemsetAsync(h->acc, 0, acc_bytes, s) == cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->dstep, &dstep0, sizeof(long long), cudaMemcpyHostToDevice, s) == cudaSuccess;
   if (n > 0) {
     cok = cok && cudaMemcpyAsync(stage, hl.data(), 5 * nn * sizeof(double), cudaMemcpyHostToDevice,
@@ -971,17 +1059,27 @@ int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double
     if (env.precision == USP_FP32)
       ch_from_host_layout<float><<<nb, 256, 0, s>>>(n, stage, (float*)h->st[0][0],
           (float*)h->st[0][1], (float*)h->st[0][2], (float*)h->st[0][3], (float*)h->st[0][4]);
+    else if (grad)
+      ch_from_host_layout<D3><<<nb, 256, 0, s>>>(n, stage, (D3*)h->st[0][0], (D3*)h->st[0][1],
+          (D3*)h->st[0][2], (D3*)h->st[0][3], (D3*)h->st[0][4]);
     else
       ch_from_host_layout<double><<<nb, 256, 0, s>>>(n, stage, (double*)h->st[0][0],
           (double*)h->st[0][1], (double*)h->st[0][2], (double*)h->st[0][3], (double*)h->st[0][4]);
     cok = cok && cudaGetLastError() == cudaSuccess;
   }
   // every cell starts with an identity pending rescale (s = r = 1, Un = Us = 0)
-  std::vector<ChCell> hc(h->ny);
-  std::memset(hc.data(), 0, sizeof(ChCell) * h->ny);
-  for (auto& c : hc) { c.s = 1.0; c.r = 1.0; }
-  cok = cok && cudaMemcpyAsync(h->cells, hc.data(), sizeof(ChCell) * h->ny, cudaMemcpyHostToDevice,
-                               s) == cudaSuccess;
+  if (grad) {
+    std::vector<ChCellT<D3>> hc(h->ny);
+    for (auto& c : hc) { c.s = D3(1.0); c.r = D3(1.0); c.active = 0; c.N = 0; c.off = 0; }
+    cok = cok && cudaMemcpyAsync(h->cells, hc.data(), cell_bytes * h->ny, cudaMemcpyHostToDevice,
+                                 s) == cudaSuccess;
+  } else {
+    std::vector<ChCellT<double>> hc(h->ny);
+    std::memset((void*)hc.data(), 0, cell_bytes * h->ny);
+    for (auto& c : hc) { c.s = 1.0; c.r = 1.0; }
+    cok = cok && cudaMemcpyAsync(h->cells, hc.data(), cell_bytes * h->ny, cudaMemcpyHostToDevice,
+                                 s) == cudaSuccess;
+  }
   cok = cok && cudaStreamSynchronize(s) == cudaSuccess;
   if (tmp) env.release(env.owner, tmp);
   if (!cok) {
@@ -998,7 +1096,7 @@ int ch_sample(ChannelCtx* h, int on) {
 }
 
 int ch_read(ChannelCtx* h, const ChEnv& env, double* h_acc, int reset) {
-  const size_t bytes = sizeof(double) * ((size_t)h->ny * kNAcc + 2);
+  const size_t bytes = sizeof(double) * ((size_t)h->ny * kNAcc + 2) * h->blocks;
   CHK(cudaMemcpyAsync(h_acc, h->acc, bytes, cudaMemcpyDeviceToHost, env.stream));
   if (reset) CHK(cudaMemsetAsync(h->acc, 0, bytes, env.stream));
   CHK(cudaStreamSynchronize(env.stream));
@@ -1013,11 +1111,17 @@ int ch_moments(ChannelCtx* h, const ChEnv& env, double* out, int out_is_device) 
   CHK(cudaMemsetAsync(h->macc, 0, sizeof(double) * 21 * h->ny, s));
   for (int pass = 0; pass < 2; ++pass) {
     if (env.precision == USP_FP32)
-      ch_mom_pass<float><<<nb, 256, 0, s>>>(pass, n, h->keycell, h->cells, (float*)h->st[b][1],
-          (float*)h->st[b][2], (float*)h->st[b][3], (float*)h->st[b][4], h->lv[b], h->macc);
+      ch_mom_pass<float, double><<<nb, 256, 0, s>>>(pass, n, h->keycell,
+          (const ChCellT<double>*)h->cells, (float*)h->st[b][1], (float*)h->st[b][2],
+          (float*)h->st[b][3], (float*)h->st[b][4], h->lv[b], h->macc);
+    else if (env.precision == USP_FP64_TANGENT)
+      ch_mom_pass<D3, D3><<<nb, 256, 0, s>>>(pass, n, h->keycell, (const ChCellT<D3>*)h->cells,
+          (D3*)h->st[b][1], (D3*)h->st[b][2], (D3*)h->st[b][3], (D3*)h->st[b][4], h->lv[b],
+          h->macc);
     else
-      ch_mom_pass<double><<<nb, 256, 0, s>>>(pass, n, h->keycell, h->cells, (double*)h->st[b][1],
-          (double*)h->st[b][2], (double*)h->st[b][3], (double*)h->st[b][4], h->lv[b], h->macc);
+      ch_mom_pass<double, double><<<nb, 256, 0, s>>>(pass, n, h->keycell,
+          (const ChCellT<double>*)h->cells, (double*)h->st[b][1], (double*)h->st[b][2],
+          (double*)h->st[b][3], (double*)h->st[b][4], h->lv[b], h->macc);
     CHK(cudaGetLastError());
   }
   ch_mom_out<<<(h->ny + 127) / 128, 128, 0, s>>>(h->ny, h->macc, h->mout, env.sp);
@@ -1038,12 +1142,17 @@ int ch_get_particles(ChannelCtx* h, const ChEnv& env, double* y, double* cx, dou
   const int b = h->cur;
   const int nb = (int)((n + 255) / 256);
   if (env.precision == USP_FP32)
-    ch_to_host_layout<float><<<nb, 256, 0, s>>>(n, h->keycell, h->cells, (float*)h->st[b][0],
-        (float*)h->st[b][1], (float*)h->st[b][2], (float*)h->st[b][3], (float*)h->st[b][4], tmp);
-  else
-    ch_to_host_layout<double><<<nb, 256, 0, s>>>(n, h->keycell, h->cells, (double*)h->st[b][0],
-        (double*)h->st[b][1], (double*)h->st[b][2], (double*)h->st[b][3], (double*)h->st[b][4],
+    ch_to_host_layout<float, double><<<nb, 256, 0, s>>>(n, h->keycell,
+        (const ChCellT<double>*)h->cells, (float*)h->st[b][0], (float*)h->st[b][1],
+        (float*)h->st[b][2], (float*)h->st[b][3], (float*)h->st[b][4], tmp);
+  else if (env.precision == USP_FP64_TANGENT)
+    ch_to_host_layout<D3, D3><<<nb, 256, 0, s>>>(n, h->keycell, (const ChCellT<D3>*)h->cells,
+        (D3*)h->st[b][0], (D3*)h->st[b][1], (D3*)h->st[b][2], (D3*)h->st[b][3], (D3*)h->st[b][4],
         tmp);
+  else
+    ch_to_host_layout<double, double><<<nb, 256, 0, s>>>(n, h->keycell,
+        (const ChCellT<double>*)h->cells, (double*)h->st[b][0], (double*)h->st[b][1],
+        (double*)h->st[b][2], (double*)h->st[b][3], (double*)h->st[b][4], tmp);
   std::vector<double> hl(5 * n);
   bool ok = cudaGetLastError() == cudaSuccess;
   ok = ok && cudaMemcpyAsync(hl.data(), tmp, 5 * n * sizeof(double), cudaMemcpyDeviceToHost, s) ==

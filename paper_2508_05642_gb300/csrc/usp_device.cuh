@@ -238,46 +238,65 @@ __device__ __forceinline__ int sample_b(int n, T p, T u, uint32_t& fl) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double gasR(const Species& s) { return kB / s.m; }
 
+// The per-cell closed forms below are templates over the scalar S: double
+// for the plain forms, a derivative number for the gradient form (with the
+// viscosity index omega and the rotational collision number Z_rot passed as
+// S so that derivatives with respect to them propagate).
+
 // e_vib(T) = R Theta / (exp(Theta/T) - 1) (Sec. 2.A)
-__device__ __forceinline__ double e_vib_T(const Species& s, double T) {
-  if (T <= 0.0) return 0.0;
+template <typename S>
+__device__ __forceinline__ S e_vib_T(const Species& s, const S& T) {
+  if (T <= 0.0) return S(0.0);
   return gasR(s) * s.theta_v / expm1(s.theta_v / T);
 }
 // c_v,vib(T) = R (Theta/2T)^2 / sinh^2(Theta/2T): the derivative of e_vib.
-__device__ __forceinline__ double cv_vib_T(const Species& s, double T) {
-  if (T <= 0.0) return 0.0;
-  const double h = 0.5 * s.theta_v / T;
-  const double sh = sinh(h);
+template <typename S>
+__device__ __forceinline__ S cv_vib_T(const Species& s, const S& T) {
+  if (T <= 0.0) return S(0.0);
+  const S h = 0.5 * s.theta_v / T;
+  const S sh = sinh(h);
   return gasR(s) * (h * h) / (sh * sh);
 }
 // temperature whose e_vib is R Theta ebar
-__device__ __forceinline__ double T_vib_of_level(const Species& s, double ebar) {
-  if (ebar <= 0.0) return 0.0;
+template <typename S>
+__device__ __forceinline__ S T_vib_of_level(const Species& s, const S& ebar) {
+  if (ebar <= 0.0) return S(0.0);
   return s.theta_v / log1p(1.0 / ebar);
 }
 // VSS viscosity and the factor tau_c = K mu / p (Sec. 4.A)
-__device__ __forceinline__ double mu_of_T(const Species& s, double T) {
-  const double ca = s.c_alpha, w = s.omega;
-  const double mu_ref = 5.0 * (ca + 1.0) * (ca + 2.0) * sqrt(s.m * kB * s.T_ref / kPi) /
-                        (4.0 * ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) * s.d_ref * s.d_ref);
+template <typename S>
+__device__ __forceinline__ S mu_of_T_w(const Species& s, const S& T, const S& w) {
+  const double ca = s.c_alpha;
+  const S mu_ref = 5.0 * (ca + 1.0) * (ca + 2.0) * sqrt(s.m * kB * s.T_ref / kPi) /
+                   (4.0 * ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) * s.d_ref * s.d_ref);
   return mu_ref * pow(T / s.T_ref, w);
 }
-__device__ __forceinline__ double tau_c_factor(const Species& s) {
-  const double ca = s.c_alpha, w = s.omega;
+template <typename S>
+__device__ __forceinline__ S tau_c_factor_w(const Species& s, const S& w) {
+  const double ca = s.c_alpha;
   return ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (ca + 1.0) * (ca + 2.0));
 }
+__device__ __forceinline__ double mu_of_T(const Species& s, double T) {
+  return mu_of_T_w<double>(s, T, s.omega);
+}
+__device__ __forceinline__ double tau_c_factor(const Species& s) {
+  return tau_c_factor_w<double>(s, s.omega);
+}
 // Eucken Pr (Sec. 4.B), xi_vib evaluated at the cell vibrational temperature
-__device__ __forceinline__ double prandtl_T(const Species& s, double Tv) {
-  double xi = 0.0;
+template <typename S>
+__device__ __forceinline__ S prandtl_T(const Species& s, const S& Tv) {
+  S xi(0.0);
   if (Tv > 0.0) {
-    const double x = s.theta_v / Tv;
+    const S x = s.theta_v / Tv;
     xi = x / expm1(x);
   }
   return (14.0 + 2.0 * xi) / (19.0 + 2.0 * xi);
 }
-__device__ __forceinline__ void collision_numbers(const Species& s, double Ttr, double& zr, double& zv) {
-  if (s.zmodel == 0) { zr = s.Z_rot; zv = s.Z_vib; return; }
-  const double r = s.T_star / Ttr;
+template <typename S>
+__device__ __forceinline__ void collision_numbers(const Species& s, const S& Ttr, const S& zrot0,
+                                                  S& zr, S& zv) {
+  if (s.zmodel == 0) { zr = zrot0; zv = S(s.Z_vib); return; }
+  const S r = s.T_star / Ttr;
   zr = s.Zrot_inf / (1.0 + 0.5 * pow(kPi, 1.5) * sqrt(r) + (kPi + 0.25 * kPi * kPi) * r);
   zv = (s.C1 / pow(Ttr, s.omega)) * exp(s.C2 * pow(Ttr, -1.0 / 3.0)) +
        (kPi * s.d_ref * s.d_ref / s.sigma_vib) * pow(s.T_ref / Ttr, s.omega - 0.5);
@@ -287,54 +306,64 @@ __device__ __forceinline__ void collision_numbers(const Species& s, double Ttr, 
 // coefficients with the implicit c_v,vib(T_1) (fixed point started at
 // c_v,vib(T_tr), relative tolerance 1e-14, at most 50 passes), and the
 // second-order energy targets.
-struct CellCoeffs {
-  double mu_p, Pr, A, B, alpha, nu_ref;
-  double g_tr_rot, g_tr_vib, g_rot_vib;
-  double e_rot_tgt, e_vib_tgt;
+template <typename S>
+struct CellCoeffsT {
+  S mu_p, Pr, A, B, alpha, nu_ref;
+  S g_tr_rot, g_tr_vib, g_rot_vib;
+  S e_rot_tgt, e_vib_tgt;
   bool ok;
 };
 
-__device__ inline CellCoeffs cell_coeffs(const Species& s, double n, double dt,
-                                         double Ttr, double Trot, double Tvib) {
-  CellCoeffs c;
+template <typename S>
+__device__ inline CellCoeffsT<S> cell_coeffs_t(const Species& s, const S& omega, const S& zrot,
+                                               double n, double dt, const S& Ttr, const S& Trot,
+                                               const S& Tvib) {
+  CellCoeffsT<S> c;
   const double R = gasR(s);
   const double ctr = 1.5 * R, crot = R;
-  const double p = n * kB * Ttr;
-  c.mu_p = mu_of_T(s, Ttr) / p;
-  const double tau_c = tau_c_factor(s) * c.mu_p;
-  double zr, zv;
-  collision_numbers(s, Ttr, zr, zv);
-  const double tau_rot = zr * tau_c, tau_vib = zv * tau_c;
-  c.Pr = prandtl_T(s, Tvib);
+  const S p = n * kB * Ttr;
+  c.mu_p = mu_of_T_w<S>(s, Ttr, omega) / p;
+  const S tau_c = tau_c_factor_w<S>(s, omega) * c.mu_p;
+  S zr, zv;
+  collision_numbers<S>(s, Ttr, zrot, zr, zv);
+  const S tau_rot = zr * tau_c, tau_vib = zv * tau_c;
+  c.Pr = prandtl_T<S>(s, Tvib);
   c.A = (2.0 * c.mu_p - c.Pr * dt) / (2.0 * c.mu_p + c.Pr * dt);
   c.B = (2.0 * c.mu_p - dt) / (2.0 * c.mu_p + dt);
   c.ok = c.A > 0.0;
-  c.alpha = c.ok ? cbrt(c.A) : 0.0;
-  const double a2 = c.alpha * c.alpha;
+  c.alpha = c.ok ? cbrt(c.A) : S(0.0);
+  const S a2 = c.alpha * c.alpha;
   c.nu_ref = (c.B - a2) / (1.0 - a2);
-  const double gr = dt / (dt + 2.0 * tau_rot);
-  const double gv = dt / (dt + 2.0 * tau_vib);
-  const double evT = e_vib_T(s, Tvib);
-  double x = cv_vib_T(s, Ttr);
+  const S gr = dt / (dt + 2.0 * tau_rot);
+  const S gv = dt / (dt + 2.0 * tau_vib);
+  const S evT = e_vib_T<S>(s, Tvib);
+  S x = cv_vib_T<S>(s, Ttr);
   for (int it = 0; it < 50; ++it) {
-    const double den = ctr + gr * crot + gv * x;
-    const double gtr = 2.0 * gr * ctr * crot / den;
-    const double gtv = 2.0 * gv * ctr * x / den;
-    const double Tc = Ttr + (0.5 * gtr * (Trot - Ttr) + 0.5 * gtv * (Tvib - Ttr)) / ctr;
-    const double scale = fmax(fabs(Tc), fabs(Tvib));
-    const double xn = (fabs(Tc - Tvib) <= 1e-9 * scale) ? cv_vib_T(s, Tvib)
-                                                         : (e_vib_T(s, Tc) - evT) / (Tc - Tvib);
-    const double ch = fabs(xn - x);
+    const S den = ctr + gr * crot + gv * x;
+    const S gtr = 2.0 * gr * ctr * crot / den;
+    const S gtv = 2.0 * gv * ctr * x / den;
+    const S Tc = Ttr + (0.5 * gtr * (Trot - Ttr) + 0.5 * gtv * (Tvib - Ttr)) / ctr;
+    const S scale = fmax(fabs(Tc), fabs(Tvib));
+    const S xn = (fabs(Tc - Tvib) <= 1e-9 * scale) ? cv_vib_T<S>(s, Tvib)
+                                                    : (e_vib_T<S>(s, Tc) - evT) / (Tc - Tvib);
+    const S ch = fabs(xn - x);
     x = xn;
     if (ch <= 1e-14 * fabs(xn)) break;
   }
-  const double den = ctr + gr * crot + gv * x;
+  const S den = ctr + gr * crot + gv * x;
   c.g_tr_rot = 2.0 * gr * ctr * crot / den;
   c.g_tr_vib = 2.0 * gv * ctr * x / den;
   c.g_rot_vib = 2.0 * gr * gv * crot * x / den;
   c.e_rot_tgt = crot * Trot + c.g_tr_rot * (Ttr - Trot) - c.g_rot_vib * (Trot - Tvib);
   c.e_vib_tgt = evT + c.g_tr_vib * (Ttr - Tvib) + c.g_rot_vib * (Trot - Tvib);
   return c;
+}
+
+typedef CellCoeffsT<double> CellCoeffs;
+
+__device__ inline CellCoeffs cell_coeffs(const Species& s, double n, double dt, double Ttr,
+                                         double Trot, double Tvib) {
+  return cell_coeffs_t<double>(s, s.omega, s.Z_rot, n, dt, Ttr, Trot, Tvib);
 }
 
 // Relaxation temperatures (Eqs. T_tr_USP, T_rot_USP, T_vib_USP) for a given

@@ -1542,7 +1542,9 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
                      const double* h_cx, const double* h_cy, const double* h_cz,
                      const double* h_erot, const int32_t* h_lev, const uint32_t* h_pid) {
   if (!out || !sp || !cfg || !ch) return USP_EINVAL;
-  if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64) return USP_EINVAL;
+  if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64 &&
+      cfg->precision != USP_FP64_TANGENT)
+    return USP_EINVAL;
   if (!(sp->m > 0) || !(sp->d_ref > 0) || !(sp->T_ref > 0) || !(sp->c_alpha > 0) ||
       !(sp->theta_v > 0))
     return USP_EINVAL;

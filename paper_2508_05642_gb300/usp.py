@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 USP_OK, USP_EINVAL, USP_ENOMEM, USP_ECUDA, USP_EDEVICE, USP_ENOTSUP = 0, -1, -2, -3, -4, -5
-USP_FP64, USP_FP32 = 0, 1
+USP_FP64, USP_FP32, USP_FP64_TANGENT = 0, 1, 2
 USP_NMOM = 22
 USP_NCOUNTERS = 8
 
@@ -251,9 +251,13 @@ def usp_channel_sample(ctx: Context, on: bool = True):
     _check(lib().usp_channel_sample(ctx.h, 1 if on else 0), "usp_channel_sample")
 
 
-def usp_channel_read(ctx: Context, reset: bool = False) -> np.ndarray:
-    """ny * 12 + 2 doubles: per-cell time-average sums, step count, wall momentum."""
-    out = np.zeros(ctx.n_cells * 12 + 2)
+def usp_channel_read(ctx: Context, reset: bool = False, blocks: int = None) -> np.ndarray:
+    """ny * 12 + 2 doubles: per-cell time-average sums, step count, wall
+    momentum (four such blocks in the USP_FP64_TANGENT form: sums, then their
+    derivatives with respect to Z_rot, omega, T_wall)."""
+    if blocks is None:
+        blocks = 4 if ctx.precision == USP_FP64_TANGENT else 1
+    out = np.zeros((ctx.n_cells * 12 + 2) * blocks)
     _check(lib().usp_channel_read(ctx.h, _p(out, C.c_double), 1 if reset else 0),
            "usp_channel_read")
     return out
