@@ -40,10 +40,12 @@ F_SAMPLER_CAP = 0x20
 F_A_NONPOS = 0x40
 F_SAMPLER_UNDERFLOW = 0x80
 F_WALL_CAP = 0x100
+F_INFLOW_CAP = 0x800
+F_CAPACITY = 0x1000
 
 C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, \
-    C_INTERP_FALLBACK, C_SKIPPED_CELLS = range(8)
-NCOUNTERS = 8
+    C_INTERP_FALLBACK, C_SKIPPED_CELLS, C_INFLOW, C_OUTFLOW, C_NU_ZERO = range(11)
+NCOUNTERS = 11
 
 
 def build(force: bool = False, openmp: bool = True) -> str:
@@ -95,6 +97,29 @@ class Channel(C.Structure):
 
 NACC = 12
 NFIELD = 13
+
+BC_OPEN, BC_SPECULAR, BC_DIFFUSE = 0, 1, 2
+
+
+class Plane(C.Structure):
+    """2D plane domain (``orc_plane``): sides in the order left, right,
+    bottom, top."""
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("x1", C.c_double),
+                ("y0", C.c_double), ("y1", C.c_double), ("cyl_xc", C.c_double),
+                ("cyl_yc", C.c_double), ("cyl_r", C.c_double), ("T_wall", C.c_double),
+                ("n_inf", C.c_double), ("T_inf", C.c_double), ("U_inf", C.c_double),
+                ("bc", C.c_int * 4), ("inflow", C.c_int * 4), ("F_num", C.c_double),
+                ("depth", C.c_double), ("reconstruct", C.c_int)]
+
+
+def plane(**kw) -> Plane:
+    c = Plane()
+    for k, v in kw.items():
+        if k in ("bc", "inflow"):
+            getattr(c, k)[:] = list(v)
+        else:
+            setattr(c, k, v)
+    return c
 
 
 def channel(**kw) -> Channel:
@@ -159,6 +184,17 @@ def lib():
             L.orc_channel_reconstruct.argtypes = [C.POINTER(Channel), _I64, _D, C.c_int, C.c_double, _D]
             L.orc_wall_reemit.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_uint32,
                                           C.c_uint32, C.c_int, C.c_double, C.c_int, _D, _I32]
+            L.orc_plane_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
+                                         C.POINTER(Plane), _D, C.c_double, _I64, C.c_int64, _D, _D,
+                                         _D, _D, _D, _D, _I32, _U32, _U32, _I64, _D, _U32, _I64]
+            L.orc_plane_step.restype = C.c_int
+            L.orc_plane_reconstruct.argtypes = [C.POINTER(Plane), _I64, _D, _D, C.c_int, C.c_double,
+                                                C.c_double, _D]
+            L.orc_inflow_flux.argtypes = [C.c_double, C.c_double, C.c_double]
+            L.orc_inflow_flux.restype = C.c_double
+            L.orc_inflow_normal_speed.argtypes = [C.c_double, C.c_double, C.c_uint32, C.c_uint32,
+                                                  C.c_uint64, C.c_int, _U32]
+            L.orc_inflow_normal_speed.restype = C.c_double
             _lib = L
     return _lib
 
@@ -219,7 +255,7 @@ def cell_coeffs(sp, n, dt, T_tr, T_rot, T_vib) -> Coeffs:
     cc = Coeffs()
     rc = lib().orc_cell_coeffs(C.byref(sp), n, dt, T_tr, T_rot, T_vib, C.byref(cc))
     if rc != 0:
-        raise ValueError("time step too large: 2 mu/p - Pr dt <= 0")
+        raise ValueError("cell coefficients undefined: mu/p not positive and finite")
     return cc
 
 
@@ -323,7 +359,7 @@ def homog_step(sp, form, seed, step0, nsteps, off, ndens, dt, st: State):
                               _p(st.erot, C.c_double), _p(st.lev, C.c_int32), _p(st.pid, C.c_uint32),
                               C.byref(fl), _p(cnt, C.c_int64))
     if rc != 0:
-        raise ValueError("time step too large for the method in some cell")
+        raise ValueError("cell coefficients undefined in some cell (mu/p not positive and finite)")
     return fl.value, cnt
 
 
@@ -363,7 +399,7 @@ def channel_step(sp, form, seed, step0, nsteps, ch: Channel, dt, st: ChannelStat
                                 _p(st.pid, C.c_uint32), _p(off, C.c_int64), accp, C.byref(fl),
                                 _p(cnt, C.c_int64))
     if rc != 0:
-        raise ValueError("time step too large for the method in some cell")
+        raise ValueError("cell coefficients undefined in some cell (mu/p not positive and finite)")
     return off, fl.value, cnt
 
 
@@ -382,3 +418,78 @@ def wall_reemit(sp, form, seed, pid, step, hit, Tw, into_positive_y):
     lib().orc_wall_reemit(C.byref(sp), form, C.c_uint64(seed), pid, step, hit, Tw,
                           1 if into_positive_y else 0, _p(out, C.c_double), C.byref(lv))
     return out, lv.value
+
+
+# ---- 2D plane (cylinder) ----------------------------------------------------
+class PlaneState:
+    """Particle state of the 2D plane path with spare capacity for inflow:
+    the first ``n`` entries of every array are live."""
+
+    def __init__(self, x, y, cx, cy, cz, erot, lev, cap, pid=None):
+        n = len(x)
+        if cap < n:
+            raise ValueError("capacity below the particle count")
+        self.cap = int(cap)
+        self.n = n
+
+        def f(a):
+            out = np.zeros(cap)
+            out[:n] = a
+            return out
+        self.x, self.y, self.cx, self.cy, self.cz, self.erot = map(f, (x, y, cx, cy, cz, erot))
+        self.lev = np.zeros(cap, dtype=np.int32)
+        self.lev[:n] = lev
+        self.pid = np.zeros(cap, dtype=np.uint32)
+        self.pid[:n] = np.arange(n, dtype=np.uint32) if pid is None else pid
+        self.next_pid = n if pid is None else int(np.max(pid)) + 1 if n else 0
+
+    def live(self):
+        n = self.n
+        return (self.x[:n], self.y[:n], self.cx[:n], self.cy[:n], self.cz[:n], self.erot[:n],
+                self.lev[:n], self.pid[:n])
+
+
+def plane_step(sp, form, seed, step0, nsteps, pl: Plane, area_frac, dt, st: PlaneState, acc=None):
+    """Advance the plane domain ``nsteps`` steps in place (live particles end
+    sorted by cell).  Returns (cell offsets, flags, counters)."""
+    ncell = pl.nx * pl.ny
+    af = np.ascontiguousarray(area_frac, dtype=np.float64)
+    if af.size != ncell:
+        raise ValueError("area_frac needs one entry per cell")
+    off = np.zeros(ncell + 1, dtype=np.int64)
+    n = C.c_int64(st.n)
+    npid = C.c_uint32(st.next_pid)
+    fl = C.c_uint32(0)
+    cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+    accp = _p(acc, C.c_double) if acc is not None else None
+    rc = lib().orc_plane_step(C.byref(sp), form, C.c_uint64(seed), step0, nsteps, C.byref(pl),
+                              _p(af, C.c_double), dt, C.byref(n), st.cap, _p(st.x, C.c_double),
+                              _p(st.y, C.c_double), _p(st.cx, C.c_double), _p(st.cy, C.c_double),
+                              _p(st.cz, C.c_double), _p(st.erot, C.c_double), _p(st.lev, C.c_int32),
+                              _p(st.pid, C.c_uint32), C.byref(npid), _p(off, C.c_int64), accp,
+                              C.byref(fl), _p(cnt, C.c_int64))
+    st.n = n.value
+    st.next_pid = npid.value
+    if rc != 0:
+        raise ValueError("cell coefficients undefined in some cell (mu/p not positive and finite)")
+    return off, fl.value, cnt
+
+
+def plane_reconstruct(pl: Plane, counts, area_frac, F, cell, x, y):
+    counts = np.ascontiguousarray(counts, dtype=np.int64)
+    af = np.ascontiguousarray(area_frac, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros(NFIELD)
+    lib().orc_plane_reconstruct(C.byref(pl), _p(counts, C.c_int64), _p(af, C.c_double),
+                                _p(F, C.c_double), cell, x, y, _p(out, C.c_double))
+    return out
+
+
+def inflow_flux(n, RT, u_n):
+    return lib().orc_inflow_flux(n, RT, u_n)
+
+
+def inflow_normal_speed(RT, u_n, pid, step, seed, form=0):
+    f = C.c_uint32(0)
+    v = lib().orc_inflow_normal_speed(RT, u_n, pid, step, C.c_uint64(seed), form, C.byref(f))
+    return v, f.value

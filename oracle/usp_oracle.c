@@ -159,7 +159,11 @@ void orc_collision_numbers(const orc_species* sp, double T_tr, double* Zrot, dou
  * iteration on c_v,vib(T_1), started at c_v,vib(T_tr), until the relative
  * change is below 1e-14 (at most 50 passes); when T_check is within 1e-9 of
  * T_vib the secant is replaced by the derivative c_v,vib(T_vib).
- * Returns 0, or -1 if A <= 0 (the time step is too large for the method). */
+ * For dt >= 2 mu / (p Pr) the ratio A is negative (behind a strong shock at
+ * a time step set by the freestream); reading: alpha is then the real cube
+ * root, in (-1, 0), which keeps alpha^3 = A for the heat flux and
+ * alpha^2 < 1 for the energies.  Returns 0, or -1 if A is not in (-1, 1)
+ * (mu/p not positive and finite: a cell without a temperature). */
 int orc_cell_coeffs(const orc_species* sp, double n, double dt,
                     double T_tr, double T_rot, double T_vib, orc_coeffs* o)
 {
@@ -178,7 +182,7 @@ int orc_cell_coeffs(const orc_species* sp, double n, double dt,
 
     o->A = (2.0 * o->mu_p - o->Pr * dt) / (2.0 * o->mu_p + o->Pr * dt);
     o->B = (2.0 * o->mu_p - dt) / (2.0 * o->mu_p + dt);
-    if (!(o->A > 0.0)) return -1;
+    if (!(o->A > -1.0 && o->A < 1.0)) return -1;
     o->alpha = cbrt(o->A);
     double a2 = o->alpha * o->alpha;
     o->nu_ref = (o->B - a2) / (1.0 - a2);
@@ -453,7 +457,8 @@ int orc_sample_b(int n, double p, double u, int form, uint32_t* flags)
 /*  - the relaxation temperatures are re-evaluated with the new alpha and   */
 /*    the test repeated; since T_tr^rel depends on alpha, the bound is      */
 /*    re-taken from the new T_tr^rel, at most four passes; if D_tr is still */
-/*    not definite, nu = 0 is used and the failure is flagged.              */
+/*    not definite, nu = 0 with alpha^2 = B (counted); only a T_tr^rel of   */
+/*    zero then is flagged as a failure.                                    */
 /* ======================================================================== */
 void orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
                           const double U[3], const double Pi[6],
@@ -515,8 +520,23 @@ void orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
             ok = orc_cholesky3(M, L);
         }
         if (!ok) {
-            *flags |= ORC_F_CHOL_FAIL_AFTER_FIX;
-            double s = sqrt(R * Ttr_rel);
+            /* the passes approach the admissible nu from outside when
+             * T_tr^rel moves with alpha; fall back to nu = 0, inside the
+             * admissible range of Eq. nu_USP_positivity whenever
+             * T_tr^rel > 0, with alpha^2 = B from Eq. alpha_USP_positivity_1
+             * at nu = 0 and the sign chosen as above */
+            counters[ORC_C_NU_ZERO] += 1;
+            nu = 0.0;
+            double a2 = cc->B;
+            if (a2 < 0.0) a2 = 0.0;
+            if (a2 > 1.0 - 1e-12) a2 = 1.0 - 1e-12;
+            double ap = sqrt(a2), am = -ap;
+            double prp = 2.0 * cc->mu_p * (1.0 - ap * ap * ap) / (cc->dt * (1.0 + ap * ap * ap));
+            double prm = 2.0 * cc->mu_p * (1.0 - am * am * am) / (cc->dt * (1.0 + am * am * am));
+            alpha = (fabs(prm - cc->Pr) < fabs(prp - cc->Pr)) ? am : ap;
+            orc_relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, &Ttr_rel, &Trot_rel, &evib_rel, &tf);
+            double s = Ttr_rel > 0.0 ? sqrt(R * Ttr_rel) : 0.0;
+            if (!(Ttr_rel > 0.0)) *flags |= ORC_F_CHOL_FAIL_AFTER_FIX;
             L[0] = s; L[1] = 0.0; L[2] = s; L[3] = 0.0; L[4] = 0.0; L[5] = s;
         }
     }
@@ -1026,5 +1046,405 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
         }
     }
     free(F); free(cellT); free(counts); free(cc); free(ok);
+    return status;
+}
+
+/* ======================================================================== */
+/* 2D plane flow past a circular cylinder (the set-up of Sec. 5.C: half    */
+/* body on a specular symmetry plane, fully diffuse cylinder at T_wall,    */
+/* freestream inflow, outflow).  One step: move (events: cylinder, sides)  */
+/* -> inject the freestream through inflow sides -> drop particles that    */
+/* left -> stable sort by cell -> collision step per cell (fields          */
+/* reconstructed per Sec. 3.B) -> conservation (Sec. 4.C).                 */
+/* ======================================================================== */
+#define PTAG_INFLOW_P 5u
+#define PTAG_INFLOW_T 6u
+#define PTAG_INFLOW_V 7u
+#define CELL_TAG_INFLOW 4
+#define INFLOW_TRY_CAP 64
+#define NSIDES 4
+
+static double plane_dx(const orc_plane* pl) { return (pl->x1 - pl->x0) / pl->nx; }
+static double plane_dy(const orc_plane* pl) { return (pl->y1 - pl->y0) / pl->ny; }
+
+static int plane_cell(const orc_plane* pl, double x, double y)
+{
+    int i = (int)floor((x - pl->x0) / plane_dx(pl));
+    int j = (int)floor((y - pl->y0) / plane_dy(pl));
+    if (i < 0) i = 0;
+    if (i >= pl->nx) i = pl->nx - 1;
+    if (j < 0) j = 0;
+    if (j >= pl->ny) j = pl->ny - 1;
+    return j * pl->nx + i;
+}
+
+/* One-way number flux through a surface element of a drifting Maxwellian
+ * (density n, R T, drift u_n along the inward normal): the kinetic-theory
+ * result n sqrt(RT / 2 pi) [exp(-s^2) + sqrt(pi) s (1 + erf s)], s = u_n / sqrt(2RT). */
+double orc_inflow_flux(double n, double RT, double u_n)
+{
+    double s = u_n / sqrt(2.0 * RT);
+    return n * sqrt(RT / (2.0 * PI)) * (exp(-s * s) + sqrt(PI) * s * (1.0 + erf(s)));
+}
+
+/* Inward normal speed of an entering particle: density proportional to
+ * w exp(-(w - s)^2) on w > 0 (w = v_n / sqrt(2RT), s = u_n / sqrt(2RT)).
+ * The paper does not say how its host code samples inflow; reading:
+ * rejection sampling, attempt k drawing the block (pid, step, 7, k).
+ *  - s >= 0: proposal (|w - s| + s) exp(-(w - s)^2) on the real line, a
+ *    mixture of a two-sided Rayleigh in t = w - s (weight 1; |t| =
+ *    sqrt(-ln u1), sign from u2) and a Gaussian t = z / sqrt(2) (weight
+ *    s sqrt(pi); z from u1, u2 by Box-Muller), component chosen by u0;
+ *    accepted if w > 0 and u3 (|t| + s) <= w;
+ *  - s < 0: proposal 2 w exp(-w^2) on w > 0 (w = sqrt(-ln u1)), accepted if
+ *    u3 <= exp(2 s w).
+ * After 64 rejected attempts the mean of the proposal is used and flagged. */
+double orc_inflow_normal_speed(double RT, double u_n, uint32_t pid, uint32_t step, uint64_t seed,
+                               int form, uint32_t* flags)
+{
+    double sc = sqrt(2.0 * RT);
+    double s = u_n / sc;
+    double p1 = 1.0 / (1.0 + s * sqrt(PI));
+    for (int k = 0; k < INFLOW_TRY_CAP; ++k) {
+        uint32_t w[4];
+        philox_words(pid, step, PTAG_INFLOW_V, (uint32_t)k, seed, w);
+        double u0 = orc_uniform(w[0], form), u1 = orc_uniform(w[1], form);
+        double u2 = orc_uniform(w[2], form), u3 = orc_uniform(w[3], form);
+        if (s < 0.0) {
+            double wn = sqrt(-log(u1));
+            if (u3 <= exp(2.0 * s * wn)) return wn * sc;
+            continue;
+        }
+        double t;
+        if (u0 < p1) {
+            t = sqrt(-log(u1));
+            if (u2 < 0.5) t = -t;
+        } else {
+            double g1, g2;
+            box_muller(u1, u2, &g1, &g2);
+            t = g1 / sqrt(2.0);
+        }
+        double wn = s + t;
+        if (!(wn > 0.0)) continue;
+        if (u3 * (fabs(t) + s) <= wn) return wn * sc;
+    }
+    *flags |= ORC_F_INFLOW_CAP;
+    return (s > 0.0 ? s : 0.5 * sqrt(PI)) * sc;
+}
+
+/* flight of one particle for t_left with events; returns 0 if it left the
+ * domain through an open side (to be dropped) */
+static int advect_plane(const orc_species* sp, int form, uint64_t seed, uint32_t step,
+                        const orc_plane* pl, double t_left, double* x, double* y, double* cx,
+                        double* cy, double* cz, double* erot, int32_t* lev, uint32_t pid,
+                        uint32_t* flags, int64_t* counters)
+{
+    double R = orc_R(sp);
+    int hits = 0;
+    for (;;) {
+        /* earliest event in (0, t_left]: 0 cylinder, 1 left, 2 right, 3 bottom, 4 top */
+        int ev = -1;
+        double te = t_left;
+        if (pl->cyl_r > 0.0) {
+            double dx = *x - pl->cyl_xc, dy = *y - pl->cyl_yc;
+            double a = *cx * *cx + *cy * *cy;
+            double b = dx * *cx + dy * *cy;
+            double c = dx * dx + dy * dy - pl->cyl_r * pl->cyl_r;
+            if (c > 0.0 && b < 0.0 && a > 0.0) {
+                double disc = b * b - a * c;
+                if (disc >= 0.0) {
+                    double t = (-b - sqrt(disc)) / a;
+                    if (t >= 0.0 && t <= te) { te = t; ev = 0; }
+                }
+            }
+        }
+        if (*cx < 0.0) { double t = (pl->x0 - *x) / *cx; if (t <= te && (ev < 0 || t < te)) { te = t < 0.0 ? 0.0 : t; ev = 1; } }
+        if (*cx > 0.0) { double t = (pl->x1 - *x) / *cx; if (t <= te && (ev < 0 || t < te)) { te = t < 0.0 ? 0.0 : t; ev = 2; } }
+        if (*cy < 0.0) { double t = (pl->y0 - *y) / *cy; if (t <= te && (ev < 0 || t < te)) { te = t < 0.0 ? 0.0 : t; ev = 3; } }
+        if (*cy > 0.0) { double t = (pl->y1 - *y) / *cy; if (t <= te && (ev < 0 || t < te)) { te = t < 0.0 ? 0.0 : t; ev = 4; } }
+        if (ev < 0) {
+            *x += *cx * t_left;
+            *y += *cy * t_left;
+            return 1;
+        }
+        *x += *cx * te;
+        *y += *cy * te;
+        t_left -= te;
+        if (hits >= WALL_HIT_CAP) {
+            *flags |= ORC_F_WALL_CAP;
+            return 1;
+        }
+        double nx_ = 0.0, ny_ = 0.0;   /* normal pointing into the gas */
+        int kind;
+        if (ev == 0) {
+            nx_ = (*x - pl->cyl_xc) / pl->cyl_r;
+            ny_ = (*y - pl->cyl_yc) / pl->cyl_r;
+            kind = ORC_BC_DIFFUSE;
+        } else {
+            int side = ev - 1;
+            kind = pl->bc[side];
+            if (side == 0) { nx_ = 1.0; *x = pl->x0; }
+            if (side == 1) { nx_ = -1.0; *x = pl->x1; }
+            if (side == 2) { ny_ = 1.0; *y = pl->y0; }
+            if (side == 3) { ny_ = -1.0; *y = pl->y1; }
+        }
+        if (kind == ORC_BC_OPEN) {
+            counters[ORC_C_OUTFLOW] += 1;
+            return 0;
+        }
+        if (kind == ORC_BC_SPECULAR) {
+            double vn = *cx * nx_ + *cy * ny_;
+            *cx -= 2.0 * vn * nx_;
+            *cy -= 2.0 * vn * ny_;
+        } else {
+            /* diffuse at T_wall: speed along the normal, one tangential
+             * component in the plane, one along z */
+            uint32_t w[4], v[4];
+            philox_words(pid, step, PTAG_WALL_A, (uint32_t)hits, seed, w);
+            philox_words(pid, step, PTAG_WALL_B, (uint32_t)hits, seed, v);
+            double Tw = pl->T_wall;
+            double vn = sqrt(-2.0 * R * Tw * log(orc_uniform(w[0], form)));
+            double g1, g2;
+            box_muller(orc_uniform(w[1], form), orc_uniform(w[2], form), &g1, &g2);
+            double st = sqrt(R * Tw);
+            double tx = -ny_, ty = nx_;
+            *cx = vn * nx_ + st * g1 * tx;
+            *cy = vn * ny_ + st * g1 * ty;
+            *cz = st * g2;
+            *erot = -R * Tw * log(orc_uniform(w[3], form));
+            *lev = (int32_t)floor(-log(orc_uniform(v[0], form)) * Tw / sp->theta_v);
+        }
+        hits += 1;
+        counters[ORC_C_WALL_HITS] += 1;
+    }
+}
+
+/* Sec. 3.B on a uniform 2D grid: the bilinear polynomial of the quadrant the
+ * particle is in, through the averages of the cell, its x and y neighbours
+ * on that side and the diagonal one (the matrix of Sec. 3.B: x-difference
+ * with (x - x_i), y-difference with (y - y_j), cross term).  A neighbour is
+ * usable if it lies in the domain, is not cut by the surface (fluid fraction
+ * 1) and holds at least two particles; an unusable side neighbour is replaced
+ * by the opposite one, and without one the direction has no slope; the cross
+ * term needs the diagonal cell of the chosen sides. */
+void orc_plane_reconstruct(const orc_plane* pl, const int64_t* counts, const double* area_frac,
+                           const double* F, int cell, double x, double y, double* out)
+{
+    int nx = pl->nx, ny = pl->ny;
+    int i = cell % nx, j = cell / nx;
+    double dx = plane_dx(pl), dy = plane_dy(pl);
+    double xc = pl->x0 + (i + 0.5) * dx, yc = pl->y0 + (j + 0.5) * dy;
+    int sx = (x >= xc) ? 1 : -1, sy = (y >= yc) ? 1 : -1;
+#define USABLE(ii, jj) ((ii) >= 0 && (ii) < nx && (jj) >= 0 && (jj) < ny && \
+                        area_frac[(jj) * nx + (ii)] >= 1.0 && counts[(jj) * nx + (ii)] >= 2)
+    int ix = -1, jy = -1;
+    if (USABLE(i + sx, j)) ix = i + sx; else if (USABLE(i - sx, j)) ix = i - sx;
+    if (USABLE(i, j + sy)) jy = j + sy; else if (USABLE(i, j - sy)) jy = j - sy;
+    int diag = ix >= 0 && jy >= 0 && USABLE(ix, jy);
+#undef USABLE
+    for (int f = 0; f < NFIELD; ++f) {
+        double p0 = F[cell * NFIELD + f];
+        double v = p0;
+        double px = 0.0, py = 0.0;
+        if (ix >= 0) {
+            px = F[(j * nx + ix) * NFIELD + f];
+            v += (px - p0) * (x - xc) / ((ix - i) * dx);
+        }
+        if (jy >= 0) {
+            py = F[(jy * nx + i) * NFIELD + f];
+            v += (py - p0) * (y - yc) / ((jy - j) * dy);
+        }
+        if (diag) {
+            double pd = F[(jy * nx + ix) * NFIELD + f];
+            v += (pd - px - py + p0) * (x - xc) * (y - yc) / ((ix - i) * (jy - j) * dx * dy);
+        }
+        out[f] = v;
+    }
+}
+
+int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0, int nsteps,
+                   const orc_plane* pl, const double* area_frac, double dt,
+                   int64_t* n_io, int64_t cap, double* x, double* y, double* cx, double* cy,
+                   double* cz, double* erot, int32_t* lev, uint32_t* pid, uint32_t* next_pid,
+                   int64_t* cell_off, double* acc, uint32_t* flags, int64_t* counters)
+{
+    double R = orc_R(sp);
+    int ncell = pl->nx * pl->ny;
+    double dx = plane_dx(pl), dy = plane_dy(pl);
+    double* F = (double*)malloc(sizeof(double) * NFIELD * ncell);
+    double* cellT = (double*)malloc(sizeof(double) * 3 * ncell);
+    int64_t* counts = (int64_t*)malloc(sizeof(int64_t) * ncell);
+    orc_coeffs* cc = (orc_coeffs*)malloc(sizeof(orc_coeffs) * ncell);
+    int* ok = (int*)malloc(sizeof(int) * ncell);
+    int* cellof = (int*)malloc(sizeof(int) * (cap > 0 ? cap : 1));
+    int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (ncell + 1));
+    double* tmpd = (double*)malloc(sizeof(double) * 6 * (cap > 0 ? cap : 1));
+    int32_t* tmpl = (int32_t*)malloc(sizeof(int32_t) * (cap > 0 ? cap : 1));
+    uint32_t* tmpp = (uint32_t*)malloc(sizeof(uint32_t) * (cap > 0 ? cap : 1));
+    int status = 0;
+    int64_t n = *n_io;
+    double RTi = R * pl->T_inf;
+    for (int s = 0; s < nsteps; ++s) {
+        uint32_t step = (uint32_t)(step0 + s);
+        /* 1. move; drop what left through open sides (order kept) */
+        int64_t m = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            int keep = advect_plane(sp, form, seed, step, pl, dt, &x[j], &y[j], &cx[j], &cy[j],
+                                    &cz[j], &erot[j], &lev[j], pid[j], flags, counters);
+            if (!keep) continue;
+            x[m] = x[j]; y[m] = y[j]; cx[m] = cx[j]; cy[m] = cy[j]; cz[m] = cz[j];
+            erot[m] = erot[j]; lev[m] = lev[j]; pid[m] = pid[j];
+            m += 1;
+        }
+        n = m;
+        /* 2. freestream inflow: sides in order left, right, bottom, top; faces
+         * along each side in order; particles numbered in that order */
+        for (int side = 0; side < NSIDES; ++side) {
+            if (!pl->inflow[side]) continue;
+            int nf = side < 2 ? pl->ny : pl->nx;
+            double flen = side < 2 ? dy : dx;
+            double nxs = side == 0 ? 1.0 : (side == 1 ? -1.0 : 0.0);
+            double nys = side == 2 ? 1.0 : (side == 3 ? -1.0 : 0.0);
+            double u_n = pl->U_inf * nxs;
+            double flux = orc_inflow_flux(pl->n_inf, RTi, u_n);
+            double expect = flux * flen * pl->depth * dt / pl->F_num;
+            for (int f = 0; f < nf; ++f) {
+                uint32_t face = ((uint32_t)side << 24) | (uint32_t)f;
+                uint32_t w[4];
+                philox_words(face, step, CELL_TAG(CELL_TAG_INFLOW), 0u, seed, w);
+                int64_t count = (int64_t)floor(expect + orc_uniform(w[0], 0));
+                for (int64_t k = 0; k < count; ++k) {
+                    uint32_t id = (*next_pid)++;
+                    counters[ORC_C_INFLOW] += 1;
+                    uint32_t a[4], b[4];
+                    philox_words(id, step, PTAG_INFLOW_P, 0u, seed, a);
+                    philox_words(id, step, PTAG_INFLOW_T, 0u, seed, b);
+                    double u_pos = orc_uniform(a[0], form), u_t = orc_uniform(a[1], form);
+                    double g1, g2;
+                    box_muller(orc_uniform(b[0], form), orc_uniform(b[1], form), &g1, &g2);
+                    double vn = orc_inflow_normal_speed(RTi, u_n, id, step, seed, form, flags);
+                    double st = sqrt(RTi);
+                    double px, py, vx, vy;
+                    if (side < 2) {
+                        px = side == 0 ? pl->x0 : pl->x1;
+                        py = pl->y0 + (f + u_pos) * dy;
+                        vx = vn * nxs;
+                        vy = st * g1;
+                    } else {
+                        px = pl->x0 + (f + u_pos) * dx;
+                        py = side == 2 ? pl->y0 : pl->y1;
+                        vx = pl->U_inf + st * g1;
+                        vy = vn * nys;
+                    }
+                    double vz = st * g2;
+                    double e = -RTi * log(orc_uniform(a[2], form));
+                    int32_t l = (int32_t)floor(-log(orc_uniform(a[3], form)) * pl->T_inf / sp->theta_v);
+                    /* enters at a uniformly distributed time of the step */
+                    int keep = advect_plane(sp, form, seed, step, pl, u_t * dt, &px, &py, &vx, &vy,
+                                            &vz, &e, &l, id, flags, counters);
+                    if (!keep) continue;
+                    if (n >= cap) { *flags |= ORC_F_CAPACITY; continue; }
+                    x[n] = px; y[n] = py; cx[n] = vx; cy[n] = vy; cz[n] = vz; erot[n] = e;
+                    lev[n] = l; pid[n] = id;
+                    n += 1;
+                }
+            }
+        }
+        /* 3. stable sort by cell */
+        for (int c = 0; c <= ncell; ++c) pos[c] = 0;
+        for (int64_t j = 0; j < n; ++j) { cellof[j] = plane_cell(pl, x[j], y[j]); pos[cellof[j] + 1] += 1; }
+        for (int c = 0; c < ncell; ++c) pos[c + 1] += pos[c];
+        for (int c = 0; c <= ncell; ++c) cell_off[c] = pos[c];
+        for (int64_t j = 0; j < n; ++j) {
+            int64_t k = pos[cellof[j]]++;
+            tmpd[k] = x[j]; tmpd[cap + k] = y[j]; tmpd[2 * cap + k] = cx[j];
+            tmpd[3 * cap + k] = cy[j]; tmpd[4 * cap + k] = cz[j]; tmpd[5 * cap + k] = erot[j];
+            tmpl[k] = lev[j]; tmpp[k] = pid[j];
+        }
+        memcpy(x, tmpd, sizeof(double) * n); memcpy(y, tmpd + cap, sizeof(double) * n);
+        memcpy(cx, tmpd + 2 * cap, sizeof(double) * n); memcpy(cy, tmpd + 3 * cap, sizeof(double) * n);
+        memcpy(cz, tmpd + 4 * cap, sizeof(double) * n); memcpy(erot, tmpd + 5 * cap, sizeof(double) * n);
+        memcpy(lev, tmpl, sizeof(int32_t) * n); memcpy(pid, tmpp, sizeof(uint32_t) * n);
+        /* 4. cell moments and coefficients */
+        for (int c = 0; c < ncell; ++c) {
+            int64_t b = cell_off[c], e = cell_off[c + 1], N = e - b;
+            counts[c] = N;
+            ok[c] = 0;
+            for (int f = 0; f < NFIELD; ++f) F[c * NFIELD + f] = 0.0;
+            if (N < 2) { counters[ORC_C_SKIPPED_CELLS] += 1; continue; }
+            double U[3] = { 0, 0, 0 }, er = 0.0, lv = 0.0, P[6] = { 0, 0, 0, 0, 0, 0 };
+            for (int64_t j = b; j < e; ++j) { U[0] += cx[j]; U[1] += cy[j]; U[2] += cz[j]; er += erot[j]; lv += lev[j]; }
+            U[0] /= N; U[1] /= N; U[2] /= N; er /= N; lv /= N;
+            for (int64_t j = b; j < e; ++j) {
+                double C0 = cx[j] - U[0], C1 = cy[j] - U[1], C2 = cz[j] - U[2];
+                P[0] += C0 * C0; P[1] += C1 * C1; P[2] += C2 * C2;
+                P[3] += C0 * C1; P[4] += C0 * C2; P[5] += C1 * C2;
+            }
+            for (int k = 0; k < 6; ++k) P[k] /= N;
+            double* Fc = &F[c * NFIELD];
+            Fc[0] = U[0]; Fc[1] = U[1]; Fc[2] = U[2];
+            Fc[3] = (P[0] + P[1] + P[2]) / (3.0 * R);
+            Fc[4] = er / R;
+            Fc[5] = orc_T_vib_from_mean_level(sp, lv);
+            for (int k = 0; k < 6; ++k) Fc[6 + k] = P[k];
+            cellT[3 * c] = Fc[3]; cellT[3 * c + 1] = Fc[4]; cellT[3 * c + 2] = Fc[5];
+            double vol = area_frac[c] * dx * dy * pl->depth;
+            if (!(vol > 0.0)) continue;
+            double nd = N * pl->F_num / vol;
+            if (orc_cell_coeffs(sp, nd, dt, Fc[3], Fc[4], Fc[5], &cc[c]) != 0) {
+                *flags |= ORC_F_A_NONPOS;
+                status = -1;
+                continue;
+            }
+            ok[c] = 1;
+        }
+        /* 5. particles */
+        for (int c = 0; c < ncell; ++c) {
+            if (!ok[c]) continue;
+            const double* Fc = &F[c * NFIELD];
+            for (int64_t j = cell_off[c]; j < cell_off[c + 1]; ++j) {
+                double f[NFIELD];
+                if (pl->reconstruct) {
+                    orc_plane_reconstruct(pl, counts, area_frac, F, c, x[j], y[j], f);
+                    if (!(f[3] > 0.0) || !(f[4] > 0.0) || !(f[5] >= 0.0)) {
+                        counters[ORC_C_INTERP_FALLBACK] += 1;
+                        memcpy(f, Fc, sizeof(f));
+                    }
+                } else {
+                    memcpy(f, Fc, sizeof(f));
+                }
+                double G[4], u5, u6, cv[3] = { cx[j], cy[j], cz[j] };
+                particle_draws(seed, pid[j], step, form, G, &u5, &u6);
+                orc_collide_particle(sp, form, &cc[c], f, f + 6, f[3], f[4], f[5], G, u5, u6,
+                                     cv, &erot[j], &lev[j], flags, counters);
+                cx[j] = cv[0]; cy[j] = cv[1]; cz[j] = cv[2];
+            }
+        }
+        /* 6. conservation */
+        for (int c = 0; c < ncell; ++c) {
+            if (!ok[c]) continue;
+            conserve_cell(sp, seed, (uint32_t)c, step, cell_off[c], cell_off[c + 1],
+                          1.5 * R * cellT[3 * c], R * cellT[3 * c + 1], orc_e_vib(sp, cellT[3 * c + 2]),
+                          &F[c * NFIELD], cc[c].e_rot_tgt, cc[c].e_vib_tgt, cx, cy, cz, erot, lev,
+                          flags, counters);
+        }
+        /* 7. time-average sums */
+        if (acc) {
+            for (int c = 0; c < ncell; ++c) {
+                double* a = &acc[c * ORC_NACC];
+                for (int64_t j = cell_off[c]; j < cell_off[c + 1]; ++j) {
+                    a[0] += 1.0;
+                    a[1] += cx[j]; a[2] += cy[j]; a[3] += cz[j];
+                    a[4] += cx[j] * cx[j]; a[5] += cy[j] * cy[j]; a[6] += cz[j] * cz[j];
+                    a[7] += cx[j] * cy[j]; a[8] += cx[j] * cz[j]; a[9] += cy[j] * cz[j];
+                    a[10] += erot[j]; a[11] += lev[j];
+                }
+            }
+            acc[ncell * ORC_NACC] += 1.0;
+        }
+    }
+    *n_io = n;
+    free(F); free(cellT); free(counts); free(cc); free(ok); free(cellof); free(pos);
+    free(tmpd); free(tmpl); free(tmpp);
     return status;
 }

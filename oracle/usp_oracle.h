@@ -40,11 +40,17 @@ extern "C" {
 #define ORC_F_A_NONPOS            0x40u  /* (2mu/p - Pr dt) <= 0: dt too large  */
 #define ORC_F_SAMPLER_UNDERFLOW   0x80u  /* P(0) underflowed even in double     */
 #define ORC_F_WALL_CAP            0x100u /* a particle hit walls too many times */
+#define ORC_F_INFLOW_CAP          0x800u /* inflow speed sampler hit 64 attempts   */
+#define ORC_F_CAPACITY            0x1000u /* particle storage full: inflow dropped */
 
 /* counters[] slots */
 enum { ORC_C_CHOL_FIX = 0, ORC_C_PB_CLAMP = 1, ORC_C_TREL_CLAMP = 2,
        ORC_C_VIB_DRAWS = 3, ORC_C_NEG_RADICAND = 4, ORC_C_WALL_HITS = 5,
-       ORC_C_INTERP_FALLBACK = 6, ORC_C_SKIPPED_CELLS = 7, ORC_NCOUNTERS = 8 };
+       ORC_C_INTERP_FALLBACK = 6, ORC_C_SKIPPED_CELLS = 7,
+       ORC_C_INFLOW = 8,     /* particles generated at inflow faces            */
+       ORC_C_OUTFLOW = 9,    /* particles removed at open sides                */
+       ORC_C_NU_ZERO = 10,   /* positivity fix ended at nu = 0                 */
+       ORC_NCOUNTERS = 11 };
 
 /* number of per-cell output moments (field-major: out[f * ncell + cell]) */
 #define ORC_NMOM 22
@@ -154,6 +160,38 @@ void   orc_channel_reconstruct(const orc_channel* ch, const int64_t* counts, con
 /* one diffuse re-emission (velocity, eps_rot, level) for tests of the wall law */
 void   orc_wall_reemit(const orc_species* sp, int form, uint64_t seed, uint32_t pid, uint32_t step,
                        int hit, double Tw, int into_positive_y, double out[4], int32_t* lev);
+
+/* ---- 2D plane flow past a circular cylinder (Sec. 5.C set-up) ------------ */
+enum { ORC_BC_OPEN = 0, ORC_BC_SPECULAR = 1, ORC_BC_DIFFUSE = 2 };
+typedef struct {
+    int    nx, ny;                 /* cells                                          */
+    double x0, x1, y0, y1;         /* domain                                         */
+    double cyl_xc, cyl_yc, cyl_r;  /* cylinder (r <= 0: none), diffuse at T_wall    */
+    double T_wall;
+    double n_inf, T_inf, U_inf;    /* freestream: density, temperature, x velocity   */
+    int    bc[4];                  /* left, right, bottom, top: ORC_BC_*            */
+    int    inflow[4];              /* 1: inject the freestream through that side    */
+    double F_num, depth;           /* particle weight; cell depth along z [m]        */
+    int    reconstruct;
+} orc_plane;
+
+/* nsteps steps of the plane domain.  Live particles are [0, *n) of arrays of
+ * capacity cap; *n and *next_pid (the id given to the next injected particle)
+ * are updated; on return the live particles are sorted by cell (cell j*nx+i)
+ * with segment starts cell_off[ncell + 1].  area_frac[cell] is the fluid
+ * fraction of each cell (volume = area_frac dx dy depth).  Accumulator layout
+ * as ORC_NACC above, plus slot [ncell * ORC_NACC] = sampled steps. */
+int    orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0, int nsteps,
+                      const orc_plane* pl, const double* area_frac, double dt,
+                      int64_t* n, int64_t cap, double* x, double* y, double* cx, double* cy,
+                      double* cz, double* erot, int32_t* lev, uint32_t* pid, uint32_t* next_pid,
+                      int64_t* cell_off, double* acc, uint32_t* flags, int64_t* counters);
+void   orc_plane_reconstruct(const orc_plane* pl, const int64_t* counts, const double* area_frac,
+                             const double* F, int cell, double x, double y, double* out);
+/* inflow sampling pieces, for tests */
+double orc_inflow_flux(double n, double RT, double u_n);
+double orc_inflow_normal_speed(double RT, double u_n, uint32_t pid, uint32_t step, uint64_t seed,
+                               int form, uint32_t* flags);
 
 #ifdef __cplusplus
 }

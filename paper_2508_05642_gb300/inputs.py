@@ -181,3 +181,115 @@ def channel_poiseuille(seed: int = 1, ny: int = 64, ppc: int = 200, n: float = 1
               reconstruct=reconstruct)
     return ChannelWorkload("force-driven Poiseuille N2, %d cells x %d particles" % (ny, ppc), sp,
                            ch, dt_over_tau_c, n, y, p, seed, steps, average_last)
+
+
+def n2_vhs_cylinder_species() -> dict:
+    """N2 with the VHS parameters of the paper's cylinder case (T_ref = 290 K,
+    d_ref = 4.11e-10 m, omega = 0.70, c_alpha = 1), Parker Z_rot (Z_inf = 23,
+    T* = 91.5 K) and Millikan-White with the high-temperature correction for
+    Z_vib (C1 = 9.1, C2 = 220, sigma_vib = 5.81e-21 m^2), Sec. 5.C."""
+    return dict(m=N2_MASS, d_ref=4.11e-10, omega=0.70, T_ref=290.0, c_alpha=1.0,
+                theta_v=N2_THETA_V, Z_rot=0.0, Z_vib=0.0, zmodel=1,
+                Zrot_inf=23.0, T_star=91.5, C1=9.1, C2=220.0, sigma_vib=5.81e-21)
+
+
+BC_OPEN, BC_SPECULAR, BC_DIFFUSE = 0, 1, 2
+
+
+def cut_cell_fractions(nx: int, ny: int, x0: float, x1: float, y0: float, y1: float,
+                       xc: float, yc: float, r: float, sub: int = 64) -> np.ndarray:
+    """Fluid area fraction of every cell of a uniform grid outside a circle:
+    1 for cells clear of it, 0 for cells inside it, and for cells the circle
+    cuts the fraction of ``sub`` x ``sub`` sub-cell midpoints outside it.
+    Cell (i, j) is entry j * nx + i."""
+    dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
+    i = np.arange(nx)
+    j = np.arange(ny)
+    xl = x0 + i * dx
+    yl = y0 + j * dy
+    # nearest and farthest points of each cell from the centre
+    nxd = np.maximum(np.maximum(xl - xc, xc - (xl + dx)), 0.0)
+    nyd = np.maximum(np.maximum(yl - yc, yc - (yl + dy)), 0.0)
+    fxd = np.maximum(np.abs(xl - xc), np.abs(xl + dx - xc))
+    fyd = np.maximum(np.abs(yl - yc), np.abs(yl + dy - yc))
+    near2 = nyd[:, None] ** 2 + nxd[None, :] ** 2
+    far2 = fyd[:, None] ** 2 + fxd[None, :] ** 2
+    frac = np.ones((ny, nx))
+    frac[far2 <= r * r] = 0.0
+    cut = (near2 < r * r) & (far2 > r * r)
+    s = (np.arange(sub) + 0.5) / sub
+    for jj, ii in zip(*np.nonzero(cut)):
+        px = xl[ii] + s * dx
+        py = yl[jj] + s * dy
+        d2 = (px[None, :] - xc) ** 2 + (py[:, None] - yc) ** 2
+        frac[jj, ii] = np.count_nonzero(d2 > r * r) / float(sub * sub)
+    return frac.ravel()
+
+
+@dataclass
+class PlaneWorkload:
+    name: str
+    species: dict
+    plane: dict                  # nx, ny, x0, x1, y0, y1, cyl_*, T_wall, n_inf, T_inf, U_inf,
+                                 # bc[4], inflow[4], F_num, depth, reconstruct
+    area_frac: np.ndarray        # fluid fraction per cell, j * nx + i
+    dt_over_tau_c: float         # dt = factor * tau_c(n_inf, T_inf)
+    x: np.ndarray
+    y: np.ndarray
+    particles: Particles
+    capacity: int
+    seed: int
+    steps: int
+
+    @property
+    def n_particles(self) -> int:
+        return len(self.x)
+
+
+def cylinder_flow(seed: int = 1, nx: int = 600, ny: int = 400, ppc: float = 30.0,
+                  x0: float = -0.35, x1: float = 0.40, y0: float = 0.0, y1: float = 0.50,
+                  r: float = 0.1, T_wall: float = 500.0, n_inf: float = 1.2012e21,
+                  T_inf: float = 200.0, U_inf: float = 2883.3, dt_over_tau_c: float = 0.5,
+                  capacity_factor: float = 2.0, steps: int = 20000, reconstruct: int = 1,
+                  cylinder: bool = True) -> PlaneWorkload:
+    """Hypersonic N2 flow past a circular cylinder (the set-up of Sec. 5.C on a
+    uniform Cartesian grid with cut cells): half body of radius 0.1 m centred on
+    the origin, specular symmetry plane y = 0, fully diffuse wall at 500 K;
+    Mach-10 freestream (200 K, 2883.3 m/s, n = 1.2012e21 m^-3) entering through
+    the left and top sides, supersonic outflow on the right; 600 x 400 cells of
+    1.25 mm, 30 particles per free cell, dt = 0.5 tau_c of the freestream.  The
+    domain starts filled with the freestream (impulsive start).  With
+    ``cylinder`` False the body is removed and the freestream also enters on
+    the right (uniform-flow checks)."""
+    sp = n2_vhs_cylinder_species()
+    rng = np.random.default_rng([seed, 0xC71D])
+    if cylinder:
+        af = cut_cell_fractions(nx, ny, x0, x1, y0, y1, 0.0, 0.0, r)
+    else:
+        af = np.ones(nx * ny)
+    dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
+    depth = 1.0
+    F_num = n_inf * dx * dy * depth / ppc
+    counts = np.floor(ppc * af + rng.uniform(size=nx * ny)).astype(np.int64)
+    N = int(counts.sum())
+    cell = np.repeat(np.arange(nx * ny), counts)
+    ci, cj = cell % nx, cell // nx
+    x = x0 + (ci + rng.uniform(size=N)) * dx
+    y = y0 + (cj + rng.uniform(size=N)) * dy
+    if cylinder:
+        k = np.nonzero(x * x + y * y <= r * r)[0]
+        while len(k):                  # redraw inside the cut cells' fluid part
+            x[k] = x0 + (ci[k] + rng.uniform(size=len(k))) * dx
+            y[k] = y0 + (cj[k] + rng.uniform(size=len(k))) * dy
+            k = k[x[k] * x[k] + y[k] * y[k] <= r * r]
+    p = equilibrium_particles(rng, N, sp["m"], sp["theta_v"], U=(U_inf, 0.0, 0.0), T_tr=T_inf,
+                              T_rot=T_inf, T_vib=T_inf)
+    pl = dict(nx=nx, ny=ny, x0=x0, x1=x1, y0=y0, y1=y1, cyl_xc=0.0, cyl_yc=0.0,
+              cyl_r=r if cylinder else 0.0, T_wall=T_wall, n_inf=n_inf, T_inf=T_inf,
+              U_inf=U_inf, bc=(BC_OPEN, BC_OPEN, BC_SPECULAR, BC_OPEN),
+              inflow=(1, 0 if cylinder else 1, 0, 1), F_num=F_num, depth=depth,
+              reconstruct=reconstruct)
+    cap = int(capacity_factor * N) + 4096
+    name = ("Mach-10 N2 past a cylinder, %dx%d cells, %.0f particles/cell" % (nx, ny, ppc)
+            if cylinder else "uniform N2 stream, %dx%d cells" % (nx, ny))
+    return PlaneWorkload(name, sp, pl, af, dt_over_tau_c, x, y, p, cap, seed, steps)
