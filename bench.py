@@ -39,7 +39,10 @@ METRIC = ("particle-steps/s on 1 GB300 and % HBM roofline; FP32-batched vs plain
 UNIT = "particle-steps/s"
 N_INST = 4096
 CPU_SAMPLE_INST = 64          # instances of the bounded oracle sample
-BYTES_PER_PARTICLE_STEP = {"f32": 40, "f64": 72}   # 2 x state (read + write)
+# algorithmic bytes per particle-step: homogeneous cells read and write the
+# state once (2 x 20 B FP32, 2 x 36 B FP64); the 2D plane path streams its
+# 32-B FP32 state through the move/sort pass and the collide pass (4 x 32 B)
+BYTES_PER_PARTICLE_STEP = {"f32": 40, "f64": 72, "plane_f32": 128}
 
 
 def parse():
@@ -53,6 +56,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--channel-steps", type=int, default=2000)
+    ap.add_argument("--cylinder-steps", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -359,6 +363,45 @@ def run_ours(args, rank, world, local):
                 "steps": args.channel_steps}
         cctx.destroy()
 
+    # ---- the 2D path: Mach-10 cylinder, 600 x 400 cells, ~6.9M particles ---
+    cyl = None
+    if args.cylinder_steps > 0:
+        from paper_2508_05642_gb300 import inputs as I
+        yw = I.cylinder_flow(seed=1 + 1000 * rank)
+        ydt = yw.dt_over_tau_c * usp.usp_tau_c(yw.species, yw.plane["n_inf"], yw.plane["T_inf"])
+        yp = yw.particles
+        yctx = usp.usp_init_plane(yw.species, yw.plane, ydt, yw.area_frac, yw.x, yw.y, yp.cx,
+                                  yp.cy, yp.cz, yp.erot, yp.lev, yw.capacity,
+                                  precision=usp.USP_FP32, seed=yw.seed,
+                                  stream=stream.cuda_stream, use_graph=True)
+        usp.usp_step(yctx, 16)
+        torch.cuda.synchronize()
+        n_a, _ = usp.usp_plane_count(yctx)
+        l0 = usp.usp_launch_count(yctx)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        usp.usp_step(yctx, args.cylinder_steps)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        yms = max_over_ranks(q0.elapsed_time(q1))
+        n_b, _ = usp.usp_plane_count(yctx)
+        yl = usp.usp_launch_count(yctx) - l0
+        usp.usp_profile_enable(yctx, True)
+        usp.usp_step(yctx, 8)
+        pk, pn = usp.usp_profile_read(yctx)
+        usp.usp_profile_enable(yctx, False)
+        yfl, ycnt = usp.usp_status(yctx)
+        # live count changes slowly; the mean of the two ends stands for it
+        n_mean = 0.5 * (n_a + n_b)
+        cyl = {"workload": yw.name + ", FP32 state, reconstruction on, dt = 0.5 tau_c",
+               "value": sum_over_ranks(n_mean) * args.cylinder_steps / (yms / 1e3), "unit": UNIT,
+               "ms_per_step": yms / args.cylinder_steps, "steps": args.cylinder_steps,
+               "first_step": 16, "particles": [int(n_a), int(n_b)], "gpu_launches": int(yl),
+               "ms_per_step_particle_passes": pk[0] / 8, "ms_per_step_cell_passes": pk[1] / 8,
+               "alg_bytes_per_particle_step": BYTES_PER_PARTICLE_STEP["plane_f32"],
+               "flags": int(yfl)}
+        yctx.destroy()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, cores, el, sample = cpu_baseline(w, args.cpu_seconds)
@@ -378,6 +421,7 @@ def run_ours(args, rank, world, local):
                              "autotune": {"blocks_per_sm": minb,
                                           "ms_by_blocks_per_sm_2_3_4": [float(x) for x in tune_ms]}},
                 "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "poiseuille_channel": chan,
+                "cylinder_plane": cyl,
                 "clocks": clk,
                 "status": {"flags": int(flags), "counters": [int(x) for x in counters]}}
         print(json.dumps(line), flush=True)

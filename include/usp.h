@@ -54,15 +54,20 @@ typedef enum {
  * the others report clamps the method applies and continues. */
 enum {
   USP_F_PB_CLAMP = 0x01,            /* p_B > 1 met (Sec. 3.A.2): binomial clamped to n   */
-  USP_F_CHOL_FAIL_AFTER_FIX = 0x02, /* D_tr not positive after the Sec. 3.A.3 fix       */
+  USP_F_CHOL_FAIL_AFTER_FIX = 0x02, /* T_tr^rel = 0 at the nu = 0 end of the Sec. 3.A.3
+                                       fix: no diffusion for that particle (a clamp)    */
   USP_F_NEG_RADICAND = 0x04,        /* velocity rescale of Sec. 4.C impossible; skipped  */
   USP_F_VIB_LOOP_CAP = 0x08,        /* vibrational +-1 correction hit 64 N draws         */
-  USP_F_TREL_CLAMP = 0x10,          /* a relaxation temperature came out negative        */
+  USP_F_TREL_CLAMP = 0x10,          /* a relaxation temperature or energy target came
+                                       out negative and was set to 0                    */
   USP_F_SAMPLER_CAP = 0x20,         /* a jump-sampler search hit 4096 steps              */
-  USP_F_A_NONPOS = 0x40,            /* 2 mu/p <= Pr dt in a cell: dt too large           */
+  USP_F_A_NONPOS = 0x40,            /* A outside (-1, 1): mu/p of a cell not finite > 0  */
   USP_F_SAMPLER_UNDERFLOW = 0x80,   /* jump pmf underflowed double                       */
+  USP_F_WALL_CAP = 0x100,           /* a particle met 16 wall events in one step         */
   USP_F_BOUNDS = 0x200,             /* an index check failed (kernel skipped the access) */
-  USP_F_WAIT_TIMEOUT = 0x400        /* a device-side wait gave up after its time limit  */
+  USP_F_WAIT_TIMEOUT = 0x400,       /* a device-side wait gave up after its time limit  */
+  USP_F_INFLOW_CAP = 0x800,         /* an inflow normal-speed draw hit 64 attempts       */
+  USP_F_CAPACITY = 0x1000           /* particle storage full: inflow of a step dropped   */
 };
 
 /* Counter slots of usp_status. */
@@ -75,7 +80,10 @@ enum {
   USP_C_WALL_HITS = 5,
   USP_C_INTERP_FALLBACK = 6,
   USP_C_SKIPPED_CELLS = 7, /* cells with fewer than two particles (not collided) */
-  USP_NCOUNTERS = 8
+  USP_C_INFLOW = 8,        /* particles generated at inflow faces (plane path)  */
+  USP_C_OUTFLOW = 9,       /* particles removed at open sides (plane path)      */
+  USP_C_NU_ZERO = 10,      /* positivity fixes that ended at nu = 0             */
+  USP_NCOUNTERS = 11
 };
 
 /* Number of per-cell moments written by usp_moments, field-major
@@ -137,6 +145,28 @@ typedef struct {
   int reconstruct;
 } usp_channel;
 
+/* 2D plane domain [x0, x1] x [y0, y1] on nx x ny uniform cells (cell
+ * j * nx + i), depth `depth` along z, with an optional circular body of
+ * radius cyl_r (<= 0: none) centred at (cyl_xc, cyl_yc), fully diffuse at
+ * T_wall (the hypersonic cylinder set-up of the paper's Sec. 5.C, on a
+ * uniform grid with cut cells).  bc[] gives the condition of the sides
+ * left, right, bottom, top (USP_BC_*); a side with inflow[k] = 1 (it must be
+ * open) lets the freestream (n_inf, T_inf, velocity U_inf along x) enter
+ * with its one-way Maxwellian flux.  F_num is the particle weight;
+ * reconstruct = 1 for the quadrant bilinear reconstruction of Sec. 3.B. */
+enum { USP_BC_OPEN = 0, USP_BC_SPECULAR = 1, USP_BC_DIFFUSE = 2 };
+typedef struct {
+  int nx, ny;
+  double x0, x1, y0, y1;
+  double cyl_xc, cyl_yc, cyl_r;
+  double T_wall;
+  double n_inf, T_inf, U_inf;
+  int bc[4];
+  int inflow[4];
+  double F_num, depth;
+  int reconstruct;
+} usp_plane;
+
 typedef struct usp_ctx usp_ctx;
 
 /* Make device `dev` current for the calling thread (cudaSetDevice) so that
@@ -197,6 +227,47 @@ int usp_channel_read(usp_ctx* ctx, double* h_acc, int reset);
 int usp_channel_get_particles(usp_ctx* ctx, double* h_y, double* h_cx, double* h_cy,
                               double* h_cz, double* h_erot, int32_t* h_lev, uint32_t* h_pid);
 
+/* Create a context for the 2D plane domain (usp_plane) with storage for
+ * `capacity` particles, holding n initial particles (x, y inside the domain,
+ * outside the body; velocities, specific rotational energies, levels and
+ * ids as in usp_init_channel; NULL ids: 0..n-1).  area_frac (nx * ny
+ * doubles in [0, 1], host) is the fluid fraction of each cell: the cell
+ * volume is area_frac dx dy depth, and only cells with fraction 1 serve as
+ * reconstruction neighbours.  dt is the time step [s].  precision USP_FP32
+ * or USP_FP64.  One step is: flight with events (body: diffuse re-emission;
+ * sides: specular reflection or removal), injection of the entering
+ * freestream particles (count floor(flux A dt / F_num + u) per face, entry
+ * point and entry time uniform, ids counted up from the largest initial
+ * id + 1), a stable sort by cell (moved particles before new ones within a
+ * cell), then per cell the collision step of Sec. 4.D with the fields
+ * reconstructed at each particle (Sec. 3.B) and the conservation scheme of
+ * Sec. 4.C.  The particle count lives on the device, so the step can be
+ * replayed from a CUDA graph; a step whose inflow would exceed `capacity`
+ * injects nothing and sets USP_F_CAPACITY.  Returns USP_EINVAL for invalid
+ * geometry, sizes, fractions or particles.  Synchronises. */
+int usp_init_plane(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
+                   const usp_plane* pl, double dt, const double* area_frac, int64_t n,
+                   int64_t capacity, const double* h_x, const double* h_y, const double* h_cx,
+                   const double* h_cy, const double* h_cz, const double* h_erot,
+                   const int32_t* h_lev, const uint32_t* h_pid);
+
+/* Live particle count of a plane context and the id the next entering
+ * particle will get.  Synchronises. */
+int usp_plane_count(usp_ctx* ctx, int64_t* n, uint32_t* next_pid);
+
+/* Current plane particles (cell order, conservation rescale applied) to host
+ * arrays of length cap; *n receives the live count (USP_EINVAL if it exceeds
+ * cap).  Any array may be NULL.  Synchronises. */
+int usp_plane_get_particles(usp_ctx* ctx, int64_t cap, int64_t* n, double* h_x, double* h_y,
+                            double* h_cx, double* h_cy, double* h_cz, double* h_erot,
+                            int32_t* h_lev, uint32_t* h_pid);
+
+/* Time averages of a spatial context (channel or plane), as
+ * usp_channel_sample / usp_channel_read; for a plane context the layout is
+ * n_cells * 12 + 2 doubles, the last two the sampled-step count and 0. */
+int usp_sample(usp_ctx* ctx, int on);
+int usp_sample_read(usp_ctx* ctx, double* h_acc, int reset);
+
 /* Enqueue nsteps collision steps (Sec. 4.D + Sec. 4.C) on the stream. */
 int usp_step(usp_ctx* ctx, int nsteps);
 
@@ -229,7 +300,9 @@ int usp_step_host(usp_ctx* ctx, const void* h_cx, const void* h_cy, const void* 
                   int32_t* h_lev_out);
 
 /* Read (and clear with reset != 0) the sticky status word and counters.
- * Synchronises.  Returns USP_EDEVICE if an error bit is set. */
+ * Synchronises.  Returns USP_EDEVICE if an error bit is set: USP_F_A_NONPOS,
+ * USP_F_SAMPLER_UNDERFLOW, USP_F_BOUNDS or USP_F_CAPACITY; the other bits
+ * record clamps and caps the method's readings define. */
 int usp_status(usp_ctx* ctx, uint32_t* flags, int64_t counters[USP_NCOUNTERS], int reset);
 
 /* Wait for all work of the context. */

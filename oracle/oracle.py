@@ -84,7 +84,8 @@ class Coeffs(C.Structure):
                  "A", "B", "alpha", "nu_ref",
                  "g_r", "g_v", "cv_T1", "T_check", "gamma_tr_rot", "gamma_tr_vib",
                  "gamma_rot_vib")] + [("t1_iters", C.c_int)] + \
-               [(n, C.c_double) for n in ("e_tr_tgt", "e_rot_tgt", "e_vib_tgt")]
+               [(n, C.c_double) for n in ("e_tr_tgt", "e_rot_tgt", "e_vib_tgt")] + \
+               [("tgt_clamped", C.c_int)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

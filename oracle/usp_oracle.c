@@ -223,6 +223,13 @@ int orc_cell_coeffs(const orc_species* sp, double n, double dt,
     o->e_tr_tgt = c_tr * T_tr - o->gamma_tr_rot * (T_tr - T_rot) - o->gamma_tr_vib * (T_tr - T_vib);
     o->e_rot_tgt = c_rot * T_rot + o->gamma_tr_rot * (T_tr - T_rot) - o->gamma_rot_vib * (T_rot - T_vib);
     o->e_vib_tgt = orc_e_vib(sp, T_vib) + o->gamma_tr_vib * (T_tr - T_vib) + o->gamma_rot_vib * (T_rot - T_vib);
+    /* For dt far above tau_rot the exchange terms overshoot and a target can
+     * come out negative (strong non-equilibrium, e.g. a near-empty cut cell);
+     * reading: such a target is 0 (the velocity rescale of Sec. 4.C still
+     * conserves the cell's energy). */
+    o->tgt_clamped = 0;
+    if (o->e_rot_tgt < 0.0) { o->e_rot_tgt = 0.0; o->tgt_clamped = 1; }
+    if (o->e_vib_tgt < 0.0) { o->e_vib_tgt = 0.0; o->tgt_clamped = 1; }
     return 0;
 }
 
@@ -772,6 +779,7 @@ int orc_homog_step(const orc_species* sp, int form, uint64_t seed,
                     lflags |= ORC_F_A_NONPOS;
                     goto merge;
                 }
+                if (cc.tgt_clamped) { lflags |= ORC_F_TREL_CLAMP; lcnt[ORC_C_TREL_CLAMP] += 1; }
                 for (int64_t j = b; j < e; ++j) {
                     double G[4], u5, u6, c[3] = { cx[j], cy[j], cz[j] };
                     uint32_t id = pid ? pid[j] : (uint32_t)j;
@@ -997,6 +1005,7 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
                 status = -1;
                 continue;
             }
+            if (cc[c].tgt_clamped) { *flags |= ORC_F_TREL_CLAMP; counters[ORC_C_TREL_CLAMP] += 1; }
             ok[c] = 1;
         }
         /* 4. particles: reconstruction (Sec. 3.B) and collision (Sec. 4.D) */
@@ -1156,6 +1165,11 @@ static int advect_plane(const orc_species* sp, int form, uint64_t seed, uint32_t
                     double t = (-b - sqrt(disc)) / a;
                     if (t >= 0.0 && t <= te) { te = t; ev = 0; }
                 }
+            } else if (c <= 0.0 && b < 0.0) {
+                /* on or (by rounding, e.g. after a specular event at the
+                 * body's foot on the symmetry plane) inside the surface and
+                 * moving inward: the wall event is now */
+                te = 0.0; ev = 0;
             }
         }
         if (*cx < 0.0) { double t = (pl->x0 - *x) / *cx; if (t <= te && (ev < 0 || t < te)) { te = t < 0.0 ? 0.0 : t; ev = 1; } }
@@ -1396,6 +1410,7 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
                 status = -1;
                 continue;
             }
+            if (cc[c].tgt_clamped) { *flags |= ORC_F_TREL_CLAMP; counters[ORC_C_TREL_CLAMP] += 1; }
             ok[c] = 1;
         }
         /* 5. particles */

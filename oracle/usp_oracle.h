@@ -80,6 +80,7 @@ typedef struct {
     int    t1_iters;
     /* second-order targets, Eqs. e_tr_relax .. e_vib_relax */
     double e_tr_tgt, e_rot_tgt, e_vib_tgt;
+    int    tgt_clamped;    /* a negative rotational / vibrational target was set to 0 */
 } orc_coeffs;
 
 /* ---- random numbers ---------------------------------------------------- */

@@ -28,9 +28,12 @@ enum : uint32_t {
   F_WALL_CAP = 0x100u,
   F_BOUNDS = 0x200u,
   F_WAIT_TIMEOUT = 0x400u,
+  F_INFLOW_CAP = 0x800u,
+  F_CAPACITY = 0x1000u,
 };
 enum { C_CHOL_FIX = 0, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND,
-       C_WALL_HITS, C_INTERP_FALLBACK, C_SKIPPED_CELLS, NCOUNTERS };
+       C_WALL_HITS, C_INTERP_FALLBACK, C_SKIPPED_CELLS, C_INFLOW, C_OUTFLOW, C_NU_ZERO,
+       NCOUNTERS };
 
 // Philox stream layout: particle counter (pid, step, tag, 0); cell counter
 // (cell, step, 0x80000000 | tag, block).
@@ -302,7 +305,8 @@ __device__ __forceinline__ void collision_numbers(const Species& s, const S& Ttr
        (kPi * s.d_ref * s.d_ref / s.sigma_vib) * pow(s.T_ref / Ttr, s.omega - 0.5);
 }
 
-// Per-cell coefficients of Sec. 3.A: alpha = A^(1/3), nu, the gamma
+// Per-cell coefficients of Sec. 3.A: alpha = A^(1/3) (the real cube root,
+// negative when dt >= 2 mu / (p Pr)), nu, the gamma
 // coefficients with the implicit c_v,vib(T_1) (fixed point started at
 // c_v,vib(T_tr), relative tolerance 1e-14, at most 50 passes), and the
 // second-order energy targets.
@@ -312,6 +316,7 @@ struct CellCoeffsT {
   S g_tr_rot, g_tr_vib, g_rot_vib;
   S e_rot_tgt, e_vib_tgt;
   bool ok;
+  bool tgt_clamped;   // a negative target was set to 0
 };
 
 template <typename S>
@@ -330,7 +335,7 @@ __device__ inline CellCoeffsT<S> cell_coeffs_t(const Species& s, const S& omega,
   c.Pr = prandtl_T<S>(s, Tvib);
   c.A = (2.0 * c.mu_p - c.Pr * dt) / (2.0 * c.mu_p + c.Pr * dt);
   c.B = (2.0 * c.mu_p - dt) / (2.0 * c.mu_p + dt);
-  c.ok = c.A > 0.0;
+  c.ok = c.A > -1.0 && c.A < 1.0;
   c.alpha = c.ok ? cbrt(c.A) : S(0.0);
   const S a2 = c.alpha * c.alpha;
   c.nu_ref = (c.B - a2) / (1.0 - a2);
@@ -356,6 +361,11 @@ __device__ inline CellCoeffsT<S> cell_coeffs_t(const Species& s, const S& omega,
   c.g_rot_vib = 2.0 * gr * gv * crot * x / den;
   c.e_rot_tgt = crot * Trot + c.g_tr_rot * (Ttr - Trot) - c.g_rot_vib * (Trot - Tvib);
   c.e_vib_tgt = evT + c.g_tr_vib * (Ttr - Tvib) + c.g_rot_vib * (Trot - Tvib);
+  // far above tau_rot the exchange terms can overshoot below zero: such a
+  // target is 0 (the velocity rescale still conserves the cell's energy)
+  c.tgt_clamped = false;
+  if (c.e_rot_tgt < 0.0) { c.e_rot_tgt = S(0.0); c.tgt_clamped = true; }
+  if (c.e_vib_tgt < 0.0) { c.e_vib_tgt = S(0.0); c.tgt_clamped = true; }
   return c;
 }
 
@@ -428,11 +438,11 @@ __device__ __forceinline__ void sym3_minmax(const T* P, T& lmin, T& lmax) {
 // clamped by Eq. nu_USP_positivity with the current T_tr^rel and shrunk by
 // 1 - 1e-6, alpha^2 from Eq. alpha_USP_positivity_1 clamped to
 // [0, 1 - 1e-12], the sign giving the Pr nearest the target, up to four
-// passes; then nu = 0).  Also returns the relaxation temperatures for that
+// passes; then nu = 0 with alpha^2 = B, a failure only if T_tr^rel is 0).  Also returns the relaxation temperatures for that
 // alpha.  chol_fix / fail report what happened.
 struct DriftDiff {
   double alpha, L[6], Ttr_rel, Trot_rel, evib_rel;
-  bool fixed, failed, clamped;
+  bool fixed, nu_zero, failed, clamped;
 };
 
 __device__ inline DriftDiff drift_diffusion(const Species& s, const CellCoeffs& c, double dt,
@@ -441,6 +451,7 @@ __device__ inline DriftDiff drift_diffusion(const Species& s, const CellCoeffs& 
   const double R = gasR(s);
   o.alpha = c.alpha;
   o.fixed = false;
+  o.nu_zero = false;
   o.failed = false;
   relax_temps(s, c, o.alpha, Ttr, Trot, Tvib, o.Ttr_rel, o.Trot_rel, o.evib_rel, o.clamped);
   double nu = c.nu_ref;
@@ -480,8 +491,19 @@ __device__ inline DriftDiff drift_diffusion(const Species& s, const CellCoeffs& 
     ok = chol3(M, o.L);
   }
   if (!ok) {
-    o.failed = true;
-    const double sq = sqrt(R * o.Ttr_rel);
+    // nu = 0 with alpha^2 = B (Eq. alpha_USP_positivity_1 at nu = 0): inside
+    // the admissible range whenever T_tr^rel > 0
+    o.nu_zero = true;
+    const double a2 = fmin(fmax(c.B, 0.0), 1.0 - 1e-12);
+    const double ap = sqrt(a2), am = -ap;
+    const double prp = 2.0 * c.mu_p * (1.0 - ap * ap * ap) / (dt * (1.0 + ap * ap * ap));
+    const double prm = 2.0 * c.mu_p * (1.0 - am * am * am) / (dt * (1.0 + am * am * am));
+    o.alpha = (fabs(prm - c.Pr) < fabs(prp - c.Pr)) ? am : ap;
+    bool cl;
+    relax_temps(s, c, o.alpha, Ttr, Trot, Tvib, o.Ttr_rel, o.Trot_rel, o.evib_rel, cl);
+    o.clamped = o.clamped || cl;
+    o.failed = !(o.Ttr_rel > 0.0);
+    const double sq = o.failed ? 0.0 : sqrt(R * o.Ttr_rel);
     o.L[0] = sq; o.L[1] = 0.0; o.L[2] = sq; o.L[3] = 0.0; o.L[4] = 0.0; o.L[5] = sq;
   }
   return o;

@@ -36,6 +36,7 @@
 
 #include "../../include/usp.h"
 #include "usp_channel.h"
+#include "usp_plane.h"
 #include "usp_device.cuh"
 
 using namespace usp;
@@ -538,10 +539,15 @@ __device__ void write_params(const Species& sp, CellState& cs, CollideParams<T>&
   }
   cs.e_rot_tgt = c.e_rot_tgt;
   cs.e_vib_tgt = c.e_vib_tgt;
+  if (c.tgt_clamped) {
+    atomicOr(flags, (uint32_t)F_TREL_CLAMP);
+    atomicAdd(&counters[C_TREL_CLAMP], 1ull);
+  }
   // homogeneous cell: the fields at every particle are the cell values, so
   // D_tr, its Cholesky factor and the relaxation temperatures are per cell
   const DriftDiff dd = drift_diffusion(sp, c, cs.dt, cs.Pi, cs.Ttr, cs.Trot, Tvib);
   if (dd.fixed) atomicAdd(&counters[C_CHOL_FIX], 1ull);
+  if (dd.nu_zero) atomicAdd(&counters[C_NU_ZERO], 1ull);
   if (dd.failed) atomicOr(flags, (uint32_t)F_CHOL_FAIL_AFTER_FIX);
   if (dd.clamped) {
     atomicOr(flags, (uint32_t)F_TREL_CLAMP);
@@ -922,8 +928,9 @@ __global__ void gather_state_native(int ncell, const CellState* __restrict__ cel
 // Host side
 // ===========================================================================
 struct usp_ctx {
-  int kind;                 // 0 homogeneous cells, 1 channel
+  int kind;                 // 0 homogeneous cells, 1 channel, 2 plane
   ChannelCtx* ch;
+  PlaneCtx* pl;
   cudaEvent_t prof_pending;
   Species sp;
   usp_config cfg;
@@ -1175,11 +1182,13 @@ int launch_step(usp_ctx* c) {
 
 int kernels_per_step(const usp_ctx* c) {
   if (c->kind == 1) return ch_kernels_per_step(c->ch);
+  if (c->kind == 2) return pl_kernels_per_step(c->pl);
   return c->precision == USP_FP32 ? 4 : 3;
 }
 
 int step_once(usp_ctx* c) {
   if (c->kind == 1) return ch_launch_step(c->ch, make_env(c), c->profiling ? prof_cb : nullptr);
+  if (c->kind == 2) return pl_launch_step(c->pl, make_env(c), c->profiling ? prof_cb : nullptr);
   return c->precision == USP_FP32 ? launch_step<float>(c) : launch_step<double>(c);
 }
 
@@ -1411,6 +1420,7 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   usp_ctx* c = new usp_ctx();
   c->kind = 0;
   c->ch = nullptr;
+  c->pl = nullptr;
   std::memset((void*)&c->sp, 0, sizeof(c->sp));
   c->cfg = *cfg;
   c->sp = to_dev(sp);
@@ -1552,6 +1562,7 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
   usp_ctx* c = new usp_ctx();
   c->kind = 1;
   c->ch = nullptr;
+  c->pl = nullptr;
   c->cfg = *cfg;
   c->sp = to_dev(sp);
   c->precision = cfg->precision;
@@ -1600,19 +1611,101 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
   return USP_OK;
 }
 
-int usp_channel_sample(usp_ctx* c, int on) {
-  if (!c || c->kind != 1) return USP_EINVAL;
+int usp_init_plane(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
+                   const usp_plane* pl, double dt, const double* area_frac, int64_t n,
+                   int64_t capacity, const double* h_x, const double* h_y, const double* h_cx,
+                   const double* h_cy, const double* h_cz, const double* h_erot,
+                   const int32_t* h_lev, const uint32_t* h_pid) {
+  if (!out || !sp || !cfg || !pl) return USP_EINVAL;
+  if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64) return USP_EINVAL;
+  if (!(sp->m > 0) || !(sp->d_ref > 0) || !(sp->T_ref > 0) || !(sp->c_alpha > 0) ||
+      !(sp->theta_v > 0))
+    return USP_EINVAL;
+  *out = nullptr;
+  usp_ctx* c = new usp_ctx();
+  c->kind = 2;
+  c->ch = nullptr;
+  c->pl = nullptr;
+  c->cfg = *cfg;
+  c->sp = to_dev(sp);
+  c->precision = cfg->precision;
+  c->ncell = 0;
+  c->nparticles = 0;
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+  c->graph_steps = 0;
+  c->graph_parity = 0;
+  c->step = cfg->step0;
+  c->launches = 0;
+  c->device_bytes = 0;
+  c->profiling = 0;
+  c->ev_used = 0;
+  c->minb = 0;
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+    c->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return USP_ECUDA;
+    }
+    c->own_stream = true;
+  }
+  auto fail = [&](int rc) {
+    cudaStreamSynchronize(c->stream);
+    if (c->pl) pl_destroy(c->pl);
+    dev_free_all(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return rc;
+  };
+  c->flags = (uint32_t*)dev_alloc(c, 256);
+  c->counters = (unsigned long long*)dev_alloc(c, 256);
+  if (!c->flags || !c->counters) return fail(USP_ENOMEM);
+  if (cudaMemsetAsync(c->flags, 0, 256, c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->counters, 0, 256, c->stream) != cudaSuccess)
+    return fail(USP_ECUDA);
+  const int rc = pl_create(&c->pl, make_env(c), pl, dt, area_frac, n, capacity, cfg->step0, h_x,
+                           h_y, h_cx, h_cy, h_cz, h_erot, h_lev, h_pid);
+  if (rc != USP_OK) return fail(rc);
+  c->nparticles = n;
+  c->ncell = pl_ncell(c->pl);
+  *out = c;
+  return USP_OK;
+}
+
+int usp_plane_count(usp_ctx* c, int64_t* n, uint32_t* next_pid) {
+  if (!c || c->kind != 2) return USP_EINVAL;
+  return pl_count(c->pl, make_env(c), n, next_pid);
+}
+
+int usp_plane_get_particles(usp_ctx* c, int64_t cap, int64_t* n, double* x, double* y,
+                            double* cx, double* cy, double* cz, double* erot, int32_t* lev,
+                            uint32_t* pid) {
+  if (!c || c->kind != 2) return USP_EINVAL;
+  return pl_get_particles(c->pl, make_env(c), cap, n, x, y, cx, cy, cz, erot, lev, pid);
+}
+
+int usp_sample(usp_ctx* c, int on) {
+  if (!c || (c->kind != 1 && c->kind != 2)) return USP_EINVAL;
   if (c->graph_exec) {  // the captured step depends on the sampling switch
     cudaGraphExecDestroy(c->graph_exec);
     cudaGraphDestroy(c->graph);
     c->graph_exec = nullptr;
   }
-  return ch_sample(c->ch, on);
+  return c->kind == 1 ? ch_sample(c->ch, on) : pl_sample(c->pl, on);
+}
+
+int usp_channel_sample(usp_ctx* c, int on) { return usp_sample(c, on); }
+
+int usp_sample_read(usp_ctx* c, double* h_acc, int reset) {
+  if (!c || (c->kind != 1 && c->kind != 2) || !h_acc) return USP_EINVAL;
+  return c->kind == 1 ? ch_read(c->ch, make_env(c), h_acc, reset)
+                      : pl_read(c->pl, make_env(c), h_acc, reset);
 }
 
 int usp_channel_read(usp_ctx* c, double* h_acc, int reset) {
-  if (!c || c->kind != 1 || !h_acc) return USP_EINVAL;
-  return ch_read(c->ch, make_env(c), h_acc, reset);
+  return usp_sample_read(c, h_acc, reset);
 }
 
 int usp_channel_get_particles(usp_ctx* c, double* y, double* cx, double* cy, double* cz,
@@ -1637,7 +1730,7 @@ int usp_step(usp_ctx* c, int nsteps) {
   // its graphs hold an even number of steps and are captured at the current
   // buffer parity; an odd remainder runs eagerly.
   int G = nsteps >= 16 ? 16 : 1;
-  if (c->kind == 1) G = nsteps >= 16 ? 16 : (nsteps >= 2 ? 2 : 0);
+  if (c->kind != 0) G = nsteps >= 16 ? 16 : (nsteps >= 2 ? 2 : 0);
   if (G == 0) {
     int rc = step_once(c);
     if (rc) return rc;
@@ -1645,7 +1738,7 @@ int usp_step(usp_ctx* c, int nsteps) {
     c->step += nsteps;
     return USP_OK;
   }
-  const int parity = c->kind == 1 ? ch_parity(c->ch) : 0;
+  const int parity = c->kind == 1 ? ch_parity(c->ch) : (c->kind == 2 ? pl_parity(c->pl) : 0);
   if (!c->graph_exec || c->graph_steps != G || c->graph_parity != parity) {
     int rc = build_graph(c, G);
     if (rc) return rc;
@@ -1669,6 +1762,7 @@ int usp_step(usp_ctx* c, int nsteps) {
 int usp_moments(usp_ctx* c, double* out, int out_is_device) {
   if (!c || !out) return USP_EINVAL;
   if (c->kind == 1) return ch_moments(c->ch, make_env(c), out, out_is_device);
+  if (c->kind == 2) return pl_moments(c->pl, make_env(c), out, out_is_device);
   int rc = c->precision == USP_FP32 ? compute_moments<float>(c, nullptr)
                                     : compute_moments<double>(c, nullptr);
   if (rc) return rc;
@@ -1786,7 +1880,7 @@ int usp_status(usp_ctx* c, uint32_t* flags, int64_t* counters, int reset) {
     CK(cudaMemsetAsync(c->counters, 0, 256, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
-  const uint32_t err = F_CHOL_FAIL_AFTER_FIX | F_A_NONPOS | F_SAMPLER_UNDERFLOW | F_BOUNDS;
+  const uint32_t err = F_A_NONPOS | F_SAMPLER_UNDERFLOW | F_BOUNDS | F_CAPACITY;
   return (f & err) ? USP_EDEVICE : USP_OK;
 }
 
@@ -1799,8 +1893,15 @@ int usp_sync(usp_ctx* c) {
 int usp_info(usp_ctx* c, int64_t* np, int* nc, int* prec, int64_t* step, int* tile,
              int64_t* bytes) {
   if (!c) return USP_EINVAL;
-  if (np) *np = c->kind == 1 ? ch_nparticles(c->ch) : c->nparticles;
-  if (nc) *nc = c->kind == 1 ? ch_ncell(c->ch) : c->ncell;
+  if (np) {
+    if (c->kind == 2) {
+      const int rc = pl_count(c->pl, make_env(c), np, nullptr);
+      if (rc) return rc;
+    } else {
+      *np = c->kind == 1 ? ch_nparticles(c->ch) : c->nparticles;
+    }
+  }
+  if (nc) *nc = c->kind == 1 ? ch_ncell(c->ch) : (c->kind == 2 ? pl_ncell(c->pl) : c->ncell);
   if (prec) *prec = c->precision;
   if (step) *step = c->step;
   if (tile) *tile = c->tile;
@@ -1858,6 +1959,7 @@ void usp_destroy(usp_ctx* c) {
   }
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ch) ch_destroy(c->ch);
+  if (c->pl) pl_destroy(c->pl);
   dev_free_all(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;

@@ -1,0 +1,1178 @@
+// usp_plane.cu -- the spatial USP-FPM step on a uniform 2D Cartesian grid
+// with a circular body (the hypersonic cylinder set-up of Kim & Jun, arXiv
+// 2508.05642, Sec. 5.C: half body on a specular symmetry plane, fully
+// diffuse cylinder, freestream inflow, supersonic outflow), on sm_103a.
+//
+// The particle count changes every step (inflow, outflow), so it lives on
+// the device and every launch reads it there: a step is a fixed launch
+// sequence that a CUDA graph can hold.  One step:
+//   pl_advect      pending conservation rescale of the previous step, flight
+//                  with events (cylinder hit -> diffuse re-emission at
+//                  T_wall, sides -> specular / removal), new cell key; a
+//                  removed particle gets the key ncell
+//   pl_inflow      per inflow face the number of entering particles
+//                  floor(flux A dt / F_num + u); exclusive scan over faces,
+//                  capacity check, ids for the new particles
+//   pl_inject      the entering particles: flux-weighted normal speed,
+//                  Maxwellian tangential components, uniform entry point
+//                  and entry time, flight for the rest of the step
+//   radix passes   stable LSD radix sort of (cell key, index) over the moved
+//                  and the new particles, 8-bit digits, removed ones last
+//   pl_offsets     cell segment starts; the new live count is the start of
+//                  the removed particles' segment
+//   pl_gather      live state permuted into cell order (other buffer)
+//   ch_moments, ch_coeffs   per-cell moments and coefficients (Sec. 2.A,
+//                  3.A), cut cells with their fluid volume
+//   pl_params      per cell the reconstruction stencil of Sec. 3.B: for each
+//                  side of the centroid the neighbour used along x and y and
+//                  whether the quadrant's diagonal neighbour is usable
+//   pl_collide     per particle: bilinear fields of its quadrant, collision
+//                  of Sec. 4.D; per-cell sums
+//   ch_levelfix, ch_update  conservation of Sec. 4.C (rescale kept pending)
+//   pl_sample      (while sampling) time-average sums of the post-step state
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "usp_plane.h"
+#include "usp_spatial.cuh"
+
+namespace {
+
+constexpr uint32_t PTAG_INFLOW_P = 5u, PTAG_INFLOW_T = 6u, PTAG_INFLOW_V = 7u;
+constexpr uint32_t CTAG_INFLOW = 0x80000004u;
+constexpr int kInflowTries = 64;
+constexpr int kBlk = 256;
+
+// Device-resident counts of the current step.
+struct PlCount {
+  long long n;        // live particles
+  long long ntot;     // live + entering (before the sort)
+  long long ninj;     // entering this step (0 if the storage was full)
+  unsigned int pid0;  // id of the first entering particle
+  unsigned int next_pid;
+};
+
+struct PlGeom {
+  int nx, ny, ncell;
+  double x0, x1, y0, y1, dx, dy;
+  double cxc, cyc, cr;
+  double Tw, dt;
+  int bc[4];          // left, right, bottom, top
+};
+
+struct PlInflow {
+  int nf[4];          // faces per side (0 if the side has no inflow)
+  int base[4];        // first face of each side in the face list
+  int nfaces;
+  double expect[4];   // entering particles per face and step (flux A dt / F_num)
+  double u_n[4];      // freestream velocity along the inward normal
+  double RT, U, T;    // freestream R T, x velocity, temperature
+};
+
+// Per-cell parameters of the particle kernel, working precision T.
+template <typename T>
+struct PlParams {
+  T alpha, nu_ref, B, mu_p, Pr, gtr, gtv, grv;
+  T R, theta, dt;
+  T xc, yc;
+  T hx[2], hy[2], hxy[4];   // (neighbour - cell) offsets: dx, dy and dx dy per choice
+  T F[kNF];
+  int xcell[2], ycell[2];   // neighbour used for sx / sy < 0 ([0]) and >= 0 ([1]), -1 none
+  int dcell[4];             // quadrant (sy >= 0) * 2 + (sx >= 0): diagonal, -1 none
+  int active, pad;
+};
+
+__device__ __forceinline__ int grid_threads() { return gridDim.x * blockDim.x; }
+
+template <typename T>
+__device__ __forceinline__ int plane_cell(const PlGeom& g, T x, T y) {
+  int i = (int)floor((x - (T)g.x0) / (T)g.dx);
+  int j = (int)floor((y - (T)g.y0) / (T)g.dy);
+  i = i < 0 ? 0 : (i >= g.nx ? g.nx - 1 : i);
+  j = j < 0 ? 0 : (j >= g.ny ? g.ny - 1 : j);
+  return j * g.nx + i;
+}
+
+// Diffuse re-emission at T_w about the inward normal (nx, ny): Rayleigh
+// normal speed, Maxwellian in-plane tangential and z components,
+// exponential eps_rot, geometric level.  Draws (pid, step, 2, hit) and
+// (pid, step, 3, hit).
+template <typename T>
+__device__ void plane_emit(const Species& sp, double Tw, double nx, double ny, uint32_t pid,
+                           uint32_t step, int hit, uint32_t k0, uint32_t k1, T& vx, T& vy, T& vz,
+                           T& e, int& l) {
+  const double R = gasR(sp);
+  const U4 w = philox4x32_10(pid, step, PTAG_WALL_A, (uint32_t)hit, k0, k1);
+  const U4 v = philox4x32_10(pid, step, PTAG_WALL_B, (uint32_t)hit, k0, k1);
+  const double u0 = (double)uniform_open<T>(w.x);
+  const double u1 = (double)uniform_open<T>(w.y);
+  const double u2 = (double)uniform_open<T>(w.z);
+  const double u3 = (double)uniform_open<T>(w.w);
+  const double u4 = (double)uniform_open<T>(v.x);
+  const double vn = sqrt(-2.0 * R * Tw * log(u0));
+  double g1, g2;
+  box_muller(u1, u2, g1, g2);
+  const double st = sqrt(R * Tw);
+  const double tx = -ny, ty = nx;
+  vx = (T)(vn * nx + st * g1 * tx);
+  vy = (T)(vn * ny + st * g1 * ty);
+  vz = (T)(st * g2);
+  e = (T)(-R * Tw * log(u3));
+  l = (int)floor(-log(u4) * Tw / sp.theta_v);
+}
+
+// Flight over t_left with events, earliest first: cylinder (diffuse; a
+// particle on or inside the surface moving inward hits it at once), left,
+// right, bottom, top (ties to the earlier in that order).  An event
+// moves the particle there and applies the side's condition; the flight
+// continues for the rest of the time.  Returns false when the particle left
+// through an open side.  hits counts the events met (at most 16).
+template <typename T>
+__device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint32_t step,
+                          uint32_t k0, uint32_t k1, T t_left, T& x, T& y, T& vx, T& vy, T& vz,
+                          T& e, int& l, int& hits, uint32_t& fl) {
+  for (;;) {
+    int ev = -1;
+    T te = t_left;
+    if (g.cr > 0.0) {
+      const T dx = x - (T)g.cxc, dy = y - (T)g.cyc;
+      const T a = vx * vx + vy * vy;
+      const T b = dx * vx + dy * vy;
+      const T c = dx * dx + dy * dy - (T)g.cr * (T)g.cr;
+      if (c > T(0) && b < T(0) && a > T(0)) {
+        const T disc = b * b - a * c;
+        if (disc >= T(0)) {
+          const T t = (-b - sqrt(disc)) / a;
+          if (t >= T(0) && t <= te) { te = t; ev = 0; }
+        }
+      } else if (c <= T(0) && b < T(0)) {
+        // on or (by rounding, e.g. after a specular event at the body's foot
+        // on the symmetry plane) inside the surface, moving inward: hit now
+        te = T(0);
+        ev = 0;
+      }
+    }
+    if (vx < T(0)) {
+      const T t = ((T)g.x0 - x) / vx;
+      if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 1; }
+    }
+    if (vx > T(0)) {
+      const T t = ((T)g.x1 - x) / vx;
+      if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 2; }
+    }
+    if (vy < T(0)) {
+      const T t = ((T)g.y0 - y) / vy;
+      if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 3; }
+    }
+    if (vy > T(0)) {
+      const T t = ((T)g.y1 - y) / vy;
+      if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 4; }
+    }
+    if (ev < 0) {
+      x += vx * t_left;
+      y += vy * t_left;
+      return true;
+    }
+    x += vx * te;
+    y += vy * te;
+    t_left -= te;
+    if (hits >= kWallHitCap) {
+      fl |= F_WALL_CAP;
+      return true;
+    }
+    T nx = T(0), ny = T(0);
+    int kind;
+    if (ev == 0) {
+      nx = (x - (T)g.cxc) / (T)g.cr;
+      ny = (y - (T)g.cyc) / (T)g.cr;
+      kind = USP_BC_DIFFUSE;
+    } else {
+      const int side = ev - 1;
+      kind = g.bc[side];
+      if (side == 0) { nx = T(1); x = (T)g.x0; }
+      if (side == 1) { nx = T(-1); x = (T)g.x1; }
+      if (side == 2) { ny = T(1); y = (T)g.y0; }
+      if (side == 3) { ny = T(-1); y = (T)g.y1; }
+    }
+    if (kind == USP_BC_OPEN) return false;
+    if (kind == USP_BC_SPECULAR) {
+      const T vn = vx * nx + vy * ny;
+      vx -= T(2) * vn * nx;
+      vy -= T(2) * vn * ny;
+    } else {
+      plane_emit<T>(sp, g.Tw, (double)nx, (double)ny, pid, step, hits, k0, k1, vx, vy, vz, e, l);
+    }
+    hits += 1;
+  }
+}
+
+template <typename T>
+__global__ void pl_advect(PlGeom g, const PlCount* __restrict__ cnt,
+                          const int* __restrict__ keycell, const ChCellT<double>* __restrict__ cells,
+                          T* __restrict__ x, T* __restrict__ y, T* __restrict__ cx,
+                          T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
+                          int* __restrict__ lev, const uint32_t* __restrict__ pid,
+                          int* __restrict__ keyout, int* __restrict__ idxout,
+                          const long long* __restrict__ dstep, Species sp, uint32_t k0,
+                          uint32_t k1, uint32_t* flags, unsigned long long* counters) {
+  const long long n = cnt->n;
+  const uint32_t step = (uint32_t)*dstep;
+  uint32_t fl = 0;
+  unsigned long long nhit = 0, nout = 0;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += grid_threads()) {
+    const ChCellT<double>& cc = cells[keycell[j]];
+    // pending conservation rescale of the previous step
+    T vx = (T)cc.Un[0] + (T)cc.s * (cx[j] - (T)cc.Us[0]);
+    T vy = (T)cc.Un[1] + (T)cc.s * (cy[j] - (T)cc.Us[1]);
+    T vz = (T)cc.Un[2] + (T)cc.s * (cz[j] - (T)cc.Us[2]);
+    T e = (T)cc.r * er[j];
+    int l = lev[j];
+    T px = x[j], py = y[j];
+    int hits = 0;
+    const bool keep = plane_fly<T>(g, sp, pid[j], step, k0, k1, (T)g.dt, px, py, vx, vy, vz, e,
+                                   l, hits, fl);
+    nhit += hits;
+    nout += keep ? 0 : 1;
+    x[j] = px; y[j] = py; cx[j] = vx; cy[j] = vy; cz[j] = vz; er[j] = e; lev[j] = l;
+    keyout[j] = keep ? plane_cell(g, px, py) : g.ncell;
+    idxout[j] = (int)j;
+  }
+  fl = __reduce_or_sync(0xffffffffu, fl);
+  nhit = wsum(nhit);
+  nout = wsum(nout);
+  if ((threadIdx.x & 31) == 0) {
+    if (fl) atomicOr(flags, fl);
+    if (nhit) atomicAdd(&counters[C_WALL_HITS], nhit);
+    if (nout) atomicAdd(&counters[C_OUTFLOW], nout);
+  }
+}
+
+// face q of the inflow list -> side and face index along the side
+__device__ __forceinline__ void face_of(const PlInflow& f, int q, int& side, int& k) {
+  side = 0;
+  while (side < 3 && (f.nf[side] == 0 || q >= f.base[side] + f.nf[side])) ++side;
+  k = q - f.base[side];
+}
+
+// One block of 1024 threads: the number of particles entering through each
+// face this step, floor(expect + u) with u from the cell stream
+// (face id, step, 0x80000004, 0), face id = side << 24 | face; its exclusive
+// scan; the capacity check and the ids of the new particles.
+__global__ void pl_inflow(PlInflow f, PlCount* __restrict__ cnt, int* __restrict__ face_off,
+                          long long cap, const long long* __restrict__ dstep, uint32_t k0,
+                          uint32_t k1, uint32_t* flags, unsigned long long* counters) {
+  __shared__ int wsums[32];
+  __shared__ long long carry;
+  const uint32_t step = (uint32_t)*dstep;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  if (t == 0) carry = 0;
+  __syncthreads();
+  for (int q0 = 0; q0 < f.nfaces; q0 += blockDim.x) {
+    const int q = q0 + t;
+    int c = 0;
+    if (q < f.nfaces) {
+      int side, k;
+      face_of(f, q, side, k);
+      const uint32_t fid = ((uint32_t)side << 24) | (uint32_t)k;
+      const U4 r = philox4x32_10(fid, step, CTAG_INFLOW, 0u, k0, k1);
+      c = (int)floor(f.expect[side] + uniform_open<double>(r.x));
+    }
+    // block exclusive scan of c
+    int v = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane == 31) wsums[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      int s = lane < (int)(blockDim.x >> 5) ? wsums[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += u;
+      }
+      wsums[lane] = s;   // inclusive over warps
+    }
+    __syncthreads();
+    const long long before = carry + (w > 0 ? wsums[w - 1] : 0) + (v - c);
+    if (q < f.nfaces) face_off[q] = (int)before;
+    __syncthreads();
+    if (t == 0) carry += wsums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (t == 0) {
+    const long long total = carry;
+    face_off[f.nfaces] = (int)total;
+    const long long n = cnt->n;
+    long long ninj = total;
+    if (n + total > cap) {
+      atomicOr(flags, (uint32_t)F_CAPACITY);
+      ninj = 0;
+    }
+    cnt->ninj = ninj;
+    cnt->ntot = n + ninj;
+    cnt->pid0 = cnt->next_pid;
+    cnt->next_pid = cnt->next_pid + (unsigned int)total;
+    if (total) atomicAdd(&counters[C_INFLOW], (unsigned long long)total);
+  }
+}
+
+// Inward normal speed of an entering particle (density proportional to
+// w exp(-(w - s)^2) on w > 0, w = v_n / sqrt(2RT), s = u_n / sqrt(2RT)),
+// by rejection, attempt k drawing the block (pid, step, 7, k): for s >= 0 a
+// mixture proposal (|w - s| + s) exp(-(w - s)^2) (two-sided Rayleigh of
+// weight 1, Gaussian of weight s sqrt(pi)), accepted if w > 0 and
+// u3 (|w - s| + s) <= w; for s < 0 the Rayleigh proposal 2 w exp(-w^2),
+// accepted if u3 <= exp(2 s w).  Double precision on uniforms of the
+// working precision.
+template <typename T>
+__device__ double inflow_speed(double RT, double u_n, uint32_t pid, uint32_t step, uint32_t k0,
+                               uint32_t k1, uint32_t& fl) {
+  const double sc = sqrt(2.0 * RT);
+  const double s = u_n / sc;
+  const double p1 = 1.0 / (1.0 + s * sqrt(kPi));
+  for (int k = 0; k < kInflowTries; ++k) {
+    const U4 r = philox4x32_10(pid, step, PTAG_INFLOW_V, (uint32_t)k, k0, k1);
+    const double u0 = (double)uniform_open<T>(r.x), u1 = (double)uniform_open<T>(r.y);
+    const double u2 = (double)uniform_open<T>(r.z), u3 = (double)uniform_open<T>(r.w);
+    if (s < 0.0) {
+      const double wn = sqrt(-log(u1));
+      if (u3 <= exp(2.0 * s * wn)) return wn * sc;
+      continue;
+    }
+    double t;
+    if (u0 < p1) {
+      t = sqrt(-log(u1));
+      if (u2 < 0.5) t = -t;
+    } else {
+      double g1, g2;
+      box_muller(u1, u2, g1, g2);
+      t = g1 / sqrt(2.0);
+    }
+    const double wn = s + t;
+    if (!(wn > 0.0)) continue;
+    if (u3 * (fabs(t) + s) <= wn) return wn * sc;
+  }
+  fl |= F_INFLOW_CAP;
+  return (s > 0.0 ? s : 0.5 * sqrt(kPi)) * sc;
+}
+
+// one warp per inflow face; lanes over the face's entering particles
+template <typename T>
+__global__ void pl_inject(PlGeom g, PlInflow f, const PlCount* __restrict__ cnt,
+                          const int* __restrict__ face_off, T* __restrict__ x, T* __restrict__ y,
+                          T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ cz,
+                          T* __restrict__ er, int* __restrict__ lev, uint32_t* __restrict__ pid,
+                          int* __restrict__ keyout, int* __restrict__ idxout,
+                          const long long* __restrict__ dstep, Species sp, uint32_t k0,
+                          uint32_t k1, uint32_t* flags, unsigned long long* counters) {
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (q >= f.nfaces || cnt->ninj == 0) return;
+  const uint32_t step = (uint32_t)*dstep;
+  const long long n = cnt->n;
+  const int b = face_off[q], count = face_off[q + 1] - b;
+  int side, k;
+  face_of(f, q, side, k);
+  const double R = gasR(sp);
+  const double st = sqrt(f.RT);
+  const double nxs = side == 0 ? 1.0 : (side == 1 ? -1.0 : 0.0);
+  const double nys = side == 2 ? 1.0 : (side == 3 ? -1.0 : 0.0);
+  uint32_t fl = 0;
+  unsigned long long nhit = 0, nout = 0;
+  for (int m = lane; m < count; m += 32) {
+    const uint32_t id = cnt->pid0 + (uint32_t)(b + m);
+    const U4 a = philox4x32_10(id, step, PTAG_INFLOW_P, 0u, k0, k1);
+    const U4 bb = philox4x32_10(id, step, PTAG_INFLOW_T, 0u, k0, k1);
+    const double u_pos = (double)uniform_open<T>(a.x), u_t = (double)uniform_open<T>(a.y);
+    double g1, g2;
+    box_muller((double)uniform_open<T>(bb.x), (double)uniform_open<T>(bb.y), g1, g2);
+    const double vn = inflow_speed<T>(f.RT, f.u_n[side], id, step, k0, k1, fl);
+    double px, py, vx, vy;
+    if (side < 2) {
+      px = side == 0 ? g.x0 : g.x1;
+      py = g.y0 + (k + u_pos) * g.dy;
+      vx = vn * nxs;
+      vy = st * g1;
+    } else {
+      px = g.x0 + (k + u_pos) * g.dx;
+      py = side == 2 ? g.y0 : g.y1;
+      vx = f.U + st * g1;
+      vy = vn * nys;
+    }
+    const double vz = st * g2;
+    const double e = -f.RT * log((double)uniform_open<T>(a.z));
+    const int l0 = (int)floor(-log((double)uniform_open<T>(a.w)) * f.T / sp.theta_v);
+    (void)R;
+    T X = (T)px, Y = (T)py, VX = (T)vx, VY = (T)vy, VZ = (T)vz, E = (T)e;
+    int L = l0, hits = 0;
+    const bool keep = plane_fly<T>(g, sp, id, step, k0, k1, (T)(u_t * g.dt), X, Y, VX, VY, VZ,
+                                   E, L, hits, fl);
+    nhit += hits;
+    nout += keep ? 0 : 1;
+    const long long j = n + b + m;
+    x[j] = X; y[j] = Y; cx[j] = VX; cy[j] = VY; cz[j] = VZ; er[j] = E; lev[j] = L; pid[j] = id;
+    keyout[j] = keep ? plane_cell(g, X, Y) : g.ncell;
+    idxout[j] = (int)j;
+  }
+  fl = __reduce_or_sync(0xffffffffu, fl);
+  nhit = wsum(nhit);
+  nout = wsum(nout);
+  if (lane == 0) {
+    if (fl) atomicOr(flags, fl);
+    if (nhit) atomicAdd(&counters[C_WALL_HITS], nhit);
+    if (nout) atomicAdd(&counters[C_OUTFLOW], nout);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort of (key, index) over the device count ntot, 8-bit
+// digits; histograms digit-major (bh[d * nblk + b])
+// ---------------------------------------------------------------------------
+__global__ void pl_hist(const int* __restrict__ key, const PlCount* __restrict__ cnt, int shift,
+                        int* __restrict__ bh, int nblk) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const long long n = cnt->ntot;
+  const long long b = (long long)blockIdx.x * kChunk;
+  if (b < n) {
+    for (int r = 0; r < kRPT; ++r) {
+      const long long i = b + (long long)r * kRB + threadIdx.x;
+      if (i < n) atomicAdd(&h[(key[i] >> shift) & 255], 1);
+    }
+  }
+  __syncthreads();
+  bh[(size_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// one block per digit: exclusive scan over the blocks, digit total
+__global__ void pl_scan_digits(int* __restrict__ bh, int nblk, int* __restrict__ tot) {
+  __shared__ int ws[8];
+  __shared__ int carry;
+  const int d = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int* row = bh + (size_t)d * nblk;
+  if (t == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nblk; b0 += kRB) {
+    const int b = b0 + t;
+    const int c = b < nblk ? row[b] : 0;
+    int v = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane == 31) ws[w] = v;
+    __syncthreads();
+    int pre = 0;
+    for (int k = 0; k < w; ++k) pre += ws[k];
+    if (b < nblk) row[b] = carry + pre + v - c;
+    __syncthreads();
+    if (t == 0) {
+      int s = 0;
+      for (int k = 0; k < kRB / 32; ++k) s += ws[k];
+      carry += s;
+    }
+    __syncthreads();
+  }
+  if (t == 0) tot[d] = carry;
+}
+
+__global__ void pl_scatter(const int* __restrict__ kin, const int* __restrict__ iin,
+                           int* __restrict__ kout, int* __restrict__ iout,
+                           const PlCount* __restrict__ cnt, int shift, const int* __restrict__ bh,
+                           const int* __restrict__ tot, int nblk) {
+  __shared__ int cntw[kRB / 32][256];
+  __shared__ int run[256];
+  __shared__ int base[256];
+  const int t = threadIdx.x, w = t >> 5;
+  const long long n = cnt->ntot;
+  const long long b = (long long)blockIdx.x * kChunk;
+  if (b >= n) return;
+  // exclusive scan of the digit totals
+  base[t] = tot[t];
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    const int v = t >= o ? base[t - o] : 0;
+    __syncthreads();
+    base[t] += v;
+    __syncthreads();
+  }
+  run[t] = (base[t] - tot[t]) + bh[(size_t)t * nblk + blockIdx.x];
+  __syncthreads();
+  for (int r = 0; r < kRPT; ++r) {
+    for (int q = 0; q < kRB / 32; ++q) cntw[q][t] = 0;
+    __syncthreads();
+    const long long i = b + (long long)r * kRB + t;
+    const bool valid = i < n;
+    const int kk = valid ? kin[i] : 0;
+    const int d = valid ? ((kk >> shift) & 255) : 256;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(peers & lane_lt());
+    if (valid && rank == 0) cntw[w][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      int pre = 0;
+      for (int q = 0; q < w; ++q) pre += cntw[q][d];
+      const int pos = run[d] + pre + rank;
+      kout[pos] = kk;
+      iout[pos] = iin[i];
+    }
+    __syncthreads();
+    int s = 0;
+    for (int q = 0; q < kRB / 32; ++q) s += cntw[q][t];
+    run[t] += s;
+    __syncthreads();
+  }
+}
+
+// cell segment starts from the sorted keys (keys in [0, ncell], ncell =
+// removed particles)
+__global__ void pl_offsets(const PlCount* __restrict__ cnt, int ncell,
+                           const int* __restrict__ key, long long* __restrict__ off) {
+  const long long n = cnt->ntot;
+  const long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n == 0) {
+    for (long long c = j0; c <= ncell; c += grid_threads()) off[c] = 0;
+    return;
+  }
+  for (long long j = j0; j < n; j += grid_threads()) {
+    const int k = key[j];
+    const int prev = j > 0 ? key[j - 1] : -1;
+    for (int c = prev + 1; c <= k; ++c) off[c] = j;
+    if (j == n - 1)
+      for (int c = k + 1; c <= ncell; ++c) off[c] = n;
+  }
+}
+
+template <typename T>
+__global__ void pl_gather(PlCount* __restrict__ cnt, int ncell,
+                          const long long* __restrict__ off, const int* __restrict__ idx,
+                          const int* __restrict__ ksorted, const T* __restrict__ x0,
+                          const T* __restrict__ y0, const T* __restrict__ vx0,
+                          const T* __restrict__ vy0, const T* __restrict__ vz0,
+                          const T* __restrict__ e0, const int* __restrict__ l0,
+                          const uint32_t* __restrict__ p0, T* __restrict__ x1,
+                          T* __restrict__ y1, T* __restrict__ vx1, T* __restrict__ vy1,
+                          T* __restrict__ vz1, T* __restrict__ e1, int* __restrict__ l1,
+                          uint32_t* __restrict__ p1, int* __restrict__ keycell) {
+  const long long n = off[ncell];
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += grid_threads()) {
+    const int s = idx[j];
+    x1[j] = x0[s]; y1[j] = y0[s]; vx1[j] = vx0[s]; vy1[j] = vy0[s]; vz1[j] = vz0[s];
+    e1[j] = e0[s]; l1[j] = l0[s]; p1[j] = p0[s];
+    keycell[j] = ksorted[j];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) cnt->n = n;
+}
+
+// ---------------------------------------------------------------------------
+// reconstruction stencils (Sec. 3.B on the uniform grid): for each side of
+// the centroid the x and y neighbour used (that side's if usable, else the
+// opposite one, else none) and the quadrant's diagonal when usable
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict__ cells,
+                          PlParams<T>* __restrict__ prm, Species sp) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const ChCellT<double>& cs = cells[c];
+  PlParams<T> P;
+  P.active = cs.active;
+  P.pad = 0;
+  P.alpha = (T)cs.alpha; P.nu_ref = (T)cs.nu_ref; P.B = (T)cs.B; P.mu_p = (T)cs.mu_p;
+  P.Pr = (T)cs.Pr; P.gtr = (T)cs.gtr; P.gtv = (T)cs.gtv; P.grv = (T)cs.grv;
+  P.R = (T)gasR(sp); P.theta = (T)sp.theta_v; P.dt = (T)g.dt;
+  const int i = c % g.nx, j = c / g.nx;
+  P.xc = (T)(g.x0 + (i + 0.5) * g.dx);
+  P.yc = (T)(g.y0 + (j + 0.5) * g.dy);
+  double f[kNF];
+  cell_fields(cs, f);
+  for (int k = 0; k < kNF; ++k) P.F[k] = (T)f[k];
+  auto usable = [&](int ii, int jj) {
+    return recon && ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && cells[jj * g.nx + ii].usable;
+  };
+  int ix[2], jy[2];
+  for (int s = 0; s < 2; ++s) {
+    const int sg = s ? 1 : -1;
+    ix[s] = usable(i + sg, j) ? i + sg : (usable(i - sg, j) ? i - sg : -1);
+    jy[s] = usable(i, j + sg) ? j + sg : (usable(i, j - sg) ? j - sg : -1);
+    P.xcell[s] = ix[s] >= 0 ? j * g.nx + ix[s] : -1;
+    P.ycell[s] = jy[s] >= 0 ? jy[s] * g.nx + i : -1;
+    P.hx[s] = ix[s] >= 0 ? (T)((ix[s] - i) * g.dx) : T(1);
+    P.hy[s] = jy[s] >= 0 ? (T)((jy[s] - j) * g.dy) : T(1);
+  }
+  for (int q = 0; q < 4; ++q) {
+    const int sx = q & 1, sy = q >> 1;
+    const bool d = ix[sx] >= 0 && jy[sy] >= 0 && usable(ix[sx], jy[sy]);
+    P.dcell[q] = d ? jy[sy] * g.nx + ix[sx] : -1;
+    P.hxy[q] = d ? (T)((double)((ix[sx] - i) * (jy[sy] - j)) * g.dx * g.dy) : T(1);
+  }
+  prm[c] = P;
+}
+
+// per particle: the bilinear polynomial of its quadrant, then the collision
+// of Sec. 4.D; one warp per cell, per-cell sums for the conservation step
+template <typename T>
+__global__ void pl_collide(int ncell, const ChCellT<double>* __restrict__ cells,
+                           const PlParams<T>* __restrict__ prm, const T* __restrict__ x,
+                           const T* __restrict__ y, T* __restrict__ cx, T* __restrict__ cy,
+                           T* __restrict__ cz, T* __restrict__ er, int* __restrict__ lev,
+                           const uint32_t* __restrict__ pid, ChSumsT<double>* __restrict__ sums,
+                           const long long* __restrict__ dstep, uint32_t k0, uint32_t k1,
+                           uint32_t* flags, unsigned long long* counters) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= ncell) return;
+  const ChCellT<double>& cs = cells[c];
+  if (!cs.active) return;
+  const PlParams<T>& P = prm[c];
+  const uint32_t step = (uint32_t)*dstep;
+  const T Uc0 = (T)cs.U[0], Uc1 = (T)cs.U[1], Uc2 = (T)cs.U[2];
+  T acc[10];
+  for (int i = 0; i < 10; ++i) acc[i] = T(0);
+  double accI = 0.0;
+  int maxI = 0;
+  CollideTally tl = {0u, 0ull, 0ull, 0ull, 0ull};
+  unsigned long long nfb = 0;
+  for (long long j = cs.off + lane; j < cs.off + cs.N; j += 32) {
+    const T ddx = x[j] - P.xc, ddy = y[j] - P.yc;
+    const int sx = ddx >= T(0) ? 1 : 0, sy = ddy >= T(0) ? 1 : 0;
+    const int xc = P.xcell[sx], yc = P.ycell[sy], dc = P.dcell[sy * 2 + sx];
+    T f[kNF];
+#pragma unroll
+    for (int i = 0; i < kNF; ++i) {
+      const T p0 = P.F[i];
+      T v = p0, px = T(0), py = T(0);
+      if (xc >= 0) {
+        px = prm[xc].F[i];
+        v += (px - p0) * ddx / P.hx[sx];
+      }
+      if (yc >= 0) {
+        py = prm[yc].F[i];
+        v += (py - p0) * ddy / P.hy[sy];
+      }
+      if (dc >= 0) v += (prm[dc].F[i] - px - py + p0) * ddx * ddy / P.hxy[sy * 2 + sx];
+      f[i] = v;
+    }
+    if (!(f[3] > T(0)) || !(f[4] > T(0)) || !(f[5] >= T(0))) {
+#pragma unroll
+      for (int i = 0; i < kNF; ++i) f[i] = P.F[i];
+      ++nfb;
+    }
+    T v0 = cx[j], v1 = cy[j], v2 = cz[j], en = er[j];
+    const int ln = collide_particle_t(P, f, v0, v1, v2, en, lev[j], pid[j], step, k0, k1, tl);
+    cx[j] = v0; cy[j] = v1; cz[j] = v2; er[j] = en;
+    lev[j] = ln;
+    maxI = max(maxI, ln);
+    const T d0 = v0 - Uc0, d1 = v1 - Uc1, d2 = v2 - Uc2;
+    acc[0] += d0; acc[1] += d1; acc[2] += d2;
+    acc[3] += d0 * d0; acc[4] += d1 * d1; acc[5] += d2 * d2;
+    acc[6] += d0 * d1; acc[7] += d0 * d2; acc[8] += d1 * d2;
+    acc[9] += en;
+    accI += (double)ln;
+  }
+  double s[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) s[i] = (double)wsum(acc[i]);
+  const double sI = wsum(accI);
+  const unsigned long long fix = wsum(tl.nfix), fb = wsum(nfb), ncl2 = wsum(tl.ncl),
+                           pb = wsum(tl.npb), nz = wsum(tl.nnz);
+  const int mI = __reduce_max_sync(0xffffffffu, maxI);
+  const uint32_t fla = __reduce_or_sync(0xffffffffu, tl.fl);
+  if (lane != 0) return;
+  ChSumsT<double>& sm = sums[c];
+  for (int i = 0; i < 10; ++i) sm.v[i] = s[i];
+  sm.I = (unsigned long long)(long long)llrint(sI);
+  sm.net = 0;
+  sm.maxI = mI;
+  if (fla) atomicOr(flags, fla);
+  if (fix) atomicAdd(&counters[C_CHOL_FIX], fix);
+  if (fb) atomicAdd(&counters[C_INTERP_FALLBACK], fb);
+  if (ncl2) atomicAdd(&counters[C_TREL_CLAMP], ncl2);
+  if (pb) atomicAdd(&counters[C_PB_CLAMP], pb);
+  if (nz) atomicAdd(&counters[C_NU_ZERO], nz);
+}
+
+// time-average sums of the post-step state, binned by cell
+template <typename T>
+__global__ void pl_sample(const PlCount* __restrict__ cnt, int ncell,
+                          const int* __restrict__ keycell,
+                          const ChCellT<double>* __restrict__ cells, const T* __restrict__ cx,
+                          const T* __restrict__ cy, const T* __restrict__ cz,
+                          const T* __restrict__ er, const int* __restrict__ lev,
+                          double* __restrict__ acc) {
+  const long long n = cnt->n;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&acc[(size_t)ncell * kNAcc], 1.0);
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += grid_threads()) {
+    const int k = keycell[j];
+    const ChCellT<double>& cc = cells[k];
+    const double v0 = cc.Un[0] + cc.s * ((double)cx[j] - cc.Us[0]);
+    const double v1 = cc.Un[1] + cc.s * ((double)cy[j] - cc.Us[1]);
+    const double v2 = cc.Un[2] + cc.s * ((double)cz[j] - cc.Us[2]);
+    const double e = cc.r * (double)er[j];
+    double* a = acc + (size_t)k * kNAcc;
+    atomicAdd(&a[0], 1.0);
+    atomicAdd(&a[1], v0); atomicAdd(&a[2], v1); atomicAdd(&a[3], v2);
+    atomicAdd(&a[4], v0 * v0); atomicAdd(&a[5], v1 * v1); atomicAdd(&a[6], v2 * v2);
+    atomicAdd(&a[7], v0 * v1); atomicAdd(&a[8], v0 * v2); atomicAdd(&a[9], v1 * v2);
+    atomicAdd(&a[10], e);
+    atomicAdd(&a[11], (double)lev[j]);
+  }
+}
+
+// on-demand moments of the current state: pass 0 raw sums, pass 1 central
+template <typename T>
+__global__ void pl_mom_pass(int pass, const PlCount* __restrict__ cnt,
+                            const int* __restrict__ keycell,
+                            const ChCellT<double>* __restrict__ cells, const T* __restrict__ cx,
+                            const T* __restrict__ cy, const T* __restrict__ cz,
+                            const T* __restrict__ er, const int* __restrict__ lev,
+                            double* __restrict__ a) {
+  const long long n = cnt->n;
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += grid_threads()) {
+    const int k = keycell[j];
+    const ChCellT<double>& cc = cells[k];
+    const double v0 = cc.Un[0] + cc.s * ((double)cx[j] - cc.Us[0]);
+    const double v1 = cc.Un[1] + cc.s * ((double)cy[j] - cc.Us[1]);
+    const double v2 = cc.Un[2] + cc.s * ((double)cz[j] - cc.Us[2]);
+    const double ep = cc.r * (double)er[j];
+    const double li = (double)lev[j];
+    double* A = a + (size_t)k * 21;
+    if (pass == 0) {
+      atomicAdd(&A[0], 1.0);
+      atomicAdd(&A[1], v0); atomicAdd(&A[2], v1); atomicAdd(&A[3], v2);
+      atomicAdd(&A[4], ep); atomicAdd(&A[5], li);
+      continue;
+    }
+    const double N = A[0];
+    const double C0 = v0 - A[1] / N, C1 = v1 - A[2] / N, C2 = v2 - A[3] / N;
+    const double q = 0.5 * (C0 * C0 + C1 * C1 + C2 * C2);
+    atomicAdd(&A[6], C0 * C0); atomicAdd(&A[7], C1 * C1); atomicAdd(&A[8], C2 * C2);
+    atomicAdd(&A[9], C0 * C1); atomicAdd(&A[10], C0 * C2); atomicAdd(&A[11], C1 * C2);
+    atomicAdd(&A[12], q * C0); atomicAdd(&A[13], q * C1); atomicAdd(&A[14], q * C2);
+    atomicAdd(&A[15], C0 * ep); atomicAdd(&A[16], C1 * ep); atomicAdd(&A[17], C2 * ep);
+    atomicAdd(&A[18], C0 * li); atomicAdd(&A[19], C1 * li); atomicAdd(&A[20], C2 * li);
+  }
+}
+
+template <typename T>
+__global__ void pl_to_host_layout(long long n, const int* __restrict__ keycell,
+                                  const ChCellT<double>* __restrict__ cells,
+                                  const T* __restrict__ x, const T* __restrict__ y,
+                                  const T* __restrict__ cx, const T* __restrict__ cy,
+                                  const T* __restrict__ cz, const T* __restrict__ er,
+                                  double* __restrict__ out) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const ChCellT<double>& cc = cells[keycell[j]];
+  out[j] = (double)x[j];
+  out[n + j] = (double)y[j];
+  out[2 * n + j] = cc.Un[0] + cc.s * ((double)cx[j] - cc.Us[0]);
+  out[3 * n + j] = cc.Un[1] + cc.s * ((double)cy[j] - cc.Us[1]);
+  out[4 * n + j] = cc.Un[2] + cc.s * ((double)cz[j] - cc.Us[2]);
+  out[5 * n + j] = cc.r * (double)er[j];
+}
+
+template <typename T>
+__global__ void pl_from_host_layout(long long n, const double* __restrict__ in,
+                                    T* __restrict__ x, T* __restrict__ y, T* __restrict__ cx,
+                                    T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  x[j] = (T)in[j]; y[j] = (T)in[n + j]; cx[j] = (T)in[2 * n + j]; cy[j] = (T)in[3 * n + j];
+  cz[j] = (T)in[4 * n + j]; er[j] = (T)in[5 * n + j];
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side
+// ===========================================================================
+struct PlaneCtx {
+  PlGeom g;
+  PlInflow inf;
+  int recon, passes, nblk, grid_p;
+  double Fnum, vol;
+  long long cap;
+  size_t es;
+  void* st[2][6];           // x, y, cx, cy, cz, eps (ping-pong)
+  int* lv[2];
+  uint32_t* pd[2];
+  int cur;
+  int* kbuf[2];
+  int* ibuf[2];
+  int* keycell;
+  int* bh;
+  int* tot;
+  int* face_off;
+  long long* off;
+  double* af;
+  PlCount* cnt;
+  ChCellT<double>* cells;
+  void* prm;                // PlParams<T>
+  ChSumsT<double>* sums;
+  double* acc;
+  double* macc;
+  double* mout;
+  long long* dstep;
+  int sampling;
+};
+
+namespace {
+
+#define CHK(x)                                 \
+  do {                                         \
+    if ((x) != cudaSuccess) return USP_ECUDA;  \
+  } while (0)
+
+double inflow_flux(double n, double RT, double u_n) {
+  // one-way number flux of a drifting Maxwellian through a surface element
+  const double s = u_n / std::sqrt(2.0 * RT);
+  return n * std::sqrt(RT / (2.0 * kPi)) * (std::exp(-s * s) + std::sqrt(kPi) * s * (1.0 + std::erf(s)));
+}
+
+template <typename T>
+int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
+  cudaStream_t s = env.stream;
+  const int a = h->cur, b = a ^ 1;
+  T* x = (T*)h->st[a][0]; T* y = (T*)h->st[a][1]; T* cx = (T*)h->st[a][2];
+  T* cy = (T*)h->st[a][3]; T* cz = (T*)h->st[a][4]; T* er = (T*)h->st[a][5];
+  const int ncell = h->g.ncell;
+  if (prof) prof(env.owner, 0, 1);
+  pl_advect<T><<<h->grid_p, kBlk, 0, s>>>(h->g, h->cnt, h->keycell, h->cells, x, y, cx, cy, cz,
+                                         er, h->lv[a], h->pd[a], h->kbuf[0], h->ibuf[0],
+                                         h->dstep, env.sp, env.k0, env.k1, env.flags,
+                                         env.counters);
+  pl_inflow<<<1, 1024, 0, s>>>(h->inf, h->cnt, h->face_off, h->cap, h->dstep, env.k0, env.k1,
+                               env.flags, env.counters);
+  if (h->inf.nfaces > 0)
+    pl_inject<T><<<(h->inf.nfaces * 32 + kBlk - 1) / kBlk, kBlk, 0, s>>>(
+        h->g, h->inf, h->cnt, h->face_off, x, y, cx, cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0],
+        h->ibuf[0], h->dstep, env.sp, env.k0, env.k1, env.flags, env.counters);
+  CHK(cudaGetLastError());
+  int src = 0;
+  for (int p = 0; p < h->passes; ++p) {
+    pl_hist<<<h->nblk, kRB, 0, s>>>(h->kbuf[src], h->cnt, 8 * p, h->bh, h->nblk);
+    pl_scan_digits<<<256, kRB, 0, s>>>(h->bh, h->nblk, h->tot);
+    pl_scatter<<<h->nblk, kRB, 0, s>>>(h->kbuf[src], h->ibuf[src], h->kbuf[src ^ 1],
+                                       h->ibuf[src ^ 1], h->cnt, 8 * p, h->bh, h->tot, h->nblk);
+    CHK(cudaGetLastError());
+    src ^= 1;
+  }
+  pl_offsets<<<h->grid_p, kBlk, 0, s>>>(h->cnt, ncell, h->kbuf[src], h->off);
+  pl_gather<T><<<h->grid_p, kBlk, 0, s>>>(h->cnt, ncell, h->off, h->ibuf[src], h->kbuf[src], x, y,
+                                          cx, cy, cz, er, h->lv[a], h->pd[a], (T*)h->st[b][0],
+                                          (T*)h->st[b][1], (T*)h->st[b][2], (T*)h->st[b][3],
+                                          (T*)h->st[b][4], (T*)h->st[b][5], h->lv[b], h->pd[b],
+                                          h->keycell);
+  CHK(cudaGetLastError());
+  h->cur = b;
+  x = (T*)h->st[b][0]; y = (T*)h->st[b][1]; cx = (T*)h->st[b][2]; cy = (T*)h->st[b][3];
+  cz = (T*)h->st[b][4]; er = (T*)h->st[b][5];
+  if (prof) prof(env.owner, 0, 0);
+  if (prof) prof(env.owner, 1, 1);
+  const int wb = (int)(((long long)ncell * 32 + 127) / 128);
+  const int cb = (ncell + 127) / 128;
+  ch_moments<T, double><<<wb, 128, 0, s>>>(ncell, h->off, h->af, cx, cy, cz, er, h->lv[b],
+                                           h->cells, env.sp, env.counters);
+  ch_coeffs<double><<<cb, 128, 0, s>>>(ncell, h->Fnum, h->vol, h->af, h->g.dt, h->cells, env.sp,
+                                       env.sp.omega, env.sp.Z_rot, env.flags, env.counters);
+  pl_params<T><<<cb, 128, 0, s>>>(h->g, h->recon, h->cells, (PlParams<T>*)h->prm, env.sp);
+  CHK(cudaGetLastError());
+  if (prof) prof(env.owner, 1, 0);
+  if (prof) prof(env.owner, 0, 1);
+  pl_collide<T><<<wb, 128, 0, s>>>(ncell, h->cells, (const PlParams<T>*)h->prm, x, y, cx, cy, cz,
+                                   er, h->lv[b], h->pd[b], h->sums, h->dstep, env.k0, env.k1,
+                                   env.flags, env.counters);
+  CHK(cudaGetLastError());
+  if (prof) prof(env.owner, 0, 0);
+  if (prof) prof(env.owner, 1, 1);
+  ch_levelfix<double><<<wb, 128, 0, s>>>(ncell, h->cells, h->sums, h->lv[b], h->dstep, env.sp,
+                                         env.k0, env.k1, env.flags, env.counters);
+  ch_update<double><<<cb, 128, 0, s>>>(ncell, h->cells, h->sums, h->dstep, env.sp, env.flags,
+                                       env.counters);
+  CHK(cudaGetLastError());
+  if (h->sampling) {
+    pl_sample<T><<<h->grid_p, kBlk, 0, s>>>(h->cnt, ncell, h->keycell, h->cells, cx, cy, cz, er,
+                                            h->lv[b], h->acc);
+    CHK(cudaGetLastError());
+  }
+  if (prof) prof(env.owner, 1, 0);
+  return USP_OK;
+}
+
+}  // namespace
+
+int pl_kernels_per_step(const PlaneCtx* h) {
+  return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 2 + 3 + 1 + 2 +
+         (h->sampling ? 1 : 0);
+}
+
+int pl_launch_step(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
+  if (env.precision == USP_FP32) return pl_step_t<float>(h, env, prof);
+  if (env.precision == USP_FP64) return pl_step_t<double>(h, env, prof);
+  return USP_ENOTSUP;
+}
+
+int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
+              const double* area_frac, int64_t n, int64_t cap, int64_t step0, const double* x,
+              const double* y, const double* cx, const double* cy, const double* cz,
+              const double* erot, const int32_t* lev, const uint32_t* pid) {
+  if (!pp || pp->nx <= 0 || pp->ny <= 0 || (long long)pp->nx * pp->ny >= (1 << 24) ||
+      !(pp->x1 > pp->x0) || !(pp->y1 > pp->y0) || !(pp->F_num > 0) || !(pp->depth > 0) ||
+      !(dt > 0) || n < 0 || cap < n || cap < 1 || cap > 0x7fffffffll)
+    return USP_EINVAL;
+  if (env.precision != USP_FP32 && env.precision != USP_FP64) return USP_ENOTSUP;
+  for (int k = 0; k < 4; ++k) {
+    if (pp->bc[k] < USP_BC_OPEN || pp->bc[k] > USP_BC_DIFFUSE) return USP_EINVAL;
+    if (pp->inflow[k] && pp->bc[k] != USP_BC_OPEN) return USP_EINVAL;
+  }
+  const bool any_inflow = pp->inflow[0] || pp->inflow[1] || pp->inflow[2] || pp->inflow[3];
+  if (any_inflow && !(pp->n_inf > 0 && pp->T_inf > 0)) return USP_EINVAL;
+  if ((pp->cyl_r > 0 || pp->bc[0] == USP_BC_DIFFUSE || pp->bc[1] == USP_BC_DIFFUSE ||
+       pp->bc[2] == USP_BC_DIFFUSE || pp->bc[3] == USP_BC_DIFFUSE) && !(pp->T_wall > 0))
+    return USP_EINVAL;
+  if (n > 0 && (!x || !y || !cx || !cy || !cz || !erot || !lev)) return USP_EINVAL;
+  if (!area_frac) return USP_EINVAL;
+  const int ncell = pp->nx * pp->ny;
+  for (int c = 0; c < ncell; ++c)
+    if (!(area_frac[c] >= 0.0 && area_frac[c] <= 1.0)) return USP_EINVAL;
+  for (int64_t j = 0; j < n; ++j)
+    if (!(x[j] >= pp->x0 && x[j] <= pp->x1 && y[j] >= pp->y0 && y[j] <= pp->y1) || lev[j] < 0)
+      return USP_EINVAL;
+  PlaneCtx* h = new PlaneCtx();
+  std::memset((void*)h, 0, sizeof(PlaneCtx));
+  PlGeom& g = h->g;
+  g.nx = pp->nx; g.ny = pp->ny; g.ncell = ncell;
+  g.x0 = pp->x0; g.x1 = pp->x1; g.y0 = pp->y0; g.y1 = pp->y1;
+  g.dx = (pp->x1 - pp->x0) / pp->nx; g.dy = (pp->y1 - pp->y0) / pp->ny;
+  g.cxc = pp->cyl_xc; g.cyc = pp->cyl_yc; g.cr = pp->cyl_r > 0 ? pp->cyl_r : 0.0;
+  g.Tw = pp->T_wall; g.dt = dt;
+  for (int k = 0; k < 4; ++k) g.bc[k] = pp->bc[k];
+  h->recon = pp->reconstruct ? 1 : 0;
+  h->Fnum = pp->F_num;
+  h->vol = g.dx * g.dy * pp->depth;
+  h->cap = cap;
+  // inflow faces, sides in the order left, right, bottom, top
+  PlInflow& f = h->inf;
+  const double R = env.sp.m > 0 ? kB / env.sp.m : 0.0;
+  f.RT = R * pp->T_inf; f.U = pp->U_inf; f.T = pp->T_inf;
+  f.nfaces = 0;
+  for (int k = 0; k < 4; ++k) {
+    f.nf[k] = pp->inflow[k] ? (k < 2 ? pp->ny : pp->nx) : 0;
+    f.base[k] = f.nfaces;
+    f.nfaces += f.nf[k];
+    const double nxs = k == 0 ? 1.0 : (k == 1 ? -1.0 : 0.0);
+    f.u_n[k] = pp->U_inf * nxs;
+    f.expect[k] = 0.0;
+    if (pp->inflow[k]) {
+      const double flen = k < 2 ? g.dy : g.dx;
+      f.expect[k] = inflow_flux(pp->n_inf, f.RT, f.u_n[k]) * flen * pp->depth * dt / pp->F_num;
+    }
+  }
+  h->es = env.precision == USP_FP32 ? 4 : 8;
+  int bits = 1;
+  while ((1 << bits) < ncell + 1) ++bits;
+  h->passes = (bits + 7) / 8;
+  h->nblk = (int)std::max<long long>(1, (cap + kChunk - 1) / kChunk);
+  h->grid_p = (int)std::min<long long>(std::max<long long>(1, (cap + kBlk - 1) / kBlk), 152 * 16);
+  auto A = [&](size_t bytes) { return env.alloc(env.owner, bytes); };
+  const size_t nn = (size_t)cap;
+  for (int k = 0; k < 2; ++k) {
+    for (int q = 0; q < 6; ++q) h->st[k][q] = A(nn * h->es);
+    h->lv[k] = (int*)A(nn * 4);
+    h->pd[k] = (uint32_t*)A(nn * 4);
+    h->kbuf[k] = (int*)A(nn * 4);
+    h->ibuf[k] = (int*)A(nn * 4);
+  }
+  h->keycell = (int*)A(nn * 4);
+  h->bh = (int*)A((size_t)h->nblk * 256 * 4);
+  h->tot = (int*)A(256 * 4);
+  h->face_off = (int*)A(sizeof(int) * (f.nfaces + 1));
+  h->off = (long long*)A(sizeof(long long) * (ncell + 1));
+  h->af = (double*)A(sizeof(double) * ncell);
+  h->cnt = (PlCount*)A(sizeof(PlCount));
+  h->cells = (ChCellT<double>*)A(sizeof(ChCellT<double>) * ncell);
+  h->prm = A((env.precision == USP_FP32 ? sizeof(PlParams<float>) : sizeof(PlParams<double>)) *
+             ncell);
+  h->sums = (ChSumsT<double>*)A(sizeof(ChSumsT<double>) * ncell);
+  const size_t acc_bytes = sizeof(double) * ((size_t)ncell * kNAcc + 2);
+  h->acc = (double*)A(acc_bytes);
+  h->macc = (double*)A(sizeof(double) * 21 * ncell);
+  h->mout = (double*)A(sizeof(double) * USP_NMOM * ncell);
+  h->dstep = (long long*)A(sizeof(long long));
+  bool ok = h->keycell && h->bh && h->tot && h->face_off && h->off && h->af && h->cnt &&
+            h->cells && h->prm && h->sums && h->acc && h->macc && h->mout && h->dstep;
+  for (int k = 0; k < 2; ++k) {
+    for (int q = 0; q < 6; ++q) ok = ok && h->st[k][q];
+    ok = ok && h->lv[k] && h->pd[k] && h->kbuf[k] && h->ibuf[k];
+  }
+  if (!ok) {
+    delete h;
+    return USP_ENOMEM;
+  }
+  cudaStream_t s = env.stream;
+  const size_t nh = (size_t)std::max<int64_t>(n, 1);
+  std::vector<double> hl(6 * nh, 0.0);
+  std::vector<int> key(nh, 0);
+  std::vector<uint32_t> hp(nh, 0);
+  uint32_t next = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    hl[j] = x[j]; hl[n + j] = y[j]; hl[2 * n + j] = cx[j]; hl[3 * n + j] = cy[j];
+    hl[4 * n + j] = cz[j]; hl[5 * n + j] = erot[j];
+    int i = (int)std::floor((x[j] - g.x0) / g.dx), jj = (int)std::floor((y[j] - g.y0) / g.dy);
+    i = std::min(std::max(i, 0), g.nx - 1);
+    jj = std::min(std::max(jj, 0), g.ny - 1);
+    key[j] = jj * g.nx + i;
+    hp[j] = pid ? pid[j] : (uint32_t)j;
+    next = std::max(next, hp[j] + 1u);
+  }
+  PlCount c0;
+  c0.n = n; c0.ntot = n; c0.ninj = 0; c0.pid0 = next; c0.next_pid = next;
+  std::vector<ChCellT<double>> hc(ncell);
+  std::memset((void*)hc.data(), 0, sizeof(ChCellT<double>) * ncell);
+  for (auto& cc : hc) { cc.s = 1.0; cc.r = 1.0; }
+  void* tmp = n > 0 ? env.alloc(env.owner, 6 * nh * sizeof(double)) : nullptr;
+  if (n > 0 && !tmp) {
+    delete h;
+    return USP_ENOMEM;
+  }
+  const long long dstep0 = step0;
+  bool cok = true;
+  if (n > 0) {
+    cok = cok && cudaMemcpyAsync(h->lv[0], lev, n * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    cok = cok && cudaMemcpyAsync(h->pd[0], hp.data(), n * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    cok = cok && cudaMemcpyAsync(h->keycell, key.data(), n * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    cok = cok && cudaMemcpyAsync(tmp, hl.data(), 6 * n * sizeof(double), cudaMemcpyHostToDevice,
+                                 s) == cudaSuccess;
+    const int nb = (int)((n + 255) / 256);
+    if (env.precision == USP_FP32)
+      pl_from_host_layout<float><<<nb, 256, 0, s>>>(n, (const double*)tmp, (float*)h->st[0][0],
+          (float*)h->st[0][1], (float*)h->st[0][2], (float*)h->st[0][3], (float*)h->st[0][4],
+          (float*)h->st[0][5]);
+    else
+      pl_from_host_layout<double><<<nb, 256, 0, s>>>(n, (const double*)tmp, (double*)h->st[0][0],
+          (double*)h->st[0][1], (double*)h->st[0][2], (double*)h->st[0][3], (double*)h->st[0][4],
+          (double*)h->st[0][5]);
+    cok = cok && cudaGetLastError() == cudaSuccess;
+  }
+  cok = cok && cudaMemcpyAsync(h->af, area_frac, sizeof(double) * ncell, cudaMemcpyHostToDevice,
+                               s) == cudaSuccess;
+  cok = cok && cudaMemcpyAsync(h->cnt, &c0, sizeof(PlCount), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  cok = cok && cudaMemcpyAsync(h->cells, hc.data(), sizeof(ChCellT<double>) * ncell,
+                               cudaMemcpyHostToDevice, s) == cudaSuccess;
+  cok = cok && cudaMemsetAsync(h->sums, 0, sizeof(ChSumsT<double>) * ncell, s) == cudaSuccess;
+  cok = cok && cudaMemsetAsync(h->acc, 0, acc_bytes, s) == cudaSuccess;
+  cok = cok && cudaMemcpyAsync(h->dstep, &dstep0, sizeof(long long), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  cok = cok && cudaStreamSynchronize(s) == cudaSuccess;
+  if (tmp) env.release(env.owner, tmp);
+  if (!cok) {
+    delete h;
+    return USP_ECUDA;
+  }
+  *out = h;
+  return USP_OK;
+}
+
+int pl_sample(PlaneCtx* h, int on) {
+  h->sampling = on ? 1 : 0;
+  return USP_OK;
+}
+
+int pl_read(PlaneCtx* h, const ChEnv& env, double* h_acc, int reset) {
+  const size_t bytes = sizeof(double) * ((size_t)h->g.ncell * kNAcc + 2);
+  CHK(cudaMemcpyAsync(h_acc, h->acc, bytes, cudaMemcpyDeviceToHost, env.stream));
+  if (reset) CHK(cudaMemsetAsync(h->acc, 0, bytes, env.stream));
+  CHK(cudaStreamSynchronize(env.stream));
+  return USP_OK;
+}
+
+int pl_count(PlaneCtx* h, const ChEnv& env, int64_t* n, uint32_t* next_pid) {
+  PlCount c;
+  CHK(cudaMemcpyAsync(&c, h->cnt, sizeof(PlCount), cudaMemcpyDeviceToHost, env.stream));
+  CHK(cudaStreamSynchronize(env.stream));
+  if (n) *n = c.n;
+  if (next_pid) *next_pid = c.next_pid;
+  return USP_OK;
+}
+
+int pl_moments(PlaneCtx* h, const ChEnv& env, double* out, int out_is_device) {
+  cudaStream_t s = env.stream;
+  const int b = h->cur, ncell = h->g.ncell;
+  CHK(cudaMemsetAsync(h->macc, 0, sizeof(double) * 21 * ncell, s));
+  for (int pass = 0; pass < 2; ++pass) {
+    if (env.precision == USP_FP32)
+      pl_mom_pass<float><<<h->grid_p, kBlk, 0, s>>>(pass, h->cnt, h->keycell, h->cells,
+          (float*)h->st[b][2], (float*)h->st[b][3], (float*)h->st[b][4], (float*)h->st[b][5],
+          h->lv[b], h->macc);
+    else
+      pl_mom_pass<double><<<h->grid_p, kBlk, 0, s>>>(pass, h->cnt, h->keycell, h->cells,
+          (double*)h->st[b][2], (double*)h->st[b][3], (double*)h->st[b][4], (double*)h->st[b][5],
+          h->lv[b], h->macc);
+    CHK(cudaGetLastError());
+  }
+  ch_mom_out<<<(ncell + 127) / 128, 128, 0, s>>>(ncell, h->macc, h->mout, env.sp);
+  CHK(cudaGetLastError());
+  CHK(cudaMemcpyAsync(out, h->mout, sizeof(double) * USP_NMOM * ncell,
+                      out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!out_is_device) CHK(cudaStreamSynchronize(s));
+  return USP_OK;
+}
+
+int pl_get_particles(PlaneCtx* h, const ChEnv& env, int64_t cap, int64_t* n_out, double* x,
+                     double* y, double* cx, double* cy, double* cz, double* erot, int32_t* lev,
+                     uint32_t* pid) {
+  int64_t n = 0;
+  int rc = pl_count(h, env, &n, nullptr);
+  if (rc) return rc;
+  if (n_out) *n_out = n;
+  if (n > cap) return USP_EINVAL;
+  if (n == 0) return USP_OK;
+  cudaStream_t s = env.stream;
+  double* tmp = (double*)env.alloc(env.owner, 6 * n * sizeof(double));
+  if (!tmp) return USP_ENOMEM;
+  const int b = h->cur;
+  const int nb = (int)((n + 255) / 256);
+  if (env.precision == USP_FP32)
+    pl_to_host_layout<float><<<nb, 256, 0, s>>>(n, h->keycell, h->cells, (float*)h->st[b][0],
+        (float*)h->st[b][1], (float*)h->st[b][2], (float*)h->st[b][3], (float*)h->st[b][4],
+        (float*)h->st[b][5], tmp);
+  else
+    pl_to_host_layout<double><<<nb, 256, 0, s>>>(n, h->keycell, h->cells, (double*)h->st[b][0],
+        (double*)h->st[b][1], (double*)h->st[b][2], (double*)h->st[b][3], (double*)h->st[b][4],
+        (double*)h->st[b][5], tmp);
+  std::vector<double> hl(6 * n);
+  bool ok = cudaGetLastError() == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(hl.data(), tmp, 6 * n * sizeof(double), cudaMemcpyDeviceToHost, s) ==
+                 cudaSuccess;
+  if (lev) ok = ok && cudaMemcpyAsync(lev, h->lv[b], n * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  if (pid) ok = ok && cudaMemcpyAsync(pid, h->pd[b], n * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+  env.release(env.owner, tmp);
+  if (!ok) return USP_ECUDA;
+  for (int64_t j = 0; j < n; ++j) {
+    if (x) x[j] = hl[j];
+    if (y) y[j] = hl[n + j];
+    if (cx) cx[j] = hl[2 * n + j];
+    if (cy) cy[j] = hl[3 * n + j];
+    if (cz) cz[j] = hl[4 * n + j];
+    if (erot) erot[j] = hl[5 * n + j];
+  }
+  return USP_OK;
+}
+
+int pl_ncell(const PlaneCtx* h) { return h->g.ncell; }
+int pl_parity(const PlaneCtx* h) { return h->cur; }
+void pl_destroy(PlaneCtx* h) { delete h; }

@@ -1,0 +1,436 @@
+// usp_spatial.cuh -- pieces shared by the spatial paths (1D channel and 2D
+// plane) of the USP-FPM step: per-cell state, warp reductions, the
+// per-particle collision of Sec. 4.D with fields at the particle, and the
+// per-cell conservation kernels of Sec. 4.C.  Included by one translation
+// unit each; everything is internal to it.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "usp_device.cuh"
+#include "usp_dual.cuh"
+
+namespace {
+
+using namespace usp;
+
+constexpr int kNF = 13;            // U(3), T_tr, T_rot, T_vib, Pi(6)
+constexpr int kRB = 256;           // radix block
+constexpr int kRPT = 16;           // keys per thread per radix block
+constexpr int kChunk = kRB * kRPT;
+constexpr int kNAcc = 12;          // time-average sums per cell
+constexpr int kWallHitCap = 16;
+constexpr uint32_t PTAG_WALL_A = 2u, PTAG_WALL_B = 3u;
+
+// Per-cell state; S = double (plain forms) or a derivative number.  T_vib
+// comes from the mean level alone (levels carry no derivative).
+template <typename S>
+struct ChCellT {
+  S U[3], Pi[6];
+  S Ttr, Trot;
+  double Tvib, ebar, n;
+  S alpha, nu_ref, B, mu_p, Pr, gtr, gtv, grv;
+  S e_rot_tgt, e_vib_tgt;
+  S Un[3], Us[3], s, r;   // pending rescale: c = Un + s (c* - Us), eps = r eps*
+  long long off, N;
+  int active, maxI;
+  int usable, pad;   // usable as a reconstruction neighbour (plane path)
+};
+
+
+template <typename S>
+struct ChSumsT {
+  S v[10];
+  unsigned long long I;
+  long long net;
+  int maxI, pad;
+};
+
+__device__ __forceinline__ unsigned lane_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ D3 wsum(D3 v) {
+  v.v = wsum(v.v);
+  for (int k = 0; k < kND; ++k) v.d[k] = wsum(v.d[k]);
+  return v;
+}
+
+// e_vib in the working precision
+template <typename T>
+__device__ __forceinline__ T evib_t(const T& Rth, const T& theta, const T& Tv) {
+  return Tv > T(0) ? Rth / expm1(theta / Tv) : T(0);
+}
+
+
+// add a quantity to block 0 of an accumulator and, for derivative numbers,
+// its derivatives to blocks 1..3 (stride blk)
+__device__ __forceinline__ void acc_add(double* a, size_t, double q) { atomicAdd(a, q); }
+__device__ __forceinline__ void acc_add(double* a, size_t blk, const D3& q) {
+  atomicAdd(a, q.v);
+  for (int k = 0; k < kND; ++k) atomicAdd(a + (k + 1) * blk, q.d[k]);
+}
+
+
+template <typename T>
+__device__ __forceinline__ bool chol3_t(const T* M, T* L) {
+  if (!(M[0] > T(0))) return false;
+  const T l00 = sqrt(M[0]);
+  const T l10 = M[3] / l00, l20 = M[4] / l00;
+  const T d1 = M[1] - l10 * l10;
+  if (!(d1 > T(0))) return false;
+  const T l11 = sqrt(d1);
+  const T l21 = (M[5] - l20 * l10) / l11;
+  const T d2 = M[2] - l20 * l20 - l21 * l21;
+  if (!(d2 > T(0))) return false;
+  L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = sqrt(d2);
+  return true;
+}
+
+template <typename T, typename P_>
+__device__ __forceinline__ void relax_t(const P_& P, T alpha, const T* f, T& ttr, T& trot,
+                                        T& evr, bool& cl) {
+  const T oma2 = T(1) - alpha * alpha;
+  ttr = f[3] - (P.gtr * (f[3] - f[4]) + P.gtv * (f[3] - f[5])) / (oma2 * T(1.5) * P.R);
+  trot = f[4] + (P.gtr * (f[3] - f[4]) - P.grv * (f[4] - f[5])) / (oma2 * P.R);
+  evr = evib_t(P.R * P.theta, P.theta, f[5]) + (P.gtv * (f[3] - f[5]) + P.grv * (f[4] - f[5])) / oma2;
+  cl = false;
+  if (ttr < T(0)) { ttr = T(0); cl = true; }
+  if (trot < T(0)) { trot = T(0); cl = true; }
+  if (evr < T(0)) { evr = T(0); cl = true; }
+}
+
+
+// Counts kept per thread by the particle collision and reduced per warp.
+struct CollideTally {
+  uint32_t fl;
+  unsigned long long nfix, ncl, npb, nnz;
+};
+
+// One particle through the collision step of Sec. 4.D with the fields f at
+// its position (U(3), T_tr, T_rot, T_vib, Pi(6)) and the cell coefficients
+// of P: relaxation temperatures, M = tau D_tr and its Cholesky factor with
+// the Sec. 3.A.3 adjustment (four passes, then nu = 0 with alpha^2 = B),
+// Eqs. update_ci / update_erot / update_evib.  Returns the new level.
+template <typename T, typename P_>
+__device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx, T& vy, T& vz,
+                                                  T& e, int I, uint32_t id, uint32_t step,
+                                                  uint32_t k0, uint32_t k1, CollideTally& t) {
+  T alpha = P.alpha, nu = P.nu_ref, ttr, trot, evr;
+  bool cl;
+  relax_t(P, alpha, f, ttr, trot, evr, cl);
+  const T RT = P.R * f[3];
+  T M[6], L[6];
+  auto fill = [&](T nu_) {
+    M[0] = P.R * ttr + nu_ * (f[6] - RT);
+    M[1] = P.R * ttr + nu_ * (f[7] - RT);
+    M[2] = P.R * ttr + nu_ * (f[8] - RT);
+    M[3] = nu_ * f[9]; M[4] = nu_ * f[10]; M[5] = nu_ * f[11];
+  };
+  fill(nu);
+  if (!chol3_t(M, L)) {
+    ++t.nfix;
+    T lmin, lmax;
+    sym3_minmax(f + 6, lmin, lmax);
+    bool ok = false;
+    for (int pass = 0; pass < 4 && !ok; ++pass) {
+      nu = P.nu_ref;
+      if (P.nu_ref <= T(0)) {
+        if (lmax - RT > T(0)) nu = fmax(nu, -P.R * ttr / (lmax - RT));
+      } else {
+        if (RT - lmin > T(0)) nu = fmin(nu, P.R * ttr / (RT - lmin));
+      }
+      nu = nu * (T(1) - T(1e-6));
+      T a2 = (nu - P.B) / (nu - T(1));
+      a2 = fmin(fmax(a2, T(0)), T(1) - (sizeof(T) == 4 ? T(1e-7) : T(1e-12)));
+      const T ap = sqrt(a2), am = -ap;
+      const T prp = T(2) * P.mu_p * (T(1) - ap * ap * ap) / (P.dt * (T(1) + ap * ap * ap));
+      const T prm_ = T(2) * P.mu_p * (T(1) - am * am * am) / (P.dt * (T(1) + am * am * am));
+      alpha = (fabs(prm_ - P.Pr) < fabs(prp - P.Pr)) ? am : ap;
+      bool cl2;
+      relax_t(P, alpha, f, ttr, trot, evr, cl2);
+      cl = cl || cl2;
+      fill(nu);
+      ok = chol3_t(M, L);
+    }
+    if (!ok) {
+      // nu = 0 with alpha^2 = B, admissible whenever T_tr^rel > 0
+      ++t.nnz;
+      const T a2 = fmin(fmax(P.B, T(0)), T(1) - (sizeof(T) == 4 ? T(1e-7) : T(1e-12)));
+      const T ap = sqrt(a2), am = -ap;
+      const T prp = T(2) * P.mu_p * (T(1) - ap * ap * ap) / (P.dt * (T(1) + ap * ap * ap));
+      const T prm_ = T(2) * P.mu_p * (T(1) - am * am * am) / (P.dt * (T(1) + am * am * am));
+      alpha = (fabs(prm_ - P.Pr) < fabs(prp - P.Pr)) ? am : ap;
+      bool cl2;
+      relax_t(P, alpha, f, ttr, trot, evr, cl2);
+      cl = cl || cl2;
+      if (!(ttr > T(0))) t.fl |= F_CHOL_FAIL_AFTER_FIX;
+      const T sq = ttr > T(0) ? sqrt(P.R * ttr) : T(0);
+      L[0] = sq; L[1] = T(0); L[2] = sq; L[3] = T(0); L[4] = T(0); L[5] = sq;
+    }
+  }
+  if (cl) { t.fl |= F_TREL_CLAMP; ++t.ncl; }
+  // draws
+  const U4 w = philox4x32_10(id, step, PTAG_NORMALS, 0u, k0, k1);
+  T g0, g1, g2, g3;
+  box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
+  box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
+  const U4 w2 = philox4x32_10(id, step, PTAG_JUMPS, 0u, k0, k1);
+  // Eq. update_ci about the interpolated bulk velocity
+  const T a2 = alpha * alpha, sq = sqrt(T(1) - a2);
+  const T v0 = f[0] + alpha * (vx - f[0]) + sq * (L[0] * g0);
+  const T v1 = f[1] + alpha * (vy - f[1]) + sq * (L[1] * g0 + L[2] * g1);
+  const T v2 = f[2] + alpha * (vz - f[2]) + sq * (L[3] * g0 + L[4] * g1 + L[5] * g2);
+  vx = v0; vy = v1; vz = v2;
+  // Eq. update_erot
+  const T a = P.R * trot * (T(1) - a2) / T(2);
+  const T root = sqrt(e) * alpha + sqrt(a) * g3;
+  e = a + root * root;
+  // Eq. update_evib
+  const T eb = evr / (P.R * P.theta);
+  const T p_nb = T(1) / (T(1) + eb * (T(1) - a2));
+  const T p_b = (T(1) + eb) * (T(1) - a2);
+  uint32_t f1 = 0;
+  const int up = sample_nb<T>(I + 1, p_nb, uniform_open<T>(w2.x), f1);
+  const int dn = sample_b<T>(I, p_b, uniform_open<T>(w2.y), f1);
+  if (f1 & F_PB_CLAMP) ++t.npb;
+  t.fl |= f1;
+  return I + up - dn;
+}
+
+// vibrational +-1 correction (Sec. 4.C), one warp per cell; same acceptance
+// rule as the one-at-a-time loop (see the homogeneous path)
+template <typename S>
+__global__ void ch_levelfix(int ny, const ChCellT<S>* __restrict__ cells,
+                            ChSumsT<S>* __restrict__ sums,
+                            int* __restrict__ lev, const long long* __restrict__ dstep, Species sp,
+                            uint32_t k0, uint32_t k1, uint32_t* flags,
+                            unsigned long long* counters) {
+  const int lane = threadIdx.x & 31;
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (c >= ny) return;
+  const ChCellT<S>& cs = cells[c];
+  if (!cs.active) return;
+  const uint32_t step = (uint32_t)*dstep;
+  const double Rth = gasR(sp) * sp.theta_v;
+  const long long N = cs.N;
+  long long Id = 0;
+  if (lane == 0) {
+    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_IDELTA, 0u, k0, k1);
+    const double u = uniform_open<double>(w.x);
+    Id = (long long)floor((double)N * value(cs.e_vib_tgt) / Rth - (double)(long long)sums[c].I + u);
+  }
+  Id = __shfl_sync(0xffffffffu, Id, 0);
+  long long remaining = Id, draws = 0, net = 0;
+  const long long cap = 64 * N;
+  int* lv = lev + cs.off;
+  while (remaining != 0 && draws < cap) {
+    const long long j = draws + lane;
+    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_PICK, (uint32_t)(j >> 2), k0, k1);
+    const uint32_t word = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
+    const long long k = (long long)(((unsigned long long)word * (unsigned long long)N) >> 32);
+    const bool valid = j < cap;
+    bool accept;
+    if (remaining > 0) {
+      accept = valid;
+    } else {
+      const int cur = valid ? __ldcg(&lv[k]) : 0;
+      const unsigned grp = __match_any_sync(0xffffffffu, valid ? k : -1ll);
+      accept = valid && __popc(grp & lane_lt()) < cur;
+    }
+    const unsigned am = __ballot_sync(0xffffffffu, accept);
+    const long long need = remaining > 0 ? remaining : -remaining;
+    const int nacc = __popc(am);
+    const int take = (int)(nacc < need ? nacc : need);
+    const bool eff = accept && __popc(am & lane_lt()) < take;
+    __syncwarp();
+    if (eff) atomicAdd(&lv[k], remaining > 0 ? 1 : -1);
+    __syncwarp();
+    long long used = 32;
+    if (take == need && take > 0) {
+      unsigned m = am;
+      for (int i = 1; i < take; ++i) m &= m - 1;
+      used = __ffs((int)m);
+    }
+    if (draws + used > cap) used = cap - draws;
+    draws += used;
+    if (remaining > 0) { remaining -= take; net += take; }
+    else { remaining += take; net -= take; }
+  }
+  if (lane != 0) return;
+  if (remaining != 0) atomicOr(flags, (uint32_t)F_VIB_LOOP_CAP);
+  if (draws) atomicAdd(&counters[C_VIB_DRAWS], (unsigned long long)draws);
+  sums[c].net = net;
+}
+
+// rescale factors of Sec. 4.C, kept pending for the next move; the step
+// counter advances after the last reader of this step
+template <typename S>
+__global__ void ch_update(int ny, ChCellT<S>* __restrict__ cells,
+                          const ChSumsT<S>* __restrict__ sums, long long* dstep, Species sp,
+                          uint32_t* flags, unsigned long long* counters) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < ny) {
+    ChCellT<S>& cs = cells[c];
+    if (cs.active) {
+      const double R = gasR(sp), Rth = R * sp.theta_v;
+      const ChSumsT<S>& sm = sums[c];
+      const double invN = 1.0 / (double)cs.N;
+      const double sumI = (double)((long long)sm.I + sm.net);
+      const S er_star = sm.v[9] * invN;
+      const S r = er_star > 0.0 ? cs.e_rot_tgt / er_star : S(1.0);
+      const S e_rot_new = r * er_star;
+      const double e_vib_new = Rth * sumI * invN;
+      const S m0 = sm.v[0] * invN, m1 = sm.v[1] * invN, m2 = sm.v[2] * invN;
+      const S etr_star = 0.5 * (sm.v[3] * invN - m0 * m0 + sm.v[4] * invN - m1 * m1 +
+                                sm.v[5] * invN - m2 * m2);
+      const S e_tr_n = 0.5 * (cs.Pi[0] + cs.Pi[1] + cs.Pi[2]);
+      const S rad = (e_tr_n + R * cs.Trot + Rth * cs.ebar - e_rot_new - e_vib_new) / etr_star;
+      S Us[3] = {cs.U[0] + m0, cs.U[1] + m1, cs.U[2] + m2};
+      if (!(etr_star > 0.0) || !(rad > 0.0)) {
+        atomicOr(flags, (uint32_t)F_NEG_RADICAND);
+        atomicAdd(&counters[C_NEG_RADICAND], 1ull);
+        for (int i = 0; i < 3; ++i) { cs.Un[i] = Us[i]; cs.Us[i] = Us[i]; }
+        cs.s = S(1.0);
+      } else {
+        for (int i = 0; i < 3; ++i) { cs.Un[i] = cs.U[i]; cs.Us[i] = Us[i]; }
+        cs.s = sqrt(rad);
+      }
+      cs.r = r;
+      cs.maxI = sm.maxI + 1;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *dstep += 1;
+}
+
+
+// ---------------------------------------------------------------------------
+// per-cell moments and coefficients
+// ---------------------------------------------------------------------------
+template <typename T, typename S>
+__global__ void ch_moments(int ny, const long long* __restrict__ off, const double* __restrict__ af,
+                           const T* __restrict__ cx,
+                           const T* __restrict__ cy, const T* __restrict__ cz,
+                           const T* __restrict__ er, const int* __restrict__ lev,
+                           ChCellT<S>* __restrict__ cells, Species sp,
+                           unsigned long long* counters) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= ny) return;
+  const long long b = off[c], e = off[c + 1], N = e - b;
+  T a0 = T(0), a1 = T(0), a2 = T(0), ae = T(0);
+  double al = 0.0;
+  for (long long j = b + lane; j < e; j += 32) {
+    a0 += cx[j]; a1 += cy[j]; a2 += cz[j]; ae += er[j]; al += (double)lev[j];
+  }
+  const S s0 = S(wsum(a0)), s1 = S(wsum(a1)), s2 = S(wsum(a2)), se = S(wsum(ae));
+  const double sl = wsum(al);
+  const double inv = N > 0 ? 1.0 / (double)N : 0.0;
+  const T m0 = (T)(s0 * inv), m1 = (T)(s1 * inv), m2 = (T)(s2 * inv);
+  T p[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  for (long long j = b + lane; j < e; j += 32) {
+    const T C0 = cx[j] - m0, C1 = cy[j] - m1, C2 = cz[j] - m2;
+    p[0] += C0 * C0; p[1] += C1 * C1; p[2] += C2 * C2;
+    p[3] += C0 * C1; p[4] += C0 * C2; p[5] += C1 * C2;
+  }
+  S P[6];
+  for (int i = 0; i < 6; ++i) P[i] = S(wsum(p[i])) * inv;
+  if (lane != 0) return;
+  ChCellT<S>& cs = cells[c];
+  const double R = gasR(sp);
+  cs.off = b;
+  cs.N = N;
+  cs.active = N >= 2;
+  // a neighbour for the reconstruction of Sec. 3.B: two or more particles and
+  // not cut by a body (af: fluid fraction, null = every cell whole)
+  cs.usable = N >= 2 && (!af || af[c] >= 1.0);
+  cs.U[0] = s0 * inv; cs.U[1] = s1 * inv; cs.U[2] = s2 * inv;
+  // identity pending rescale until the cell is updated
+  for (int i = 0; i < 3; ++i) { cs.Un[i] = S(0.0); cs.Us[i] = S(0.0); }
+  cs.s = S(1.0);
+  cs.r = S(1.0);
+  if (!cs.active) {
+    atomicAdd(&counters[C_SKIPPED_CELLS], 1ull);
+    return;
+  }
+  for (int i = 0; i < 6; ++i) cs.Pi[i] = P[i];
+  cs.Ttr = (P[0] + P[1] + P[2]) / (3.0 * R);
+  cs.Trot = se * inv / R;
+  cs.ebar = sl * inv;
+  cs.Tvib = T_vib_of_level<double>(sp, cs.ebar);
+}
+
+template <typename S>
+__global__ void ch_coeffs(int ny, double F_num, double vol, const double* __restrict__ af,
+                          double dt, ChCellT<S>* __restrict__ cells, Species sp, S omega, S zrot,
+                          uint32_t* flags, unsigned long long* counters) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ny) return;
+  ChCellT<S>& cs = cells[c];
+  if (!cs.active) return;
+  const double v = af ? af[c] * vol : vol;   // fluid volume of a cut cell
+  if (!(v > 0.0)) {
+    cs.active = 0;
+    return;
+  }
+  cs.n = (double)cs.N * F_num / v;
+  const CellCoeffsT<S> k =
+      cell_coeffs_t<S>(sp, omega, zrot, cs.n, dt, cs.Ttr, cs.Trot, S(cs.Tvib));
+  if (!k.ok) {
+    atomicOr(flags, (uint32_t)F_A_NONPOS);
+    cs.active = 0;
+    return;
+  }
+  cs.alpha = k.alpha; cs.nu_ref = k.nu_ref; cs.B = k.B; cs.mu_p = k.mu_p; cs.Pr = k.Pr;
+  cs.gtr = k.g_tr_rot; cs.gtv = k.g_tr_vib; cs.grv = k.g_rot_vib;
+  cs.e_rot_tgt = k.e_rot_tgt;
+  cs.e_vib_tgt = k.e_vib_tgt;
+  if (k.tgt_clamped) {
+    atomicOr(flags, (uint32_t)F_TREL_CLAMP);
+    atomicAdd(&counters[C_TREL_CLAMP], 1ull);
+  }
+}
+
+template <typename S>
+__device__ __forceinline__ void cell_fields(const ChCellT<S>& c, S* f) {
+  f[0] = c.U[0]; f[1] = c.U[1]; f[2] = c.U[2];
+  f[3] = c.Ttr; f[4] = c.Trot; f[5] = S(c.Tvib);
+  for (int i = 0; i < 6; ++i) f[6 + i] = c.Pi[i];
+}
+
+__global__ void ch_mom_out(int ny, const double* __restrict__ a, double* __restrict__ out,
+                           Species sp) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ny) return;
+  const double* A = a + (size_t)c * 21;
+  const double N = A[0];
+  if (!(N > 0.0)) {
+    for (int f = 0; f < USP_NMOM; ++f) out[(size_t)f * ny + c] = 0.0;
+    return;
+  }
+  const double R = gasR(sp), inv = 1.0 / N;
+  out[c] = N;
+  for (int i = 0; i < 3; ++i) out[(size_t)(1 + i) * ny + c] = A[1 + i] * inv;
+  out[(size_t)4 * ny + c] = (A[6] + A[7] + A[8]) * inv / (3.0 * R);
+  out[(size_t)5 * ny + c] = A[4] * inv / R;
+  out[(size_t)6 * ny + c] = T_vib_of_level(sp, A[5] * inv);
+  for (int i = 0; i < 6; ++i) out[(size_t)(7 + i) * ny + c] = A[6 + i] * inv;
+  for (int i = 0; i < 3; ++i) {
+    out[(size_t)(13 + i) * ny + c] = A[12 + i] * inv;
+    out[(size_t)(16 + i) * ny + c] = A[15 + i] * inv;
+    out[(size_t)(19 + i) * ny + c] = A[18 + i] * inv * R * sp.theta_v;
+  }
+}
+
+}  // namespace

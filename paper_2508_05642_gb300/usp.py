@@ -18,7 +18,7 @@ from . import build as _build
 USP_OK, USP_EINVAL, USP_ENOMEM, USP_ECUDA, USP_EDEVICE, USP_ENOTSUP = 0, -1, -2, -3, -4, -5
 USP_FP64, USP_FP32, USP_FP64_TANGENT = 0, 1, 2
 USP_NMOM = 22
-USP_NCOUNTERS = 8
+USP_NCOUNTERS = 11
 
 F_PB_CLAMP = 0x01
 F_CHOL_FAIL_AFTER_FIX = 0x02
@@ -29,17 +29,20 @@ F_SAMPLER_CAP = 0x20
 F_A_NONPOS = 0x40
 F_SAMPLER_UNDERFLOW = 0x80
 F_BOUNDS = 0x200
+F_INFLOW_CAP = 0x800
+F_CAPACITY = 0x1000
 F_WAIT_TIMEOUT = 0x400
-ERROR_FLAGS = F_CHOL_FAIL_AFTER_FIX | F_A_NONPOS | F_SAMPLER_UNDERFLOW | F_BOUNDS | F_WAIT_TIMEOUT
+ERROR_FLAGS = F_A_NONPOS | F_SAMPLER_UNDERFLOW | F_BOUNDS | F_WAIT_TIMEOUT | F_CAPACITY
 
 C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, \
-    C_INTERP_FALLBACK, C_SKIPPED_CELLS = range(8)
+    C_INTERP_FALLBACK, C_SKIPPED_CELLS, C_INFLOW, C_OUTFLOW, C_NU_ZERO = range(11)
 
 EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogeneous", "usp_step", "usp_moments",
             "usp_get_particles", "usp_set_particles", "usp_step_host", "usp_status", "usp_sync",
             "usp_info", "usp_tuning", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
             "usp_moments_noalloc", "usp_init_channel", "usp_channel_sample",
-            "usp_channel_read", "usp_channel_get_particles", "usp_destroy"]
+            "usp_channel_read", "usp_channel_get_particles", "usp_init_plane", "usp_plane_count",
+            "usp_plane_get_particles", "usp_sample", "usp_sample_read", "usp_destroy"]
 USP_NOALLOC_MAX_CELLS = 8192
 
 
@@ -58,6 +61,18 @@ class usp_channel(C.Structure):
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+USP_BC_OPEN, USP_BC_SPECULAR, USP_BC_DIFFUSE = 0, 1, 2
+
+
+class usp_plane(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("x1", C.c_double),
+                ("y0", C.c_double), ("y1", C.c_double), ("cyl_xc", C.c_double),
+                ("cyl_yc", C.c_double), ("cyl_r", C.c_double), ("T_wall", C.c_double),
+                ("n_inf", C.c_double), ("T_inf", C.c_double), ("U_inf", C.c_double),
+                ("bc", C.c_int * 4), ("inflow", C.c_int * 4), ("F_num", C.c_double),
+                ("depth", C.c_double), ("reconstruct", C.c_int)]
 
 
 class usp_config(C.Structure):
@@ -119,6 +134,15 @@ def lib():
             L.usp_channel_sample.argtypes = [_CTX, C.c_int]
             L.usp_channel_read.argtypes = [_CTX, _D, C.c_int]
             L.usp_channel_get_particles.argtypes = [_CTX, _D, _D, _D, _D, _D, _I32, _U32]
+            L.usp_init_plane.argtypes = [C.POINTER(_CTX), C.POINTER(usp_species),
+                                         C.POINTER(usp_config), C.POINTER(usp_plane), C.c_double,
+                                         _D, C.c_int64, C.c_int64, _D, _D, _D, _D, _D, _D, _I32,
+                                         _U32]
+            L.usp_plane_count.argtypes = [_CTX, _I64, _U32]
+            L.usp_plane_get_particles.argtypes = [_CTX, C.c_int64, _I64, _D, _D, _D, _D, _D, _D,
+                                                  _I32, _U32]
+            L.usp_sample.argtypes = [_CTX, C.c_int]
+            L.usp_sample_read.argtypes = [_CTX, _D, C.c_int]
             L.usp_destroy.argtypes = [_CTX]
             L.usp_destroy.restype = None
             _lib = L
@@ -272,6 +296,83 @@ def usp_channel_get_particles(ctx: Context):
                                            _p(lev, C.c_int32), _p(pid, C.c_uint32)),
            "usp_channel_get_particles")
     return y, cx, cy, cz, er, lev, pid
+
+
+def usp_init_plane(species: dict, plane: dict, dt: float, area_frac, x, y, cx, cy, cz, erot, lev,
+                   capacity: int, pid=None, *, precision=USP_FP32, seed=1, step0=0, stream=None,
+                   use_graph=True, allocator=None) -> Context:
+    """Create a 2D plane context (host numpy inputs)."""
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    x, y, cx, cy, cz, erot, af = f(x), f(y), f(cx), f(cy), f(cz), f(erot), f(area_frac)
+    lev = np.ascontiguousarray(lev, dtype=np.int32)
+    pidp = None
+    if pid is not None:
+        pid = np.ascontiguousarray(pid, dtype=np.uint32)
+        pidp = _p(pid, C.c_uint32)
+    cfg = usp_config()
+    cfg.precision = precision
+    cfg.seed = seed
+    cfg.step0 = step0
+    cfg.stream = stream or None
+    cfg.use_graph = 1 if use_graph else 0
+    keep = []
+    if allocator is not None:
+        a_fn, f_fn, user = allocator
+        cfg.alloc, cfg.free_, cfg.alloc_user = a_fn, f_fn, user
+        keep += [a_fn, f_fn]
+    pl = usp_plane()
+    for k, _ in usp_plane._fields_:
+        if k in ("bc", "inflow"):
+            getattr(pl, k)[:] = list(plane[k])
+        else:
+            setattr(pl, k, plane[k])
+    sp = make_species(species)
+    h = _CTX()
+    n = len(x)
+    rc = lib().usp_init_plane(C.byref(h), C.byref(sp), C.byref(cfg), C.byref(pl), dt,
+                              _p(af, C.c_double), n, int(capacity), _p(x, C.c_double),
+                              _p(y, C.c_double), _p(cx, C.c_double), _p(cy, C.c_double),
+                              _p(cz, C.c_double), _p(erot, C.c_double), _p(lev, C.c_int32), pidp)
+    _check(rc, "usp_init_plane")
+    ctx = Context(h, n, int(plane["nx"]) * int(plane["ny"]), precision, keep)
+    ctx.capacity = int(capacity)
+    return ctx
+
+
+def usp_plane_count(ctx: Context):
+    """(live particle count, id of the next entering particle)."""
+    n = np.zeros(1, dtype=np.int64)
+    nxt = np.zeros(1, dtype=np.uint32)
+    _check(lib().usp_plane_count(ctx.h, _p(n, C.c_int64), _p(nxt, C.c_uint32)), "usp_plane_count")
+    return int(n[0]), int(nxt[0])
+
+
+def usp_plane_get_particles(ctx: Context):
+    """x, y, cx, cy, cz, erot, lev, pid of the live particles (cell order)."""
+    cap = ctx.capacity
+    out = [np.zeros(cap) for _ in range(6)]
+    lev = np.zeros(cap, dtype=np.int32)
+    pid = np.zeros(cap, dtype=np.uint32)
+    n = np.zeros(1, dtype=np.int64)
+    _check(lib().usp_plane_get_particles(ctx.h, cap, _p(n, C.c_int64),
+                                         *[_p(a, C.c_double) for a in out], _p(lev, C.c_int32),
+                                         _p(pid, C.c_uint32)), "usp_plane_get_particles")
+    k = int(n[0])
+    return tuple(a[:k] for a in out) + (lev[:k], pid[:k])
+
+
+def usp_sample(ctx: Context, on: bool = True):
+    _check(lib().usp_sample(ctx.h, 1 if on else 0), "usp_sample")
+
+
+def usp_sample_read(ctx: Context, reset: bool = False) -> np.ndarray:
+    """Per-cell time-average sums of a channel or plane context (n_cells * 12
+    + 2 doubles)."""
+    blocks = 4 if ctx.precision == USP_FP64_TANGENT else 1
+    out = np.zeros((ctx.n_cells * 12 + 2) * blocks)
+    _check(lib().usp_sample_read(ctx.h, _p(out, C.c_double), 1 if reset else 0),
+           "usp_sample_read")
+    return out
 
 
 def usp_step(ctx: Context, nsteps: int):
