@@ -120,9 +120,10 @@ class Clocks:
 
 
 def source_hash():
+    """Hash of the sources the batched collide kernel is compiled from."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2508_05642_gb300", "csrc", "*"))):
-        h.update(open(p, "rb").read())
+    for f in ("usp_device.cuh", "usp_homog.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2508_05642_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -314,7 +314,7 @@ __global__ void ch_collide(int ny, const ChCellT<S>* __restrict__ cells,
                            const T* __restrict__ y, T* __restrict__ cx, T* __restrict__ cy,
                            T* __restrict__ cz, T* __restrict__ er, int* __restrict__ lev,
                            const uint32_t* __restrict__ pid, ChSumsT<S>* __restrict__ sums,
-                           const long long* __restrict__ dstep, uint32_t k0, uint32_t k1,
+                           const long long* __restrict__ dstep, const PhiloxRoundKeys rk,
                            uint32_t* flags, unsigned long long* counters) {
   const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -343,7 +343,7 @@ __global__ void ch_collide(int ny, const ChCellT<S>* __restrict__ cells,
       ++nfb;
     }
     T v0 = cx[j], v1 = cy[j], v2 = cz[j], en = er[j];
-    const int ln = collide_particle_t(P, f, v0, v1, v2, en, lev[j], pid[j], step, k0, k1, tl);
+    const int ln = collide_particle_t(P, f, v0, v1, v2, en, lev[j], pid[j], step, rk, tl);
     cx[j] = v0; cy[j] = v1; cz[j] = v2; er[j] = en;
     lev[j] = ln;
     maxI = max(maxI, ln);
@@ -559,8 +559,8 @@ int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
   if (prof) prof(env.owner, 1, 1);
   const int wb = (h->ny * 32 + 127) / 128;
   const int cb = (h->ny + 127) / 128;
-  ch_moments<T, S><<<wb, 128, 0, s>>>(h->ny, h->off, nullptr, cx, cy, cz, er, h->lv[b], cells,
-                                      env.sp, env.counters);
+  ch_moments<T, S><<<wb, 128, 0, s>>>(h->ny, 1, h->off, nullptr, cx, cy, cz, er, h->lv[b], cells,
+                                      env.sp, env.counters, nullptr);
   ch_coeffs<S><<<cb, 128, 0, s>>>(h->ny, h->Fnum, h->area * h->dy, nullptr, h->dt, cells, env.sp,
                                   omega, zrot, env.flags, env.counters);
   ch_recon<T, S><<<cb, 128, 0, s>>>(h->ny, h->dy, h->recon, h->dt, cells, (ChParams<T>*)h->prm,
@@ -569,14 +569,15 @@ int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
   if (prof) prof(env.owner, 1, 0);
   if (prof) prof(env.owner, 0, 1);
   ch_collide<T, S><<<wb, 128, 0, s>>>(h->ny, cells, (const ChParams<T>*)h->prm, y, cx, cy, cz,
-                                      er, h->lv[b], h->pd[b], sums, h->dstep, env.k0, env.k1,
-                                      env.flags, env.counters);
+                                      er, h->lv[b], h->pd[b], sums, h->dstep,
+                                      philox_round_keys(env.k0, env.k1), env.flags, env.counters);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 0, 0);
   if (prof) prof(env.owner, 1, 1);
-  ch_levelfix<S><<<wb, 128, 0, s>>>(h->ny, cells, sums, h->lv[b], h->dstep, env.sp, env.k0,
+  ch_levelfix<S><<<wb, 128, 0, s>>>(h->ny, 1, cells, sums, h->lv[b], h->dstep, env.sp, env.k0,
                                     env.k1, env.flags, env.counters);
-  ch_update<S><<<cb, 128, 0, s>>>(h->ny, cells, sums, h->dstep, env.sp, env.flags, env.counters);
+  ch_update<S><<<cb, 128, 0, s>>>(h->ny, cells, sums, h->dstep, env.sp, env.flags, env.counters,
+                                  nullptr);
   CHK(cudaGetLastError());
   if (h->sampling) {
     ch_sample<T, S><<<nb, 256, 0, s>>>(n, h->ny, h->keycell, cells, cx, cy, cz, er, h->lv[b],

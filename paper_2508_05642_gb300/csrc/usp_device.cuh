@@ -44,6 +44,8 @@ struct Species {
   double m, d_ref, omega, T_ref, c_alpha, theta_v, Z_rot, Z_vib;
   int zmodel;
   double Zrot_inf, T_star, C1, C2, sigma_vib;
+  // derived on the host: T_ref^omega and pi d_ref^2 / sigma_vib
+  double Tref_w, zv_ht;
 };
 
 // ---------------------------------------------------------------------------
@@ -56,12 +58,60 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
                                             uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t n0 = hi1 ^ c1 ^ k0;
-    const uint32_t n2 = hi0 ^ c3 ^ k1;
-    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c0 = n0; c1 = (uint32_t)p1; c2 = n2; c3 = (uint32_t)p0;
     k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// The ten round keys of one key, computed once on the host: kernels take
+// them as a by-value parameter, so each round reads its key from the
+// parameter bank instead of advancing it per thread.
+struct PhiloxRoundKeys {
+  uint32_t k0[10], k1[10];
+};
+inline PhiloxRoundKeys philox_round_keys(uint32_t k0, uint32_t k1) {
+  PhiloxRoundKeys rk;
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0;
+    rk.k1[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return rk;
+}
+// Two blocks whose counters differ only in word 2, rounds interleaved so the
+// two independent multiply chains overlap.
+__device__ __forceinline__ void philox4x32_10_pair(uint32_t c0, uint32_t c1, uint32_t c2a,
+                                                   uint32_t c2b, uint32_t c3,
+                                                   const PhiloxRoundKeys& rk, U4& a, U4& b) {
+  uint32_t a0 = c0, a1 = c1, a2 = c2a, a3 = c3;
+  uint32_t b0 = c0, b1 = c1, b2 = c2b, b3 = c3;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t pa0 = (uint64_t)0xD2511F53u * a0, pa1 = (uint64_t)0xCD9E8D57u * a2;
+    const uint64_t pb0 = (uint64_t)0xD2511F53u * b0, pb1 = (uint64_t)0xCD9E8D57u * b2;
+    const uint32_t na0 = (uint32_t)(pa1 >> 32) ^ a1 ^ rk.k0[r];
+    const uint32_t na2 = (uint32_t)(pa0 >> 32) ^ a3 ^ rk.k1[r];
+    const uint32_t nb0 = (uint32_t)(pb1 >> 32) ^ b1 ^ rk.k0[r];
+    const uint32_t nb2 = (uint32_t)(pb0 >> 32) ^ b3 ^ rk.k1[r];
+    a0 = na0; a1 = (uint32_t)pa1; a2 = na2; a3 = (uint32_t)pa0;
+    b0 = nb0; b1 = (uint32_t)pb1; b2 = nb2; b3 = (uint32_t)pb0;
+  }
+  a = U4{a0, a1, a2, a3};
+  b = U4{b0, b1, b2, b3};
+}
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            const PhiloxRoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk.k1[r];
+    c0 = n0; c1 = (uint32_t)p1; c2 = n2; c3 = (uint32_t)p0;
   }
   return U4{c0, c1, c2, c3};
 }
@@ -295,14 +345,17 @@ __device__ __forceinline__ S prandtl_T(const Species& s, const S& Tv) {
   }
   return (14.0 + 2.0 * xi) / (19.0 + 2.0 * xi);
 }
+// Collision numbers: zmodel 0 the fixed ones, zmodel 1 Parker's Z_rot and
+// Millikan-White with the high-temperature term for Z_vib (Sec. 5.C).  xw is
+// (T_tr/T_ref)^omega, shared with the viscosity, so that
+// T^omega = T_ref^omega xw and (T_ref/T)^(omega - 1/2) = sqrt(T/T_ref) / xw.
 template <typename S>
-__device__ __forceinline__ void collision_numbers(const Species& s, const S& Ttr, const S& zrot0,
-                                                  S& zr, S& zv) {
+__device__ __forceinline__ void collision_numbers(const Species& s, const S& Ttr, const S& xw,
+                                                  const S& zrot0, S& zr, S& zv) {
   if (s.zmodel == 0) { zr = zrot0; zv = S(s.Z_vib); return; }
   const S r = s.T_star / Ttr;
-  zr = s.Zrot_inf / (1.0 + 0.5 * pow(kPi, 1.5) * sqrt(r) + (kPi + 0.25 * kPi * kPi) * r);
-  zv = (s.C1 / pow(Ttr, s.omega)) * exp(s.C2 * pow(Ttr, -1.0 / 3.0)) +
-       (kPi * s.d_ref * s.d_ref / s.sigma_vib) * pow(s.T_ref / Ttr, s.omega - 0.5);
+  zr = s.Zrot_inf / (1.0 + 0.5 * kPi * sqrt(kPi) * sqrt(r) + (kPi + 0.25 * kPi * kPi) * r);
+  zv = (s.C1 / (s.Tref_w * xw)) * exp(s.C2 / cbrt(Ttr)) + s.zv_ht * sqrt(Ttr / s.T_ref) / xw;
 }
 
 // Per-cell coefficients of Sec. 3.A: alpha = A^(1/3) (the real cube root,
@@ -327,10 +380,15 @@ __device__ inline CellCoeffsT<S> cell_coeffs_t(const Species& s, const S& omega,
   const double R = gasR(s);
   const double ctr = 1.5 * R, crot = R;
   const S p = n * kB * Ttr;
-  c.mu_p = mu_of_T_w<S>(s, Ttr, omega) / p;
+  // (T/T_ref)^omega, shared by the viscosity and the collision numbers
+  const S xw = exp(omega * log(Ttr / s.T_ref));
+  const double ca = s.c_alpha;
+  const S mu_ref = 5.0 * (ca + 1.0) * (ca + 2.0) * sqrt(s.m * kB * s.T_ref / kPi) /
+                   (4.0 * ca * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega) * s.d_ref * s.d_ref);
+  c.mu_p = mu_ref * xw / p;
   const S tau_c = tau_c_factor_w<S>(s, omega) * c.mu_p;
   S zr, zv;
-  collision_numbers<S>(s, Ttr, zrot, zr, zv);
+  collision_numbers<S>(s, Ttr, xw, zrot, zr, zv);
   const S tau_rot = zr * tau_c, tau_vib = zv * tau_c;
   c.Pr = prandtl_T<S>(s, Tvib);
   c.A = (2.0 * c.mu_p - c.Pr * dt) / (2.0 * c.mu_p + c.Pr * dt);

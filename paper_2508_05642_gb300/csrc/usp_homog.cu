@@ -98,7 +98,7 @@ __device__ __forceinline__ void flag_or(uint32_t* flags, uint32_t f) {
 // sequential search, as does a search running past the row.
 // ---------------------------------------------------------------------------
 constexpr int kJR = 32;   // rows: NB r = 1..32, B n = 0..31
-constexpr int kJK = 48;   // cumulative values per row
+constexpr int kJK = 48;   // cumulative values per row (rows 16-byte aligned)
 
 __device__ void nb_row(int r, float p, float* T) {
   const float q = rn_sub(1.0f, p);
@@ -148,12 +148,28 @@ __device__ void b_row(int n, float p, float* T) {
   }
 }
 
+// Search of a table row: the number of leading entries <= u.  Rows are
+// non-decreasing (cumulative sums, +inf once the sum stops growing), so the
+// entries <= u of a group of four are its leading ones and their count is
+// the step of the sequential search through the group.
+__device__ __forceinline__ int row_search(const float* __restrict__ T, float u) {
+  const float4* T4 = reinterpret_cast<const float4*>(T);
+  int k = 0;
+#pragma unroll 1
+  for (int q = 0; q < kJK / 4; ++q) {
+    const float4 t = T4[q];
+    const int c = (u >= t.x) + (u >= t.y) + (u >= t.z) + (u >= t.w);
+    k += c;
+    if (c < 4) break;
+  }
+  return k;
+}
+
 __device__ __forceinline__ int nb_tab(const float* __restrict__ T, int r, float p, float u,
                                       uint32_t& fl) {
   if (r <= 0 || !(p < 1.0f)) return 0;
   if (r > kJR || T[0] < 0.0f) return nb_inv(r, p, u, fl);
-  int k = 0;
-  while (k < kJK && u >= T[k]) ++k;
+  const int k = row_search(T, u);
   return k < kJK ? k : nb_inv(r, p, u, fl);
 }
 
@@ -170,8 +186,7 @@ __device__ __forceinline__ int b_tab(const float* __restrict__ T, int n, float p
   if (n >= kJR || T[0] < 0.0f) {
     k = binv(n, flip ? rn_sub(1.0f, p) : p, u, fl);
   } else {
-    k = 0;
-    while (u >= T[k]) ++k;   // T[n] = +inf ends the scan by k = n < kJK
+    k = row_search(T, u);    // T[n] = +inf ends the scan by k = n < kJK
   }
   return flip ? n - k : k;
 }
@@ -180,12 +195,14 @@ __device__ __forceinline__ int b_tab(const float* __restrict__ T, int n, float p
 // One particle: pending rescale, velocity, rotation, vibration.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t pid, uint32_t k0,
-                                            uint32_t k1, T& cx, T& cy, T& cz, T& er, int& lv,
+__device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t pid,
+                                            const PhiloxRoundKeys& rk, T& cx, T& cy, T& cz, T& er,
+                                            int& lv,
                                             T* acc, int& accI, int& maxI, uint32_t& fl,
                                             const float* __restrict__ tnb,
                                             const float* __restrict__ tb) {
-  const U4 w = philox4x32_10(pid, P.step, PTAG_NORMALS, 0u, k0, k1);
+  U4 w, w2;
+  philox4x32_10_pair(pid, P.step, PTAG_NORMALS, PTAG_JUMPS, 0u, rk, w, w2);
   T g0, g1, g2, g3;
   box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
   box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
@@ -201,7 +218,6 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   const T root = sqrt(er) * P.ar + P.sqrt_a * g3;
   er = P.a_rot + root * root;
   // I' = I + NB(I + 1, p_NB) - B(I, p_B)
-  const U4 w2 = philox4x32_10(pid, P.step, PTAG_JUMPS, 0u, k0, k1);
   const T u5 = uniform_open<T>(w2.x), u6 = uniform_open<T>(w2.y);
   const int I = lv;
   int up, dn;
@@ -375,7 +391,7 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
                const CollideParams<T>* __restrict__ prm, T* __restrict__ cx,
                T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
                int* __restrict__ lev, CellSums* __restrict__ sums, uint32_t* flags,
-               unsigned long long* counters, uint32_t k0, uint32_t k1,
+               unsigned long long* counters, const PhiloxRoundKeys rk,
                const float* __restrict__ tab_nb, const float* __restrict__ tab_b) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[2];
@@ -442,7 +458,7 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
         T x = X[k], y = X[k + kTileMax], z = X[k + 2 * kTileMax], e = X[k + 3 * kTileMax];
         int l = Lv[k];
         uint32_t f1 = 0;
-        collide_one<T>(P, pid0 + (uint32_t)k, k0, k1, x, y, z, e, l, acc, accI, maxI, f1, tnb, tb);
+        collide_one<T>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb, tb);
         X[k] = x; X[k + kTileMax] = y; X[k + 2 * kTileMax] = z; X[k + 3 * kTileMax] = e;
         Lv[k] = l;
         npb += (f1 & F_PB_CLAMP) ? 1 : 0;
@@ -1021,6 +1037,8 @@ Species to_dev(const usp_species* s) {
   d.c_alpha = s->c_alpha; d.theta_v = s->theta_v; d.Z_rot = s->Z_rot; d.Z_vib = s->Z_vib;
   d.zmodel = s->zmodel; d.Zrot_inf = s->Zrot_inf; d.T_star = s->T_star; d.C1 = s->C1;
   d.C2 = s->C2; d.sigma_vib = s->sigma_vib;
+  d.Tref_w = std::pow(s->T_ref, s->omega);
+  d.zv_ht = s->sigma_vib > 0 ? kPi * s->d_ref * s->d_ref / s->sigma_vib : 0.0;
   return d;
 }
 
@@ -1133,18 +1151,18 @@ int launch_collide(usp_ctx* c, int minb, int grid, const Tile* tiles, int ntiles
   const size_t smem = 2 * stage_bytes<T>();
   const CollideParams<T>* prm = (const CollideParams<T>*)c->prm;
   T* x = (T*)cx; T* y = (T*)cy; T* z = (T*)cz; T* e = (T*)er;
-  const uint32_t a = key0(c), b = key1(c);
+  const PhiloxRoundKeys rk = philox_round_keys(key0(c), key1(c));
   const float* tn = c->tab_nb;
   const float* tb = c->tab_b;
   if (minb == 2)
     collide_kernel<T, 2><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
-                                                            sums, flags, counters, a, b, tn, tb);
+                                                            sums, flags, counters, rk, tn, tb);
   else if (minb == 3)
     collide_kernel<T, 3><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
-                                                            sums, flags, counters, a, b, tn, tb);
+                                                            sums, flags, counters, rk, tn, tb);
   else
     collide_kernel<T, 4><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
-                                                            sums, flags, counters, a, b, tn, tb);
+                                                            sums, flags, counters, rk, tn, tb);
   CK(cudaGetLastError());
   return USP_OK;
 }

@@ -61,7 +61,7 @@ struct PlGeom {
   double x0, x1, y0, y1, dx, dy;
   double cxc, cyc, cr;
   double Tw, dt;
-  int bc[4];          // left, right, bottom, top
+  int bcbits;         // 2 bits per side (USP_BC_*): left, right, bottom, top
 };
 
 struct PlInflow {
@@ -192,7 +192,7 @@ __device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint
       kind = USP_BC_DIFFUSE;
     } else {
       const int side = ev - 1;
-      kind = g.bc[side];
+      kind = (g.bcbits >> (2 * side)) & 3;
       if (side == 0) { nx = T(1); x = (T)g.x0; }
       if (side == 1) { nx = T(-1); x = (T)g.x1; }
       if (side == 2) { ny = T(1); y = (T)g.y0; }
@@ -211,26 +211,39 @@ __device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint
 }
 
 template <typename T>
-__global__ void pl_advect(PlGeom g, const PlCount* __restrict__ cnt,
+__global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, const PlCount* __restrict__ cnt,
                           const int* __restrict__ keycell, const ChCellT<double>* __restrict__ cells,
+                          const float* __restrict__ pend,
                           T* __restrict__ x, T* __restrict__ y, T* __restrict__ cx,
                           T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
                           int* __restrict__ lev, const uint32_t* __restrict__ pid,
                           int* __restrict__ keyout, int* __restrict__ idxout,
                           const long long* __restrict__ dstep, Species sp, uint32_t k0,
                           uint32_t k1, uint32_t* flags, unsigned long long* counters) {
+  __shared__ BlockTally tal;
+  tally_init(tal);
   const long long n = cnt->n;
   const uint32_t step = (uint32_t)*dstep;
   uint32_t fl = 0;
   unsigned long long nhit = 0, nout = 0;
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += grid_threads()) {
-    const ChCellT<double>& cc = cells[keycell[j]];
-    // pending conservation rescale of the previous step
-    T vx = (T)cc.Un[0] + (T)cc.s * (cx[j] - (T)cc.Us[0]);
-    T vy = (T)cc.Un[1] + (T)cc.s * (cy[j] - (T)cc.Us[1]);
-    T vz = (T)cc.Un[2] + (T)cc.s * (cz[j] - (T)cc.Us[2]);
-    T e = (T)cc.r * er[j];
+    // pending conservation rescale of the previous step (FP32 state: its
+    // FP32 copy, so no FP64 conversion per particle)
+    T vx, vy, vz, e;
+    if constexpr (sizeof(T) == 4) {
+      const float* pc = pend + (size_t)keycell[j] * 8;
+      vx = pc[0] + pc[6] * (cx[j] - pc[3]);
+      vy = pc[1] + pc[6] * (cy[j] - pc[4]);
+      vz = pc[2] + pc[6] * (cz[j] - pc[5]);
+      e = pc[7] * er[j];
+    } else {
+      const ChCellT<double>& cc = cells[keycell[j]];
+      vx = (T)cc.Un[0] + (T)cc.s * (cx[j] - (T)cc.Us[0]);
+      vy = (T)cc.Un[1] + (T)cc.s * (cy[j] - (T)cc.Us[1]);
+      vz = (T)cc.Un[2] + (T)cc.s * (cz[j] - (T)cc.Us[2]);
+      e = (T)cc.r * er[j];
+    }
     int l = lev[j];
     T px = x[j], py = y[j];
     int hits = 0;
@@ -246,17 +259,25 @@ __global__ void pl_advect(PlGeom g, const PlCount* __restrict__ cnt,
   nhit = wsum(nhit);
   nout = wsum(nout);
   if ((threadIdx.x & 31) == 0) {
-    if (fl) atomicOr(flags, fl);
-    if (nhit) atomicAdd(&counters[C_WALL_HITS], nhit);
-    if (nout) atomicAdd(&counters[C_OUTFLOW], nout);
+    tally_or(tal, fl);
+    tally_add(tal, C_WALL_HITS, nhit);
+    tally_add(tal, C_OUTFLOW, nout);
   }
+  tally_flush(tal, flags, counters);
+}
+
+// per-side value without a dynamically indexed (local-memory) array
+template <typename V>
+__device__ __forceinline__ V pick4(const V (&a)[4], int side) {
+  return side == 0 ? a[0] : (side == 1 ? a[1] : (side == 2 ? a[2] : a[3]));
 }
 
 // face q of the inflow list -> side and face index along the side
 __device__ __forceinline__ void face_of(const PlInflow& f, int q, int& side, int& k) {
-  side = 0;
-  while (side < 3 && (f.nf[side] == 0 || q >= f.base[side] + f.nf[side])) ++side;
-  k = q - f.base[side];
+  side = (f.nf[0] > 0 && q < f.base[0] + f.nf[0]) ? 0
+       : (f.nf[1] > 0 && q < f.base[1] + f.nf[1]) ? 1
+       : (f.nf[2] > 0 && q < f.base[2] + f.nf[2]) ? 2 : 3;
+  k = q - pick4(f.base, side);
 }
 
 // One block of 1024 threads: the number of particles entering through each
@@ -280,7 +301,7 @@ __global__ void pl_inflow(PlInflow f, PlCount* __restrict__ cnt, int* __restrict
       face_of(f, q, side, k);
       const uint32_t fid = ((uint32_t)side << 24) | (uint32_t)k;
       const U4 r = philox4x32_10(fid, step, CTAG_INFLOW, 0u, k0, k1);
-      c = (int)floor(f.expect[side] + uniform_open<double>(r.x));
+      c = (int)floor(pick4(f.expect, side) + uniform_open<double>(r.x));
     }
     // block exclusive scan of c
     int v = c;
@@ -364,37 +385,44 @@ __device__ double inflow_speed(double RT, double u_n, uint32_t pid, uint32_t ste
   return (s > 0.0 ? s : 0.5 * sqrt(kPi)) * sc;
 }
 
-// one warp per inflow face; lanes over the face's entering particles
+// one thread per entering particle (grid-stride over the step's count); its
+// face by binary search of the face offsets
 template <typename T>
-__global__ void pl_inject(PlGeom g, PlInflow f, const PlCount* __restrict__ cnt,
+__global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, PlInflow f, const PlCount* __restrict__ cnt,
                           const int* __restrict__ face_off, T* __restrict__ x, T* __restrict__ y,
                           T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ cz,
                           T* __restrict__ er, int* __restrict__ lev, uint32_t* __restrict__ pid,
                           int* __restrict__ keyout, int* __restrict__ idxout,
                           const long long* __restrict__ dstep, Species sp, uint32_t k0,
                           uint32_t k1, uint32_t* flags, unsigned long long* counters) {
-  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (q >= f.nfaces || cnt->ninj == 0) return;
+  __shared__ BlockTally tal;
+  tally_init(tal);
+  const long long ninj = cnt->ninj;
   const uint32_t step = (uint32_t)*dstep;
   const long long n = cnt->n;
-  const int b = face_off[q], count = face_off[q + 1] - b;
-  int side, k;
-  face_of(f, q, side, k);
-  const double R = gasR(sp);
   const double st = sqrt(f.RT);
-  const double nxs = side == 0 ? 1.0 : (side == 1 ? -1.0 : 0.0);
-  const double nys = side == 2 ? 1.0 : (side == 3 ? -1.0 : 0.0);
   uint32_t fl = 0;
   unsigned long long nhit = 0, nout = 0;
-  for (int m = lane; m < count; m += 32) {
-    const uint32_t id = cnt->pid0 + (uint32_t)(b + m);
+  for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < ninj;
+       m += grid_threads()) {
+    // face q: face_off[q] <= m < face_off[q + 1]
+    int lo = 0, hi = f.nfaces - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (face_off[mid] <= m) lo = mid; else hi = mid - 1;
+    }
+    const int q = lo;
+    int side, k;
+    face_of(f, q, side, k);
+    const double nxs = side == 0 ? 1.0 : (side == 1 ? -1.0 : 0.0);
+    const double nys = side == 2 ? 1.0 : (side == 3 ? -1.0 : 0.0);
+    const uint32_t id = cnt->pid0 + (uint32_t)m;
     const U4 a = philox4x32_10(id, step, PTAG_INFLOW_P, 0u, k0, k1);
     const U4 bb = philox4x32_10(id, step, PTAG_INFLOW_T, 0u, k0, k1);
     const double u_pos = (double)uniform_open<T>(a.x), u_t = (double)uniform_open<T>(a.y);
     double g1, g2;
     box_muller((double)uniform_open<T>(bb.x), (double)uniform_open<T>(bb.y), g1, g2);
-    const double vn = inflow_speed<T>(f.RT, f.u_n[side], id, step, k0, k1, fl);
+    const double vn = inflow_speed<T>(f.RT, pick4(f.u_n, side), id, step, k0, k1, fl);
     double px, py, vx, vy;
     if (side < 2) {
       px = side == 0 ? g.x0 : g.x1;
@@ -410,14 +438,13 @@ __global__ void pl_inject(PlGeom g, PlInflow f, const PlCount* __restrict__ cnt,
     const double vz = st * g2;
     const double e = -f.RT * log((double)uniform_open<T>(a.z));
     const int l0 = (int)floor(-log((double)uniform_open<T>(a.w)) * f.T / sp.theta_v);
-    (void)R;
     T X = (T)px, Y = (T)py, VX = (T)vx, VY = (T)vy, VZ = (T)vz, E = (T)e;
     int L = l0, hits = 0;
     const bool keep = plane_fly<T>(g, sp, id, step, k0, k1, (T)(u_t * g.dt), X, Y, VX, VY, VZ,
                                    E, L, hits, fl);
     nhit += hits;
     nout += keep ? 0 : 1;
-    const long long j = n + b + m;
+    const long long j = n + m;
     x[j] = X; y[j] = Y; cx[j] = VX; cy[j] = VY; cz[j] = VZ; er[j] = E; lev[j] = L; pid[j] = id;
     keyout[j] = keep ? plane_cell(g, X, Y) : g.ncell;
     idxout[j] = (int)j;
@@ -425,37 +452,42 @@ __global__ void pl_inject(PlGeom g, PlInflow f, const PlCount* __restrict__ cnt,
   fl = __reduce_or_sync(0xffffffffu, fl);
   nhit = wsum(nhit);
   nout = wsum(nout);
-  if (lane == 0) {
-    if (fl) atomicOr(flags, fl);
-    if (nhit) atomicAdd(&counters[C_WALL_HITS], nhit);
-    if (nout) atomicAdd(&counters[C_OUTFLOW], nout);
+  if ((threadIdx.x & 31) == 0) {
+    tally_or(tal, fl);
+    tally_add(tal, C_WALL_HITS, nhit);
+    tally_add(tal, C_OUTFLOW, nout);
   }
+  tally_flush(tal, flags, counters);
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort of (key, index) over the device count ntot, 8-bit
-// digits; histograms digit-major (bh[d * nblk + b])
+// stable LSD radix sort of (key, index) over the device count ntot, kDig-bit
+// digits (two passes cover the 240,001 keys of the 600 x 400 grid);
+// histograms digit-major (bh[d * nblk + b])
 // ---------------------------------------------------------------------------
+constexpr int kDig = 9;
+constexpr int kNB = 1 << kDig;
+
 __global__ void pl_hist(const int* __restrict__ key, const PlCount* __restrict__ cnt, int shift,
                         int* __restrict__ bh, int nblk) {
-  __shared__ int h[256];
-  h[threadIdx.x] = 0;
+  __shared__ int h[kNB];
+  for (int d = threadIdx.x; d < kNB; d += kRB) h[d] = 0;
   __syncthreads();
   const long long n = cnt->ntot;
   const long long b = (long long)blockIdx.x * kChunk;
   if (b < n) {
     for (int r = 0; r < kRPT; ++r) {
       const long long i = b + (long long)r * kRB + threadIdx.x;
-      if (i < n) atomicAdd(&h[(key[i] >> shift) & 255], 1);
+      if (i < n) atomicAdd(&h[(key[i] >> shift) & (kNB - 1)], 1);
     }
   }
   __syncthreads();
-  bh[(size_t)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+  for (int d = threadIdx.x; d < kNB; d += kRB) bh[(size_t)d * nblk + blockIdx.x] = h[d];
 }
 
 // one block per digit: exclusive scan over the blocks, digit total
 __global__ void pl_scan_digits(int* __restrict__ bh, int nblk, int* __restrict__ tot) {
-  __shared__ int ws[8];
+  __shared__ int ws[kRB / 32];
   __shared__ int carry;
   const int d = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
   int* row = bh + (size_t)d * nblk;
@@ -477,9 +509,9 @@ __global__ void pl_scan_digits(int* __restrict__ bh, int nblk, int* __restrict__
     if (b < nblk) row[b] = carry + pre + v - c;
     __syncthreads();
     if (t == 0) {
-      int s = 0;
-      for (int k = 0; k < kRB / 32; ++k) s += ws[k];
-      carry += s;
+      int sum = 0;
+      for (int k = 0; k < kRB / 32; ++k) sum += ws[k];
+      carry += sum;
     }
     __syncthreads();
   }
@@ -490,46 +522,64 @@ __global__ void pl_scatter(const int* __restrict__ kin, const int* __restrict__ 
                            int* __restrict__ kout, int* __restrict__ iout,
                            const PlCount* __restrict__ cnt, int shift, const int* __restrict__ bh,
                            const int* __restrict__ tot, int nblk) {
-  __shared__ int cntw[kRB / 32][256];
-  __shared__ int run[256];
-  __shared__ int base[256];
-  const int t = threadIdx.x, w = t >> 5;
+  __shared__ int cntw[kRB / 32][kNB];
+  __shared__ int run[kNB];
+  __shared__ int wsum_[kRB / 32];
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const long long n = cnt->ntot;
   const long long b = (long long)blockIdx.x * kChunk;
   if (b >= n) return;
-  // exclusive scan of the digit totals
-  base[t] = tot[t];
-  __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    const int v = t >= o ? base[t - o] : 0;
-    __syncthreads();
-    base[t] += v;
-    __syncthreads();
+  // exclusive scan of the digit totals: thread t owns digits t * kPer .. + kPer - 1
+  constexpr int kPer = kNB / kRB;
+  int loc[kPer];
+  int own = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    loc[q] = tot[t * kPer + q];
+    own += loc[q];
   }
-  run[t] = (base[t] - tot[t]) + bh[(size_t)t * nblk + blockIdx.x];
+  int v = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  if (lane == 31) wsum_[w] = v;
+  __syncthreads();
+  int pre = v - own;
+  for (int k = 0; k < w; ++k) pre += wsum_[k];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int d = t * kPer + q;
+    run[d] = pre + bh[(size_t)d * nblk + blockIdx.x];
+    pre += loc[q];
+  }
   __syncthreads();
   for (int r = 0; r < kRPT; ++r) {
-    for (int q = 0; q < kRB / 32; ++q) cntw[q][t] = 0;
+    for (int q = 0; q < kRB / 32; ++q)
+      for (int d = t; d < kNB; d += kRB) cntw[q][d] = 0;
     __syncthreads();
     const long long i = b + (long long)r * kRB + t;
     const bool valid = i < n;
     const int kk = valid ? kin[i] : 0;
-    const int d = valid ? ((kk >> shift) & 255) : 256;
+    const int d = valid ? ((kk >> shift) & (kNB - 1)) : kNB;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & lane_lt());
     if (valid && rank == 0) cntw[w][d] = __popc(peers);
     __syncthreads();
     if (valid) {
-      int pre = 0;
-      for (int q = 0; q < w; ++q) pre += cntw[q][d];
-      const int pos = run[d] + pre + rank;
+      int p = 0;
+      for (int q = 0; q < w; ++q) p += cntw[q][d];
+      const int pos = run[d] + p + rank;
       kout[pos] = kk;
       iout[pos] = iin[i];
     }
     __syncthreads();
-    int s = 0;
-    for (int q = 0; q < kRB / 32; ++q) s += cntw[q][t];
-    run[t] += s;
+    for (int dd = t; dd < kNB; dd += kRB) {
+      int sum = 0;
+      for (int q = 0; q < kRB / 32; ++q) sum += cntw[q][dd];
+      run[dd] += sum;
+    }
     __syncthreads();
   }
 }
@@ -623,84 +673,97 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
 // per particle: the bilinear polynomial of its quadrant, then the collision
 // of Sec. 4.D; one warp per cell, per-cell sums for the conservation step
 template <typename T>
-__global__ void pl_collide(int ncell, const ChCellT<double>* __restrict__ cells,
+__global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<double>* __restrict__ cells,
                            const PlParams<T>* __restrict__ prm, const T* __restrict__ x,
                            const T* __restrict__ y, T* __restrict__ cx, T* __restrict__ cy,
                            T* __restrict__ cz, T* __restrict__ er, int* __restrict__ lev,
                            const uint32_t* __restrict__ pid, ChSumsT<double>* __restrict__ sums,
-                           const long long* __restrict__ dstep, uint32_t k0, uint32_t k1,
+                           const long long* __restrict__ dstep, const PhiloxRoundKeys rk,
                            uint32_t* flags, unsigned long long* counters) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  __shared__ BlockTally tal;
+  tally_init(tal);
   const int lane = threadIdx.x & 31;
-  if (c >= ncell) return;
-  const ChCellT<double>& cs = cells[c];
-  if (!cs.active) return;
-  const PlParams<T>& P = prm[c];
   const uint32_t step = (uint32_t)*dstep;
-  const T Uc0 = (T)cs.U[0], Uc1 = (T)cs.U[1], Uc2 = (T)cs.U[2];
-  T acc[10];
-  for (int i = 0; i < 10; ++i) acc[i] = T(0);
-  double accI = 0.0;
-  int maxI = 0;
-  CollideTally tl = {0u, 0ull, 0ull, 0ull, 0ull};
-  unsigned long long nfb = 0;
-  for (long long j = cs.off + lane; j < cs.off + cs.N; j += 32) {
-    const T ddx = x[j] - P.xc, ddy = y[j] - P.yc;
-    const int sx = ddx >= T(0) ? 1 : 0, sy = ddy >= T(0) ? 1 : 0;
-    const int xc = P.xcell[sx], yc = P.ycell[sy], dc = P.dcell[sy * 2 + sx];
-    T f[kNF];
+  for (int c = warp_global(); c < ncell; c += warps_total()) {
+    const ChCellT<double>& cs = cells[c];
+    if (!cs.active) continue;
+    const PlParams<T>& P = prm[c];
+    // cell velocity in T: one conversion per warp (lanes 0-2), then broadcast
+    const T uc = (T)(lane < 3 ? cs.U[lane < 3 ? lane : 0] : 0.0);
+    const T Uc0 = __shfl_sync(0xffffffffu, uc, 0), Uc1 = __shfl_sync(0xffffffffu, uc, 1),
+            Uc2 = __shfl_sync(0xffffffffu, uc, 2);
+    T acc[10];
 #pragma unroll
-    for (int i = 0; i < kNF; ++i) {
-      const T p0 = P.F[i];
-      T v = p0, px = T(0), py = T(0);
-      if (xc >= 0) {
-        px = prm[xc].F[i];
-        v += (px - p0) * ddx / P.hx[sx];
-      }
-      if (yc >= 0) {
-        py = prm[yc].F[i];
-        v += (py - p0) * ddy / P.hy[sy];
-      }
-      if (dc >= 0) v += (prm[dc].F[i] - px - py + p0) * ddx * ddy / P.hxy[sy * 2 + sx];
-      f[i] = v;
-    }
-    if (!(f[3] > T(0)) || !(f[4] > T(0)) || !(f[5] >= T(0))) {
+    for (int i = 0; i < 10; ++i) acc[i] = T(0);
+    long long accI = 0;
+    int maxI = 0;
+    CollideTally tl = {0u, 0ull, 0ull, 0ull, 0ull};
+    unsigned long long nfb = 0;
+    for (long long j = cs.off + lane; j < cs.off + cs.N; j += 32) {
+      const T ddx = x[j] - P.xc, ddy = y[j] - P.yc;
+      const int sx = ddx >= T(0) ? 1 : 0, sy = ddy >= T(0) ? 1 : 0;
+      const int xc = P.xcell[sx], yc = P.ycell[sy], dc = P.dcell[sy * 2 + sx];
+      T f[kNF];
 #pragma unroll
-      for (int i = 0; i < kNF; ++i) f[i] = P.F[i];
-      ++nfb;
+      for (int i = 0; i < kNF; ++i) {
+        const T p0 = P.F[i];
+        T v = p0, px = T(0), py = T(0);
+        if (xc >= 0) {
+          px = prm[xc].F[i];
+          v += (px - p0) * ddx / P.hx[sx];
+        }
+        if (yc >= 0) {
+          py = prm[yc].F[i];
+          v += (py - p0) * ddy / P.hy[sy];
+        }
+        if (dc >= 0) v += (prm[dc].F[i] - px - py + p0) * ddx * ddy / P.hxy[sy * 2 + sx];
+        f[i] = v;
+      }
+      if (!(f[3] > T(0)) || !(f[4] > T(0)) || !(f[5] >= T(0))) {
+#pragma unroll
+        for (int i = 0; i < kNF; ++i) f[i] = P.F[i];
+        ++nfb;
+      }
+      T v0 = cx[j], v1 = cy[j], v2 = cz[j], en = er[j];
+      const int ln = collide_particle_t(P, f, v0, v1, v2, en, lev[j], pid[j], step, rk, tl);
+      cx[j] = v0; cy[j] = v1; cz[j] = v2; er[j] = en;
+      lev[j] = ln;
+      maxI = max(maxI, ln);
+      const T d0 = v0 - Uc0, d1 = v1 - Uc1, d2 = v2 - Uc2;
+      acc[0] += d0; acc[1] += d1; acc[2] += d2;
+      acc[3] += d0 * d0; acc[4] += d1 * d1; acc[5] += d2 * d2;
+      acc[6] += d0 * d1; acc[7] += d0 * d2; acc[8] += d1 * d2;
+      acc[9] += en;
+      accI += ln;
     }
-    T v0 = cx[j], v1 = cy[j], v2 = cz[j], en = er[j];
-    const int ln = collide_particle_t(P, f, v0, v1, v2, en, lev[j], pid[j], step, k0, k1, tl);
-    cx[j] = v0; cy[j] = v1; cz[j] = v2; er[j] = en;
-    lev[j] = ln;
-    maxI = max(maxI, ln);
-    const T d0 = v0 - Uc0, d1 = v1 - Uc1, d2 = v2 - Uc2;
-    acc[0] += d0; acc[1] += d1; acc[2] += d2;
-    acc[3] += d0 * d0; acc[4] += d1 * d1; acc[5] += d2 * d2;
-    acc[6] += d0 * d1; acc[7] += d0 * d2; acc[8] += d1 * d2;
-    acc[9] += en;
-    accI += (double)ln;
+    // warp totals; lane i < 10 converts total i (one FP64 conversion per warp)
+    T mine = T(0);
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+      const T t = wsum(acc[i]);
+      mine = lane == i ? t : mine;
+    }
+    const double sv = (double)mine;
+    const long long sI = wsum(accI);
+    const unsigned long long fix = wsum(tl.nfix), fb = wsum(nfb), ncl2 = wsum(tl.ncl),
+                             pb = wsum(tl.npb), nz = wsum(tl.nnz);
+    const int mI = __reduce_max_sync(0xffffffffu, maxI);
+    const uint32_t fla = __reduce_or_sync(0xffffffffu, tl.fl);
+    ChSumsT<double>& sm = sums[c];
+    if (lane < 10) sm.v[lane] = sv;
+    if (lane == 0) {
+      sm.I = (unsigned long long)sI;
+      sm.net = 0;
+      sm.maxI = mI;
+      tally_or(tal, fla);
+      tally_add(tal, C_CHOL_FIX, fix);
+      tally_add(tal, C_INTERP_FALLBACK, fb);
+      tally_add(tal, C_TREL_CLAMP, ncl2);
+      tally_add(tal, C_PB_CLAMP, pb);
+      tally_add(tal, C_NU_ZERO, nz);
+    }
   }
-  double s[10];
-#pragma unroll
-  for (int i = 0; i < 10; ++i) s[i] = (double)wsum(acc[i]);
-  const double sI = wsum(accI);
-  const unsigned long long fix = wsum(tl.nfix), fb = wsum(nfb), ncl2 = wsum(tl.ncl),
-                           pb = wsum(tl.npb), nz = wsum(tl.nnz);
-  const int mI = __reduce_max_sync(0xffffffffu, maxI);
-  const uint32_t fla = __reduce_or_sync(0xffffffffu, tl.fl);
-  if (lane != 0) return;
-  ChSumsT<double>& sm = sums[c];
-  for (int i = 0; i < 10; ++i) sm.v[i] = s[i];
-  sm.I = (unsigned long long)(long long)llrint(sI);
-  sm.net = 0;
-  sm.maxI = mI;
-  if (fla) atomicOr(flags, fla);
-  if (fix) atomicAdd(&counters[C_CHOL_FIX], fix);
-  if (fb) atomicAdd(&counters[C_INTERP_FALLBACK], fb);
-  if (ncl2) atomicAdd(&counters[C_TREL_CLAMP], ncl2);
-  if (pb) atomicAdd(&counters[C_PB_CLAMP], pb);
-  if (nz) atomicAdd(&counters[C_NU_ZERO], nz);
+  tally_flush(tal, flags, counters);
 }
 
 // time-average sums of the post-step state, binned by cell
@@ -804,6 +867,8 @@ struct PlaneCtx {
   PlGeom g;
   PlInflow inf;
   int recon, passes, nblk, grid_p;
+  int grid_wc, grid_tc;     // grids of the warp-per-cell and thread-per-cell passes
+  int grid_inj;             // grid of the inflow pass (grid-stride over entering particles)
   double Fnum, vol;
   long long cap;
   size_t es;
@@ -821,6 +886,7 @@ struct PlaneCtx {
   double* af;
   PlCount* cnt;
   ChCellT<double>* cells;
+  float* pend;              // FP32 copy of the pending rescale (Un, Us, s, r) per cell
   void* prm;                // PlParams<T>
   ChSumsT<double>* sums;
   double* acc;
@@ -851,23 +917,23 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   T* cy = (T*)h->st[a][3]; T* cz = (T*)h->st[a][4]; T* er = (T*)h->st[a][5];
   const int ncell = h->g.ncell;
   if (prof) prof(env.owner, 0, 1);
-  pl_advect<T><<<h->grid_p, kBlk, 0, s>>>(h->g, h->cnt, h->keycell, h->cells, x, y, cx, cy, cz,
-                                         er, h->lv[a], h->pd[a], h->kbuf[0], h->ibuf[0],
+  pl_advect<T><<<h->grid_p, kBlk, 0, s>>>(h->g, h->cnt, h->keycell, h->cells, h->pend, x, y, cx,
+                                         cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0], h->ibuf[0],
                                          h->dstep, env.sp, env.k0, env.k1, env.flags,
                                          env.counters);
   pl_inflow<<<1, 1024, 0, s>>>(h->inf, h->cnt, h->face_off, h->cap, h->dstep, env.k0, env.k1,
                                env.flags, env.counters);
   if (h->inf.nfaces > 0)
-    pl_inject<T><<<(h->inf.nfaces * 32 + kBlk - 1) / kBlk, kBlk, 0, s>>>(
+    pl_inject<T><<<h->grid_inj, kBlk, 0, s>>>(
         h->g, h->inf, h->cnt, h->face_off, x, y, cx, cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0],
         h->ibuf[0], h->dstep, env.sp, env.k0, env.k1, env.flags, env.counters);
   CHK(cudaGetLastError());
   int src = 0;
   for (int p = 0; p < h->passes; ++p) {
-    pl_hist<<<h->nblk, kRB, 0, s>>>(h->kbuf[src], h->cnt, 8 * p, h->bh, h->nblk);
-    pl_scan_digits<<<256, kRB, 0, s>>>(h->bh, h->nblk, h->tot);
+    pl_hist<<<h->nblk, kRB, 0, s>>>(h->kbuf[src], h->cnt, kDig * p, h->bh, h->nblk);
+    pl_scan_digits<<<kNB, kRB, 0, s>>>(h->bh, h->nblk, h->tot);
     pl_scatter<<<h->nblk, kRB, 0, s>>>(h->kbuf[src], h->ibuf[src], h->kbuf[src ^ 1],
-                                       h->ibuf[src ^ 1], h->cnt, 8 * p, h->bh, h->tot, h->nblk);
+                                       h->ibuf[src ^ 1], h->cnt, kDig * p, h->bh, h->tot, h->nblk);
     CHK(cudaGetLastError());
     src ^= 1;
   }
@@ -883,26 +949,27 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   cz = (T*)h->st[b][4]; er = (T*)h->st[b][5];
   if (prof) prof(env.owner, 0, 0);
   if (prof) prof(env.owner, 1, 1);
-  const int wb = (int)(((long long)ncell * 32 + 127) / 128);
+  const int wb = h->grid_wc, tb = h->grid_tc;
   const int cb = (ncell + 127) / 128;
-  ch_moments<T, double><<<wb, 128, 0, s>>>(ncell, h->off, h->af, cx, cy, cz, er, h->lv[b],
-                                           h->cells, env.sp, env.counters);
-  ch_coeffs<double><<<cb, 128, 0, s>>>(ncell, h->Fnum, h->vol, h->af, h->g.dt, h->cells, env.sp,
-                                       env.sp.omega, env.sp.Z_rot, env.flags, env.counters);
+  float* pend = env.precision == USP_FP32 ? h->pend : nullptr;
+  ch_moments<T, double><<<wb, kBlk, 0, s>>>(ncell, 32, h->off, h->af, cx, cy, cz, er, h->lv[b],
+                                            h->cells, env.sp, env.counters, pend);
+  ch_coeffs<double><<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->af, h->g.dt, h->cells, env.sp,
+                                        env.sp.omega, env.sp.Z_rot, env.flags, env.counters);
   pl_params<T><<<cb, 128, 0, s>>>(h->g, h->recon, h->cells, (PlParams<T>*)h->prm, env.sp);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 1, 0);
   if (prof) prof(env.owner, 0, 1);
-  pl_collide<T><<<wb, 128, 0, s>>>(ncell, h->cells, (const PlParams<T>*)h->prm, x, y, cx, cy, cz,
-                                   er, h->lv[b], h->pd[b], h->sums, h->dstep, env.k0, env.k1,
-                                   env.flags, env.counters);
+  pl_collide<T><<<wb, kBlk, 0, s>>>(ncell, h->cells, (const PlParams<T>*)h->prm, x, y, cx, cy,
+                                    cz, er, h->lv[b], h->pd[b], h->sums, h->dstep,
+                                    philox_round_keys(env.k0, env.k1), env.flags, env.counters);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 0, 0);
   if (prof) prof(env.owner, 1, 1);
-  ch_levelfix<double><<<wb, 128, 0, s>>>(ncell, h->cells, h->sums, h->lv[b], h->dstep, env.sp,
-                                         env.k0, env.k1, env.flags, env.counters);
-  ch_update<double><<<cb, 128, 0, s>>>(ncell, h->cells, h->sums, h->dstep, env.sp, env.flags,
-                                       env.counters);
+  ch_levelfix<double><<<wb, kBlk, 0, s>>>(ncell, 32, h->cells, h->sums, h->lv[b], h->dstep, env.sp,
+                                          env.k0, env.k1, env.flags, env.counters);
+  ch_update<double><<<tb, kBlk, 0, s>>>(ncell, h->cells, h->sums, h->dstep, env.sp, env.flags,
+                                        env.counters, pend);
   CHK(cudaGetLastError());
   if (h->sampling) {
     pl_sample<T><<<h->grid_p, kBlk, 0, s>>>(h->cnt, ncell, h->keycell, h->cells, cx, cy, cz, er,
@@ -960,7 +1027,8 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   g.dx = (pp->x1 - pp->x0) / pp->nx; g.dy = (pp->y1 - pp->y0) / pp->ny;
   g.cxc = pp->cyl_xc; g.cyc = pp->cyl_yc; g.cr = pp->cyl_r > 0 ? pp->cyl_r : 0.0;
   g.Tw = pp->T_wall; g.dt = dt;
-  for (int k = 0; k < 4; ++k) g.bc[k] = pp->bc[k];
+  g.bcbits = 0;
+  for (int k = 0; k < 4; ++k) g.bcbits |= (pp->bc[k] & 3) << (2 * k);
   h->recon = pp->reconstruct ? 1 : 0;
   h->Fnum = pp->F_num;
   h->vol = g.dx * g.dy * pp->depth;
@@ -985,9 +1053,16 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->es = env.precision == USP_FP32 ? 4 : 8;
   int bits = 1;
   while ((1 << bits) < ncell + 1) ++bits;
-  h->passes = (bits + 7) / 8;
+  h->passes = (bits + kDig - 1) / kDig;
   h->nblk = (int)std::max<long long>(1, (cap + kChunk - 1) / kChunk);
-  h->grid_p = (int)std::min<long long>(std::max<long long>(1, (cap + kBlk - 1) / kBlk), 152 * 16);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (nsm <= 0) nsm = 1;
+  h->grid_p = (int)std::min<long long>(std::max<long long>(1, (cap + kBlk - 1) / kBlk), nsm * 16);
+  h->grid_wc = (int)std::min<long long>(((long long)ncell * 32 + kBlk - 1) / kBlk, nsm * 8);
+  h->grid_tc = (int)std::min<long long>((ncell + kBlk - 1) / kBlk, nsm * 8);
+  h->grid_inj = nsm * 4;
   auto A = [&](size_t bytes) { return env.alloc(env.owner, bytes); };
   const size_t nn = (size_t)cap;
   for (int k = 0; k < 2; ++k) {
@@ -998,13 +1073,14 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
     h->ibuf[k] = (int*)A(nn * 4);
   }
   h->keycell = (int*)A(nn * 4);
-  h->bh = (int*)A((size_t)h->nblk * 256 * 4);
-  h->tot = (int*)A(256 * 4);
+  h->bh = (int*)A((size_t)h->nblk * kNB * 4);
+  h->tot = (int*)A(kNB * 4);
   h->face_off = (int*)A(sizeof(int) * (f.nfaces + 1));
   h->off = (long long*)A(sizeof(long long) * (ncell + 1));
   h->af = (double*)A(sizeof(double) * ncell);
   h->cnt = (PlCount*)A(sizeof(PlCount));
   h->cells = (ChCellT<double>*)A(sizeof(ChCellT<double>) * ncell);
+  h->pend = (float*)A(sizeof(float) * 8 * ncell);
   h->prm = A((env.precision == USP_FP32 ? sizeof(PlParams<float>) : sizeof(PlParams<double>)) *
              ncell);
   h->sums = (ChSumsT<double>*)A(sizeof(ChSumsT<double>) * ncell);
@@ -1014,7 +1090,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->mout = (double*)A(sizeof(double) * USP_NMOM * ncell);
   h->dstep = (long long*)A(sizeof(long long));
   bool ok = h->keycell && h->bh && h->tot && h->face_off && h->off && h->af && h->cnt &&
-            h->cells && h->prm && h->sums && h->acc && h->macc && h->mout && h->dstep;
+            h->cells && h->pend && h->prm && h->sums && h->acc && h->macc && h->mout && h->dstep;
   for (int k = 0; k < 2; ++k) {
     for (int q = 0; q < 6; ++q) ok = ok && h->st[k][q];
     ok = ok && h->lv[k] && h->pd[k] && h->kbuf[k] && h->ibuf[k];
@@ -1074,6 +1150,13 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   cok = cok && cudaMemcpyAsync(h->cells, hc.data(), sizeof(ChCellT<double>) * ncell,
                                cudaMemcpyHostToDevice, s) == cudaSuccess;
   cok = cok && cudaMemsetAsync(h->sums, 0, sizeof(ChSumsT<double>) * ncell, s) == cudaSuccess;
+  {
+    std::vector<float> pe((size_t)ncell * 8, 0.0f);
+    for (int c = 0; c < ncell; ++c) pe[(size_t)c * 8 + 6] = pe[(size_t)c * 8 + 7] = 1.0f;
+    cok = cok && cudaMemcpyAsync(h->pend, pe.data(), sizeof(float) * 8 * ncell,
+                                 cudaMemcpyHostToDevice, s) == cudaSuccess;
+    cok = cok && cudaStreamSynchronize(s) == cudaSuccess;
+  }
   cok = cok && cudaMemsetAsync(h->acc, 0, acc_bytes, s) == cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->dstep, &dstep0, sizeof(long long), cudaMemcpyHostToDevice, s) == cudaSuccess;
   cok = cok && cudaStreamSynchronize(s) == cudaSuccess;

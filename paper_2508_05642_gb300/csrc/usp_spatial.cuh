@@ -126,7 +126,7 @@ struct CollideTally {
 template <typename T, typename P_>
 __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx, T& vy, T& vz,
                                                   T& e, int I, uint32_t id, uint32_t step,
-                                                  uint32_t k0, uint32_t k1, CollideTally& t) {
+                                                  const PhiloxRoundKeys& rk, CollideTally& t) {
   T alpha = P.alpha, nu = P.nu_ref, ttr, trot, evr;
   bool cl;
   relax_t(P, alpha, f, ttr, trot, evr, cl);
@@ -182,11 +182,11 @@ __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx
   }
   if (cl) { t.fl |= F_TREL_CLAMP; ++t.ncl; }
   // draws
-  const U4 w = philox4x32_10(id, step, PTAG_NORMALS, 0u, k0, k1);
+  U4 w, w2;
+  philox4x32_10_pair(id, step, PTAG_NORMALS, PTAG_JUMPS, 0u, rk, w, w2);
   T g0, g1, g2, g3;
   box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
   box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
-  const U4 w2 = philox4x32_10(id, step, PTAG_JUMPS, 0u, k0, k1);
   // Eq. update_ci about the interpolated bulk velocity
   const T a2 = alpha * alpha, sq = sqrt(T(1) - a2);
   const T v0 = f[0] + alpha * (vx - f[0]) + sq * (L[0] * g0);
@@ -209,69 +209,114 @@ __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx
   return I + up - dn;
 }
 
+// Block-level tally of the status word and counters: kernels over many cells
+// add into shared memory and flush once per block, so that a counter bumped
+// by a large share of 240,000 cells does not serialise on one global address.
+struct BlockTally {
+  unsigned long long cnt[NCOUNTERS];
+  uint32_t fl;
+};
+__device__ __forceinline__ void tally_init(BlockTally& t) {
+  for (int i = threadIdx.x; i < NCOUNTERS; i += blockDim.x) t.cnt[i] = 0ull;
+  if (threadIdx.x == 0) t.fl = 0u;
+  __syncthreads();
+}
+__device__ __forceinline__ void tally_add(BlockTally& t, int k, unsigned long long v) {
+  if (v) atomicAdd(&t.cnt[k], v);
+}
+__device__ __forceinline__ void tally_or(BlockTally& t, uint32_t f) {
+  if (f) atomicOr(&t.fl, f);
+}
+__device__ __forceinline__ void tally_flush(BlockTally& t, uint32_t* flags,
+                                            unsigned long long* counters) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < NCOUNTERS; i += blockDim.x)
+    if (t.cnt[i]) atomicAdd(&counters[i], t.cnt[i]);
+  if (threadIdx.x == 0 && t.fl) atomicOr(flags, t.fl);
+}
+
+// warp-per-cell and thread-per-cell grid-stride indices
+__device__ __forceinline__ int warp_global() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ int warps_total() { return (gridDim.x * blockDim.x) >> 5; }
+
 // vibrational +-1 correction (Sec. 4.C), one warp per cell; same acceptance
 // rule as the one-at-a-time loop (see the homogeneous path)
 template <typename S>
-__global__ void ch_levelfix(int ny, const ChCellT<S>* __restrict__ cells,
+__global__ void ch_levelfix(int ny, int cpw, const ChCellT<S>* __restrict__ cells,
                             ChSumsT<S>* __restrict__ sums,
                             int* __restrict__ lev, const long long* __restrict__ dstep, Species sp,
                             uint32_t k0, uint32_t k1, uint32_t* flags,
                             unsigned long long* counters) {
+  __shared__ BlockTally tal;
+  tally_init(tal);
   const int lane = threadIdx.x & 31;
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (c >= ny) return;
-  const ChCellT<S>& cs = cells[c];
-  if (!cs.active) return;
   const uint32_t step = (uint32_t)*dstep;
   const double Rth = gasR(sp) * sp.theta_v;
-  const long long N = cs.N;
-  long long Id = 0;
-  if (lane == 0) {
-    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_IDELTA, 0u, k0, k1);
-    const double u = uniform_open<double>(w.x);
-    Id = (long long)floor((double)N * value(cs.e_vib_tgt) / Rth - (double)(long long)sums[c].I + u);
-  }
-  Id = __shfl_sync(0xffffffffu, Id, 0);
-  long long remaining = Id, draws = 0, net = 0;
-  const long long cap = 64 * N;
-  int* lv = lev + cs.off;
-  while (remaining != 0 && draws < cap) {
-    const long long j = draws + lane;
-    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_PICK, (uint32_t)(j >> 2), k0, k1);
-    const uint32_t word = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
-    const long long k = (long long)(((unsigned long long)word * (unsigned long long)N) >> 32);
-    const bool valid = j < cap;
-    bool accept;
-    if (remaining > 0) {
-      accept = valid;
-    } else {
-      const int cur = valid ? __ldcg(&lv[k]) : 0;
-      const unsigned grp = __match_any_sync(0xffffffffu, valid ? k : -1ll);
-      accept = valid && __popc(grp & lane_lt()) < cur;
+  for (long long c0 = (long long)warp_global() * cpw; c0 < ny;
+       c0 += (long long)warps_total() * cpw) {
+    const int ng = (int)(ny - c0 < cpw ? ny - c0 : cpw);
+    // I_Delta of Sec. 4.C for cell c0 + lane (FP64, one cell per lane)
+    long long myId = 0;
+    if (lane < ng) {
+      const long long c = c0 + lane;
+      const ChCellT<S>& cs = cells[c];
+      if (cs.active) {
+        const U4 w = philox4x32_10((uint32_t)c, step, CTAG_IDELTA, 0u, k0, k1);
+        const double u = uniform_open<double>(w.x);
+        myId = (long long)floor((double)cs.N * value(cs.e_vib_tgt) / Rth -
+                                (double)(long long)sums[c].I + u);
+      }
     }
-    const unsigned am = __ballot_sync(0xffffffffu, accept);
-    const long long need = remaining > 0 ? remaining : -remaining;
-    const int nacc = __popc(am);
-    const int take = (int)(nacc < need ? nacc : need);
-    const bool eff = accept && __popc(am & lane_lt()) < take;
-    __syncwarp();
-    if (eff) atomicAdd(&lv[k], remaining > 0 ? 1 : -1);
-    __syncwarp();
-    long long used = 32;
-    if (take == need && take > 0) {
-      unsigned m = am;
-      for (int i = 1; i < take; ++i) m &= m - 1;
-      used = __ffs((int)m);
+    for (int g = 0; g < ng; ++g) {
+      const long long Id = __shfl_sync(0xffffffffu, myId, g);
+      const long long c = c0 + g;
+      const ChCellT<S>& cs = cells[c];
+      if (!cs.active) continue;
+      const long long N = cs.N;
+      long long remaining = Id, draws = 0, net = 0;
+      const long long cap = 64 * N;
+      int* lv = lev + cs.off;
+      while (remaining != 0 && draws < cap) {
+        const long long j = draws + lane;
+        const U4 w = philox4x32_10((uint32_t)c, step, CTAG_PICK, (uint32_t)(j >> 2), k0, k1);
+        const uint32_t word = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
+        const long long k = (long long)(((unsigned long long)word * (unsigned long long)N) >> 32);
+        const bool valid = j < cap;
+        bool accept;
+        if (remaining > 0) {
+          accept = valid;
+        } else {
+          const int cur = valid ? __ldcg(&lv[k]) : 0;
+          const unsigned grp = __match_any_sync(0xffffffffu, valid ? k : -1ll);
+          accept = valid && __popc(grp & lane_lt()) < cur;
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, accept);
+        const long long need = remaining > 0 ? remaining : -remaining;
+        const int nacc = __popc(am);
+        const int take = (int)(nacc < need ? nacc : need);
+        const bool eff = accept && __popc(am & lane_lt()) < take;
+        __syncwarp();
+        if (eff) atomicAdd(&lv[k], remaining > 0 ? 1 : -1);
+        __syncwarp();
+        long long used = 32;
+        if (take == need && take > 0) {
+          unsigned m = am;
+          for (int i = 1; i < take; ++i) m &= m - 1;
+          used = __ffs((int)m);
+        }
+        if (draws + used > cap) used = cap - draws;
+        draws += used;
+        if (remaining > 0) { remaining -= take; net += take; }
+        else { remaining += take; net -= take; }
+      }
+      if (lane == 0) {
+        if (remaining != 0) tally_or(tal, (uint32_t)F_VIB_LOOP_CAP);
+        tally_add(tal, C_VIB_DRAWS, (unsigned long long)draws);
+        sums[c].net = net;
+      }
     }
-    if (draws + used > cap) used = cap - draws;
-    draws += used;
-    if (remaining > 0) { remaining -= take; net += take; }
-    else { remaining += take; net -= take; }
   }
-  if (lane != 0) return;
-  if (remaining != 0) atomicOr(flags, (uint32_t)F_VIB_LOOP_CAP);
-  if (draws) atomicAdd(&counters[C_VIB_DRAWS], (unsigned long long)draws);
-  sums[c].net = net;
+  tally_flush(tal, flags, counters);
 }
 
 // rescale factors of Sec. 4.C, kept pending for the next move; the step
@@ -279,38 +324,49 @@ __global__ void ch_levelfix(int ny, const ChCellT<S>* __restrict__ cells,
 template <typename S>
 __global__ void ch_update(int ny, ChCellT<S>* __restrict__ cells,
                           const ChSumsT<S>* __restrict__ sums, long long* dstep, Species sp,
-                          uint32_t* flags, unsigned long long* counters) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < ny) {
+                          uint32_t* flags, unsigned long long* counters,
+                          float* __restrict__ pend) {
+  __shared__ BlockTally tal;
+  tally_init(tal);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ny; c += gridDim.x * blockDim.x) {
     ChCellT<S>& cs = cells[c];
-    if (cs.active) {
-      const double R = gasR(sp), Rth = R * sp.theta_v;
-      const ChSumsT<S>& sm = sums[c];
-      const double invN = 1.0 / (double)cs.N;
-      const double sumI = (double)((long long)sm.I + sm.net);
-      const S er_star = sm.v[9] * invN;
-      const S r = er_star > 0.0 ? cs.e_rot_tgt / er_star : S(1.0);
-      const S e_rot_new = r * er_star;
-      const double e_vib_new = Rth * sumI * invN;
-      const S m0 = sm.v[0] * invN, m1 = sm.v[1] * invN, m2 = sm.v[2] * invN;
-      const S etr_star = 0.5 * (sm.v[3] * invN - m0 * m0 + sm.v[4] * invN - m1 * m1 +
-                                sm.v[5] * invN - m2 * m2);
-      const S e_tr_n = 0.5 * (cs.Pi[0] + cs.Pi[1] + cs.Pi[2]);
-      const S rad = (e_tr_n + R * cs.Trot + Rth * cs.ebar - e_rot_new - e_vib_new) / etr_star;
-      S Us[3] = {cs.U[0] + m0, cs.U[1] + m1, cs.U[2] + m2};
-      if (!(etr_star > 0.0) || !(rad > 0.0)) {
-        atomicOr(flags, (uint32_t)F_NEG_RADICAND);
-        atomicAdd(&counters[C_NEG_RADICAND], 1ull);
-        for (int i = 0; i < 3; ++i) { cs.Un[i] = Us[i]; cs.Us[i] = Us[i]; }
-        cs.s = S(1.0);
-      } else {
-        for (int i = 0; i < 3; ++i) { cs.Un[i] = cs.U[i]; cs.Us[i] = Us[i]; }
-        cs.s = sqrt(rad);
+    if (!cs.active) continue;
+    const double R = gasR(sp), Rth = R * sp.theta_v;
+    const ChSumsT<S>& sm = sums[c];
+    const double invN = 1.0 / (double)cs.N;
+    const double sumI = (double)((long long)sm.I + sm.net);
+    const S er_star = sm.v[9] * invN;
+    const S r = er_star > 0.0 ? cs.e_rot_tgt / er_star : S(1.0);
+    const S e_rot_new = r * er_star;
+    const double e_vib_new = Rth * sumI * invN;
+    const S m0 = sm.v[0] * invN, m1 = sm.v[1] * invN, m2 = sm.v[2] * invN;
+    const S etr_star = 0.5 * (sm.v[3] * invN - m0 * m0 + sm.v[4] * invN - m1 * m1 +
+                              sm.v[5] * invN - m2 * m2);
+    const S e_tr_n = 0.5 * (cs.Pi[0] + cs.Pi[1] + cs.Pi[2]);
+    const S rad = (e_tr_n + R * cs.Trot + Rth * cs.ebar - e_rot_new - e_vib_new) / etr_star;
+    S Us[3] = {cs.U[0] + m0, cs.U[1] + m1, cs.U[2] + m2};
+    if (!(etr_star > 0.0) || !(rad > 0.0)) {
+      tally_or(tal, (uint32_t)F_NEG_RADICAND);
+      tally_add(tal, C_NEG_RADICAND, 1ull);
+      for (int i = 0; i < 3; ++i) { cs.Un[i] = Us[i]; cs.Us[i] = Us[i]; }
+      cs.s = S(1.0);
+    } else {
+      for (int i = 0; i < 3; ++i) { cs.Un[i] = cs.U[i]; cs.Us[i] = Us[i]; }
+      cs.s = sqrt(rad);
+    }
+    cs.r = r;
+    cs.maxI = sm.maxI + 1;
+    if (pend) {   // FP32 copy for the next move of an FP32 state
+      float* pc = pend + (size_t)c * 8;
+      for (int i = 0; i < 3; ++i) {
+        pc[i] = (float)value(cs.Un[i]);
+        pc[3 + i] = (float)value(cs.Us[i]);
       }
-      cs.r = r;
-      cs.maxI = sm.maxI + 1;
+      pc[6] = (float)value(cs.s);
+      pc[7] = (float)value(cs.r);
     }
   }
+  tally_flush(tal, flags, counters);
   if (blockIdx.x == 0 && threadIdx.x == 0) *dstep += 1;
 }
 
@@ -318,88 +374,129 @@ __global__ void ch_update(int ny, ChCellT<S>* __restrict__ cells,
 // ---------------------------------------------------------------------------
 // per-cell moments and coefficients
 // ---------------------------------------------------------------------------
+// A warp takes cpw consecutive cells (1 or 32): the particle sums of each
+// cell are warp-wide FP32 (or working-precision) reductions, kept by lane k
+// for the k-th cell; the FP64 per-cell arithmetic then runs one cell per lane,
+// so each FP64 warp instruction serves up to 32 cells on the narrow FP64 pipe.
 template <typename T, typename S>
-__global__ void ch_moments(int ny, const long long* __restrict__ off, const double* __restrict__ af,
-                           const T* __restrict__ cx,
+__global__ void ch_moments(int ny, int cpw, const long long* __restrict__ off,
+                           const double* __restrict__ af, const T* __restrict__ cx,
                            const T* __restrict__ cy, const T* __restrict__ cz,
                            const T* __restrict__ er, const int* __restrict__ lev,
                            ChCellT<S>* __restrict__ cells, Species sp,
-                           unsigned long long* counters) {
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+                           unsigned long long* counters, float* __restrict__ pend) {
+  __shared__ BlockTally tal;
+  tally_init(tal);
   const int lane = threadIdx.x & 31;
-  if (c >= ny) return;
-  const long long b = off[c], e = off[c + 1], N = e - b;
-  T a0 = T(0), a1 = T(0), a2 = T(0), ae = T(0);
-  double al = 0.0;
-  for (long long j = b + lane; j < e; j += 32) {
-    a0 += cx[j]; a1 += cy[j]; a2 += cz[j]; ae += er[j]; al += (double)lev[j];
-  }
-  const S s0 = S(wsum(a0)), s1 = S(wsum(a1)), s2 = S(wsum(a2)), se = S(wsum(ae));
-  const double sl = wsum(al);
-  const double inv = N > 0 ? 1.0 / (double)N : 0.0;
-  const T m0 = (T)(s0 * inv), m1 = (T)(s1 * inv), m2 = (T)(s2 * inv);
-  T p[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-  for (long long j = b + lane; j < e; j += 32) {
-    const T C0 = cx[j] - m0, C1 = cy[j] - m1, C2 = cz[j] - m2;
-    p[0] += C0 * C0; p[1] += C1 * C1; p[2] += C2 * C2;
-    p[3] += C0 * C1; p[4] += C0 * C2; p[5] += C1 * C2;
-  }
-  S P[6];
-  for (int i = 0; i < 6; ++i) P[i] = S(wsum(p[i])) * inv;
-  if (lane != 0) return;
-  ChCellT<S>& cs = cells[c];
   const double R = gasR(sp);
-  cs.off = b;
-  cs.N = N;
-  cs.active = N >= 2;
-  // a neighbour for the reconstruction of Sec. 3.B: two or more particles and
-  // not cut by a body (af: fluid fraction, null = every cell whole)
-  cs.usable = N >= 2 && (!af || af[c] >= 1.0);
-  cs.U[0] = s0 * inv; cs.U[1] = s1 * inv; cs.U[2] = s2 * inv;
-  // identity pending rescale until the cell is updated
-  for (int i = 0; i < 3; ++i) { cs.Un[i] = S(0.0); cs.Us[i] = S(0.0); }
-  cs.s = S(1.0);
-  cs.r = S(1.0);
-  if (!cs.active) {
-    atomicAdd(&counters[C_SKIPPED_CELLS], 1ull);
-    return;
+  constexpr bool f32 = sizeof(T) == 4;
+  for (long long c0 = (long long)warp_global() * cpw; c0 < ny;
+       c0 += (long long)warps_total() * cpw) {
+    const int ng = (int)(ny - c0 < cpw ? ny - c0 : cpw);
+    T k0 = T(0), k1 = T(0), k2 = T(0), ke = T(0), kq[6];
+    long long kl = 0, kb = 0, kN = 0;
+    for (int i = 0; i < 6; ++i) kq[i] = T(0);
+    for (int g = 0; g < ng; ++g) {
+      const long long c = c0 + g;
+      const long long b = off[c], e = off[c + 1], N = e - b;
+      T a0 = T(0), a1 = T(0), a2 = T(0), ae = T(0);
+      long long al = 0;
+      for (long long j = b + lane; j < e; j += 32) {
+        a0 += cx[j]; a1 += cy[j]; a2 += cz[j]; ae += er[j]; al += lev[j];
+      }
+      const T t0 = wsum(a0), t1 = wsum(a1), t2 = wsum(a2), te = wsum(ae);
+      const long long sl = wsum(al);
+      // the reference mean of the second pass (an FP32 state keeps FP32)
+      T m0, m1, m2;
+      if constexpr (f32) {
+        const float fn = N > 0 ? (float)N : 1.0f;
+        m0 = t0 / fn; m1 = t1 / fn; m2 = t2 / fn;
+      } else {
+        const double inv = N > 0 ? 1.0 / (double)N : 0.0;
+        m0 = (T)(S(t0) * inv); m1 = (T)(S(t1) * inv); m2 = (T)(S(t2) * inv);
+      }
+      T p[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+      for (long long j = b + lane; j < e; j += 32) {
+        const T C0 = cx[j] - m0, C1 = cy[j] - m1, C2 = cz[j] - m2;
+        p[0] += C0 * C0; p[1] += C1 * C1; p[2] += C2 * C2;
+        p[3] += C0 * C1; p[4] += C0 * C2; p[5] += C1 * C2;
+      }
+      T q[6];
+      for (int i = 0; i < 6; ++i) q[i] = wsum(p[i]);
+      if (lane == g) {
+        k0 = t0; k1 = t1; k2 = t2; ke = te; kl = sl; kb = b; kN = N;
+        for (int i = 0; i < 6; ++i) kq[i] = q[i];
+      }
+    }
+    if (lane >= ng) continue;
+    const long long c = c0 + lane;
+    const long long N = kN;
+    const double inv = N > 0 ? 1.0 / (double)N : 0.0;
+    const S s0 = S(k0), s1 = S(k1), s2 = S(k2), se = S(ke);
+    S P[6];
+    for (int i = 0; i < 6; ++i) P[i] = S(kq[i]) * inv;
+    if (pend) {   // identity pending rescale (FP32 copy)
+      float* pc = pend + (size_t)c * 8;
+      pc[0] = pc[1] = pc[2] = pc[3] = pc[4] = pc[5] = 0.0f;
+      pc[6] = pc[7] = 1.0f;
+    }
+    ChCellT<S>& cs = cells[c];
+    cs.off = kb;
+    cs.N = N;
+    cs.active = N >= 2;
+    // a neighbour for the reconstruction of Sec. 3.B: two or more particles
+    // and not cut by a body (af: fluid fraction, null = every cell whole)
+    cs.usable = N >= 2 && (!af || af[c] >= 1.0);
+    cs.U[0] = s0 * inv; cs.U[1] = s1 * inv; cs.U[2] = s2 * inv;
+    // identity pending rescale until the cell is updated
+    for (int i = 0; i < 3; ++i) { cs.Un[i] = S(0.0); cs.Us[i] = S(0.0); }
+    cs.s = S(1.0);
+    cs.r = S(1.0);
+    if (!cs.active) {
+      tally_add(tal, C_SKIPPED_CELLS, 1ull);
+      continue;
+    }
+    for (int i = 0; i < 6; ++i) cs.Pi[i] = P[i];
+    cs.Ttr = (P[0] + P[1] + P[2]) / (3.0 * R);
+    cs.Trot = se * inv / R;
+    cs.ebar = (double)kl * inv;
+    cs.Tvib = T_vib_of_level<double>(sp, cs.ebar);
   }
-  for (int i = 0; i < 6; ++i) cs.Pi[i] = P[i];
-  cs.Ttr = (P[0] + P[1] + P[2]) / (3.0 * R);
-  cs.Trot = se * inv / R;
-  cs.ebar = sl * inv;
-  cs.Tvib = T_vib_of_level<double>(sp, cs.ebar);
+  tally_flush(tal, nullptr, counters);
 }
 
 template <typename S>
 __global__ void ch_coeffs(int ny, double F_num, double vol, const double* __restrict__ af,
                           double dt, ChCellT<S>* __restrict__ cells, Species sp, S omega, S zrot,
                           uint32_t* flags, unsigned long long* counters) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ny) return;
-  ChCellT<S>& cs = cells[c];
-  if (!cs.active) return;
-  const double v = af ? af[c] * vol : vol;   // fluid volume of a cut cell
-  if (!(v > 0.0)) {
-    cs.active = 0;
-    return;
+  __shared__ BlockTally tal;
+  tally_init(tal);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ny; c += gridDim.x * blockDim.x) {
+    ChCellT<S>& cs = cells[c];
+    if (!cs.active) continue;
+    const double v = af ? af[c] * vol : vol;   // fluid volume of a cut cell
+    if (!(v > 0.0)) {
+      cs.active = 0;
+      continue;
+    }
+    cs.n = (double)cs.N * F_num / v;
+    const CellCoeffsT<S> k =
+        cell_coeffs_t<S>(sp, omega, zrot, cs.n, dt, cs.Ttr, cs.Trot, S(cs.Tvib));
+    if (!k.ok) {
+      tally_or(tal, (uint32_t)F_A_NONPOS);
+      cs.active = 0;
+      continue;
+    }
+    cs.alpha = k.alpha; cs.nu_ref = k.nu_ref; cs.B = k.B; cs.mu_p = k.mu_p; cs.Pr = k.Pr;
+    cs.gtr = k.g_tr_rot; cs.gtv = k.g_tr_vib; cs.grv = k.g_rot_vib;
+    cs.e_rot_tgt = k.e_rot_tgt;
+    cs.e_vib_tgt = k.e_vib_tgt;
+    if (k.tgt_clamped) {
+      tally_or(tal, (uint32_t)F_TREL_CLAMP);
+      tally_add(tal, C_TREL_CLAMP, 1ull);
+    }
   }
-  cs.n = (double)cs.N * F_num / v;
-  const CellCoeffsT<S> k =
-      cell_coeffs_t<S>(sp, omega, zrot, cs.n, dt, cs.Ttr, cs.Trot, S(cs.Tvib));
-  if (!k.ok) {
-    atomicOr(flags, (uint32_t)F_A_NONPOS);
-    cs.active = 0;
-    return;
-  }
-  cs.alpha = k.alpha; cs.nu_ref = k.nu_ref; cs.B = k.B; cs.mu_p = k.mu_p; cs.Pr = k.Pr;
-  cs.gtr = k.g_tr_rot; cs.gtv = k.g_tr_vib; cs.grv = k.g_rot_vib;
-  cs.e_rot_tgt = k.e_rot_tgt;
-  cs.e_vib_tgt = k.e_vib_tgt;
-  if (k.tgt_clamped) {
-    atomicOr(flags, (uint32_t)F_TREL_CLAMP);
-    atomicAdd(&counters[C_TREL_CLAMP], 1ull);
-  }
+  tally_flush(tal, flags, counters);
 }
 
 template <typename S>

@@ -245,3 +245,34 @@ def test_fp32_hot_levels_match_oracle():
     assert gl.max() > 48
     assert np.mean(gl != r["ost"].lev) < 1e-5
     _check_moments(r["om"], r["gm"], r["sp"])
+
+
+def test_moments_of_dyadic_states_are_bitwise_equal():
+    """FP64 form, cells of 2^k <= 1024 particles with dyadic-rational
+    velocities (multiples of 1/8 below 32 in magnitude), energies and small
+    levels: N, U and Pi (sums of at most 52-bit terms) are exact in FP64 in any
+    order, so the GPU's equal the oracle's bit for bit; the heat fluxes (cubes)
+    agree to rounding."""
+    sp_d = I.n2_vhs_relaxation_species()
+    sp = O.species(**sp_d)
+    rng = np.random.default_rng(5)
+    sizes = [2, 4, 8, 16, 32, 64, 128, 256, 1024] * 3
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    d = lambda: rng.integers(-256, 256, n) / 8.0
+    cx, cy, cz = d(), d(), d()
+    er = np.abs(d()) * 1024
+    lev = rng.integers(0, 3, n).astype(np.int32)
+    ndens = np.full(len(sizes), 1e23)
+    dt = np.full(len(sizes), 1e-9)
+    ctx = usp.usp_init_homogeneous(sp_d, off, ndens, dt, cx, cy, cz, er, lev,
+                                   precision=usp.USP_FP64, seed=1, tile=256)
+    gm = usp.usp_moments(ctx)
+    om = O.moments(sp, off, O.State.from_arrays(cx, cy, cz, er, lev))
+    for f in list(range(0, 4)) + list(range(7, 13)):
+        assert np.array_equal(gm[f], om[f]), f
+    np.testing.assert_allclose(gm[4], om[4], rtol=1e-15)
+    np.testing.assert_allclose(gm[5], om[5], rtol=1e-15)
+    np.testing.assert_allclose(gm[6], om[6], rtol=1e-13)
+    scale = np.abs(om[13:22]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(gm[13:22] - om[13:22]) <= 1e-13 * scale)

@@ -552,3 +552,42 @@ def test_positivity_fix_keeps_stress_relaxation():
     m1 = O.moments(sp, off, st)
     s0, s1 = _sigma_q(m0)[0], _sigma_q(m1)[0]
     assert np.allclose(s1, cc.B * s0, atol=R * T * math.sqrt(8.0 / N) * 4)
+
+
+def test_moments_match_brute_force_definitions():
+    """Sec. 2.A moments of small cells (N <= 8) against their definitions
+    evaluated term by term: U = <c>, Pi = <C C>, T_tr = tr(Pi)/3R, T_rot =
+    <eps>/R, T_vib from <I>, q_tr = <C |C|^2 / 2>, q_rot = <C eps>, q_vib =
+    <C I R Theta> (C = c - U); dyadic-rational states make every sum exact."""
+    sp = O.species(**I.n2_vhs_relaxation_species())
+    R = O.R(sp)
+    rng = np.random.default_rng(17)
+    sizes = [1, 2, 3, 5, 8, 8, 4]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    d = lambda: rng.integers(-64, 64, n) / 8.0
+    st = O.State.from_arrays(d() * 100, d() * 100, d() * 100, np.abs(d()) * R * 50,
+                             rng.integers(0, 4, n))
+    m = O.moments(sp, off, st)
+    for ci, N in enumerate(sizes):
+        b, e = off[ci], off[ci + 1]
+        c = np.stack([st.cx[b:e], st.cy[b:e], st.cz[b:e]], axis=1)
+        U = sum(c[k] for k in range(N)) / N
+        C = c - U
+        Pi = [sum(C[k, i] * C[k, j] for k in range(N)) / N
+              for i, j in ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))]
+        eps, lev = st.erot[b:e], st.lev[b:e]
+        assert m[0, ci] == N
+        assert np.array_equal(m[1:4, ci], U)
+        assert np.array_equal(m[7:13, ci], Pi)
+        assert m[4, ci] == pytest.approx((Pi[0] + Pi[1] + Pi[2]) / (3 * R), rel=1e-15)
+        assert m[5, ci] == pytest.approx(eps.mean() / R, rel=1e-15)
+        ebar = lev.mean()
+        Tv = 0.0 if ebar == 0 else sp.theta_v / math.log(1.0 + 1.0 / ebar)
+        assert m[6, ci] == pytest.approx(Tv, rel=1e-14)
+        q = [sum(0.5 * (C[k] @ C[k]) * C[k, i] for k in range(N)) / N for i in range(3)]
+        assert np.array_equal(m[13:16, ci], q)
+        assert np.array_equal(m[16:19, ci], [sum(C[k, i] * eps[k] for k in range(N)) / N
+                                              for i in range(3)])
+        qv = [sum(C[k, i] * lev[k] for k in range(N)) / N * R * sp.theta_v for i in range(3)]
+        np.testing.assert_allclose(m[19:22, ci], qv, rtol=1e-15, atol=1e-300)

@@ -253,3 +253,24 @@ def test_cylinder_run_keeps_the_body_empty_and_books_every_particle():
     xs = pl.x0 + (np.arange(nx) + 0.5) * (pl.x1 - pl.x0) / nx
     ahead = (xs > -r - 0.05) & (xs < -r)
     assert counts[0, ahead].mean() > 1.5 * 10
+
+
+def test_reconstructed_temperature_is_the_trace_of_reconstructed_stress():
+    """T_tr = tr(Pi)/3R holds at every particle position when it holds for the
+    cell averages: the reconstruction of Sec. 3.B is linear in the cell values."""
+    pl, dx, dy, xc, yc = _grid()
+    nx, ny = pl.nx, pl.ny
+    R = 296.9
+    rng = np.random.default_rng(9)
+    F = rng.uniform(1.0, 2.0, (nx * ny, O.NFIELD)) * 1e4
+    F[:, 3] = (F[:, 6] + F[:, 7] + F[:, 8]) / (3 * R)
+    counts = np.full(nx * ny, 5, dtype=np.int64)
+    counts[rng.integers(0, nx * ny, 6)] = 1
+    af = np.ones(nx * ny)
+    af[rng.integers(0, nx * ny, 4)] = 0.5
+    for cell in range(nx * ny):
+        i, j = cell % nx, cell // nx
+        x = xc[i] + rng.uniform(-0.5, 0.5) * dx
+        y = yc[j] + rng.uniform(-0.5, 0.5) * dy
+        f = O.plane_reconstruct(pl, counts, af, F, cell, x, y)
+        assert f[3] == pytest.approx((f[6] + f[7] + f[8]) / (3 * R), rel=1e-12)
