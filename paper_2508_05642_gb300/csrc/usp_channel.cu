@@ -560,7 +560,7 @@ int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
   const int wb = (h->ny * 32 + 127) / 128;
   const int cb = (h->ny + 127) / 128;
   ch_moments<T, S><<<wb, 128, 0, s>>>(h->ny, 1, h->off, nullptr, cx, cy, cz, er, h->lv[b], cells,
-                                      env.sp, env.counters, nullptr);
+                                      env.sp, env.counters, nullptr, (T*)nullptr, nullptr);
   ch_coeffs<S><<<cb, 128, 0, s>>>(h->ny, h->Fnum, h->area * h->dy, nullptr, h->dt, cells, env.sp,
                                   omega, zrot, env.flags, env.counters);
   ch_recon<T, S><<<cb, 128, 0, s>>>(h->ny, h->dy, h->recon, h->dt, cells, (ChParams<T>*)h->prm,

@@ -44,8 +44,9 @@ struct Species {
   double m, d_ref, omega, T_ref, c_alpha, theta_v, Z_rot, Z_vib;
   int zmodel;
   double Zrot_inf, T_star, C1, C2, sigma_vib;
-  // derived on the host: T_ref^omega and pi d_ref^2 / sigma_vib
-  double Tref_w, zv_ht;
+  // derived on the host: T_ref^omega, pi d_ref^2 / sigma_vib, R = k_B / m,
+  // and the VSS mu_ref and tau_c / (mu / p) at this omega
+  double Tref_w, zv_ht, R, mu_ref0, tauf0;
 };
 
 // ---------------------------------------------------------------------------
@@ -289,7 +290,7 @@ __device__ __forceinline__ int sample_b(int n, T p, T u, uint32_t& fl) {
 // ---------------------------------------------------------------------------
 // Closed forms (FP64, per cell).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double gasR(const Species& s) { return kB / s.m; }
+__device__ __forceinline__ double gasR(const Species& s) { return s.R; }
 
 // The per-cell closed forms below are templates over the scalar S: double
 // for the plain forms, a derivative number for the gradient form (with the
@@ -382,11 +383,18 @@ __device__ inline CellCoeffsT<S> cell_coeffs_t(const Species& s, const S& omega,
   const S p = n * kB * Ttr;
   // (T/T_ref)^omega, shared by the viscosity and the collision numbers
   const S xw = exp(omega * log(Ttr / s.T_ref));
-  const double ca = s.c_alpha;
-  const S mu_ref = 5.0 * (ca + 1.0) * (ca + 2.0) * sqrt(s.m * kB * s.T_ref / kPi) /
-                   (4.0 * ca * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega) * s.d_ref * s.d_ref);
+  S mu_ref, tauf;
+  if constexpr (sizeof(S) == sizeof(double)) {   // plain forms: species constants
+    mu_ref = S(s.mu_ref0);
+    tauf = S(s.tauf0);
+  } else {                                        // derivative form: through omega
+    const double ca = s.c_alpha;
+    mu_ref = 5.0 * (ca + 1.0) * (ca + 2.0) * sqrt(s.m * kB * s.T_ref / kPi) /
+             (4.0 * ca * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega) * s.d_ref * s.d_ref);
+    tauf = tau_c_factor_w<S>(s, omega);
+  }
   c.mu_p = mu_ref * xw / p;
-  const S tau_c = tau_c_factor_w<S>(s, omega) * c.mu_p;
+  const S tau_c = tauf * c.mu_p;
   S zr, zv;
   collision_numbers<S>(s, Ttr, xw, zrot, zr, zv);
   const S tau_rot = zr * tau_c, tau_vib = zv * tau_c;

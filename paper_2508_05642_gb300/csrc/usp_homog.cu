@@ -785,21 +785,32 @@ moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
                const T* __restrict__ cy, const T* __restrict__ cz, const T* __restrict__ er,
                const int* __restrict__ lev, double* __restrict__ acc_out) {
   __shared__ double red[kBlock / 32][15];
+  __shared__ T cp[11];   // U (3), U* (3), s, r, pass-0 mean (3) in T
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const Tile tl = tiles[t];
     const CellState& cs = cells[tl.cell];
     const long long base = cs.off + tl.start;
+    // the tile's cell constants, converted once (one value per thread: the
+    // FP64 pipe is narrow, so no per-thread FP64 work per tile)
+    if (threadIdx.x < 11) {
+      const int i = threadIdx.x;
+      double v;
+      if (i < 3) v = cs.U[i];
+      else if (i < 6) v = cs.Us[i - 3];
+      else if (i == 6) v = cs.s;
+      else if (i == 7) v = cs.r;
+      else v = (pass == 1 && cs.N > 0)
+                   ? acc_out[(size_t)tl.cell * kMomAcc + (i - 8)] / (double)cs.N : 0.0;
+      cp[i] = (T)v;
+    }
+    __syncthreads();
     T a[15];
     for (int i = 0; i < 15; ++i) a[i] = T(0);
-    T mean[3] = {T(0), T(0), T(0)};
-    if (pass == 1 && cs.N > 0) {
-      for (int i = 0; i < 3; ++i)
-        mean[i] = (T)(acc_out[(size_t)tl.cell * kMomAcc + i] / (double)cs.N);
-    }
-    const T U0 = (T)cs.U[0], U1 = (T)cs.U[1], U2 = (T)cs.U[2];
-    const T S0 = (T)cs.Us[0], S1 = (T)cs.Us[1], S2 = (T)cs.Us[2];
-    const T sc = (T)cs.s, rc = (T)cs.r;
+    const T U0 = cp[0], U1 = cp[1], U2 = cp[2];
+    const T S0 = cp[3], S1 = cp[4], S2 = cp[5];
+    const T sc = cp[6], rc = cp[7];
+    const T mean0 = cp[8], mean1 = cp[9], mean2 = cp[10];
     for (int k = threadIdx.x; k < tl.count; k += kBlock) {
       const long long e = base + k;
       const T c0 = U0 + sc * (cx[e] - S0);
@@ -810,7 +821,7 @@ moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
       if (pass == 0) {
         a[0] += c0; a[1] += c1; a[2] += c2; a[3] += ep; a[4] += li;
       } else {
-        const T C0 = c0 - mean[0], C1 = c1 - mean[1], C2 = c2 - mean[2];
+        const T C0 = c0 - mean0, C1 = c1 - mean1, C2 = c2 - mean2;
         const T q = T(0.5) * (C0 * C0 + C1 * C1 + C2 * C2);
         a[0] += C0 * C0; a[1] += C1 * C1; a[2] += C2 * C2;
         a[3] += C0 * C1; a[4] += C0 * C2; a[5] += C1 * C2;
@@ -820,10 +831,13 @@ moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
       }
     }
     const int na = pass == 0 ? 5 : 15;
+    // warp totals; lane i < na converts total i (one conversion per warp)
+    T mine = T(0);
     for (int i = 0; i < na; ++i) {
       const T s = warp_sum(a[i]);
-      if (lane == 0) red[wid][i] = (double)s;
+      mine = lane == i ? s : mine;
     }
+    if (lane < na) red[wid][lane] = (double)mine;
     __syncthreads();
     if (threadIdx.x < na) {
       double s = 0.0;
@@ -1039,6 +1053,11 @@ Species to_dev(const usp_species* s) {
   d.C2 = s->C2; d.sigma_vib = s->sigma_vib;
   d.Tref_w = std::pow(s->T_ref, s->omega);
   d.zv_ht = s->sigma_vib > 0 ? kPi * s->d_ref * s->d_ref / s->sigma_vib : 0.0;
+  d.R = kB / s->m;
+  const double ca = s->c_alpha, w = s->omega;
+  d.mu_ref0 = 5.0 * (ca + 1.0) * (ca + 2.0) * std::sqrt(s->m * kB * s->T_ref / kPi) /
+              (4.0 * ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) * s->d_ref * s->d_ref);
+  d.tauf0 = ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (ca + 1.0) * (ca + 2.0));
   return d;
 }
 

@@ -79,10 +79,10 @@ struct PlParams {
   T alpha, nu_ref, B, mu_p, Pr, gtr, gtv, grv;
   T R, theta, dt;
   T xc, yc;
-  T hx[2], hy[2], hxy[4];   // (neighbour - cell) offsets: dx, dy and dx dy per choice
   T F[kNF];
-  int xcell[2], ycell[2];   // neighbour used for sx / sy < 0 ([0]) and >= 0 ([1]), -1 none
-  int dcell[4];             // quadrant (sy >= 0) * 2 + (sx >= 0): diagonal, -1 none
+  // the bilinear polynomial of each quadrant (sx, sy = 0 below / 1 at or
+  // above the centroid): f = F + gx[sx] dx + gy[sy] dy + gxy[2 sy + sx] dx dy
+  T gx[2][kNF], gy[2][kNF], gxy[4][kNF];
   int active, pad;
 };
 
@@ -632,6 +632,7 @@ __global__ void pl_gather(PlCount* __restrict__ cnt, int ncell,
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict__ cells,
+                          const T* __restrict__ fT, const int* __restrict__ usable_c,
                           PlParams<T>* __restrict__ prm, Species sp) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
@@ -645,27 +646,45 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
   const int i = c % g.nx, j = c / g.nx;
   P.xc = (T)(g.x0 + (i + 0.5) * g.dx);
   P.yc = (T)(g.y0 + (j + 0.5) * g.dy);
-  double f[kNF];
-  cell_fields(cs, f);
-  for (int k = 0; k < kNF; ++k) P.F[k] = (T)f[k];
+  const T* f = fT + (size_t)c * kNF;
+  for (int k = 0; k < kNF; ++k) P.F[k] = f[k];
   auto usable = [&](int ii, int jj) {
-    return recon && ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && cells[jj * g.nx + ii].usable;
+    return recon && ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && usable_c[jj * g.nx + ii];
   };
+  // slopes in the working precision from the cell values, times 1/offset
+  const T idx = (T)(1.0 / g.dx), idy = (T)(1.0 / g.dy);
   int ix[2], jy[2];
-  for (int s = 0; s < 2; ++s) {
-    const int sg = s ? 1 : -1;
-    ix[s] = usable(i + sg, j) ? i + sg : (usable(i - sg, j) ? i - sg : -1);
-    jy[s] = usable(i, j + sg) ? j + sg : (usable(i, j - sg) ? j - sg : -1);
-    P.xcell[s] = ix[s] >= 0 ? j * g.nx + ix[s] : -1;
-    P.ycell[s] = jy[s] >= 0 ? jy[s] * g.nx + i : -1;
-    P.hx[s] = ix[s] >= 0 ? (T)((ix[s] - i) * g.dx) : T(1);
-    P.hy[s] = jy[s] >= 0 ? (T)((jy[s] - j) * g.dy) : T(1);
+  for (int sd = 0; sd < 2; ++sd) {
+    const int sg = sd ? 1 : -1;
+    ix[sd] = usable(i + sg, j) ? i + sg : (usable(i - sg, j) ? i - sg : -1);
+    jy[sd] = usable(i, j + sg) ? j + sg : (usable(i, j - sg) ? j - sg : -1);
+    if (ix[sd] >= 0) {
+      const T* fn = fT + (size_t)(j * g.nx + ix[sd]) * kNF;
+      const T ih = ix[sd] > i ? idx : -idx;
+      for (int k = 0; k < kNF; ++k) P.gx[sd][k] = (fn[k] - f[k]) * ih;
+    } else {
+      for (int k = 0; k < kNF; ++k) P.gx[sd][k] = T(0);
+    }
+    if (jy[sd] >= 0) {
+      const T* fn = fT + (size_t)(jy[sd] * g.nx + i) * kNF;
+      const T ih = jy[sd] > j ? idy : -idy;
+      for (int k = 0; k < kNF; ++k) P.gy[sd][k] = (fn[k] - f[k]) * ih;
+    } else {
+      for (int k = 0; k < kNF; ++k) P.gy[sd][k] = T(0);
+    }
   }
   for (int q = 0; q < 4; ++q) {
     const int sx = q & 1, sy = q >> 1;
     const bool d = ix[sx] >= 0 && jy[sy] >= 0 && usable(ix[sx], jy[sy]);
-    P.dcell[q] = d ? jy[sy] * g.nx + ix[sx] : -1;
-    P.hxy[q] = d ? (T)((double)((ix[sx] - i) * (jy[sy] - j)) * g.dx * g.dy) : T(1);
+    if (d) {
+      const T* fd = fT + (size_t)(jy[sy] * g.nx + ix[sx]) * kNF;
+      const T* fx = fT + (size_t)(j * g.nx + ix[sx]) * kNF;
+      const T* fy = fT + (size_t)(jy[sy] * g.nx + i) * kNF;
+      const T ih = ((ix[sx] > i) == (jy[sy] > j) ? T(1) : T(-1)) * idx * idy;
+      for (int k = 0; k < kNF; ++k) P.gxy[q][k] = (fd[k] - fx[k] - fy[k] + f[k]) * ih;
+    } else {
+      for (int k = 0; k < kNF; ++k) P.gxy[q][k] = T(0);
+    }
   }
   prm[c] = P;
 }
@@ -702,23 +721,13 @@ __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<d
     for (long long j = cs.off + lane; j < cs.off + cs.N; j += 32) {
       const T ddx = x[j] - P.xc, ddy = y[j] - P.yc;
       const int sx = ddx >= T(0) ? 1 : 0, sy = ddy >= T(0) ? 1 : 0;
-      const int xc = P.xcell[sx], yc = P.ycell[sy], dc = P.dcell[sy * 2 + sx];
+      const T dxy = ddx * ddy;
+      const T* gx = P.gx[sx];
+      const T* gy = P.gy[sy];
+      const T* gxy = P.gxy[sy * 2 + sx];
       T f[kNF];
 #pragma unroll
-      for (int i = 0; i < kNF; ++i) {
-        const T p0 = P.F[i];
-        T v = p0, px = T(0), py = T(0);
-        if (xc >= 0) {
-          px = prm[xc].F[i];
-          v += (px - p0) * ddx / P.hx[sx];
-        }
-        if (yc >= 0) {
-          py = prm[yc].F[i];
-          v += (py - p0) * ddy / P.hy[sy];
-        }
-        if (dc >= 0) v += (prm[dc].F[i] - px - py + p0) * ddx * ddy / P.hxy[sy * 2 + sx];
-        f[i] = v;
-      }
+      for (int i = 0; i < kNF; ++i) f[i] = P.F[i] + gx[i] * ddx + gy[i] * ddy + gxy[i] * dxy;
       if (!(f[3] > T(0)) || !(f[4] > T(0)) || !(f[5] >= T(0))) {
 #pragma unroll
         for (int i = 0; i < kNF; ++i) f[i] = P.F[i];
@@ -887,6 +896,8 @@ struct PlaneCtx {
   PlCount* cnt;
   ChCellT<double>* cells;
   float* pend;              // FP32 copy of the pending rescale (Un, Us, s, r) per cell
+  void* fT;                 // cell fields in the particle precision (ncell x 13)
+  int* usable_c;            // reconstruction-neighbour flag per cell
   void* prm;                // PlParams<T>
   ChSumsT<double>* sums;
   double* acc;
@@ -953,10 +964,12 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   const int cb = (ncell + 127) / 128;
   float* pend = env.precision == USP_FP32 ? h->pend : nullptr;
   ch_moments<T, double><<<wb, kBlk, 0, s>>>(ncell, 32, h->off, h->af, cx, cy, cz, er, h->lv[b],
-                                            h->cells, env.sp, env.counters, pend);
+                                            h->cells, env.sp, env.counters, pend, (T*)h->fT,
+                                            h->usable_c);
   ch_coeffs<double><<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->af, h->g.dt, h->cells, env.sp,
                                         env.sp.omega, env.sp.Z_rot, env.flags, env.counters);
-  pl_params<T><<<cb, 128, 0, s>>>(h->g, h->recon, h->cells, (PlParams<T>*)h->prm, env.sp);
+  pl_params<T><<<cb, 128, 0, s>>>(h->g, h->recon, h->cells, (const T*)h->fT, h->usable_c,
+                                  (PlParams<T>*)h->prm, env.sp);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 1, 0);
   if (prof) prof(env.owner, 0, 1);
@@ -1081,6 +1094,8 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->cnt = (PlCount*)A(sizeof(PlCount));
   h->cells = (ChCellT<double>*)A(sizeof(ChCellT<double>) * ncell);
   h->pend = (float*)A(sizeof(float) * 8 * ncell);
+  h->fT = A(h->es * kNF * ncell);
+  h->usable_c = (int*)A(sizeof(int) * ncell);
   h->prm = A((env.precision == USP_FP32 ? sizeof(PlParams<float>) : sizeof(PlParams<double>)) *
              ncell);
   h->sums = (ChSumsT<double>*)A(sizeof(ChSumsT<double>) * ncell);
@@ -1090,7 +1105,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->mout = (double*)A(sizeof(double) * USP_NMOM * ncell);
   h->dstep = (long long*)A(sizeof(long long));
   bool ok = h->keycell && h->bh && h->tot && h->face_off && h->off && h->af && h->cnt &&
-            h->cells && h->pend && h->prm && h->sums && h->acc && h->macc && h->mout && h->dstep;
+            h->cells && h->pend && h->fT && h->usable_c && h->prm && h->sums && h->acc && h->macc && h->mout && h->dstep;
   for (int k = 0; k < 2; ++k) {
     for (int q = 0; q < 6; ++q) ok = ok && h->st[k][q];
     ok = ok && h->lv[k] && h->pd[k] && h->kbuf[k] && h->ibuf[k];

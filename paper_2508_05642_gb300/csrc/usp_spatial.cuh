@@ -384,7 +384,8 @@ __global__ void ch_moments(int ny, int cpw, const long long* __restrict__ off,
                            const T* __restrict__ cy, const T* __restrict__ cz,
                            const T* __restrict__ er, const int* __restrict__ lev,
                            ChCellT<S>* __restrict__ cells, Species sp,
-                           unsigned long long* counters, float* __restrict__ pend) {
+                           unsigned long long* counters, float* __restrict__ pend,
+                           T* __restrict__ fT, int* __restrict__ usable_c) {
   __shared__ BlockTally tal;
   tally_init(tal);
   const int lane = threadIdx.x & 31;
@@ -447,6 +448,7 @@ __global__ void ch_moments(int ny, int cpw, const long long* __restrict__ off,
     // a neighbour for the reconstruction of Sec. 3.B: two or more particles
     // and not cut by a body (af: fluid fraction, null = every cell whole)
     cs.usable = N >= 2 && (!af || af[c] >= 1.0);
+    if (usable_c) usable_c[c] = cs.usable;
     cs.U[0] = s0 * inv; cs.U[1] = s1 * inv; cs.U[2] = s2 * inv;
     // identity pending rescale until the cell is updated
     for (int i = 0; i < 3; ++i) { cs.Un[i] = S(0.0); cs.Us[i] = S(0.0); }
@@ -461,6 +463,12 @@ __global__ void ch_moments(int ny, int cpw, const long long* __restrict__ off,
     cs.Trot = se * inv / R;
     cs.ebar = (double)kl * inv;
     cs.Tvib = T_vib_of_level<double>(sp, cs.ebar);
+    if (fT) {   // the 13 fields in the particle precision, for the stencils
+      T* o = fT + (size_t)c * kNF;
+      for (int i = 0; i < 3; ++i) o[i] = (T)cs.U[i];
+      o[3] = (T)cs.Ttr; o[4] = (T)cs.Trot; o[5] = (T)cs.Tvib;
+      for (int i = 0; i < 6; ++i) o[6 + i] = (T)cs.Pi[i];
+    }
   }
   tally_flush(tal, nullptr, counters);
 }
