@@ -410,10 +410,10 @@ __device__ inline CellCoeffsT<S> cell_coeffs_t(const Species& s, const S& omega,
   const S evT = e_vib_T<S>(s, Tvib);
   S x = cv_vib_T<S>(s, Ttr);
   for (int it = 0; it < 50; ++it) {
-    const S den = ctr + gr * crot + gv * x;
-    const S gtr = 2.0 * gr * ctr * crot / den;
-    const S gtv = 2.0 * gv * ctr * x / den;
-    const S Tc = Ttr + (0.5 * gtr * (Trot - Ttr) + 0.5 * gtv * (Tvib - Ttr)) / ctr;
+    // T_check = T_tr + (gamma_tr-rot/2 (T_rot - T_tr) + gamma_tr-vib/2 (T_vib - T_tr)) / c_tr
+    // with gamma / 2 c_tr = g c / den: one division per pass
+    const S idn = 1.0 / (ctr + gr * crot + gv * x);
+    const S Tc = Ttr + (gr * crot * (Trot - Ttr) + gv * x * (Tvib - Ttr)) * idn;
     const S scale = fmax(fabs(Tc), fabs(Tvib));
     const S xn = (fabs(Tc - Tvib) <= 1e-9 * scale) ? cv_vib_T<S>(s, Tvib)
                                                     : (e_vib_T<S>(s, Tc) - evT) / (Tc - Tvib);
@@ -421,10 +421,10 @@ __device__ inline CellCoeffsT<S> cell_coeffs_t(const Species& s, const S& omega,
     x = xn;
     if (ch <= 1e-14 * fabs(xn)) break;
   }
-  const S den = ctr + gr * crot + gv * x;
-  c.g_tr_rot = 2.0 * gr * ctr * crot / den;
-  c.g_tr_vib = 2.0 * gv * ctr * x / den;
-  c.g_rot_vib = 2.0 * gr * gv * crot * x / den;
+  const S idn = 1.0 / (ctr + gr * crot + gv * x);
+  c.g_tr_rot = 2.0 * gr * ctr * crot * idn;
+  c.g_tr_vib = 2.0 * gv * ctr * x * idn;
+  c.g_rot_vib = 2.0 * gr * gv * crot * x * idn;
   c.e_rot_tgt = crot * Trot + c.g_tr_rot * (Ttr - Trot) - c.g_rot_vib * (Trot - Tvib);
   c.e_vib_tgt = evT + c.g_tr_vib * (Ttr - Tvib) + c.g_rot_vib * (Trot - Tvib);
   // far above tau_rot the exchange terms can overshoot below zero: such a

@@ -890,13 +890,13 @@ __global__ void reset_pending(int ncell, CellState* cells, CellSums* sums) {
 // Scatter an unpadded host-layout state (type S) into the padded device
 // layout (type T), or gather back with the pending rescale applied.
 template <typename S, typename T>
-__global__ void scatter_state(int ncell, const CellState* __restrict__ cells,
+__global__ void scatter_state(int c_begin, int ncell, const CellState* __restrict__ cells,
                               const long long* __restrict__ uoff, const S* __restrict__ ix,
                               const S* __restrict__ iy, const S* __restrict__ iz,
                               const S* __restrict__ ie, const int* __restrict__ il,
                               T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ cz,
                               T* __restrict__ er, int* __restrict__ lev) {
-  for (int c = blockIdx.y; c < ncell; c += gridDim.y) {
+  for (int c = c_begin + blockIdx.y; c < ncell; c += gridDim.y) {
   const long long b = uoff[c], n = uoff[c + 1] - b, o = cells[c].off;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
@@ -1001,6 +1001,10 @@ struct usp_ctx {
   cudaGraph_t graph;
   long long device_bytes;
   std::vector<void*> owned;
+  void* stage;              // host-path staging buffer, kept between calls
+  size_t stage_bytes;
+  cudaStream_t copy_stream; // host-path uploads, overlapped with the scatter
+  cudaEvent_t up_ev[9];     // upload pipeline: start + one per chunk
   // per-kernel event timing
   int profiling;
   std::vector<cudaEvent_t> ev_pool;
@@ -1262,13 +1266,22 @@ int init_params(usp_ctx* c) {
   return USP_OK;
 }
 
+// The host paths stage the state in one device buffer, allocated on first use
+// and kept (the largest request so far), so a call makes no allocation.
+void* staging(usp_ctx* c, size_t bytes) {
+  if (c->stage && c->stage_bytes >= bytes) return c->stage;
+  if (c->stage) dev_release(c, c->stage);
+  c->stage = dev_alloc(c, bytes);
+  c->stage_bytes = c->stage ? bytes : 0;
+  return c->stage;
+}
+
 int upload_state(usp_ctx* c, const void* hx, const void* hy, const void* hz, const void* he,
                  const int32_t* hl, bool host_is_native) {
   const long long n = c->nparticles;
   const size_t es = host_is_native ? (c->precision == USP_FP32 ? 4 : 8) : 8;
-  // staging buffers (unpadded), reused across calls
   static_assert(sizeof(int) == 4, "int32");
-  void* st = dev_alloc(c, (size_t)n * (4 * es + 4) + 64);
+  void* st = staging(c, (size_t)n * (4 * es + 4) + 64);
   if (!st) return USP_ENOMEM;
   char* p = (char*)st;
   void* sx = p; void* sy = p + n * es; void* sz = p + 2 * n * es; void* se = p + 3 * n * es;
@@ -1285,26 +1298,74 @@ int upload_state(usp_ctx* c, const void* hx, const void* hy, const void* hz, con
   if (c->precision == USP_FP32) {
     if (es == 4)
       scatter_state<float, float><<<grid, 256, 0, c->stream>>>(
-          c->ncell, c->cells, c->uoff, (const float*)sx, (const float*)sy, (const float*)sz,
+          0, c->ncell, c->cells, c->uoff, (const float*)sx, (const float*)sy, (const float*)sz,
           (const float*)se, sl, (float*)c->cx, (float*)c->cy, (float*)c->cz, (float*)c->er, c->lev);
     else
       scatter_state<double, float><<<grid, 256, 0, c->stream>>>(
-          c->ncell, c->cells, c->uoff, (const double*)sx, (const double*)sy, (const double*)sz,
+          0, c->ncell, c->cells, c->uoff, (const double*)sx, (const double*)sy, (const double*)sz,
           (const double*)se, sl, (float*)c->cx, (float*)c->cy, (float*)c->cz, (float*)c->er, c->lev);
   } else {
     scatter_state<double, double><<<grid, 256, 0, c->stream>>>(
-        c->ncell, c->cells, c->uoff, (const double*)sx, (const double*)sy, (const double*)sz,
+        0, c->ncell, c->cells, c->uoff, (const double*)sx, (const double*)sy, (const double*)sz,
         (const double*)se, sl, (double*)c->cx, (double*)c->cy, (double*)c->cz, (double*)c->er,
         c->lev);
   }
   CK(cudaGetLastError());
   c->launches += 1;
-  CK(cudaStreamSynchronize(c->stream));
-  // release the staging buffer
-  if (c->cfg.alloc && c->cfg.free_) c->cfg.free_(st, c->cfg.alloc_user);
-  else if (!c->cfg.alloc) cudaFree(st);
-  c->owned.erase(std::find(c->owned.begin(), c->owned.end(), st));
-  c->device_bytes -= (long long)(((size_t)n * (4 * es + 4) + 64 + 255) & ~(size_t)255);
+  return USP_OK;
+}
+
+// Upload of a native-precision host state in 8 chunks of whole cells: the
+// copies of chunk k+1 (on a copy stream) overlap the scatter of chunk k into
+// the padded device layout (on the context stream).
+int upload_state_pipelined(usp_ctx* c, const void* hx, const void* hy, const void* hz,
+                           const void* he, const int32_t* hl) {
+  constexpr int K = 8;
+  const long long n = c->nparticles;
+  const size_t es = c->precision == USP_FP32 ? 4 : 8;
+  void* st = staging(c, (size_t)n * (4 * es + 4) + 64);
+  if (!st) return USP_ENOMEM;
+  if (!c->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    for (int k = 0; k <= K; ++k) CK(cudaEventCreateWithFlags(&c->up_ev[k], cudaEventDisableTiming));
+  }
+  char* p = (char*)st;
+  char* dst[5] = {p, p + n * es, p + 2 * n * es, p + 3 * n * es, p + 4 * n * es};
+  const char* src[5] = {(const char*)hx, (const char*)hy, (const char*)hz, (const char*)he,
+                        (const char*)hl};
+  const size_t sz[5] = {es, es, es, es, 4};
+  // the staging buffer is free once the context stream has passed this point
+  CK(cudaEventRecord(c->up_ev[0], c->stream));
+  CK(cudaStreamWaitEvent(c->copy_stream, c->up_ev[0], 0));
+  reset_pending<<<(c->ncell + 127) / 128, 128, 0, c->stream>>>(c->ncell, c->cells, c->sums);
+  CK(cudaGetLastError());
+  c->launches += 1;
+  int cb = 0;
+  for (int k = 0; k < K; ++k) {
+    const int ca = cb;
+    const long long target = n * (k + 1) / K;
+    while (cb < c->ncell && (c->h_uoff[cb + 1] <= target || k == K - 1)) ++cb;
+    if (cb == ca) continue;
+    const long long b = c->h_uoff[ca], e = c->h_uoff[cb];
+    for (int f = 0; f < 5; ++f)
+      CK(cudaMemcpyAsync(dst[f] + b * sz[f], src[f] + b * sz[f], (e - b) * sz[f],
+                         cudaMemcpyHostToDevice, c->copy_stream));
+    CK(cudaEventRecord(c->up_ev[k + 1], c->copy_stream));
+    CK(cudaStreamWaitEvent(c->stream, c->up_ev[k + 1], 0));
+    dim3 grid(64, std::min(cb - ca, 65535));
+    if (c->precision == USP_FP32)
+      scatter_state<float, float><<<grid, 256, 0, c->stream>>>(
+          ca, cb, c->cells, c->uoff, (const float*)dst[0], (const float*)dst[1],
+          (const float*)dst[2], (const float*)dst[3], (const int*)dst[4], (float*)c->cx,
+          (float*)c->cy, (float*)c->cz, (float*)c->er, c->lev);
+    else
+      scatter_state<double, double><<<grid, 256, 0, c->stream>>>(
+          ca, cb, c->cells, c->uoff, (const double*)dst[0], (const double*)dst[1],
+          (const double*)dst[2], (const double*)dst[3], (const int*)dst[4], (double*)c->cx,
+          (double*)c->cy, (double*)c->cz, (double*)c->er, c->lev);
+    CK(cudaGetLastError());
+    c->launches += 1;
+  }
   return USP_OK;
 }
 
@@ -1328,8 +1389,9 @@ int build_graph(usp_ctx* c, int steps) {
 }
 
 // Autotuner of the particle pass: times each register-budget variant (2, 3
-// or 4 resident blocks per SM) on a scratch copy of a prefix of the tile list
-// (up to ~8M particles, so the data exceeds L2) and keeps the fastest.
+// or 4 resident blocks per SM) on a scratch copy of the whole state (each
+// variant starts from the same copy; one untimed and two timed launches) and
+// keeps the fastest; within 1 % the variant with more resident blocks wins.
 template <typename T>
 int autotune(usp_ctx* c) {
   const size_t es = sizeof(T);
@@ -1338,7 +1400,7 @@ int autotune(usp_ctx* c) {
   std::vector<Tile> ht(c->ntiles);
   CK(cudaMemcpy(ht.data(), c->tiles, sizeof(Tile) * c->ntiles, cudaMemcpyDeviceToHost));
   int last_cell = 0;
-  while (nt < c->ntiles && np < (8ll << 20)) {
+  while (nt < c->ntiles) {
     np += ht[nt].count;
     last_cell = ht[nt].cell;
     ++nt;
@@ -1356,24 +1418,29 @@ int autotune(usp_ctx* c) {
   CellSums* ssum = (CellSums*)(scratch + ((bytes + 255) & ~(size_t)255));
   uint32_t* sflags = (uint32_t*)((unsigned char*)ssum + sizeof(CellSums) * c->ncell);
   unsigned long long* scnt = (unsigned long long*)((unsigned char*)sflags + 256);
-  CK(cudaMemcpyAsync(sx, c->cx, end * es, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(sy, c->cy, end * es, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(sz, c->cz, end * es, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(se, c->er, end * es, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemcpyAsync(sl, c->lev, end * 4, cudaMemcpyDeviceToDevice, c->stream));
-  CK(cudaMemsetAsync(ssum, 0, sizeof(CellSums) * c->ncell + 512, c->stream));
+  auto fresh = [&]() -> int {
+    CK(cudaMemcpyAsync(sx, c->cx, end * es, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(sy, c->cy, end * es, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(sz, c->cz, end * es, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(se, c->er, end * es, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(sl, c->lev, end * 4, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(ssum, 0, sizeof(CellSums) * c->ncell + 512, c->stream));
+    return USP_OK;
+  };
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
   int best_mb = 3;
   c->tune_ms.assign(3, 0.f);
-  for (int mb = 2; mb <= 4; ++mb) {
+  for (int mb = 4; mb >= 2; --mb) {
+    int rc = fresh();
+    if (rc) return rc;
     const int grid = std::max(1, std::min(nt, c->grid_by_minb[mb]));
-    int rc = launch_collide<T>(c, mb, grid, c->tiles, nt, sx, sy, sz, se, sl, ssum, sflags, scnt);
+    rc = launch_collide<T>(c, mb, grid, c->tiles, nt, sx, sy, sz, se, sl, ssum, sflags, scnt);
     if (rc) return rc;
     CK(cudaEventRecord(e0, c->stream));
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < 2; ++r) {
       rc = launch_collide<T>(c, mb, grid, c->tiles, nt, sx, sy, sz, se, sl, ssum, sflags, scnt);
       if (rc) return rc;
     }
@@ -1381,12 +1448,12 @@ int autotune(usp_ctx* c) {
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
-    c->tune_ms[mb - 2] = ms / 3.f;
-    if (ms < best) { best = ms; best_mb = mb; }
+    c->tune_ms[mb - 2] = ms / 2.f;
+    if (ms < 0.99f * best) { best = ms; best_mb = mb; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->launches += 12;
+  c->launches += 9;
   c->minb = best_mb;
   c->grid_collide = c->grid_by_minb[best_mb];
   CK(cudaStreamSynchronize(c->stream));
@@ -1572,6 +1639,11 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   if (n > 0) {
     rc = upload_state(c, h_cx, h_cy, h_cz, h_erot, h_lev, false);
     if (rc) return fail(rc);
+    // the FP64 host layout of the initial upload is staged once only
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(USP_ECUDA);
+    dev_release(c, c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
   }
   rc = c->precision == USP_FP32 ? init_params<float>(c) : init_params<double>(c);
   if (rc) return fail(rc);
@@ -1615,6 +1687,8 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
   c->profiling = 0;
   c->ev_used = 0;
   c->minb = 0;
+  c->stage = nullptr;
+  c->stage_bytes = 0;
   if (cfg->stream) {
     c->stream = (cudaStream_t)cfg->stream;
     c->own_stream = false;
@@ -1678,6 +1752,8 @@ int usp_init_plane(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
   c->profiling = 0;
   c->ev_used = 0;
   c->minb = 0;
+  c->stage = nullptr;
+  c->stage_bytes = 0;
   if (cfg->stream) {
     c->stream = (cudaStream_t)cfg->stream;
     c->own_stream = false;
@@ -1861,7 +1937,7 @@ int usp_step_host(usp_ctx* c, const void* hx, const void* hy, const void* hz, co
                   void* oe, int32_t* ol) {
   if (!c || !hx || !hy || !hz || !he || !hl || !h_moments || nsteps < 0) return USP_EINVAL;
   if (c->kind != 0) return USP_ENOTSUP;
-  int rc = upload_state(c, hx, hy, hz, he, hl, true);
+  int rc = upload_state_pipelined(c, hx, hy, hz, he, hl);
   if (rc) return rc;
   rc = c->precision == USP_FP32 ? init_params<float>(c) : init_params<double>(c);
   if (rc) return rc;
@@ -1872,7 +1948,7 @@ int usp_step_host(usp_ctx* c, const void* hx, const void* hy, const void* hz, co
   if (ox && oy && oz && oe && ol) {
     const long long n = c->nparticles;
     const size_t es = c->precision == USP_FP32 ? 4 : 8;
-    void* st = dev_alloc(c, (size_t)n * (4 * es + 4) + 64);
+    void* st = staging(c, (size_t)n * (4 * es + 4) + 64);
     if (!st) return USP_ENOMEM;
     char* p = (char*)st;
     dim3 grid(64, std::min(c->ncell, 65535));
@@ -1894,10 +1970,6 @@ int usp_step_host(usp_ctx* c, const void* hx, const void* hy, const void* hz, co
     CK(cudaMemcpyAsync(oe, p + 3 * n * es, n * es, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(ol, p + 4 * n * es, n * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (c->cfg.alloc && c->cfg.free_) c->cfg.free_(st, c->cfg.alloc_user);
-    else if (!c->cfg.alloc) cudaFree(st);
-    c->owned.erase(std::find(c->owned.begin(), c->owned.end(), st));
-    c->device_bytes -= (long long)(((size_t)n * (4 * es + 4) + 64 + 255) & ~(size_t)255);
   }
   return USP_OK;
 }
@@ -1997,6 +2069,10 @@ void usp_destroy(usp_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->ch) ch_destroy(c->ch);
   if (c->pl) pl_destroy(c->pl);
+  if (c->copy_stream) {
+    cudaStreamDestroy(c->copy_stream);
+    for (cudaEvent_t e : c->up_ev) cudaEventDestroy(e);
+  }
   dev_free_all(c);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
