@@ -153,9 +153,42 @@ def hbm_peak():
     return 6800.0, "fallback"
 
 
+def rank_seed(rank):
+    """Each rank simulates its own independent instances (weak scaling)."""
+    return 1 + 1000 * rank
+
+
 def workload(rank, scale):
     from paper_2508_05642_gb300 import inputs as I
-    return I.batched_instances(seed=1 + 1000 * rank, n_inst=N_INST, steps=500, scale=scale)
+    return I.batched_instances(seed=rank_seed(rank), n_inst=N_INST, steps=500, scale=scale)
+
+
+class RankReducer:
+    """Reductions of host scalars over the ranks of a process group (identity
+    without one): the job's time is the slowest rank's, its particle count
+    the sum over ranks."""
+
+    def __init__(self, dist=None, device="cpu"):
+        self.dist = dist
+        self.device = device
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, self.dist.ReduceOp.MAX if self.dist else None)
+
+    def sum(self, x):
+        return self._reduce(x, self.dist.ReduceOp.SUM if self.dist else None)
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
 
 
 def config_of(w, steps, precision="f32"):
@@ -237,23 +270,8 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    red = RankReducer(dist, "cuda")
+    barrier, max_over_ranks, sum_over_ranks = red.barrier, red.max, red.sum
 
     w = workload(rank, args.scale)
     dt = np.array([w.dt_over_tau_c * usp.usp_tau_c(w.species, w.ndens[i], w.T_nominal[i, 0])
@@ -344,7 +362,7 @@ def run_ours(args, rank, world, local):
     chan = None
     if args.channel_steps > 0:
         from paper_2508_05642_gb300 import inputs as I
-        cw = I.channel_poiseuille(seed=1 + 1000 * rank)
+        cw = I.channel_poiseuille(seed=rank_seed(rank))
         cdt = cw.dt_over_tau_c * usp.usp_tau_c(cw.species, cw.n, cw.channel["T_wall"])
         cp = cw.particles
         cctx = usp.usp_init_channel(cw.species, cw.channel, cdt, cw.y, cp.cx, cp.cy, cp.cz, cp.erot,
@@ -368,7 +386,7 @@ def run_ours(args, rank, world, local):
     cyl = None
     if args.cylinder_steps > 0:
         from paper_2508_05642_gb300 import inputs as I
-        yw = I.cylinder_flow(seed=1 + 1000 * rank)
+        yw = I.cylinder_flow(seed=rank_seed(rank))
         ydt = yw.dt_over_tau_c * usp.usp_tau_c(yw.species, yw.plane["n_inf"], yw.plane["T_inf"])
         yp = yw.particles
         yctx = usp.usp_init_plane(yw.species, yw.plane, ydt, yw.area_frac, yw.x, yw.y, yp.cx,
