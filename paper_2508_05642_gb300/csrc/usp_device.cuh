@@ -498,6 +498,84 @@ __device__ __forceinline__ void sym3_minmax(const T* P, T& lmin, T& lmax) {
   lmin = q + T(2) * p * cos(phi + T(2.0943951023931954923));
 }
 
+// The per-cell coefficients of cell_coeffs_t evaluated in FP32 (the FP32-state
+// form of the 2D path, where 240,000 cells a step would keep the narrow FP64
+// pipe busy): the same formulas in the same order, FP32 transcendentals, the
+// T_1 fixed point to a relative change of 1e-6, the secant replaced by the
+// derivative when T_check is within 2e-3 of T_vib.
+struct CellCoeffsF {
+  float mu_p, Pr, A, B, alpha, nu_ref, g_tr_rot, g_tr_vib, g_rot_vib, e_rot_tgt, e_vib_tgt;
+  bool ok, tgt_clamped;
+};
+
+__device__ inline CellCoeffsF cell_coeffs_f32(const Species& s, double n, double dt_d, float Ttr,
+                                              float Trot, float Tvib) {
+  CellCoeffsF c;
+  const float R = (float)s.R, ctr = 1.5f * R, crot = R;
+  const float th = (float)s.theta_v, Rth = R * th;
+  const float dt = (float)dt_d;
+  const float p = (float)(n * kB) * Ttr;
+  const float xw = expf((float)s.omega * logf(Ttr / (float)s.T_ref));
+  c.mu_p = (float)s.mu_ref0 * xw / p;
+  const float tau_c = (float)s.tauf0 * c.mu_p;
+  float zr, zv;
+  if (s.zmodel == 0) {
+    zr = (float)s.Z_rot;
+    zv = (float)s.Z_vib;
+  } else {
+    const float r = (float)s.T_star / Ttr;
+    zr = (float)s.Zrot_inf /
+         (1.0f + (float)(0.5 * kPi * 1.7724538509055159) * sqrtf(r) +
+          (float)(kPi + 0.25 * kPi * kPi) * r);
+    zv = ((float)s.C1 / ((float)s.Tref_w * xw)) * expf((float)s.C2 / cbrtf(Ttr)) +
+         (float)s.zv_ht * sqrtf(Ttr / (float)s.T_ref) / xw;
+  }
+  const float tau_rot = zr * tau_c, tau_vib = zv * tau_c;
+  float xi = 0.0f;
+  if (Tvib > 0.0f) {
+    const float x = th / Tvib;
+    xi = x / expm1f(x);
+  }
+  c.Pr = (14.0f + 2.0f * xi) / (19.0f + 2.0f * xi);
+  c.A = (2.0f * c.mu_p - c.Pr * dt) / (2.0f * c.mu_p + c.Pr * dt);
+  c.B = (2.0f * c.mu_p - dt) / (2.0f * c.mu_p + dt);
+  c.ok = c.A > -1.0f && c.A < 1.0f;
+  c.alpha = c.ok ? cbrtf(c.A) : 0.0f;
+  const float a2 = c.alpha * c.alpha;
+  c.nu_ref = (c.B - a2) / (1.0f - a2);
+  const float gr = dt / (dt + 2.0f * tau_rot);
+  const float gv = dt / (dt + 2.0f * tau_vib);
+  auto evib = [&](float T) { return T > 0.0f ? Rth / expm1f(th / T) : 0.0f; };
+  auto cv = [&](float T) {
+    if (T <= 0.0f) return 0.0f;
+    const float h = 0.5f * th / T;
+    const float q = h / sinhf(h);
+    return R * q * q;
+  };
+  const float evT = evib(Tvib);
+  float x = cv(Ttr);
+  for (int it = 0; it < 50; ++it) {
+    const float idn = 1.0f / (ctr + gr * crot + gv * x);
+    const float Tc = Ttr + (gr * crot * (Trot - Ttr) + gv * x * (Tvib - Ttr)) * idn;
+    const float scale = fmaxf(fabsf(Tc), fabsf(Tvib));
+    const float xn = (fabsf(Tc - Tvib) <= 2e-3f * scale) ? cv(Tvib)
+                                                          : (evib(Tc) - evT) / (Tc - Tvib);
+    const float ch = fabsf(xn - x);
+    x = xn;
+    if (ch <= 1e-6f * fabsf(xn)) break;
+  }
+  const float idn = 1.0f / (ctr + gr * crot + gv * x);
+  c.g_tr_rot = 2.0f * gr * ctr * crot * idn;
+  c.g_tr_vib = 2.0f * gv * ctr * x * idn;
+  c.g_rot_vib = 2.0f * gr * gv * crot * x * idn;
+  c.e_rot_tgt = crot * Trot + c.g_tr_rot * (Ttr - Trot) - c.g_rot_vib * (Trot - Tvib);
+  c.e_vib_tgt = evT + c.g_tr_vib * (Ttr - Tvib) + c.g_rot_vib * (Trot - Tvib);
+  c.tgt_clamped = false;
+  if (c.e_rot_tgt < 0.0f) { c.e_rot_tgt = 0.0f; c.tgt_clamped = true; }
+  if (c.e_vib_tgt < 0.0f) { c.e_vib_tgt = 0.0f; c.tgt_clamped = true; }
+  return c;
+}
+
 // Drift-diffusion factor for one set of macroscopic fields: returns the
 // alpha actually used and L with L L^T = tau D_tr (Eq. D_tr), applying the
 // positivity adjustment of Sec. 3.A.3 when the Cholesky test fails (nu

@@ -784,29 +784,39 @@ moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
                const CellState* __restrict__ cells, const T* __restrict__ cx,
                const T* __restrict__ cy, const T* __restrict__ cz, const T* __restrict__ er,
                const int* __restrict__ lev, double* __restrict__ acc_out) {
+  // each block owns a contiguous range of the tile list; per-thread sums run
+  // over all its tiles of one cell and are reduced and added to the cell's
+  // accumulators once per (block, cell)
   __shared__ double red[kBlock / 32][15];
   __shared__ T cp[11];   // U (3), U* (3), s, r, pass-0 mean (3) in T
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  const int G = gridDim.x;
+  const int t_begin = (int)(((long long)ntiles * blockIdx.x) / G);
+  const int t_end = (int)(((long long)ntiles * (blockIdx.x + 1)) / G);
+  const int na = pass == 0 ? 5 : 15;
+  T a[15];
+  for (int i = 0; i < 15; ++i) a[i] = T(0);
+  for (int t = t_begin; t < t_end; ++t) {
     const Tile tl = tiles[t];
     const CellState& cs = cells[tl.cell];
-    const long long base = cs.off + tl.start;
-    // the tile's cell constants, converted once (one value per thread: the
-    // FP64 pipe is narrow, so no per-thread FP64 work per tile)
-    if (threadIdx.x < 11) {
-      const int i = threadIdx.x;
-      double v;
-      if (i < 3) v = cs.U[i];
-      else if (i < 6) v = cs.Us[i - 3];
-      else if (i == 6) v = cs.s;
-      else if (i == 7) v = cs.r;
-      else v = (pass == 1 && cs.N > 0)
-                   ? acc_out[(size_t)tl.cell * kMomAcc + (i - 8)] / (double)cs.N : 0.0;
-      cp[i] = (T)v;
+    const bool first = t == t_begin || tiles[t - 1].cell != tl.cell;
+    if (first) {
+      // the cell's constants, converted once (one value per thread)
+      __syncthreads();
+      if (threadIdx.x < 11) {
+        const int i = threadIdx.x;
+        double v;
+        if (i < 3) v = cs.U[i];
+        else if (i < 6) v = cs.Us[i - 3];
+        else if (i == 6) v = cs.s;
+        else if (i == 7) v = cs.r;
+        else v = (pass == 1 && cs.N > 0)
+                     ? acc_out[(size_t)tl.cell * kMomAcc + (i - 8)] / (double)cs.N : 0.0;
+        cp[i] = (T)v;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    T a[15];
-    for (int i = 0; i < 15; ++i) a[i] = T(0);
+    const long long base = cs.off + tl.start;
     const T U0 = cp[0], U1 = cp[1], U2 = cp[2];
     const T S0 = cp[3], S1 = cp[4], S2 = cp[5];
     const T sc = cp[6], rc = cp[7];
@@ -830,21 +840,23 @@ moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
         a[12] += C0 * li; a[13] += C1 * li; a[14] += C2 * li;
       }
     }
-    const int na = pass == 0 ? 5 : 15;
-    // warp totals; lane i < na converts total i (one conversion per warp)
-    T mine = T(0);
-    for (int i = 0; i < na; ++i) {
-      const T s = warp_sum(a[i]);
-      mine = lane == i ? s : mine;
+    const bool last = t + 1 >= t_end || tiles[t + 1].cell != tl.cell;
+    if (last) {
+      // warp totals; lane i < na converts total i (one conversion per warp)
+      T mine = T(0);
+      for (int i = 0; i < na; ++i) {
+        const T sm = warp_sum(a[i]);
+        mine = lane == i ? sm : mine;
+      }
+      if (lane < na) red[wid][lane] = (double)mine;
+      __syncthreads();
+      if (threadIdx.x < na) {
+        double sm = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) sm += red[w][threadIdx.x];
+        atomicAdd(&acc_out[(size_t)tl.cell * kMomAcc + (pass == 0 ? 0 : 5) + threadIdx.x], sm);
+      }
+      for (int i = 0; i < 15; ++i) a[i] = T(0);
     }
-    if (lane < na) red[wid][lane] = (double)mine;
-    __syncthreads();
-    if (threadIdx.x < na) {
-      double s = 0.0;
-      for (int w = 0; w < kBlock / 32; ++w) s += red[w][threadIdx.x];
-      atomicAdd(&acc_out[(size_t)tl.cell * kMomAcc + (pass == 0 ? 0 : 5) + threadIdx.x], s);
-    }
-    __syncthreads();
   }
 }
 

@@ -46,6 +46,7 @@ constexpr uint32_t PTAG_INFLOW_P = 5u, PTAG_INFLOW_T = 6u, PTAG_INFLOW_V = 7u;
 constexpr uint32_t CTAG_INFLOW = 0x80000004u;
 constexpr int kInflowTries = 64;
 constexpr int kBlk = 256;
+constexpr int kParamBlock = 32;   // cells per block of the stencil pass
 
 // Device-resident counts of the current step.
 struct PlCount {
@@ -634,10 +635,16 @@ template <typename T>
 __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict__ cells,
                           const T* __restrict__ fT, const int* __restrict__ usable_c,
                           PlParams<T>* __restrict__ prm, Species sp) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
+  // a thread builds its cell's record in shared memory; the block then copies
+  // its kParamBlock records out as consecutive 8-byte words (coalesced), where
+  // one thread storing a ~0.5 KB record would scatter every store
+  __shared__ PlParams<T> buf[kParamBlock];
+  const int c0 = blockIdx.x * kParamBlock;
+  const int c = c0 + threadIdx.x;
+  const int nb = min(kParamBlock, g.ncell - c0);
+  if (c < g.ncell) {
   const ChCellT<double>& cs = cells[c];
-  PlParams<T> P;
+  PlParams<T>& P = buf[threadIdx.x];
   P.active = cs.active;
   P.pad = 0;
   P.alpha = (T)cs.alpha; P.nu_ref = (T)cs.nu_ref; P.B = (T)cs.B; P.mu_p = (T)cs.mu_p;
@@ -686,7 +693,13 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
       for (int k = 0; k < kNF; ++k) P.gxy[q][k] = T(0);
     }
   }
-  prm[c] = P;
+  }
+  __syncthreads();
+  static_assert(sizeof(PlParams<T>) % 8 == 0, "records copied as 8-byte words");
+  const int words = nb * (int)(sizeof(PlParams<T>) / 8);
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(buf);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(prm + c0);
+  for (int w = threadIdx.x; w < words; w += kParamBlock) dst[w] = src[w];
 }
 
 // per particle: the bilinear polynomial of its quadrant, then the collision
@@ -961,15 +974,19 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   if (prof) prof(env.owner, 0, 0);
   if (prof) prof(env.owner, 1, 1);
   const int wb = h->grid_wc, tb = h->grid_tc;
-  const int cb = (ncell + 127) / 128;
   float* pend = env.precision == USP_FP32 ? h->pend : nullptr;
   ch_moments<T, double><<<wb, kBlk, 0, s>>>(ncell, 32, h->off, h->af, cx, cy, cz, er, h->lv[b],
                                             h->cells, env.sp, env.counters, pend, (T*)h->fT,
                                             h->usable_c);
-  ch_coeffs<double><<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->af, h->g.dt, h->cells, env.sp,
-                                        env.sp.omega, env.sp.Z_rot, env.flags, env.counters);
-  pl_params<T><<<cb, 128, 0, s>>>(h->g, h->recon, h->cells, (const T*)h->fT, h->usable_c,
-                                  (PlParams<T>*)h->prm, env.sp);
+  if (env.precision == USP_FP32)
+    ch_coeffs_f32<<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->af, h->g.dt, h->cells, env.sp,
+                                      env.flags, env.counters);
+  else
+    ch_coeffs<double><<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->af, h->g.dt, h->cells,
+                                          env.sp, env.sp.omega, env.sp.Z_rot, env.flags,
+                                          env.counters);
+  pl_params<T><<<(ncell + kParamBlock - 1) / kParamBlock, kParamBlock, 0, s>>>(
+      h->g, h->recon, h->cells, (const T*)h->fT, h->usable_c, (PlParams<T>*)h->prm, env.sp);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 1, 0);
   if (prof) prof(env.owner, 0, 1);

@@ -507,6 +507,41 @@ __global__ void ch_coeffs(int ny, double F_num, double vol, const double* __rest
   tally_flush(tal, flags, counters);
 }
 
+// ch_coeffs with the coefficients evaluated in FP32 (cell_coeffs_f32): the
+// FP32-state form of the 2D path
+__global__ void ch_coeffs_f32(int ny, double F_num, double vol, const double* __restrict__ af,
+                              double dt, ChCellT<double>* __restrict__ cells, Species sp,
+                              uint32_t* flags, unsigned long long* counters) {
+  __shared__ BlockTally tal;
+  tally_init(tal);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ny; c += gridDim.x * blockDim.x) {
+    ChCellT<double>& cs = cells[c];
+    if (!cs.active) continue;
+    const double v = af ? af[c] * vol : vol;
+    if (!(v > 0.0)) {
+      cs.active = 0;
+      continue;
+    }
+    cs.n = (double)cs.N * F_num / v;
+    const CellCoeffsF k =
+        cell_coeffs_f32(sp, cs.n, dt, (float)cs.Ttr, (float)cs.Trot, (float)cs.Tvib);
+    if (!k.ok) {
+      tally_or(tal, (uint32_t)F_A_NONPOS);
+      cs.active = 0;
+      continue;
+    }
+    cs.alpha = k.alpha; cs.nu_ref = k.nu_ref; cs.B = k.B; cs.mu_p = k.mu_p; cs.Pr = k.Pr;
+    cs.gtr = k.g_tr_rot; cs.gtv = k.g_tr_vib; cs.grv = k.g_rot_vib;
+    cs.e_rot_tgt = k.e_rot_tgt;
+    cs.e_vib_tgt = k.e_vib_tgt;
+    if (k.tgt_clamped) {
+      tally_or(tal, (uint32_t)F_TREL_CLAMP);
+      tally_add(tal, C_TREL_CLAMP, 1ull);
+    }
+  }
+  tally_flush(tal, flags, counters);
+}
+
 template <typename S>
 __device__ __forceinline__ void cell_fields(const ChCellT<S>& c, S* f) {
   f[0] = c.U[0]; f[1] = c.U[1]; f[2] = c.U[2];

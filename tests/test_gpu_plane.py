@@ -218,7 +218,9 @@ def test_full_size_fp32_graph_run_invariants():
     gx, gy, *_, gp = usp.usp_plane_get_particles(ctx)
     pl = w.plane
     assert np.all(gx * gx + gy * gy >= pl["cyl_r"] ** 2 * (1 - 1e-5))
-    assert np.all((gx >= pl["x0"]) & (gx <= pl["x1"]) & (gy >= pl["y0"]) & (gy <= pl["y1"]))
+    # the FP32 state holds the domain bounds rounded to float
+    b = {k: float(np.float32(pl[k])) for k in ("x0", "x1", "y0", "y1")}
+    assert np.all((gx >= b["x0"]) & (gx <= b["x1"]) & (gy >= b["y0"]) & (gy <= b["y1"]))
     dx = (pl["x1"] - pl["x0"]) / pl["nx"]
     dy = (pl["y1"] - pl["y0"]) / pl["ny"]
     i = np.clip(np.floor((gx.astype(np.float32) - np.float32(pl["x0"])) / np.float32(dx)), 0,
