@@ -276,3 +276,42 @@ def test_moments_of_dyadic_states_are_bitwise_equal():
     np.testing.assert_allclose(gm[6], om[6], rtol=1e-13)
     scale = np.abs(om[13:22]).max(axis=1, keepdims=True)
     assert np.all(np.abs(gm[13:22] - om[13:22]) <= 1e-13 * scale)
+
+
+def test_full_size_batched_fp32_sampled_instances_match_oracle():
+    """The benchmark configuration (4096 instances, 154M particles, FP32 state,
+    autotuned register budget, graph-replayed steps): after 5 steps, sampled
+    instances (the smallest, the largest and four others) against the oracle
+    run on those instances alone, with the same particle ids and cell index."""
+    w = I.batched_instances(seed=1, n_inst=4096, steps=5)
+    p = w.particles
+    ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, _gpu_dt(w), p.cx, p.cy, p.cz,
+                                   p.erot, p.lev, precision=usp.USP_FP32, seed=w.seed,
+                                   use_graph=True)
+    usp.usp_step(ctx, 5)
+    gm = usp.usp_moments(ctx)
+    flags, _ = usp.usp_status(ctx)
+    assert flags & usp.ERROR_FLAGS == 0
+    ctx.destroy()
+    sizes = np.diff(w.offsets)
+    sample = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 1, 1000, 2048, 4095})
+    sp = O.species(**w.species)
+    dto = _oracle_dt(w)
+    p32 = p.astype_f32_exact()
+    for k in sample:
+        b, e = int(w.offsets[k]), int(w.offsets[k + 1])
+        st = O.State.from_arrays(p32.cx[b:e], p32.cy[b:e], p32.cz[b:e], p32.erot[b:e],
+                                 p32.lev[b:e], pid=np.arange(b, e, dtype=np.uint32))
+        # cells 0..k-1 empty: the cell streams (I_Delta, +-1 picks) are keyed
+        # by the cell index, so the instance keeps its index k
+        off = np.zeros(k + 2, dtype=np.int64)
+        off[k + 1] = e - b
+        O.homog_step(sp, 1, w.seed, 0, 5, off, w.ndens[:k + 1], dto[:k + 1], st)
+        om = O.moments(sp, off, st)[:, k]
+        g = gm[:, k]
+        assert g[0] == om[0]
+        for f in (4, 5):
+            assert g[f] == pytest.approx(om[f], rel=1e-4), (k, f)
+        assert abs(g[6] - om[6]) < 1e-3 * max(om[6], 100.0), k
+        vth = math.sqrt(O.R(sp) * om[4])
+        assert np.all(np.abs(g[1:4] - om[1:4]) < 1e-4 * vth), k
