@@ -282,7 +282,7 @@ def run_ours(args, rank, world, local):
                                    p.lev, precision=usp.USP_FP32, seed=w.seed,
                                    stream=stream.cuda_stream, use_graph=True)
     N = w.n_particles
-    minb, tune_ms = usp.usp_tuning(ctx)
+    (warp_tiles, minb), tune_ms = usp.usp_tuning(ctx)
     usp.usp_step(ctx, args.warmup)
     torch.cuda.synchronize()
 
@@ -434,11 +434,14 @@ def run_ours(args, rank, world, local):
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_kind,
-                             "traffic": profiled_traffic(N), "kernel": "collide_kernel<float>",
+                             "traffic": profiled_traffic(N),
+                             "kernel": ("collide_warp_kernel<float>" if warp_tiles
+                                        else "collide_kernel<float>"),
                              "kernel_ms": collide_ms, "alg_bytes_per_launch": alg_bytes,
                              "finalize_ms": finalize_ms, "ms_per_step_profiled": ms_prof / args.steps,
-                             "autotune": {"blocks_per_sm": minb,
-                                          "ms_by_blocks_per_sm_2_3_4": [float(x) for x in tune_ms]}},
+                             "autotune": {"warp_tiles": warp_tiles, "blocks_per_sm": minb,
+                                          "ms_block_tiled_2_3_4": [float(x) for x in tune_ms[:3]],
+                                          "ms_warp_tiled_2_3_4": [float(x) for x in tune_ms[3:]]}},
                 "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "poiseuille_channel": chan,
                 "cylinder_plane": cyl,
                 "clocks": clk,

@@ -312,11 +312,22 @@ int usp_sync(usp_ctx* ctx);
 int usp_info(usp_ctx* ctx, int64_t* n_particles, int* n_cells, int* precision, int64_t* step,
              int* tile, int64_t* device_bytes);
 
-/* Particle-pass variant in use: resident blocks per SM its register budget
- * targets (2, 3 or 4), and the autotuner's milliseconds per launch of each
- * variant on its sample (zeros when the tuner did not run: explicit tile
- * size, or fewer than 2^20 particles). */
-int usp_tuning(usp_ctx* ctx, int* blocks_per_sm, double ms[3]);
+/* Particle-pass variant of a homogeneous context: its design (*warp_tiles =
+ * 1: every warp pipelines its own tiles of <= 128 particles; 0: a block
+ * stages tiles of <= 1024 particles shared by its 256 threads), the resident
+ * blocks per SM its register budget targets (2, 3 or 4), and the autotuner's
+ * milliseconds per launch of each variant on the whole state, ordered
+ * block-tiled 2, 3, 4 then warp-tiled 2, 3, 4 (zeros when the tuner did not
+ * run: explicit tile size, or fewer than 2^20 particles).  Other contexts
+ * report zeros.  Any output pointer may be NULL. */
+int usp_tuning(usp_ctx* ctx, int* warp_tiles, int* blocks_per_sm, double ms[6]);
+
+/* Force the particle-pass variant of a homogeneous context (warp_tiles 0 or
+ * 1, blocks_per_sm 2..4; USP_EINVAL otherwise or for another kind of
+ * context).  Synchronises the context's stream and drops a captured graph.
+ * The variants make the same per-particle decisions and differ only in the
+ * order in which the FP64 cell sums are added up. */
+int usp_set_variant(usp_ctx* ctx, int warp_tiles, int blocks_per_sm);
 
 /* Number of kernel launches the library enqueued since creation (graph
  * replays count every kernel in the graph). */

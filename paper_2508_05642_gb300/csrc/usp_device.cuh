@@ -120,11 +120,19 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
 // Open-interval uniforms.  double: (x + 0.5) 2^-32 (exact).
 // float: (2 (x >> 9) + 1) 2^-24 (exact; 23 random bits).
 template <typename T> __device__ __forceinline__ T uniform_open(uint32_t x);
+// Both are formed without an integer-to-float conversion: the word goes into
+// the mantissa of a number in [1, 2), from which 1 - (half a step) is
+// subtracted.  The subtraction is exact (Sterbenz: the operands are within a
+// factor of two), so the results are exactly (x + 1/2) 2^-32 and
+// (2 (x >> 9) + 1) 2^-24.
 template <> __device__ __forceinline__ double uniform_open<double>(uint32_t x) {
-  return __dmul_rn(__dadd_rn(__uint2double_rn(x), 0.5), 2.3283064365386963e-10);
+  const double a =
+      __longlong_as_double((long long)(0x3FF0000000000000ull | ((unsigned long long)x << 20)));
+  return __dsub_rn(a, 0.99999999988358467817306518554688);   // 1 - 2^-33
 }
 template <> __device__ __forceinline__ float uniform_open<float>(uint32_t x) {
-  return __fmul_rn(__uint2float_rn((x >> 9) * 2u + 1u), 5.9604644775390625e-08f);
+  const float a = __int_as_float((int)(0x3F800000u | (x >> 9)));
+  return __fsub_rn(a, 0.999999940395355224609375f);          // 1 - 2^-24
 }
 
 // Box-Muller pair: G_a = sqrt(-2 ln u_a) cos(2 pi u_b), G_b = ... sin(2 pi u_b).

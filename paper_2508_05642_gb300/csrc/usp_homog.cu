@@ -10,19 +10,23 @@
 //   conservation rescale), CollideParams<T> (everything the particle kernel
 //   needs, precomputed per cell), CellSums (FP64 post-collision sums).
 //
-// One step = two kernels:
-//   collide_kernel   one pass over the particles (read 1x, write 1x).  It
+// One step = one particle pass and three per-cell kernels:
+//   collide (warp- or block-tiled, chosen by the autotuner)
+//                    one pass over the particles (read 1x, write 1x).  It
 //                    applies the previous step's pending conservation rescale
 //                    on load (c = U + s (c* - U*), eps = r eps*), performs the
 //                    particle updates of Eqs. update_ci, update_erot and
 //                    update_evib with per-cell coefficients, stores the
 //                    post-collision state and accumulates per-cell sums.
-//   finalize_kernel  one warp per cell: the vibrational +-1 correction of
-//                    Sec. 4.C (warp-parallel with the sequential semantics),
-//                    the rotational and velocity rescale factors, the
-//                    moments of the next step (exact under the affine
-//                    rescale: U' = U, Pi' = s^2 Pi*, e_rot' = r e_rot*), and
-//                    the next step's coefficients (Sec. 3.A) in FP64.
+//   levelfix_kernel  one warp per cell: the vibrational +-1 correction of
+//                    Sec. 4.C (warp-parallel with the sequential semantics).
+//   cellupdate_kernel one thread per cell: the rotational and velocity
+//                    rescale factors, the moments of the next step (exact
+//                    under the affine rescale: U' = U, Pi' = s^2 Pi*,
+//                    e_rot' = r e_rot*), and the next step's coefficients
+//                    (Sec. 3.A) in FP64.
+//   jumptable_kernel (FP32 form) the per-cell inversion tables of the
+//                    vibrational jump samplers for the next step.
 // The rescale is never written back as a separate pass: it rides along with
 // the next collide pass, or with usp_moments / usp_get_particles.
 #include <cuda_runtime.h>
@@ -501,6 +505,203 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
     // the block's shared memory is released
     for (int b = 0; b < 2; ++b)
       if (inflight[b]) (void)mbar_wait_bounded(&bar[b], phase[b]);
+    bulk_wait_all();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-tiled particle pass.  Every warp runs its own pipeline over a
+// contiguous range of small tiles (<= kWT particles of one cell): kWS staging
+// buffers, bulk loads issued by lane 0 up to two tiles ahead, bulk stores of
+// the updated tile, cell sums reduced across the warp when its cell changes.
+// There is no block-wide barrier, so a warp never waits for the slowest
+// thread of its block.
+// ---------------------------------------------------------------------------
+constexpr int kWT = 128;            // particles per warp tile
+constexpr int kWS = 3;              // staging buffers per warp
+constexpr int kWarps = kBlock / 32;
+
+template <typename T>
+constexpr size_t wstage_bytes() {
+  return (size_t)kWT * (4 * sizeof(T) + sizeof(int));
+}
+template <typename T>
+constexpr size_t wsmem_bytes() {
+  return (size_t)kWarps * kWS * wstage_bytes<T>();
+}
+
+// all but the most recent bulk group have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read_1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void wstage_load(const Tile& tl, long long off, unsigned char* b,
+                                            uint64_t* bar, const T* cx, const T* cy, const T* cz,
+                                            const T* er, const int* lev) {
+  const int n4 = round4(tl.count);
+  const long long base = off + tl.start;
+  const uint32_t bt = (uint32_t)(n4 * sizeof(T)), bl = (uint32_t)(n4 * sizeof(int));
+  T* X = reinterpret_cast<T*>(b);
+  mbar_expect_tx(bar, 4 * bt + bl);
+  if (n4 > 0) {
+    bulk_g2s(X, cx + base, bt, bar);
+    bulk_g2s(X + kWT, cy + base, bt, bar);
+    bulk_g2s(X + 2 * kWT, cz + base, bt, bar);
+    bulk_g2s(X + 3 * kWT, er + base, bt, bar);
+    bulk_g2s(reinterpret_cast<int*>(b + 4 * kWT * sizeof(T)), lev + base, bl, bar);
+  }
+}
+
+// Warp reduction of the cell sums and one FP64 atomic per sum.
+template <typename T>
+__device__ __forceinline__ void flush_sums_warp(const T* acc, int accI, int maxI,
+                                                CellSums* dst) {
+  const int lane = threadIdx.x & 31;
+  double mine = 0.0;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    const T s = warp_sum(acc[i]);
+    if (lane == i) mine = (double)s;
+  }
+  const int sI = warp_sum(accI);
+  const int mI = __reduce_max_sync(0xffffffffu, maxI);
+  if (lane < 10) atomicAdd(&dst->v[lane], mine);
+  if (lane == 10) atomicAdd(&dst->I, (unsigned long long)(long long)sI);
+  if (lane == 11 && mI > 0) atomicMax(&dst->maxI, mI);
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
+collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
+                    const CollideParams<T>* __restrict__ prm, T* __restrict__ cx,
+                    T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
+                    int* __restrict__ lev, CellSums* __restrict__ sums, uint32_t* flags,
+                    unsigned long long* counters, const PhiloxRoundKeys rk,
+                    const float* __restrict__ tab_nb, const float* __restrict__ tab_b) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_all[kWarps][kWS];
+  __shared__ __align__(16) CollideParams<T> Pw[kWarps];   // the warp's current cell
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long W = (long long)gridDim.x * kWarps;
+  const long long gw = (long long)blockIdx.x * kWarps + wid;
+  const int t_begin = (int)(((long long)ntiles * gw) / W);
+  const int t_end = (int)(((long long)ntiles * (gw + 1)) / W);
+  if (t_begin >= t_end) return;
+  unsigned char* wbuf = smem + (size_t)wid * kWS * wstage_bytes<T>();
+  uint64_t* bar = bar_all[wid];
+  CollideParams<T>& P = Pw[wid];
+  if (lane == 0) {
+#pragma unroll
+    for (int s = 0; s < kWS; ++s) mbar_init(&bar[s], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  uint32_t inflight = 0;   // lane 0: buffers with a load in flight
+  if (lane == 0) {
+    for (int s = 0; s < kWS - 1 && t_begin + s < t_end; ++s) {
+      const Tile tl = tiles[t_begin + s];
+      wstage_load<T>(tl, prm[tl.cell].off, wbuf + s * wstage_bytes<T>(), &bar[s], cx, cy, cz, er,
+                     lev);
+      inflight |= 1u << s;
+    }
+  }
+  uint32_t phase = 0;      // bit s: parity of buffer s's next completion
+  T acc[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) acc[i] = T(0);
+  int accI = 0, maxI = 0;
+  uint32_t fl = 0;
+  int npb = 0;
+  int cell = -1;
+  int s = 0;
+  for (int t = t_begin; t < t_end; ++t) {
+    const Tile tl = tiles[t];
+    if (tl.cell != cell) {
+      constexpr int nw = (int)(sizeof(CollideParams<T>) / 4);
+      __syncwarp();
+      for (int i = lane; i < nw; i += 32)
+        reinterpret_cast<uint32_t*>(&P)[i] = reinterpret_cast<const uint32_t*>(&prm[tl.cell])[i];
+      __syncwarp();
+      cell = tl.cell;
+    }
+    const bool ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
+      break;
+    }
+    phase ^= 1u << s;
+    if (lane == 0) inflight &= ~(1u << s);
+    unsigned char* b = wbuf + s * wstage_bytes<T>();
+    if (P.active) {
+      T* X = reinterpret_cast<T*>(b);
+      int* Lv = reinterpret_cast<int*>(b + 4 * kWT * sizeof(T));
+      const uint32_t pid0 = P.pid0 + (uint32_t)tl.start;
+      const float* tnb = tab_nb + (size_t)tl.cell * kJR * kJK;
+      const float* tb = tab_b + (size_t)tl.cell * kJR * kJK;
+#pragma unroll 1
+      for (int k = lane; k < tl.count; k += 32) {
+        T x = X[k], y = X[k + kWT], z = X[k + 2 * kWT], e = X[k + 3 * kWT];
+        int l = Lv[k];
+        uint32_t f1 = 0;
+        collide_one<T>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb, tb);
+        X[k] = x; X[k + kWT] = y; X[k + 2 * kWT] = z; X[k + 3 * kWT] = e;
+        Lv[k] = l;
+        npb += (f1 & F_PB_CLAMP) ? 1 : 0;
+        fl |= f1;
+      }
+      // results in shared memory -> visible to the bulk-copy engine
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        const int n4 = round4(tl.count);
+        const long long base = P.off + tl.start;
+        const uint32_t bt = (uint32_t)(n4 * sizeof(T)), bl = (uint32_t)(n4 * sizeof(int));
+        if (n4 > 0) {
+          bulk_s2g(cx + base, X, bt);
+          bulk_s2g(cy + base, X + kWT, bt);
+          bulk_s2g(cz + base, X + 2 * kWT, bt);
+          bulk_s2g(er + base, X + 3 * kWT, bt);
+          bulk_s2g(lev + base, Lv, bl);
+        }
+      }
+      if (t + 1 >= t_end || tiles[t + 1].cell != tl.cell) {
+        flush_sums_warp<T>(acc, accI, maxI, &sums[tl.cell]);
+#pragma unroll
+        for (int i = 0; i < 10; ++i) acc[i] = T(0);
+        accI = 0;
+        maxI = 0;
+      }
+    }
+    if (lane == 0) {
+      // one bulk group per tile (empty for an inactive cell), so that the
+      // group before the newest is always the previous tile's store
+      bulk_commit();
+      const int tn = t + kWS - 1;
+      if (tn < t_end) {
+        // the buffer of tile t - 1 takes tile t + kWS - 1 once its store has
+        // read it
+        const int sn = s == 0 ? kWS - 1 : s - 1;
+        bulk_wait_read_1();
+        const Tile tn_l = tiles[tn];
+        wstage_load<T>(tn_l, prm[tn_l.cell].off, wbuf + sn * wstage_bytes<T>(), &bar[sn], cx, cy,
+                       cz, er, lev);
+        inflight |= 1u << sn;
+      }
+    }
+    s = s == kWS - 1 ? 0 : s + 1;
+  }
+  fl = __reduce_or_sync(0xffffffffu, fl);
+  npb = __reduce_add_sync(0xffffffffu, npb);
+  if (lane == 0) {
+    if (fl) {
+      atomicOr(flags, fl);
+      if (npb) atomicAdd(&counters[C_PB_CLAMP], (unsigned long long)npb);
+    }
+    // loads still in flight after a timeout: wait for them (bounded) before
+    // the block's shared memory is released
+    for (int q = 0; q < kWS; ++q)
+      if (inflight & (1u << q)) (void)mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
     bulk_wait_all();
   }
 }
@@ -988,8 +1189,10 @@ struct usp_ctx {
   CellState* cells;
   void* prm;
   CellSums* sums;
-  Tile* tiles;
+  Tile* tiles;              // tiles of <= tile particles (block-tiled kernels)
   int ntiles;
+  Tile* wtiles;             // tiles of <= kWT particles (warp-tiled particle pass)
+  int nwtiles;
   long long* uoff;          // unpadded offsets (device)
   double* macc;             // moment accumulators
   double* mout;             // moment output (device)
@@ -1000,11 +1203,12 @@ struct usp_ctx {
   unsigned long long* counters;
   std::vector<long long> h_uoff;
   std::vector<long long> h_poff;   // padded segment starts
-  std::vector<float> tune_ms;      // autotuner timings per variant (2, 3, 4)
+  std::vector<float> tune_ms;      // autotuner timings: block-tiled 2, 3, 4, warp-tiled 2, 3, 4
   int tile;
   int grid_collide;
   int minb;                 // register-budget variant of the particle pass
-  int grid_by_minb[5];
+  int warp_tiles;           // 1: warp-tiled particle pass, 0: block-tiled
+  int grid_by_minb[2][5];   // persistent grid per (design, variant)
   long long step;
   long long launches;
   cudaGraphExec_t graph_exec;
@@ -1113,7 +1317,8 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
-int build_tiles(usp_ctx* c, int tile) {
+// Cells split into tiles of at most `tile` particles, in cell order.
+int make_tiles(usp_ctx* c, int tile, Tile** out, int* nout) {
   std::vector<Tile> t;
   for (int i = 0; i < c->ncell; ++i) {
     const long long n = c->h_uoff[i + 1] - c->h_uoff[i];
@@ -1134,8 +1339,16 @@ int build_tiles(usp_ctx* c, int tile) {
   if (!d) return USP_ENOMEM;
   CK(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(Tile), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  c->tiles = d;
-  c->ntiles = (int)t.size();
+  *out = d;
+  *nout = (int)t.size();
+  return USP_OK;
+}
+
+int build_tiles(usp_ctx* c, int tile) {
+  int rc = make_tiles(c, tile, &c->tiles, &c->ntiles);
+  if (rc) return rc;
+  rc = make_tiles(c, std::min(tile, kWT), &c->wtiles, &c->nwtiles);
+  if (rc) return rc;
   c->tile = tile;
   return USP_OK;
 }
@@ -1169,26 +1382,50 @@ int prof_cb(void* owner, int kind, int begin) {
 }
 
 template <typename T, int MINB>
-void* collide_fn() {
-  return (void*)collide_kernel<T, MINB>;
+void* collide_fn(int warp_tiles) {
+  return warp_tiles ? (void*)collide_warp_kernel<T, MINB> : (void*)collide_kernel<T, MINB>;
 }
 
 template <typename T>
-void* collide_variant(int minb) {
-  return minb == 2 ? collide_fn<T, 2>() : minb == 3 ? collide_fn<T, 3>() : collide_fn<T, 4>();
+void* collide_variant(int warp_tiles, int minb) {
+  return minb == 2 ? collide_fn<T, 2>(warp_tiles)
+                   : minb == 3 ? collide_fn<T, 3>(warp_tiles) : collide_fn<T, 4>(warp_tiles);
 }
 
-// Launch the particle pass on the given state / sums buffers.
 template <typename T>
-int launch_collide(usp_ctx* c, int minb, int grid, const Tile* tiles, int ntiles, void* cx,
-                   void* cy, void* cz, void* er, int* lev, CellSums* sums, uint32_t* flags,
+size_t collide_smem(int warp_tiles) {
+  return warp_tiles ? wsmem_bytes<T>() : 2 * stage_bytes<T>();
+}
+
+// Launch the particle pass (design warp_tiles, register-budget variant minb)
+// on the given state / sums buffers.
+template <typename T>
+int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, void* cy, void* cz,
+                   void* er, int* lev, CellSums* sums, uint32_t* flags,
                    unsigned long long* counters) {
-  const size_t smem = 2 * stage_bytes<T>();
+  const size_t smem = collide_smem<T>(warp_tiles);
   const CollideParams<T>* prm = (const CollideParams<T>*)c->prm;
   T* x = (T*)cx; T* y = (T*)cy; T* z = (T*)cz; T* e = (T*)er;
   const PhiloxRoundKeys rk = philox_round_keys(key0(c), key1(c));
   const float* tn = c->tab_nb;
   const float* tb = c->tab_b;
+  if (warp_tiles) {
+    const Tile* tiles = c->wtiles;
+    const int ntiles = c->nwtiles;
+    if (minb == 2)
+      collide_warp_kernel<T, 2><<<grid, kBlock, smem, c->stream>>>(
+          tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
+    else if (minb == 3)
+      collide_warp_kernel<T, 3><<<grid, kBlock, smem, c->stream>>>(
+          tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
+    else
+      collide_warp_kernel<T, 4><<<grid, kBlock, smem, c->stream>>>(
+          tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
+    CK(cudaGetLastError());
+    return USP_OK;
+  }
+  const Tile* tiles = c->tiles;
+  const int ntiles = c->ntiles;
   if (minb == 2)
     collide_kernel<T, 2><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
                                                             sums, flags, counters, rk, tn, tb);
@@ -1216,8 +1453,8 @@ int launch_step(usp_ctx* c) {
   cudaEvent_t e1 = nullptr;
   int rc = prof_begin(c, 0, &e1);
   if (rc) return rc;
-  rc = launch_collide<T>(c, c->minb, c->grid_collide, c->tiles, c->ntiles, c->cx, c->cy, c->cz,
-                         c->er, c->lev, c->sums, c->flags, c->counters);
+  rc = launch_collide<T>(c, c->warp_tiles, c->minb, c->grid_collide, c->cx, c->cy, c->cz, c->er,
+                         c->lev, c->sums, c->flags, c->counters);
   if (rc) return rc;
   if ((rc = prof_end(c, e1))) return rc;
   if ((rc = prof_begin(c, 1, &e1))) return rc;
@@ -1400,25 +1637,16 @@ int build_graph(usp_ctx* c, int steps) {
   return USP_OK;
 }
 
-// Autotuner of the particle pass: times each register-budget variant (2, 3
-// or 4 resident blocks per SM) on a scratch copy of the whole state (each
-// variant starts from the same copy; one untimed and two timed launches) and
-// keeps the fastest; within 1 % the variant with more resident blocks wins.
+// Autotuner of the particle pass: times each design (block-tiled, warp-tiled)
+// and register-budget variant (2, 3 or 4 resident blocks per SM) on a scratch
+// copy of the whole state (each variant starts from the same copy; one
+// untimed and two timed launches) and keeps the fastest; within 1 % the
+// earlier candidate wins (warp-tiled before block-tiled, more resident blocks
+// before fewer).
 template <typename T>
 int autotune(usp_ctx* c) {
   const size_t es = sizeof(T);
-  long long np = 0;
-  int nt = 0;
-  std::vector<Tile> ht(c->ntiles);
-  CK(cudaMemcpy(ht.data(), c->tiles, sizeof(Tile) * c->ntiles, cudaMemcpyDeviceToHost));
-  int last_cell = 0;
-  while (nt < c->ntiles) {
-    np += ht[nt].count;
-    last_cell = ht[nt].cell;
-    ++nt;
-  }
-  // include whole cells only: extend to the end of last_cell's tiles
-  while (nt < c->ntiles && ht[nt].cell == last_cell) ++nt;
+  const int last_cell = c->ncell - 1;
   const long long end = c->h_poff[last_cell] +
       ((c->h_uoff[last_cell + 1] - c->h_uoff[last_cell]) + kAlign - 1) / kAlign * kAlign;
   const size_t bytes = (size_t)end * (4 * es + 4);
@@ -1443,31 +1671,32 @@ int autotune(usp_ctx* c) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_mb = 3;
-  c->tune_ms.assign(3, 0.f);
-  for (int mb = 4; mb >= 2; --mb) {
-    int rc = fresh();
-    if (rc) return rc;
-    const int grid = std::max(1, std::min(nt, c->grid_by_minb[mb]));
-    rc = launch_collide<T>(c, mb, grid, c->tiles, nt, sx, sy, sz, se, sl, ssum, sflags, scnt);
-    if (rc) return rc;
-    CK(cudaEventRecord(e0, c->stream));
-    for (int r = 0; r < 2; ++r) {
-      rc = launch_collide<T>(c, mb, grid, c->tiles, nt, sx, sy, sz, se, sl, ssum, sflags, scnt);
+  int best_mb = 3, best_wt = 1;
+  c->tune_ms.assign(6, 0.f);
+  for (int wt = 1; wt >= 0; --wt) {
+    for (int mb = 4; mb >= 2; --mb) {
+      int rc = fresh();
       if (rc) return rc;
+      const int grid = c->grid_by_minb[wt][mb];
+      for (int r = 0; r < 3; ++r) {
+        if (r == 1) CK(cudaEventRecord(e0, c->stream));
+        rc = launch_collide<T>(c, wt, mb, grid, sx, sy, sz, se, sl, ssum, sflags, scnt);
+        if (rc) return rc;
+      }
+      CK(cudaEventRecord(e1, c->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      c->tune_ms[3 * wt + mb - 2] = ms / 2.f;
+      if (ms < 0.99f * best) { best = ms; best_mb = mb; best_wt = wt; }
     }
-    CK(cudaEventRecord(e1, c->stream));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    c->tune_ms[mb - 2] = ms / 2.f;
-    if (ms < 0.99f * best) { best = ms; best_mb = mb; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->launches += 9;
+  c->launches += 18;
   c->minb = best_mb;
-  c->grid_collide = c->grid_by_minb[best_mb];
+  c->warp_tiles = best_wt;
+  c->grid_collide = c->grid_by_minb[best_wt][best_mb];
   CK(cudaStreamSynchronize(c->stream));
   if (!c->cfg.alloc) cudaFree(scratch);
   else if (c->cfg.free_) c->cfg.free_(scratch, c->cfg.alloc_user);
@@ -1633,20 +1862,25 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   int rc = build_tiles(c, tile);
   if (rc) return fail(rc);
   {
-    // persistent grid per register-budget variant: as many resident blocks
-    // as the SMs hold
-    const size_t smem = 2 * (size_t)kTileMax * (4 * es + sizeof(int));
-    for (int mb = 2; mb <= 4; ++mb) {
-      void* fn = c->precision == USP_FP32 ? collide_variant<float>(mb) : collide_variant<double>(mb);
-      int per_sm = 1;
-      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-              cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem) != cudaSuccess)
-        return fail(USP_ECUDA);
-      c->grid_by_minb[mb] = std::max(1, std::min(c->ntiles, sm_count() * std::max(1, per_sm)));
+    // persistent grid per design and register-budget variant: as many
+    // resident blocks as the SMs hold (warp-tiled: no more warps than tiles)
+    const bool f32 = c->precision == USP_FP32;
+    for (int wt = 0; wt < 2; ++wt) {
+      const size_t smem = f32 ? collide_smem<float>(wt) : collide_smem<double>(wt);
+      for (int mb = 2; mb <= 4; ++mb) {
+        void* fn = f32 ? collide_variant<float>(wt, mb) : collide_variant<double>(wt, mb);
+        int per_sm = 1;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, smem) != cudaSuccess)
+          return fail(USP_ECUDA);
+        const int units = wt ? (c->nwtiles + kWarps - 1) / kWarps : c->ntiles;
+        c->grid_by_minb[wt][mb] = std::max(1, std::min(units, sm_count() * std::max(1, per_sm)));
+      }
     }
     c->minb = 3;
-    c->grid_collide = c->grid_by_minb[3];
+    c->warp_tiles = 1;
+    c->grid_collide = c->grid_by_minb[1][3];
   }
   if (n > 0) {
     rc = upload_state(c, h_cx, h_cy, h_cz, h_erot, h_lev, false);
@@ -2032,16 +2266,29 @@ int usp_info(usp_ctx* c, int64_t* np, int* nc, int* prec, int64_t* step, int* ti
 
 int64_t usp_launch_count(usp_ctx* c) { return c ? c->launches : -1; }
 
-int usp_tuning(usp_ctx* c, int* blocks_per_sm, double* ms) {
+int usp_tuning(usp_ctx* c, int* warp_tiles, int* blocks_per_sm, double* ms) {
   if (!c) return USP_EINVAL;
-  if (c->kind != 0) {
-    if (blocks_per_sm) *blocks_per_sm = 0;
-    if (ms) ms[0] = ms[1] = ms[2] = 0.0;
-    return USP_OK;
-  }
-  if (blocks_per_sm) *blocks_per_sm = c->minb;
+  const bool homog = c->kind == 0;
+  if (warp_tiles) *warp_tiles = homog ? c->warp_tiles : 0;
+  if (blocks_per_sm) *blocks_per_sm = homog ? c->minb : 0;
   if (ms)
-    for (int i = 0; i < 3; ++i) ms[i] = i < (int)c->tune_ms.size() ? c->tune_ms[i] : 0.0;
+    for (int i = 0; i < 6; ++i) ms[i] = homog && i < (int)c->tune_ms.size() ? c->tune_ms[i] : 0.0;
+  return USP_OK;
+}
+
+int usp_set_variant(usp_ctx* c, int warp_tiles, int blocks_per_sm) {
+  if (!c || c->kind != 0 || (warp_tiles != 0 && warp_tiles != 1) || blocks_per_sm < 2 ||
+      blocks_per_sm > 4)
+    return USP_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->graph_exec) {  // the captured step launches the previous variant
+    cudaGraphExecDestroy(c->graph_exec);
+    cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+  }
+  c->warp_tiles = warp_tiles;
+  c->minb = blocks_per_sm;
+  c->grid_collide = c->grid_by_minb[warp_tiles][blocks_per_sm];
   return USP_OK;
 }
 

@@ -39,7 +39,7 @@ C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, 
 
 EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogeneous", "usp_step", "usp_moments",
             "usp_get_particles", "usp_set_particles", "usp_step_host", "usp_status", "usp_sync",
-            "usp_info", "usp_tuning", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
+            "usp_info", "usp_tuning", "usp_set_variant", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
             "usp_moments_noalloc", "usp_init_channel", "usp_channel_sample",
             "usp_channel_read", "usp_channel_get_particles", "usp_init_plane", "usp_plane_count",
             "usp_plane_get_particles", "usp_sample", "usp_sample_read", "usp_destroy"]
@@ -120,7 +120,8 @@ def lib():
             L.usp_sync.argtypes = [_CTX]
             L.usp_info.argtypes = [_CTX, _I64, C.POINTER(C.c_int), C.POINTER(C.c_int), _I64,
                                    C.POINTER(C.c_int), _I64]
-            L.usp_tuning.argtypes = [_CTX, C.POINTER(C.c_int), _D]
+            L.usp_tuning.argtypes = [_CTX, C.POINTER(C.c_int), C.POINTER(C.c_int), _D]
+            L.usp_set_variant.argtypes = [_CTX, C.c_int, C.c_int]
             L.usp_launch_count.argtypes = [_CTX]
             L.usp_launch_count.restype = C.c_int64
             L.usp_profile_enable.argtypes = [_CTX, C.c_int]
@@ -444,11 +445,18 @@ def usp_info(ctx: Context) -> dict:
 
 
 def usp_tuning(ctx: Context):
-    """(blocks_per_sm of the particle-pass variant in use, autotuner ms[3])."""
+    """(warp_tiles, blocks_per_sm) of the particle-pass variant in use and the
+    autotuner's ms per launch [block-tiled 2, 3, 4, warp-tiled 2, 3, 4]."""
+    wt = C.c_int()
     mb = C.c_int()
-    ms = np.zeros(3)
-    _check(lib().usp_tuning(ctx.h, C.byref(mb), _p(ms, C.c_double)), "usp_tuning")
-    return mb.value, ms
+    ms = np.zeros(6)
+    _check(lib().usp_tuning(ctx.h, C.byref(wt), C.byref(mb), _p(ms, C.c_double)), "usp_tuning")
+    return (wt.value, mb.value), ms
+
+
+def usp_set_variant(ctx: Context, warp_tiles: int, blocks_per_sm: int):
+    """Force the particle-pass variant of a homogeneous context."""
+    _check(lib().usp_set_variant(ctx.h, int(warp_tiles), int(blocks_per_sm)), "usp_set_variant")
 
 
 def usp_launch_count(ctx: Context) -> int:

@@ -144,6 +144,36 @@ def test_fp32_multi_step_field_error_is_small():
     assert np.max(np.abs(gm[6] - om[6]) / np.maximum(om[6], 100.0)) < 1e-3
 
 
+@pytest.mark.parametrize("precision,steps", [(usp.USP_FP64, 4), (usp.USP_FP32, 1)])
+def test_every_particle_pass_variant_matches_oracle(precision, steps):
+    """The block-tiled and the warp-tiled particle pass at each register
+    budget, forced in turn, against one oracle run: cells of 2 to 6000
+    particles, so that cells span several tiles of either size with ragged
+    tails."""
+    w = I.batched_instances(seed=21, n_inst=30, nmin=2, nmax=6000, steps=steps)
+    form = 1 if precision == usp.USP_FP32 else 0
+    p = w.particles.astype_f32_exact() if form else w.particles
+    st = O.State.from_arrays(p.cx, p.cy, p.cz, p.erot, p.lev)
+    sp = O.species(**w.species)
+    O.homog_step(sp, form, w.seed, 0, steps, w.offsets, w.ndens, _oracle_dt(w), st)
+    om = O.moments(sp, w.offsets, st)
+    for wt in (0, 1):
+        for mb in (2, 3, 4):
+            ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, _gpu_dt(w), p.cx, p.cy,
+                                           p.cz, p.erot, p.lev, precision=precision,
+                                           seed=w.seed, use_graph=True)
+            usp.usp_set_variant(ctx, wt, mb)
+            assert usp.usp_tuning(ctx)[0] == (wt, mb)
+            usp.usp_step(ctx, steps)
+            gm = usp.usp_moments(ctx)
+            gl = usp.usp_get_particles(ctx)[4]
+            flags, _ = usp.usp_status(ctx)
+            ctx.destroy()
+            assert flags & usp.ERROR_FLAGS == 0, (wt, mb)
+            _check_moments(om, gm, sp)
+            assert np.mean(gl != st.lev) < 1e-5, (wt, mb)
+
+
 def test_conservation_on_gpu_fp64():
     w = I.batched_instances(seed=11, n_inst=8, nmin=1000, nmax=5000, steps=0)
     sp = O.species(**w.species)
