@@ -155,30 +155,38 @@ __device__ void b_row(int n, float p, float* T) {
 // Search of a table row: the number of leading entries <= u.  Rows are
 // non-decreasing (cumulative sums, +inf once the sum stops growing), so the
 // entries <= u of a group of four are its leading ones and their count is
-// the step of the sequential search through the group.
-__device__ __forceinline__ int row_search(const float* __restrict__ T, float u) {
+// the step of the sequential search through the group.  The caller holds the
+// row's first group (t0, loaded before the particle's draws so that its
+// latency hides behind them); the rest of the row is read only when u lies
+// beyond all four.
+__device__ __forceinline__ int count4(const float4& t, float u) {
+  return (u >= t.x) + (u >= t.y) + (u >= t.z) + (u >= t.w);
+}
+
+__device__ __forceinline__ int row_search(const float* __restrict__ T, const float4& t0,
+                                          float u) {
+  int k = count4(t0, u);
+  if (k < 4) return k;
   const float4* T4 = reinterpret_cast<const float4*>(T);
-  int k = 0;
 #pragma unroll 1
-  for (int q = 0; q < kJK / 4; ++q) {
-    const float4 t = T4[q];
-    const int c = (u >= t.x) + (u >= t.y) + (u >= t.z) + (u >= t.w);
+  for (int q = 1; q < kJK / 4; ++q) {
+    const int c = count4(T4[q], u);
     k += c;
     if (c < 4) break;
   }
   return k;
 }
 
-__device__ __forceinline__ int nb_tab(const float* __restrict__ T, int r, float p, float u,
-                                      uint32_t& fl) {
+__device__ __forceinline__ int nb_tab(const float* __restrict__ T, const float4& t0, int r,
+                                      float p, float u, uint32_t& fl) {
   if (r <= 0 || !(p < 1.0f)) return 0;
-  if (r > kJR || T[0] < 0.0f) return nb_inv(r, p, u, fl);
-  const int k = row_search(T, u);
+  if (r > kJR || t0.x < 0.0f) return nb_inv(r, p, u, fl);
+  const int k = row_search(T, t0, u);
   return k < kJK ? k : nb_inv(r, p, u, fl);
 }
 
-__device__ __forceinline__ int b_tab(const float* __restrict__ T, int n, float p, float u,
-                                     uint32_t& fl) {
+__device__ __forceinline__ int b_tab(const float* __restrict__ T, const float4& t0, int n,
+                                     float p, float u, uint32_t& fl) {
   if (n <= 0) return 0;
   if (p >= 1.0f) {
     if (p > 1.0f) fl |= F_PB_CLAMP;
@@ -187,10 +195,10 @@ __device__ __forceinline__ int b_tab(const float* __restrict__ T, int n, float p
   if (!(p > 0.0f)) return 0;
   const bool flip = p > 0.5f;
   int k;
-  if (n >= kJR || T[0] < 0.0f) {
+  if (n >= kJR || t0.x < 0.0f) {
     k = binv(n, flip ? rn_sub(1.0f, p) : p, u, fl);
   } else {
-    k = row_search(T, u);    // T[n] = +inf ends the scan by k = n < kJK
+    k = row_search(T, t0, u);    // T[n] = +inf ends the scan by k = n < kJK
   }
   return flip ? n - k : k;
 }
@@ -205,6 +213,17 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
                                             T* acc, int& accI, int& maxI, uint32_t& fl,
                                             const float* __restrict__ tnb,
                                             const float* __restrict__ tb) {
+  // the particle's jump-table rows (FP32 form): first groups loaded ahead
+  const int I = lv;
+  const float* rnb = tnb;
+  const float* rb = tb;
+  float4 t_nb = make_float4(0.f, 0.f, 0.f, 0.f), t_b = t_nb;
+  if constexpr (sizeof(T) == 4) {
+    rnb += (size_t)(I < kJR ? I : 0) * kJK;
+    rb += (size_t)(I < kJR ? I : 0) * kJK;
+    t_nb = __ldg(reinterpret_cast<const float4*>(rnb));
+    t_b = __ldg(reinterpret_cast<const float4*>(rb));
+  }
   U4 w, w2;
   philox4x32_10_pair(pid, P.step, PTAG_NORMALS, PTAG_JUMPS, 0u, rk, w, w2);
   T g0, g1, g2, g3;
@@ -223,11 +242,10 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   er = P.a_rot + root * root;
   // I' = I + NB(I + 1, p_NB) - B(I, p_B)
   const T u5 = uniform_open<T>(w2.x), u6 = uniform_open<T>(w2.y);
-  const int I = lv;
   int up, dn;
   if constexpr (sizeof(T) == 4) {
-    up = nb_tab(tnb + (size_t)(I < kJR ? I : 0) * kJK, I + 1, P.p_nb, u5, fl);
-    dn = b_tab(tb + (size_t)(I < kJR ? I : 0) * kJK, I, P.p_b, u6, fl);
+    up = nb_tab(rnb, t_nb, I + 1, P.p_nb, u5, fl);
+    dn = b_tab(rb, t_b, I, P.p_b, u6, fl);
   } else {
     up = sample_nb<T>(I + 1, P.p_nb, u5, fl);
     dn = sample_b<T>(I, P.p_b, u6, fl);

@@ -703,7 +703,11 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
 }
 
 // per particle: the bilinear polynomial of its quadrant, then the collision
-// of Sec. 4.D; one warp per cell, per-cell sums for the conservation step
+// of Sec. 4.D; one warp per cell, per-cell sums for the conservation step.
+// The warp copies its cell's stencil record into shared memory with
+// coalesced 8-byte loads, so that the per-particle reads of the polynomial
+// coefficients are shared-memory broadcasts rather than ~80 dependent global
+// loads per particle.
 template <typename T>
 __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<double>* __restrict__ cells,
                            const PlParams<T>* __restrict__ prm, const T* __restrict__ x,
@@ -713,13 +717,23 @@ __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<d
                            const long long* __restrict__ dstep, const PhiloxRoundKeys rk,
                            uint32_t* flags, unsigned long long* counters) {
   __shared__ BlockTally tal;
+  static_assert(sizeof(PlParams<T>) % 8 == 0, "records copied as 8-byte words");
+  constexpr int kWords = (int)(sizeof(PlParams<T>) / 8);
+  __shared__ unsigned long long sP[kBlk / 32][kWords];
   tally_init(tal);
   const int lane = threadIdx.x & 31;
   const uint32_t step = (uint32_t)*dstep;
+  unsigned long long* myP = sP[threadIdx.x >> 5];
+  const PlParams<T>& P = *reinterpret_cast<const PlParams<T>*>(myP);
   for (int c = warp_global(); c < ncell; c += warps_total()) {
     const ChCellT<double>& cs = cells[c];
     if (!cs.active) continue;
-    const PlParams<T>& P = prm[c];
+    {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(prm + c);
+      __syncwarp();   // the previous cell's readers are done
+      for (int w = lane; w < kWords; w += 32) myP[w] = src[w];
+      __syncwarp();
+    }
     // cell velocity in T: one conversion per warp (lanes 0-2), then broadcast
     const T uc = (T)(lane < 3 ? cs.U[lane < 3 ? lane : 0] : 0.0);
     const T Uc0 = __shfl_sync(0xffffffffu, uc, 0), Uc1 = __shfl_sync(0xffffffffu, uc, 1),
@@ -747,7 +761,8 @@ __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<d
         ++nfb;
       }
       T v0 = cx[j], v1 = cy[j], v2 = cz[j], en = er[j];
-      const int ln = collide_particle_t(P, f, v0, v1, v2, en, lev[j], pid[j], step, rk, tl);
+      const int ln = collide_particle_t<sizeof(T) == 4>(P, f, v0, v1, v2, en, lev[j], pid[j],
+                                                          step, rk, tl);
       cx[j] = v0; cy[j] = v1; cz[j] = v2; er[j] = en;
       lev[j] = ln;
       maxI = max(maxI, ln);

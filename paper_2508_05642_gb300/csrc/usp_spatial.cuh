@@ -112,6 +112,55 @@ __device__ __forceinline__ void relax_t(const P_& P, T alpha, const T* f, T& ttr
 }
 
 
+// FP32 forms of relax_t / chol3_t / the jump parameters with one correctly
+// rounded reciprocal (or reciprocal square root) in place of each group of
+// divisions.  Used by the FP32 plane path, whose per-particle arithmetic is
+// compared with the oracle statistically; the other forms keep the IEEE
+// divisions operation for operation.
+__device__ __forceinline__ bool chol3_fast(const float* M, float* L) {
+  if (!(M[0] > 0.f)) return false;
+  const float r0 = rsqrtf(M[0]);
+  const float l00 = M[0] * r0;
+  const float l10 = M[3] * r0, l20 = M[4] * r0;
+  const float d1 = M[1] - l10 * l10;
+  if (!(d1 > 0.f)) return false;
+  const float r1 = rsqrtf(d1);
+  const float l11 = d1 * r1;
+  const float l21 = (M[5] - l20 * l10) * r1;
+  const float d2 = M[2] - l20 * l20 - l21 * l21;
+  if (!(d2 > 0.f)) return false;
+  L[0] = l00; L[1] = l10; L[2] = l11; L[3] = l20; L[4] = l21; L[5] = sqrtf(d2);
+  return true;
+}
+
+template <typename P_>
+__device__ __forceinline__ void relax_fast(const P_& P, float alpha, const float* f, float& ttr,
+                                           float& trot, float& evr, bool& cl) {
+  const float ioR = __frcp_rn((1.f - alpha * alpha) * P.R);   // 1 / ((1 - alpha^2) R)
+  ttr = f[3] - (P.gtr * (f[3] - f[4]) + P.gtv * (f[3] - f[5])) * ioR * (2.f / 3.f);
+  trot = f[4] + (P.gtr * (f[3] - f[4]) - P.grv * (f[4] - f[5])) * ioR;
+  const float ev = f[5] > 0.f ? P.R * P.theta * __frcp_rn(expm1f(P.theta * __frcp_rn(f[5])))
+                              : 0.f;
+  evr = ev + (P.gtv * (f[3] - f[5]) + P.grv * (f[4] - f[5])) * (ioR * P.R);
+  cl = false;
+  if (ttr < 0.f) { ttr = 0.f; cl = true; }
+  if (trot < 0.f) { trot = 0.f; cl = true; }
+  if (evr < 0.f) { evr = 0.f; cl = true; }
+}
+
+template <bool kFast, typename T, typename P_>
+__device__ __forceinline__ void relax_sel(const P_& P, T alpha, const T* f, T& ttr, T& trot,
+                                          T& evr, bool& cl) {
+  if constexpr (kFast) relax_fast(P, alpha, f, ttr, trot, evr, cl);
+  else relax_t(P, alpha, f, ttr, trot, evr, cl);
+}
+
+template <bool kFast, typename T>
+__device__ __forceinline__ bool chol3_sel(const T* M, T* L) {
+  if constexpr (kFast) return chol3_fast(M, L);
+  else return chol3_t(M, L);
+}
+
 // Counts kept per thread by the particle collision and reduced per warp.
 struct CollideTally {
   uint32_t fl;
@@ -123,13 +172,14 @@ struct CollideTally {
 // of P: relaxation temperatures, M = tau D_tr and its Cholesky factor with
 // the Sec. 3.A.3 adjustment (four passes, then nu = 0 with alpha^2 = B),
 // Eqs. update_ci / update_erot / update_evib.  Returns the new level.
-template <typename T, typename P_>
+template <bool kFast = false, typename T, typename P_>
 __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx, T& vy, T& vz,
                                                   T& e, int I, uint32_t id, uint32_t step,
                                                   const PhiloxRoundKeys& rk, CollideTally& t) {
+  static_assert(!kFast || sizeof(T) == 4, "the fast forms are FP32");
   T alpha = P.alpha, nu = P.nu_ref, ttr, trot, evr;
   bool cl;
-  relax_t(P, alpha, f, ttr, trot, evr, cl);
+  relax_sel<kFast>(P, alpha, f, ttr, trot, evr, cl);
   const T RT = P.R * f[3];
   T M[6], L[6];
   auto fill = [&](T nu_) {
@@ -139,7 +189,7 @@ __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx
     M[3] = nu_ * f[9]; M[4] = nu_ * f[10]; M[5] = nu_ * f[11];
   };
   fill(nu);
-  if (!chol3_t(M, L)) {
+  if (!chol3_sel<kFast>(M, L)) {
     ++t.nfix;
     T lmin, lmax;
     sym3_minmax(f + 6, lmin, lmax);
@@ -159,10 +209,10 @@ __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx
       const T prm_ = T(2) * P.mu_p * (T(1) - am * am * am) / (P.dt * (T(1) + am * am * am));
       alpha = (fabs(prm_ - P.Pr) < fabs(prp - P.Pr)) ? am : ap;
       bool cl2;
-      relax_t(P, alpha, f, ttr, trot, evr, cl2);
+      relax_sel<kFast>(P, alpha, f, ttr, trot, evr, cl2);
       cl = cl || cl2;
       fill(nu);
-      ok = chol3_t(M, L);
+      ok = chol3_sel<kFast>(M, L);
     }
     if (!ok) {
       // nu = 0 with alpha^2 = B, admissible whenever T_tr^rel > 0
@@ -173,7 +223,7 @@ __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx
       const T prm_ = T(2) * P.mu_p * (T(1) - am * am * am) / (P.dt * (T(1) + am * am * am));
       alpha = (fabs(prm_ - P.Pr) < fabs(prp - P.Pr)) ? am : ap;
       bool cl2;
-      relax_t(P, alpha, f, ttr, trot, evr, cl2);
+      relax_sel<kFast>(P, alpha, f, ttr, trot, evr, cl2);
       cl = cl || cl2;
       if (!(ttr > T(0))) t.fl |= F_CHOL_FAIL_AFTER_FIX;
       const T sq = ttr > T(0) ? sqrt(P.R * ttr) : T(0);
@@ -198,8 +248,14 @@ __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx
   const T root = sqrt(e) * alpha + sqrt(a) * g3;
   e = a + root * root;
   // Eq. update_evib
-  const T eb = evr / (P.R * P.theta);
-  const T p_nb = T(1) / (T(1) + eb * (T(1) - a2));
+  T eb, p_nb;
+  if constexpr (kFast) {
+    eb = evr * __frcp_rn(P.R * P.theta);
+    p_nb = __frcp_rn(T(1) + eb * (T(1) - a2));
+  } else {
+    eb = evr / (P.R * P.theta);
+    p_nb = T(1) / (T(1) + eb * (T(1) - a2));
+  }
   const T p_b = (T(1) + eb) * (T(1) - a2);
   uint32_t f1 = 0;
   const int up = sample_nb<T>(I + 1, p_nb, uniform_open<T>(w2.x), f1);
