@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--cylinder-steps", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--variant", default=None,
+                    help="force the FP32 particle-pass variant after autotuning: "
+                         "'b2'..'b4' block-tiled or 'w2'..'w4' warp-tiled (for profiling a "
+                         "given kernel on a smaller case)")
     return ap.parse_args()
 
 
@@ -282,6 +286,8 @@ def run_ours(args, rank, world, local):
                                    p.lev, precision=usp.USP_FP32, seed=w.seed,
                                    stream=stream.cuda_stream, use_graph=True)
     N = w.n_particles
+    if args.variant:
+        usp.usp_set_variant(ctx, 1 if args.variant[0] == "w" else 0, int(args.variant[1:]))
     (warp_tiles, minb), tune_ms = usp.usp_tuning(ctx)
     usp.usp_step(ctx, args.warmup)
     torch.cuda.synchronize()

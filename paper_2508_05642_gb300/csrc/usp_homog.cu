@@ -62,8 +62,10 @@ struct CellState {
   int maxI;                  // bound on the levels entering the step (jump-table rows)
 };
 
+// 16-byte aligned and sized: the block-tiled particle pass bulk-copies a
+// cell's record into shared memory with its particles
 template <typename T>
-struct CollideParams {
+struct alignas(16) CollideParams {
   T U[3], Us[3];
   T as, ar;                  // alpha * s, alpha * sqrt(r)
   T Lp[6];                   // sqrt(1 - alpha^2) L, L L^T = tau D_tr
@@ -85,10 +87,6 @@ struct CellSums {
 struct Tile {
   int cell, start, count, pad_;
 };
-
-__device__ __forceinline__ void flag_or(uint32_t* flags, uint32_t f) {
-  if (f) atomicOr(flags, f);
-}
 
 // ---------------------------------------------------------------------------
 // Jump tables of the FP32 form.  In a homogeneous cell p_NB and p_B are cell
@@ -382,151 +380,6 @@ __device__ __forceinline__ int* sb_l(unsigned char* b) {
 // segment padding, so every copy is a multiple of 16 bytes)
 __device__ __forceinline__ int round4(int n) { return (n + 3) & ~3; }
 
-// Issue the five bulk loads of tile t into buffer b (one thread).
-template <typename T>
-__device__ __forceinline__ void stage_load(const Tile& tl, long long off, unsigned char* b,
-                                           uint64_t* bar, const T* cx, const T* cy, const T* cz,
-                                           const T* er, const int* lev) {
-  const int n4 = round4(tl.count);
-  const long long base = off + tl.start;
-  const uint32_t bt = (uint32_t)(n4 * sizeof(T)), bl = (uint32_t)(n4 * sizeof(int));
-  T* X = sb_x<T>(b);
-  mbar_expect_tx(bar, 4 * bt + bl);
-  if (n4 > 0) {
-    bulk_g2s(X, cx + base, bt, bar);
-    bulk_g2s(X + kTileMax, cy + base, bt, bar);
-    bulk_g2s(X + 2 * kTileMax, cz + base, bt, bar);
-    bulk_g2s(X + 3 * kTileMax, er + base, bt, bar);
-    bulk_g2s(sb_l<T>(b), lev + base, bl, bar);
-  }
-}
-
-// Particle pass of one step.  Each persistent block owns a contiguous range
-// of the tile list (tiles of one cell are adjacent, so a block meets few cell
-// boundaries); each tile (<= kTileMax particles of one cell) is brought into
-// shared memory by bulk copies while the previous tile is being processed (two
-// buffers), updated in place, and written back by bulk copies.  Cell sums are
-// flushed when the cell changes.
-template <typename T, int MINB>
-__global__ void __launch_bounds__(kBlock, MINB)
-collide_kernel(const Tile* __restrict__ tiles, int ntiles,
-               const CollideParams<T>* __restrict__ prm, T* __restrict__ cx,
-               T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
-               int* __restrict__ lev, CellSums* __restrict__ sums, uint32_t* flags,
-               unsigned long long* counters, const PhiloxRoundKeys rk,
-               const float* __restrict__ tab_nb, const float* __restrict__ tab_b) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ __align__(16) CollideParams<T> Ps;   // the current tile's cell parameters
-  const int tid = threadIdx.x;
-  const int G = gridDim.x;
-  const int t_begin = (int)(((long long)ntiles * blockIdx.x) / G);
-  const int t_end = (int)(((long long)ntiles * (blockIdx.x + 1)) / G);
-  if (t_begin >= t_end) return;
-  if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    mbar_init_fence();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const Tile tl = tiles[t_begin];
-    stage_load<T>(tl, prm[tl.cell].off, smem, &bar[0], cx, cy, cz, er, lev);
-  }
-  uint32_t phase[2] = {0u, 0u};
-  bool inflight[2] = {true, false};  // meaningful in thread 0, which issues the loads
-  T acc[10];
-#pragma unroll
-  for (int i = 0; i < 10; ++i) acc[i] = T(0);
-  int accI = 0, maxI = 0;
-  uint32_t fl = 0;
-  int npb = 0;
-  int it = 0;
-  for (int t = t_begin; t < t_end; ++t, ++it) {
-    const int b = it & 1;
-    const int tn = t + 1;
-    if (tid == 0 && tn < t_end) {
-      // buffer b^1 was the source of the previous tile's bulk store
-      bulk_wait_read_all();
-      const Tile tn_l = tiles[tn];
-      stage_load<T>(tn_l, prm[tn_l.cell].off, smem + (b ^ 1) * stage_bytes<T>(), &bar[b ^ 1], cx,
-                    cy, cz, er, lev);
-      inflight[b ^ 1] = true;
-    }
-    const Tile tl = tiles[t];
-    {
-      // stage the cell parameters of tile t (visible after the barrier below)
-      constexpr int nw = (int)(sizeof(CollideParams<T>) / 4);
-      if (tid < nw)
-        reinterpret_cast<uint32_t*>(&Ps)[tid] =
-            reinterpret_cast<const uint32_t*>(&prm[tl.cell])[tid];
-    }
-    const bool ok = mbar_wait_bounded(&bar[b], phase[b]);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
-      break;
-    }
-    phase[b] ^= 1u;
-    if (tid == 0) inflight[b] = false;
-    const CollideParams<T>& P = Ps;
-    if (P.active) {
-      T* X = sb_x<T>(smem + b * stage_bytes<T>());
-      int* Lv = sb_l<T>(smem + b * stage_bytes<T>());
-      const uint32_t pid0 = P.pid0 + (uint32_t)tl.start;
-      const float* tnb = tab_nb + (size_t)tl.cell * kJR * kJK;
-      const float* tb = tab_b + (size_t)tl.cell * kJR * kJK;
-#pragma unroll 1
-      for (int k = tid; k < tl.count; k += kBlock) {
-        T x = X[k], y = X[k + kTileMax], z = X[k + 2 * kTileMax], e = X[k + 3 * kTileMax];
-        int l = Lv[k];
-        uint32_t f1 = 0;
-        collide_one<T>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb, tb);
-        X[k] = x; X[k + kTileMax] = y; X[k + 2 * kTileMax] = z; X[k + 3 * kTileMax] = e;
-        Lv[k] = l;
-        npb += (f1 & F_PB_CLAMP) ? 1 : 0;
-        fl |= f1;
-      }
-      // results in shared memory -> visible to the bulk-copy engine
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        const int n4 = round4(tl.count);
-        const long long base = P.off + tl.start;
-        const uint32_t bt = (uint32_t)(n4 * sizeof(T)), bl = (uint32_t)(n4 * sizeof(int));
-        if (n4 > 0) {
-          bulk_s2g(cx + base, X, bt);
-          bulk_s2g(cy + base, X + kTileMax, bt);
-          bulk_s2g(cz + base, X + 2 * kTileMax, bt);
-          bulk_s2g(er + base, X + 3 * kTileMax, bt);
-          bulk_s2g(lev + base, Lv, bl);
-        }
-        bulk_commit();
-      }
-      // sums of a cell are flushed once its last tile in this range is done
-      if (tn >= t_end || tiles[tn].cell != tl.cell) {
-        flush_sums<T>(acc, accI, maxI, &sums[tl.cell]);
-#pragma unroll
-        for (int i = 0; i < 10; ++i) acc[i] = T(0);
-        accI = 0;
-        maxI = 0;
-      }
-    } else {
-      __syncthreads();
-    }
-  }
-  if (fl) {
-    flag_or(flags, fl);
-    if (npb) atomicAdd(&counters[C_PB_CLAMP], (unsigned long long)npb);
-  }
-  if (tid == 0) {
-    // loads still in flight after a timeout: wait for them (bounded) before
-    // the block's shared memory is released
-    for (int b = 0; b < 2; ++b)
-      if (inflight[b]) (void)mbar_wait_bounded(&bar[b], phase[b]);
-    bulk_wait_all();
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Warp-tiled particle pass.  Every warp runs its own pipeline over a
 // contiguous range of small tiles (<= kWT particles of one cell): kWS staging
@@ -723,6 +576,191 @@ collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
     bulk_wait_all();
   }
 }
+
+// ---------------------------------------------------------------------------
+// Block-tiled particle pass.  Each persistent block owns a contiguous range
+// of the tile list (tiles of one cell are adjacent, so a block meets few cell
+// boundaries); each tile (<= kTileMax particles of one cell) and its cell's
+// CollideParams are brought into shared memory by bulk copies while the
+// previous tile is being processed (two buffers), updated in place, and
+// written back by bulk copies.  The block's warps share each tile but never
+// wait for one another: a warp that finishes its part of a tile counts itself
+// done; the last one issues the tile's bulk store and, once the store has
+// read the buffer, releases it to the producer (thread 0), which refills it
+// with the tile after next.  Cell sums are reduced per warp when the cell
+// changes.
+// ---------------------------------------------------------------------------
+template <typename T>
+constexpr size_t bstage_bytes() {
+  return stage_bytes<T>() + sizeof(CollideParams<T>);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+      : "memory");
+}
+
+// the five state loads of a tile and its cell's record (one thread)
+template <typename T>
+__device__ __forceinline__ void stage_load_p(const Tile& tl, const CollideParams<T>* prm,
+                                             unsigned char* b, uint64_t* bar, const T* cx,
+                                             const T* cy, const T* cz, const T* er,
+                                             const int* lev) {
+  const CollideParams<T>* pc = prm + tl.cell;
+  const int n4 = round4(tl.count);
+  const long long base = pc->off + tl.start;
+  const uint32_t bt = (uint32_t)(n4 * sizeof(T)), bl = (uint32_t)(n4 * sizeof(int));
+  T* X = sb_x<T>(b);
+  mbar_expect_tx(bar, 4 * bt + bl + (uint32_t)sizeof(CollideParams<T>));
+  bulk_g2s(b + stage_bytes<T>(), pc, (uint32_t)sizeof(CollideParams<T>), bar);
+  if (n4 > 0) {
+    bulk_g2s(X, cx + base, bt, bar);
+    bulk_g2s(X + kTileMax, cy + base, bt, bar);
+    bulk_g2s(X + 2 * kTileMax, cz + base, bt, bar);
+    bulk_g2s(X + 3 * kTileMax, er + base, bt, bar);
+    bulk_g2s(sb_l<T>(b), lev + base, bl, bar);
+  }
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
+collide_kernel(const Tile* __restrict__ tiles, int ntiles,
+               const CollideParams<T>* __restrict__ prm, T* __restrict__ cx,
+               T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
+               int* __restrict__ lev, CellSums* __restrict__ sums, uint32_t* flags,
+               unsigned long long* counters, const PhiloxRoundKeys rk,
+               const float* __restrict__ tab_nb, const float* __restrict__ tab_b) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[2], empty[2];
+  __shared__ int done[2];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int G = gridDim.x;
+  const int t_begin = (int)(((long long)ntiles * blockIdx.x) / G);
+  const int t_end = (int)(((long long)ntiles * (blockIdx.x + 1)) / G);
+  if (t_begin >= t_end) return;
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], 1);
+    mbar_init(&empty[1], 1);
+    done[0] = done[1] = 0;
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t inflight = 0;   // thread 0: buffers with a load in flight
+  if (tid == 0) {
+    stage_load_p<T>(tiles[t_begin], prm, smem, &full[0], cx, cy, cz, er, lev);
+    inflight = 1u;
+  }
+  uint32_t fph = 0, eph = 0;   // parities of the next full / empty completion per buffer
+  T acc[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) acc[i] = T(0);
+  int accI = 0, maxI = 0;
+  uint32_t fl = 0;
+  int npb = 0;
+  int it = 0;
+  for (int t = t_begin; t < t_end; ++t, ++it) {
+    const int b = it & 1;
+    unsigned char* buf = smem + b * bstage_bytes<T>();
+    if (tid == 0 && t + 1 < t_end) {
+      // the other buffer takes tile t + 1 once every warp is done with tile
+      // t - 1 there and its store has read it
+      bool ok = true;
+      if (it >= 1) {
+        ok = mbar_wait_bounded(&empty[b ^ 1], (eph >> (b ^ 1)) & 1u);
+        eph ^= 1u << (b ^ 1);
+      }
+      if (ok) {
+        stage_load_p<T>(tiles[t + 1], prm, smem + (b ^ 1) * bstage_bytes<T>(), &full[b ^ 1], cx,
+                        cy, cz, er, lev);
+        inflight |= 1u << (b ^ 1);
+      } else {
+        atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
+      }
+    }
+    const Tile tl = tiles[t];
+    const bool ok = mbar_wait_bounded(&full[b], (fph >> b) & 1u);
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
+      break;
+    }
+    fph ^= 1u << b;
+    if (tid == 0) inflight &= ~(1u << b);
+    const CollideParams<T>& P = *reinterpret_cast<const CollideParams<T>*>(buf + stage_bytes<T>());
+    const bool active = P.active != 0;
+    if (active) {
+      T* X = sb_x<T>(buf);
+      int* Lv = sb_l<T>(buf);
+      const uint32_t pid0 = P.pid0 + (uint32_t)tl.start;
+      const float* tnb = tab_nb + (size_t)tl.cell * kJR * kJK;
+      const float* tb = tab_b + (size_t)tl.cell * kJR * kJK;
+#pragma unroll 1
+      for (int k = tid; k < tl.count; k += kBlock) {
+        T x = X[k], y = X[k + kTileMax], z = X[k + 2 * kTileMax], e = X[k + 3 * kTileMax];
+        int l = Lv[k];
+        uint32_t f1 = 0;
+        collide_one<T>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb, tb);
+        X[k] = x; X[k + kTileMax] = y; X[k + 2 * kTileMax] = z; X[k + 3 * kTileMax] = e;
+        Lv[k] = l;
+        npb += (f1 & F_PB_CLAMP) ? 1 : 0;
+        fl |= f1;
+      }
+    }
+    // this warp's results -> visible to the bulk-copy engine; count it done
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      if (atomicAdd(&done[b], 1) == kBlock / 32 - 1) {
+        // last warp of the tile: store it, wait until the store has read the
+        // buffer, release the buffer
+        __threadfence_block();
+        done[b] = 0;
+        const int n4 = round4(tl.count);
+        if (active && n4 > 0) {
+          const long long base = P.off + tl.start;
+          const uint32_t bt = (uint32_t)(n4 * sizeof(T)), bl = (uint32_t)(n4 * sizeof(int));
+          T* X = sb_x<T>(buf);
+          bulk_s2g(cx + base, X, bt);
+          bulk_s2g(cy + base, X + kTileMax, bt);
+          bulk_s2g(cz + base, X + 2 * kTileMax, bt);
+          bulk_s2g(er + base, X + 3 * kTileMax, bt);
+          bulk_s2g(lev + base, sb_l<T>(buf), bl);
+        }
+        bulk_commit();
+        bulk_wait_read_all();
+        mbar_arrive(&empty[b]);
+      }
+    }
+    // sums of a cell are flushed once its last tile in this range is done
+    if (t + 1 >= t_end || tiles[t + 1].cell != tl.cell) {
+      if (active) flush_sums_warp<T>(acc, accI, maxI, &sums[tl.cell]);
+#pragma unroll
+      for (int i = 0; i < 10; ++i) acc[i] = T(0);
+      accI = 0;
+      maxI = 0;
+    }
+  }
+  fl = __reduce_or_sync(0xffffffffu, fl);
+  npb = __reduce_add_sync(0xffffffffu, npb);
+  if (lane == 0) {
+    if (fl) {
+      atomicOr(flags, fl);
+      if (npb) atomicAdd(&counters[C_PB_CLAMP], (unsigned long long)npb);
+    }
+    bulk_wait_all();
+  }
+  if (tid == 0) {
+    // loads still in flight after a timeout: wait for them (bounded) before
+    // the block's shared memory is released
+    for (int q = 0; q < 2; ++q)
+      if (inflight & (1u << q)) (void)mbar_wait_bounded(&full[q], (fph >> q) & 1u);
+  }
+}
+
 
 // Jump-table rows of every cell for the coming step (FP32 form): thread j <
 // kJR builds the NB row r = j + 1, thread kJR + n the binomial row n, for the
@@ -1412,7 +1450,7 @@ void* collide_variant(int warp_tiles, int minb) {
 
 template <typename T>
 size_t collide_smem(int warp_tiles) {
-  return warp_tiles ? wsmem_bytes<T>() : 2 * stage_bytes<T>();
+  return warp_tiles ? wsmem_bytes<T>() : 2 * bstage_bytes<T>();
 }
 
 // Launch the particle pass (design warp_tiles, register-budget variant minb)

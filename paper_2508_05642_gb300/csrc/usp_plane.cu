@@ -702,12 +702,52 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
   for (int w = threadIdx.x; w < words; w += kParamBlock) dst[w] = src[w];
 }
 
+// Asynchronous global -> shared copies of 4, 8 or 16 bytes (cp.async): the
+// plane collision prefetches the next cell's data while it works on the
+// current one.
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  static_assert(B == 4 || B == 8 || B == 16, "cp.async copies 4, 8 or 16 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "n"(B)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Per-warp staging of one cell for pl_collide: its stencil record, then up to
+// kPC particles (x, y, cx, cy, cz, erot in T; level; id).  A cell with more
+// particles reads the rest directly.
+constexpr int kPC = 64;
+template <typename T>
+struct PlStage {
+  static constexpr size_t arr = (sizeof(PlParams<T>) + 15) / 16 * 16;
+  static constexpr size_t bytes = arr + (size_t)kPC * (6 * sizeof(T) + 8);
+};
+// the cell's place and size, active flag and bulk velocity, staged one cell
+// ahead of the particles
+struct PlMeta {
+  long long off, N;
+  double U[3];
+  int active, pad;
+};
+template <typename T>
+constexpr size_t pl_collide_smem() {
+  return (size_t)(kBlk / 32) * (2 * PlStage<T>::bytes + 3 * sizeof(PlMeta));
+}
+
 // per particle: the bilinear polynomial of its quadrant, then the collision
 // of Sec. 4.D; one warp per cell, per-cell sums for the conservation step.
-// The warp copies its cell's stencil record into shared memory with
-// coalesced 8-byte loads, so that the per-particle reads of the polynomial
-// coefficients are shared-memory broadcasts rather than ~80 dependent global
-// loads per particle.
+// Each warp walks its cells (c, c + W, c + 2W, ...) as a pipeline: while it
+// works on cell c out of shared memory, cp.async copies of cell c + W's
+// stencil record and particles and of cell c + 2W's place and size are in
+// flight, so the DRAM latency of a cell overlaps the previous cell's
+// arithmetic.
 template <typename T>
 __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<double>* __restrict__ cells,
                            const PlParams<T>* __restrict__ prm, const T* __restrict__ x,
@@ -716,90 +756,167 @@ __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<d
                            const uint32_t* __restrict__ pid, ChSumsT<double>* __restrict__ sums,
                            const long long* __restrict__ dstep, const PhiloxRoundKeys rk,
                            uint32_t* flags, unsigned long long* counters) {
+  extern __shared__ __align__(16) unsigned char pl_smem[];
   __shared__ BlockTally tal;
-  static_assert(sizeof(PlParams<T>) % 8 == 0, "records copied as 8-byte words");
-  constexpr int kWords = (int)(sizeof(PlParams<T>) / 8);
-  __shared__ unsigned long long sP[kBlk / 32][kWords];
+  using L = PlStage<T>;
   tally_init(tal);
   const int lane = threadIdx.x & 31;
   const uint32_t step = (uint32_t)*dstep;
-  unsigned long long* myP = sP[threadIdx.x >> 5];
-  const PlParams<T>& P = *reinterpret_cast<const PlParams<T>*>(myP);
-  for (int c = warp_global(); c < ncell; c += warps_total()) {
-    const ChCellT<double>& cs = cells[c];
-    if (!cs.active) continue;
-    {
-      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(prm + c);
-      __syncwarp();   // the previous cell's readers are done
-      for (int w = lane; w < kWords; w += 32) myP[w] = src[w];
-      __syncwarp();
+  unsigned char* wbase =
+      pl_smem + (size_t)(threadIdx.x >> 5) * (2 * L::bytes + 3 * sizeof(PlMeta));
+  PlMeta* meta = reinterpret_cast<PlMeta*>(wbase + 2 * L::bytes);
+  const int W = warps_total();
+
+  // copy cell cc's place, size, flag and velocity into slot m (lanes 0-5)
+  auto stage_meta = [&](int cc, PlMeta* m) {
+    if (cc < ncell) {
+      const ChCellT<double>& cs = cells[cc];
+      if (lane == 0) cp_async<8>(&m->off, &cs.off);
+      else if (lane == 1) cp_async<8>(&m->N, &cs.N);
+      else if (lane < 5) cp_async<8>(&m->U[lane - 2], &cs.U[lane - 2]);
+      else if (lane == 5) cp_async<4>(&m->active, &cs.active);
+    } else if (lane == 0) {
+      m->active = 0;
+      m->N = 0;
     }
-    // cell velocity in T: one conversion per warp (lanes 0-2), then broadcast
-    const T uc = (T)(lane < 3 ? cs.U[lane < 3 ? lane : 0] : 0.0);
-    const T Uc0 = __shfl_sync(0xffffffffu, uc, 0), Uc1 = __shfl_sync(0xffffffffu, uc, 1),
-            Uc2 = __shfl_sync(0xffffffffu, uc, 2);
-    T acc[10];
+  };
+  // copy cell cc's stencil record and first kPC particles into buffer b
+  auto stage_cell = [&](int cc, const PlMeta* m, unsigned char* b) {
+    if (cc >= ncell || !m->active) return;
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(prm + cc);
+    if constexpr (sizeof(PlParams<T>) % 16 == 0) {
+      for (int w = lane; w < (int)(sizeof(PlParams<T>) / 16); w += 32)
+        cp_async<16>(b + 16 * w, src + 16 * w);
+    } else {
+      for (int w = lane; w < (int)(sizeof(PlParams<T>) / 8); w += 32)
+        cp_async<8>(b + 8 * w, src + 8 * w);
+    }
+    const long long off = m->off;
+    const int n = (int)min(m->N, (long long)kPC);
+    T* A = reinterpret_cast<T*>(b + L::arr);
+    int* Lv = reinterpret_cast<int*>(A + 6 * kPC);
+    uint32_t* Pd = reinterpret_cast<uint32_t*>(Lv + kPC);
+    for (int i = lane; i < n; i += 32) {
+      const long long j = off + i;
+      cp_async<sizeof(T)>(A + i, x + j);
+      cp_async<sizeof(T)>(A + kPC + i, y + j);
+      cp_async<sizeof(T)>(A + 2 * kPC + i, cx + j);
+      cp_async<sizeof(T)>(A + 3 * kPC + i, cy + j);
+      cp_async<sizeof(T)>(A + 4 * kPC + i, cz + j);
+      cp_async<sizeof(T)>(A + 5 * kPC + i, er + j);
+      cp_async<4>(Lv + i, lev + j);
+      cp_async<4>(Pd + i, pid + j);
+    }
+  };
+
+  int c = warp_global();
+  // prologue: place of the first cell, then its data and the next one's place
+  stage_meta(c, &meta[0]);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncwarp();
+  stage_cell(c, &meta[0], wbase);
+  stage_meta(c + W, &meta[1]);
+  cp_async_commit();
+  int slot = 0, buf = 0;
+  for (; c < ncell; c += W) {
+    // cell c's data and cell c + W's place are in shared memory once every
+    // lane's copies are done; the previous cell's readers are done too
+    cp_async_wait_all();
+    __syncwarp();
+    const int s1 = slot == 2 ? 0 : slot + 1, s2 = s1 == 2 ? 0 : s1 + 1;
+    stage_cell(c + W, &meta[s1], wbase + (buf ^ 1) * L::bytes);
+    stage_meta(c + 2 * W, &meta[s2]);
+    cp_async_commit();
+    const PlMeta& m = meta[slot];
+    if (m.active) {
+      const unsigned char* b = wbase + buf * L::bytes;
+      const PlParams<T>& P = *reinterpret_cast<const PlParams<T>*>(b);
+      const T* A = reinterpret_cast<const T*>(b + L::arr);
+      const int* Lv = reinterpret_cast<const int*>(A + 6 * kPC);
+      const uint32_t* Pd = reinterpret_cast<const uint32_t*>(Lv + kPC);
+      const long long off = m.off;
+      const int n = (int)m.N;
+      // cell velocity in T: one conversion per warp (lanes 0-2), then broadcast
+      const T uc = (T)(lane < 3 ? m.U[lane < 3 ? lane : 0] : 0.0);
+      const T Uc0 = __shfl_sync(0xffffffffu, uc, 0), Uc1 = __shfl_sync(0xffffffffu, uc, 1),
+              Uc2 = __shfl_sync(0xffffffffu, uc, 2);
+      T acc[10];
 #pragma unroll
-    for (int i = 0; i < 10; ++i) acc[i] = T(0);
-    long long accI = 0;
-    int maxI = 0;
-    CollideTally tl = {0u, 0ull, 0ull, 0ull, 0ull};
-    unsigned long long nfb = 0;
-    for (long long j = cs.off + lane; j < cs.off + cs.N; j += 32) {
-      const T ddx = x[j] - P.xc, ddy = y[j] - P.yc;
-      const int sx = ddx >= T(0) ? 1 : 0, sy = ddy >= T(0) ? 1 : 0;
-      const T dxy = ddx * ddy;
-      const T* gx = P.gx[sx];
-      const T* gy = P.gy[sy];
-      const T* gxy = P.gxy[sy * 2 + sx];
-      T f[kNF];
+      for (int i = 0; i < 10; ++i) acc[i] = T(0);
+      int accI = 0;
+      int maxI = 0;
+      CollideTally tl = {0u, 0ull, 0ull, 0ull, 0ull};
+      unsigned nfb = 0;
+      for (int i = lane; i < n; i += 32) {
+        const long long j = off + i;
+        T xv, yv, v0, v1, v2, en;
+        int l0;
+        uint32_t id;
+        if (i < kPC) {
+          xv = A[i]; yv = A[kPC + i]; v0 = A[2 * kPC + i]; v1 = A[3 * kPC + i];
+          v2 = A[4 * kPC + i]; en = A[5 * kPC + i]; l0 = Lv[i]; id = Pd[i];
+        } else {
+          xv = x[j]; yv = y[j]; v0 = cx[j]; v1 = cy[j]; v2 = cz[j]; en = er[j];
+          l0 = lev[j]; id = pid[j];
+        }
+        const T ddx = xv - P.xc, ddy = yv - P.yc;
+        const int sx = ddx >= T(0) ? 1 : 0, sy = ddy >= T(0) ? 1 : 0;
+        const T dxy = ddx * ddy;
+        const T* gx = P.gx[sx];
+        const T* gy = P.gy[sy];
+        const T* gxy = P.gxy[sy * 2 + sx];
+        T f[kNF];
 #pragma unroll
-      for (int i = 0; i < kNF; ++i) f[i] = P.F[i] + gx[i] * ddx + gy[i] * ddy + gxy[i] * dxy;
-      if (!(f[3] > T(0)) || !(f[4] > T(0)) || !(f[5] >= T(0))) {
+        for (int q = 0; q < kNF; ++q) f[q] = P.F[q] + gx[q] * ddx + gy[q] * ddy + gxy[q] * dxy;
+        if (!(f[3] > T(0)) || !(f[4] > T(0)) || !(f[5] >= T(0))) {
 #pragma unroll
-        for (int i = 0; i < kNF; ++i) f[i] = P.F[i];
-        ++nfb;
+          for (int q = 0; q < kNF; ++q) f[q] = P.F[q];
+          ++nfb;
+        }
+        const int ln = collide_particle_t<sizeof(T) == 4>(P, f, v0, v1, v2, en, l0, id, step,
+                                                            rk, tl);
+        cx[j] = v0; cy[j] = v1; cz[j] = v2; er[j] = en;
+        lev[j] = ln;
+        maxI = max(maxI, ln);
+        const T d0 = v0 - Uc0, d1 = v1 - Uc1, d2 = v2 - Uc2;
+        acc[0] += d0; acc[1] += d1; acc[2] += d2;
+        acc[3] += d0 * d0; acc[4] += d1 * d1; acc[5] += d2 * d2;
+        acc[6] += d0 * d1; acc[7] += d0 * d2; acc[8] += d1 * d2;
+        acc[9] += en;
+        accI += ln;
       }
-      T v0 = cx[j], v1 = cy[j], v2 = cz[j], en = er[j];
-      const int ln = collide_particle_t<sizeof(T) == 4>(P, f, v0, v1, v2, en, lev[j], pid[j],
-                                                          step, rk, tl);
-      cx[j] = v0; cy[j] = v1; cz[j] = v2; er[j] = en;
-      lev[j] = ln;
-      maxI = max(maxI, ln);
-      const T d0 = v0 - Uc0, d1 = v1 - Uc1, d2 = v2 - Uc2;
-      acc[0] += d0; acc[1] += d1; acc[2] += d2;
-      acc[3] += d0 * d0; acc[4] += d1 * d1; acc[5] += d2 * d2;
-      acc[6] += d0 * d1; acc[7] += d0 * d2; acc[8] += d1 * d2;
-      acc[9] += en;
-      accI += ln;
-    }
-    // warp totals; lane i < 10 converts total i (one FP64 conversion per warp)
-    T mine = T(0);
+      // warp totals; lane i < 10 converts total i (one FP64 conversion per warp)
+      T mine = T(0);
 #pragma unroll
-    for (int i = 0; i < 10; ++i) {
-      const T t = wsum(acc[i]);
-      mine = lane == i ? t : mine;
+      for (int i = 0; i < 10; ++i) {
+        const T t = wsum(acc[i]);
+        mine = lane == i ? t : mine;
+      }
+      const double sv = (double)mine;
+      const long long sI = wsum((long long)accI);
+      const unsigned long long fix = wsum(tl.nfix), fb = wsum((unsigned long long)nfb),
+                               ncl2 = wsum(tl.ncl), pb = wsum(tl.npb), nz = wsum(tl.nnz);
+      const int mI = __reduce_max_sync(0xffffffffu, maxI);
+      const uint32_t fla = __reduce_or_sync(0xffffffffu, tl.fl);
+      ChSumsT<double>& sm = sums[c];
+      if (lane < 10) sm.v[lane] = sv;
+      if (lane == 0) {
+        sm.I = (unsigned long long)sI;
+        sm.net = 0;
+        sm.maxI = mI;
+        tally_or(tal, fla);
+        tally_add(tal, C_CHOL_FIX, fix);
+        tally_add(tal, C_INTERP_FALLBACK, fb);
+        tally_add(tal, C_TREL_CLAMP, ncl2);
+        tally_add(tal, C_PB_CLAMP, pb);
+        tally_add(tal, C_NU_ZERO, nz);
+      }
     }
-    const double sv = (double)mine;
-    const long long sI = wsum(accI);
-    const unsigned long long fix = wsum(tl.nfix), fb = wsum(nfb), ncl2 = wsum(tl.ncl),
-                             pb = wsum(tl.npb), nz = wsum(tl.nnz);
-    const int mI = __reduce_max_sync(0xffffffffu, maxI);
-    const uint32_t fla = __reduce_or_sync(0xffffffffu, tl.fl);
-    ChSumsT<double>& sm = sums[c];
-    if (lane < 10) sm.v[lane] = sv;
-    if (lane == 0) {
-      sm.I = (unsigned long long)sI;
-      sm.net = 0;
-      sm.maxI = mI;
-      tally_or(tal, fla);
-      tally_add(tal, C_CHOL_FIX, fix);
-      tally_add(tal, C_INTERP_FALLBACK, fb);
-      tally_add(tal, C_TREL_CLAMP, ncl2);
-      tally_add(tal, C_PB_CLAMP, pb);
-      tally_add(tal, C_NU_ZERO, nz);
-    }
+    slot = s1;
+    buf ^= 1;
   }
+  cp_async_wait_all();
   tally_flush(tal, flags, counters);
 }
 
@@ -905,6 +1022,7 @@ struct PlaneCtx {
   PlInflow inf;
   int recon, passes, nblk, grid_p;
   int grid_wc, grid_tc;     // grids of the warp-per-cell and thread-per-cell passes
+  int grid_col;             // persistent grid of the collision pass
   int grid_inj;             // grid of the inflow pass (grid-stride over entering particles)
   double Fnum, vol;
   long long cap;
@@ -1005,7 +1123,8 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 1, 0);
   if (prof) prof(env.owner, 0, 1);
-  pl_collide<T><<<wb, kBlk, 0, s>>>(ncell, h->cells, (const PlParams<T>*)h->prm, x, y, cx, cy,
+  pl_collide<T><<<h->grid_col, kBlk, pl_collide_smem<T>(), s>>>(
+      ncell, h->cells, (const PlParams<T>*)h->prm, x, y, cx, cy,
                                     cz, er, h->lv[b], h->pd[b], h->sums, h->dstep,
                                     philox_round_keys(env.k0, env.k1), env.flags, env.counters);
   CHK(cudaGetLastError());
@@ -1107,6 +1226,21 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->grid_p = (int)std::min<long long>(std::max<long long>(1, (cap + kBlk - 1) / kBlk), nsm * 16);
   h->grid_wc = (int)std::min<long long>(((long long)ncell * 32 + kBlk - 1) / kBlk, nsm * 8);
   h->grid_tc = (int)std::min<long long>((ncell + kBlk - 1) / kBlk, nsm * 8);
+  {
+    // the collision pass keeps one block per resident slot, each warp a
+    // pipeline over its cells
+    const bool f32 = env.precision == USP_FP32;
+    const void* fn = f32 ? (const void*)pl_collide<float> : (const void*)pl_collide<double>;
+    const int smem = (int)(f32 ? pl_collide_smem<float>() : pl_collide_smem<double>());
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlk, smem) != cudaSuccess)
+      per_sm = 0;
+    if (per_sm <= 0) { pl_destroy(h); return USP_ECUDA; }
+    h->grid_col = (int)std::min<long long>(((long long)ncell * 32 + kBlk - 1) / kBlk,
+                                           (long long)nsm * per_sm);
+  }
   h->grid_inj = nsm * 4;
   auto A = [&](size_t bytes) { return env.alloc(env.owner, bytes); };
   const size_t nn = (size_t)cap;
