@@ -292,8 +292,10 @@ int usp_set_particles(usp_ctx* ctx, const double* h_cx, const double* h_cy, cons
  * context's precision: float for USP_FP32, double for USP_FP64; int32
  * levels), run nsteps steps, download the moments into h_moments (USP_NMOM x
  * n_cells doubles) and, if h_*_out are not NULL, the resulting state.
- * Synchronises.  For pinned host buffers the copies overlap nothing else but
- * run at full link speed. */
+ * Synchronises.  The cells are independent, so the upload goes in eight runs
+ * of whole cells and each run is stepped while the next one is in transit;
+ * with pinned host buffers the copies run at full link speed and hide most
+ * of the arithmetic.  Homogeneous contexts only (USP_ENOTSUP otherwise). */
 int usp_step_host(usp_ctx* ctx, const void* h_cx, const void* h_cy, const void* h_cz,
                   const void* h_erot, const int32_t* h_lev, int nsteps, double* h_moments,
                   void* h_cx_out, void* h_cy_out, void* h_cz_out, void* h_erot_out,

@@ -765,12 +765,12 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
 // Jump-table rows of every cell for the coming step (FP32 form): thread j <
 // kJR builds the NB row r = j + 1, thread kJR + n the binomial row n, for the
 // rows the cell's levels can reach.
-__global__ void jumptable_kernel(int ncell, const CollideParams<float>* __restrict__ prm,
+__global__ void jumptable_kernel(int c0, int c1, const CollideParams<float>* __restrict__ prm,
                                  const CellState* __restrict__ cells, float* __restrict__ tab_nb,
                                  float* __restrict__ tab_b) {
-  const int c = blockIdx.x;
+  const int c = c0 + blockIdx.x;
   const int j = threadIdx.x;
-  if (c >= ncell) return;
+  if (c >= c1) return;
   const CollideParams<float>& P = prm[c];
   if (!P.active) return;
   const int rows = min(kJR, cells[c].maxI + 1);
@@ -841,11 +841,12 @@ __device__ void write_params(const Species& sp, CellState& cs, CollideParams<T>&
 // Initial coefficients from freshly reduced moments (identity pending rescale).
 // mom: field-major USP_NMOM x ncell as written by assemble_moments.
 template <typename T>
-__global__ void init_params_kernel(Species sp, int ncell, const double* __restrict__ mom,
-                                   CellState* cells, CollideParams<T>* prm, uint32_t* flags,
+__global__ void init_params_kernel(Species sp, int ncell, int c0, int c1,
+                                   const double* __restrict__ mom, CellState* cells,
+                                   CollideParams<T>* prm, uint32_t* flags,
                                    unsigned long long* counters) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
   CellState cs = cells[c];
   const double R = gasR(sp);
   for (int i = 0; i < 3; ++i) { cs.U[i] = mom[(1 + i) * ncell + c]; cs.Us[i] = cs.U[i]; }
@@ -865,11 +866,11 @@ __global__ void init_params_kernel(Species sp, int ncell, const double* __restri
 }
 
 template <typename T>
-__global__ void init_params_finish(Species sp, int ncell, const double* __restrict__ levsum,
+__global__ void init_params_finish(Species sp, int c0, int c1, const double* __restrict__ levsum,
                                    CellState* cells, CollideParams<T>* prm, uint32_t* flags,
                                    unsigned long long* counters) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
   CellState cs = cells[c];
   cs.ebar = cs.N > 0 ? levsum[c] / (double)cs.N : 0.0;
   CollideParams<T> P;
@@ -894,13 +895,13 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // acceptance of draw j is decided exactly as in the one-at-a-time loop: a
 // decrement on particle k is accepted iff fewer than lev[k] earlier accepted
 // decrements in the round hit k.  The net level change goes to sums[c].net.
-__global__ void levelfix_kernel(Species sp, int ncell, const CellState* __restrict__ cells,
+__global__ void levelfix_kernel(Species sp, int c0, int c1, const CellState* __restrict__ cells,
                                 CellSums* __restrict__ sums, int* __restrict__ lev,
                                 uint32_t* flags, unsigned long long* counters, uint32_t k0,
                                 uint32_t k1) {
   const int lane = threadIdx.x & 31;
-  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (c >= ncell) return;
+  const int c = c0 + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (c >= c1) return;
   const CellState& cs = cells[c];
   if (!cs.active) return;
   const double Rth = gasR(sp) * sp.theta_v;
@@ -964,12 +965,12 @@ __global__ void levelfix_kernel(Species sp, int ncell, const CellState* __restri
 // coefficients; one thread per cell so that the FP64 work of 32 cells shares
 // each warp instruction.
 template <typename T>
-__global__ void cellupdate_kernel(Species sp, int ncell, CellState* __restrict__ cells,
+__global__ void cellupdate_kernel(Species sp, int c0, int c1, CellState* __restrict__ cells,
                                   CollideParams<T>* __restrict__ prm,
                                   CellSums* __restrict__ sums, uint32_t* flags,
                                   unsigned long long* counters) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
   CellState cs = cells[c];
   if (!cs.active) return;
   const double R = gasR(sp);
@@ -1117,11 +1118,12 @@ moments_kernel(int pass, const Tile* __restrict__ tiles, int ntiles,
   }
 }
 
-__global__ void assemble_moments(Species sp, int ncell, const CellState* __restrict__ cells,
+__global__ void assemble_moments(Species sp, int ncell, int c0, int c1,
+                                 const CellState* __restrict__ cells,
                                  const double* __restrict__ acc, double* __restrict__ out,
                                  double* __restrict__ levsum) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= ncell) return;
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
   const double R = gasR(sp);
   const double N = (double)cells[c].N;
   const double* a = acc + (size_t)c * kMomAcc;
@@ -1249,6 +1251,7 @@ struct usp_ctx {
   int ntiles;
   Tile* wtiles;             // tiles of <= kWT particles (warp-tiled particle pass)
   int nwtiles;
+  std::vector<int> h_tfirst, h_wfirst;   // first tile of each cell in either list (ncell + 1)
   long long* uoff;          // unpadded offsets (device)
   double* macc;             // moment accumulators
   double* mout;             // moment output (device)
@@ -1373,10 +1376,13 @@ int sm_count() {
   return n > 0 ? n : 1;
 }
 
-// Cells split into tiles of at most `tile` particles, in cell order.
-int make_tiles(usp_ctx* c, int tile, Tile** out, int* nout) {
+// Cells split into tiles of at most `tile` particles, in cell order; first[i]
+// is the index of cell i's first tile (first[ncell] = the number of tiles).
+int make_tiles(usp_ctx* c, int tile, Tile** out, int* nout, std::vector<int>& first) {
   std::vector<Tile> t;
+  first.assign(c->ncell + 1, 0);
   for (int i = 0; i < c->ncell; ++i) {
+    first[i] = (int)t.size();
     const long long n = c->h_uoff[i + 1] - c->h_uoff[i];
     for (long long s = 0; s < n; s += tile) {
       Tile x;
@@ -1387,6 +1393,7 @@ int make_tiles(usp_ctx* c, int tile, Tile** out, int* nout) {
       t.push_back(x);
     }
   }
+  first[c->ncell] = (int)t.size();
   if (t.empty()) {
     Tile x = {0, 0, 0, 0};
     t.push_back(x);
@@ -1401,9 +1408,9 @@ int make_tiles(usp_ctx* c, int tile, Tile** out, int* nout) {
 }
 
 int build_tiles(usp_ctx* c, int tile) {
-  int rc = make_tiles(c, tile, &c->tiles, &c->ntiles);
+  int rc = make_tiles(c, tile, &c->tiles, &c->ntiles, c->h_tfirst);
   if (rc) return rc;
-  rc = make_tiles(c, std::min(tile, kWT), &c->wtiles, &c->nwtiles);
+  rc = make_tiles(c, std::min(tile, kWT), &c->wtiles, &c->nwtiles, c->h_wfirst);
   if (rc) return rc;
   c->tile = tile;
   return USP_OK;
@@ -1453,12 +1460,23 @@ size_t collide_smem(int warp_tiles) {
   return warp_tiles ? wsmem_bytes<T>() : 2 * bstage_bytes<T>();
 }
 
+// A run of consecutive cells [c0, c1) and its tiles in either tile list.
+struct CellRange {
+  int c0, c1;
+  int t0, t1;   // block tiles
+  int w0, w1;   // warp tiles
+};
+CellRange cell_range(const usp_ctx* c, int c0, int c1) {
+  return CellRange{c0, c1, c->h_tfirst[c0], c->h_tfirst[c1], c->h_wfirst[c0], c->h_wfirst[c1]};
+}
+CellRange all_cells(const usp_ctx* c) { return cell_range(c, 0, c->ncell); }
+
 // Launch the particle pass (design warp_tiles, register-budget variant minb)
-// on the given state / sums buffers.
+// over the tiles of the cell range r, on the given state / sums buffers.
 template <typename T>
 int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, void* cy, void* cz,
                    void* er, int* lev, CellSums* sums, uint32_t* flags,
-                   unsigned long long* counters) {
+                   unsigned long long* counters, const CellRange& r) {
   const size_t smem = collide_smem<T>(warp_tiles);
   const CollideParams<T>* prm = (const CollideParams<T>*)c->prm;
   T* x = (T*)cx; T* y = (T*)cy; T* z = (T*)cz; T* e = (T*)er;
@@ -1466,8 +1484,8 @@ int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, voi
   const float* tn = c->tab_nb;
   const float* tb = c->tab_b;
   if (warp_tiles) {
-    const Tile* tiles = c->wtiles;
-    const int ntiles = c->nwtiles;
+    const Tile* tiles = c->wtiles + r.w0;
+    const int ntiles = r.w1 - r.w0;
     if (minb == 2)
       collide_warp_kernel<T, 2><<<grid, kBlock, smem, c->stream>>>(
           tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
@@ -1480,8 +1498,8 @@ int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, voi
     CK(cudaGetLastError());
     return USP_OK;
   }
-  const Tile* tiles = c->tiles;
-  const int ntiles = c->ntiles;
+  const Tile* tiles = c->tiles + r.t0;
+  const int ntiles = r.t1 - r.t0;
   if (minb == 2)
     collide_kernel<T, 2><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
                                                             sums, flags, counters, rk, tn, tb);
@@ -1496,33 +1514,36 @@ int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, voi
 }
 
 // jump tables for the coming step (FP32 form only)
-int launch_tables(usp_ctx* c) {
-  if (c->precision != USP_FP32) return USP_OK;
-  jumptable_kernel<<<c->ncell, 2 * kJR, 0, c->stream>>>(
-      c->ncell, (const CollideParams<float>*)c->prm, c->cells, c->tab_nb, c->tab_b);
+int launch_tables(usp_ctx* c, const CellRange& r) {
+  if (c->precision != USP_FP32 || r.c1 <= r.c0) return USP_OK;
+  jumptable_kernel<<<r.c1 - r.c0, 2 * kJR, 0, c->stream>>>(
+      r.c0, r.c1, (const CollideParams<float>*)c->prm, c->cells, c->tab_nb, c->tab_b);
   CK(cudaGetLastError());
   return USP_OK;
 }
 
+// one step of the cells of r
 template <typename T>
-int launch_step(usp_ctx* c) {
+int launch_step(usp_ctx* c, const CellRange& r) {
+  if (r.c1 <= r.c0) return USP_OK;
   cudaEvent_t e1 = nullptr;
   int rc = prof_begin(c, 0, &e1);
   if (rc) return rc;
   rc = launch_collide<T>(c, c->warp_tiles, c->minb, c->grid_collide, c->cx, c->cy, c->cz, c->er,
-                         c->lev, c->sums, c->flags, c->counters);
+                         c->lev, c->sums, c->flags, c->counters, r);
   if (rc) return rc;
   if ((rc = prof_end(c, e1))) return rc;
   if ((rc = prof_begin(c, 1, &e1))) return rc;
+  const int n = r.c1 - r.c0;
   const int warps_per_block = 4;
-  const int blocks = (c->ncell + warps_per_block - 1) / warps_per_block;
+  const int blocks = (n + warps_per_block - 1) / warps_per_block;
   levelfix_kernel<<<blocks, 32 * warps_per_block, 0, c->stream>>>(
-      c->sp, c->ncell, c->cells, c->sums, c->lev, c->flags, c->counters, key0(c), key1(c));
+      c->sp, r.c0, r.c1, c->cells, c->sums, c->lev, c->flags, c->counters, key0(c), key1(c));
   CK(cudaGetLastError());
-  cellupdate_kernel<T><<<(c->ncell + 63) / 64, 64, 0, c->stream>>>(
-      c->sp, c->ncell, c->cells, (CollideParams<T>*)c->prm, c->sums, c->flags, c->counters);
+  cellupdate_kernel<T><<<(n + 63) / 64, 64, 0, c->stream>>>(
+      c->sp, r.c0, r.c1, c->cells, (CollideParams<T>*)c->prm, c->sums, c->flags, c->counters);
   CK(cudaGetLastError());
-  if ((rc = launch_tables(c))) return rc;
+  if ((rc = launch_tables(c, r))) return rc;
   return prof_end(c, e1);
 }
 
@@ -1535,40 +1556,58 @@ int kernels_per_step(const usp_ctx* c) {
 int step_once(usp_ctx* c) {
   if (c->kind == 1) return ch_launch_step(c->ch, make_env(c), c->profiling ? prof_cb : nullptr);
   if (c->kind == 2) return pl_launch_step(c->pl, make_env(c), c->profiling ? prof_cb : nullptr);
-  return c->precision == USP_FP32 ? launch_step<float>(c) : launch_step<double>(c);
+  return c->precision == USP_FP32 ? launch_step<float>(c, all_cells(c))
+                                  : launch_step<double>(c, all_cells(c));
 }
 
+// moments of the cells of r (pending rescale applied) into mout
 template <typename T>
-int compute_moments(usp_ctx* c, double* levsum) {
-  CK(cudaMemsetAsync(c->macc, 0, sizeof(double) * kMomAcc * c->ncell, c->stream));
-  for (int pass = 0; pass < 2; ++pass) {
-    moments_kernel<T><<<c->grid_collide, kBlock, 0, c->stream>>>(
-        pass, c->tiles, c->ntiles, c->cells, (const T*)c->cx, (const T*)c->cy, (const T*)c->cz,
-        (const T*)c->er, c->lev, c->macc);
-    CK(cudaGetLastError());
+int compute_moments(usp_ctx* c, double* levsum, const CellRange& r) {
+  if (r.c1 <= r.c0) return USP_OK;
+  CK(cudaMemsetAsync(c->macc + (size_t)r.c0 * kMomAcc, 0,
+                     sizeof(double) * kMomAcc * (r.c1 - r.c0), c->stream));
+  if (r.t1 > r.t0) {
+    for (int pass = 0; pass < 2; ++pass) {
+      moments_kernel<T><<<c->grid_collide, kBlock, 0, c->stream>>>(
+          pass, c->tiles + r.t0, r.t1 - r.t0, c->cells, (const T*)c->cx, (const T*)c->cy,
+          (const T*)c->cz, (const T*)c->er, c->lev, c->macc);
+      CK(cudaGetLastError());
+    }
+    c->launches += 2;
   }
-  assemble_moments<<<(c->ncell + 127) / 128, 128, 0, c->stream>>>(c->sp, c->ncell, c->cells,
-                                                                   c->macc, c->mout, levsum);
+  assemble_moments<<<(r.c1 - r.c0 + 127) / 128, 128, 0, c->stream>>>(
+      c->sp, c->ncell, r.c0, r.c1, c->cells, c->macc, c->mout, levsum);
   CK(cudaGetLastError());
-  c->launches += 3;
+  c->launches += 1;
   return USP_OK;
 }
-
 template <typename T>
-int init_params(usp_ctx* c) {
-  int rc = compute_moments<T>(c, c->levsum);
+int compute_moments(usp_ctx* c, double* levsum) {
+  return compute_moments<T>(c, levsum, all_cells(c));
+}
+
+// coefficients of the cells of r from freshly uploaded particles
+template <typename T>
+int init_params(usp_ctx* c, const CellRange& r) {
+  if (r.c1 <= r.c0) return USP_OK;
+  int rc = compute_moments<T>(c, c->levsum, r);
   if (rc) return rc;
-  const int b = (c->ncell + 127) / 128;
-  init_params_kernel<T><<<b, 128, 0, c->stream>>>(c->sp, c->ncell, c->mout, c->cells,
-                                                  (CollideParams<T>*)c->prm, c->flags, c->counters);
+  const int b = (r.c1 - r.c0 + 127) / 128;
+  init_params_kernel<T><<<b, 128, 0, c->stream>>>(c->sp, c->ncell, r.c0, r.c1, c->mout,
+                                                  c->cells, (CollideParams<T>*)c->prm, c->flags,
+                                                  c->counters);
   CK(cudaGetLastError());
-  init_params_finish<T><<<b, 128, 0, c->stream>>>(c->sp, c->ncell, c->levsum, c->cells,
+  init_params_finish<T><<<b, 128, 0, c->stream>>>(c->sp, r.c0, r.c1, c->levsum, c->cells,
                                                   (CollideParams<T>*)c->prm, c->flags, c->counters);
   CK(cudaGetLastError());
   c->launches += 2;
-  if ((rc = launch_tables(c))) return rc;
+  if ((rc = launch_tables(c, r))) return rc;
   c->launches += c->precision == USP_FP32 ? 1 : 0;
   return USP_OK;
+}
+template <typename T>
+int init_params(usp_ctx* c) {
+  return init_params<T>(c, all_cells(c));
 }
 
 // The host paths stage the state in one device buffer, allocated on first use
@@ -1620,14 +1659,17 @@ int upload_state(usp_ctx* c, const void* hx, const void* hy, const void* hz, con
   return USP_OK;
 }
 
-// Upload of a native-precision host state in 8 chunks of whole cells: the
-// copies of chunk k+1 (on a copy stream) overlap the scatter of chunk k into
-// the padded device layout (on the context stream).
-int upload_state_pipelined(usp_ctx* c, const void* hx, const void* hy, const void* hz,
-                           const void* he, const int32_t* hl) {
+// Host-buffer step of a homogeneous context.  Cells are independent, so the
+// state goes up in kUpChunks runs of whole cells on the copy stream, and each
+// run is scattered, set up, stepped nsteps times and reduced to its moments
+// (into mout) on the context stream while the next run is still in transit:
+// the transfer hides the arithmetic instead of preceding it.
+template <typename T>
+int step_host_chunked(usp_ctx* c, const void* hx, const void* hy, const void* hz,
+                      const void* he, const int32_t* hl, int nsteps) {
   constexpr int K = 8;
   const long long n = c->nparticles;
-  const size_t es = c->precision == USP_FP32 ? 4 : 8;
+  const size_t es = sizeof(T);
   void* st = staging(c, (size_t)n * (4 * es + 4) + 64);
   if (!st) return USP_ENOMEM;
   if (!c->copy_stream) {
@@ -1658,19 +1700,21 @@ int upload_state_pipelined(usp_ctx* c, const void* hx, const void* hy, const voi
     CK(cudaEventRecord(c->up_ev[k + 1], c->copy_stream));
     CK(cudaStreamWaitEvent(c->stream, c->up_ev[k + 1], 0));
     dim3 grid(64, std::min(cb - ca, 65535));
-    if (c->precision == USP_FP32)
-      scatter_state<float, float><<<grid, 256, 0, c->stream>>>(
-          ca, cb, c->cells, c->uoff, (const float*)dst[0], (const float*)dst[1],
-          (const float*)dst[2], (const float*)dst[3], (const int*)dst[4], (float*)c->cx,
-          (float*)c->cy, (float*)c->cz, (float*)c->er, c->lev);
-    else
-      scatter_state<double, double><<<grid, 256, 0, c->stream>>>(
-          ca, cb, c->cells, c->uoff, (const double*)dst[0], (const double*)dst[1],
-          (const double*)dst[2], (const double*)dst[3], (const int*)dst[4], (double*)c->cx,
-          (double*)c->cy, (double*)c->cz, (double*)c->er, c->lev);
+    scatter_state<T, T><<<grid, 256, 0, c->stream>>>(
+        ca, cb, c->cells, c->uoff, (const T*)dst[0], (const T*)dst[1], (const T*)dst[2],
+        (const T*)dst[3], (const int*)dst[4], (T*)c->cx, (T*)c->cy, (T*)c->cz, (T*)c->er, c->lev);
     CK(cudaGetLastError());
     c->launches += 1;
+    const CellRange r = cell_range(c, ca, cb);
+    int rc = init_params<T>(c, r);
+    if (rc) return rc;
+    for (int s = 0; s < nsteps; ++s) {
+      if ((rc = launch_step<T>(c, r))) return rc;
+      c->launches += kernels_per_step(c);
+    }
+    if ((rc = compute_moments<T>(c, nullptr, r))) return rc;
   }
+  c->step += nsteps;
   return USP_OK;
 }
 
@@ -1736,7 +1780,8 @@ int autotune(usp_ctx* c) {
       const int grid = c->grid_by_minb[wt][mb];
       for (int r = 0; r < 3; ++r) {
         if (r == 1) CK(cudaEventRecord(e0, c->stream));
-        rc = launch_collide<T>(c, wt, mb, grid, sx, sy, sz, se, sl, ssum, sflags, scnt);
+        rc = launch_collide<T>(c, wt, mb, grid, sx, sy, sz, se, sl, ssum, sflags, scnt,
+                             all_cells(c));
         if (rc) return rc;
       }
       CK(cudaEventRecord(e1, c->stream));
@@ -2239,14 +2284,12 @@ int usp_step_host(usp_ctx* c, const void* hx, const void* hy, const void* hz, co
                   void* oe, int32_t* ol) {
   if (!c || !hx || !hy || !hz || !he || !hl || !h_moments || nsteps < 0) return USP_EINVAL;
   if (c->kind != 0) return USP_ENOTSUP;
-  int rc = upload_state_pipelined(c, hx, hy, hz, he, hl);
+  int rc = c->precision == USP_FP32 ? step_host_chunked<float>(c, hx, hy, hz, he, hl, nsteps)
+                                    : step_host_chunked<double>(c, hx, hy, hz, he, hl, nsteps);
   if (rc) return rc;
-  rc = c->precision == USP_FP32 ? init_params<float>(c) : init_params<double>(c);
-  if (rc) return rc;
-  rc = usp_step(c, nsteps);
-  if (rc) return rc;
-  rc = usp_moments(c, h_moments, 0);
-  if (rc) return rc;
+  CK(cudaMemcpyAsync(h_moments, c->mout, sizeof(double) * USP_NMOM * c->ncell,
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   if (ox && oy && oz && oe && ol) {
     const long long n = c->nparticles;
     const size_t es = c->precision == USP_FP32 ? 4 : 8;
