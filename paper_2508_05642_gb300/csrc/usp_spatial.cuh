@@ -453,12 +453,35 @@ __global__ void ch_moments(int ny, int cpw, const long long* __restrict__ off,
     T k0 = T(0), k1 = T(0), k2 = T(0), ke = T(0), kq[6];
     long long kl = 0, kb = 0, kN = 0;
     for (int i = 0; i < 6; ++i) kq[i] = T(0);
+    // the task's cell offsets (lane k: start of cell k), and each cell's first
+    // 32 particles held one per lane, loaded one cell ahead so that their
+    // latency overlaps the previous cell's reductions; the sums keep the
+    // order of a plain strided loop
+    const long long offl = lane < ng ? off[c0 + lane] : 0;
+    const long long offend = off[c0 + ng];
+    auto cell_b = [&](int g) { return __shfl_sync(0xffffffffu, offl, g); };
+    auto cell_e = [&](int g) { return g + 1 < ng ? __shfl_sync(0xffffffffu, offl, g + 1) : offend; };
+    T nx0 = T(0), ny0 = T(0), nz0 = T(0), ne0 = T(0);
+    int nl0 = 0;
+    auto first = [&](int g) {
+      const long long j = cell_b(g) + lane;
+      if (j < cell_e(g)) {
+        nx0 = cx[j]; ny0 = cy[j]; nz0 = cz[j]; ne0 = er[j]; nl0 = lev[j];
+      } else {
+        nx0 = ny0 = nz0 = ne0 = T(0); nl0 = 0;
+      }
+    };
+    first(0);
     for (int g = 0; g < ng; ++g) {
-      const long long c = c0 + g;
-      const long long b = off[c], e = off[c + 1], N = e - b;
+      const long long b = cell_b(g), e = cell_e(g), N = e - b;
+      const bool has = lane < N;
+      const T fx = nx0, fy = ny0, fz = nz0, fe = ne0;
+      const int fl = nl0;
+      if (g + 1 < ng) first(g + 1);
       T a0 = T(0), a1 = T(0), a2 = T(0), ae = T(0);
       long long al = 0;
-      for (long long j = b + lane; j < e; j += 32) {
+      if (has) { a0 += fx; a1 += fy; a2 += fz; ae += fe; al += fl; }
+      for (long long j = b + 32 + lane; j < e; j += 32) {
         a0 += cx[j]; a1 += cy[j]; a2 += cz[j]; ae += er[j]; al += lev[j];
       }
       const T t0 = wsum(a0), t1 = wsum(a1), t2 = wsum(a2), te = wsum(ae);
@@ -473,7 +496,12 @@ __global__ void ch_moments(int ny, int cpw, const long long* __restrict__ off,
         m0 = (T)(S(t0) * inv); m1 = (T)(S(t1) * inv); m2 = (T)(S(t2) * inv);
       }
       T p[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-      for (long long j = b + lane; j < e; j += 32) {
+      if (has) {
+        const T C0 = fx - m0, C1 = fy - m1, C2 = fz - m2;
+        p[0] += C0 * C0; p[1] += C1 * C1; p[2] += C2 * C2;
+        p[3] += C0 * C1; p[4] += C0 * C2; p[5] += C1 * C2;
+      }
+      for (long long j = b + 32 + lane; j < e; j += 32) {
         const T C0 = cx[j] - m0, C1 = cy[j] - m1, C2 = cz[j] - m2;
         p[0] += C0 * C0; p[1] += C1 * C1; p[2] += C2 * C2;
         p[3] += C0 * C1; p[4] += C0 * C2; p[5] += C1 * C2;
