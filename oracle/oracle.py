@@ -91,6 +91,15 @@ class Coeffs(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class FpmCoeffs(C.Structure):
+    """orc_fpm: per-cell coefficients of the plain FPM method (Sec. 2.B/2.C)."""
+    _fields_ = [(n, C.c_double) for n in
+                ("n", "dt", "T_tr", "T_rot", "T_vib",
+                 "mu", "p", "tau_c", "Z_rot", "Z_vib", "tau_rot", "tau_vib", "Pr",
+                 "nu", "tau", "alpha", "T_tr_rel", "T_rot_rel", "e_vib_rel",
+                 "lam_up", "lam_dn", "e_rot_tgt", "e_vib_tgt")] + [("clamped", C.c_int)]
+
+
 class Channel(C.Structure):
     _fields_ = [("ny", C.c_int), ("L", C.c_double), ("T_wall", C.c_double), ("g", C.c_double),
                 ("F_num", C.c_double), ("area", C.c_double), ("reconstruct", C.c_int)]
@@ -196,6 +205,11 @@ def lib():
             L.orc_inflow_normal_speed.argtypes = [C.c_double, C.c_double, C.c_uint32, C.c_uint32,
                                                   C.c_uint64, C.c_int, _U32]
             L.orc_inflow_normal_speed.restype = C.c_double
+            L.orc_fpm_coeffs.argtypes = [C.POINTER(Species)] + [C.c_double] * 5 + \
+                [C.POINTER(FpmCoeffs)]
+            L.orc_gillespie.argtypes = [C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
+                                        C.c_uint32, C.c_int, _U32]
+            L.orc_homog_step_fpm.argtypes = L.orc_homog_step.argtypes
             _lib = L
     return _lib
 
@@ -258,6 +272,23 @@ def cell_coeffs(sp, n, dt, T_tr, T_rot, T_vib) -> Coeffs:
     if rc != 0:
         raise ValueError("cell coefficients undefined: mu/p not positive and finite")
     return cc
+
+
+def fpm_coeffs(sp, n, dt, T_tr, T_rot, T_vib) -> FpmCoeffs:
+    """Per-cell coefficients of the plain FPM method."""
+    fc = FpmCoeffs()
+    rc = lib().orc_fpm_coeffs(C.byref(sp), n, dt, T_tr, T_rot, T_vib, C.byref(fc))
+    if rc != 0:
+        raise ValueError("FPM coefficients undefined: tau not positive")
+    return fc
+
+
+def gillespie(I, lam_up, lam_dn, seed, pid, step, form=0):
+    """(new level, flags) of one particle after one step of Gillespie's method."""
+    fl = C.c_uint32(0)
+    k = lib().orc_gillespie(int(I), float(lam_up), float(lam_dn), C.c_uint64(seed),
+                            C.c_uint32(pid), C.c_uint32(step), int(form), C.byref(fl))
+    return k, fl.value
 
 
 def relaxation_temperatures(sp, cc: Coeffs, alpha, T_tr, T_rot, T_vib):
@@ -361,6 +392,26 @@ def homog_step(sp, form, seed, step0, nsteps, off, ndens, dt, st: State):
                               C.byref(fl), _p(cnt, C.c_int64))
     if rc != 0:
         raise ValueError("cell coefficients undefined in some cell (mu/p not positive and finite)")
+    return fl.value, cnt
+
+
+def homog_step_fpm(sp, form, seed, step0, nsteps, off, ndens, dt, st: State):
+    """Advance independent homogeneous cells ``nsteps`` steps of the plain FPM
+    method (Sec. 2.C) in place.
+
+    Returns (flags, counters)."""
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    ndens = np.ascontiguousarray(ndens, dtype=np.float64)
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    fl = C.c_uint32(0)
+    cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+    rc = lib().orc_homog_step_fpm(C.byref(sp), form, C.c_uint64(seed), step0, nsteps, len(off) - 1,
+                              _p(off, C.c_int64), _p(ndens, C.c_double), _p(dt, C.c_double),
+                              _p(st.cx, C.c_double), _p(st.cy, C.c_double), _p(st.cz, C.c_double),
+                              _p(st.erot, C.c_double), _p(st.lev, C.c_int32), _p(st.pid, C.c_uint32),
+                              C.byref(fl), _p(cnt, C.c_int64))
+    if rc != 0:
+        raise ValueError("FPM coefficients undefined in some cell")
     return fl.value, cnt
 
 

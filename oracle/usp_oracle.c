@@ -807,6 +807,247 @@ int orc_homog_step(const orc_species* sp, int form, uint64_t seed,
 }
 
 /* ======================================================================== */
+/* The plain FPM method (Sec. 2.B model, Sec. 2.C particle scheme).          */
+/* ======================================================================== */
+#define PTAG_GILLESPIE 8u
+
+/* Per-cell coefficients of the FPM method:
+ *   nu = 1 - 3/(2 Pr) (the Pr the model reproduces), tau = 2 mu (1 - nu)/p,
+ *   alpha = exp(-dt/tau) (Eq. conventionial-velo: C exp(-dt/tau) and the
+ *   noise amplitude sqrt(tau (1 - exp(-2dt/tau))) d = sqrt(1 - alpha^2) L
+ *   with L L^T = tau D_tr);
+ *   relaxation energies of Eqs. T_tr_FPM, T_rot_FPM, T_vib_FPM with
+ *   tau_rot = Z_rot tau_c and tau_vib = Z_vib tau_c (Landau-Teller, Sec. 2.A);
+ *   a negative relaxation energy is set to 0 (flagged), as in the USP form.
+ *   Gillespie rates of the master-equation term: with
+ *   ebar_rel = e_vib(T_vib^rel)/(R Theta) = q/(1-q), q = exp(-Theta/T_vib^rel),
+ *   omega_{I,I+1} = 2 (I+1) q / (tau (1-q)) = 2 (I+1) ebar_rel / tau and
+ *   omega_{I,I-1} = 2 I / (tau (1-q)) = 2 I (1 + ebar_rel) / tau; times dt
+ *   they are lam_up (I+1) and lam_dn I.
+ * Reading (the paper applies the conservation scheme of Sec. 4.C to its
+ * methods but states targets only for the USP form): the targets are the
+ * expected mode energies after dt under the FPM update itself,
+ *   e_rot^{n+1} = e_rot(T_rot^rel) + (e_rot^n - e_rot(T_rot^rel)) alpha^2,
+ *   e_vib^{n+1} = e_vib_rel + (e_vib^n - e_vib_rel) alpha^2
+ * (the Milstein square form gives E[eps'] = alpha^2 eps + (1 - alpha^2) R T^rel;
+ * the linear birth-death rates above move the mean level at rate 2/tau toward
+ * ebar_rel). */
+int orc_fpm_coeffs(const orc_species* sp, double n, double dt,
+                   double T_tr, double T_rot, double T_vib, orc_fpm* o)
+{
+    memset(o, 0, sizeof(*o));
+    double R = orc_R(sp);
+    o->n = n; o->dt = dt; o->T_tr = T_tr; o->T_rot = T_rot; o->T_vib = T_vib;
+    o->p = n * KB * T_tr;
+    o->mu = orc_mu(sp, T_tr);
+    o->tau_c = orc_tau_c(sp, n, T_tr);
+    orc_collision_numbers(sp, T_tr, &o->Z_rot, &o->Z_vib);
+    o->tau_rot = o->Z_rot * o->tau_c;
+    o->tau_vib = o->Z_vib * o->tau_c;
+    o->Pr = orc_prandtl(sp, T_vib);
+    o->nu = 1.0 - 3.0 / (2.0 * o->Pr);
+    o->tau = 2.0 * o->mu * (1.0 - o->nu) / o->p;
+    if (!(o->tau > 0.0)) return -1;
+    o->alpha = exp(-dt / o->tau);
+
+    double grot = o->tau / (2.0 * o->tau_rot), gvib = o->tau / (2.0 * o->tau_vib);
+    double e_tr = 1.5 * R * T_tr, e_rot = R * T_rot, e_vib = orc_e_vib(sp, T_vib);
+    double e_tr_rel = e_tr + grot * (R * T_rot - R * T_tr) + gvib * (e_vib - orc_e_vib(sp, T_tr));
+    double e_rot_rel = e_rot + grot * (R * T_tr - R * T_rot);
+    double e_vib_rel = e_vib + gvib * (orc_e_vib(sp, T_tr) - e_vib);
+    if (e_tr_rel < 0.0) { e_tr_rel = 0.0; o->clamped = 1; }
+    if (e_rot_rel < 0.0) { e_rot_rel = 0.0; o->clamped = 1; }
+    if (e_vib_rel < 0.0) { e_vib_rel = 0.0; o->clamped = 1; }
+    o->T_tr_rel = e_tr_rel / (1.5 * R);
+    o->T_rot_rel = e_rot_rel / R;
+    o->e_vib_rel = e_vib_rel;
+
+    double ebar_rel = e_vib_rel / (R * sp->theta_v);
+    o->lam_up = 2.0 * dt * ebar_rel / o->tau;
+    o->lam_dn = 2.0 * dt * (1.0 + ebar_rel) / o->tau;
+
+    double a2 = o->alpha * o->alpha;
+    o->e_rot_tgt = e_rot_rel + (e_rot - e_rot_rel) * a2;
+    o->e_vib_tgt = e_vib_rel + (e_vib - e_vib_rel) * a2;
+    return 0;
+}
+
+/* Gillespie's direct method over one step (Sec. 2.C), time in units of dt:
+ * the waiting time to the next transition is -ln(U1) / rate with
+ * rate = lam_up (I+1) + lam_dn I; the step ends when the accumulated time
+ * passes 1; otherwise U2 < lam_up (I+1) / rate raises the level, else it is
+ * lowered.  Draws: counter (pid, step, 8, k) gives the (U1, U2) pairs of
+ * transitions 2k and 2k+1.  Form 1 takes every operation in float. */
+#define GILLESPIE_CAP 4096
+int orc_gillespie(int I, double lam_up, double lam_dn, uint64_t seed, uint32_t pid,
+                  uint32_t step, int form, uint32_t* flags)
+{
+    uint32_t w[4];
+    if (form == 1) {
+        float lu = (float)lam_up, ld = (float)lam_dn, t = 0.0f;
+        for (int ev = 0; ev < GILLESPIE_CAP; ++ev) {
+            if ((ev & 1) == 0) philox_words(pid, step, PTAG_GILLESPIE, (uint32_t)(ev >> 1), seed, w);
+            float u1 = (float)orc_uniform(w[(ev & 1) * 2], 1);
+            float u2 = (float)orc_uniform(w[(ev & 1) * 2 + 1], 1);
+            float up = lu * (float)(I + 1), dn = ld * (float)I;
+            float rate = up + dn;
+            if (!(rate > 0.0f)) return I;
+            float wait = -logf(u1) / rate;
+            t = t + wait;
+            if (t > 1.0f) return I;
+            if (u2 < up / rate) I += 1; else I -= 1;
+        }
+    } else {
+        double t = 0.0;
+        for (int ev = 0; ev < GILLESPIE_CAP; ++ev) {
+            if ((ev & 1) == 0) philox_words(pid, step, PTAG_GILLESPIE, (uint32_t)(ev >> 1), seed, w);
+            double u1 = orc_uniform(w[(ev & 1) * 2], 0);
+            double u2 = orc_uniform(w[(ev & 1) * 2 + 1], 0);
+            double up = lam_up * (double)(I + 1), dn = lam_dn * (double)I;
+            double rate = up + dn;
+            if (!(rate > 0.0)) return I;
+            double wait = -log(u1) / rate;
+            t = t + wait;
+            if (t > 1.0) return I;
+            if (u2 < up / rate) I += 1; else I -= 1;
+        }
+    }
+    *flags |= ORC_F_SAMPLER_CAP;
+    return I;
+}
+
+/* One particle of the FPM method: Eq. conventionial-velo (C = c - U,
+ * c' = U + alpha C + sqrt(1 - alpha^2) L G with L L^T = tau D_tr =
+ * R T_tr^rel I + nu (Pi - R T_tr I), Eq. D_tr), Eq. conventionial-erot
+ * (the same square form as the USP rotational update with this alpha), and
+ * the Gillespie levels.  Reading (Sec. 2 gives no positivity fix for the FPM
+ * method): when tau D_tr is not positive definite, nu is limited to the
+ * admissible bound of Eq. nu_USP_positivity (times 1 - 1e-6), and if the
+ * factorisation still fails nu = 0; alpha stays exp(-dt/tau). */
+void orc_collide_particle_fpm(const orc_species* sp, int form, const orc_fpm* fc,
+                              const double U[3], const double Pi[6], const double G[4],
+                              uint64_t seed, uint32_t pid, uint32_t step,
+                              double c[3], double* erot, int32_t* lev,
+                              uint32_t* flags, int64_t* counters)
+{
+    double R = orc_R(sp);
+    double nu = fc->nu;
+    double RT = R * fc->T_tr, RTrel = R * fc->T_tr_rel;
+    double M[6], L[6];
+    M[0] = RTrel + nu * (Pi[0] - RT);
+    M[1] = RTrel + nu * (Pi[1] - RT);
+    M[2] = RTrel + nu * (Pi[2] - RT);
+    M[3] = nu * Pi[3];
+    M[4] = nu * Pi[4];
+    M[5] = nu * Pi[5];
+    if (!orc_cholesky3(M, L)) {
+        counters[ORC_C_CHOL_FIX] += 1;
+        double lmin, lmax;
+        orc_sym3_eig_minmax(Pi, &lmin, &lmax);
+        if (nu <= 0.0) {
+            if (lmax - RT > 0.0) { double bd = -RTrel / (lmax - RT); if (bd > nu) nu = bd; }
+        } else {
+            if (RT - lmin > 0.0) { double bd = RTrel / (RT - lmin); if (bd < nu) nu = bd; }
+        }
+        nu = nu * (1.0 - 1e-6);
+        M[0] = RTrel + nu * (Pi[0] - RT);
+        M[1] = RTrel + nu * (Pi[1] - RT);
+        M[2] = RTrel + nu * (Pi[2] - RT);
+        M[3] = nu * Pi[3];
+        M[4] = nu * Pi[4];
+        M[5] = nu * Pi[5];
+        if (!orc_cholesky3(M, L)) {
+            counters[ORC_C_NU_ZERO] += 1;
+            double s = RTrel > 0.0 ? sqrt(RTrel) : 0.0;
+            if (!(RTrel > 0.0)) *flags |= ORC_F_CHOL_FAIL_AFTER_FIX;
+            L[0] = s; L[1] = 0.0; L[2] = s; L[3] = 0.0; L[4] = 0.0; L[5] = s;
+        }
+    }
+    double alpha = fc->alpha, a2 = alpha * alpha, sq = sqrt(1.0 - a2);
+    double LG0 = L[0] * G[0];
+    double LG1 = L[1] * G[0] + L[2] * G[1];
+    double LG2 = L[3] * G[0] + L[4] * G[1] + L[5] * G[2];
+    c[0] = U[0] + alpha * (c[0] - U[0]) + sq * LG0;
+    c[1] = U[1] + alpha * (c[1] - U[1]) + sq * LG1;
+    c[2] = U[2] + alpha * (c[2] - U[2]) + sq * LG2;
+
+    double a = R * fc->T_rot_rel * (1.0 - a2) / 2.0;
+    double root = sqrt(*erot) * alpha + sqrt(a) * G[3];
+    *erot = a + root * root;
+
+    *lev = orc_gillespie(*lev, fc->lam_up, fc->lam_dn, seed, pid, step, form, flags);
+}
+
+/* Steps of independent homogeneous cells with the FPM method: the cell
+ * loop of orc_homog_step with orc_fpm_coeffs, orc_collide_particle_fpm and
+ * the conservation scheme of Sec. 4.C with the FPM targets. */
+int orc_homog_step_fpm(const orc_species* sp, int form, uint64_t seed,
+                       int64_t step0, int nsteps, int n_inst, const int64_t* off,
+                       const double* ndens, const double* dt,
+                       double* cx, double* cy, double* cz, double* erot,
+                       int32_t* lev, const uint32_t* pid,
+                       uint32_t* flags, int64_t* counters)
+{
+    double R = orc_R(sp);
+    int status = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        uint32_t step = (uint32_t)(step0 + s);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+        for (int ci = 0; ci < n_inst; ++ci) {
+            uint32_t lflags = 0;
+            int64_t lcnt[ORC_NCOUNTERS] = { 0 };
+            int64_t b = off[ci], e = off[ci + 1];
+            int64_t N = e - b;
+            if (N < 2) { lcnt[ORC_C_SKIPPED_CELLS] += 1; goto merge; }
+            {
+                double U[3] = { 0, 0, 0 }, er = 0.0, lv = 0.0, P[6] = { 0, 0, 0, 0, 0, 0 };
+                for (int64_t j = b; j < e; ++j) { U[0] += cx[j]; U[1] += cy[j]; U[2] += cz[j]; er += erot[j]; lv += lev[j]; }
+                U[0] /= N; U[1] /= N; U[2] /= N; er /= N; lv /= N;
+                for (int64_t j = b; j < e; ++j) {
+                    double C0 = cx[j] - U[0], C1 = cy[j] - U[1], C2 = cz[j] - U[2];
+                    P[0] += C0 * C0; P[1] += C1 * C1; P[2] += C2 * C2;
+                    P[3] += C0 * C1; P[4] += C0 * C2; P[5] += C1 * C2;
+                }
+                for (int k = 0; k < 6; ++k) P[k] /= N;
+                double T_tr = (P[0] + P[1] + P[2]) / (3.0 * R);
+                double T_rot = er / R;
+                double T_vib = orc_T_vib_from_mean_level(sp, lv);
+
+                orc_fpm fc;
+                if (orc_fpm_coeffs(sp, ndens[ci], dt[ci], T_tr, T_rot, T_vib, &fc) != 0) {
+                    lflags |= ORC_F_A_NONPOS;
+                    goto merge;
+                }
+                if (fc.clamped) { lflags |= ORC_F_TREL_CLAMP; lcnt[ORC_C_TREL_CLAMP] += 1; }
+                for (int64_t j = b; j < e; ++j) {
+                    double G[4], u5, u6, c[3] = { cx[j], cy[j], cz[j] };
+                    uint32_t id = pid ? pid[j] : (uint32_t)j;
+                    particle_draws(seed, id, step, form, G, &u5, &u6);
+                    orc_collide_particle_fpm(sp, form, &fc, U, P, G, seed, id, step,
+                                             c, &erot[j], &lev[j], &lflags, lcnt);
+                    cx[j] = c[0]; cy[j] = c[1]; cz[j] = c[2];
+                }
+                conserve_cell(sp, seed, (uint32_t)ci, step, b, e,
+                              1.5 * R * T_tr, R * T_rot, orc_e_vib(sp, T_vib), U,
+                              fc.e_rot_tgt, fc.e_vib_tgt, cx, cy, cz, erot, lev, &lflags, lcnt);
+            }
+        merge:
+#ifdef _OPENMP
+#pragma omp critical(orc_merge_fpm)
+#endif
+            {
+                *flags |= lflags;
+                for (int k = 0; k < ORC_NCOUNTERS; ++k) counters[k] += lcnt[k];
+            }
+        }
+        if (*flags & ORC_F_A_NONPOS) status = -1;
+    }
+    return status;
+}
+
+/* ======================================================================== */
 /* 1D channel between two fully diffuse plates (the Poiseuille set-up of    */
 /* Sec. 5.B, force-driven).  One step, in the order of the host particle    */
 /* framework the paper builds on: move (with wall interaction) -> sort by   */

@@ -125,6 +125,39 @@ void   orc_moments(const orc_species* sp, int ncell, const int64_t* off,
                    const double* cx, const double* cy, const double* cz,
                    const double* erot, const int32_t* lev, double* out);
 
+/* ---- the plain FPM method (Sec. 2.B model, Sec. 2.C particle scheme) -----
+ * The first-order method the paper builds on: Gorji's velocity integrator
+ * with alpha = exp(-dt/tau), the modified-Milstein rotational update with the
+ * same alpha, Gillespie's direct method for the vibrational levels, and the
+ * conservation scheme of Sec. 4.C. */
+typedef struct {
+    double n, dt, T_tr, T_rot, T_vib;
+    double mu, p, tau_c, Z_rot, Z_vib, tau_rot, tau_vib, Pr;
+    double nu;        /* 1 - 3 / (2 Pr)                                        */
+    double tau;       /* 2 mu (1 - nu) / p                                     */
+    double alpha;     /* exp(-dt / tau)                                        */
+    double T_tr_rel, T_rot_rel, e_vib_rel;   /* Eqs. T_tr_FPM .. T_vib_FPM      */
+    double lam_up, lam_dn;   /* level rates per unit (I+1) and I, times dt     */
+    double e_rot_tgt, e_vib_tgt;   /* expected mode energies after dt          */
+    int    clamped;   /* a relaxation energy was negative and set to 0         */
+} orc_fpm;
+
+int    orc_fpm_coeffs(const orc_species* sp, double n, double dt,
+                      double T_tr, double T_rot, double T_vib, orc_fpm* out);
+int    orc_gillespie(int I, double lam_up, double lam_dn, uint64_t seed, uint32_t pid,
+                     uint32_t step, int form, uint32_t* flags);
+void   orc_collide_particle_fpm(const orc_species* sp, int form, const orc_fpm* fc,
+                                const double U[3], const double Pi[6], const double G[4],
+                                uint64_t seed, uint32_t pid, uint32_t step,
+                                double c[3], double* erot, int32_t* lev,
+                                uint32_t* flags, int64_t* counters);
+int    orc_homog_step_fpm(const orc_species* sp, int form, uint64_t seed,
+                          int64_t step0, int nsteps, int n_inst, const int64_t* off,
+                          const double* ndens, const double* dt,
+                          double* cx, double* cy, double* cz, double* erot,
+                          int32_t* lev, const uint32_t* pid,
+                          uint32_t* flags, int64_t* counters);
+
 /* ---- one or more steps of independent homogeneous cells ("instances") ---- */
 int    orc_homog_step(const orc_species* sp, int form, uint64_t seed,
                       int64_t step0, int nsteps, int n_inst, const int64_t* off,
