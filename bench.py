@@ -55,6 +55,8 @@ def parse():
                     help="shrink particle counts (debug only; the default is the full workload)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--fpm-steps", type=int, default=100,
+                    help="steps of the plain FPM method (Sec. 2.C) on the same workload, FP32")
     ap.add_argument("--channel-steps", type=int, default=2000)
     ap.add_argument("--cylinder-steps", type=int, default=64)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -364,6 +366,27 @@ def run_ours(args, rank, world, local):
                 "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
         c64.destroy()
 
+    # ---- the first-order FPM method on the same workload (FP32 state) -----
+    fpm = None
+    if args.fpm_steps > 0:
+        cf = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, dt, p.cx, p.cy, p.cz,
+                                      p.erot, p.lev, precision=usp.USP_FP32, seed=w.seed,
+                                      stream=stream.cuda_stream, use_graph=True,
+                                      method=usp.USP_METHOD_FPM)
+        usp.usp_step(cf, 3)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        usp.usp_step(cf, args.fpm_steps)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        msf = max_over_ranks(g0.elapsed_time(g1))
+        ffl, _ = usp.usp_status(cf)
+        fpm = {"method": "plain FPM (Gorji integrator, Milstein rotation, Gillespie levels)",
+               "value": total_particles * args.fpm_steps / (msf / 1e3), "unit": UNIT,
+               "ms_per_step": msf / args.fpm_steps, "steps": args.fpm_steps, "flags": int(ffl)}
+        cf.destroy()
+
     # ---- the spatial path: force-driven Poiseuille channel (64 x 200) -----
     chan = None
     if args.channel_steps > 0:
@@ -448,7 +471,8 @@ def run_ours(args, rank, world, local):
                              "autotune": {"warp_tiles": warp_tiles, "blocks_per_sm": minb,
                                           "ms_block_tiled_2_3_4": [float(x) for x in tune_ms[:3]],
                                           "ms_warp_tiled_2_3_4": [float(x) for x in tune_ms[3:]]}},
-                "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "poiseuille_channel": chan,
+                "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "fpm_method": fpm,
+                "poiseuille_channel": chan,
                 "cylinder_plane": cyl,
                 "clocks": clk,
                 "status": {"flags": int(flags), "counters": [int(x) for x in counters]}}

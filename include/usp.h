@@ -104,6 +104,20 @@ enum {
  * random numbers; discrete outcomes held fixed). */
 enum { USP_FP64 = 0, USP_FP32 = 1, USP_FP64_TANGENT = 2 };
 
+/* Particle method (usp_config.method, homogeneous contexts):
+ * USP_METHOD_USP_FPM  the second-order USP-FPM method (Sec. 3, 4), default;
+ * USP_METHOD_FPM      the first-order FPM method it extends (Sec. 2.B model,
+ *                     Sec. 2.C scheme): alpha = exp(-dt/tau),
+ *                     tau = 2 mu (1 - nu)/p, nu = 1 - 3/(2 Pr), relaxation
+ *                     temperatures of Eqs. T_tr_FPM .. T_vib_FPM, Gillespie's
+ *                     direct method for the vibrational levels (draws: Philox
+ *                     counter (particle id, step, 8, k), two transitions per
+ *                     block), and the conservation scheme of Sec. 4.C with the
+ *                     expected mode energies after dt as targets.  When
+ *                     tau D_tr is not positive definite, nu is limited to the
+ *                     admissible bound of Eq. nu_USP_positivity, then set to 0. */
+enum { USP_METHOD_USP_FPM = 0, USP_METHOD_FPM = 1 };
+
 /* Gas species.  VSS/VHS viscosity parameters of Sec. 4.A; theta_v of the
  * harmonic vibrational model (Sec. 2.A); zmodel 0 uses the fixed collision
  * numbers Z_rot, Z_vib (Sec. 2.A), zmodel 1 the Parker and Millikan-White /
@@ -132,6 +146,8 @@ typedef struct {
   usp_alloc_fn alloc;   /* optional allocator (NULL = cudaMalloc)            */
   usp_free_fn free_;
   void* alloc_user;
+  int method;           /* USP_METHOD_*; channel and plane contexts take only
+                           USP_METHOD_USP_FPM (USP_ENOTSUP otherwise)         */
 } usp_config;
 
 /* 1D channel between two fully diffuse plates at y = 0 and y = L (the

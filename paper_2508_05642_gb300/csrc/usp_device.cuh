@@ -37,7 +37,7 @@ enum { C_CHOL_FIX = 0, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND,
 
 // Philox stream layout: particle counter (pid, step, tag, 0); cell counter
 // (cell, step, 0x80000000 | tag, block).
-enum : uint32_t { PTAG_NORMALS = 0u, PTAG_JUMPS = 1u };
+enum : uint32_t { PTAG_NORMALS = 0u, PTAG_JUMPS = 1u, PTAG_GILLESPIE = 8u };
 enum : uint32_t { CTAG_IDELTA = 0x80000000u, CTAG_PICK = 0x80000001u };
 
 struct Species {
@@ -47,6 +47,7 @@ struct Species {
   // derived on the host: T_ref^omega, pi d_ref^2 / sigma_vib, R = k_B / m,
   // and the VSS mu_ref and tau_c / (mu / p) at this omega
   double Tref_w, zv_ht, R, mu_ref0, tauf0;
+  int method;   // 0 USP-FPM (Sec. 3, 4), 1 the plain FPM method (Sec. 2.C)
 };
 
 // ---------------------------------------------------------------------------
@@ -592,6 +593,114 @@ __device__ inline CellCoeffsF cell_coeffs_f32(const Species& s, double n, double
 // [0, 1 - 1e-12], the sign giving the Pr nearest the target, up to four
 // passes; then nu = 0 with alpha^2 = B, a failure only if T_tr^rel is 0).  Also returns the relaxation temperatures for that
 // alpha.  chol_fix / fail report what happened.
+// ---------------------------------------------------------------------------
+// The plain FPM method (Sec. 2.B model, Sec. 2.C particle scheme), per cell
+// in FP64: nu = 1 - 3/(2 Pr), tau = 2 mu (1 - nu)/p, alpha = exp(-dt/tau);
+// relaxation energies of Eqs. T_tr_FPM, T_rot_FPM, T_vib_FPM with
+// tau_rot = Z_rot tau_c, tau_vib = Z_vib tau_c (negative ones set to 0);
+// the Cholesky factor of tau D_tr = R T_tr^rel I + nu (Pi - R T_tr I), nu
+// limited to the admissible bound of Eq. nu_USP_positivity (times 1 - 1e-6)
+// when it is not positive definite, then 0; the Gillespie rates per unit
+// (I+1) and I times dt: lam_up = 2 dt ebar_rel / tau and
+// lam_dn = 2 dt (1 + ebar_rel) / tau with ebar_rel = e_vib_rel / (R Theta);
+// the conservation targets: the expected rotational and vibrational energies
+// after dt, e_rel + (e^n - e_rel) alpha^2.
+// ---------------------------------------------------------------------------
+struct FpmCell {
+  double alpha, L[6], Trot_rel, lam_up, lam_dn, e_rot_tgt, e_vib_tgt;
+  bool ok, fixed, nu_zero, failed, clamped;
+};
+
+__device__ inline FpmCell fpm_cell(const Species& s, double n, double dt, const double* Pi,
+                                   double Ttr, double Trot, double Tvib) {
+  FpmCell o;
+  o.fixed = o.nu_zero = o.failed = o.clamped = false;
+  const double R = gasR(s);
+  const double p = n * kB * Ttr;
+  const double xw = exp(s.omega * log(Ttr / s.T_ref));
+  const double mu = s.mu_ref0 * xw;
+  const double tau_c = s.tauf0 * mu / p;
+  double zr, zv;
+  collision_numbers<double>(s, Ttr, xw, s.Z_rot, zr, zv);
+  const double Pr = prandtl_T<double>(s, Tvib);
+  const double nu0 = 1.0 - 3.0 / (2.0 * Pr);
+  const double tau = 2.0 * mu * (1.0 - nu0) / p;
+  o.ok = tau > 0.0;
+  o.alpha = o.ok ? exp(-dt / tau) : 0.0;
+  const double grot = tau / (2.0 * zr * tau_c), gvib = tau / (2.0 * zv * tau_c);
+  const double ev = e_vib_T<double>(s, Tvib), evt = e_vib_T<double>(s, Ttr);
+  double etr = 1.5 * R * Ttr + grot * (R * Trot - R * Ttr) + gvib * (ev - evt);
+  double erot = R * Trot + grot * (R * Ttr - R * Trot);
+  double evib = ev + gvib * (evt - ev);
+  if (etr < 0.0) { etr = 0.0; o.clamped = true; }
+  if (erot < 0.0) { erot = 0.0; o.clamped = true; }
+  if (evib < 0.0) { evib = 0.0; o.clamped = true; }
+  const double RT = R * Ttr, RTrel = etr / 1.5;
+  o.Trot_rel = erot / R;
+  const double ebar = evib / (R * s.theta_v);
+  o.lam_up = 2.0 * dt * ebar / tau;
+  o.lam_dn = 2.0 * dt * (1.0 + ebar) / tau;
+  const double a2 = o.alpha * o.alpha;
+  o.e_rot_tgt = erot + (R * Trot - erot) * a2;
+  o.e_vib_tgt = evib + (ev - evib) * a2;
+  double nu = nu0, M[6];
+  auto fill = [&](double nu_) {
+    M[0] = RTrel + nu_ * (Pi[0] - RT);
+    M[1] = RTrel + nu_ * (Pi[1] - RT);
+    M[2] = RTrel + nu_ * (Pi[2] - RT);
+    M[3] = nu_ * Pi[3];
+    M[4] = nu_ * Pi[4];
+    M[5] = nu_ * Pi[5];
+  };
+  fill(nu);
+  if (chol3(M, o.L)) return o;
+  o.fixed = true;
+  double lmin, lmax;
+  sym3_minmax(Pi, lmin, lmax);
+  if (nu <= 0.0) {
+    if (lmax - RT > 0.0) nu = fmax(nu, -RTrel / (lmax - RT));
+  } else {
+    if (RT - lmin > 0.0) nu = fmin(nu, RTrel / (RT - lmin));
+  }
+  nu = nu * (1.0 - 1e-6);
+  fill(nu);
+  if (chol3(M, o.L)) return o;
+  o.nu_zero = true;
+  const double sq = RTrel > 0.0 ? sqrt(RTrel) : 0.0;
+  o.failed = !(RTrel > 0.0);
+  o.L[0] = sq; o.L[1] = 0.0; o.L[2] = sq; o.L[3] = 0.0; o.L[4] = 0.0; o.L[5] = sq;
+  return o;
+}
+
+// Gillespie's direct method over one step (Sec. 2.C), time in units of dt:
+// waiting time -ln(U1) / rate with rate = lam_up (I+1) + lam_dn I, the step
+// ends once the time passes 1, else U2 < lam_up (I+1) / rate raises the
+// level and otherwise lowers it.  Counter (pid, step, 8, k) draws the (U1,
+// U2) pairs of transitions 2k and 2k+1.  Every operation is an explicit
+// round-to-nearest one in the working precision, so the outcome is a fixed
+// function of (I, lam_up, lam_dn, the draws) up to the logarithm.
+constexpr int kGillespieCap = 4096;
+template <typename T>
+__device__ __forceinline__ int gillespie(int I, T lu, T ld, uint32_t pid, uint32_t step,
+                                         const PhiloxRoundKeys& rk, uint32_t& fl) {
+  T t = T(0);
+  U4 w = {0u, 0u, 0u, 0u};
+#pragma unroll 1
+  for (int ev = 0; ev < kGillespieCap; ++ev) {
+    if ((ev & 1) == 0) w = philox4x32_10(pid, step, PTAG_GILLESPIE, (uint32_t)(ev >> 1), rk);
+    const T u1 = uniform_open<T>((ev & 1) ? w.z : w.x);
+    const T u2 = uniform_open<T>((ev & 1) ? w.w : w.y);
+    const T up = rn_mul(lu, rn_i2f(I + 1, T(0))), dn = rn_mul(ld, rn_i2f(I, T(0)));
+    const T rate = rn_add(up, dn);
+    if (!(rate > T(0))) return I;
+    t = rn_add(t, rn_div(-log(u1), rate));
+    if (t > T(1)) return I;
+    I += (u2 < rn_div(up, rate)) ? 1 : -1;
+  }
+  fl |= F_SAMPLER_CAP;
+  return I;
+}
+
 struct DriftDiff {
   double alpha, L[6], Ttr_rel, Trot_rel, evib_rel;
   bool fixed, nu_zero, failed, clamped;

@@ -70,10 +70,11 @@ struct alignas(16) CollideParams {
   T as, ar;                  // alpha * s, alpha * sqrt(r)
   T Lp[6];                   // sqrt(1 - alpha^2) L, L L^T = tau D_tr
   T a_rot, sqrt_a;           // R T_rot^rel (1 - alpha^2) / 2 and its root
-  T p_nb, p_b;
+  T p_nb, p_b;               // USP-FPM: jump parameters; FPM: lam_up, lam_dn
   unsigned int step, pid0;
   long long off;
   int count, active;
+  int method, pad_;          // Species::method of the context
 };
 
 struct CellSums {
@@ -240,15 +241,20 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   er = P.a_rot + root * root;
   // I' = I + NB(I + 1, p_NB) - B(I, p_B)
   const T u5 = uniform_open<T>(w2.x), u6 = uniform_open<T>(w2.y);
-  int up, dn;
-  if constexpr (sizeof(T) == 4) {
-    up = nb_tab(rnb, t_nb, I + 1, P.p_nb, u5, fl);
-    dn = b_tab(rb, t_b, I, P.p_b, u6, fl);
+  if (P.method == 1) {
+    // plain FPM method: Gillespie's direct method (Sec. 2.C)
+    lv = gillespie<T>(I, P.p_nb, P.p_b, pid, P.step, rk, fl);
   } else {
-    up = sample_nb<T>(I + 1, P.p_nb, u5, fl);
-    dn = sample_b<T>(I, P.p_b, u6, fl);
+    int up, dn;
+    if constexpr (sizeof(T) == 4) {
+      up = nb_tab(rnb, t_nb, I + 1, P.p_nb, u5, fl);
+      dn = b_tab(rb, t_b, I, P.p_b, u6, fl);
+    } else {
+      up = sample_nb<T>(I + 1, P.p_nb, u5, fl);
+      dn = sample_b<T>(I, P.p_b, u6, fl);
+    }
+    lv = I + up - dn;
   }
-  lv = I + up - dn;
   maxI = max(maxI, lv);
   acc[0] += r0; acc[1] += r1; acc[2] += r2;
   acc[3] += r0 * r0; acc[4] += r1 * r1; acc[5] += r2 * r2;
@@ -801,8 +807,40 @@ __device__ void write_params(const Species& sp, CellState& cs, CollideParams<T>&
   P.count = (int)cs.N;
   P.active = cs.active;
   for (int i = 0; i < 3; ++i) { P.U[i] = (T)cs.U[i]; P.Us[i] = (T)cs.Us[i]; }
+  P.method = sp.method;
+  P.pad_ = 0;
   if (!cs.active) return;
   const double Tvib = T_vib_of_level(sp, cs.ebar);
+  if (sp.method == 1) {
+    // the plain FPM method (Sec. 2.C): Gorji's velocity update and the
+    // Milstein square form with alpha = exp(-dt/tau), Gillespie levels
+    const FpmCell f = fpm_cell(sp, cs.ndens, cs.dt, cs.Pi, cs.Ttr, cs.Trot, Tvib);
+    if (!f.ok) {
+      atomicOr(flags, (uint32_t)F_A_NONPOS);
+      cs.active = 0;
+      P.active = 0;
+      return;
+    }
+    cs.e_rot_tgt = f.e_rot_tgt;
+    cs.e_vib_tgt = f.e_vib_tgt;
+    if (f.fixed) atomicAdd(&counters[C_CHOL_FIX], 1ull);
+    if (f.nu_zero) atomicAdd(&counters[C_NU_ZERO], 1ull);
+    if (f.failed) atomicOr(flags, (uint32_t)F_CHOL_FAIL_AFTER_FIX);
+    if (f.clamped) {
+      atomicOr(flags, (uint32_t)F_TREL_CLAMP);
+      atomicAdd(&counters[C_TREL_CLAMP], 1ull);
+    }
+    const double a = f.alpha, oma2 = 1.0 - a * a, sq = sqrt(oma2);
+    P.as = (T)(a * cs.s);
+    P.ar = (T)(a * sqrt(cs.r));
+    for (int i = 0; i < 6; ++i) P.Lp[i] = (T)(sq * f.L[i]);
+    const double arot = R * f.Trot_rel * oma2 / 2.0;
+    P.a_rot = (T)arot;
+    P.sqrt_a = (T)sqrt(arot);
+    P.p_nb = (T)f.lam_up;
+    P.p_b = (T)f.lam_dn;
+    return;
+  }
   const CellCoeffs c = cell_coeffs(sp, cs.ndens, cs.dt, cs.Ttr, cs.Trot, Tvib);
   if (!c.ok) {
     atomicOr(flags, (uint32_t)F_A_NONPOS);
@@ -1337,6 +1375,7 @@ Species to_dev(const usp_species* s) {
   d.mu_ref0 = 5.0 * (ca + 1.0) * (ca + 2.0) * std::sqrt(s->m * kB * s->T_ref / kPi) /
               (4.0 * ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) * s->d_ref * s->d_ref);
   d.tauf0 = ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (ca + 1.0) * (ca + 2.0));
+  d.method = 0;
   return d;
 }
 
@@ -1515,7 +1554,7 @@ int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, voi
 
 // jump tables for the coming step (FP32 form only)
 int launch_tables(usp_ctx* c, const CellRange& r) {
-  if (c->precision != USP_FP32 || r.c1 <= r.c0) return USP_OK;
+  if (c->precision != USP_FP32 || c->sp.method != 0 || r.c1 <= r.c0) return USP_OK;
   jumptable_kernel<<<r.c1 - r.c0, 2 * kJR, 0, c->stream>>>(
       r.c0, r.c1, (const CollideParams<float>*)c->prm, c->cells, c->tab_nb, c->tab_b);
   CK(cudaGetLastError());
@@ -1550,7 +1589,7 @@ int launch_step(usp_ctx* c, const CellRange& r) {
 int kernels_per_step(const usp_ctx* c) {
   if (c->kind == 1) return ch_kernels_per_step(c->ch);
   if (c->kind == 2) return pl_kernels_per_step(c->pl);
-  return c->precision == USP_FP32 ? 4 : 3;
+  return c->precision == USP_FP32 && c->sp.method == 0 ? 4 : 3;
 }
 
 int step_once(usp_ctx* c) {
@@ -1602,7 +1641,7 @@ int init_params(usp_ctx* c, const CellRange& r) {
   CK(cudaGetLastError());
   c->launches += 2;
   if ((rc = launch_tables(c, r))) return rc;
-  c->launches += c->precision == USP_FP32 ? 1 : 0;
+  c->launches += c->precision == USP_FP32 && c->sp.method == 0 ? 1 : 0;
   return USP_OK;
 }
 template <typename T>
@@ -1863,6 +1902,7 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
       !(sp->theta_v > 0))
     return USP_EINVAL;
   *out = nullptr;
+  if (cfg->method != USP_METHOD_USP_FPM && cfg->method != USP_METHOD_FPM) return USP_EINVAL;
   usp_ctx* c = new usp_ctx();
   c->kind = 0;
   c->ch = nullptr;
@@ -1870,6 +1910,7 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   std::memset((void*)&c->sp, 0, sizeof(c->sp));
   c->cfg = *cfg;
   c->sp = to_dev(sp);
+  c->sp.method = cfg->method;
   c->precision = cfg->precision;
   c->ncell = n_cells;
   c->nparticles = n;
@@ -2008,6 +2049,7 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
                      const double* h_cx, const double* h_cy, const double* h_cz,
                      const double* h_erot, const int32_t* h_lev, const uint32_t* h_pid) {
   if (!out || !sp || !cfg || !ch) return USP_EINVAL;
+  if (cfg->method != USP_METHOD_USP_FPM) return USP_ENOTSUP;
   if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64 &&
       cfg->precision != USP_FP64_TANGENT)
     return USP_EINVAL;
@@ -2075,6 +2117,7 @@ int usp_init_plane(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
                    const double* h_cy, const double* h_cz, const double* h_erot,
                    const int32_t* h_lev, const uint32_t* h_pid) {
   if (!out || !sp || !cfg || !pl) return USP_EINVAL;
+  if (cfg->method != USP_METHOD_USP_FPM) return USP_ENOTSUP;
   if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64) return USP_EINVAL;
   if (!(sp->m > 0) || !(sp->d_ref > 0) || !(sp->T_ref > 0) || !(sp->c_alpha > 0) ||
       !(sp->theta_v > 0))

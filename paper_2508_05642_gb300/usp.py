@@ -43,6 +43,7 @@ EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogene
             "usp_moments_noalloc", "usp_init_channel", "usp_channel_sample",
             "usp_channel_read", "usp_channel_get_particles", "usp_init_plane", "usp_plane_count",
             "usp_plane_get_particles", "usp_sample", "usp_sample_read", "usp_destroy"]
+USP_METHOD_USP_FPM, USP_METHOD_FPM = 0, 1
 USP_NOALLOC_MAX_CELLS = 8192
 
 
@@ -78,7 +79,8 @@ class usp_plane(C.Structure):
 class usp_config(C.Structure):
     _fields_ = [("precision", C.c_int), ("seed", C.c_uint64), ("step0", C.c_int64),
                 ("stream", C.c_void_p), ("use_graph", C.c_int), ("tile", C.c_int),
-                ("alloc", ALLOC_FN), ("free_", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("alloc", ALLOC_FN), ("free_", FREE_FN), ("alloc_user", C.c_void_p),
+                ("method", C.c_int)]
 
 
 _lock = threading.Lock()
@@ -205,8 +207,9 @@ class Context:
 
 def usp_init_homogeneous(species: dict, offsets, ndens, dt, cx, cy, cz, erot, lev, *,
                          precision=USP_FP32, seed=1, step0=0, stream=None, use_graph=True,
-                         tile=0, allocator=None) -> Context:
-    """Create a context for independent homogeneous cells; arrays are host numpy."""
+                         tile=0, allocator=None, method=0) -> Context:
+    """Create a context for independent homogeneous cells; arrays are host numpy.
+    ``method``: USP_METHOD_USP_FPM (0) or USP_METHOD_FPM (1)."""
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     nd = np.ascontiguousarray(ndens, dtype=np.float64)
     dtv = np.ascontiguousarray(dt, dtype=np.float64)
@@ -220,6 +223,7 @@ def usp_init_homogeneous(species: dict, offsets, ndens, dt, cx, cy, cz, erot, le
     cfg.stream = stream or None
     cfg.use_graph = 1 if use_graph else 0
     cfg.tile = tile
+    cfg.method = int(method)
     keep = []
     if allocator is not None:
         a_fn, f_fn, user = allocator

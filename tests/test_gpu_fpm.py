@@ -1,0 +1,128 @@
+"""GPU parity of the plain FPM method (Sec. 2.B model, Sec. 2.C scheme:
+Gorji's velocity integrator, the modified-Milstein rotational update,
+Gillespie's direct method for the levels, the conservation scheme of
+Sec. 4.C) against the oracle's FPM method on the same seeded inputs, with the
+bars of the USP-FPM parity tests."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2508_05642_gb300 import inputs as I
+from paper_2508_05642_gb300 import usp
+from test_gpu_homog import _check_moments, _gpu_dt, _oracle_dt
+
+pytestmark = pytest.mark.gpu
+
+
+def _ragged(seed, n_inst, nmin, nmax, steps, small=True):
+    w = I.batched_instances(seed=seed, n_inst=n_inst, nmin=nmin, nmax=nmax, steps=steps)
+    if not small:
+        return w
+    counts = np.diff(w.offsets)
+    counts[:4] = [0, 1, 2, 3]
+    off = np.zeros(len(counts) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(counts)
+    rng = np.random.default_rng(seed + 1)
+    sp = w.species
+    parts = [I.equilibrium_particles(rng, int(n), sp["m"], sp["theta_v"], T_tr=w.T_nominal[i, 0],
+                                     T_rot=w.T_nominal[i, 1], T_vib=w.T_nominal[i, 2])
+             for i, n in enumerate(counts)]
+    cat = lambda k: np.concatenate([getattr(p, k) for p in parts])
+    w.offsets = off
+    w.particles = I.Particles(cat("cx"), cat("cy"), cat("cz"), cat("erot"), cat("lev"))
+    return w
+
+
+def _run(w, steps, precision, **kw):
+    form = 1 if precision == usp.USP_FP32 else 0
+    p = w.particles.astype_f32_exact() if form else w.particles
+    st = O.State.from_arrays(p.cx, p.cy, p.cz, p.erot, p.lev)
+    sp = O.species(**w.species)
+    ofl, _ = O.homog_step_fpm(sp, form, w.seed, 0, steps, w.offsets, w.ndens, _oracle_dt(w), st)
+    ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, _gpu_dt(w), p.cx, p.cy, p.cz,
+                                   p.erot, p.lev, precision=precision, seed=w.seed,
+                                   method=usp.USP_METHOD_FPM, **kw)
+    return ctx, st, sp, ofl
+
+
+def test_fpm_fp64_batched_ragged_matches_oracle():
+    """FP64 form, ten steps, 40 cells of uneven size (0 to 3000 particles,
+    several tiles with ragged tails); cells of fewer than two particles stay
+    untouched."""
+    w = _ragged(31, 40, 50, 3000, 10)
+    ctx, st, sp, ofl = _run(w, 10, usp.USP_FP64, tile=256)
+    usp.usp_step(ctx, 10)
+    gm = usp.usp_moments(ctx)
+    gs = usp.usp_get_particles(ctx)
+    fl, _ = usp.usp_status(ctx)
+    assert fl & usp.ERROR_FLAGS == 0 and ofl & O.F_SAMPLER_CAP == 0
+    om = O.moments(sp, w.offsets, st)
+    _check_moments(om, gm, sp)
+    assert np.mean(gs[4] != st.lev) < 1e-5
+    for i in range(2):
+        b, e = w.offsets[i], w.offsets[i + 1]
+        assert np.array_equal(gs[0][b:e], w.particles.cx[b:e])
+
+
+def test_fpm_fp32_single_step_matches_oracle():
+    """FP32 state, one step from the identical state; the Gillespie decisions
+    are taken in float on both sides."""
+    w = _ragged(33, 24, 500, 20000, 1, small=False)
+    ctx, st, sp, _ = _run(w, 1, usp.USP_FP32, tile=1024)
+    usp.usp_step(ctx, 1)
+    gm = usp.usp_moments(ctx)
+    gx, gy, gz, ge, gl = usp.usp_get_particles(ctx)
+    om = O.moments(sp, w.offsets, st)
+    _check_moments(om, gm, sp)
+    assert np.mean(gl != st.lev) < 1e-4
+    R = O.R(sp)
+    for i in range(w.n_cells):
+        b, e = w.offsets[i], w.offsets[i + 1]
+        vth = math.sqrt(R * om[4, i])
+        assert np.max(np.abs(gx[b:e] - st.cx[b:e])) < 2e-5 * vth
+        assert np.max(np.abs(gz[b:e] - st.cz[b:e])) < 2e-5 * vth
+
+
+@pytest.mark.parametrize("wt,mb", [(0, 2), (0, 3), (0, 4), (1, 2), (1, 3), (1, 4)])
+def test_fpm_every_particle_pass_variant(wt, mb):
+    """Both particle-pass designs at each register budget, FP64 form, four
+    steps, against one oracle run."""
+    w = _ragged(35, 30, 2, 6000, 4, small=False)
+    ctx, st, sp, _ = _run(w, 4, usp.USP_FP64)
+    usp.usp_set_variant(ctx, wt, mb)
+    usp.usp_step(ctx, 4)
+    gm = usp.usp_moments(ctx)
+    gl = usp.usp_get_particles(ctx)[4]
+    fl, _ = usp.usp_status(ctx)
+    assert fl & usp.ERROR_FLAGS == 0
+    _check_moments(O.moments(sp, w.offsets, st), gm, sp)
+    assert np.mean(gl != st.lev) < 1e-5
+
+
+def test_fpm_conservation_on_gpu_fp64():
+    """Sec. 4.C with the FPM method on the GPU: per-cell momentum and total
+    energy conserved to FP64 rounding over ten steps."""
+    w = _ragged(37, 12, 200, 5000, 10, small=False)
+    p = w.particles
+    ctx = usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, _gpu_dt(w), p.cx, p.cy, p.cz,
+                                   p.erot, p.lev, precision=usp.USP_FP64, seed=3,
+                                   method=usp.USP_METHOD_FPM)
+    sp = O.species(**w.species)
+    Rth = O.R(sp) * sp.theta_v
+    def totals(cx, cy, cz, er, lv):
+        out = []
+        for i in range(w.n_cells):
+            b, e = w.offsets[i], w.offsets[i + 1]
+            out.append((np.array([cx[b:e].sum(), cy[b:e].sum(), cz[b:e].sum()]),
+                        (0.5 * (cx[b:e] ** 2 + cy[b:e] ** 2 + cz[b:e] ** 2) + er[b:e]
+                         + Rth * lv[b:e]).sum(),
+                        np.sqrt((cx[b:e] ** 2).sum())))
+        return out
+    t0 = totals(p.cx, p.cy, p.cz, p.erot, p.lev)
+    usp.usp_step(ctx, 10)
+    t1 = totals(*usp.usp_get_particles(ctx))
+    for (m0, e0, v0), (m1, e1, _) in zip(t0, t1):
+        assert np.max(np.abs(m1 - m0)) <= 1e-11 * v0
+        assert e1 == pytest.approx(e0, rel=1e-12)
