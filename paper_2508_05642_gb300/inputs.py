@@ -20,6 +20,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass, field
 
+import math
+
 import numpy as np
 
 KB = 1.380649e-23            # Boltzmann constant [J/K]
@@ -77,6 +79,75 @@ def equilibrium_particles(rng: np.random.Generator, N: int, m: float, theta_v: f
     else:
         lev = np.zeros(N, dtype=np.int32)
     return Particles(cx, cy, cz, erot, lev)
+
+
+def grad17_particles(rng: np.random.Generator, N: int, m: float, theta_v: float, T_eq: float,
+                     sigma_frac: float = 0.1, q_frac: float = 0.1) -> Particles:
+    """N particles from Grad's 17-moment distribution at T_eq (the initial state
+    of the homogeneous stress / heat-flux relaxation, Sec. 5.A.1): the
+    equilibrium distribution (Maxwellian velocities, exponential rotational
+    energy, geometric levels) times
+      1 + sigma_ij (C_i C_j - C^2 delta_ij / 3) / (2 p R T)
+        + q_tr,i C_i (C^2 - 5 R T) / (5 p (R T)^2)
+        + q_rot,i C_i (eps_rot - R T) / (p (R T)^2)
+        + q_vib,i C_i (sinh(x/2)/(x/2))^2 (eps_vib - e_vib(T)) / (p (R T)^2),
+    x = Theta/T, p = rho R T.  Reading of the printed sigma_ij(0) = 0.1 rho R T
+    (a viscous stress is traceless): the three off-diagonal components are
+    sigma_frac rho R T and the diagonal ones 0; every component of the three
+    heat fluxes is q_frac rho (R T)^1.5.  Sampled by acceptance from the
+    equilibrium distribution with probability w / max(w) over each batch, the
+    weight w clamped at 0 in the far tails (so the moments come out within a
+    fraction of a per cent of the targets; the measured initial values are the
+    reference of the relaxation)."""
+    R = KB / m
+    RT = R * T_eq
+    s = math.sqrt(RT)
+    x = theta_v / T_eq
+    qv = math.exp(-x)
+    ev_eq = R * theta_v * qv / (1.0 - qv)
+    sh2 = (math.sinh(0.5 * x) / (0.5 * x)) ** 2
+    sig = sigma_frac * RT          # per unit mass, off-diagonal
+    qh = q_frac * RT ** 1.5        # per unit mass, every component
+    out = []
+    got = 0
+    while got < N:
+        B = max(4096, int(1.4 * (N - got)))
+        c = s * rng.standard_normal((B, 3))
+        er = rng.exponential(RT, B)
+        lev = (rng.geometric(1.0 - qv, B) - 1).astype(np.int32)
+        ev = R * theta_v * lev
+        C2 = (c * c).sum(axis=1)
+        csum = c.sum(axis=1)
+        w = (1.0
+             + sig / (RT * RT) * (c[:, 0] * c[:, 1] + c[:, 0] * c[:, 2] + c[:, 1] * c[:, 2])
+             + qh / (5.0 * RT ** 3) * csum * (C2 - 5.0 * RT)
+             + qh / RT ** 3 * csum * (er - RT)
+             + qh / RT ** 3 * csum * sh2 * (ev - ev_eq))
+        w = np.maximum(w, 0.0)
+        acc = rng.uniform(0.0, w.max(), B) < w
+        take = np.flatnonzero(acc)[:N - got]
+        out.append((c[take], er[take], lev[take]))
+        got += len(take)
+    c = np.concatenate([o[0] for o in out])
+    er = np.concatenate([o[1] for o in out])
+    lev = np.concatenate([o[2] for o in out])
+    return Particles(c[:, 0].copy(), c[:, 1].copy(), c[:, 2].copy(), er, lev)
+
+
+def stress_heat_flux_relaxation(seed: int = 1, N: int = 10_000_000, dt_over_tau_c: float = 0.5,
+                                t_end_over_tau_c: float = 8.0) -> Workload:
+    """The homogeneous relaxation of viscous stress and heat flux of Sec. 5.A.1:
+    one cell of N2 (VSS), n = 1e24 m^-3, T_tr = T_rot = T_vib = 4000 K,
+    Z_rot = 10, Z_vib = 50, Grad-17 initial state with sigma(0) = 0.1 rho R T
+    and q(0) = 0.1 rho (R T)^1.5, 1e7 particles; steps to t_end."""
+    sp = n2_vss_species(Z_rot=10.0, Z_vib=50.0)
+    rng = np.random.default_rng([seed, 0x6A17])
+    T = 4000.0
+    p = grad17_particles(rng, N, sp["m"], sp["theta_v"], T)
+    steps = int(round(t_end_over_tau_c / dt_over_tau_c))
+    return Workload("homogeneous stress / heat-flux relaxation, 1 cell x %d particles, Grad-17"
+                    % N, sp, np.array([0, N], dtype=np.int64), np.array([1e24]),
+                    np.array([[T, T, T]]), dt_over_tau_c, p, seed, steps)
 
 
 @dataclass
