@@ -280,7 +280,15 @@ int usp_plane_get_particles(usp_ctx* ctx, int64_t cap, int64_t* n, double* h_x, 
 
 /* Time averages of a spatial context (channel or plane), as
  * usp_channel_sample / usp_channel_read; for a plane context the layout is
- * n_cells * 12 + 2 doubles, the last two the sampled-step count and 0. */
+ * n_cells * 12 + 2 + 4 * USP_NSURF doubles: the per-cell sums, the
+ * sampled-step count, 0, then the surface tallies of the cylinder (Sec. 5.C,
+ * surface coefficients C_f, C_h, drag, heat flux): USP_NSURF bins of the
+ * polar angle phi = atan2(y - yc, x - xc) in [-pi, pi), 4 sums each over the
+ * wall events of the sampled steps, per unit particle mass: the momentum
+ * given to the wall (c_in - c_out, x then y), the energy given to it
+ * (1/2 |c|^2 + eps_rot + R Theta I, in minus out) and the event count.
+ * Multiply by F_num m / (sampled steps dt) for forces and powers. */
+#define USP_NSURF 180
 int usp_sample(usp_ctx* ctx, int on);
 int usp_sample_read(usp_ctx* ctx, double* h_acc, int reset);
 

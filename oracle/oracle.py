@@ -107,6 +107,7 @@ class Channel(C.Structure):
 
 NACC = 12
 NFIELD = 13
+NSURF = 180   # cylinder surface bins of the plane accumulator (ORC_NSURF)
 
 BC_OPEN, BC_SPECULAR, BC_DIFFUSE = 0, 1, 2
 
@@ -501,6 +502,13 @@ class PlaneState:
                 self.lev[:n], self.pid[:n])
 
 
+def plane_acc(pl: "Plane") -> np.ndarray:
+    """A zeroed time-average accumulator of the plane: per-cell sums
+    (NACC each), the sampled-step count, 0, then NSURF cylinder surface bins
+    of 4 sums (momentum to the wall x, y; energy to the wall; events)."""
+    return np.zeros(pl.nx * pl.ny * NACC + 2 + 4 * NSURF)
+
+
 def plane_step(sp, form, seed, step0, nsteps, pl: Plane, area_frac, dt, st: PlaneState, acc=None):
     """Advance the plane domain ``nsteps`` steps in place (live particles end
     sorted by cell).  Returns (cell offsets, flags, counters)."""
@@ -513,6 +521,8 @@ def plane_step(sp, form, seed, step0, nsteps, pl: Plane, area_frac, dt, st: Plan
     npid = C.c_uint32(st.next_pid)
     fl = C.c_uint32(0)
     cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+    if acc is not None and acc.size < ncell * NACC + 2 + 4 * NSURF:
+        raise ValueError("plane accumulator too small: use plane_acc()")
     accp = _p(acc, C.c_double) if acc is not None else None
     rc = lib().orc_plane_step(C.byref(sp), form, C.c_uint64(seed), step0, nsteps, C.byref(pl),
                               _p(af, C.c_double), dt, C.byref(n), st.cap, _p(st.x, C.c_double),

@@ -1387,7 +1387,7 @@ double orc_inflow_normal_speed(double RT, double u_n, uint32_t pid, uint32_t ste
 static int advect_plane(const orc_species* sp, int form, uint64_t seed, uint32_t step,
                         const orc_plane* pl, double t_left, double* x, double* y, double* cx,
                         double* cy, double* cz, double* erot, int32_t* lev, uint32_t pid,
-                        uint32_t* flags, int64_t* counters)
+                        double* surf, uint32_t* flags, int64_t* counters)
 {
     double R = orc_R(sp);
     int hits = 0;
@@ -1454,6 +1454,9 @@ static int advect_plane(const orc_species* sp, int form, uint64_t seed, uint32_t
         } else {
             /* diffuse at T_wall: speed along the normal, one tangential
              * component in the plane, one along z */
+            double in_x = *cx, in_y = *cy;
+            double in_e = 0.5 * (*cx * *cx + *cy * *cy + *cz * *cz) + *erot
+                        + R * sp->theta_v * (double)*lev;
             uint32_t w[4], v[4];
             philox_words(pid, step, PTAG_WALL_A, (uint32_t)hits, seed, w);
             philox_words(pid, step, PTAG_WALL_B, (uint32_t)hits, seed, v);
@@ -1468,6 +1471,19 @@ static int advect_plane(const orc_species* sp, int form, uint64_t seed, uint32_t
             *cz = st * g2;
             *erot = -R * Tw * log(orc_uniform(w[3], form));
             *lev = (int32_t)floor(-log(orc_uniform(v[0], form)) * Tw / sp->theta_v);
+            if (surf && ev == 0) {
+                /* surface tally of this wall event (bin of the polar angle) */
+                double phi = atan2(*y - pl->cyl_yc, *x - pl->cyl_xc);
+                int b = (int)floor((phi + PI) / (2.0 * PI) * ORC_NSURF);
+                if (b < 0) b = 0;
+                if (b > ORC_NSURF - 1) b = ORC_NSURF - 1;
+                double out_e = 0.5 * (*cx * *cx + *cy * *cy + *cz * *cz) + *erot
+                             + R * sp->theta_v * (double)*lev;
+                surf[4 * b + 0] += in_x - *cx;
+                surf[4 * b + 1] += in_y - *cy;
+                surf[4 * b + 2] += in_e - out_e;
+                surf[4 * b + 3] += 1.0;
+            }
         }
         hits += 1;
         counters[ORC_C_WALL_HITS] += 1;
@@ -1539,13 +1555,14 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
     int status = 0;
     int64_t n = *n_io;
     double RTi = R * pl->T_inf;
+    double* surf = acc ? acc + (size_t)ncell * ORC_NACC + 2 : NULL;
     for (int s = 0; s < nsteps; ++s) {
         uint32_t step = (uint32_t)(step0 + s);
         /* 1. move; drop what left through open sides (order kept) */
         int64_t m = 0;
         for (int64_t j = 0; j < n; ++j) {
             int keep = advect_plane(sp, form, seed, step, pl, dt, &x[j], &y[j], &cx[j], &cy[j],
-                                    &cz[j], &erot[j], &lev[j], pid[j], flags, counters);
+                                    &cz[j], &erot[j], &lev[j], pid[j], surf, flags, counters);
             if (!keep) continue;
             x[m] = x[j]; y[m] = y[j]; cx[m] = cx[j]; cy[m] = cy[j]; cz[m] = cz[j];
             erot[m] = erot[j]; lev[m] = lev[j]; pid[m] = pid[j];
@@ -1596,7 +1613,7 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
                     int32_t l = (int32_t)floor(-log(orc_uniform(a[3], form)) * pl->T_inf / sp->theta_v);
                     /* enters at a uniformly distributed time of the step */
                     int keep = advect_plane(sp, form, seed, step, pl, u_t * dt, &px, &py, &vx, &vy,
-                                            &vz, &e, &l, id, flags, counters);
+                                            &vz, &e, &l, id, surf, flags, counters);
                     if (!keep) continue;
                     if (n >= cap) { *flags |= ORC_F_CAPACITY; continue; }
                     x[n] = px; y[n] = py; cx[n] = vx; cy[n] = vy; cz[n] = vz; erot[n] = e;

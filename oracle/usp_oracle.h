@@ -214,7 +214,14 @@ typedef struct {
  * are updated; on return the live particles are sorted by cell (cell j*nx+i)
  * with segment starts cell_off[ncell + 1].  area_frac[cell] is the fluid
  * fraction of each cell (volume = area_frac dx dy depth).  Accumulator layout
- * as ORC_NACC above, plus slot [ncell * ORC_NACC] = sampled steps. */
+ * as ORC_NACC above, plus slot [ncell * ORC_NACC] = sampled steps, slot
+ * [ncell * ORC_NACC + 1] = 0, then the surface tallies of the cylinder
+ * (Sec. 5.C, surface coefficients): ORC_NSURF bins of the polar angle
+ * phi = atan2(y - yc, x - xc) in [-pi, pi), 4 sums each over the wall events
+ * of the sampled steps, per unit particle mass: the momentum given to the
+ * wall (c_in - c_out, x and y) and the energy given to it
+ * (1/2 |c|^2 + eps_rot + R Theta I, in minus out), and the event count. */
+#define ORC_NSURF 180
 int    orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0, int nsteps,
                       const orc_plane* pl, const double* area_frac, double dt,
                       int64_t* n, int64_t cap, double* x, double* y, double* cx, double* cy,

@@ -46,6 +46,7 @@ constexpr uint32_t PTAG_INFLOW_P = 5u, PTAG_INFLOW_T = 6u, PTAG_INFLOW_V = 7u;
 constexpr uint32_t CTAG_INFLOW = 0x80000004u;
 constexpr int kInflowTries = 64;
 constexpr int kBlk = 256;
+constexpr int kNSurf = USP_NSURF;   // cylinder surface bins of the polar angle
 constexpr int kParamBlock = 32;   // cells per block of the stencil pass
 
 // Device-resident counts of the current step.
@@ -135,7 +136,7 @@ __device__ void plane_emit(const Species& sp, double Tw, double nx, double ny, u
 template <typename T>
 __device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint32_t step,
                           uint32_t k0, uint32_t k1, T t_left, T& x, T& y, T& vx, T& vy, T& vz,
-                          T& e, int& l, int& hits, uint32_t& fl) {
+                          T& e, int& l, int& hits, uint32_t& fl, double* surf) {
   for (;;) {
     int ev = -1;
     T te = t_left;
@@ -205,7 +206,21 @@ __device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint
       vx -= T(2) * vn * nx;
       vy -= T(2) * vn * ny;
     } else {
+      const T Rth = (T)(gasR(sp) * sp.theta_v);
+      const T in_x = vx, in_y = vy;
+      const T in_e = T(0.5) * (vx * vx + vy * vy + vz * vz) + e + Rth * (T)l;
       plane_emit<T>(sp, g.Tw, (double)nx, (double)ny, pid, step, hits, k0, k1, vx, vy, vz, e, l);
+      if (surf && ev == 0) {
+        // surface tally of this wall event (bin of the polar angle)
+        const double phi = atan2((double)(y - (T)g.cyc), (double)(x - (T)g.cxc));
+        int b = (int)floor((phi + kPi) / (2.0 * kPi) * kNSurf);
+        b = b < 0 ? 0 : (b > kNSurf - 1 ? kNSurf - 1 : b);
+        const T out_e = T(0.5) * (vx * vx + vy * vy + vz * vz) + e + Rth * (T)l;
+        atomicAdd(&surf[4 * b + 0], (double)(in_x - vx));
+        atomicAdd(&surf[4 * b + 1], (double)(in_y - vy));
+        atomicAdd(&surf[4 * b + 2], (double)(in_e - out_e));
+        atomicAdd(&surf[4 * b + 3], 1.0);
+      }
     }
     hits += 1;
   }
@@ -220,7 +235,8 @@ __global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, const PlCount* __
                           int* __restrict__ lev, const uint32_t* __restrict__ pid,
                           int* __restrict__ keyout, int* __restrict__ idxout,
                           const long long* __restrict__ dstep, Species sp, uint32_t k0,
-                          uint32_t k1, uint32_t* flags, unsigned long long* counters) {
+                          uint32_t k1, uint32_t* flags, unsigned long long* counters,
+                          double* surf) {
   __shared__ BlockTally tal;
   tally_init(tal);
   const long long n = cnt->n;
@@ -249,7 +265,7 @@ __global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, const PlCount* __
     T px = x[j], py = y[j];
     int hits = 0;
     const bool keep = plane_fly<T>(g, sp, pid[j], step, k0, k1, (T)g.dt, px, py, vx, vy, vz, e,
-                                   l, hits, fl);
+                                   l, hits, fl, surf);
     nhit += hits;
     nout += keep ? 0 : 1;
     x[j] = px; y[j] = py; cx[j] = vx; cy[j] = vy; cz[j] = vz; er[j] = e; lev[j] = l;
@@ -395,7 +411,8 @@ __global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, PlInflow f, const
                           T* __restrict__ er, int* __restrict__ lev, uint32_t* __restrict__ pid,
                           int* __restrict__ keyout, int* __restrict__ idxout,
                           const long long* __restrict__ dstep, Species sp, uint32_t k0,
-                          uint32_t k1, uint32_t* flags, unsigned long long* counters) {
+                          uint32_t k1, uint32_t* flags, unsigned long long* counters,
+                          double* surf) {
   __shared__ BlockTally tal;
   tally_init(tal);
   const long long ninj = cnt->ninj;
@@ -442,7 +459,7 @@ __global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, PlInflow f, const
     T X = (T)px, Y = (T)py, VX = (T)vx, VY = (T)vy, VZ = (T)vz, E = (T)e;
     int L = l0, hits = 0;
     const bool keep = plane_fly<T>(g, sp, id, step, k0, k1, (T)(u_t * g.dt), X, Y, VX, VY, VZ,
-                                   E, L, hits, fl);
+                                   E, L, hits, fl, surf);
     nhit += hits;
     nout += keep ? 0 : 1;
     const long long j = n + m;
@@ -1074,16 +1091,18 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   T* cy = (T*)h->st[a][3]; T* cz = (T*)h->st[a][4]; T* er = (T*)h->st[a][5];
   const int ncell = h->g.ncell;
   if (prof) prof(env.owner, 0, 1);
+  // surface tallies of the cylinder while sampling
+  double* surf = h->sampling ? h->acc + (size_t)ncell * kNAcc + 2 : nullptr;
   pl_advect<T><<<h->grid_p, kBlk, 0, s>>>(h->g, h->cnt, h->keycell, h->cells, h->pend, x, y, cx,
                                          cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0], h->ibuf[0],
                                          h->dstep, env.sp, env.k0, env.k1, env.flags,
-                                         env.counters);
+                                         env.counters, surf);
   pl_inflow<<<1, 1024, 0, s>>>(h->inf, h->cnt, h->face_off, h->cap, h->dstep, env.k0, env.k1,
                                env.flags, env.counters);
   if (h->inf.nfaces > 0)
     pl_inject<T><<<h->grid_inj, kBlk, 0, s>>>(
         h->g, h->inf, h->cnt, h->face_off, x, y, cx, cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0],
-        h->ibuf[0], h->dstep, env.sp, env.k0, env.k1, env.flags, env.counters);
+        h->ibuf[0], h->dstep, env.sp, env.k0, env.k1, env.flags, env.counters, surf);
   CHK(cudaGetLastError());
   int src = 0;
   for (int p = 0; p < h->passes; ++p) {
@@ -1265,7 +1284,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->prm = A((env.precision == USP_FP32 ? sizeof(PlParams<float>) : sizeof(PlParams<double>)) *
              ncell);
   h->sums = (ChSumsT<double>*)A(sizeof(ChSumsT<double>) * ncell);
-  const size_t acc_bytes = sizeof(double) * ((size_t)ncell * kNAcc + 2);
+  const size_t acc_bytes = sizeof(double) * ((size_t)ncell * kNAcc + 2 + 4 * kNSurf);
   h->acc = (double*)A(acc_bytes);
   h->macc = (double*)A(sizeof(double) * 21 * ncell);
   h->mout = (double*)A(sizeof(double) * USP_NMOM * ncell);
@@ -1356,7 +1375,7 @@ int pl_sample(PlaneCtx* h, int on) {
 }
 
 int pl_read(PlaneCtx* h, const ChEnv& env, double* h_acc, int reset) {
-  const size_t bytes = sizeof(double) * ((size_t)h->g.ncell * kNAcc + 2);
+  const size_t bytes = sizeof(double) * ((size_t)h->g.ncell * kNAcc + 2 + 4 * kNSurf);
   CHK(cudaMemcpyAsync(h_acc, h->acc, bytes, cudaMemcpyDeviceToHost, env.stream));
   if (reset) CHK(cudaMemsetAsync(h->acc, 0, bytes, env.stream));
   CHK(cudaStreamSynchronize(env.stream));

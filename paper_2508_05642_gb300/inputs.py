@@ -364,3 +364,30 @@ def cylinder_flow(seed: int = 1, nx: int = 600, ny: int = 400, ppc: float = 30.0
     name = ("Mach-10 N2 past a cylinder, %dx%d cells, %.0f particles/cell" % (nx, ny, ppc)
             if cylinder else "uniform N2 stream, %dx%d cells" % (nx, ny))
     return PlaneWorkload(name, sp, pl, af, dt_over_tau_c, x, y, p, cap, seed, steps)
+
+
+def cylinder_paper(seed: int = 1, ppc: float = 30.0, dt: float = 1.6e-7,
+                   capacity_factor: float = 2.0) -> PlaneWorkload:
+    """The cylinder case of Sec. 5.C with the paper's parameters on a uniform
+    grid: freestream n = 2.124e21 m^-3, 200 K, 2883 m/s (Mach 10), radius
+    0.1524 m, wall at 500 K, 0.8 m x 0.6 m half domain, cells of the paper's
+    coarse Level 1 grid (1.25 mm: 640 x 480), its coarse time step 1.6e-7 s.
+    Readings: the three-level refinement around the body is replaced by that
+    uniform grid with cut cells, the domain spans x in [-0.4, 0.4], y in
+    [0, 0.6] with the cylinder centred on the origin, and ``ppc`` particles
+    per free cell (the paper: 100)."""
+    sp = n2_vhs_cylinder_species()
+    n_inf, T_inf = 2.124e21, 200.0
+    # mean collision time of the freestream (VHS, Eq. tau_c), to express dt
+    ca, w = sp["c_alpha"], sp["omega"]
+    mu_ref = (5.0 * (ca + 1.0) * (ca + 2.0) * math.sqrt(sp["m"] * KB * sp["T_ref"] / math.pi)
+              / (4.0 * ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) * sp["d_ref"] ** 2))
+    mu = mu_ref * (T_inf / sp["T_ref"]) ** w
+    tau_c = ca * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (ca + 1.0) * (ca + 2.0)) \
+        * mu / (n_inf * KB * T_inf)
+    wl = cylinder_flow(seed=seed, nx=640, ny=480, ppc=ppc, x0=-0.4, x1=0.4, y0=0.0, y1=0.6,
+                       r=0.1524, T_wall=500.0, n_inf=n_inf, T_inf=T_inf, U_inf=2883.0,
+                       dt_over_tau_c=dt / tau_c, capacity_factor=capacity_factor)
+    wl.name = ("Mach-10 N2 past a 0.1524 m cylinder (Sec. 5.C parameters), 640x480 cells, "
+               "%.0f particles/cell, dt = %.3g s" % (ppc, dt))
+    return wl

@@ -44,6 +44,7 @@ EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogene
             "usp_channel_read", "usp_channel_get_particles", "usp_init_plane", "usp_plane_count",
             "usp_plane_get_particles", "usp_sample", "usp_sample_read", "usp_destroy"]
 USP_METHOD_USP_FPM, USP_METHOD_FPM = 0, 1
+USP_NSURF = 180
 USP_NOALLOC_MAX_CELLS = 8192
 
 
@@ -189,12 +190,13 @@ def usp_tau_c(species: dict, n: float, T: float) -> float:
 class Context:
     """Owns one ``usp_ctx``; methods map 1:1 onto the C entry points."""
 
-    def __init__(self, handle, n_particles, n_cells, precision, keepalive):
+    def __init__(self, handle, n_particles, n_cells, precision, keepalive, kind=0):
         self.h = handle
         self.n_particles = n_particles
         self.n_cells = n_cells
         self.precision = precision
         self._keep = keepalive
+        self.kind = kind          # 0 homogeneous, 1 channel, 2 plane
 
     def __del__(self):
         self.destroy()
@@ -273,7 +275,7 @@ def usp_init_channel(species: dict, channel: dict, dt: float, y, cx, cy, cz, ero
                                 _p(y, C.c_double), _p(cx, C.c_double), _p(cy, C.c_double),
                                 _p(cz, C.c_double), _p(erot, C.c_double), _p(lev, C.c_int32), pidp)
     _check(rc, "usp_init_channel")
-    return Context(h, n, int(channel["ny"]), precision, keep)
+    return Context(h, n, int(channel["ny"]), precision, keep, kind=1)
 
 
 def usp_channel_sample(ctx: Context, on: bool = True):
@@ -339,7 +341,7 @@ def usp_init_plane(species: dict, plane: dict, dt: float, area_frac, x, y, cx, c
                               _p(y, C.c_double), _p(cx, C.c_double), _p(cy, C.c_double),
                               _p(cz, C.c_double), _p(erot, C.c_double), _p(lev, C.c_int32), pidp)
     _check(rc, "usp_init_plane")
-    ctx = Context(h, n, int(plane["nx"]) * int(plane["ny"]), precision, keep)
+    ctx = Context(h, n, int(plane["nx"]) * int(plane["ny"]), precision, keep, kind=2)
     ctx.capacity = int(capacity)
     return ctx
 
@@ -372,9 +374,10 @@ def usp_sample(ctx: Context, on: bool = True):
 
 def usp_sample_read(ctx: Context, reset: bool = False) -> np.ndarray:
     """Per-cell time-average sums of a channel or plane context (n_cells * 12
-    + 2 doubles)."""
+    + 2 doubles; a plane context appends USP_NSURF x 4 cylinder surface sums)."""
     blocks = 4 if ctx.precision == USP_FP64_TANGENT else 1
-    out = np.zeros((ctx.n_cells * 12 + 2) * blocks)
+    extra = 4 * USP_NSURF if ctx.kind == 2 else 0
+    out = np.zeros((ctx.n_cells * 12 + 2) * blocks + extra)
     _check(lib().usp_sample_read(ctx.h, _p(out, C.c_double), 1 if reset else 0),
            "usp_sample_read")
     return out

@@ -38,7 +38,7 @@ def _pair(w, steps, precision, sample_last=0, use_graph=True, seed=None):
     ctx = usp.usp_init_plane(w.species, w.plane, dtg, w.area_frac, x, y, cx, cy, cz, er, lev,
                              w.capacity, precision=precision, seed=seed, use_graph=use_graph)
     ncell = pl.nx * pl.ny
-    acc = np.zeros(ncell * O.NACC + 2)
+    acc = O.plane_acc(pl)
     cnt = np.zeros(O.NCOUNTERS, dtype=np.int64)
     if steps - sample_last > 0:
         _, f1, c1 = O.plane_step(sp, form, seed, 0, steps - sample_last, pl, w.area_frac, dto, st)
@@ -75,6 +75,13 @@ def test_fp64_plane_matches_oracle_step_by_step():
         assert np.max(np.abs(a - b[:st.n])) < 1e-7 * vth
     assert np.max(np.abs(ge - st.erot[:st.n])) < 1e-7 * R * 200.0
     np.testing.assert_allclose(r["gacc"], r["acc"], rtol=1e-7, atol=1e-3)
+    # cylinder surface tallies (momentum and energy to the wall per angle bin)
+    ncell = r["pl"].nx * r["pl"].ny
+    gs = r["gacc"][ncell * 12 + 2:].reshape(-1, 4)
+    osf = r["acc"][ncell * 12 + 2:].reshape(-1, 4)
+    assert len(gs) == usp.USP_NSURF and osf[:, 3].sum() > 100
+    assert np.array_equal(gs[:, 3], osf[:, 3])
+    np.testing.assert_allclose(gs[:, :3], osf[:, :3], rtol=1e-9, atol=1e-6)
     for k in (usp.C_INFLOW, usp.C_OUTFLOW, usp.C_WALL_HITS, usp.C_CHOL_FIX, usp.C_NU_ZERO):
         assert r["gcnt"][k] == r["cnt"][k], k
     assert r["gfl"] & usp.ERROR_FLAGS == 0
@@ -152,7 +159,7 @@ def test_fp32_plane_statistics_match_oracle():
     x, y, cx, cy, cz, er, lev = _state(w)
     st = O.PlaneState(x, y, cx, cy, cz, er, lev, w.capacity)
     O.plane_step(sp, 0, 21, 0, 80, pl, w.area_frac, dto, st)
-    acc = np.zeros(ncell * O.NACC + 2)
+    acc = O.plane_acc(pl)
     O.plane_step(sp, 0, 21, 80, 80, pl, w.area_frac, dto, st, acc)
     x, y, cx, cy, cz, er, lev = _state(w, True)
     ctx = usp.usp_init_plane(w.species, w.plane, dtg, w.area_frac, x, y, cx, cy, cz, er, lev,

@@ -274,3 +274,45 @@ def test_reconstructed_temperature_is_the_trace_of_reconstructed_stress():
         y = yc[j] + rng.uniform(-0.5, 0.5) * dy
         f = O.plane_reconstruct(pl, counts, af, F, cell, x, y)
         assert f[3] == pytest.approx((f[6] + f[7] + f[8]) / (3 * R), rel=1e-12)
+
+
+def test_surface_tallies_of_a_gas_at_rest_at_the_wall_temperature():
+    """Cylinder in a closed specular box of N2 at rest at T = T_wall: the
+    surface tallies give the ideal-gas pressure n k_B T on the wall (half from
+    the incoming, half from the re-emitted momentum flux), and no net shear
+    and no net heat flux (the re-emitted gas carries back what arrives).
+    About 3,000 wall events: bars of three standard deviations."""
+    T = 500.0
+    w = I.cylinder_flow(nx=24, ny=16, ppc=200, U_inf=0.0, T_inf=T)
+    w.plane["bc"] = (O.BC_SPECULAR,) * 4
+    w.plane["inflow"] = (0, 0, 0, 0)
+    sp = O.species(**w.species)
+    pl = O.plane(**w.plane)
+    dt = 1.0 * O.tau_c(sp, w.plane["n_inf"], T)
+    p = w.particles
+    st = O.PlaneState(w.x, w.y, p.cx, p.cy, p.cz, p.erot, p.lev, w.capacity)
+    acc = O.plane_acc(pl)
+    steps = 150
+    fl, _ = O.plane_step(sp, 0, 5, 0, steps, pl, w.area_frac, dt, st, acc)[1:]
+    assert fl & (O.F_A_NONPOS | O.F_CAPACITY) == 0
+    ncell = pl.nx * pl.ny
+    assert acc[ncell * O.NACC] == steps
+    s = acc[ncell * O.NACC + 2:].reshape(-1, 4)
+    nb = len(s)
+    phi = -math.pi + (np.arange(nb) + 0.5) * 2 * math.pi / nb
+    up = phi > 0.05
+    assert np.all(s[phi < -0.05, 3] == 0)          # no wall below the symmetry plane
+    assert s[:, 3].sum() > 2000
+    m = sp.m
+    area = w.plane["cyl_r"] * (2 * math.pi / nb) * w.plane["depth"]
+    fx = w.plane["F_num"] * m * s[:, 0] / (steps * dt)
+    fy = w.plane["F_num"] * m * s[:, 1] / (steps * dt)
+    press = -(fx * np.cos(phi) + fy * np.sin(phi)) / area
+    shear = (fx * np.sin(phi) - fy * np.cos(phi)) / area
+    p_ideal = w.plane["n_inf"] * KB * T
+    assert np.mean(press[up]) == pytest.approx(p_ideal, rel=0.06)
+    assert abs(np.mean(shear[up])) < 0.06 * p_ideal
+    # heat flux: energy in minus out, against the one-way energy flux scale
+    q = w.plane["F_num"] * m * s[:, 2] / (steps * dt) / area
+    one_way = p_ideal * math.sqrt(8 * O.R(sp) * T / math.pi)
+    assert abs(np.mean(q[up])) < 0.08 * one_way
