@@ -205,7 +205,7 @@ __device__ __forceinline__ int b_tab(const float* __restrict__ T, const float4& 
 // ---------------------------------------------------------------------------
 // One particle: pending rescale, velocity, rotation, vibration.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int METHOD>
 __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t pid,
                                             const PhiloxRoundKeys& rk, T& cx, T& cy, T& cz, T& er,
                                             int& lv,
@@ -217,7 +217,7 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   const float* rnb = tnb;
   const float* rb = tb;
   float4 t_nb = make_float4(0.f, 0.f, 0.f, 0.f), t_b = t_nb;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4 && METHOD == 0) {
     rnb += (size_t)(I < kJR ? I : 0) * kJK;
     rb += (size_t)(I < kJR ? I : 0) * kJK;
     t_nb = __ldg(reinterpret_cast<const float4*>(rnb));
@@ -241,7 +241,7 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   er = P.a_rot + root * root;
   // I' = I + NB(I + 1, p_NB) - B(I, p_B)
   const T u5 = uniform_open<T>(w2.x), u6 = uniform_open<T>(w2.y);
-  if (P.method == 1) {
+  if constexpr (METHOD == 1) {
     // plain FPM method: Gillespie's direct method (Sec. 2.C)
     lv = gillespie<T>(I, P.p_nb, P.p_b, pid, P.step, rk, fl);
   } else {
@@ -448,7 +448,7 @@ __device__ __forceinline__ void flush_sums_warp(const T* acc, int accI, int maxI
   if (lane == 11 && mI > 0) atomicMax(&dst->maxI, mI);
 }
 
-template <typename T, int MINB>
+template <typename T, int MINB, int METHOD>
 __global__ void __launch_bounds__(kBlock, MINB)
 collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
                     const CollideParams<T>* __restrict__ prm, T* __restrict__ cx,
@@ -521,7 +521,8 @@ collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
         T x = X[k], y = X[k + kWT], z = X[k + 2 * kWT], e = X[k + 3 * kWT];
         int l = Lv[k];
         uint32_t f1 = 0;
-        collide_one<T>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb, tb);
+        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb,
+                               tb);
         X[k] = x; X[k + kWT] = y; X[k + 2 * kWT] = z; X[k + 3 * kWT] = e;
         Lv[k] = l;
         npb += (f1 & F_PB_CLAMP) ? 1 : 0;
@@ -630,7 +631,7 @@ __device__ __forceinline__ void stage_load_p(const Tile& tl, const CollideParams
   }
 }
 
-template <typename T, int MINB>
+template <typename T, int MINB, int METHOD>
 __global__ void __launch_bounds__(kBlock, MINB)
 collide_kernel(const Tile* __restrict__ tiles, int ntiles,
                const CollideParams<T>* __restrict__ prm, T* __restrict__ cx,
@@ -708,7 +709,8 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
         T x = X[k], y = X[k + kTileMax], z = X[k + 2 * kTileMax], e = X[k + 3 * kTileMax];
         int l = Lv[k];
         uint32_t f1 = 0;
-        collide_one<T>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb, tb);
+        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb,
+                               tb);
         X[k] = x; X[k + kTileMax] = y; X[k + 2 * kTileMax] = z; X[k + 3 * kTileMax] = e;
         Lv[k] = l;
         npb += (f1 & F_PB_CLAMP) ? 1 : 0;
@@ -1483,15 +1485,23 @@ int prof_cb(void* owner, int kind, int begin) {
   return prof_end(c, c->prof_pending);
 }
 
-template <typename T, int MINB>
+template <typename T, int MINB, int METHOD>
 void* collide_fn(int warp_tiles) {
-  return warp_tiles ? (void*)collide_warp_kernel<T, MINB> : (void*)collide_kernel<T, MINB>;
+  return warp_tiles ? (void*)collide_warp_kernel<T, MINB, METHOD>
+                    : (void*)collide_kernel<T, MINB, METHOD>;
+}
+
+template <typename T, int METHOD>
+void* collide_variant_m(int warp_tiles, int minb) {
+  return minb == 2 ? collide_fn<T, 2, METHOD>(warp_tiles)
+                   : minb == 3 ? collide_fn<T, 3, METHOD>(warp_tiles)
+                               : collide_fn<T, 4, METHOD>(warp_tiles);
 }
 
 template <typename T>
-void* collide_variant(int warp_tiles, int minb) {
-  return minb == 2 ? collide_fn<T, 2>(warp_tiles)
-                   : minb == 3 ? collide_fn<T, 3>(warp_tiles) : collide_fn<T, 4>(warp_tiles);
+void* collide_variant(int warp_tiles, int minb, int method) {
+  return method == 1 ? collide_variant_m<T, 1>(warp_tiles, minb)
+                     : collide_variant_m<T, 0>(warp_tiles, minb);
 }
 
 template <typename T>
@@ -1510,12 +1520,13 @@ CellRange cell_range(const usp_ctx* c, int c0, int c1) {
 }
 CellRange all_cells(const usp_ctx* c) { return cell_range(c, 0, c->ncell); }
 
-// Launch the particle pass (design warp_tiles, register-budget variant minb)
-// over the tiles of the cell range r, on the given state / sums buffers.
-template <typename T>
-int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, void* cy, void* cz,
-                   void* er, int* lev, CellSums* sums, uint32_t* flags,
-                   unsigned long long* counters, const CellRange& r) {
+// Launch the particle pass (design warp_tiles, register-budget variant minb,
+// the context's particle method) over the tiles of the cell range r, on the
+// given state / sums buffers.
+template <typename T, int METHOD>
+int launch_collide_m(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, void* cy,
+                     void* cz, void* er, int* lev, CellSums* sums, uint32_t* flags,
+                     unsigned long long* counters, const CellRange& r) {
   const size_t smem = collide_smem<T>(warp_tiles);
   const CollideParams<T>* prm = (const CollideParams<T>*)c->prm;
   T* x = (T*)cx; T* y = (T*)cy; T* z = (T*)cz; T* e = (T*)er;
@@ -1526,13 +1537,13 @@ int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, voi
     const Tile* tiles = c->wtiles + r.w0;
     const int ntiles = r.w1 - r.w0;
     if (minb == 2)
-      collide_warp_kernel<T, 2><<<grid, kBlock, smem, c->stream>>>(
+      collide_warp_kernel<T, 2, METHOD><<<grid, kBlock, smem, c->stream>>>(
           tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
     else if (minb == 3)
-      collide_warp_kernel<T, 3><<<grid, kBlock, smem, c->stream>>>(
+      collide_warp_kernel<T, 3, METHOD><<<grid, kBlock, smem, c->stream>>>(
           tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
     else
-      collide_warp_kernel<T, 4><<<grid, kBlock, smem, c->stream>>>(
+      collide_warp_kernel<T, 4, METHOD><<<grid, kBlock, smem, c->stream>>>(
           tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
     CK(cudaGetLastError());
     return USP_OK;
@@ -1540,16 +1551,26 @@ int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, voi
   const Tile* tiles = c->tiles + r.t0;
   const int ntiles = r.t1 - r.t0;
   if (minb == 2)
-    collide_kernel<T, 2><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
-                                                            sums, flags, counters, rk, tn, tb);
+    collide_kernel<T, 2, METHOD><<<grid, kBlock, smem, c->stream>>>(
+        tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
   else if (minb == 3)
-    collide_kernel<T, 3><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
-                                                            sums, flags, counters, rk, tn, tb);
+    collide_kernel<T, 3, METHOD><<<grid, kBlock, smem, c->stream>>>(
+        tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
   else
-    collide_kernel<T, 4><<<grid, kBlock, smem, c->stream>>>(tiles, ntiles, prm, x, y, z, e, lev,
-                                                            sums, flags, counters, rk, tn, tb);
+    collide_kernel<T, 4, METHOD><<<grid, kBlock, smem, c->stream>>>(
+        tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
   CK(cudaGetLastError());
   return USP_OK;
+}
+template <typename T>
+int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, void* cy, void* cz,
+                   void* er, int* lev, CellSums* sums, uint32_t* flags,
+                   unsigned long long* counters, const CellRange& r) {
+  return c->sp.method == 1
+             ? launch_collide_m<T, 1>(c, warp_tiles, minb, grid, cx, cy, cz, er, lev, sums, flags,
+                                      counters, r)
+             : launch_collide_m<T, 0>(c, warp_tiles, minb, grid, cx, cy, cz, er, lev, sums, flags,
+                                      counters, r);
 }
 
 // jump tables for the coming step (FP32 form only)
@@ -2010,7 +2031,8 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
     for (int wt = 0; wt < 2; ++wt) {
       const size_t smem = f32 ? collide_smem<float>(wt) : collide_smem<double>(wt);
       for (int mb = 2; mb <= 4; ++mb) {
-        void* fn = f32 ? collide_variant<float>(wt, mb) : collide_variant<double>(wt, mb);
+        void* fn = f32 ? collide_variant<float>(wt, mb, c->sp.method)
+                       : collide_variant<double>(wt, mb, c->sp.method);
         int per_sm = 1;
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
                 cudaSuccess ||
