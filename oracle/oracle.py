@@ -120,7 +120,8 @@ class Plane(C.Structure):
                 ("cyl_yc", C.c_double), ("cyl_r", C.c_double), ("T_wall", C.c_double),
                 ("n_inf", C.c_double), ("T_inf", C.c_double), ("U_inf", C.c_double),
                 ("bc", C.c_int * 4), ("inflow", C.c_int * 4), ("F_num", C.c_double),
-                ("depth", C.c_double), ("reconstruct", C.c_int)]
+                ("depth", C.c_double), ("reconstruct", C.c_int), ("amr_levels", C.c_int),
+                ("amr_r2", C.c_double), ("amr_r3", C.c_double)]
 
 
 def plane(**kw) -> Plane:
@@ -206,6 +207,10 @@ def lib():
             L.orc_inflow_normal_speed.argtypes = [C.c_double, C.c_double, C.c_uint32, C.c_uint32,
                                                   C.c_uint64, C.c_int, _U32]
             L.orc_inflow_normal_speed.restype = C.c_double
+            L.orc_plane_nleaf.argtypes = [C.POINTER(Plane)]
+            L.orc_plane_leaves.argtypes = [C.POINTER(Plane), C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+            L.orc_plane_leaf_of.argtypes = [C.POINTER(Plane), C.c_double, C.c_double]
             L.orc_fpm_coeffs.argtypes = [C.POINTER(Species)] + [C.c_double] * 5 + \
                 [C.POINTER(FpmCoeffs)]
             L.orc_gillespie.argtypes = [C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
@@ -502,17 +507,41 @@ class PlaneState:
                 self.lev[:n], self.pid[:n])
 
 
+def plane_nleaf(pl: "Plane") -> int:
+    """Number of cells (leaves) of the plane's grid, refined or not."""
+    return lib().orc_plane_nleaf(C.byref(pl))
+
+
+def plane_leaves(pl: "Plane"):
+    """(level, ii, jj) of every leaf: level 1..3 and integer coordinates at
+    its own level (centre x0 + (ii + 1/2) dx / 2^(level-1))."""
+    n = plane_nleaf(pl)
+    if n < 0:
+        raise ValueError("refined grid: neighbouring fluid cells differ by two levels")
+    lv = np.zeros(n, dtype=np.int32)
+    ii = np.zeros(n, dtype=np.int32)
+    jj = np.zeros(n, dtype=np.int32)
+    lib().orc_plane_leaves(C.byref(pl), _p(lv, C.c_int32), _p(ii, C.c_int32), _p(jj, C.c_int32))
+    return lv, ii, jj
+
+
+def plane_leaf_of(pl: "Plane", x: float, y: float) -> int:
+    return lib().orc_plane_leaf_of(C.byref(pl), float(x), float(y))
+
+
 def plane_acc(pl: "Plane") -> np.ndarray:
     """A zeroed time-average accumulator of the plane: per-cell sums
     (NACC each), the sampled-step count, 0, then NSURF cylinder surface bins
     of 4 sums (momentum to the wall x, y; energy to the wall; events)."""
-    return np.zeros(pl.nx * pl.ny * NACC + 2 + 4 * NSURF)
+    return np.zeros(plane_nleaf(pl) * NACC + 2 + 4 * NSURF)
 
 
 def plane_step(sp, form, seed, step0, nsteps, pl: Plane, area_frac, dt, st: PlaneState, acc=None):
     """Advance the plane domain ``nsteps`` steps in place (live particles end
     sorted by cell).  Returns (cell offsets, flags, counters)."""
-    ncell = pl.nx * pl.ny
+    ncell = plane_nleaf(pl)
+    if ncell < 0:
+        raise ValueError("refined grid: neighbouring fluid cells differ by two levels")
     af = np.ascontiguousarray(area_frac, dtype=np.float64)
     if af.size != ncell:
         raise ValueError("area_frac needs one entry per cell")

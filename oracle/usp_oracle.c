@@ -1317,7 +1317,7 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
 static double plane_dx(const orc_plane* pl) { return (pl->x1 - pl->x0) / pl->nx; }
 static double plane_dy(const orc_plane* pl) { return (pl->y1 - pl->y0) / pl->ny; }
 
-static int plane_cell(const orc_plane* pl, double x, double y)
+static int plane_l1(const orc_plane* pl, double x, double y, int* pi, int* pj)
 {
     int i = (int)floor((x - pl->x0) / plane_dx(pl));
     int j = (int)floor((y - pl->y0) / plane_dy(pl));
@@ -1325,7 +1325,173 @@ static int plane_cell(const orc_plane* pl, double x, double y)
     if (i >= pl->nx) i = pl->nx - 1;
     if (j < 0) j = 0;
     if (j >= pl->ny) j = pl->ny - 1;
+    *pi = i;
+    *pj = j;
     return j * pl->nx + i;
+}
+
+/* ---- refined grid (Sec. 5.C: three levels, each doubling the resolution) -- */
+typedef struct {
+    int levels, nleaf;
+    int balanced;         /* 1: no level-1 fluid leaf touches a level-3 leaf       */
+    int* l1_first;        /* nx*ny + 1: first leaf of each level-1 cell            */
+    int* l2_first;        /* 4 nx ny: first leaf of each level-2 child; -1 = none  */
+    signed char* l2_ref;  /* 4 nx ny: 1 when that level-2 cell is split again      */
+    int* level;           /* per leaf                                              */
+    int* ii;              /* per leaf: integer coordinates at its own level (the   */
+    int* jj;              /* centre is x0 + (ii + 1/2) dx / 2^(level-1))           */
+} amr_grid;
+
+static int amr_levels(const orc_plane* pl) { return pl->amr_levels >= 2 ? pl->amr_levels : 1; }
+
+/* centre of the square (xl, yl) + (w, h) within radius r of the cylinder centre */
+static int centre_within(const orc_plane* pl, double xl, double yl, double w, double h, double r)
+{
+    double ex = xl + 0.5 * w - pl->cyl_xc, ey = yl + 0.5 * h - pl->cyl_yc;
+    return ex * ex + ey * ey < r * r;
+}
+
+/* the square lies inside the body (its four corners within the radius):
+ * it holds no fluid and is not split */
+static int square_solid(const orc_plane* pl, double xl, double yl, double w, double h)
+{
+    if (!(pl->cyl_r > 0.0)) return 0;
+    double r2 = pl->cyl_r * pl->cyl_r;
+    for (int q = 0; q < 4; ++q) {
+        double ex = xl + (q & 1) * w - pl->cyl_xc, ey = yl + (q >> 1) * h - pl->cyl_yc;
+        if (ex * ex + ey * ey > r2) return 0;
+    }
+    return 1;
+}
+
+static void amr_build(const orc_plane* pl, amr_grid* g)
+{
+    int nx = pl->nx, ny = pl->ny, n1 = nx * ny;
+    double dx = plane_dx(pl), dy = plane_dy(pl);
+    g->levels = amr_levels(pl);
+    g->l1_first = (int*)malloc(sizeof(int) * (n1 + 1));
+    g->l2_first = (int*)malloc(sizeof(int) * 4 * n1);
+    g->l2_ref = (signed char*)calloc(4 * (size_t)n1, 1);
+    /* pass 1: count */
+    int nleaf = 0;
+    for (int c = 0; c < n1; ++c) {
+        int i = c % nx, j = c / nx;
+        g->l1_first[c] = nleaf;
+        double xl = pl->x0 + i * dx, yl = pl->y0 + j * dy;
+        int split = g->levels >= 2 && centre_within(pl, xl, yl, dx, dy, pl->amr_r2) &&
+                    !square_solid(pl, xl, yl, dx, dy);
+        if (!split) {
+            for (int k = 0; k < 4; ++k) g->l2_first[4 * c + k] = -1;
+            nleaf += 1;
+            continue;
+        }
+        for (int k = 0; k < 4; ++k) {
+            double x2 = xl + (k & 1) * 0.5 * dx, y2 = yl + (k >> 1) * 0.5 * dy;
+            int s3 = g->levels >= 3 && centre_within(pl, x2, y2, 0.5 * dx, 0.5 * dy, pl->amr_r3) &&
+                     !square_solid(pl, x2, y2, 0.5 * dx, 0.5 * dy);
+            g->l2_first[4 * c + k] = nleaf;
+            g->l2_ref[4 * c + k] = (signed char)s3;
+            nleaf += s3 ? 4 : 1;
+        }
+    }
+    g->l1_first[n1] = nleaf;
+    g->nleaf = nleaf;
+    g->level = (int*)malloc(sizeof(int) * nleaf);
+    g->ii = (int*)malloc(sizeof(int) * nleaf);
+    g->jj = (int*)malloc(sizeof(int) * nleaf);
+    /* pass 2: geometry */
+    for (int c = 0; c < n1; ++c) {
+        int i = c % nx, j = c / nx;
+        if (g->l2_first[4 * c] < 0) {
+            int l = g->l1_first[c];
+            g->level[l] = 1; g->ii[l] = i; g->jj[l] = j;
+            continue;
+        }
+        for (int k = 0; k < 4; ++k) {
+            int i2 = 2 * i + (k & 1), j2 = 2 * j + (k >> 1);
+            int l = g->l2_first[4 * c + k];
+            if (!g->l2_ref[4 * c + k]) {
+                g->level[l] = 2; g->ii[l] = i2; g->jj[l] = j2;
+                continue;
+            }
+            for (int q = 0; q < 4; ++q) {
+                g->level[l + q] = 3;
+                g->ii[l + q] = 2 * i2 + (q & 1);
+                g->jj[l + q] = 2 * j2 + (q >> 1);
+            }
+        }
+    }
+    /* levels of neighbouring leaves differ by at most one (the reconstruction
+     * of Sec. 3.B takes the four finer cells over a neighbour's square): every
+     * level-1 cell holding level-3 leaves has its eight neighbours split or
+     * inside the body */
+    g->balanced = 1;
+    for (int c = 0; c < n1 && g->balanced; ++c) {
+        int deep = 0;
+        for (int k = 0; k < 4; ++k) deep |= g->l2_ref[4 * c + k];
+        if (!deep) continue;
+        int i = c % nx, j = c / nx;
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+                int a = i + di, b = j + dj;
+                if (a < 0 || a >= nx || b < 0 || b >= ny || (di == 0 && dj == 0)) continue;
+                int m = b * nx + a;
+                if (g->l2_first[4 * m] < 0 &&
+                    !square_solid(pl, pl->x0 + a * dx, pl->y0 + b * dy, dx, dy))
+                    g->balanced = 0;
+            }
+    }
+}
+
+static void amr_free(amr_grid* g)
+{
+    free(g->l1_first); free(g->l2_first); free(g->l2_ref);
+    free(g->level); free(g->ii); free(g->jj);
+}
+
+/* the leaf holding (x, y): the level-1 cell as on the uniform grid, then
+ * the half (and quarter) of it the point lies in, from its offset within the
+ * cell */
+static int amr_leaf(const orc_plane* pl, const amr_grid* g, double x, double y)
+{
+    int i, j;
+    int c = plane_l1(pl, x, y, &i, &j);
+    if (g->levels < 2 || g->l2_first[4 * c] < 0) return g->l1_first[c];
+    double dx = plane_dx(pl), dy = plane_dy(pl);
+    double ux = (x - (pl->x0 + i * dx)) / (0.5 * dx), uy = (y - (pl->y0 + j * dy)) / (0.5 * dy);
+    int ci = ux >= 1.0 ? 1 : 0, cj = uy >= 1.0 ? 1 : 0;
+    int k = cj * 2 + ci;
+    int l = g->l2_first[4 * c + k];
+    if (!g->l2_ref[4 * c + k]) return l;
+    double vx = (ux - ci) * 2.0, vy = (uy - cj) * 2.0;
+    int qi = vx >= 1.0 ? 1 : 0, qj = vy >= 1.0 ? 1 : 0;
+    return l + qj * 2 + qi;
+}
+
+int orc_plane_nleaf(const orc_plane* pl)
+{
+    amr_grid g;
+    amr_build(pl, &g);
+    int n = g.balanced ? g.nleaf : -1;
+    amr_free(&g);
+    return n;
+}
+
+void orc_plane_leaves(const orc_plane* pl, int32_t* level, int32_t* ii, int32_t* jj)
+{
+    amr_grid g;
+    amr_build(pl, &g);
+    for (int l = 0; l < g.nleaf; ++l) { level[l] = g.level[l]; ii[l] = g.ii[l]; jj[l] = g.jj[l]; }
+    amr_free(&g);
+}
+
+int orc_plane_leaf_of(const orc_plane* pl, double x, double y)
+{
+    amr_grid g;
+    amr_build(pl, &g);
+    int l = amr_leaf(pl, &g, x, y);
+    amr_free(&g);
+    return l;
 }
 
 /* One-way number flux through a surface element of a drifting Maxwellian
@@ -1490,47 +1656,106 @@ static int advect_plane(const orc_species* sp, int form, uint64_t seed, uint32_t
     }
 }
 
-/* Sec. 3.B on a uniform 2D grid: the bilinear polynomial of the quadrant the
- * particle is in, through the averages of the cell, its x and y neighbours
- * on that side and the diagonal one (the matrix of Sec. 3.B: x-difference
- * with (x - x_i), y-difference with (y - y_j), cross term).  A neighbour is
- * usable if it lies in the domain, is not cut by the surface (fluid fraction
- * 1) and holds at least two particles; an unusable side neighbour is replaced
+/* Sec. 3.B: the bilinear polynomial of the quadrant the particle is in,
+ * through the averages of the cell and of the three squares of the cell's
+ * size beside it on that side (x, y and diagonal; the matrix of Sec. 3.B:
+ * x-difference with (x - x_i), y-difference with (y - y_j), cross term).  On
+ * a refined grid (Sec. 3.B, non-uniform grids) the average over such a square
+ * is the leaf of the same size there, the particle-number weighted mean of
+ * the four leaves one level finer that fill it, or the value of the coarser
+ * leaf's polynomial at the square's centre (its integral over the square
+ * divided by the area, exact for a bilinear polynomial).  A square is usable
+ * if it lies in the domain and every leaf in it is whole (fluid fraction 1)
+ * with, in all, at least two particles; an unusable side square is replaced
  * by the opposite one, and without one the direction has no slope; the cross
- * term needs the diagonal cell of the chosen sides. */
-void orc_plane_reconstruct(const orc_plane* pl, const int64_t* counts, const double* area_frac,
-                           const double* F, int cell, double x, double y, double* out)
+ * term needs the diagonal square of the chosen sides. */
+static void plane_reconstruct_g(const orc_plane* pl, const amr_grid* g, const int64_t* counts,
+                                const double* area_frac, const double* F, int cell, double x,
+                                double y, double* out);
+
+static int region_value(const orc_plane* pl, const amr_grid* g, const int64_t* counts,
+                        const double* area_frac, const double* F, int cell, int di, int dj,
+                        double* val)
 {
-    int nx = pl->nx, ny = pl->ny;
-    int i = cell % nx, j = cell / nx;
     double dx = plane_dx(pl), dy = plane_dy(pl);
-    double xc = pl->x0 + (i + 0.5) * dx, yc = pl->y0 + (j + 0.5) * dy;
+    int lvl = g->level[cell];
+    double h = dx / (double)(1 << (lvl - 1)), k = dy / (double)(1 << (lvl - 1));
+    double cx = pl->x0 + (g->ii[cell] + di + 0.5) * h, cy = pl->y0 + (g->jj[cell] + dj + 0.5) * k;
+    if (!(cx > pl->x0 && cx < pl->x1 && cy > pl->y0 && cy < pl->y1)) return 0;
+    int l = amr_leaf(pl, g, cx, cy);
+    int ll = g->level[l];
+    if (ll == lvl) {
+        if (!(area_frac[l] >= 1.0 && counts[l] >= 2)) return 0;
+        for (int f = 0; f < NFIELD; ++f) val[f] = F[l * NFIELD + f];
+        return 1;
+    }
+    if (ll > lvl) {
+        /* the four finer leaves filling the square, at the centres of its quarters */
+        int q[4];
+        int64_t nsum = 0;
+        for (int a = 0; a < 4; ++a) {
+            double px = cx + ((a & 1) ? 0.25 : -0.25) * h, py = cy + ((a >> 1) ? 0.25 : -0.25) * k;
+            q[a] = amr_leaf(pl, g, px, py);
+            if (g->level[q[a]] != lvl + 1 || !(area_frac[q[a]] >= 1.0)) return 0;
+            nsum += counts[q[a]];
+        }
+        if (nsum < 2) return 0;
+        for (int f = 0; f < NFIELD; ++f) {
+            double s = 0.0;
+            for (int a = 0; a < 4; ++a) s += (double)counts[q[a]] * F[q[a] * NFIELD + f];
+            val[f] = s / (double)nsum;
+        }
+        return 1;
+    }
+    /* coarser leaf: its own polynomial at the square's centre */
+    if (!(area_frac[l] >= 1.0 && counts[l] >= 2)) return 0;
+    plane_reconstruct_g(pl, g, counts, area_frac, F, l, cx, cy, val);
+    return 1;
+}
+
+static void plane_reconstruct_g(const orc_plane* pl, const amr_grid* g, const int64_t* counts,
+                                const double* area_frac, const double* F, int cell, double x,
+                                double y, double* out)
+{
+    double dx = plane_dx(pl), dy = plane_dy(pl);
+    int lvl = g->level[cell];
+    double h = dx / (double)(1 << (lvl - 1)), k = dy / (double)(1 << (lvl - 1));
+    double xc = pl->x0 + (g->ii[cell] + 0.5) * h, yc = pl->y0 + (g->jj[cell] + 0.5) * k;
     int sx = (x >= xc) ? 1 : -1, sy = (y >= yc) ? 1 : -1;
-#define USABLE(ii, jj) ((ii) >= 0 && (ii) < nx && (jj) >= 0 && (jj) < ny && \
-                        area_frac[(jj) * nx + (ii)] >= 1.0 && counts[(jj) * nx + (ii)] >= 2)
-    int ix = -1, jy = -1;
-    if (USABLE(i + sx, j)) ix = i + sx; else if (USABLE(i - sx, j)) ix = i - sx;
-    if (USABLE(i, j + sy)) jy = j + sy; else if (USABLE(i, j - sy)) jy = j - sy;
-    int diag = ix >= 0 && jy >= 0 && USABLE(ix, jy);
-#undef USABLE
+    double PX[NFIELD], PY[NFIELD], PD[NFIELD];
+    int ox = 0, oy = 0;
+    if (region_value(pl, g, counts, area_frac, F, cell, sx, 0, PX)) ox = sx;
+    else if (region_value(pl, g, counts, area_frac, F, cell, -sx, 0, PX)) ox = -sx;
+    if (region_value(pl, g, counts, area_frac, F, cell, 0, sy, PY)) oy = sy;
+    else if (region_value(pl, g, counts, area_frac, F, cell, 0, -sy, PY)) oy = -sy;
+    int diag = ox != 0 && oy != 0 && region_value(pl, g, counts, area_frac, F, cell, ox, oy, PD);
     for (int f = 0; f < NFIELD; ++f) {
         double p0 = F[cell * NFIELD + f];
         double v = p0;
         double px = 0.0, py = 0.0;
-        if (ix >= 0) {
-            px = F[(j * nx + ix) * NFIELD + f];
-            v += (px - p0) * (x - xc) / ((ix - i) * dx);
+        if (ox != 0) {
+            px = PX[f];
+            v += (px - p0) * (x - xc) / ((double)ox * h);
         }
-        if (jy >= 0) {
-            py = F[(jy * nx + i) * NFIELD + f];
-            v += (py - p0) * (y - yc) / ((jy - j) * dy);
+        if (oy != 0) {
+            py = PY[f];
+            v += (py - p0) * (y - yc) / ((double)oy * k);
         }
         if (diag) {
-            double pd = F[(jy * nx + ix) * NFIELD + f];
-            v += (pd - px - py + p0) * (x - xc) * (y - yc) / ((ix - i) * (jy - j) * dx * dy);
+            double pd = PD[f];
+            v += (pd - px - py + p0) * (x - xc) * (y - yc) / ((double)(ox * oy) * h * k);
         }
         out[f] = v;
     }
+}
+
+void orc_plane_reconstruct(const orc_plane* pl, const int64_t* counts, const double* area_frac,
+                           const double* F, int cell, double x, double y, double* out)
+{
+    amr_grid g;
+    amr_build(pl, &g);
+    plane_reconstruct_g(pl, &g, counts, area_frac, F, cell, x, y, out);
+    amr_free(&g);
 }
 
 int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0, int nsteps,
@@ -1540,7 +1765,13 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
                    int64_t* cell_off, double* acc, uint32_t* flags, int64_t* counters)
 {
     double R = orc_R(sp);
-    int ncell = pl->nx * pl->ny;
+    amr_grid grid;
+    amr_build(pl, &grid);
+    if (!grid.balanced) {
+        amr_free(&grid);
+        return -2;
+    }
+    int ncell = grid.nleaf;
     double dx = plane_dx(pl), dy = plane_dy(pl);
     double* F = (double*)malloc(sizeof(double) * NFIELD * ncell);
     double* cellT = (double*)malloc(sizeof(double) * 3 * ncell);
@@ -1624,7 +1855,7 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
         }
         /* 3. stable sort by cell */
         for (int c = 0; c <= ncell; ++c) pos[c] = 0;
-        for (int64_t j = 0; j < n; ++j) { cellof[j] = plane_cell(pl, x[j], y[j]); pos[cellof[j] + 1] += 1; }
+        for (int64_t j = 0; j < n; ++j) { cellof[j] = amr_leaf(pl, &grid, x[j], y[j]); pos[cellof[j] + 1] += 1; }
         for (int c = 0; c < ncell; ++c) pos[c + 1] += pos[c];
         for (int c = 0; c <= ncell; ++c) cell_off[c] = pos[c];
         for (int64_t j = 0; j < n; ++j) {
@@ -1660,7 +1891,8 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
             Fc[5] = orc_T_vib_from_mean_level(sp, lv);
             for (int k = 0; k < 6; ++k) Fc[6 + k] = P[k];
             cellT[3 * c] = Fc[3]; cellT[3 * c + 1] = Fc[4]; cellT[3 * c + 2] = Fc[5];
-            double vol = area_frac[c] * dx * dy * pl->depth;
+            double sc = (double)(1 << (grid.level[c] - 1));
+            double vol = area_frac[c] * (dx / sc) * (dy / sc) * pl->depth;
             if (!(vol > 0.0)) continue;
             double nd = N * pl->F_num / vol;
             if (orc_cell_coeffs(sp, nd, dt, Fc[3], Fc[4], Fc[5], &cc[c]) != 0) {
@@ -1678,7 +1910,7 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
             for (int64_t j = cell_off[c]; j < cell_off[c + 1]; ++j) {
                 double f[NFIELD];
                 if (pl->reconstruct) {
-                    orc_plane_reconstruct(pl, counts, area_frac, F, c, x[j], y[j], f);
+                    plane_reconstruct_g(pl, &grid, counts, area_frac, F, c, x[j], y[j], f);
                     if (!(f[3] > 0.0) || !(f[4] > 0.0) || !(f[5] >= 0.0)) {
                         counters[ORC_C_INTERP_FALLBACK] += 1;
                         memcpy(f, Fc, sizeof(f));
@@ -1719,5 +1951,6 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
     *n_io = n;
     free(F); free(cellT); free(counts); free(cc); free(ok); free(cellof); free(pos);
     free(tmpd); free(tmpl); free(tmpp);
+    amr_free(&grid);
     return status;
 }

@@ -207,13 +207,37 @@ typedef struct {
     int    inflow[4];              /* 1: inject the freestream through that side    */
     double F_num, depth;           /* particle weight; cell depth along z [m]        */
     int    reconstruct;
+    /* mesh refinement about the cylinder (Sec. 5.C three-level grid): with
+     * amr_levels 2 or 3, a level-1 cell whose centre lies within amr_r2 of
+     * the cylinder centre is split into 2 x 2 level-2 cells, and (levels 3)
+     * a level-2 cell whose centre lies within amr_r3 into 2 x 2 level-3
+     * cells; a cell whose four corners lie inside the body is not split.
+     * The cells ("leaves") are numbered level-1 cell by level-1 cell
+     * (row-major), the children of a split cell in the order (0,0), (1,0),
+     * (0,1), (1,1) of (x, y) halves.  Neighbouring fluid leaves must differ
+     * by one level at most: every level-1 cell holding level-3 leaves needs
+     * its eight neighbours split or inside the body.  0 or 1: the uniform
+     * grid. */
+    int    amr_levels;
+    double amr_r2, amr_r3;
 } orc_plane;
+
+/* Leaves of the plane's grid: count (-1 when the levels of neighbouring
+ * fluid leaves differ by two), and per leaf its level (1..3) and integer
+ * coordinates at its own level (centre x0 + (ii + 1/2) dx / 2^(level-1), y
+ * likewise; arrays of orc_plane_nleaf entries); the leaf holding a point. */
+int    orc_plane_nleaf(const orc_plane* pl);
+void   orc_plane_leaves(const orc_plane* pl, int32_t* level, int32_t* ii, int32_t* jj);
+int    orc_plane_leaf_of(const orc_plane* pl, double x, double y);
 
 /* nsteps steps of the plane domain.  Live particles are [0, *n) of arrays of
  * capacity cap; *n and *next_pid (the id given to the next injected particle)
- * are updated; on return the live particles are sorted by cell (cell j*nx+i)
- * with segment starts cell_off[ncell + 1].  area_frac[cell] is the fluid
- * fraction of each cell (volume = area_frac dx dy depth).  Accumulator layout
+ * are updated; on return the live particles are sorted by cell (leaf order
+ * above; cell j*nx+i on the uniform grid) with segment starts
+ * cell_off[ncell + 1], ncell = orc_plane_nleaf.  area_frac[cell] is the fluid
+ * fraction of each cell (volume = area_frac dx dy depth / 4^(level-1)).
+ * Returns 0, -1 when a cell's coefficients failed (flags say which), -2 for
+ * a refined grid whose neighbouring levels differ by two.  Accumulator layout
  * as ORC_NACC above, plus slot [ncell * ORC_NACC] = sampled steps, slot
  * [ncell * ORC_NACC + 1] = 0, then the surface tallies of the cylinder
  * (Sec. 5.C, surface coefficients): ORC_NSURF bins of the polar angle

@@ -297,6 +297,67 @@ def cut_cell_fractions(nx: int, ny: int, x0: float, x1: float, y0: float, y1: fl
     return frac.ravel()
 
 
+def refined_leaves(nx: int, ny: int, x0: float, x1: float, y0: float, y1: float,
+                   xc: float, yc: float, r: float, levels: int, r2: float, r3: float):
+    """Cells ("leaves") of the three-level grid of Sec. 5.C, in the order the
+    plane step numbers them: level-1 cells row-major; a level-1 cell whose
+    centre lies within ``r2`` of (xc, yc) is replaced by its 2 x 2 level-2
+    children in the order (0,0), (1,0), (0,1), (1,1) of (x, y) halves, and
+    with ``levels`` 3 a child whose centre lies within ``r3`` by its own 2 x 2
+    level-3 children; a cell whose four corners lie inside the body (radius
+    ``r``) is not split.  Returns (level, ii, jj) per leaf: integer
+    coordinates at the leaf's own level, so that its lower-left corner is
+    x0 + ii dx / 2^(level-1)."""
+    dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
+
+    def within(xl, yl, w, h, rr):
+        ex, ey = xl + 0.5 * w - xc, yl + 0.5 * h - yc
+        return ex * ex + ey * ey < rr * rr
+
+    def solid(xl, yl, w, h):
+        if not r > 0.0:
+            return False
+        for q in range(4):
+            ex, ey = xl + (q & 1) * w - xc, yl + (q >> 1) * h - yc
+            if ex * ex + ey * ey > r * r:
+                return False
+        return True
+
+    lv, li, lj = [], [], []
+    for j in range(ny):
+        for i in range(nx):
+            xl, yl = x0 + i * dx, y0 + j * dy
+            if not (levels >= 2 and within(xl, yl, dx, dy, r2) and not solid(xl, yl, dx, dy)):
+                lv.append(1); li.append(i); lj.append(j)
+                continue
+            for k in range(4):
+                xk, yk = xl + (k & 1) * 0.5 * dx, yl + (k >> 1) * 0.5 * dy
+                i2, j2 = 2 * i + (k & 1), 2 * j + (k >> 1)
+                if levels >= 3 and within(xk, yk, 0.5 * dx, 0.5 * dy, r3) and \
+                        not solid(xk, yk, 0.5 * dx, 0.5 * dy):
+                    for q in range(4):
+                        lv.append(3); li.append(2 * i2 + (q & 1)); lj.append(2 * j2 + (q >> 1))
+                else:
+                    lv.append(2); li.append(i2); lj.append(j2)
+    return (np.array(lv, dtype=np.int32), np.array(li, dtype=np.int32),
+            np.array(lj, dtype=np.int32))
+
+
+def refined_cut_fractions(nx: int, ny: int, x0: float, x1: float, y0: float, y1: float,
+                          xc: float, yc: float, r: float, leaves) -> np.ndarray:
+    """Fluid area fraction of every leaf of a refined grid (cut_cell_fractions
+    on the grid of the leaf's level)."""
+    lv, li, lj = leaves
+    af = np.ones(len(lv))
+    for L in np.unique(lv):
+        k = np.nonzero(lv == L)[0]
+        s = 1 << (int(L) - 1)
+        if r > 0:
+            fr = cut_cell_fractions(nx * s, ny * s, x0, x1, y0, y1, xc, yc, r)
+            af[k] = fr[lj[k].astype(np.int64) * (nx * s) + li[k]]
+    return af
+
+
 @dataclass
 class PlaneWorkload:
     name: str
@@ -322,7 +383,8 @@ def cylinder_flow(seed: int = 1, nx: int = 600, ny: int = 400, ppc: float = 30.0
                   r: float = 0.1, T_wall: float = 500.0, n_inf: float = 1.2012e21,
                   T_inf: float = 200.0, U_inf: float = 2883.3, dt_over_tau_c: float = 0.5,
                   capacity_factor: float = 2.0, steps: int = 20000, reconstruct: int = 1,
-                  cylinder: bool = True) -> PlaneWorkload:
+                  cylinder: bool = True, amr_levels: int = 0, amr_r2: float = 0.0,
+                  amr_r3: float = 0.0) -> PlaneWorkload:
     """Hypersonic N2 flow past a circular cylinder (the set-up of Sec. 5.C on a
     uniform Cartesian grid with cut cells): half body of radius 0.1 m centred on
     the origin, specular symmetry plane y = 0, fully diffuse wall at 500 K;
@@ -331,9 +393,15 @@ def cylinder_flow(seed: int = 1, nx: int = 600, ny: int = 400, ppc: float = 30.0
     1.25 mm, 30 particles per free cell, dt = 0.5 tau_c of the freestream.  The
     domain starts filled with the freestream (impulsive start).  With
     ``cylinder`` False the body is removed and the freestream also enters on
-    the right (uniform-flow checks)."""
+    the right (uniform-flow checks).  With ``amr_levels`` 2 or 3 the grid is
+    refined about the body (refined_leaves): ``ppc`` particles per free
+    level-1 cell, the same density in the finer cells (ppc / 4^(level-1))."""
     sp = n2_vhs_cylinder_species()
     rng = np.random.default_rng([seed, 0xC71D])
+    if amr_levels >= 2:
+        return _cylinder_refined(rng, sp, seed, nx, ny, ppc, x0, x1, y0, y1, r, T_wall, n_inf,
+                                 T_inf, U_inf, dt_over_tau_c, capacity_factor, steps,
+                                 reconstruct, cylinder, amr_levels, amr_r2, amr_r3)
     if cylinder:
         af = cut_cell_fractions(nx, ny, x0, x1, y0, y1, 0.0, 0.0, r)
     else:
@@ -359,23 +427,64 @@ def cylinder_flow(seed: int = 1, nx: int = 600, ny: int = 400, ppc: float = 30.0
               cyl_r=r if cylinder else 0.0, T_wall=T_wall, n_inf=n_inf, T_inf=T_inf,
               U_inf=U_inf, bc=(BC_OPEN, BC_OPEN, BC_SPECULAR, BC_OPEN),
               inflow=(1, 0 if cylinder else 1, 0, 1), F_num=F_num, depth=depth,
-              reconstruct=reconstruct)
+              reconstruct=reconstruct, amr_levels=0, amr_r2=0.0, amr_r3=0.0)
     cap = int(capacity_factor * N) + 4096
     name = ("Mach-10 N2 past a cylinder, %dx%d cells, %.0f particles/cell" % (nx, ny, ppc)
             if cylinder else "uniform N2 stream, %dx%d cells" % (nx, ny))
     return PlaneWorkload(name, sp, pl, af, dt_over_tau_c, x, y, p, cap, seed, steps)
 
 
+def _cylinder_refined(rng, sp, seed, nx, ny, ppc, x0, x1, y0, y1, r, T_wall, n_inf, T_inf, U_inf,
+                      dt_over_tau_c, capacity_factor, steps, reconstruct, cylinder, levels, r2,
+                      r3) -> PlaneWorkload:
+    """cylinder_flow on the refined grid: per leaf floor(ppc af / 4^(level-1)
+    + u) particles placed uniformly in it (redrawn inside it while in the
+    body), so the density is the freestream's everywhere."""
+    rb = r if cylinder else 0.0
+    leaves = refined_leaves(nx, ny, x0, x1, y0, y1, 0.0, 0.0, rb, levels, r2, r3)
+    lv, li, lj = leaves
+    af = refined_cut_fractions(nx, ny, x0, x1, y0, y1, 0.0, 0.0, rb, leaves)
+    dx, dy = (x1 - x0) / nx, (y1 - y0) / ny
+    depth = 1.0
+    F_num = n_inf * dx * dy * depth / ppc
+    scale = 1.0 / (1 << (lv - 1)).astype(np.float64)
+    counts = np.floor(ppc * af * scale * scale + rng.uniform(size=len(lv))).astype(np.int64)
+    N = int(counts.sum())
+    leaf = np.repeat(np.arange(len(lv)), counts)
+    h, k = dx * scale[leaf], dy * scale[leaf]
+    xl, yl = x0 + li[leaf] * h, y0 + lj[leaf] * k
+    x = xl + rng.uniform(size=N) * h
+    y = yl + rng.uniform(size=N) * k
+    if cylinder:
+        m = np.nonzero(x * x + y * y <= r * r)[0]
+        while len(m):
+            x[m] = xl[m] + rng.uniform(size=len(m)) * h[m]
+            y[m] = yl[m] + rng.uniform(size=len(m)) * k[m]
+            m = m[x[m] * x[m] + y[m] * y[m] <= r * r]
+    p = equilibrium_particles(rng, N, sp["m"], sp["theta_v"], U=(U_inf, 0.0, 0.0), T_tr=T_inf,
+                              T_rot=T_inf, T_vib=T_inf)
+    pl = dict(nx=nx, ny=ny, x0=x0, x1=x1, y0=y0, y1=y1, cyl_xc=0.0, cyl_yc=0.0,
+              cyl_r=rb, T_wall=T_wall, n_inf=n_inf, T_inf=T_inf,
+              U_inf=U_inf, bc=(BC_OPEN, BC_OPEN, BC_SPECULAR, BC_OPEN),
+              inflow=(1, 0 if cylinder else 1, 0, 1), F_num=F_num, depth=depth,
+              reconstruct=reconstruct, amr_levels=levels, amr_r2=r2, amr_r3=r3)
+    cap = int(capacity_factor * N) + 4096
+    name = ("Mach-10 N2 past a cylinder, %dx%d level-1 cells refined to %d levels "
+            "(%d cells), %.0f particles/level-1 cell" % (nx, ny, levels, len(lv), ppc))
+    return PlaneWorkload(name, sp, pl, af, dt_over_tau_c, x, y, p, cap, seed, steps)
+
+
 def cylinder_paper(seed: int = 1, ppc: float = 30.0, dt: float = 1.6e-7,
-                   capacity_factor: float = 2.0) -> PlaneWorkload:
-    """The cylinder case of Sec. 5.C with the paper's parameters on a uniform
-    grid: freestream n = 2.124e21 m^-3, 200 K, 2883 m/s (Mach 10), radius
-    0.1524 m, wall at 500 K, 0.8 m x 0.6 m half domain, cells of the paper's
-    coarse Level 1 grid (1.25 mm: 640 x 480), its coarse time step 1.6e-7 s.
-    Readings: the three-level refinement around the body is replaced by that
-    uniform grid with cut cells, the domain spans x in [-0.4, 0.4], y in
-    [0, 0.6] with the cylinder centred on the origin, and ``ppc`` particles
-    per free cell (the paper: 100)."""
+                   capacity_factor: float = 2.0, refined: bool = False) -> PlaneWorkload:
+    """The cylinder case of Sec. 5.C with the paper's parameters: freestream
+    n = 2.124e21 m^-3, 200 K, 2883 m/s (Mach 10), radius 0.1524 m, wall at
+    500 K, 0.8 m x 0.6 m half domain, cells of the paper's coarse Level 1
+    grid (1.25 mm: 640 x 480), its coarse time step 1.6e-7 s.  With
+    ``refined`` the paper's three levels (Level 2 within 0.24 m of the
+    centre, Level 3 within 0.155 m), else that uniform grid with cut cells.
+    Readings: the domain spans x in [-0.4, 0.4], y in [0, 0.6] with the
+    cylinder centred on the origin, and ``ppc`` particles per free level-1
+    cell (the paper: 100)."""
     sp = n2_vhs_cylinder_species()
     n_inf, T_inf = 2.124e21, 200.0
     # mean collision time of the freestream (VHS, Eq. tau_c), to express dt
@@ -387,7 +496,11 @@ def cylinder_paper(seed: int = 1, ppc: float = 30.0, dt: float = 1.6e-7,
         * mu / (n_inf * KB * T_inf)
     wl = cylinder_flow(seed=seed, nx=640, ny=480, ppc=ppc, x0=-0.4, x1=0.4, y0=0.0, y1=0.6,
                        r=0.1524, T_wall=500.0, n_inf=n_inf, T_inf=T_inf, U_inf=2883.0,
-                       dt_over_tau_c=dt / tau_c, capacity_factor=capacity_factor)
-    wl.name = ("Mach-10 N2 past a 0.1524 m cylinder (Sec. 5.C parameters), 640x480 cells, "
-               "%.0f particles/cell, dt = %.3g s" % (ppc, dt))
+                       dt_over_tau_c=dt / tau_c, capacity_factor=capacity_factor,
+                       amr_levels=3 if refined else 0, amr_r2=0.24 if refined else 0.0,
+                       amr_r3=0.155 if refined else 0.0)
+    wl.name = ("Mach-10 N2 past a 0.1524 m cylinder (Sec. 5.C parameters), 640x480 %s, "
+               "%.0f particles/%s, dt = %.3g s"
+               % ("level-1 cells on 3 levels (%d cells)" % len(wl.area_frac) if refined
+                  else "cells", ppc, "level-1 cell" if refined else "cell", dt))
     return wl
