@@ -59,6 +59,8 @@ def parse():
                     help="steps of the plain FPM method (Sec. 2.C) on the same workload, FP32")
     ap.add_argument("--channel-steps", type=int, default=2000)
     ap.add_argument("--cylinder-steps", type=int, default=64)
+    ap.add_argument("--refined-steps", type=int, default=64,
+                    help="steps of the paper's cylinder on its three-level grid (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--variant", default=None,
@@ -411,11 +413,9 @@ def run_ours(args, rank, world, local):
                 "steps": args.channel_steps}
         cctx.destroy()
 
-    # ---- the 2D path: Mach-10 cylinder, 600 x 400 cells, ~6.9M particles ---
-    cyl = None
-    if args.cylinder_steps > 0:
-        from paper_2508_05642_gb300 import inputs as I
-        yw = I.cylinder_flow(seed=rank_seed(rank))
+    # ---- the 2D path: Mach-10 cylinder, 600 x 400 cells, ~6.9M particles;
+    # the paper's cylinder on its three-level grid, 422,730 cells, ~8.5M ----
+    def plane_run(yw, steps, label):
         ydt = yw.dt_over_tau_c * usp.usp_tau_c(yw.species, yw.plane["n_inf"], yw.plane["T_inf"])
         yp = yw.particles
         yctx = usp.usp_init_plane(yw.species, yw.plane, ydt, yw.area_frac, yw.x, yw.y, yp.cx,
@@ -428,7 +428,7 @@ def run_ours(args, rank, world, local):
         l0 = usp.usp_launch_count(yctx)
         q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         q0.record(stream)
-        usp.usp_step(yctx, args.cylinder_steps)
+        usp.usp_step(yctx, steps)
         q1.record(stream)
         torch.cuda.synchronize()
         yms = max_over_ranks(q0.elapsed_time(q1))
@@ -441,14 +441,26 @@ def run_ours(args, rank, world, local):
         yfl, ycnt = usp.usp_status(yctx)
         # live count changes slowly; the mean of the two ends stands for it
         n_mean = 0.5 * (n_a + n_b)
-        cyl = {"workload": yw.name + ", FP32 state, reconstruction on, dt = 0.5 tau_c",
-               "value": sum_over_ranks(n_mean) * args.cylinder_steps / (yms / 1e3), "unit": UNIT,
-               "ms_per_step": yms / args.cylinder_steps, "steps": args.cylinder_steps,
+        out = {"workload": yw.name + label,
+               "value": sum_over_ranks(n_mean) * steps / (yms / 1e3), "unit": UNIT,
+               "ms_per_step": yms / steps, "steps": steps, "cells": len(yw.area_frac),
                "first_step": 16, "particles": [int(n_a), int(n_b)], "gpu_launches": int(yl),
                "ms_per_step_particle_passes": pk[0] / 8, "ms_per_step_cell_passes": pk[1] / 8,
                "alg_bytes_per_particle_step": BYTES_PER_PARTICLE_STEP["plane_f32"],
                "flags": int(yfl)}
         yctx.destroy()
+        return out
+
+    cyl = None
+    cyl_ref = None
+    if args.cylinder_steps > 0 or args.refined_steps > 0:
+        from paper_2508_05642_gb300 import inputs as I
+    if args.cylinder_steps > 0:
+        cyl = plane_run(I.cylinder_flow(seed=rank_seed(rank)), args.cylinder_steps,
+                        ", FP32 state, reconstruction on, dt = 0.5 tau_c")
+    if args.refined_steps > 0:
+        cyl_ref = plane_run(I.cylinder_paper(seed=rank_seed(rank), refined=True),
+                            args.refined_steps, ", FP32 state, reconstruction on")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -473,7 +485,7 @@ def run_ours(args, rank, world, local):
                                           "ms_warp_tiled_2_3_4": [float(x) for x in tune_ms[3:]]}},
                 "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "fpm_method": fpm,
                 "poiseuille_channel": chan,
-                "cylinder_plane": cyl,
+                "cylinder_plane": cyl, "cylinder_plane_refined": cyl_ref,
                 "clocks": clk,
                 "status": {"flags": int(flags), "counters": [int(x) for x in counters]}}
         print(json.dumps(line), flush=True)

@@ -161,15 +161,29 @@ typedef struct {
   int reconstruct;
 } usp_channel;
 
-/* 2D plane domain [x0, x1] x [y0, y1] on nx x ny uniform cells (cell
+/* 2D plane domain [x0, x1] x [y0, y1] on nx x ny level-1 cells (cell
  * j * nx + i), depth `depth` along z, with an optional circular body of
  * radius cyl_r (<= 0: none) centred at (cyl_xc, cyl_yc), fully diffuse at
- * T_wall (the hypersonic cylinder set-up of the paper's Sec. 5.C, on a
- * uniform grid with cut cells).  bc[] gives the condition of the sides
- * left, right, bottom, top (USP_BC_*); a side with inflow[k] = 1 (it must be
- * open) lets the freestream (n_inf, T_inf, velocity U_inf along x) enter
- * with its one-way Maxwellian flux.  F_num is the particle weight;
- * reconstruct = 1 for the quadrant bilinear reconstruction of Sec. 3.B. */
+ * T_wall (the hypersonic cylinder set-up of the paper's Sec. 5.C, with cut
+ * cells).  bc[] gives the condition of the sides left, right, bottom, top
+ * (USP_BC_*); a side with inflow[k] = 1 (it must be open) lets the freestream
+ * (n_inf, T_inf, velocity U_inf along x) enter with its one-way Maxwellian
+ * flux.  F_num is the particle weight; reconstruct = 1 for the quadrant
+ * bilinear reconstruction of Sec. 3.B.
+ *
+ * Mesh refinement (Sec. 5.C, three levels each doubling the resolution):
+ * amr_levels 0 or 1 keeps the uniform grid.  With 2 or 3, a level-1 cell
+ * whose centre lies within amr_r2 of (cyl_xc, cyl_yc) is split into 2 x 2
+ * level-2 cells and, with 3, a level-2 cell whose centre lies within amr_r3
+ * into 2 x 2 level-3 cells; a cell whose four corners lie inside the body is
+ * not split.  The cells ("leaves") are numbered level-1 cell by level-1 cell
+ * (row-major), the children of a split cell in the order (0,0), (1,0),
+ * (0,1), (1,1) of (x, y) halves (usp_plane_leaves lists them).  Neighbouring
+ * fluid cells must differ by one level at most: every level-1 cell holding
+ * level-3 cells needs its eight neighbours split or inside the body.  The
+ * reconstruction takes a finer neighbour's square as the particle-number
+ * weighted mean of its four cells and a coarser neighbour's as that cell's
+ * own polynomial at the square's centre (Sec. 3.B, non-uniform grids). */
 enum { USP_BC_OPEN = 0, USP_BC_SPECULAR = 1, USP_BC_DIFFUSE = 2 };
 typedef struct {
   int nx, ny;
@@ -181,7 +195,17 @@ typedef struct {
   int inflow[4];
   double F_num, depth;
   int reconstruct;
+  int amr_levels;
+  double amr_r2, amr_r3;
 } usp_plane;
+
+/* Cells of a plane's grid: returns their count (USP_EINVAL for invalid
+ * sizes or refinement parameters or neighbouring levels that differ by two)
+ * and, for the arrays that are not NULL, per cell its level (1..3) and
+ * integer coordinates at that level: the cell spans
+ * [x0 + ii h, x0 + (ii + 1) h] x [y0 + jj k, y0 + (jj + 1) k] with
+ * h = (x1 - x0) / nx / 2^(level-1), k likewise.  Host only; needs no GPU. */
+int usp_plane_leaves(const usp_plane* pl, int32_t* level, int32_t* ii, int32_t* jj);
 
 typedef struct usp_ctx usp_ctx;
 
@@ -246,10 +270,10 @@ int usp_channel_get_particles(usp_ctx* ctx, double* h_y, double* h_cx, double* h
 /* Create a context for the 2D plane domain (usp_plane) with storage for
  * `capacity` particles, holding n initial particles (x, y inside the domain,
  * outside the body; velocities, specific rotational energies, levels and
- * ids as in usp_init_channel; NULL ids: 0..n-1).  area_frac (nx * ny
- * doubles in [0, 1], host) is the fluid fraction of each cell: the cell
- * volume is area_frac dx dy depth, and only cells with fraction 1 serve as
- * reconstruction neighbours.  dt is the time step [s].  precision USP_FP32
+ * ids as in usp_init_channel; NULL ids: 0..n-1).  area_frac (one double in
+ * [0, 1] per cell, usp_plane_leaves order, host) is the fluid fraction of
+ * each cell: the cell volume is area_frac dx dy depth / 4^(level-1), and only
+ * cells with fraction 1 serve as reconstruction neighbours.  dt is the time step [s].  precision USP_FP32
  * or USP_FP64.  One step is: flight with events (body: diffuse re-emission;
  * sides: specular reflection or removal), injection of the entering
  * freestream particles (count floor(flux A dt / F_num + u) per face, entry

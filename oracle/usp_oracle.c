@@ -1666,7 +1666,9 @@ static int advect_plane(const orc_species* sp, int form, uint64_t seed, uint32_t
  * leaf's polynomial at the square's centre (its integral over the square
  * divided by the area, exact for a bilinear polynomial).  A square is usable
  * if it lies in the domain and every leaf in it is whole (fluid fraction 1)
- * with, in all, at least two particles; an unusable side square is replaced
+ * with at least two particles (a cell average needs two for the stress and
+ * temperature, as for a neighbour on the uniform grid); an unusable side
+ * square is replaced
  * by the opposite one, and without one the direction has no slope; the cross
  * term needs the diagonal square of the chosen sides. */
 static void plane_reconstruct_g(const orc_plane* pl, const amr_grid* g, const int64_t* counts,
@@ -1696,10 +1698,10 @@ static int region_value(const orc_plane* pl, const amr_grid* g, const int64_t* c
         for (int a = 0; a < 4; ++a) {
             double px = cx + ((a & 1) ? 0.25 : -0.25) * h, py = cy + ((a >> 1) ? 0.25 : -0.25) * k;
             q[a] = amr_leaf(pl, g, px, py);
-            if (g->level[q[a]] != lvl + 1 || !(area_frac[q[a]] >= 1.0)) return 0;
+            if (g->level[q[a]] != lvl + 1 || !(area_frac[q[a]] >= 1.0 && counts[q[a]] >= 2))
+                return 0;
             nsum += counts[q[a]];
         }
-        if (nsum < 2) return 0;
         for (int f = 0; f < NFIELD; ++f) {
             double s = 0.0;
             for (int a = 0; a < 4; ++a) s += (double)counts[q[a]] * F[q[a] * NFIELD + f];

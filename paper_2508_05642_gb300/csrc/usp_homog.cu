@@ -2199,6 +2199,10 @@ int usp_init_plane(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
   return USP_OK;
 }
 
+int usp_plane_leaves(const usp_plane* pl, int32_t* level, int32_t* ii, int32_t* jj) {
+  return pl_leaves(pl, level, ii, jj);
+}
+
 int usp_plane_count(usp_ctx* c, int64_t* n, uint32_t* next_pid) {
   if (!c || c->kind != 2) return USP_EINVAL;
   return pl_count(c->pl, make_env(c), n, next_pid);

@@ -64,6 +64,17 @@ struct PlGeom {
   double cxc, cyc, cr;
   double Tw, dt;
   int bcbits;         // 2 bits per side (USP_BC_*): left, right, bottom, top
+  // refined grid (levels 2, 3; 1 = uniform): per level-1 cell its first
+  // cell, per level-2 child its first cell (-1: the level-1 cell is not
+  // split) and whether it is split again; per cell its level and integer
+  // coordinates at that level
+  int levels;
+  const int* l1_first;
+  const int* l2_first;
+  const signed char* l2_ref;
+  const int* lvl;
+  const int* lii;
+  const int* ljj;
 };
 
 struct PlInflow {
@@ -90,13 +101,28 @@ struct PlParams {
 
 __device__ __forceinline__ int grid_threads() { return gridDim.x * blockDim.x; }
 
+// the cell holding (x, y): the level-1 cell, then on a refined grid the
+// half (and quarter) of it from the point's offset in units of half a cell
+// (round-to-nearest operations: the FP64 form places points exactly as the
+// plain definition does)
 template <typename T>
 __device__ __forceinline__ int plane_cell(const PlGeom& g, T x, T y) {
   int i = (int)floor((x - (T)g.x0) / (T)g.dx);
   int j = (int)floor((y - (T)g.y0) / (T)g.dy);
   i = i < 0 ? 0 : (i >= g.nx ? g.nx - 1 : i);
   j = j < 0 ? 0 : (j >= g.ny ? g.ny - 1 : j);
-  return j * g.nx + i;
+  const int c = j * g.nx + i;
+  if (g.levels < 2) return c;
+  const int first = g.l2_first[4 * c];
+  if (first < 0) return g.l1_first[c];
+  const T ux = rn_div(rn_sub(x, rn_add((T)g.x0, rn_mul((T)i, (T)g.dx))), rn_mul(T(0.5), (T)g.dx));
+  const T uy = rn_div(rn_sub(y, rn_add((T)g.y0, rn_mul((T)j, (T)g.dy))), rn_mul(T(0.5), (T)g.dy));
+  const int ci = ux >= T(1) ? 1 : 0, cj = uy >= T(1) ? 1 : 0;
+  const int k = 2 * cj + ci;
+  const int l = g.l2_first[4 * c + k];
+  if (!g.l2_ref[4 * c + k]) return l;
+  const T vx = rn_mul(rn_sub(ux, (T)ci), T(2)), vy = rn_mul(rn_sub(uy, (T)cj), T(2));
+  return l + 2 * (vy >= T(1) ? 1 : 0) + (vx >= T(1) ? 1 : 0);
 }
 
 // Diffuse re-emission at T_w about the inward normal (nx, ny): Rayleigh
@@ -719,6 +745,123 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
   for (int w = threadIdx.x; w < words; w += kParamBlock) dst[w] = src[w];
 }
 
+// ---------------------------------------------------------------------------
+// reconstruction stencils on the refined grid (Sec. 3.B, non-uniform grids):
+// the same formula as on the uniform grid, with the average over each
+// neighbouring square of the cell's own size taken from the cell of that
+// size there, the particle-number weighted mean of the four finer cells
+// filling it, or the coarser cell's polynomial at the square's centre (its
+// average over the square).  A square is usable when every cell in it is
+// (whole, two particles or more).  One launch per level, coarsest first, so that
+// a coarser neighbour's record is complete when a finer cell reads it.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ bool pl_region(const PlGeom& g, const PlParams<T>* __restrict__ prm,
+                          const T* __restrict__ fT, const int* __restrict__ usable_c,
+                          const long long* __restrict__ off, int lvl, int ii, int jj, int di,
+                          int dj, double h, double k, T* val) {
+  const double cx = rn_add(g.x0, rn_mul((double)(ii + di) + 0.5, h));
+  const double cy = rn_add(g.y0, rn_mul((double)(jj + dj) + 0.5, k));
+  if (!(cx > g.x0 && cx < g.x1 && cy > g.y0 && cy < g.y1)) return false;
+  const int l = plane_cell<double>(g, cx, cy);
+  const int ll = g.lvl[l];
+  if (ll == lvl) {
+    if (!usable_c[l]) return false;
+    for (int f = 0; f < kNF; ++f) val[f] = fT[(size_t)l * kNF + f];
+    return true;
+  }
+  if (ll > lvl) {
+    int q[4];
+    long long nq[4], ns = 0;
+    for (int a = 0; a < 4; ++a) {
+      const double px = rn_add(cx, rn_mul((a & 1) ? 0.25 : -0.25, h));
+      const double py = rn_add(cy, rn_mul((a >> 1) ? 0.25 : -0.25, k));
+      q[a] = plane_cell<double>(g, px, py);
+      if (g.lvl[q[a]] != lvl + 1 || !usable_c[q[a]]) return false;
+      nq[a] = off[q[a] + 1] - off[q[a]];
+      ns += nq[a];
+    }
+    for (int f = 0; f < kNF; ++f) {
+      T sum = T(0);
+      for (int a = 0; a < 4; ++a) sum += (T)nq[a] * fT[(size_t)q[a] * kNF + f];
+      val[f] = sum / (T)ns;
+    }
+    return true;
+  }
+  if (!usable_c[l]) return false;
+  const PlParams<T>& C = prm[l];
+  const T ex = (T)cx - C.xc, ey = (T)cy - C.yc;
+  const int sx = ex >= T(0) ? 1 : 0, sy = ey >= T(0) ? 1 : 0;
+  for (int f = 0; f < kNF; ++f)
+    val[f] = C.F[f] + C.gx[sx][f] * ex + C.gy[sy][f] * ey + C.gxy[2 * sy + sx][f] * ex * ey;
+  return true;
+}
+
+template <typename T>
+__global__ void pl_params_amr(PlGeom g, int recon, int level,
+                              const ChCellT<double>* __restrict__ cells, const T* __restrict__ fT,
+                              const int* __restrict__ usable_c, const long long* __restrict__ off,
+                              PlParams<T>* __restrict__ prm, Species sp) {
+  __shared__ PlParams<T> buf[kParamBlock];
+  const int c0 = blockIdx.x * kParamBlock;
+  const int c = c0 + threadIdx.x;
+  const int nb = min(kParamBlock, g.ncell - c0);
+  if (c < g.ncell && g.lvl[c] == level) {
+    const ChCellT<double>& cs = cells[c];
+    PlParams<T>& P = buf[threadIdx.x];
+    P.active = cs.active;
+    P.pad = 0;
+    P.alpha = (T)cs.alpha; P.nu_ref = (T)cs.nu_ref; P.B = (T)cs.B; P.mu_p = (T)cs.mu_p;
+    P.Pr = (T)cs.Pr; P.gtr = (T)cs.gtr; P.gtv = (T)cs.gtv; P.grv = (T)cs.grv;
+    P.R = (T)gasR(sp); P.theta = (T)sp.theta_v; P.dt = (T)g.dt;
+    const double sc = (double)(1 << (level - 1));
+    const double h = g.dx / sc, k = g.dy / sc;
+    const int ii = g.lii[c], jj = g.ljj[c];
+    P.xc = (T)rn_add(g.x0, rn_mul((double)ii + 0.5, h));
+    P.yc = (T)rn_add(g.y0, rn_mul((double)jj + 0.5, k));
+    const T* f = fT + (size_t)c * kNF;
+    for (int q = 0; q < kNF; ++q) P.F[q] = f[q];
+    const T ih = (T)(1.0 / h), ik = (T)(1.0 / k);
+    T PX[2][kNF], PY[2][kNF], PD[kNF];
+    int ox[2] = {0, 0}, oy[2] = {0, 0};
+    for (int sd = 0; sd < 2; ++sd) {
+      const int sg = sd ? 1 : -1;
+      if (recon) {
+        if (pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, sg, 0, h, k, PX[sd]))
+          ox[sd] = sg;
+        else if (pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, -sg, 0, h, k, PX[sd]))
+          ox[sd] = -sg;
+        if (pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, 0, sg, h, k, PY[sd]))
+          oy[sd] = sg;
+        else if (pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, 0, -sg, h, k, PY[sd]))
+          oy[sd] = -sg;
+      }
+      const T sx = ox[sd] > 0 ? ih : -ih, sy = oy[sd] > 0 ? ik : -ik;
+      for (int q = 0; q < kNF; ++q) {
+        P.gx[sd][q] = ox[sd] ? (PX[sd][q] - f[q]) * sx : T(0);
+        P.gy[sd][q] = oy[sd] ? (PY[sd][q] - f[q]) * sy : T(0);
+      }
+    }
+    for (int q = 0; q < 4; ++q) {
+      const int sx = q & 1, sy = q >> 1;
+      const bool d = ox[sx] && oy[sy] &&
+                     pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, ox[sx], oy[sy], h,
+                                  k, PD);
+      const T s = (ox[sx] * oy[sy] > 0 ? T(1) : T(-1)) * ih * ik;
+      for (int m = 0; m < kNF; ++m)
+        P.gxy[q][m] = d ? (PD[m] - PX[sx][m] - PY[sy][m] + f[m]) * s : T(0);
+    }
+  }
+  __syncthreads();
+  // copy out the records of this level only (the others belong to the other
+  // launches)
+  constexpr int kW = (int)(sizeof(PlParams<T>) / 8);
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(buf);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(prm + c0);
+  for (int w = threadIdx.x; w < nb * kW; w += kParamBlock)
+    if (g.lvl[c0 + w / kW] == level) dst[w] = src[w];
+}
+
 // Asynchronous global -> shared copies of 4, 8 or 16 bytes (cp.async): the
 // plane collision prefetches the next cell's data while it works on the
 // current one.
@@ -1056,6 +1199,7 @@ struct PlaneCtx {
   int* face_off;
   long long* off;
   double* af;
+  double* afv;              // af / 4^(level-1): the cell volume over dx dy depth
   PlCount* cnt;
   ChCellT<double>* cells;
   float* pend;              // FP32 copy of the pending rescale (Un, Us, s, r) per cell
@@ -1081,6 +1225,115 @@ double inflow_flux(double n, double RT, double u_n) {
   // one-way number flux of a drifting Maxwellian through a surface element
   const double s = u_n / std::sqrt(2.0 * RT);
   return n * std::sqrt(RT / (2.0 * kPi)) * (std::exp(-s * s) + std::sqrt(kPi) * s * (1.0 + std::erf(s)));
+}
+
+// Refined grid of a plane (Sec. 5.C): level-1 cells row-major, a split cell
+// replaced by its 2 x 2 children in the order (0,0), (1,0), (0,1), (1,1),
+// each of which may be split once more.  A cell is split when its centre
+// lies within the level's radius of the body centre and not all of it lies
+// inside the body.  Plain arithmetic (the host build keeps a * b + c
+// unfused), so the layout and point location repeat the plain definition.
+struct PlGrid {
+  int levels = 1, nleaf = 0;
+  bool balanced = true;
+  std::vector<int> l1_first, l2_first, lvl, lii, ljj;
+  std::vector<signed char> l2_ref;
+};
+
+bool pg_centre_in(const usp_plane* p, double xl, double yl, double w, double h, double r) {
+  const double ex = xl + 0.5 * w - p->cyl_xc, ey = yl + 0.5 * h - p->cyl_yc;
+  return ex * ex + ey * ey < r * r;
+}
+
+bool pg_solid(const usp_plane* p, double xl, double yl, double w, double h) {
+  if (!(p->cyl_r > 0.0)) return false;
+  const double r2 = p->cyl_r * p->cyl_r;
+  for (int q = 0; q < 4; ++q) {
+    const double ex = xl + (q & 1) * w - p->cyl_xc, ey = yl + (q >> 1) * h - p->cyl_yc;
+    if (ex * ex + ey * ey > r2) return false;
+  }
+  return true;
+}
+
+void pg_build(const usp_plane* p, PlGrid& G) {
+  const int nx = p->nx, ny = p->ny, n1 = nx * ny;
+  const double dx = (p->x1 - p->x0) / nx, dy = (p->y1 - p->y0) / ny;
+  G.levels = p->amr_levels >= 2 ? p->amr_levels : 1;
+  G.l1_first.assign(n1 + 1, 0);
+  G.l2_first.assign((size_t)4 * n1, -1);
+  G.l2_ref.assign((size_t)4 * n1, 0);
+  G.lvl.clear(); G.lii.clear(); G.ljj.clear();
+  for (int c = 0; c < n1; ++c) {
+    const int i = c % nx, j = c / nx;
+    G.l1_first[c] = (int)G.lvl.size();
+    const double xl = p->x0 + i * dx, yl = p->y0 + j * dy;
+    if (!(G.levels >= 2 && pg_centre_in(p, xl, yl, dx, dy, p->amr_r2) &&
+          !pg_solid(p, xl, yl, dx, dy))) {
+      G.lvl.push_back(1); G.lii.push_back(i); G.ljj.push_back(j);
+      continue;
+    }
+    for (int k = 0; k < 4; ++k) {
+      const double xk = xl + (k & 1) * 0.5 * dx, yk = yl + (k >> 1) * 0.5 * dy;
+      const int i2 = 2 * i + (k & 1), j2 = 2 * j + (k >> 1);
+      const bool s3 = G.levels >= 3 && pg_centre_in(p, xk, yk, 0.5 * dx, 0.5 * dy, p->amr_r3) &&
+                      !pg_solid(p, xk, yk, 0.5 * dx, 0.5 * dy);
+      G.l2_first[(size_t)4 * c + k] = (int)G.lvl.size();
+      G.l2_ref[(size_t)4 * c + k] = s3 ? 1 : 0;
+      if (!s3) {
+        G.lvl.push_back(2); G.lii.push_back(i2); G.ljj.push_back(j2);
+        continue;
+      }
+      for (int q = 0; q < 4; ++q) {
+        G.lvl.push_back(3); G.lii.push_back(2 * i2 + (q & 1)); G.ljj.push_back(2 * j2 + (q >> 1));
+      }
+    }
+  }
+  G.nleaf = (int)G.lvl.size();
+  G.l1_first[n1] = G.nleaf;
+  // neighbouring fluid cells differ by one level at most: the eight
+  // neighbours of a level-1 cell holding level-3 cells are split or solid
+  G.balanced = true;
+  for (int c = 0; c < n1 && G.balanced; ++c) {
+    bool deep = false;
+    for (int k = 0; k < 4; ++k) deep = deep || G.l2_ref[(size_t)4 * c + k];
+    if (!deep) continue;
+    const int i = c % nx, j = c / nx;
+    for (int b = j - 1; b <= j + 1; ++b)
+      for (int a = i - 1; a <= i + 1; ++a) {
+        if (a < 0 || a >= nx || b < 0 || b >= ny || (a == i && b == j)) continue;
+        const int m = b * nx + a;
+        if (G.l2_first[(size_t)4 * m] < 0 && !pg_solid(p, p->x0 + a * dx, p->y0 + b * dy, dx, dy))
+          G.balanced = false;
+      }
+  }
+}
+
+// the cell holding (x, y), as plane_cell on the device
+int pg_leaf(const usp_plane* p, const PlGrid& G, double x, double y) {
+  const double dx = (p->x1 - p->x0) / p->nx, dy = (p->y1 - p->y0) / p->ny;
+  int i = (int)std::floor((x - p->x0) / dx), j = (int)std::floor((y - p->y0) / dy);
+  i = std::min(std::max(i, 0), p->nx - 1);
+  j = std::min(std::max(j, 0), p->ny - 1);
+  const int c = j * p->nx + i;
+  if (G.levels < 2 || G.l2_first[(size_t)4 * c] < 0) return G.l1_first[c];
+  const double ux = (x - (p->x0 + i * dx)) / (0.5 * dx), uy = (y - (p->y0 + j * dy)) / (0.5 * dy);
+  const int ci = ux >= 1.0 ? 1 : 0, cj = uy >= 1.0 ? 1 : 0;
+  const int k = 2 * cj + ci;
+  const int l = G.l2_first[(size_t)4 * c + k];
+  if (!G.l2_ref[(size_t)4 * c + k]) return l;
+  const double vx = (ux - ci) * 2.0, vy = (uy - cj) * 2.0;
+  return l + 2 * (vy >= 1.0 ? 1 : 0) + (vx >= 1.0 ? 1 : 0);
+}
+
+// sizes and refinement parameters of a plane; 0 or USP_EINVAL
+int pg_check(const usp_plane* p) {
+  if (!p || p->nx <= 0 || p->ny <= 0 || (long long)p->nx * p->ny >= (1 << 24) ||
+      !(p->x1 > p->x0) || !(p->y1 > p->y0))
+    return USP_EINVAL;
+  if (p->amr_levels < 0 || p->amr_levels > 3) return USP_EINVAL;
+  if (p->amr_levels >= 2 && !(p->amr_r2 > 0.0 && std::isfinite(p->amr_r2))) return USP_EINVAL;
+  if (p->amr_levels >= 3 && !(p->amr_r3 > 0.0 && std::isfinite(p->amr_r3))) return USP_EINVAL;
+  return 0;
 }
 
 template <typename T>
@@ -1131,14 +1384,20 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
                                             h->cells, env.sp, env.counters, pend, (T*)h->fT,
                                             h->usable_c);
   if (env.precision == USP_FP32)
-    ch_coeffs_f32<<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->af, h->g.dt, h->cells, env.sp,
+    ch_coeffs_f32<<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->afv, h->g.dt, h->cells, env.sp,
                                       env.flags, env.counters);
   else
-    ch_coeffs<double><<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->af, h->g.dt, h->cells,
+    ch_coeffs<double><<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->afv, h->g.dt, h->cells,
                                           env.sp, env.sp.omega, env.sp.Z_rot, env.flags,
                                           env.counters);
-  pl_params<T><<<(ncell + kParamBlock - 1) / kParamBlock, kParamBlock, 0, s>>>(
-      h->g, h->recon, h->cells, (const T*)h->fT, h->usable_c, (PlParams<T>*)h->prm, env.sp);
+  if (h->g.levels < 2)
+    pl_params<T><<<(ncell + kParamBlock - 1) / kParamBlock, kParamBlock, 0, s>>>(
+        h->g, h->recon, h->cells, (const T*)h->fT, h->usable_c, (PlParams<T>*)h->prm, env.sp);
+  else
+    for (int L = 1; L <= h->g.levels; ++L)
+      pl_params_amr<T><<<(ncell + kParamBlock - 1) / kParamBlock, kParamBlock, 0, s>>>(
+          h->g, h->recon, L, h->cells, (const T*)h->fT, h->usable_c, h->off,
+          (PlParams<T>*)h->prm, env.sp);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 1, 0);
   if (prof) prof(env.owner, 0, 1);
@@ -1166,8 +1425,8 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
 }  // namespace
 
 int pl_kernels_per_step(const PlaneCtx* h) {
-  return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 2 + 3 + 1 + 2 +
-         (h->sampling ? 1 : 0);
+  return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 2 + 2 +
+         (h->g.levels < 2 ? 1 : h->g.levels) + 1 + 2 + (h->sampling ? 1 : 0);
 }
 
 int pl_launch_step(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
@@ -1180,9 +1439,8 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
               const double* area_frac, int64_t n, int64_t cap, int64_t step0, const double* x,
               const double* y, const double* cx, const double* cy, const double* cz,
               const double* erot, const int32_t* lev, const uint32_t* pid) {
-  if (!pp || pp->nx <= 0 || pp->ny <= 0 || (long long)pp->nx * pp->ny >= (1 << 24) ||
-      !(pp->x1 > pp->x0) || !(pp->y1 > pp->y0) || !(pp->F_num > 0) || !(pp->depth > 0) ||
-      !(dt > 0) || n < 0 || cap < n || cap < 1 || cap > 0x7fffffffll)
+  if (pg_check(pp) || !(pp->F_num > 0) || !(pp->depth > 0) || !(dt > 0) || n < 0 || cap < n ||
+      cap < 1 || cap > 0x7fffffffll)
     return USP_EINVAL;
   if (env.precision != USP_FP32 && env.precision != USP_FP64) return USP_ENOTSUP;
   for (int k = 0; k < 4; ++k) {
@@ -1196,7 +1454,10 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
     return USP_EINVAL;
   if (n > 0 && (!x || !y || !cx || !cy || !cz || !erot || !lev)) return USP_EINVAL;
   if (!area_frac) return USP_EINVAL;
-  const int ncell = pp->nx * pp->ny;
+  PlGrid G;
+  pg_build(pp, G);
+  if (!G.balanced || G.nleaf >= (1 << 24)) return USP_EINVAL;
+  const int ncell = G.nleaf;
   for (int c = 0; c < ncell; ++c)
     if (!(area_frac[c] >= 0.0 && area_frac[c] <= 1.0)) return USP_EINVAL;
   for (int64_t j = 0; j < n; ++j)
@@ -1210,6 +1471,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   g.dx = (pp->x1 - pp->x0) / pp->nx; g.dy = (pp->y1 - pp->y0) / pp->ny;
   g.cxc = pp->cyl_xc; g.cyc = pp->cyl_yc; g.cr = pp->cyl_r > 0 ? pp->cyl_r : 0.0;
   g.Tw = pp->T_wall; g.dt = dt;
+  g.levels = G.levels;
   g.bcbits = 0;
   for (int k = 0; k < 4; ++k) g.bcbits |= (pp->bc[k] & 3) << (2 * k);
   h->recon = pp->reconstruct ? 1 : 0;
@@ -1276,6 +1538,17 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->face_off = (int*)A(sizeof(int) * (f.nfaces + 1));
   h->off = (long long*)A(sizeof(long long) * (ncell + 1));
   h->af = (double*)A(sizeof(double) * ncell);
+  h->afv = h->af;
+  const int n1 = pp->nx * pp->ny;
+  if (G.levels >= 2) {
+    h->afv = (double*)A(sizeof(double) * ncell);
+    g.l1_first = (const int*)A(sizeof(int) * (n1 + 1));
+    g.l2_first = (const int*)A(sizeof(int) * 4 * (size_t)n1);
+    g.l2_ref = (const signed char*)A(4 * (size_t)n1);
+    g.lvl = (const int*)A(sizeof(int) * ncell);
+    g.lii = (const int*)A(sizeof(int) * ncell);
+    g.ljj = (const int*)A(sizeof(int) * ncell);
+  }
   h->cnt = (PlCount*)A(sizeof(PlCount));
   h->cells = (ChCellT<double>*)A(sizeof(ChCellT<double>) * ncell);
   h->pend = (float*)A(sizeof(float) * 8 * ncell);
@@ -1289,7 +1562,8 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->macc = (double*)A(sizeof(double) * 21 * ncell);
   h->mout = (double*)A(sizeof(double) * USP_NMOM * ncell);
   h->dstep = (long long*)A(sizeof(long long));
-  bool ok = h->keycell && h->bh && h->tot && h->face_off && h->off && h->af && h->cnt &&
+  bool ok = h->keycell && h->bh && h->tot && h->face_off && h->off && h->af && h->afv && h->cnt &&
+            (G.levels < 2 || (g.l1_first && g.l2_first && g.l2_ref && g.lvl && g.lii && g.ljj)) &&
             h->cells && h->pend && h->fT && h->usable_c && h->prm && h->sums && h->acc && h->macc && h->mout && h->dstep;
   for (int k = 0; k < 2; ++k) {
     for (int q = 0; q < 6; ++q) ok = ok && h->st[k][q];
@@ -1308,10 +1582,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   for (int64_t j = 0; j < n; ++j) {
     hl[j] = x[j]; hl[n + j] = y[j]; hl[2 * n + j] = cx[j]; hl[3 * n + j] = cy[j];
     hl[4 * n + j] = cz[j]; hl[5 * n + j] = erot[j];
-    int i = (int)std::floor((x[j] - g.x0) / g.dx), jj = (int)std::floor((y[j] - g.y0) / g.dy);
-    i = std::min(std::max(i, 0), g.nx - 1);
-    jj = std::min(std::max(jj, 0), g.ny - 1);
-    key[j] = jj * g.nx + i;
+    key[j] = pg_leaf(pp, G, x[j], y[j]);
     hp[j] = pid ? pid[j] : (uint32_t)j;
     next = std::max(next, hp[j] + 1u);
   }
@@ -1346,6 +1617,26 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   }
   cok = cok && cudaMemcpyAsync(h->af, area_frac, sizeof(double) * ncell, cudaMemcpyHostToDevice,
                                s) == cudaSuccess;
+  std::vector<double> afv;
+  if (G.levels >= 2) {
+    // the grid tables and the volume factor af / 4^(level-1) of every cell
+    afv.resize(ncell);
+    for (int c = 0; c < ncell; ++c) {
+      const double sc = (double)(1 << (G.lvl[c] - 1));
+      afv[c] = area_frac[c] / (sc * sc);
+    }
+    auto up = [&](const void* dst, const void* src, size_t bytes) {
+      return cudaMemcpyAsync(const_cast<void*>(dst), src, bytes, cudaMemcpyHostToDevice, s) ==
+             cudaSuccess;
+    };
+    cok = cok && up(h->afv, afv.data(), sizeof(double) * ncell);
+    cok = cok && up(g.l1_first, G.l1_first.data(), sizeof(int) * (n1 + 1));
+    cok = cok && up(g.l2_first, G.l2_first.data(), sizeof(int) * 4 * (size_t)n1);
+    cok = cok && up(g.l2_ref, G.l2_ref.data(), 4 * (size_t)n1);
+    cok = cok && up(g.lvl, G.lvl.data(), sizeof(int) * ncell);
+    cok = cok && up(g.lii, G.lii.data(), sizeof(int) * ncell);
+    cok = cok && up(g.ljj, G.ljj.data(), sizeof(int) * ncell);
+  }
   cok = cok && cudaMemcpyAsync(h->cnt, &c0, sizeof(PlCount), cudaMemcpyHostToDevice, s) == cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->cells, hc.data(), sizeof(ChCellT<double>) * ncell,
                                cudaMemcpyHostToDevice, s) == cudaSuccess;
@@ -1454,6 +1745,19 @@ int pl_get_particles(PlaneCtx* h, const ChEnv& env, int64_t cap, int64_t* n_out,
     if (erot) erot[j] = hl[5 * n + j];
   }
   return USP_OK;
+}
+
+int pl_leaves(const usp_plane* pp, int32_t* level, int32_t* ii, int32_t* jj) {
+  if (pg_check(pp)) return USP_EINVAL;
+  PlGrid G;
+  pg_build(pp, G);
+  if (!G.balanced || G.nleaf >= (1 << 24)) return USP_EINVAL;
+  for (int c = 0; c < G.nleaf; ++c) {
+    if (level) level[c] = G.lvl[c];
+    if (ii) ii[c] = G.lii[c];
+    if (jj) jj[c] = G.ljj[c];
+  }
+  return G.nleaf;
 }
 
 int pl_ncell(const PlaneCtx* h) { return h->g.ncell; }

@@ -26,5 +26,7 @@ int pl_get_particles(PlaneCtx* pl, const ChEnv& env, int64_t cap, int64_t* n, do
                      double* y, double* cx, double* cy, double* cz, double* erot, int32_t* lev,
                      uint32_t* pid);
 int pl_ncell(const PlaneCtx* pl);
+// cells of a plane's grid (count or USP_EINVAL; arrays may be NULL); host only
+int pl_leaves(const usp_plane* pp, int32_t* level, int32_t* ii, int32_t* jj);
 int pl_parity(const PlaneCtx* pl);
 void pl_destroy(PlaneCtx* pl);

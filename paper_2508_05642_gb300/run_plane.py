@@ -1,5 +1,5 @@
-"""Run the 2D cylinder workload (Mach-10 N2 past a half cylinder on a uniform
-grid with cut cells) through the library and print one JSON line with the
+"""Run the 2D cylinder workload (Mach-10 N2 past a half cylinder on a grid
+with cut cells, uniform or refined about the body) through the library and print one JSON line with the
 particle counts, the status word, the counters and the device time per step.
 
     python -m paper_2508_05642_gb300.run_plane --steps 64 --nx 600 --ny 400
@@ -29,8 +29,7 @@ def surface_coefficients(acc, plane: dict, species: dict, dt: float) -> dict:
     (theta = 180 deg - phi on the upper half), the drag per unit length of
     the whole cylinder (twice the half body's, the lower half being the
     mirror image across the symmetry plane) and the peak heat flux."""
-    nx, ny = int(plane["nx"]), int(plane["ny"])
-    ncell = nx * ny
+    ncell = usp.usp_plane_leaves(plane)
     steps = acc[ncell * 12]
     s = np.asarray(acc[ncell * 12 + 2:ncell * 12 + 2 + 4 * usp.USP_NSURF]).reshape(-1, 4)
     nb = len(s)
@@ -74,12 +73,13 @@ def main(argv=None):
     ap.add_argument("--eager", action="store_true", help="no CUDA graph replay")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--sample", type=int, default=0, help="sampled steps after the timed ones")
-    ap.add_argument("--case", choices=("mach10", "paper"), default="mach10",
+    ap.add_argument("--case", choices=("mach10", "paper", "paper-refined"), default="mach10",
                     help="mach10: the 0.1 m cylinder benchmark grid (--nx/--ny/--ppc); paper: "
-                         "the parameters of Sec. 5.C on its coarse Level 1 grid (--ppc)")
+                         "the parameters of Sec. 5.C on its coarse Level 1 grid (--ppc); "
+                         "paper-refined: the same with its Level 2 and Level 3 cells")
     a = ap.parse_args(argv)
-    if a.case == "paper":
-        w = I.cylinder_paper(seed=a.seed, ppc=a.ppc)
+    if a.case.startswith("paper"):
+        w = I.cylinder_paper(seed=a.seed, ppc=a.ppc, refined=a.case == "paper-refined")
     else:
         w = I.cylinder_flow(seed=a.seed, nx=a.nx, ny=a.ny, ppc=a.ppc)
     dt = w.dt_over_tau_c * usp.usp_tau_c(w.species, w.plane["n_inf"], w.plane["T_inf"])

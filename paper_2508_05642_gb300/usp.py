@@ -41,7 +41,7 @@ EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogene
             "usp_get_particles", "usp_set_particles", "usp_step_host", "usp_status", "usp_sync",
             "usp_info", "usp_tuning", "usp_set_variant", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
             "usp_moments_noalloc", "usp_init_channel", "usp_channel_sample",
-            "usp_channel_read", "usp_channel_get_particles", "usp_init_plane", "usp_plane_count",
+            "usp_channel_read", "usp_channel_get_particles", "usp_init_plane", "usp_plane_leaves", "usp_plane_count",
             "usp_plane_get_particles", "usp_sample", "usp_sample_read", "usp_destroy"]
 USP_METHOD_USP_FPM, USP_METHOD_FPM = 0, 1
 USP_NSURF = 180
@@ -74,7 +74,8 @@ class usp_plane(C.Structure):
                 ("cyl_yc", C.c_double), ("cyl_r", C.c_double), ("T_wall", C.c_double),
                 ("n_inf", C.c_double), ("T_inf", C.c_double), ("U_inf", C.c_double),
                 ("bc", C.c_int * 4), ("inflow", C.c_int * 4), ("F_num", C.c_double),
-                ("depth", C.c_double), ("reconstruct", C.c_int)]
+                ("depth", C.c_double), ("reconstruct", C.c_int), ("amr_levels", C.c_int),
+                ("amr_r2", C.c_double), ("amr_r3", C.c_double)]
 
 
 class usp_config(C.Structure):
@@ -143,6 +144,8 @@ def lib():
                                          _D, C.c_int64, C.c_int64, _D, _D, _D, _D, _D, _D, _I32,
                                          _U32]
             L.usp_plane_count.argtypes = [_CTX, _I64, _U32]
+            L.usp_plane_leaves.argtypes = [C.POINTER(usp_plane), C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
             L.usp_plane_get_particles.argtypes = [_CTX, C.c_int64, _I64, _D, _D, _D, _D, _D, _D,
                                                   _I32, _U32]
             L.usp_sample.argtypes = [_CTX, C.c_int]
@@ -305,6 +308,33 @@ def usp_channel_get_particles(ctx: Context):
     return y, cx, cy, cz, er, lev, pid
 
 
+def make_plane(plane: dict) -> usp_plane:
+    """usp_plane from a dict of its fields (refinement fields default to the
+    uniform grid)."""
+    pl = usp_plane()
+    for k, _ in usp_plane._fields_:
+        if k in ("bc", "inflow"):
+            getattr(pl, k)[:] = list(plane[k])
+        elif k.startswith("amr_"):
+            setattr(pl, k, plane.get(k, 0))
+        else:
+            setattr(pl, k, plane[k])
+    return pl
+
+
+def usp_plane_leaves(plane: dict, arrays: bool = False):
+    """Cell count of a plane's grid, or with ``arrays`` (level, ii, jj) per
+    cell (usp_plane_leaves)."""
+    pl = make_plane(plane)
+    n = lib().usp_plane_leaves(C.byref(pl), None, None, None)
+    _check(n if n < 0 else 0, "usp_plane_leaves")
+    if not arrays:
+        return n
+    lv, ii, jj = (np.zeros(n, dtype=np.int32) for _ in range(3))
+    lib().usp_plane_leaves(C.byref(pl), _p(lv, C.c_int32), _p(ii, C.c_int32), _p(jj, C.c_int32))
+    return lv, ii, jj
+
+
 def usp_init_plane(species: dict, plane: dict, dt: float, area_frac, x, y, cx, cy, cz, erot, lev,
                    capacity: int, pid=None, *, precision=USP_FP32, seed=1, step0=0, stream=None,
                    use_graph=True, allocator=None) -> Context:
@@ -327,12 +357,8 @@ def usp_init_plane(species: dict, plane: dict, dt: float, area_frac, x, y, cx, c
         a_fn, f_fn, user = allocator
         cfg.alloc, cfg.free_, cfg.alloc_user = a_fn, f_fn, user
         keep += [a_fn, f_fn]
-    pl = usp_plane()
-    for k, _ in usp_plane._fields_:
-        if k in ("bc", "inflow"):
-            getattr(pl, k)[:] = list(plane[k])
-        else:
-            setattr(pl, k, plane[k])
+    pl = make_plane(plane)
+    ncell = usp_plane_leaves(plane)
     sp = make_species(species)
     h = _CTX()
     n = len(x)
@@ -341,7 +367,7 @@ def usp_init_plane(species: dict, plane: dict, dt: float, area_frac, x, y, cx, c
                               _p(y, C.c_double), _p(cx, C.c_double), _p(cy, C.c_double),
                               _p(cz, C.c_double), _p(erot, C.c_double), _p(lev, C.c_int32), pidp)
     _check(rc, "usp_init_plane")
-    ctx = Context(h, n, int(plane["nx"]) * int(plane["ny"]), precision, keep, kind=2)
+    ctx = Context(h, n, ncell, precision, keep, kind=2)
     ctx.capacity = int(capacity)
     return ctx
 

@@ -65,3 +65,26 @@ def test_invalid_arguments_rejected_before_device_work():
     bad = dict(sp, m=0.0)
     with pytest.raises(usp.USPError):
         usp.usp_init_homogeneous(bad, [0, 4], [1e23], [1e-9], z, z, z, z, lev)
+
+
+@pytest.mark.parametrize("levels,r2,r3,r", [(0, 0.0, 0.0, 0.1), (2, 0.3, 0.0, 0.0),
+                                            (3, 0.3, 0.2, 0.1524), (3, 0.24, 0.155, 0.1524)])
+def test_plane_leaves_on_the_host_match_the_oracle(levels, r2, r3, r):
+    """The library's refined-grid layout (host code, no GPU) is the oracle's:
+    same cells, levels and coordinates, in the same order; a grid whose
+    neighbouring levels differ by two is rejected by both."""
+    from oracle import oracle as O
+    d = dict(nx=64, ny=48, x0=-0.4, x1=0.4, y0=0.0, y1=0.6, cyl_xc=0.0, cyl_yc=0.0, cyl_r=r,
+             amr_levels=levels, amr_r2=r2, amr_r3=r3)
+    lv, ii, jj = usp.usp_plane_leaves(dict(d, T_wall=500.0, n_inf=1e21, T_inf=200.0, U_inf=0.0,
+                                           bc=(0, 0, 1, 0), inflow=(1, 0, 0, 1), F_num=1.0,
+                                           depth=1.0, reconstruct=1), arrays=True)
+    olv, oii, ojj = O.plane_leaves(O.plane(**d))
+    for a, b in zip((lv, ii, jj), (olv, oii, ojj)):
+        np.testing.assert_array_equal(a, b)
+    bad = dict(d, amr_levels=3, amr_r2=0.2, amr_r3=0.2)
+    assert O.plane_nleaf(O.plane(**bad)) == -1
+    with pytest.raises(usp.USPError):
+        usp.usp_plane_leaves(dict(bad, T_wall=500.0, n_inf=1e21, T_inf=200.0, U_inf=0.0,
+                                  bc=(0, 0, 1, 0), inflow=(1, 0, 0, 1), F_num=1.0, depth=1.0,
+                                  reconstruct=1))

@@ -170,7 +170,7 @@ def test_refined_neighbour_is_the_count_weighted_average():
                 for b in (0, 1) for a in (0, 1)]
     af[t] = 1.0
     af[quarters] = 1.0              # ... but the four finer leaves on the right
-    Nq = np.array([1, 3, 2, 7])
+    Nq = np.array([2, 3, 5, 7])
     counts[quarters] = Nq
     F = np.zeros((n, O.NFIELD))
     F[t] = 10.0
@@ -184,6 +184,11 @@ def test_refined_neighbour_is_the_count_weighted_average():
     # left half: the right square replaces the unusable left one (one-sided)
     out = O.plane_reconstruct(pl, counts, af, F, int(t), xc - 0.3 * dx, yc)
     np.testing.assert_allclose(out, F[t] + (P - F[t]) * (-0.3), rtol=1e-13)
+    # a finer cell with a single particle has no stress or temperature: the
+    # square is unusable and the x slope vanishes
+    counts[quarters[2]] = 1
+    out = O.plane_reconstruct(pl, counts, af, F, int(t), xc + 0.3 * dx, yc)
+    np.testing.assert_allclose(out, F[t], rtol=1e-13)
 
 
 # ---- whole steps -------------------------------------------------------------
