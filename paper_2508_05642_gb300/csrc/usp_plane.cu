@@ -755,15 +755,28 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
 // (whole, two particles or more).  One launch per level, coarsest first, so that
 // a coarser neighbour's record is complete when a finer cell reads it.
 // ---------------------------------------------------------------------------
+// The cell holding the centre of the level-L square (I, J) (integer
+// coordinates at level L, inside the domain): the point location of that
+// centre in integer form.  A centre never lies on the edge of a cell of level
+// L or coarser; where it is the common corner of finer cells, any of them
+// stands for "finer" (here the one the >= rule of the point location takes).
+__device__ __forceinline__ int leaf_at(const PlGeom& g, int L, int I, int J) {
+  const int c = (J >> (L - 1)) * g.nx + (I >> (L - 1));
+  if (g.l2_first[4 * c] < 0) return g.l1_first[c];
+  const int k = L == 1 ? 3 : ((((J >> (L - 2)) & 1) << 1) | ((I >> (L - 2)) & 1));
+  const int l = g.l2_first[4 * c + k];
+  if (!g.l2_ref[4 * c + k]) return l;
+  return L <= 2 ? l + 3 : l + (((J & 1) << 1) | (I & 1));
+}
+
 template <typename T>
 __device__ bool pl_region(const PlGeom& g, const PlParams<T>* __restrict__ prm,
                           const T* __restrict__ fT, const int* __restrict__ usable_c,
                           const long long* __restrict__ off, int lvl, int ii, int jj, int di,
                           int dj, double h, double k, T* val) {
-  const double cx = rn_add(g.x0, rn_mul((double)(ii + di) + 0.5, h));
-  const double cy = rn_add(g.y0, rn_mul((double)(jj + dj) + 0.5, k));
-  if (!(cx > g.x0 && cx < g.x1 && cy > g.y0 && cy < g.y1)) return false;
-  const int l = plane_cell<double>(g, cx, cy);
+  const int I = ii + di, J = jj + dj;
+  if (I < 0 || J < 0 || I >= (g.nx << (lvl - 1)) || J >= (g.ny << (lvl - 1))) return false;
+  const int l = leaf_at(g, lvl, I, J);
   const int ll = g.lvl[l];
   if (ll == lvl) {
     if (!usable_c[l]) return false;
@@ -774,9 +787,7 @@ __device__ bool pl_region(const PlGeom& g, const PlParams<T>* __restrict__ prm,
     int q[4];
     long long nq[4], ns = 0;
     for (int a = 0; a < 4; ++a) {
-      const double px = rn_add(cx, rn_mul((a & 1) ? 0.25 : -0.25, h));
-      const double py = rn_add(cy, rn_mul((a >> 1) ? 0.25 : -0.25, k));
-      q[a] = plane_cell<double>(g, px, py);
+      q[a] = leaf_at(g, lvl + 1, 2 * I + (a & 1), 2 * J + (a >> 1));
       if (g.lvl[q[a]] != lvl + 1 || !usable_c[q[a]]) return false;
       nq[a] = off[q[a] + 1] - off[q[a]];
       ns += nq[a];
@@ -790,6 +801,8 @@ __device__ bool pl_region(const PlGeom& g, const PlParams<T>* __restrict__ prm,
   }
   if (!usable_c[l]) return false;
   const PlParams<T>& C = prm[l];
+  const double cx = rn_add(g.x0, rn_mul((double)I + 0.5, h));
+  const double cy = rn_add(g.y0, rn_mul((double)J + 0.5, k));
   const T ex = (T)cx - C.xc, ey = (T)cy - C.yc;
   const int sx = ex >= T(0) ? 1 : 0, sy = ey >= T(0) ? 1 : 0;
   for (int f = 0; f < kNF; ++f)
@@ -797,13 +810,14 @@ __device__ bool pl_region(const PlGeom& g, const PlParams<T>* __restrict__ prm,
   return true;
 }
 
+// blocks: the kParamBlock-cell blocks holding cells of this level
 template <typename T>
-__global__ void pl_params_amr(PlGeom g, int recon, int level,
+__global__ void pl_params_amr(PlGeom g, int recon, int level, const int* __restrict__ blocks,
                               const ChCellT<double>* __restrict__ cells, const T* __restrict__ fT,
                               const int* __restrict__ usable_c, const long long* __restrict__ off,
                               PlParams<T>* __restrict__ prm, Species sp) {
   __shared__ PlParams<T> buf[kParamBlock];
-  const int c0 = blockIdx.x * kParamBlock;
+  const int c0 = blocks[blockIdx.x] * kParamBlock;
   const int c = c0 + threadIdx.x;
   const int nb = min(kParamBlock, g.ncell - c0);
   if (c < g.ncell && g.lvl[c] == level) {
@@ -1200,6 +1214,8 @@ struct PlaneCtx {
   long long* off;
   double* af;
   double* afv;              // af / 4^(level-1): the cell volume over dx dy depth
+  int* blk_lv;              // refined grid: per level the stencil blocks holding its cells
+  int blk_off[4], nblk_lv[4];
   PlCount* cnt;
   ChCellT<double>* cells;
   float* pend;              // FP32 copy of the pending rescale (Un, Us, s, r) per cell
@@ -1395,9 +1411,10 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
         h->g, h->recon, h->cells, (const T*)h->fT, h->usable_c, (PlParams<T>*)h->prm, env.sp);
   else
     for (int L = 1; L <= h->g.levels; ++L)
-      pl_params_amr<T><<<(ncell + kParamBlock - 1) / kParamBlock, kParamBlock, 0, s>>>(
-          h->g, h->recon, L, h->cells, (const T*)h->fT, h->usable_c, h->off,
-          (PlParams<T>*)h->prm, env.sp);
+      if (h->nblk_lv[L] > 0)
+        pl_params_amr<T><<<h->nblk_lv[L], kParamBlock, 0, s>>>(
+            h->g, h->recon, L, h->blk_lv + h->blk_off[L], h->cells, (const T*)h->fT,
+            h->usable_c, h->off, (PlParams<T>*)h->prm, env.sp);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 1, 0);
   if (prof) prof(env.owner, 0, 1);
@@ -1425,8 +1442,13 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
 }  // namespace
 
 int pl_kernels_per_step(const PlaneCtx* h) {
-  return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 2 + 2 +
-         (h->g.levels < 2 ? 1 : h->g.levels) + 1 + 2 + (h->sampling ? 1 : 0);
+  int params = 1;
+  if (h->g.levels >= 2) {
+    params = 0;
+    for (int L = 1; L <= h->g.levels; ++L) params += h->nblk_lv[L] > 0 ? 1 : 0;
+  }
+  return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 2 + 2 + params + 1 + 2 +
+         (h->sampling ? 1 : 0);
 }
 
 int pl_launch_step(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
@@ -1549,6 +1571,23 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
     g.lii = (const int*)A(sizeof(int) * ncell);
     g.ljj = (const int*)A(sizeof(int) * ncell);
   }
+  // per level the stencil blocks (kParamBlock consecutive cells) holding its cells
+  std::vector<int> blk;
+  if (G.levels >= 2) {
+    const int nb = (ncell + kParamBlock - 1) / kParamBlock;
+    for (int L = 1; L <= 3; ++L) {
+      h->blk_off[L] = (int)blk.size();
+      if (L <= G.levels)
+        for (int b = 0; b < nb; ++b) {
+          bool has = false;
+          for (int c = b * kParamBlock; c < std::min(ncell, (b + 1) * kParamBlock) && !has; ++c)
+            has = G.lvl[c] == L;
+          if (has) blk.push_back(b);
+        }
+      h->nblk_lv[L] = (int)blk.size() - h->blk_off[L];
+    }
+    h->blk_lv = (int*)A(sizeof(int) * std::max<size_t>(1, blk.size()));
+  }
   h->cnt = (PlCount*)A(sizeof(PlCount));
   h->cells = (ChCellT<double>*)A(sizeof(ChCellT<double>) * ncell);
   h->pend = (float*)A(sizeof(float) * 8 * ncell);
@@ -1563,7 +1602,8 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->mout = (double*)A(sizeof(double) * USP_NMOM * ncell);
   h->dstep = (long long*)A(sizeof(long long));
   bool ok = h->keycell && h->bh && h->tot && h->face_off && h->off && h->af && h->afv && h->cnt &&
-            (G.levels < 2 || (g.l1_first && g.l2_first && g.l2_ref && g.lvl && g.lii && g.ljj)) &&
+            (G.levels < 2 || (g.l1_first && g.l2_first && g.l2_ref && g.lvl && g.lii && g.ljj &&
+                              h->blk_lv)) &&
             h->cells && h->pend && h->fT && h->usable_c && h->prm && h->sums && h->acc && h->macc && h->mout && h->dstep;
   for (int k = 0; k < 2; ++k) {
     for (int q = 0; q < 6; ++q) ok = ok && h->st[k][q];
@@ -1636,6 +1676,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
     cok = cok && up(g.lvl, G.lvl.data(), sizeof(int) * ncell);
     cok = cok && up(g.lii, G.lii.data(), sizeof(int) * ncell);
     cok = cok && up(g.ljj, G.ljj.data(), sizeof(int) * ncell);
+    if (!blk.empty()) cok = cok && up(h->blk_lv, blk.data(), sizeof(int) * blk.size());
   }
   cok = cok && cudaMemcpyAsync(h->cnt, &c0, sizeof(PlCount), cudaMemcpyHostToDevice, s) == cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->cells, hc.data(), sizeof(ChCellT<double>) * ncell,
