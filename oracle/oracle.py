@@ -121,7 +121,7 @@ class Plane(C.Structure):
                 ("n_inf", C.c_double), ("T_inf", C.c_double), ("U_inf", C.c_double),
                 ("bc", C.c_int * 4), ("inflow", C.c_int * 4), ("F_num", C.c_double),
                 ("depth", C.c_double), ("reconstruct", C.c_int), ("amr_levels", C.c_int),
-                ("amr_r2", C.c_double), ("amr_r3", C.c_double)]
+                ("amr_r2", C.c_double), ("amr_r3", C.c_double), ("method", C.c_int)]
 
 
 def plane(**kw) -> Plane:

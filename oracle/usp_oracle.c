@@ -1779,6 +1779,7 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
     double* cellT = (double*)malloc(sizeof(double) * 3 * ncell);
     int64_t* counts = (int64_t*)malloc(sizeof(int64_t) * ncell);
     orc_coeffs* cc = (orc_coeffs*)malloc(sizeof(orc_coeffs) * ncell);
+    orc_fpm* fcs = pl->method == 1 ? (orc_fpm*)malloc(sizeof(orc_fpm) * ncell) : NULL;
     int* ok = (int*)malloc(sizeof(int) * ncell);
     int* cellof = (int*)malloc(sizeof(int) * (cap > 0 ? cap : 1));
     int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (ncell + 1));
@@ -1897,6 +1898,17 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
             double vol = area_frac[c] * (dx / sc) * (dy / sc) * pl->depth;
             if (!(vol > 0.0)) continue;
             double nd = N * pl->F_num / vol;
+            if (fcs) {
+                /* the plain FPM method: per-cell coefficients of Sec. 2.B */
+                if (orc_fpm_coeffs(sp, nd, dt, Fc[3], Fc[4], Fc[5], &fcs[c]) != 0) {
+                    *flags |= ORC_F_A_NONPOS;
+                    status = -1;
+                    continue;
+                }
+                if (fcs[c].clamped) { *flags |= ORC_F_TREL_CLAMP; counters[ORC_C_TREL_CLAMP] += 1; }
+                ok[c] = 1;
+                continue;
+            }
             if (orc_cell_coeffs(sp, nd, dt, Fc[3], Fc[4], Fc[5], &cc[c]) != 0) {
                 *flags |= ORC_F_A_NONPOS;
                 status = -1;
@@ -1910,6 +1922,15 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
             if (!ok[c]) continue;
             const double* Fc = &F[c * NFIELD];
             for (int64_t j = cell_off[c]; j < cell_off[c + 1]; ++j) {
+                if (fcs) {
+                    /* FPM: the cell values at every particle (first order) */
+                    double G[4], u5, u6, cv[3] = { cx[j], cy[j], cz[j] };
+                    particle_draws(seed, pid[j], step, form, G, &u5, &u6);
+                    orc_collide_particle_fpm(sp, form, &fcs[c], Fc, Fc + 6, G, seed, pid[j], step,
+                                             cv, &erot[j], &lev[j], flags, counters);
+                    cx[j] = cv[0]; cy[j] = cv[1]; cz[j] = cv[2];
+                    continue;
+                }
                 double f[NFIELD];
                 if (pl->reconstruct) {
                     plane_reconstruct_g(pl, &grid, counts, area_frac, F, c, x[j], y[j], f);
@@ -1932,7 +1953,8 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
             if (!ok[c]) continue;
             conserve_cell(sp, seed, (uint32_t)c, step, cell_off[c], cell_off[c + 1],
                           1.5 * R * cellT[3 * c], R * cellT[3 * c + 1], orc_e_vib(sp, cellT[3 * c + 2]),
-                          &F[c * NFIELD], cc[c].e_rot_tgt, cc[c].e_vib_tgt, cx, cy, cz, erot, lev,
+                          &F[c * NFIELD], fcs ? fcs[c].e_rot_tgt : cc[c].e_rot_tgt,
+                          fcs ? fcs[c].e_vib_tgt : cc[c].e_vib_tgt, cx, cy, cz, erot, lev,
                           flags, counters);
         }
         /* 7. time-average sums */
@@ -1951,7 +1973,7 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
         }
     }
     *n_io = n;
-    free(F); free(cellT); free(counts); free(cc); free(ok); free(cellof); free(pos);
+    free(F); free(cellT); free(counts); free(cc); free(fcs); free(ok); free(cellof); free(pos);
     free(tmpd); free(tmpl); free(tmpp);
     amr_free(&grid);
     return status;

@@ -220,6 +220,9 @@ typedef struct {
      * grid. */
     int    amr_levels;
     double amr_r2, amr_r3;
+    /* collision method: 0 USP-FPM (Sec. 4.D, reconstructed fields), 1 the
+     * plain FPM method (Sec. 2.B-C) with the cell values */
+    int    method;
 } orc_plane;
 
 /* Leaves of the plane's grid: count (-1 when the levels of neighbouring

@@ -316,3 +316,39 @@ def test_surface_tallies_of_a_gas_at_rest_at_the_wall_temperature():
     q = w.plane["F_num"] * m * s[:, 2] / (steps * dt) / area
     one_way = p_ideal * math.sqrt(8 * O.R(sp) * T / math.pi)
     assert abs(np.mean(q[up])) < 0.08 * one_way
+
+
+# ---- the plain FPM method on the plane (Sec. 2.B-C, cell values) ------------
+@pytest.mark.parametrize("form", [0, 1])
+def test_plane_fpm_step_is_the_homogeneous_fpm_step_in_one_cell(form):
+    """One 1 m x 1 m cell with specular sides and particles far from them (no
+    wall event in the step): the plane step with the plain FPM method is the
+    homogeneous FPM step (pinned by its own closed forms) at the cell's density
+    n = N F_num / V, particle for particle, bitwise."""
+    rng = np.random.default_rng(21)
+    w = I.cylinder_flow(nx=1, ny=1, ppc=1, cylinder=False)
+    N = 3000
+    sp_d = w.species
+    p = I.equilibrium_particles(rng, N, sp_d["m"], sp_d["theta_v"], U=(40.0, -10.0, 5.0),
+                                T_tr=3000.0, T_rot=800.0, T_vib=1500.0)
+    pl_d = dict(w.plane, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=(O.BC_SPECULAR,) * 4,
+                inflow=(0, 0, 0, 0), method=1, reconstruct=1)
+    pl_d["F_num"] = 1e23 / N
+    x = rng.uniform(0.45, 0.55, N)
+    y = rng.uniform(0.45, 0.55, N)
+    sp = O.species(**sp_d)
+    pl = O.plane(**pl_d)
+    dt = 0.7 * O.tau_c(sp, 1e23, 3000.0)
+    st = O.PlaneState(x, y, p.cx, p.cy, p.cz, p.erot, p.lev, N + 16)
+    _, fl, cnt = O.plane_step(sp, form, 9, 4, 1, pl, np.ones(1), dt, st)
+    assert cnt[O.C_WALL_HITS] == 0 and st.n == N
+    hs = O.State.from_arrays(p.cx, p.cy, p.cz, p.erot, p.lev)
+    O.homog_step_fpm(sp, form, 9, 4, 1, np.array([0, N]), np.array([1e23]), np.array([dt]), hs)
+    for a, b in ((st.cx, hs.cx), (st.cy, hs.cy), (st.cz, hs.cz), (st.erot, hs.erot)):
+        np.testing.assert_array_equal(a[:N], b)
+    np.testing.assert_array_equal(st.lev[:N], hs.lev)
+    # and it differs from the USP-FPM step of the same cell
+    pl2 = O.plane(**dict(pl_d, method=0))
+    st2 = O.PlaneState(x, y, p.cx, p.cy, p.cz, p.erot, p.lev, N + 16)
+    O.plane_step(sp, form, 9, 4, 1, pl2, np.ones(1), dt, st2)
+    assert not np.array_equal(st2.cx[:N], hs.cx)
