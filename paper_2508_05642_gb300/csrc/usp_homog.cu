@@ -2139,7 +2139,7 @@ int usp_init_plane(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
                    const double* h_cy, const double* h_cz, const double* h_erot,
                    const int32_t* h_lev, const uint32_t* h_pid) {
   if (!out || !sp || !cfg || !pl) return USP_EINVAL;
-  if (cfg->method != USP_METHOD_USP_FPM) return USP_ENOTSUP;
+  if (cfg->method != USP_METHOD_USP_FPM && cfg->method != USP_METHOD_FPM) return USP_EINVAL;
   if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64) return USP_EINVAL;
   if (!(sp->m > 0) || !(sp->d_ref > 0) || !(sp->T_ref > 0) || !(sp->c_alpha > 0) ||
       !(sp->theta_v > 0))
@@ -2151,6 +2151,7 @@ int usp_init_plane(usp_ctx** out, const usp_species* sp, const usp_config* cfg,
   c->pl = nullptr;
   c->cfg = *cfg;
   c->sp = to_dev(sp);
+  c->sp.method = cfg->method;
   c->precision = cfg->precision;
   c->ncell = 0;
   c->nparticles = 0;

@@ -95,9 +95,16 @@ struct PlParams {
   T F[kNF];
   // the bilinear polynomial of each quadrant (sx, sy = 0 below / 1 at or
   // above the centroid): f = F + gx[sx] dx + gy[sy] dy + gxy[2 sy + sx] dx dy
-  T gx[2][kNF], gy[2][kNF], gxy[4][kNF];
+  T gx[2][kNF], gy[2][kNF];
+  union {
+    T gxy[4][kNF];
+    // the plain FPM method (cell values, no polynomial): alpha, sqrt(1 -
+    // alpha^2) L, the rotational square-form constants and the level rates
+    struct { T as, Lp[6], a_rot, sqrt_a, lam_up, lam_dn; } fpm;
+  };
   int active, pad;
 };
+constexpr int kFpmRec = 11;   // doubles per cell of the FPM coefficient pass
 
 __device__ __forceinline__ int grid_threads() { return gridDim.x * blockDim.x; }
 
@@ -670,6 +677,57 @@ __global__ void pl_gather(PlCount* __restrict__ cnt, int ncell,
 }
 
 // ---------------------------------------------------------------------------
+// the plain FPM method (Sec. 2.B-C) per cell, FP64: alpha = exp(-dt / tau),
+// the Cholesky factor of tau D_tr from the cell's stress, the rotational
+// square-form constants, the Gillespie rates and the conservation targets
+// (the first-order method takes the cell values at every particle)
+// ---------------------------------------------------------------------------
+__global__ void ch_coeffs_fpm(int ncell, double F_num, double vol, const double* __restrict__ afv,
+                              double dt, ChCellT<double>* __restrict__ cells,
+                              double* __restrict__ rec, Species sp, uint32_t* flags,
+                              unsigned long long* counters) {
+  __shared__ BlockTally tal;
+  tally_init(tal);
+  const double R = gasR(sp);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    ChCellT<double>& cs = cells[c];
+    if (!cs.active) continue;
+    const double v = afv[c] * vol;
+    if (!(v > 0.0)) {
+      cs.active = 0;
+      continue;
+    }
+    cs.n = (double)cs.N * F_num / v;
+    const FpmCell f = fpm_cell(sp, cs.n, dt, cs.Pi, cs.Ttr, cs.Trot, cs.Tvib);
+    if (!f.ok) {
+      tally_or(tal, (uint32_t)F_A_NONPOS);
+      cs.active = 0;
+      continue;
+    }
+    cs.alpha = f.alpha;
+    cs.e_rot_tgt = f.e_rot_tgt;
+    cs.e_vib_tgt = f.e_vib_tgt;
+    if (f.fixed) tally_add(tal, C_CHOL_FIX, 1ull);
+    if (f.nu_zero) tally_add(tal, C_NU_ZERO, 1ull);
+    if (f.failed) tally_or(tal, (uint32_t)F_CHOL_FAIL_AFTER_FIX);
+    if (f.clamped) {
+      tally_or(tal, (uint32_t)F_TREL_CLAMP);
+      tally_add(tal, C_TREL_CLAMP, 1ull);
+    }
+    const double a = f.alpha, oma2 = 1.0 - a * a, sq = sqrt(oma2);
+    const double arot = R * f.Trot_rel * oma2 / 2.0;
+    double* o = rec + (size_t)c * kFpmRec;
+    o[0] = a;
+    for (int i = 0; i < 6; ++i) o[1 + i] = sq * f.L[i];
+    o[7] = arot;
+    o[8] = sqrt(arot);
+    o[9] = f.lam_up;
+    o[10] = f.lam_dn;
+  }
+  tally_flush(tal, flags, counters);
+}
+
+// ---------------------------------------------------------------------------
 // reconstruction stencils (Sec. 3.B on the uniform grid): for each side of
 // the centroid the x and y neighbour used (that side's if usable, else the
 // opposite one, else none) and the quadrant's diagonal when usable
@@ -677,7 +735,8 @@ __global__ void pl_gather(PlCount* __restrict__ cnt, int ncell,
 template <typename T>
 __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict__ cells,
                           const T* __restrict__ fT, const int* __restrict__ usable_c,
-                          PlParams<T>* __restrict__ prm, Species sp) {
+                          PlParams<T>* __restrict__ prm, Species sp,
+                          const double* __restrict__ fpm) {
   // a thread builds its cell's record in shared memory; the block then copies
   // its kParamBlock records out as consecutive 8-byte words (coalesced), where
   // one thread storing a ~0.5 KB record would scatter every store
@@ -698,6 +757,15 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
   P.yc = (T)(g.y0 + (j + 0.5) * g.dy);
   const T* f = fT + (size_t)c * kNF;
   for (int k = 0; k < kNF; ++k) P.F[k] = f[k];
+  if (fpm) {
+    // the plain FPM method: cell values, its per-cell constants
+    for (int k = 0; k < kNF; ++k) { P.gx[0][k] = P.gx[1][k] = P.gy[0][k] = P.gy[1][k] = T(0); }
+    const double* r = fpm + (size_t)c * kFpmRec;
+    P.fpm.as = (T)r[0];
+    for (int k = 0; k < 6; ++k) P.fpm.Lp[k] = (T)r[1 + k];
+    P.fpm.a_rot = (T)r[7]; P.fpm.sqrt_a = (T)r[8];
+    P.fpm.lam_up = (T)r[9]; P.fpm.lam_dn = (T)r[10];
+  } else {
   auto usable = [&](int ii, int jj) {
     return recon && ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && usable_c[jj * g.nx + ii];
   };
@@ -735,6 +803,7 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
     } else {
       for (int k = 0; k < kNF; ++k) P.gxy[q][k] = T(0);
     }
+  }
   }
   }
   __syncthreads();
@@ -922,7 +991,29 @@ constexpr size_t pl_collide_smem() {
 // stencil record and particles and of cell c + 2W's place and size are in
 // flight, so the DRAM latency of a cell overlaps the previous cell's
 // arithmetic.
+// the plain FPM method for one particle (Sec. 2.C): Gorji's velocity update
+// and the Milstein square form for eps_rot with the cell values, Gillespie's
+// direct method for the level
 template <typename T>
+__device__ __forceinline__ int fpm_particle(const PlParams<T>& P, T& v0, T& v1, T& v2, T& en,
+                                            int l0, uint32_t id, uint32_t step,
+                                            const PhiloxRoundKeys& rk, uint32_t& fl) {
+  const U4 w = philox4x32_10(id, step, PTAG_NORMALS, 0u, rk);
+  T g0, g1, g2, g3;
+  box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
+  box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
+  const T a = P.fpm.as;
+  const T d0 = v0 - P.F[0], d1 = v1 - P.F[1], d2 = v2 - P.F[2];
+  v0 = P.F[0] + a * d0 + P.fpm.Lp[0] * g0;
+  v1 = P.F[1] + a * d1 + (P.fpm.Lp[1] * g0 + P.fpm.Lp[2] * g1);
+  v2 = P.F[2] + a * d2 + (P.fpm.Lp[3] * g0 + P.fpm.Lp[4] * g1 + P.fpm.Lp[5] * g2);
+  const T root = sqrt(en) * a + P.fpm.sqrt_a * g3;
+  en = P.fpm.a_rot + root * root;
+  return gillespie<T>(l0, P.fpm.lam_up, P.fpm.lam_dn, id, step, rk, fl);
+}
+
+// METHOD 0: USP-FPM with the reconstructed fields; 1: the plain FPM method
+template <typename T, int METHOD>
 __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<double>* __restrict__ cells,
                            const PlParams<T>* __restrict__ prm, const T* __restrict__ x,
                            const T* __restrict__ y, T* __restrict__ cx, T* __restrict__ cy,
@@ -1034,22 +1125,26 @@ __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<d
           xv = x[j]; yv = y[j]; v0 = cx[j]; v1 = cy[j]; v2 = cz[j]; en = er[j];
           l0 = lev[j]; id = pid[j];
         }
-        const T ddx = xv - P.xc, ddy = yv - P.yc;
-        const int sx = ddx >= T(0) ? 1 : 0, sy = ddy >= T(0) ? 1 : 0;
-        const T dxy = ddx * ddy;
-        const T* gx = P.gx[sx];
-        const T* gy = P.gy[sy];
-        const T* gxy = P.gxy[sy * 2 + sx];
-        T f[kNF];
+        int ln;
+        if constexpr (METHOD == 1) {
+          ln = fpm_particle<T>(P, v0, v1, v2, en, l0, id, step, rk, tl.fl);
+        } else {
+          const T ddx = xv - P.xc, ddy = yv - P.yc;
+          const int sx = ddx >= T(0) ? 1 : 0, sy = ddy >= T(0) ? 1 : 0;
+          const T dxy = ddx * ddy;
+          const T* gx = P.gx[sx];
+          const T* gy = P.gy[sy];
+          const T* gxy = P.gxy[sy * 2 + sx];
+          T f[kNF];
 #pragma unroll
-        for (int q = 0; q < kNF; ++q) f[q] = P.F[q] + gx[q] * ddx + gy[q] * ddy + gxy[q] * dxy;
-        if (!(f[3] > T(0)) || !(f[4] > T(0)) || !(f[5] >= T(0))) {
+          for (int q = 0; q < kNF; ++q) f[q] = P.F[q] + gx[q] * ddx + gy[q] * ddy + gxy[q] * dxy;
+          if (!(f[3] > T(0)) || !(f[4] > T(0)) || !(f[5] >= T(0))) {
 #pragma unroll
-          for (int q = 0; q < kNF; ++q) f[q] = P.F[q];
-          ++nfb;
+            for (int q = 0; q < kNF; ++q) f[q] = P.F[q];
+            ++nfb;
+          }
+          ln = collide_particle_t<sizeof(T) == 4>(P, f, v0, v1, v2, en, l0, id, step, rk, tl);
         }
-        const int ln = collide_particle_t<sizeof(T) == 4>(P, f, v0, v1, v2, en, l0, id, step,
-                                                            rk, tl);
         cx[j] = v0; cy[j] = v1; cz[j] = v2; er[j] = en;
         lev[j] = ln;
         maxI = max(maxI, ln);
@@ -1215,6 +1310,7 @@ struct PlaneCtx {
   double* af;
   double* afv;              // af / 4^(level-1): the cell volume over dx dy depth
   int* blk_lv;              // refined grid: per level the stencil blocks holding its cells
+  double* fpmrec;           // the plain FPM method: kFpmRec per-cell constants (else null)
   int blk_off[4], nblk_lv[4];
   PlCount* cnt;
   ChCellT<double>* cells;
@@ -1399,16 +1495,21 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   ch_moments<T, double><<<wb, kBlk, 0, s>>>(ncell, 32, h->off, h->af, cx, cy, cz, er, h->lv[b],
                                             h->cells, env.sp, env.counters, pend, (T*)h->fT,
                                             h->usable_c);
-  if (env.precision == USP_FP32)
+  const bool fpm = h->fpmrec != nullptr;
+  if (fpm)
+    ch_coeffs_fpm<<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->afv, h->g.dt, h->cells,
+                                      h->fpmrec, env.sp, env.flags, env.counters);
+  else if (env.precision == USP_FP32)
     ch_coeffs_f32<<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->afv, h->g.dt, h->cells, env.sp,
                                       env.flags, env.counters);
   else
     ch_coeffs<double><<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->afv, h->g.dt, h->cells,
                                           env.sp, env.sp.omega, env.sp.Z_rot, env.flags,
                                           env.counters);
-  if (h->g.levels < 2)
+  if (fpm || h->g.levels < 2)
     pl_params<T><<<(ncell + kParamBlock - 1) / kParamBlock, kParamBlock, 0, s>>>(
-        h->g, h->recon, h->cells, (const T*)h->fT, h->usable_c, (PlParams<T>*)h->prm, env.sp);
+        h->g, fpm ? 0 : h->recon, h->cells, (const T*)h->fT, h->usable_c, (PlParams<T>*)h->prm,
+        env.sp, h->fpmrec);
   else
     for (int L = 1; L <= h->g.levels; ++L)
       if (h->nblk_lv[L] > 0)
@@ -1418,10 +1519,14 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 1, 0);
   if (prof) prof(env.owner, 0, 1);
-  pl_collide<T><<<h->grid_col, kBlk, pl_collide_smem<T>(), s>>>(
-      ncell, h->cells, (const PlParams<T>*)h->prm, x, y, cx, cy,
-                                    cz, er, h->lv[b], h->pd[b], h->sums, h->dstep,
-                                    philox_round_keys(env.k0, env.k1), env.flags, env.counters);
+  if (fpm)
+    pl_collide<T, 1><<<h->grid_col, kBlk, pl_collide_smem<T>(), s>>>(
+        ncell, h->cells, (const PlParams<T>*)h->prm, x, y, cx, cy, cz, er, h->lv[b], h->pd[b],
+        h->sums, h->dstep, philox_round_keys(env.k0, env.k1), env.flags, env.counters);
+  else
+    pl_collide<T, 0><<<h->grid_col, kBlk, pl_collide_smem<T>(), s>>>(
+        ncell, h->cells, (const PlParams<T>*)h->prm, x, y, cx, cy, cz, er, h->lv[b], h->pd[b],
+        h->sums, h->dstep, philox_round_keys(env.k0, env.k1), env.flags, env.counters);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 0, 0);
   if (prof) prof(env.owner, 1, 1);
@@ -1443,7 +1548,7 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
 
 int pl_kernels_per_step(const PlaneCtx* h) {
   int params = 1;
-  if (h->g.levels >= 2) {
+  if (h->g.levels >= 2 && !h->fpmrec) {
     params = 0;
     for (int L = 1; L <= h->g.levels; ++L) params += h->nblk_lv[L] > 0 ? 1 : 0;
   }
@@ -1533,7 +1638,9 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
     // the collision pass keeps one block per resident slot, each warp a
     // pipeline over its cells
     const bool f32 = env.precision == USP_FP32;
-    const void* fn = f32 ? (const void*)pl_collide<float> : (const void*)pl_collide<double>;
+    const bool m1 = env.sp.method == 1;
+    const void* fn = f32 ? (m1 ? (const void*)pl_collide<float, 1> : (const void*)pl_collide<float, 0>)
+                         : (m1 ? (const void*)pl_collide<double, 1> : (const void*)pl_collide<double, 0>);
     const int smem = (int)(f32 ? pl_collide_smem<float>() : pl_collide_smem<double>());
     int per_sm = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
@@ -1561,6 +1668,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->off = (long long*)A(sizeof(long long) * (ncell + 1));
   h->af = (double*)A(sizeof(double) * ncell);
   h->afv = h->af;
+  if (env.sp.method == 1) h->fpmrec = (double*)A(sizeof(double) * kFpmRec * (size_t)ncell);
   const int n1 = pp->nx * pp->ny;
   if (G.levels >= 2) {
     h->afv = (double*)A(sizeof(double) * ncell);
@@ -1602,6 +1710,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->mout = (double*)A(sizeof(double) * USP_NMOM * ncell);
   h->dstep = (long long*)A(sizeof(long long));
   bool ok = h->keycell && h->bh && h->tot && h->face_off && h->off && h->af && h->afv && h->cnt &&
+            (env.sp.method != 1 || h->fpmrec) &&
             (G.levels < 2 || (g.l1_first && g.l2_first && g.l2_ref && g.lvl && g.lii && g.ljj &&
                               h->blk_lv)) &&
             h->cells && h->pend && h->fT && h->usable_c && h->prm && h->sums && h->acc && h->macc && h->mout && h->dstep;

@@ -71,6 +71,8 @@ def main(argv=None):
     ap.add_argument("--ppc", type=float, default=30.0)
     ap.add_argument("--fp64", action="store_true", help="plain FP64 form (default FP32 state)")
     ap.add_argument("--eager", action="store_true", help="no CUDA graph replay")
+    ap.add_argument("--fpm", action="store_true",
+                    help="the plain FPM method (cell values) instead of USP-FPM")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--sample", type=int, default=0, help="sampled steps after the timed ones")
     ap.add_argument("--case", choices=("mach10", "paper", "paper-refined"), default="mach10",
@@ -87,7 +89,8 @@ def main(argv=None):
     prec = usp.USP_FP64 if a.fp64 else usp.USP_FP32
     ctx = usp.usp_init_plane(w.species, w.plane, dt, w.area_frac, w.x, w.y, p.cx, p.cy, p.cz,
                              p.erot, p.lev, w.capacity, precision=prec, seed=a.seed,
-                             use_graph=not a.eager)
+                             use_graph=not a.eager,
+                             method=usp.USP_METHOD_FPM if a.fpm else usp.USP_METHOD_USP_FPM)
     if a.warmup:
         usp.usp_step(ctx, a.warmup)
     usp.usp_sync(ctx)
@@ -104,7 +107,8 @@ def main(argv=None):
         usp.usp_step(ctx, a.sample)
         surf = surface_coefficients(usp.usp_sample_read(ctx), w.plane, w.species, dt)
         fl, cnt = usp.usp_status(ctx)
-    print(json.dumps({"workload": w.name, "steps": a.steps, "warmup": a.warmup,
+    print(json.dumps({"workload": w.name, "method": "FPM" if a.fpm else "USP-FPM",
+                      "steps": a.steps, "warmup": a.warmup,
                       "surface": surf,
                       "precision": "f64" if a.fp64 else "f32", "graph": not a.eager,
                       "particles": [int(n0), int(n1)], "next_id": int(nxt),

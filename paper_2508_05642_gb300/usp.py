@@ -337,8 +337,9 @@ def usp_plane_leaves(plane: dict, arrays: bool = False):
 
 def usp_init_plane(species: dict, plane: dict, dt: float, area_frac, x, y, cx, cy, cz, erot, lev,
                    capacity: int, pid=None, *, precision=USP_FP32, seed=1, step0=0, stream=None,
-                   use_graph=True, allocator=None) -> Context:
-    """Create a 2D plane context (host numpy inputs)."""
+                   use_graph=True, allocator=None, method=USP_METHOD_USP_FPM) -> Context:
+    """Create a 2D plane context (host numpy inputs); ``method`` USP_METHOD_FPM
+    runs the plain FPM method with the cell values."""
     f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
     x, y, cx, cy, cz, erot, af = f(x), f(y), f(cx), f(cy), f(cz), f(erot), f(area_frac)
     lev = np.ascontiguousarray(lev, dtype=np.int32)
@@ -352,6 +353,7 @@ def usp_init_plane(species: dict, plane: dict, dt: float, area_frac, x, y, cx, c
     cfg.step0 = step0
     cfg.stream = stream or None
     cfg.use_graph = 1 if use_graph else 0
+    cfg.method = method
     keep = []
     if allocator is not None:
         a_fn, f_fn, user = allocator
