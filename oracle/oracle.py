@@ -102,7 +102,8 @@ class FpmCoeffs(C.Structure):
 
 class Channel(C.Structure):
     _fields_ = [("ny", C.c_int), ("L", C.c_double), ("T_wall", C.c_double), ("g", C.c_double),
-                ("F_num", C.c_double), ("area", C.c_double), ("reconstruct", C.c_int)]
+                ("F_num", C.c_double), ("area", C.c_double), ("reconstruct", C.c_int),
+                ("method", C.c_int)]
 
 
 NACC = 12

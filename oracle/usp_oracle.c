@@ -1205,6 +1205,7 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
     double* cellT = (double*)malloc(sizeof(double) * 3 * ny);
     int64_t* counts = (int64_t*)malloc(sizeof(int64_t) * ny);
     orc_coeffs* cc = (orc_coeffs*)malloc(sizeof(orc_coeffs) * ny);
+    orc_fpm* fcs = ch->method == 1 ? (orc_fpm*)malloc(sizeof(orc_fpm) * ny) : NULL;
     int* ok = (int*)malloc(sizeof(int) * ny);
     int status = 0;
     for (int s = 0; s < nsteps; ++s) {
@@ -1241,6 +1242,17 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
             for (int k = 0; k < 6; ++k) Fc[6 + k] = P[k];
             cellT[3 * c] = T_tr; cellT[3 * c + 1] = T_rot; cellT[3 * c + 2] = T_vib;
             double nd = N * ch->F_num / vol;
+            if (fcs) {
+                /* the plain FPM method: per-cell coefficients of Sec. 2.B */
+                if (orc_fpm_coeffs(sp, nd, dt, T_tr, T_rot, T_vib, &fcs[c]) != 0) {
+                    *flags |= ORC_F_A_NONPOS;
+                    status = -1;
+                    continue;
+                }
+                if (fcs[c].clamped) { *flags |= ORC_F_TREL_CLAMP; counters[ORC_C_TREL_CLAMP] += 1; }
+                ok[c] = 1;
+                continue;
+            }
             if (orc_cell_coeffs(sp, nd, dt, T_tr, T_rot, T_vib, &cc[c]) != 0) {
                 *flags |= ORC_F_A_NONPOS;
                 status = -1;
@@ -1254,6 +1266,15 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
             if (!ok[c]) continue;
             const double* Fc = &F[c * NFIELD];
             for (int64_t j = cell_off[c]; j < cell_off[c + 1]; ++j) {
+                if (fcs) {
+                    /* FPM: the cell values at every particle (first order) */
+                    double G[4], u5, u6, cv[3] = { cx[j], cy[j], cz[j] };
+                    particle_draws(seed, pid[j], step, form, G, &u5, &u6);
+                    orc_collide_particle_fpm(sp, form, &fcs[c], Fc, Fc + 6, G, seed, pid[j], step,
+                                             cv, &erot[j], &lev[j], flags, counters);
+                    cx[j] = cv[0]; cy[j] = cv[1]; cz[j] = cv[2];
+                    continue;
+                }
                 double f[NFIELD];
                 if (ch->reconstruct) {
                     orc_channel_reconstruct(ch, counts, F, c, y[j], f);
@@ -1277,7 +1298,9 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
             const double* Fc = &F[c * NFIELD];
             conserve_cell(sp, seed, (uint32_t)c, step, cell_off[c], cell_off[c + 1],
                           1.5 * R * cellT[3 * c], R * cellT[3 * c + 1], orc_e_vib(sp, cellT[3 * c + 2]),
-                          Fc, cc[c].e_rot_tgt, cc[c].e_vib_tgt, cx, cy, cz, erot, lev, flags, counters);
+                          Fc, fcs ? fcs[c].e_rot_tgt : cc[c].e_rot_tgt,
+                          fcs ? fcs[c].e_vib_tgt : cc[c].e_vib_tgt, cx, cy, cz, erot, lev, flags,
+                          counters);
         }
         /* 6. time-average sums */
         if (acc) {
@@ -1295,7 +1318,7 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
             acc[ny * ORC_NACC + 1] += wall_mom;
         }
     }
-    free(F); free(cellT); free(counts); free(cc); free(ok);
+    free(F); free(cellT); free(counts); free(cc); free(fcs); free(ok);
     return status;
 }
 

@@ -175,6 +175,8 @@ typedef struct {
     double F_num;     /* real molecules per simulation particle               */
     double area;      /* cross-section normal to y [m^2]; V_cell = area * dy  */
     int    reconstruct; /* 1: first-order reconstruction (Sec. 3.B), 0: cell values */
+    int    method;    /* 0 USP-FPM (Sec. 4.D); 1 the plain FPM method (Sec. 2.B-C)
+                         with the cell values at every particle               */
 } orc_channel;
 
 /* Per-cell accumulator layout of orc_channel_step (time-average sums, FP64):

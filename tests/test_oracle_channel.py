@@ -134,3 +134,30 @@ def test_poiseuille_profile_develops():
     n = len(st.y)
     wall = acc[ch.ny * O.NACC + 1] / nav
     assert wall == pytest.approx(n * ch.g * dt, rel=0.03)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_channel_fpm_step_is_the_homogeneous_fpm_step_in_one_cell(form):
+    """One channel cell, no body force, particles far from the plates (no
+    wall event in the step): the channel step with the plain FPM method is the
+    homogeneous FPM step at the cell's density n = N F_num / (area L),
+    particle for particle, bitwise."""
+    w = I.channel_poiseuille()
+    rng = np.random.default_rng(17)
+    N = 2500
+    p = I.equilibrium_particles(rng, N, w.species["m"], w.species["theta_v"], U=(30.0, 0.0, -8.0),
+                                T_tr=2500.0, T_rot=600.0, T_vib=1200.0)
+    L = 1.0
+    F_num = 1e23 * L / N
+    ch = O.channel(ny=1, L=L, T_wall=300.0, g=0.0, F_num=F_num, area=1.0, reconstruct=1, method=1)
+    sp = O.species(**w.species)
+    dt = 0.6 * O.tau_c(sp, 1e23, 2500.0)
+    y = rng.uniform(0.45, 0.55, N)
+    st = O.ChannelState.from_arrays(y, p.cx, p.cy, p.cz, p.erot, p.lev)
+    _, fl, cnt = O.channel_step(sp, form, 5, 2, 1, ch, dt, st)
+    assert cnt[O.C_WALL_HITS] == 0
+    hs = O.State.from_arrays(p.cx, p.cy, p.cz, p.erot, p.lev)
+    O.homog_step_fpm(sp, form, 5, 2, 1, np.array([0, N]), np.array([1e23]), np.array([dt]), hs)
+    for a, b in ((st.cx, hs.cx), (st.cy, hs.cy), (st.cz, hs.cz), (st.erot, hs.erot)):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(st.lev, hs.lev)
