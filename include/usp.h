@@ -146,11 +146,11 @@ typedef struct {
   usp_alloc_fn alloc;   /* optional allocator (NULL = cudaMalloc)            */
   usp_free_fn free_;
   void* alloc_user;
-  int method;           /* USP_METHOD_*; channel contexts take only
-                           USP_METHOD_USP_FPM (USP_ENOTSUP otherwise); plane
-                           contexts run USP_METHOD_FPM with the cell values
-                           at every particle (the first-order method: no
-                           reconstruction)                                    */
+  int method;           /* USP_METHOD_*; channel and plane contexts run
+                           USP_METHOD_FPM with the cell values at every
+                           particle (the first-order method: no
+                           reconstruction); not with USP_FP64_TANGENT
+                           (USP_ENOTSUP)                                      */
 } usp_config;
 
 /* 1D channel between two fully diffuse plates at y = 0 and y = L (the

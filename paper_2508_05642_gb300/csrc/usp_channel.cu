@@ -23,6 +23,8 @@
 //   ch_sample      (while sampling) time-average sums of the post-step state
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -376,6 +378,60 @@ __global__ void ch_collide(int ny, const ChCellT<S>* __restrict__ cells,
   if (nz) atomicAdd(&counters[C_NU_ZERO], nz);
 }
 
+// the plain FPM method (Sec. 2.C) per particle with the cell values: one warp
+// per cell, per-cell sums for the conservation step as in ch_collide
+template <typename T>
+__global__ void ch_collide_fpm(int ny, const ChCellT<double>* __restrict__ cells,
+                               const double* __restrict__ rec, T* __restrict__ cx,
+                               T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
+                               int* __restrict__ lev, const uint32_t* __restrict__ pid,
+                               ChSumsT<double>* __restrict__ sums,
+                               const long long* __restrict__ dstep, const PhiloxRoundKeys rk,
+                               uint32_t* flags) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (c >= ny) return;
+  const ChCellT<double>& cs = cells[c];
+  if (!cs.active) return;
+  const uint32_t step = (uint32_t)*dstep;
+  const double* r = rec + (size_t)c * kFpmRec;
+  const T U[3] = {(T)cs.U[0], (T)cs.U[1], (T)cs.U[2]};
+  const T Lp[6] = {(T)r[1], (T)r[2], (T)r[3], (T)r[4], (T)r[5], (T)r[6]};
+  const T a = (T)r[0], a_rot = (T)r[7], sqrt_a = (T)r[8], lu = (T)r[9], ld = (T)r[10];
+  T acc[10];
+  for (int i = 0; i < 10; ++i) acc[i] = T(0);
+  double accI = 0.0;
+  int maxI = 0;
+  uint32_t fl = 0;
+  for (long long j = cs.off + lane; j < cs.off + cs.N; j += 32) {
+    T v0 = cx[j], v1 = cy[j], v2 = cz[j], en = er[j];
+    const int ln = fpm_particle<T>(U, a, Lp, a_rot, sqrt_a, lu, ld, v0, v1, v2, en, lev[j],
+                                   pid[j], step, rk, fl);
+    cx[j] = v0; cy[j] = v1; cz[j] = v2; er[j] = en;
+    lev[j] = ln;
+    maxI = max(maxI, ln);
+    const T d0 = v0 - U[0], d1 = v1 - U[1], d2 = v2 - U[2];
+    acc[0] += d0; acc[1] += d1; acc[2] += d2;
+    acc[3] += d0 * d0; acc[4] += d1 * d1; acc[5] += d2 * d2;
+    acc[6] += d0 * d1; acc[7] += d0 * d2; acc[8] += d1 * d2;
+    acc[9] += en;
+    accI += (double)ln;
+  }
+  double s[10];
+#pragma unroll
+  for (int i = 0; i < 10; ++i) s[i] = (double)wsum(acc[i]);
+  const double sI = wsum(accI);
+  const int mI = __reduce_max_sync(0xffffffffu, maxI);
+  const uint32_t fla = __reduce_or_sync(0xffffffffu, fl);
+  if (lane != 0) return;
+  ChSumsT<double>& sm = sums[c];
+  for (int i = 0; i < 10; ++i) sm.v[i] = s[i];
+  sm.I = (unsigned long long)(long long)llrint(sI);
+  sm.net = 0;
+  sm.maxI = mI;
+  if (fla) atomicOr(flags, fla);
+}
+
 // time-average sums of the post-step state, binned by its cell
 // (gradient form: block 0 holds the sums, blocks 1..3 their derivatives)
 template <typename T, typename S>
@@ -497,6 +553,7 @@ struct ChannelCtx {
   double* mout;
   long long* dstep;
   int sampling;
+  double* fpmrec;           // the plain FPM method: kFpmRec per-cell constants (else null)
 };
 
 namespace {
@@ -561,6 +618,20 @@ int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
   const int cb = (h->ny + 127) / 128;
   ch_moments<T, S><<<wb, 128, 0, s>>>(h->ny, 1, h->off, nullptr, cx, cy, cz, er, h->lv[b], cells,
                                       env.sp, env.counters, nullptr, (T*)nullptr, nullptr);
+  if constexpr (std::is_same<S, double>::value) {
+    if (h->fpmrec) {
+      // the plain FPM method: cell values at every particle, no reconstruction
+      ch_coeffs_fpm<<<cb, 128, 0, s>>>(h->ny, h->Fnum, h->area * h->dy, nullptr, h->dt, cells,
+                                       h->fpmrec, env.sp, env.flags, env.counters);
+      CHK(cudaGetLastError());
+      if (prof) prof(env.owner, 1, 0);
+      if (prof) prof(env.owner, 0, 1);
+      ch_collide_fpm<T><<<wb, 128, 0, s>>>(h->ny, cells, h->fpmrec, cx, cy, cz, er, h->lv[b],
+                                           h->pd[b], sums, h->dstep,
+                                           philox_round_keys(env.k0, env.k1), env.flags);
+    }
+  }
+  if (!h->fpmrec) {
   ch_coeffs<S><<<cb, 128, 0, s>>>(h->ny, h->Fnum, h->area * h->dy, nullptr, h->dt, cells, env.sp,
                                   omega, zrot, env.flags, env.counters);
   ch_recon<T, S><<<cb, 128, 0, s>>>(h->ny, h->dy, h->recon, h->dt, cells, (ChParams<T>*)h->prm,
@@ -571,6 +642,7 @@ int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
   ch_collide<T, S><<<wb, 128, 0, s>>>(h->ny, cells, (const ChParams<T>*)h->prm, y, cx, cy, cz,
                                       er, h->lv[b], h->pd[b], sums, h->dstep,
                                       philox_round_keys(env.k0, env.k1), env.flags, env.counters);
+  }
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 0, 0);
   if (prof) prof(env.owner, 1, 1);
@@ -591,7 +663,7 @@ int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
 }  // namespace
 
 int ch_kernels_per_step(const ChannelCtx* h) {
-  return 2 + 3 * h->passes + 8 + (h->sampling ? 1 : 0);
+  return 2 + 3 * h->passes + (h->fpmrec ? 7 : 8) + (h->sampling ? 1 : 0);
 }
 
 int ch_launch_step(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
@@ -643,12 +715,14 @@ int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double
                                         : (grad ? sizeof(ChParams<D3>) : sizeof(ChParams<double>))) *
              h->ny);
   h->sums = A(sums_bytes * h->ny);
+  if (env.sp.method == 1) h->fpmrec = (double*)A(sizeof(double) * kFpmRec * (size_t)h->ny);
   h->acc = (double*)A(acc_bytes);
   h->wallmom = (double*)A(sizeof(double));
   h->macc = (double*)A(sizeof(double) * 21 * h->ny);
   h->mout = (double*)A(sizeof(double) * USP_NMOM * h->ny);
   h->dstep = (long long*)A(sizeof(long long));
   bool ok = h->keycell && h->bh && h->off && h->cells && h->prm && h->sums && h->acc &&
+            (env.sp.method != 1 || h->fpmrec) &&
             h->wallmom && h->macc && h->mout && h->dstep;
   for (int k = 0; k < 2; ++k) {
     for (int f = 0; f < 5; ++f) ok = ok && h->st[k][f];

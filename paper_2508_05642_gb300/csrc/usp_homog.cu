@@ -2071,7 +2071,8 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
                      const double* h_cx, const double* h_cy, const double* h_cz,
                      const double* h_erot, const int32_t* h_lev, const uint32_t* h_pid) {
   if (!out || !sp || !cfg || !ch) return USP_EINVAL;
-  if (cfg->method != USP_METHOD_USP_FPM) return USP_ENOTSUP;
+  if (cfg->method != USP_METHOD_USP_FPM && cfg->method != USP_METHOD_FPM) return USP_EINVAL;
+  if (cfg->method == USP_METHOD_FPM && cfg->precision == USP_FP64_TANGENT) return USP_ENOTSUP;
   if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64 &&
       cfg->precision != USP_FP64_TANGENT)
     return USP_EINVAL;
@@ -2085,6 +2086,7 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
   c->pl = nullptr;
   c->cfg = *cfg;
   c->sp = to_dev(sp);
+  c->sp.method = cfg->method;
   c->precision = cfg->precision;
   c->ncell = 0;
   c->nparticles = 0;

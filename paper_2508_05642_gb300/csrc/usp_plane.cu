@@ -104,7 +104,6 @@ struct PlParams {
   };
   int active, pad;
 };
-constexpr int kFpmRec = 11;   // doubles per cell of the FPM coefficient pass
 
 __device__ __forceinline__ int grid_threads() { return gridDim.x * blockDim.x; }
 
@@ -677,57 +676,6 @@ __global__ void pl_gather(PlCount* __restrict__ cnt, int ncell,
 }
 
 // ---------------------------------------------------------------------------
-// the plain FPM method (Sec. 2.B-C) per cell, FP64: alpha = exp(-dt / tau),
-// the Cholesky factor of tau D_tr from the cell's stress, the rotational
-// square-form constants, the Gillespie rates and the conservation targets
-// (the first-order method takes the cell values at every particle)
-// ---------------------------------------------------------------------------
-__global__ void ch_coeffs_fpm(int ncell, double F_num, double vol, const double* __restrict__ afv,
-                              double dt, ChCellT<double>* __restrict__ cells,
-                              double* __restrict__ rec, Species sp, uint32_t* flags,
-                              unsigned long long* counters) {
-  __shared__ BlockTally tal;
-  tally_init(tal);
-  const double R = gasR(sp);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
-    ChCellT<double>& cs = cells[c];
-    if (!cs.active) continue;
-    const double v = afv[c] * vol;
-    if (!(v > 0.0)) {
-      cs.active = 0;
-      continue;
-    }
-    cs.n = (double)cs.N * F_num / v;
-    const FpmCell f = fpm_cell(sp, cs.n, dt, cs.Pi, cs.Ttr, cs.Trot, cs.Tvib);
-    if (!f.ok) {
-      tally_or(tal, (uint32_t)F_A_NONPOS);
-      cs.active = 0;
-      continue;
-    }
-    cs.alpha = f.alpha;
-    cs.e_rot_tgt = f.e_rot_tgt;
-    cs.e_vib_tgt = f.e_vib_tgt;
-    if (f.fixed) tally_add(tal, C_CHOL_FIX, 1ull);
-    if (f.nu_zero) tally_add(tal, C_NU_ZERO, 1ull);
-    if (f.failed) tally_or(tal, (uint32_t)F_CHOL_FAIL_AFTER_FIX);
-    if (f.clamped) {
-      tally_or(tal, (uint32_t)F_TREL_CLAMP);
-      tally_add(tal, C_TREL_CLAMP, 1ull);
-    }
-    const double a = f.alpha, oma2 = 1.0 - a * a, sq = sqrt(oma2);
-    const double arot = R * f.Trot_rel * oma2 / 2.0;
-    double* o = rec + (size_t)c * kFpmRec;
-    o[0] = a;
-    for (int i = 0; i < 6; ++i) o[1 + i] = sq * f.L[i];
-    o[7] = arot;
-    o[8] = sqrt(arot);
-    o[9] = f.lam_up;
-    o[10] = f.lam_dn;
-  }
-  tally_flush(tal, flags, counters);
-}
-
-// ---------------------------------------------------------------------------
 // reconstruction stencils (Sec. 3.B on the uniform grid): for each side of
 // the centroid the x and y neighbour used (that side's if usable, else the
 // opposite one, else none) and the quadrant's diagonal when usable
@@ -991,27 +939,6 @@ constexpr size_t pl_collide_smem() {
 // stencil record and particles and of cell c + 2W's place and size are in
 // flight, so the DRAM latency of a cell overlaps the previous cell's
 // arithmetic.
-// the plain FPM method for one particle (Sec. 2.C): Gorji's velocity update
-// and the Milstein square form for eps_rot with the cell values, Gillespie's
-// direct method for the level
-template <typename T>
-__device__ __forceinline__ int fpm_particle(const PlParams<T>& P, T& v0, T& v1, T& v2, T& en,
-                                            int l0, uint32_t id, uint32_t step,
-                                            const PhiloxRoundKeys& rk, uint32_t& fl) {
-  const U4 w = philox4x32_10(id, step, PTAG_NORMALS, 0u, rk);
-  T g0, g1, g2, g3;
-  box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
-  box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
-  const T a = P.fpm.as;
-  const T d0 = v0 - P.F[0], d1 = v1 - P.F[1], d2 = v2 - P.F[2];
-  v0 = P.F[0] + a * d0 + P.fpm.Lp[0] * g0;
-  v1 = P.F[1] + a * d1 + (P.fpm.Lp[1] * g0 + P.fpm.Lp[2] * g1);
-  v2 = P.F[2] + a * d2 + (P.fpm.Lp[3] * g0 + P.fpm.Lp[4] * g1 + P.fpm.Lp[5] * g2);
-  const T root = sqrt(en) * a + P.fpm.sqrt_a * g3;
-  en = P.fpm.a_rot + root * root;
-  return gillespie<T>(l0, P.fpm.lam_up, P.fpm.lam_dn, id, step, rk, fl);
-}
-
 // METHOD 0: USP-FPM with the reconstructed fields; 1: the plain FPM method
 template <typename T, int METHOD>
 __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<double>* __restrict__ cells,
@@ -1127,7 +1054,8 @@ __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<d
         }
         int ln;
         if constexpr (METHOD == 1) {
-          ln = fpm_particle<T>(P, v0, v1, v2, en, l0, id, step, rk, tl.fl);
+          ln = fpm_particle<T>(P.F, P.fpm.as, P.fpm.Lp, P.fpm.a_rot, P.fpm.sqrt_a, P.fpm.lam_up,
+                               P.fpm.lam_dn, v0, v1, v2, en, l0, id, step, rk, tl.fl);
         } else {
           const T ddx = xv - P.xc, ddy = yv - P.yc;
           const int sx = ddx >= T(0) ? 1 : 0, sy = ddy >= T(0) ? 1 : 0;

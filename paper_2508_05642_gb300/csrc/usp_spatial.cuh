@@ -626,6 +626,81 @@ __global__ void ch_coeffs_f32(int ny, double F_num, double vol, const double* __
   tally_flush(tal, flags, counters);
 }
 
+constexpr int kFpmRec = 11;   // doubles per cell of the FPM coefficient pass
+
+// ---------------------------------------------------------------------------
+// the plain FPM method (Sec. 2.B-C) per cell, FP64: alpha = exp(-dt / tau),
+// the Cholesky factor of tau D_tr from the cell's stress, the rotational
+// square-form constants, the Gillespie rates and the conservation targets
+// (the first-order method takes the cell values at every particle)
+// ---------------------------------------------------------------------------
+__global__ void ch_coeffs_fpm(int ncell, double F_num, double vol, const double* __restrict__ afv,
+                              double dt, ChCellT<double>* __restrict__ cells,
+                              double* __restrict__ rec, Species sp, uint32_t* flags,
+                              unsigned long long* counters) {
+  __shared__ BlockTally tal;
+  tally_init(tal);
+  const double R = gasR(sp);
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    ChCellT<double>& cs = cells[c];
+    if (!cs.active) continue;
+    const double v = afv ? afv[c] * vol : vol;   // fluid volume (null: whole cells)
+    if (!(v > 0.0)) {
+      cs.active = 0;
+      continue;
+    }
+    cs.n = (double)cs.N * F_num / v;
+    const FpmCell f = fpm_cell(sp, cs.n, dt, cs.Pi, cs.Ttr, cs.Trot, cs.Tvib);
+    if (!f.ok) {
+      tally_or(tal, (uint32_t)F_A_NONPOS);
+      cs.active = 0;
+      continue;
+    }
+    cs.alpha = f.alpha;
+    cs.e_rot_tgt = f.e_rot_tgt;
+    cs.e_vib_tgt = f.e_vib_tgt;
+    if (f.fixed) tally_add(tal, C_CHOL_FIX, 1ull);
+    if (f.nu_zero) tally_add(tal, C_NU_ZERO, 1ull);
+    if (f.failed) tally_or(tal, (uint32_t)F_CHOL_FAIL_AFTER_FIX);
+    if (f.clamped) {
+      tally_or(tal, (uint32_t)F_TREL_CLAMP);
+      tally_add(tal, C_TREL_CLAMP, 1ull);
+    }
+    const double a = f.alpha, oma2 = 1.0 - a * a, sq = sqrt(oma2);
+    const double arot = R * f.Trot_rel * oma2 / 2.0;
+    double* o = rec + (size_t)c * kFpmRec;
+    o[0] = a;
+    for (int i = 0; i < 6; ++i) o[1 + i] = sq * f.L[i];
+    o[7] = arot;
+    o[8] = sqrt(arot);
+    o[9] = f.lam_up;
+    o[10] = f.lam_dn;
+  }
+  tally_flush(tal, flags, counters);
+}
+
+// the plain FPM method for one particle (Sec. 2.C) with the cell values U:
+// Gorji's velocity update c' = U + alpha (c - U) + sqrt(1 - alpha^2) L G, the
+// Milstein square form eps' = a + (sqrt(eps) alpha + sqrt(a) G4)^2 and
+// Gillespie's direct method for the level
+template <typename T>
+__device__ __forceinline__ int fpm_particle(const T* U, T a, const T* Lp, T a_rot, T sqrt_a,
+                                            T lam_up, T lam_dn, T& v0, T& v1, T& v2, T& en,
+                                            int l0, uint32_t id, uint32_t step,
+                                            const PhiloxRoundKeys& rk, uint32_t& fl) {
+  const U4 w = philox4x32_10(id, step, PTAG_NORMALS, 0u, rk);
+  T g0, g1, g2, g3;
+  box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
+  box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
+  const T d0 = v0 - U[0], d1 = v1 - U[1], d2 = v2 - U[2];
+  v0 = U[0] + a * d0 + Lp[0] * g0;
+  v1 = U[1] + a * d1 + (Lp[1] * g0 + Lp[2] * g1);
+  v2 = U[2] + a * d2 + (Lp[3] * g0 + Lp[4] * g1 + Lp[5] * g2);
+  const T root = sqrt(en) * a + sqrt_a * g3;
+  en = a_rot + root * root;
+  return gillespie<T>(l0, lam_up, lam_dn, id, step, rk, fl);
+}
+
 template <typename S>
 __device__ __forceinline__ void cell_fields(const ChCellT<S>& c, S* f) {
   f[0] = c.U[0]; f[1] = c.U[1]; f[2] = c.U[2];

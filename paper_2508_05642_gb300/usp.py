@@ -248,7 +248,7 @@ def usp_init_homogeneous(species: dict, offsets, ndens, dt, cx, cy, cz, erot, le
 
 def usp_init_channel(species: dict, channel: dict, dt: float, y, cx, cy, cz, erot, lev, pid=None,
                      *, precision=USP_FP32, seed=1, step0=0, stream=None, use_graph=True,
-                     allocator=None) -> Context:
+                     allocator=None, method=USP_METHOD_USP_FPM) -> Context:
     """Create a 1D-channel context (host numpy inputs)."""
     f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
     y, cx, cy, cz, erot = f(y), f(cx), f(cy), f(cz), f(erot)
@@ -263,6 +263,7 @@ def usp_init_channel(species: dict, channel: dict, dt: float, y, cx, cy, cz, ero
     cfg.step0 = step0
     cfg.stream = stream or None
     cfg.use_graph = 1 if use_graph else 0
+    cfg.method = method
     keep = []
     if allocator is not None:
         a_fn, f_fn, user = allocator

@@ -194,3 +194,47 @@ def test_fp32_plane_fpm_levels_and_fields_track_the_oracle():
     vth = math.sqrt(Oo.R(sp) * 200.0)
     dv = np.abs(gvx[go] - st.cx[:st.n][oo])
     assert np.quantile(dv, 0.99) < 1e-3 * vth
+
+
+@pytest.mark.parametrize("precision", [usp.USP_FP64, usp.USP_FP32])
+def test_channel_fpm_matches_oracle(precision):
+    """The Poiseuille channel (16 cells x 100 particles) with the plain FPM
+    method, 30 steps: FP64 form particle for particle (ids, order, levels,
+    values within FP64 rounding of the arithmetic); FP32 form against the
+    FP32-form oracle (levels equal for all but a few, velocities within FP32
+    arithmetic at the 99th percentile); same wall-event counts in FP64."""
+    from oracle import oracle as Oo
+    w = I.channel_poiseuille(ny=16, ppc=100, steps=0)
+    sp = Oo.species(**w.species)
+    ch = Oo.channel(**dict(w.channel, method=1))
+    p = w.particles
+    y = w.y
+    form = 1 if precision == usp.USP_FP32 else 0
+    if form == 1:
+        p = p.astype_f32_exact()
+        y = y.astype(np.float32).astype(np.float64)
+    dto = w.dt_over_tau_c * Oo.tau_c(sp, w.n, w.channel["T_wall"])
+    dtg = w.dt_over_tau_c * usp.usp_tau_c(w.species, w.n, w.channel["T_wall"])
+    st = Oo.ChannelState.from_arrays(y, p.cx, p.cy, p.cz, p.erot, p.lev)
+    ctx = usp.usp_init_channel(w.species, w.channel, dtg, y, p.cx, p.cy, p.cz, p.erot, p.lev,
+                               precision=precision, seed=w.seed, method=usp.USP_METHOD_FPM)
+    _, fl, cnt = Oo.channel_step(sp, form, w.seed, 0, 30, ch, dto, st)
+    usp.usp_step(ctx, 30)
+    gy, gvx, gvy, gvz, ge, gl, gp = usp.usp_channel_get_particles(ctx)
+    gfl, gcnt = usp.usp_status(ctx)
+    assert gfl & usp.ERROR_FLAGS == 0
+    vth = math.sqrt(Oo.R(sp) * 300.0)
+    if form == 0:
+        assert np.array_equal(gp, st.pid) and np.array_equal(gl, st.lev)
+        assert np.max(np.abs(gy - st.y)) < 1e-12
+        for a, b in ((gvx, st.cx), (gvy, st.cy), (gvz, st.cz)):
+            assert np.max(np.abs(a - b)) < 1e-7 * vth
+        assert gcnt[usp.C_WALL_HITS] == cnt[Oo.C_WALL_HITS]
+    else:
+        go, oo = np.argsort(gp), np.argsort(st.pid)
+        assert np.array_equal(gp[go], st.pid[oo])
+        assert np.mean(gl[go] != st.lev[oo]) < 2e-3
+        assert np.quantile(np.abs(gvx[go] - st.cx[oo]), 0.99) < 1e-3 * vth
+    with pytest.raises(usp.USPError):
+        usp.usp_init_channel(w.species, w.channel, dtg, y, p.cx, p.cy, p.cz, p.erot, p.lev,
+                             precision=usp.USP_FP64_TANGENT, method=usp.USP_METHOD_FPM)
