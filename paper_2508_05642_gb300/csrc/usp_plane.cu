@@ -64,11 +64,14 @@ struct PlGeom {
   double cxc, cyc, cr;
   double Tw, dt;
   int bcbits;         // 2 bits per side (USP_BC_*): left, right, bottom, top
-  // refined grid (levels 2, 3; 1 = uniform): per level-1 cell its first
-  // cell, per level-2 child its first cell (-1: the level-1 cell is not
-  // split) and whether it is split again; per cell its level and integer
-  // coordinates at that level
-  int levels;
+};
+
+// Refined grid (levels 2, 3), in device memory: per level-1 cell its first
+// cell, per level-2 child its first cell (-1: the level-1 cell is not split)
+// and whether it is split again; per cell its level and integer coordinates
+// at that level.  Kept out of PlGeom so that the uniform grid's flight
+// kernels take the same parameters as without refinement.
+struct PlTree {
   const int* l1_first;
   const int* l2_first;
   const signed char* l2_ref;
@@ -111,22 +114,23 @@ __device__ __forceinline__ int grid_threads() { return gridDim.x * blockDim.x; }
 // half (and quarter) of it from the point's offset in units of half a cell
 // (round-to-nearest operations: the FP64 form places points exactly as the
 // plain definition does)
-template <typename T>
-__device__ __forceinline__ int plane_cell(const PlGeom& g, T x, T y) {
+template <typename T, bool AMR>
+__device__ __forceinline__ int plane_cell(const PlGeom& g, const PlTree* __restrict__ tr, T x,
+                                          T y) {
   int i = (int)floor((x - (T)g.x0) / (T)g.dx);
   int j = (int)floor((y - (T)g.y0) / (T)g.dy);
   i = i < 0 ? 0 : (i >= g.nx ? g.nx - 1 : i);
   j = j < 0 ? 0 : (j >= g.ny ? g.ny - 1 : j);
   const int c = j * g.nx + i;
-  if (g.levels < 2) return c;
-  const int first = g.l2_first[4 * c];
-  if (first < 0) return g.l1_first[c];
+  if (!AMR) return c;
+  const int first = tr->l2_first[4 * c];
+  if (first < 0) return tr->l1_first[c];
   const T ux = rn_div(rn_sub(x, rn_add((T)g.x0, rn_mul((T)i, (T)g.dx))), rn_mul(T(0.5), (T)g.dx));
   const T uy = rn_div(rn_sub(y, rn_add((T)g.y0, rn_mul((T)j, (T)g.dy))), rn_mul(T(0.5), (T)g.dy));
   const int ci = ux >= T(1) ? 1 : 0, cj = uy >= T(1) ? 1 : 0;
   const int k = 2 * cj + ci;
-  const int l = g.l2_first[4 * c + k];
-  if (!g.l2_ref[4 * c + k]) return l;
+  const int l = tr->l2_first[4 * c + k];
+  if (!tr->l2_ref[4 * c + k]) return l;
   const T vx = rn_mul(rn_sub(ux, (T)ci), T(2)), vy = rn_mul(rn_sub(uy, (T)cj), T(2));
   return l + 2 * (vy >= T(1) ? 1 : 0) + (vx >= T(1) ? 1 : 0);
 }
@@ -258,8 +262,9 @@ __device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, const PlCount* __restrict__ cnt,
+template <typename T, bool AMR>
+__global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, const PlTree* __restrict__ tr,
+                                                     const PlCount* __restrict__ cnt,
                           const int* __restrict__ keycell, const ChCellT<double>* __restrict__ cells,
                           const float* __restrict__ pend,
                           T* __restrict__ x, T* __restrict__ y, T* __restrict__ cx,
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, const PlCount* __
     nhit += hits;
     nout += keep ? 0 : 1;
     x[j] = px; y[j] = py; cx[j] = vx; cy[j] = vy; cz[j] = vz; er[j] = e; lev[j] = l;
-    keyout[j] = keep ? plane_cell(g, px, py) : g.ncell;
+    keyout[j] = keep ? plane_cell<T, AMR>(g, tr, px, py) : g.ncell;
     idxout[j] = (int)j;
   }
   fl = __reduce_or_sync(0xffffffffu, fl);
@@ -436,8 +441,9 @@ __device__ double inflow_speed(double RT, double u_n, uint32_t pid, uint32_t ste
 
 // one thread per entering particle (grid-stride over the step's count); its
 // face by binary search of the face offsets
-template <typename T>
-__global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, PlInflow f, const PlCount* __restrict__ cnt,
+template <typename T, bool AMR>
+__global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, const PlTree* __restrict__ tr,
+                                                     PlInflow f, const PlCount* __restrict__ cnt,
                           const int* __restrict__ face_off, T* __restrict__ x, T* __restrict__ y,
                           T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ cz,
                           T* __restrict__ er, int* __restrict__ lev, uint32_t* __restrict__ pid,
@@ -496,7 +502,7 @@ __global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, PlInflow f, const
     nout += keep ? 0 : 1;
     const long long j = n + m;
     x[j] = X; y[j] = Y; cx[j] = VX; cy[j] = VY; cz[j] = VZ; er[j] = E; lev[j] = L; pid[j] = id;
-    keyout[j] = keep ? plane_cell(g, X, Y) : g.ncell;
+    keyout[j] = keep ? plane_cell<T, AMR>(g, tr, X, Y) : g.ncell;
     idxout[j] = (int)j;
   }
   fl = __reduce_or_sync(0xffffffffu, fl);
@@ -777,24 +783,26 @@ __global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict
 // centre in integer form.  A centre never lies on the edge of a cell of level
 // L or coarser; where it is the common corner of finer cells, any of them
 // stands for "finer" (here the one the >= rule of the point location takes).
-__device__ __forceinline__ int leaf_at(const PlGeom& g, int L, int I, int J) {
+__device__ __forceinline__ int leaf_at(const PlGeom& g, const PlTree* __restrict__ tr, int L, int I,
+                                       int J) {
   const int c = (J >> (L - 1)) * g.nx + (I >> (L - 1));
-  if (g.l2_first[4 * c] < 0) return g.l1_first[c];
+  if (tr->l2_first[4 * c] < 0) return tr->l1_first[c];
   const int k = L == 1 ? 3 : ((((J >> (L - 2)) & 1) << 1) | ((I >> (L - 2)) & 1));
-  const int l = g.l2_first[4 * c + k];
-  if (!g.l2_ref[4 * c + k]) return l;
+  const int l = tr->l2_first[4 * c + k];
+  if (!tr->l2_ref[4 * c + k]) return l;
   return L <= 2 ? l + 3 : l + (((J & 1) << 1) | (I & 1));
 }
 
 template <typename T>
-__device__ bool pl_region(const PlGeom& g, const PlParams<T>* __restrict__ prm,
+__device__ bool pl_region(const PlGeom& g, const PlTree* __restrict__ tr,
+                          const PlParams<T>* __restrict__ prm,
                           const T* __restrict__ fT, const int* __restrict__ usable_c,
                           const long long* __restrict__ off, int lvl, int ii, int jj, int di,
                           int dj, double h, double k, T* val) {
   const int I = ii + di, J = jj + dj;
   if (I < 0 || J < 0 || I >= (g.nx << (lvl - 1)) || J >= (g.ny << (lvl - 1))) return false;
-  const int l = leaf_at(g, lvl, I, J);
-  const int ll = g.lvl[l];
+  const int l = leaf_at(g, tr, lvl, I, J);
+  const int ll = tr->lvl[l];
   if (ll == lvl) {
     if (!usable_c[l]) return false;
     for (int f = 0; f < kNF; ++f) val[f] = fT[(size_t)l * kNF + f];
@@ -804,8 +812,8 @@ __device__ bool pl_region(const PlGeom& g, const PlParams<T>* __restrict__ prm,
     int q[4];
     long long nq[4], ns = 0;
     for (int a = 0; a < 4; ++a) {
-      q[a] = leaf_at(g, lvl + 1, 2 * I + (a & 1), 2 * J + (a >> 1));
-      if (g.lvl[q[a]] != lvl + 1 || !usable_c[q[a]]) return false;
+      q[a] = leaf_at(g, tr, lvl + 1, 2 * I + (a & 1), 2 * J + (a >> 1));
+      if (tr->lvl[q[a]] != lvl + 1 || !usable_c[q[a]]) return false;
       nq[a] = off[q[a] + 1] - off[q[a]];
       ns += nq[a];
     }
@@ -829,7 +837,8 @@ __device__ bool pl_region(const PlGeom& g, const PlParams<T>* __restrict__ prm,
 
 // blocks: the kParamBlock-cell blocks holding cells of this level
 template <typename T>
-__global__ void pl_params_amr(PlGeom g, int recon, int level, const int* __restrict__ blocks,
+__global__ void pl_params_amr(PlGeom g, const PlTree* __restrict__ tr, int recon, int level,
+                              const int* __restrict__ blocks,
                               const ChCellT<double>* __restrict__ cells, const T* __restrict__ fT,
                               const int* __restrict__ usable_c, const long long* __restrict__ off,
                               PlParams<T>* __restrict__ prm, Species sp) {
@@ -837,7 +846,7 @@ __global__ void pl_params_amr(PlGeom g, int recon, int level, const int* __restr
   const int c0 = blocks[blockIdx.x] * kParamBlock;
   const int c = c0 + threadIdx.x;
   const int nb = min(kParamBlock, g.ncell - c0);
-  if (c < g.ncell && g.lvl[c] == level) {
+  if (c < g.ncell && tr->lvl[c] == level) {
     const ChCellT<double>& cs = cells[c];
     PlParams<T>& P = buf[threadIdx.x];
     P.active = cs.active;
@@ -847,7 +856,7 @@ __global__ void pl_params_amr(PlGeom g, int recon, int level, const int* __restr
     P.R = (T)gasR(sp); P.theta = (T)sp.theta_v; P.dt = (T)g.dt;
     const double sc = (double)(1 << (level - 1));
     const double h = g.dx / sc, k = g.dy / sc;
-    const int ii = g.lii[c], jj = g.ljj[c];
+    const int ii = tr->lii[c], jj = tr->ljj[c];
     P.xc = (T)rn_add(g.x0, rn_mul((double)ii + 0.5, h));
     P.yc = (T)rn_add(g.y0, rn_mul((double)jj + 0.5, k));
     const T* f = fT + (size_t)c * kNF;
@@ -858,13 +867,13 @@ __global__ void pl_params_amr(PlGeom g, int recon, int level, const int* __restr
     for (int sd = 0; sd < 2; ++sd) {
       const int sg = sd ? 1 : -1;
       if (recon) {
-        if (pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, sg, 0, h, k, PX[sd]))
+        if (pl_region<T>(g, tr, prm, fT, usable_c, off, level, ii, jj, sg, 0, h, k, PX[sd]))
           ox[sd] = sg;
-        else if (pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, -sg, 0, h, k, PX[sd]))
+        else if (pl_region<T>(g, tr, prm, fT, usable_c, off, level, ii, jj, -sg, 0, h, k, PX[sd]))
           ox[sd] = -sg;
-        if (pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, 0, sg, h, k, PY[sd]))
+        if (pl_region<T>(g, tr, prm, fT, usable_c, off, level, ii, jj, 0, sg, h, k, PY[sd]))
           oy[sd] = sg;
-        else if (pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, 0, -sg, h, k, PY[sd]))
+        else if (pl_region<T>(g, tr, prm, fT, usable_c, off, level, ii, jj, 0, -sg, h, k, PY[sd]))
           oy[sd] = -sg;
       }
       const T sx = ox[sd] > 0 ? ih : -ih, sy = oy[sd] > 0 ? ik : -ik;
@@ -876,7 +885,7 @@ __global__ void pl_params_amr(PlGeom g, int recon, int level, const int* __restr
     for (int q = 0; q < 4; ++q) {
       const int sx = q & 1, sy = q >> 1;
       const bool d = ox[sx] && oy[sy] &&
-                     pl_region<T>(g, prm, fT, usable_c, off, level, ii, jj, ox[sx], oy[sy], h,
+                     pl_region<T>(g, tr, prm, fT, usable_c, off, level, ii, jj, ox[sx], oy[sy], h,
                                   k, PD);
       const T s = (ox[sx] * oy[sy] > 0 ? T(1) : T(-1)) * ih * ik;
       for (int m = 0; m < kNF; ++m)
@@ -890,7 +899,7 @@ __global__ void pl_params_amr(PlGeom g, int recon, int level, const int* __restr
   const unsigned long long* src = reinterpret_cast<const unsigned long long*>(buf);
   unsigned long long* dst = reinterpret_cast<unsigned long long*>(prm + c0);
   for (int w = threadIdx.x; w < nb * kW; w += kParamBlock)
-    if (g.lvl[c0 + w / kW] == level) dst[w] = src[w];
+    if (tr->lvl[c0 + w / kW] == level) dst[w] = src[w];
 }
 
 // Asynchronous global -> shared copies of 4, 8 or 16 bytes (cp.async): the
@@ -1239,6 +1248,9 @@ struct PlaneCtx {
   double* afv;              // af / 4^(level-1): the cell volume over dx dy depth
   int* blk_lv;              // refined grid: per level the stencil blocks holding its cells
   double* fpmrec;           // the plain FPM method: kFpmRec per-cell constants (else null)
+  int levels;               // 1 uniform, 2 or 3 refined
+  PlTree* tree;             // refined grid tables (device; null on the uniform grid)
+  PlTree htree;             // the same pointers, host copy
   int blk_off[4], nblk_lv[4];
   PlCount* cnt;
   ChCellT<double>* cells;
@@ -1386,15 +1398,16 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   if (prof) prof(env.owner, 0, 1);
   // surface tallies of the cylinder while sampling
   double* surf = h->sampling ? h->acc + (size_t)ncell * kNAcc + 2 : nullptr;
-  pl_advect<T><<<h->grid_p, kBlk, 0, s>>>(h->g, h->cnt, h->keycell, h->cells, h->pend, x, y, cx,
-                                         cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0], h->ibuf[0],
-                                         h->dstep, env.sp, env.k0, env.k1, env.flags,
-                                         env.counters, surf);
+  // the uniform grid takes the point location without the refined-grid branch
+  const bool amr = h->levels >= 2;
+  (amr ? pl_advect<T, true> : pl_advect<T, false>)<<<h->grid_p, kBlk, 0, s>>>(
+      h->g, h->tree, h->cnt, h->keycell, h->cells, h->pend, x, y, cx, cy, cz, er, h->lv[a], h->pd[a],
+      h->kbuf[0], h->ibuf[0], h->dstep, env.sp, env.k0, env.k1, env.flags, env.counters, surf);
   pl_inflow<<<1, 1024, 0, s>>>(h->inf, h->cnt, h->face_off, h->cap, h->dstep, env.k0, env.k1,
                                env.flags, env.counters);
   if (h->inf.nfaces > 0)
-    pl_inject<T><<<h->grid_inj, kBlk, 0, s>>>(
-        h->g, h->inf, h->cnt, h->face_off, x, y, cx, cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0],
+    (amr ? pl_inject<T, true> : pl_inject<T, false>)<<<h->grid_inj, kBlk, 0, s>>>(
+        h->g, h->tree, h->inf, h->cnt, h->face_off, x, y, cx, cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0],
         h->ibuf[0], h->dstep, env.sp, env.k0, env.k1, env.flags, env.counters, surf);
   CHK(cudaGetLastError());
   int src = 0;
@@ -1434,15 +1447,15 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
     ch_coeffs<double><<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->afv, h->g.dt, h->cells,
                                           env.sp, env.sp.omega, env.sp.Z_rot, env.flags,
                                           env.counters);
-  if (fpm || h->g.levels < 2)
+  if (fpm || h->levels < 2)
     pl_params<T><<<(ncell + kParamBlock - 1) / kParamBlock, kParamBlock, 0, s>>>(
         h->g, fpm ? 0 : h->recon, h->cells, (const T*)h->fT, h->usable_c, (PlParams<T>*)h->prm,
         env.sp, h->fpmrec);
   else
-    for (int L = 1; L <= h->g.levels; ++L)
+    for (int L = 1; L <= h->levels; ++L)
       if (h->nblk_lv[L] > 0)
         pl_params_amr<T><<<h->nblk_lv[L], kParamBlock, 0, s>>>(
-            h->g, h->recon, L, h->blk_lv + h->blk_off[L], h->cells, (const T*)h->fT,
+            h->g, h->tree, h->recon, L, h->blk_lv + h->blk_off[L], h->cells, (const T*)h->fT,
             h->usable_c, h->off, (PlParams<T>*)h->prm, env.sp);
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 1, 0);
@@ -1476,9 +1489,9 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
 
 int pl_kernels_per_step(const PlaneCtx* h) {
   int params = 1;
-  if (h->g.levels >= 2 && !h->fpmrec) {
+  if (h->levels >= 2 && !h->fpmrec) {
     params = 0;
-    for (int L = 1; L <= h->g.levels; ++L) params += h->nblk_lv[L] > 0 ? 1 : 0;
+    for (int L = 1; L <= h->levels; ++L) params += h->nblk_lv[L] > 0 ? 1 : 0;
   }
   return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 2 + 2 + params + 1 + 2 +
          (h->sampling ? 1 : 0);
@@ -1526,7 +1539,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   g.dx = (pp->x1 - pp->x0) / pp->nx; g.dy = (pp->y1 - pp->y0) / pp->ny;
   g.cxc = pp->cyl_xc; g.cyc = pp->cyl_yc; g.cr = pp->cyl_r > 0 ? pp->cyl_r : 0.0;
   g.Tw = pp->T_wall; g.dt = dt;
-  g.levels = G.levels;
+  h->levels = G.levels;
   g.bcbits = 0;
   for (int k = 0; k < 4; ++k) g.bcbits |= (pp->bc[k] & 3) << (2 * k);
   h->recon = pp->reconstruct ? 1 : 0;
@@ -1600,12 +1613,14 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   const int n1 = pp->nx * pp->ny;
   if (G.levels >= 2) {
     h->afv = (double*)A(sizeof(double) * ncell);
-    g.l1_first = (const int*)A(sizeof(int) * (n1 + 1));
-    g.l2_first = (const int*)A(sizeof(int) * 4 * (size_t)n1);
-    g.l2_ref = (const signed char*)A(4 * (size_t)n1);
-    g.lvl = (const int*)A(sizeof(int) * ncell);
-    g.lii = (const int*)A(sizeof(int) * ncell);
-    g.ljj = (const int*)A(sizeof(int) * ncell);
+    PlTree& t = h->htree;
+    t.l1_first = (const int*)A(sizeof(int) * (n1 + 1));
+    t.l2_first = (const int*)A(sizeof(int) * 4 * (size_t)n1);
+    t.l2_ref = (const signed char*)A(4 * (size_t)n1);
+    t.lvl = (const int*)A(sizeof(int) * ncell);
+    t.lii = (const int*)A(sizeof(int) * ncell);
+    t.ljj = (const int*)A(sizeof(int) * ncell);
+    h->tree = (PlTree*)A(sizeof(PlTree));
   }
   // per level the stencil blocks (kParamBlock consecutive cells) holding its cells
   std::vector<int> blk;
@@ -1639,8 +1654,9 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->dstep = (long long*)A(sizeof(long long));
   bool ok = h->keycell && h->bh && h->tot && h->face_off && h->off && h->af && h->afv && h->cnt &&
             (env.sp.method != 1 || h->fpmrec) &&
-            (G.levels < 2 || (g.l1_first && g.l2_first && g.l2_ref && g.lvl && g.lii && g.ljj &&
-                              h->blk_lv)) &&
+            (G.levels < 2 || (h->htree.l1_first && h->htree.l2_first && h->htree.l2_ref &&
+                               h->htree.lvl && h->htree.lii && h->htree.ljj && h->blk_lv &&
+                               h->tree)) &&
             h->cells && h->pend && h->fT && h->usable_c && h->prm && h->sums && h->acc && h->macc && h->mout && h->dstep;
   for (int k = 0; k < 2; ++k) {
     for (int q = 0; q < 6; ++q) ok = ok && h->st[k][q];
@@ -1707,12 +1723,14 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
              cudaSuccess;
     };
     cok = cok && up(h->afv, afv.data(), sizeof(double) * ncell);
-    cok = cok && up(g.l1_first, G.l1_first.data(), sizeof(int) * (n1 + 1));
-    cok = cok && up(g.l2_first, G.l2_first.data(), sizeof(int) * 4 * (size_t)n1);
-    cok = cok && up(g.l2_ref, G.l2_ref.data(), 4 * (size_t)n1);
-    cok = cok && up(g.lvl, G.lvl.data(), sizeof(int) * ncell);
-    cok = cok && up(g.lii, G.lii.data(), sizeof(int) * ncell);
-    cok = cok && up(g.ljj, G.ljj.data(), sizeof(int) * ncell);
+    const PlTree& t = h->htree;
+    cok = cok && up(t.l1_first, G.l1_first.data(), sizeof(int) * (n1 + 1));
+    cok = cok && up(t.l2_first, G.l2_first.data(), sizeof(int) * 4 * (size_t)n1);
+    cok = cok && up(t.l2_ref, G.l2_ref.data(), 4 * (size_t)n1);
+    cok = cok && up(t.lvl, G.lvl.data(), sizeof(int) * ncell);
+    cok = cok && up(t.lii, G.lii.data(), sizeof(int) * ncell);
+    cok = cok && up(t.ljj, G.ljj.data(), sizeof(int) * ncell);
+    cok = cok && up(h->tree, &h->htree, sizeof(PlTree));
     if (!blk.empty()) cok = cok && up(h->blk_lv, blk.data(), sizeof(int) * blk.size());
   }
   cok = cok && cudaMemcpyAsync(h->cnt, &c0, sizeof(PlCount), cudaMemcpyHostToDevice, s) == cudaSuccess;
