@@ -343,7 +343,7 @@ int usp_set_particles(usp_ctx* ctx, const double* h_cx, const double* h_cy, cons
  * context's precision: float for USP_FP32, double for USP_FP64; int32
  * levels), run nsteps steps, download the moments into h_moments (USP_NMOM x
  * n_cells doubles) and, if h_*_out are not NULL, the resulting state.
- * Synchronises.  The cells are independent, so the upload goes in eight runs
+ * Synchronises.  The cells are independent, so the upload goes in sixteen runs
  * of whole cells and each run is stepped while the next one is in transit;
  * with pinned host buffers the copies run at full link speed and hide most
  * of the arithmetic.  Homogeneous contexts only (USP_ENOTSUP otherwise). */

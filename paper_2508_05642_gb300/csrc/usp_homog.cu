@@ -1268,6 +1268,10 @@ __global__ void gather_state_native(int ncell, const CellState* __restrict__ cel
 // ===========================================================================
 // Host side
 // ===========================================================================
+// runs of cells of the host-buffer step: each run's upload overlaps the
+// previous run's arithmetic, and only the last run's arithmetic is exposed
+constexpr int kHostRuns = 16;
+
 struct usp_ctx {
   int kind;                 // 0 homogeneous cells, 1 channel, 2 plane
   ChannelCtx* ch;
@@ -1319,7 +1323,7 @@ struct usp_ctx {
   void* stage;              // host-path staging buffer, kept between calls
   size_t stage_bytes;
   cudaStream_t copy_stream; // host-path uploads, overlapped with the scatter
-  cudaEvent_t up_ev[9];     // upload pipeline: start + one per chunk
+  cudaEvent_t up_ev[kHostRuns + 1];   // upload pipeline: start + one per run of cells
   // per-kernel event timing
   int profiling;
   std::vector<cudaEvent_t> ev_pool;
@@ -1727,7 +1731,7 @@ int upload_state(usp_ctx* c, const void* hx, const void* hy, const void* hz, con
 template <typename T>
 int step_host_chunked(usp_ctx* c, const void* hx, const void* hy, const void* hz,
                       const void* he, const int32_t* hl, int nsteps) {
-  constexpr int K = 8;
+  constexpr int K = kHostRuns;
   const long long n = c->nparticles;
   const size_t es = sizeof(T);
   void* st = staging(c, (size_t)n * (4 * es + 4) + 64);
