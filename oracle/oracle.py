@@ -48,6 +48,20 @@ C_CHOL_FIX, C_PB_CLAMP, C_TREL_CLAMP, C_VIB_DRAWS, C_NEG_RADICAND, C_WALL_HITS, 
 NCOUNTERS = 11
 
 
+def _compile(src: str, out: str, openmp: bool) -> None:
+    tmp = out + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+            "-fPIC", "-shared", "-Wall", "-Wno-misleading-indentation",
+            "-I", _HERE, src, "-o", tmp, "-lm"]
+    cmd = base[:1] + (["-fopenmp"] if openmp else []) + base[1:]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0 and openmp:
+        r = subprocess.run(base, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle build failed:\n" + r.stderr)
+    os.replace(tmp, out)
+
+
 def build(force: bool = False, openmp: bool = True) -> str:
     """Compile the oracle with gcc into ``oracle/_build/liborc.so``."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -55,18 +69,28 @@ def build(force: bool = False, openmp: bool = True) -> str:
         t = os.path.getmtime(_LIB_PATH)
         if t >= os.path.getmtime(_SRC) and t >= os.path.getmtime(_HDR):
             return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-            "-fPIC", "-shared", "-Wall", "-Wno-misleading-indentation",
-            _SRC, "-o", tmp, "-lm"]
-    cmd = base[:1] + (["-fopenmp"] if openmp else []) + base[1:]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0 and openmp:
-        r = subprocess.run(base, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("oracle build failed:\n" + r.stderr)
-    os.replace(tmp, _LIB_PATH)
+    _compile(_SRC, _LIB_PATH, openmp)
     return _LIB_PATH
+
+
+def load_variant(source_text: str, tag: str):
+    """Compile a modified copy of the oracle source (a test planting a
+    mistake in the oracle to show that a pin catches it) into
+    ``oracle/_build/liborc_<tag>.so`` and return it bound like ``lib()``.
+    The regular library is not touched."""
+    os.makedirs(_BUILD, exist_ok=True)
+    src = os.path.join(_BUILD, f"usp_oracle_{tag}.c")
+    out = os.path.join(_BUILD, f"liborc_{tag}.so")
+    with open(src, "w") as f:
+        f.write(source_text)
+    _compile(src, out, openmp=False)
+    return _bind(C.CDLL(out))
+
+
+def source() -> str:
+    """Text of the oracle's C source."""
+    with open(_SRC) as f:
+        return f.read()
 
 
 class Species(C.Structure):
@@ -155,69 +179,72 @@ _U32 = C.POINTER(C.c_uint32)
 _I64 = C.POINTER(C.c_int64)
 
 
+def _bind(L):
+    L.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
+    L.orc_uniform.argtypes = [C.c_uint32, C.c_int]
+    L.orc_uniform.restype = C.c_double
+    for fn in ("orc_e_vib", "orc_cv_vib", "orc_T_vib_from_mean_level", "orc_mu",
+               "orc_prandtl"):
+        getattr(L, fn).argtypes = [C.POINTER(Species), C.c_double]
+        getattr(L, fn).restype = C.c_double
+    L.orc_R.argtypes = [C.POINTER(Species)]
+    L.orc_R.restype = C.c_double
+    L.orc_tau_c.argtypes = [C.POINTER(Species), C.c_double, C.c_double]
+    L.orc_tau_c.restype = C.c_double
+    L.orc_collision_numbers.argtypes = [C.POINTER(Species), C.c_double, _D, _D]
+    L.orc_cell_coeffs.argtypes = [C.POINTER(Species)] + [C.c_double] * 5 + [C.POINTER(Coeffs)]
+    L.orc_cell_coeffs.restype = C.c_int
+    L.orc_relaxation_temperatures.argtypes = [C.POINTER(Species), C.POINTER(Coeffs), C.c_double,
+                                              C.c_double, C.c_double, C.c_double, _D, _D, _D, _U32]
+    L.orc_sym3_eig_minmax.argtypes = [_D, _D, _D]
+    L.orc_cholesky3.argtypes = [_D, _D]
+    L.orc_cholesky3.restype = C.c_int
+    L.orc_sample_nb.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, _U32]
+    L.orc_sample_nb.restype = C.c_int
+    L.orc_sample_b.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, _U32]
+    L.orc_sample_b.restype = C.c_int
+    L.orc_collide_particle.argtypes = [C.POINTER(Species), C.c_int, C.POINTER(Coeffs), _D, _D,
+                                       C.c_double, C.c_double, C.c_double, _D, C.c_double,
+                                       C.c_double, _D, _D, _I32, _U32, _I64]
+    L.orc_moments.argtypes = [C.POINTER(Species), C.c_int, _I64, _D, _D, _D, _D, _I32, _D]
+    L.orc_homog_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
+                                 C.c_int, _I64, _D, _D, _D, _D, _D, _D, _I32, _U32, _U32, _I64]
+    L.orc_homog_step.restype = C.c_int
+    L.orc_channel_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
+                                   C.POINTER(Channel), C.c_double, C.c_int64, _D, _D, _D, _D, _D,
+                                   _I32, _U32, _I64, _D, _U32, _I64]
+    L.orc_channel_step.restype = C.c_int
+    L.orc_channel_reconstruct.argtypes = [C.POINTER(Channel), _I64, _D, C.c_int, C.c_double, _D]
+    L.orc_wall_reemit.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_uint32,
+                                  C.c_uint32, C.c_int, C.c_double, C.c_int, _D, _I32]
+    L.orc_plane_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
+                                 C.POINTER(Plane), _D, C.c_double, _I64, C.c_int64, _D, _D,
+                                 _D, _D, _D, _D, _I32, _U32, _U32, _I64, _D, _U32, _I64]
+    L.orc_plane_step.restype = C.c_int
+    L.orc_plane_reconstruct.argtypes = [C.POINTER(Plane), _I64, _D, _D, C.c_int, C.c_double,
+                                        C.c_double, _D]
+    L.orc_inflow_flux.argtypes = [C.c_double, C.c_double, C.c_double]
+    L.orc_inflow_flux.restype = C.c_double
+    L.orc_inflow_normal_speed.argtypes = [C.c_double, C.c_double, C.c_uint32, C.c_uint32,
+                                          C.c_uint64, C.c_int, _U32]
+    L.orc_inflow_normal_speed.restype = C.c_double
+    L.orc_plane_nleaf.argtypes = [C.POINTER(Plane)]
+    L.orc_plane_leaves.argtypes = [C.POINTER(Plane), C.POINTER(C.c_int32),
+                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.orc_plane_leaf_of.argtypes = [C.POINTER(Plane), C.c_double, C.c_double]
+    L.orc_fpm_coeffs.argtypes = [C.POINTER(Species)] + [C.c_double] * 5 + \
+        [C.POINTER(FpmCoeffs)]
+    L.orc_gillespie.argtypes = [C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
+                                C.c_uint32, C.c_int, _U32]
+    L.orc_homog_step_fpm.argtypes = L.orc_homog_step.argtypes
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            L.orc_philox4x32_10.argtypes = [_U32, _U32, _U32]
-            L.orc_uniform.argtypes = [C.c_uint32, C.c_int]
-            L.orc_uniform.restype = C.c_double
-            for fn in ("orc_e_vib", "orc_cv_vib", "orc_T_vib_from_mean_level", "orc_mu",
-                       "orc_prandtl"):
-                getattr(L, fn).argtypes = [C.POINTER(Species), C.c_double]
-                getattr(L, fn).restype = C.c_double
-            L.orc_R.argtypes = [C.POINTER(Species)]
-            L.orc_R.restype = C.c_double
-            L.orc_tau_c.argtypes = [C.POINTER(Species), C.c_double, C.c_double]
-            L.orc_tau_c.restype = C.c_double
-            L.orc_collision_numbers.argtypes = [C.POINTER(Species), C.c_double, _D, _D]
-            L.orc_cell_coeffs.argtypes = [C.POINTER(Species)] + [C.c_double] * 5 + [C.POINTER(Coeffs)]
-            L.orc_cell_coeffs.restype = C.c_int
-            L.orc_relaxation_temperatures.argtypes = [C.POINTER(Species), C.POINTER(Coeffs), C.c_double,
-                                                      C.c_double, C.c_double, C.c_double, _D, _D, _D, _U32]
-            L.orc_sym3_eig_minmax.argtypes = [_D, _D, _D]
-            L.orc_cholesky3.argtypes = [_D, _D]
-            L.orc_cholesky3.restype = C.c_int
-            L.orc_sample_nb.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, _U32]
-            L.orc_sample_nb.restype = C.c_int
-            L.orc_sample_b.argtypes = [C.c_int, C.c_double, C.c_double, C.c_int, _U32]
-            L.orc_sample_b.restype = C.c_int
-            L.orc_collide_particle.argtypes = [C.POINTER(Species), C.c_int, C.POINTER(Coeffs), _D, _D,
-                                               C.c_double, C.c_double, C.c_double, _D, C.c_double,
-                                               C.c_double, _D, _D, _I32, _U32, _I64]
-            L.orc_moments.argtypes = [C.POINTER(Species), C.c_int, _I64, _D, _D, _D, _D, _I32, _D]
-            L.orc_homog_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
-                                         C.c_int, _I64, _D, _D, _D, _D, _D, _D, _I32, _U32, _U32, _I64]
-            L.orc_homog_step.restype = C.c_int
-            L.orc_channel_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
-                                           C.POINTER(Channel), C.c_double, C.c_int64, _D, _D, _D, _D, _D,
-                                           _I32, _U32, _I64, _D, _U32, _I64]
-            L.orc_channel_step.restype = C.c_int
-            L.orc_channel_reconstruct.argtypes = [C.POINTER(Channel), _I64, _D, C.c_int, C.c_double, _D]
-            L.orc_wall_reemit.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_uint32,
-                                          C.c_uint32, C.c_int, C.c_double, C.c_int, _D, _I32]
-            L.orc_plane_step.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_int64, C.c_int,
-                                         C.POINTER(Plane), _D, C.c_double, _I64, C.c_int64, _D, _D,
-                                         _D, _D, _D, _D, _I32, _U32, _U32, _I64, _D, _U32, _I64]
-            L.orc_plane_step.restype = C.c_int
-            L.orc_plane_reconstruct.argtypes = [C.POINTER(Plane), _I64, _D, _D, C.c_int, C.c_double,
-                                                C.c_double, _D]
-            L.orc_inflow_flux.argtypes = [C.c_double, C.c_double, C.c_double]
-            L.orc_inflow_flux.restype = C.c_double
-            L.orc_inflow_normal_speed.argtypes = [C.c_double, C.c_double, C.c_uint32, C.c_uint32,
-                                                  C.c_uint64, C.c_int, _U32]
-            L.orc_inflow_normal_speed.restype = C.c_double
-            L.orc_plane_nleaf.argtypes = [C.POINTER(Plane)]
-            L.orc_plane_leaves.argtypes = [C.POINTER(Plane), C.POINTER(C.c_int32),
-                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
-            L.orc_plane_leaf_of.argtypes = [C.POINTER(Plane), C.c_double, C.c_double]
-            L.orc_fpm_coeffs.argtypes = [C.POINTER(Species)] + [C.c_double] * 5 + \
-                [C.POINTER(FpmCoeffs)]
-            L.orc_gillespie.argtypes = [C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
-                                        C.c_uint32, C.c_int, _U32]
-            L.orc_homog_step_fpm.argtypes = L.orc_homog_step.argtypes
-            _lib = L
+            _lib = _bind(C.CDLL(build()))
     return _lib
 
 
