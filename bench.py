@@ -9,8 +9,9 @@ state with FP64 cell sums and coefficients.  Synthetic, seeded inputs.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One JSON line is printed by rank 0.  ``value`` is particle-steps/s of the whole
-job (all ranks; each rank runs its own 4096 instances: weak scaling, no
-collective on the data path), from CUDA events on the library's stream with the
+job (all ranks: N GPUs share one population of N x 4096 instances, split by
+particle count -- weak scaling, no collective on the data path), from CUDA
+events on the library's stream with the
 state resident in HBM.  ``e2e`` repeats the measurement through the C-ABI call
 on pinned host buffers (state uploaded and moments read back every step).
 ``roofline`` rates the dominant kernel (the particle collide pass) against the
@@ -162,13 +163,41 @@ def hbm_peak():
 
 
 def rank_seed(rank):
-    """Each rank simulates its own independent instances (weak scaling)."""
+    """Key of the Philox stream of a rank's instances: the ranks' streams are
+    independent (particle ids are positions within a rank's arrays)."""
     return 1 + 1000 * rank
 
 
-def workload(rank, scale):
+def partition(counts, world):
+    """Instances of one workload split over ``world`` ranks by particle count
+    (longest processing time first: the largest remaining instance goes to
+    the rank with the fewest particles), each rank's list ascending.  With
+    item sizes far below the per-rank total, the ranks' particle counts differ
+    by less than the largest instance."""
+    import heapq
+    order = sorted(range(len(counts)), key=lambda i: (-int(counts[i]), i))
+    heap = [(0, r) for r in range(world)]
+    parts = [[] for _ in range(world)]
+    for i in order:
+        tot, r = heapq.heappop(heap)
+        parts[r].append(i)
+        heapq.heappush(heap, (tot + int(counts[i]), r))
+    return [sorted(p) for p in parts]
+
+
+def workload(rank, scale, world=1):
+    """The batched workload of a world of ``world`` ranks: one population of
+    world x 4096 instances (weak scaling: the same particles per GPU on
+    average at every world size), partitioned over the ranks by particle
+    count with no collective; ``rank``'s share."""
     from paper_2508_05642_gb300 import inputs as I
-    return I.batched_instances(seed=rank_seed(rank), n_inst=N_INST, steps=500, scale=scale)
+    n_inst = N_INST * world
+    counts, _ = I.batched_parameters(seed=1, n_inst=n_inst, scale=scale)
+    mine = partition(counts, world)[rank]
+    w = I.batched_instances(seed=1, n_inst=n_inst, steps=500, scale=scale,
+                            select=None if world == 1 else mine)
+    w.seed = rank_seed(rank)
+    return w
 
 
 class RankReducer:
@@ -205,7 +234,8 @@ def config_of(w, steps, precision="f32"):
             "instances": w.n_cells, "particles_per_gpu": w.n_particles,
             "steps_timed": steps, "dt": "0.5 tau_c per instance",
             "l2": "inputs larger than L2 (state %.1f GB per GPU)" % (w.n_particles * 20 / 1e9),
-            "parallelism": "independent instances per GPU (weak scaling, no collective)"}
+            "parallelism": "one population of 4096 x N instances partitioned over the N GPUs by "
+                           "particle count (weak scaling, no collective)"}
 
 
 def cpu_baseline(w, target_s, fixed_steps=None):
@@ -281,7 +311,7 @@ def run_ours(args, rank, world, local):
     red = RankReducer(dist, "cuda")
     barrier, max_over_ranks, sum_over_ranks = red.barrier, red.max, red.sum
 
-    w = workload(rank, args.scale)
+    w = workload(rank, args.scale, world)
     dt = np.array([w.dt_over_tau_c * usp.usp_tau_c(w.species, w.ndens[i], w.T_nominal[i, 0])
                    for i in range(w.n_cells)])
     p = w.particles

@@ -50,8 +50,8 @@ typedef enum {
   USP_ENOTSUP = -5   /* the request is not supported by this context       */
 } usp_err;
 
-/* Device status bits (usp_status).  Bits 0x02, 0x40, 0x80, 0x200, 0x400 are errors;
- * the others report clamps the method applies and continues. */
+/* Device status bits (usp_status).  Bits 0x40, 0x80, 0x200, 0x400 and 0x1000
+ * are errors; the others report clamps the method applies and continues. */
 enum {
   USP_F_PB_CLAMP = 0x01,            /* p_B > 1 met (Sec. 3.A.2): binomial clamped to n   */
   USP_F_CHOL_FAIL_AFTER_FIX = 0x02, /* T_tr^rel = 0 at the nu = 0 end of the Sec. 3.A.3
@@ -265,6 +265,55 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
 int usp_channel_sample(usp_ctx* ctx, int on);
 int usp_channel_read(usp_ctx* ctx, double* h_acc, int reset);
 
+/* Time-averaged profiles of a channel context, formed on the device from the
+ * sums pooled over the sampled steps (usp_channel_sample): USP_NPROF fields
+ * per cell, field-major (out[f * ny + cell]):
+ *   0 mean particle count per sampled step | 1-3 U (m/s) | 4 T_tr |
+ *   5 T_rot | 6 T_vib (K)
+ * with the pooled sample means of Sec. 2.A (ensemble averages as 1/N means
+ * over every particle-step of the window): U = sum c / sum N,
+ * T_tr = (sum |c|^2 / sum N - |U|^2) / 3R, T_rot = sum eps / (R sum N),
+ * T_vib inverting e_vib at the mean level (0 for no excitation).  Cells
+ * that held no particle give zeros.  In the USP_FP64_TANGENT form out holds
+ * 4 such blocks of USP_NPROF * ny doubles: the profiles, then their
+ * derivatives with respect to Z_rot, omega and T_wall (0 for the count and
+ * T_vib: counts and levels are held).  out_is_device = 1: device memory,
+ * asynchronous; 0: host memory, synchronises.  USP_EINVAL for a context
+ * that is not a channel. */
+#define USP_NPROF 7
+int usp_profiles(usp_ctx* ctx, double* out, int out_is_device);
+
+/* Gradient of a scalar objective L(profiles) with respect to the parameters
+ * (Z_rot, omega, T_wall) of a USP_FP64_TANGENT channel context: the pathwise
+ * derivative under common random numbers,
+ *   grad3[k] = sum_{f, cell} dL_dprof[f * ny + cell] * d prof[f][cell] / d theta_k,
+ * contracted on the device from the derivative sums the run accumulated.
+ * The derivative holds every discrete outcome (levels, cell membership,
+ * wall events and their times, the Cholesky / positivity-fix branch and
+ * root, the +-1 level picks) and the particle positions at their values.
+ *   d_dL_dprof: device, USP_NPROF * ny doubles (layout of usp_profiles).
+ *   grad3:      3 doubles; grad_is_device = 1: device memory, asynchronous;
+ *               0: host memory, synchronises.
+ * USP_ENOTSUP for another form or kind of context.  Enqueued on the
+ * context's stream after the steps it differentiates. */
+int usp_backward(usp_ctx* ctx, const double* d_dL_dprof, double* grad3, int grad_is_device);
+
+/* Checkpoints (channel and homogeneous contexts): everything a step carries
+ * into the next one -- the particle state with its pending conservation
+ * rescale, the per-cell records (and the jump tables of the FP32 form), the
+ * time-average sums and sampling switch, the step counter, the status word
+ * and counters -- as one opaque buffer of usp_checkpoint_bytes bytes.
+ * usp_save writes it into buf; usp_load restores a context created with the
+ * same sizes, form, method and seed from it, after which the run continues
+ * bit for bit as the one that saved it.  buf_is_device = 1: device memory,
+ * asynchronous on the context's stream; 0: host memory, synchronises.
+ * usp_load returns USP_EINVAL for a buffer from another kind of context
+ * (header mismatch) and leaves the context unchanged then; plane contexts
+ * return USP_ENOTSUP. */
+int usp_checkpoint_bytes(usp_ctx* ctx, size_t* bytes);
+int usp_save(usp_ctx* ctx, void* buf, int buf_is_device);
+int usp_load(usp_ctx* ctx, const void* buf, int buf_is_device);
+
 /* Current channel particles (cell order, conservation rescale applied) to
  * host arrays of length n; y and pid may be NULL.  Synchronises. */
 int usp_channel_get_particles(usp_ctx* ctx, double* h_y, double* h_cx, double* h_cy,
@@ -354,9 +403,29 @@ int usp_step_host(usp_ctx* ctx, const void* h_cx, const void* h_cy, const void* 
 
 /* Read (and clear with reset != 0) the sticky status word and counters.
  * Synchronises.  Returns USP_EDEVICE if an error bit is set: USP_F_A_NONPOS,
- * USP_F_SAMPLER_UNDERFLOW, USP_F_BOUNDS or USP_F_CAPACITY; the other bits
- * record clamps and caps the method's readings define. */
+ * USP_F_SAMPLER_UNDERFLOW, USP_F_BOUNDS, USP_F_CAPACITY or
+ * USP_F_WAIT_TIMEOUT; the other bits record clamps and caps the method's
+ * readings define. */
 int usp_status(usp_ctx* ctx, uint32_t* flags, int64_t counters[USP_NCOUNTERS], int reset);
+
+/* Limit, in SM clock cycles, of every wait of the homogeneous particle pass
+ * on its bulk copies (cycles = 0 restores the default of 2e9, about a
+ * second).  A wait that runs out sets USP_F_WAIT_TIMEOUT (usp_status then
+ * returns USP_EDEVICE): the pass stops there, waits with the default limit
+ * for its own copies still in flight and returns, leaving that step's state
+ * incomplete.  Synchronises the stream and drops a captured graph.
+ * USP_ENOTSUP for channel and plane contexts, USP_EINVAL for cycles < 0. */
+int usp_set_wait_limit(usp_ctx* ctx, int64_t cycles);
+
+/* Check of the device-side timeout path, for callers that monitor a run:
+ * enqueues on the context's stream one block that waits, with the same
+ * bounded wait as the particle pass and a limit of `cycles` SM clock cycles
+ * (1 .. 2e9), on an mbarrier that nothing completes.  When the limit runs
+ * out the block records USP_F_WAIT_TIMEOUT in the context's status word and
+ * returns, so a following usp_status reports USP_EDEVICE; the context's
+ * state is untouched and stays usable after usp_status(..., reset = 1).
+ * USP_EINVAL for cycles out of range. */
+int usp_wait_check(usp_ctx* ctx, int64_t cycles);
 
 /* Wait for all work of the context. */
 int usp_sync(usp_ctx* ctx);
@@ -417,9 +486,14 @@ int usp_profile_read(usp_ctx* ctx, double ms[2], int64_t launches[2]);
  *              the call returns without waiting.
  * Working space is one fixed device array of 20 * USP_NOALLOC_MAX_CELLS
  * doubles (1.25 MiB) that every device loading the library holds until the
- * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  All calls share the array and it keeps
+ * process exits.  Under CUDA's default lazy module loading the array is
+ * reserved when the library's module is loaded on a device, at the first call
+ * there at the latest; that call also looks up the array's device address
+ * (cudaGetSymbolAddress) with the device current.  Make one warm-up call at
+ * start-up, before any stream capture (or set CUDA_MODULE_LOADING=EAGER);
+ * the address is kept, so a cudaDeviceReset between calls is not supported.
+ * An error pending from the caller's earlier work (cudaPeekAtLastError)
+ * makes the call return USP_ECUDA without launching.  All calls share the array and it keeps
  * the last call's contents: each call clears it on its stream first, and
  * calls whose work overlaps on the GPU race on it.  No cudaMalloc, cudaFree
  * or other allocating routine is called. */

@@ -214,6 +214,12 @@ def _bind(L):
                                    C.POINTER(Channel), C.c_double, C.c_int64, _D, _D, _D, _D, _D,
                                    _I32, _U32, _I64, _D, _U32, _I64]
     L.orc_channel_step.restype = C.c_int
+    L.orc_channel_step_frozen.argtypes = L.orc_channel_step.argtypes + [C.c_void_p]
+    L.orc_channel_step_frozen.restype = C.c_int
+    L.orc_declog_new.restype = C.c_void_p
+    L.orc_declog_free.argtypes = [C.c_void_p]
+    L.orc_declog_set_mode.argtypes = [C.c_void_p, C.c_int]
+    L.orc_declog_stats.argtypes = [C.c_void_p, _I64]
     L.orc_channel_reconstruct.argtypes = [C.POINTER(Channel), _I64, _D, C.c_int, C.c_double, _D]
     L.orc_wall_reemit.argtypes = [C.POINTER(Species), C.c_int, C.c_uint64, C.c_uint32,
                                   C.c_uint32, C.c_int, C.c_double, C.c_int, _D, _I32]
@@ -484,6 +490,89 @@ def channel_step(sp, form, seed, step0, nsteps, ch: Channel, dt, st: ChannelStat
                                 _p(st.cz, C.c_double), _p(st.erot, C.c_double), _p(st.lev, C.c_int32),
                                 _p(st.pid, C.c_uint32), _p(off, C.c_int64), accp, C.byref(fl),
                                 _p(cnt, C.c_int64))
+    if rc != 0:
+        raise ValueError("cell coefficients undefined in some cell (mu/p not positive and finite)")
+    return off, fl.value, cnt
+
+
+def channel_profiles(acc, ny: int, sp: Species):
+    """Time-averaged profiles (7, ny) from the channel's pooled sums: mean
+    particle count per sampled step, U (3), T_tr, T_rot, T_vib -- the sample
+    means of Sec. 2.A over every particle-step of the window (T_tr from the
+    pooled second moment less |U|^2, T_vib inverting e_vib at the mean
+    level).  Cells that never held a particle give zeros."""
+    acc = np.asarray(acc, dtype=np.float64)
+    A = acc[: ny * NACC].reshape(ny, NACC)
+    steps = acc[ny * NACC]
+    N = A[:, 0]
+    out = np.zeros((7, ny))
+    m = N > 0
+    Nm = N[m]
+    U = A[m, 1:4] / Nm[:, None]
+    Rg = R(sp)
+    out[0, m] = Nm / steps if steps > 0 else 0.0
+    out[1:4, m] = U.T
+    out[4, m] = (A[m, 4:7].sum(axis=1) / Nm - (U ** 2).sum(axis=1)) / (3.0 * Rg)
+    out[5, m] = A[m, 10] / (Nm * Rg)
+    out[6, m] = [T_vib_from_mean_level(sp, e) for e in A[m, 11] / Nm]
+    return out
+
+
+class DecisionLog:
+    """Record / replay of every discrete decision of a channel run (the
+    frozen-discrete form used to check pathwise gradients by finite
+    differences): ``record()`` before the base run, ``replay()`` before each
+    perturbed run."""
+
+    OFF, RECORD, REPLAY = 0, 1, 2
+
+    def __init__(self):
+        self._L = lib()
+        self.h = self._L.orc_declog_new()
+        if not self.h:
+            raise MemoryError("orc_declog_new")
+
+    def record(self):
+        self._L.orc_declog_set_mode(self.h, self.RECORD)
+
+    def replay(self):
+        self._L.orc_declog_set_mode(self.h, self.REPLAY)
+
+    def off(self):
+        self._L.orc_declog_set_mode(self.h, self.OFF)
+
+    def stats(self) -> dict:
+        """Decisions recorded (yes/no, integer), replayed decisions that
+        differ from the run's own, replay requests past the end."""
+        out = np.zeros(4, dtype=np.int64)
+        self._L.orc_declog_stats(self.h, _p(out, C.c_int64))
+        return {"bits": int(out[0]), "ints": int(out[1]), "mismatches": int(out[2]),
+                "overruns": int(out[3])}
+
+    def __del__(self):
+        h, self.h = getattr(self, "h", None), None
+        if h:
+            self._L.orc_declog_free(h)
+
+
+def channel_step_frozen(sp, form, seed, step0, nsteps, ch: Channel, dt, st: ChannelState,
+                        log: DecisionLog, acc=None):
+    """``channel_step`` with its discrete decisions recorded into or replayed
+    from ``log`` (USP-FPM method only)."""
+    n = len(st.y)
+    off = np.zeros(ch.ny + 1, dtype=np.int64)
+    fl = C.c_uint32(0)
+    cnt = np.zeros(NCOUNTERS, dtype=np.int64)
+    accp = _p(acc, C.c_double) if acc is not None else None
+    rc = lib().orc_channel_step_frozen(C.byref(sp), form, C.c_uint64(seed), step0, nsteps,
+                                       C.byref(ch), dt, n, _p(st.y, C.c_double),
+                                       _p(st.cx, C.c_double), _p(st.cy, C.c_double),
+                                       _p(st.cz, C.c_double), _p(st.erot, C.c_double),
+                                       _p(st.lev, C.c_int32), _p(st.pid, C.c_uint32),
+                                       _p(off, C.c_int64), accp, C.byref(fl),
+                                       _p(cnt, C.c_int64), C.c_void_p(log.h))
+    if rc == -3:
+        raise ValueError("the frozen-discrete channel step runs the USP-FPM method only")
     if rc != 0:
         raise ValueError("cell coefficients undefined in some cell (mu/p not positive and finite)")
     return off, fl.value, cnt

@@ -18,6 +18,111 @@
 #define SAMPLER_KCAP 4096        /* search cap of one inversion              */
 
 /* ======================================================================== */
+/* Decision log: the frozen-discrete form of a run.  The pathwise gradient   */
+/* of the method differentiates everything continuous and holds every        */
+/* discrete outcome at its value (levels, cell membership, wall events, the  */
+/* Cholesky / positivity-fix branch and root, the +-1 correction).  To       */
+/* check it by finite differences, the base run records each discrete        */
+/* decision in the order it is taken (mode 1) and the perturbed runs take    */
+/* the recorded decision instead of their own (mode 2), so that they follow  */
+/* the base run's branch with perturbed continuous values.  A replayed       */
+/* decision that differs from the one the perturbed run would have taken is  */
+/* counted.  Mode 0 (or no log) leaves every decision to the run.           */
+/* ======================================================================== */
+struct orc_declog {
+    int mode;
+    uint8_t* bits; int64_t nbits, capbits, rbit;
+    int32_t* ints; int64_t nints, capints, rint;
+    double* reals; int64_t nreals, capreals, rreal;
+    int64_t mismatches, overruns;
+};
+
+orc_declog* orc_declog_new(void)
+{
+    return (orc_declog*)calloc(1, sizeof(orc_declog));
+}
+
+void orc_declog_free(orc_declog* dl)
+{
+    if (!dl) return;
+    free(dl->bits); free(dl->ints); free(dl->reals); free(dl);
+}
+
+void orc_declog_set_mode(orc_declog* dl, int mode)
+{
+    dl->mode = mode;
+    dl->rbit = 0; dl->rint = 0; dl->rreal = 0; dl->mismatches = 0; dl->overruns = 0;
+    if (mode == 1) {
+        dl->nbits = 0; dl->nints = 0; dl->nreals = 0;
+        if (dl->bits) memset(dl->bits, 0, (size_t)dl->capbits);
+    }
+}
+
+void orc_declog_stats(const orc_declog* dl, int64_t out[4])
+{
+    out[0] = dl->nbits; out[1] = dl->nints; out[2] = dl->mismatches; out[3] = dl->overruns;
+}
+
+/* a yes/no decision */
+static int dec_b(orc_declog* dl, int v)
+{
+    v = v ? 1 : 0;
+    if (!dl || dl->mode == 0) return v;
+    if (dl->mode == 1) {
+        if (dl->nbits == dl->capbits * 8) {
+            int64_t cap = dl->capbits ? 2 * dl->capbits : 1 << 16;
+            dl->bits = (uint8_t*)realloc(dl->bits, (size_t)cap);
+            memset(dl->bits + dl->capbits, 0, (size_t)(cap - dl->capbits));
+            dl->capbits = cap;
+        }
+        if (v) dl->bits[dl->nbits >> 3] |= (uint8_t)(1u << (dl->nbits & 7));
+        dl->nbits += 1;
+        return v;
+    }
+    if (dl->rbit >= dl->nbits) { dl->overruns += 1; return v; }
+    int r = (dl->bits[dl->rbit >> 3] >> (dl->rbit & 7)) & 1;
+    dl->rbit += 1;
+    if (r != v) dl->mismatches += 1;
+    return r;
+}
+
+/* a continuous quantity held at the base run's value (a wall-event time) */
+static double dec_d(orc_declog* dl, double v)
+{
+    if (!dl || dl->mode == 0) return v;
+    if (dl->mode == 1) {
+        if (dl->nreals == dl->capreals) {
+            int64_t cap = dl->capreals ? 2 * dl->capreals : 1 << 12;
+            dl->reals = (double*)realloc(dl->reals, sizeof(double) * (size_t)cap);
+            dl->capreals = cap;
+        }
+        dl->reals[dl->nreals++] = v;
+        return v;
+    }
+    if (dl->rreal >= dl->nreals) { dl->overruns += 1; return v; }
+    return dl->reals[dl->rreal++];
+}
+
+/* an integer outcome (a level, a cell index, a rounded count) */
+static int64_t dec_i(orc_declog* dl, int64_t v)
+{
+    if (!dl || dl->mode == 0) return v;
+    if (dl->mode == 1) {
+        if (dl->nints == dl->capints) {
+            int64_t cap = dl->capints ? 2 * dl->capints : 1 << 16;
+            dl->ints = (int32_t*)realloc(dl->ints, sizeof(int32_t) * (size_t)cap);
+            dl->capints = cap;
+        }
+        dl->ints[dl->nints++] = (int32_t)v;
+        return v;
+    }
+    if (dl->rint >= dl->nints) { dl->overruns += 1; return v; }
+    int64_t r = dl->ints[dl->rint++];
+    if (r != v) dl->mismatches += 1;
+    return r;
+}
+
+/* ======================================================================== */
 /* Random numbers.  The paper names no generator; the method only needs      */
 /* independent uniforms and standard normals per particle and per cell.      */
 /* Philox4x32-10 is Salmon, Moraes, Dror & Shaw, "Parallel random numbers:   */
@@ -238,10 +343,10 @@ int orc_cell_coeffs(const orc_species* sp, double n, double dt,
  * fix, Eq. alpha_USP_positivity_4), so the one alpha passed in is used.
  * Negative results (possible only for very large dt) are clamped to zero and
  * flagged. */
-void orc_relaxation_temperatures(const orc_species* sp, const orc_coeffs* cc, double alpha,
-                                 double T_tr, double T_rot, double T_vib,
-                                 double* T_tr_rel, double* T_rot_rel, double* e_vib_rel,
-                                 uint32_t* flags)
+static void relaxation_temperatures(const orc_species* sp, const orc_coeffs* cc, double alpha,
+                                    double T_tr, double T_rot, double T_vib,
+                                    double* T_tr_rel, double* T_rot_rel, double* e_vib_rel,
+                                    uint32_t* flags, orc_declog* dl)
 {
     double R = orc_R(sp);
     double oma2 = 1.0 - alpha * alpha;
@@ -251,10 +356,19 @@ void orc_relaxation_temperatures(const orc_species* sp, const orc_coeffs* cc, do
                         / (oma2 * R);
     double evr = orc_e_vib(sp, T_vib)
                + (cc->gamma_tr_vib * (T_tr - T_vib) + cc->gamma_rot_vib * (T_rot - T_vib)) / oma2;
-    if (ttr < 0.0) { ttr = 0.0; *flags |= ORC_F_TREL_CLAMP; }
-    if (tro < 0.0) { tro = 0.0; *flags |= ORC_F_TREL_CLAMP; }
-    if (evr < 0.0) { evr = 0.0; *flags |= ORC_F_TREL_CLAMP; }
+    if (dec_b(dl, ttr < 0.0)) { ttr = 0.0; *flags |= ORC_F_TREL_CLAMP; }
+    if (dec_b(dl, tro < 0.0)) { tro = 0.0; *flags |= ORC_F_TREL_CLAMP; }
+    if (dec_b(dl, evr < 0.0)) { evr = 0.0; *flags |= ORC_F_TREL_CLAMP; }
     *T_tr_rel = ttr; *T_rot_rel = tro; *e_vib_rel = evr;
+}
+
+void orc_relaxation_temperatures(const orc_species* sp, const orc_coeffs* cc, double alpha,
+                                 double T_tr, double T_rot, double T_vib,
+                                 double* T_tr_rel, double* T_rot_rel, double* e_vib_rel,
+                                 uint32_t* flags)
+{
+    relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, T_tr_rel, T_rot_rel, e_vib_rel,
+                            flags, NULL);
 }
 
 /* ======================================================================== */
@@ -467,19 +581,19 @@ int orc_sample_b(int n, double p, double u, int form, uint32_t* flags)
 /*    not definite, nu = 0 with alpha^2 = B (counted); only a T_tr^rel of   */
 /*    zero then is flagged as a failure.                                    */
 /* ======================================================================== */
-void orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
-                          const double U[3], const double Pi[6],
-                          double T_tr, double T_rot, double T_vib,
-                          const double G[4], double u5, double u6,
-                          double c[3], double* erot, int32_t* lev,
-                          uint32_t* flags, int64_t* counters)
+static void collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
+                             const double U[3], const double Pi[6],
+                             double T_tr, double T_rot, double T_vib,
+                             const double G[4], double u5, double u6,
+                             double c[3], double* erot, int32_t* lev,
+                             uint32_t* flags, int64_t* counters, orc_declog* dl)
 {
     double R = orc_R(sp);
     double alpha = cc->alpha;
     double nu = cc->nu_ref;
     double Ttr_rel, Trot_rel, evib_rel;
     uint32_t tf = 0;
-    orc_relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, &Ttr_rel, &Trot_rel, &evib_rel, &tf);
+    relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, &Ttr_rel, &Trot_rel, &evib_rel, &tf, dl);
 
     double M[6], L[6];
     M[0] = R * Ttr_rel + nu * (Pi[0] - R * T_tr);
@@ -488,7 +602,7 @@ void orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
     M[3] = nu * Pi[3];
     M[4] = nu * Pi[4];
     M[5] = nu * Pi[5];
-    if (!orc_cholesky3(M, L)) {
+    if (!dec_b(dl, orc_cholesky3(M, L))) {
         counters[ORC_C_CHOL_FIX] += 1;
         double lmin, lmax;
         orc_sym3_eig_minmax(Pi, &lmin, &lmax);
@@ -497,34 +611,34 @@ void orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
             /* Eq. nu_USP_positivity with the current T_tr^rel */
             double nref = cc->nu_ref;
             nu = nref;
-            if (nref <= 0.0) {
-                if (lmax - R * T_tr > 0.0) {
+            if (dec_b(dl, nref <= 0.0)) {
+                if (dec_b(dl, lmax - R * T_tr > 0.0)) {
                     double bound = -R * Ttr_rel / (lmax - R * T_tr);
-                    if (bound > nu) nu = bound;
+                    if (dec_b(dl, bound > nu)) nu = bound;
                 }
             } else {
-                if (R * T_tr - lmin > 0.0) {
+                if (dec_b(dl, R * T_tr - lmin > 0.0)) {
                     double bound = R * Ttr_rel / (R * T_tr - lmin);
-                    if (bound < nu) nu = bound;
+                    if (dec_b(dl, bound < nu)) nu = bound;
                 }
             }
             nu = nu * (1.0 - 1e-6);
             /* Eqs. alpha_USP_positivity_1 .. _4 */
             double a2 = (nu - cc->B) / (nu - 1.0);
-            if (a2 < 0.0) a2 = 0.0;
-            if (a2 > 1.0 - 1e-12) a2 = 1.0 - 1e-12;
+            if (dec_b(dl, a2 < 0.0)) a2 = 0.0;
+            if (dec_b(dl, a2 > 1.0 - 1e-12)) a2 = 1.0 - 1e-12;
             double ap = sqrt(a2), am = -ap;
             double prp = 2.0 * cc->mu_p * (1.0 - ap * ap * ap) / (cc->dt * (1.0 + ap * ap * ap));
             double prm = 2.0 * cc->mu_p * (1.0 - am * am * am) / (cc->dt * (1.0 + am * am * am));
-            alpha = (fabs(prm - cc->Pr) < fabs(prp - cc->Pr)) ? am : ap;
-            orc_relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, &Ttr_rel, &Trot_rel, &evib_rel, &tf);
+            alpha = dec_b(dl, fabs(prm - cc->Pr) < fabs(prp - cc->Pr)) ? am : ap;
+            relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, &Ttr_rel, &Trot_rel, &evib_rel, &tf, dl);
             M[0] = R * Ttr_rel + nu * (Pi[0] - R * T_tr);
             M[1] = R * Ttr_rel + nu * (Pi[1] - R * T_tr);
             M[2] = R * Ttr_rel + nu * (Pi[2] - R * T_tr);
             M[3] = nu * Pi[3];
             M[4] = nu * Pi[4];
             M[5] = nu * Pi[5];
-            ok = orc_cholesky3(M, L);
+            ok = dec_b(dl, orc_cholesky3(M, L));
         }
         if (!ok) {
             /* the passes approach the admissible nu from outside when
@@ -535,15 +649,16 @@ void orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
             counters[ORC_C_NU_ZERO] += 1;
             nu = 0.0;
             double a2 = cc->B;
-            if (a2 < 0.0) a2 = 0.0;
-            if (a2 > 1.0 - 1e-12) a2 = 1.0 - 1e-12;
+            if (dec_b(dl, a2 < 0.0)) a2 = 0.0;
+            if (dec_b(dl, a2 > 1.0 - 1e-12)) a2 = 1.0 - 1e-12;
             double ap = sqrt(a2), am = -ap;
             double prp = 2.0 * cc->mu_p * (1.0 - ap * ap * ap) / (cc->dt * (1.0 + ap * ap * ap));
             double prm = 2.0 * cc->mu_p * (1.0 - am * am * am) / (cc->dt * (1.0 + am * am * am));
-            alpha = (fabs(prm - cc->Pr) < fabs(prp - cc->Pr)) ? am : ap;
-            orc_relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, &Ttr_rel, &Trot_rel, &evib_rel, &tf);
-            double s = Ttr_rel > 0.0 ? sqrt(R * Ttr_rel) : 0.0;
-            if (!(Ttr_rel > 0.0)) *flags |= ORC_F_CHOL_FAIL_AFTER_FIX;
+            alpha = dec_b(dl, fabs(prm - cc->Pr) < fabs(prp - cc->Pr)) ? am : ap;
+            relaxation_temperatures(sp, cc, alpha, T_tr, T_rot, T_vib, &Ttr_rel, &Trot_rel, &evib_rel, &tf, dl);
+            int pos = dec_b(dl, Ttr_rel > 0.0);
+            double s = pos ? sqrt(R * Ttr_rel) : 0.0;
+            if (!pos) *flags |= ORC_F_CHOL_FAIL_AFTER_FIX;
             L[0] = s; L[1] = 0.0; L[2] = s; L[3] = 0.0; L[4] = 0.0; L[5] = s;
         }
     }
@@ -573,11 +688,22 @@ void orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
     double p_b = (1.0 + ebar) * (1.0 - a2);
     int I = *lev;
     uint32_t sf = 0;
-    int up = orc_sample_nb(I + 1, p_nb, u5, form, &sf);
-    int dn = orc_sample_b(I, p_b, u6, form, &sf);
+    int up = (int)dec_i(dl, orc_sample_nb(I + 1, p_nb, u5, form, &sf));
+    int dn = (int)dec_i(dl, orc_sample_b(I, p_b, u6, form, &sf));
     if (sf & ORC_F_PB_CLAMP) counters[ORC_C_PB_CLAMP] += 1;
     *flags |= sf;
     *lev = I + up - dn;
+}
+
+void orc_collide_particle(const orc_species* sp, int form, const orc_coeffs* cc,
+                          const double U[3], const double Pi[6],
+                          double T_tr, double T_rot, double T_vib,
+                          const double G[4], double u5, double u6,
+                          double c[3], double* erot, int32_t* lev,
+                          uint32_t* flags, int64_t* counters)
+{
+    collide_particle(sp, form, cc, U, Pi, T_tr, T_rot, T_vib, G, u5, u6, c, erot, lev, flags,
+                     counters, NULL);
 }
 
 /* ======================================================================== */
@@ -652,7 +778,7 @@ static void conserve_cell(const orc_species* sp, uint64_t seed, uint32_t cell, u
                           double e_tr_n, double e_rot_n, double e_vib_n, const double Un[3],
                           double e_rot_tgt, double e_vib_tgt,
                           double* cx, double* cy, double* cz, double* erot, int32_t* lev,
-                          uint32_t* flags, int64_t* counters)
+                          uint32_t* flags, int64_t* counters, orc_declog* dl)
 {
     double R = orc_R(sp);
     double Rth = R * sp->theta_v;
@@ -664,7 +790,7 @@ static void conserve_cell(const orc_species* sp, uint64_t seed, uint32_t cell, u
     for (int64_t j = b; j < e; ++j) sumI += lev[j];
     philox_words(cell, step, CELL_TAG(CELL_TAG_IDELTA), 0u, seed, w);
     double u = orc_uniform(w[0], 0);
-    int64_t Id = (int64_t)floor((double)N * e_vib_tgt / Rth - (double)sumI + u);
+    int64_t Id = dec_i(dl, (int64_t)floor((double)N * e_vib_tgt / Rth - (double)sumI + u));
     int64_t draws = 0, cap = 64 * N;
     while (Id != 0) {
         if (draws >= cap) { *flags |= ORC_F_VIB_LOOP_CAP; break; }
@@ -682,7 +808,7 @@ static void conserve_cell(const orc_species* sp, uint64_t seed, uint32_t cell, u
     double er_star = 0.0;
     for (int64_t j = b; j < e; ++j) er_star += erot[j];
     er_star /= N;
-    if (er_star > 0.0) {
+    if (dec_b(dl, er_star > 0.0)) {
         double r = e_rot_tgt / er_star;
         for (int64_t j = b; j < e; ++j) erot[j] = r * erot[j];
     }
@@ -702,7 +828,7 @@ static void conserve_cell(const orc_species* sp, uint64_t seed, uint32_t cell, u
     }
     etr_star /= N;
     double rad = (e_tr_n + e_rot_n + e_vib_n - e_rot_new - e_vib_new) / etr_star;
-    if (!(etr_star > 0.0) || !(rad > 0.0)) {
+    if (dec_b(dl, !(etr_star > 0.0) || !(rad > 0.0))) {
         *flags |= ORC_F_NEG_RADICAND;
         counters[ORC_C_NEG_RADICAND] += 1;
         return;
@@ -790,7 +916,7 @@ int orc_homog_step(const orc_species* sp, int form, uint64_t seed,
                 }
                 conserve_cell(sp, seed, (uint32_t)ci, step, b, e,
                               1.5 * R * T_tr, R * T_rot, orc_e_vib(sp, T_vib), U,
-                              cc.e_rot_tgt, cc.e_vib_tgt, cx, cy, cz, erot, lev, &lflags, lcnt);
+                              cc.e_rot_tgt, cc.e_vib_tgt, cx, cy, cz, erot, lev, &lflags, lcnt, NULL);
             }
         merge:
 #ifdef _OPENMP
@@ -1031,7 +1157,7 @@ int orc_homog_step_fpm(const orc_species* sp, int form, uint64_t seed,
                 }
                 conserve_cell(sp, seed, (uint32_t)ci, step, b, e,
                               1.5 * R * T_tr, R * T_rot, orc_e_vib(sp, T_vib), U,
-                              fc.e_rot_tgt, fc.e_vib_tgt, cx, cy, cz, erot, lev, &lflags, lcnt);
+                              fc.e_rot_tgt, fc.e_vib_tgt, cx, cy, cz, erot, lev, &lflags, lcnt, NULL);
             }
         merge:
 #ifdef _OPENMP
@@ -1066,7 +1192,8 @@ int orc_homog_step_fpm(const orc_species* sp, int form, uint64_t seed,
  * and (pid, step, 3, hit). */
 static void diffuse_reemit(const orc_species* sp, int form, uint64_t seed, uint32_t pid,
                            uint32_t step, int hit, double Tw, int into_positive_y,
-                           double* cx, double* cy, double* cz, double* erot, int32_t* lev)
+                           double* cx, double* cy, double* cz, double* erot, int32_t* lev,
+                           orc_declog* dl)
 {
     double R = orc_R(sp);
     uint32_t w[4], v[4];
@@ -1081,14 +1208,14 @@ static void diffuse_reemit(const orc_species* sp, int form, uint64_t seed, uint3
     *cz = s * g2;
     *erot = -R * Tw * log(orc_uniform(w[3], form));
     /* P(I >= k) = exp(-k Theta / T_w)  ->  I = floor(-ln(u) T_w / Theta) */
-    *lev = (int32_t)floor(-log(orc_uniform(v[0], form)) * Tw / sp->theta_v);
+    *lev = (int32_t)dec_i(dl, (int64_t)floor(-log(orc_uniform(v[0], form)) * Tw / sp->theta_v));
 }
 
 void orc_wall_reemit(const orc_species* sp, int form, uint64_t seed, uint32_t pid, uint32_t step,
                      int hit, double Tw, int into_positive_y, double out[4], int32_t* lev)
 {
     diffuse_reemit(sp, form, seed, pid, step, hit, Tw, into_positive_y,
-                   &out[0], &out[1], &out[2], &out[3], lev);
+                   &out[0], &out[1], &out[2], &out[3], lev, NULL);
 }
 
 /* Ballistic flight over dt with the body force along x, reflecting off the
@@ -1098,37 +1225,40 @@ void orc_wall_reemit(const orc_species* sp, int form, uint64_t seed, uint32_t pi
 static double advect_channel(const orc_species* sp, int form, uint64_t seed, uint32_t step,
                              const orc_channel* ch, double dt, double* y, double* cx, double* cy,
                              double* cz, double* erot, int32_t* lev, uint32_t pid,
-                             uint32_t* flags, int64_t* counters)
+                             uint32_t* flags, int64_t* counters, orc_declog* dl)
 {
     double t_left = dt, mom = 0.0;
     int hits = 0;
     for (;;) {
         double yn = *y + *cy * t_left;
-        if (yn >= 0.0 && yn <= ch->L) {
+        if (dec_b(dl, yn >= 0.0 && yn <= ch->L)) {
             *y = yn;
             *cx += ch->g * t_left;
             break;
         }
         if (hits >= WALL_HIT_CAP) {
             *flags |= ORC_F_WALL_CAP;
-            *y = yn < 0.0 ? 0.0 : ch->L;
+            *y = dec_b(dl, yn < 0.0) ? 0.0 : ch->L;
             *cx += ch->g * t_left;
             break;
         }
-        double wall = yn < 0.0 ? 0.0 : ch->L;
-        double t_hit = (wall - *y) / *cy;
-        if (t_hit < 0.0) t_hit = 0.0;
-        if (t_hit > t_left) t_hit = t_left;
+        double wall = dec_b(dl, yn < 0.0) ? 0.0 : ch->L;
+        /* the time of a wall event is held with the event itself */
+        double t_hit = dec_d(dl, (wall - *y) / *cy);
+        if (dec_b(dl, t_hit < 0.0)) t_hit = 0.0;
+        if (dec_b(dl, t_hit > t_left)) t_hit = t_left;
         *cx += ch->g * t_hit;
         mom += *cx;
         *y = wall;
         t_left -= t_hit;
         diffuse_reemit(sp, form, seed, pid, step, hits, ch->T_wall, wall == 0.0,
-                       cx, cy, cz, erot, lev);
+                       cx, cy, cz, erot, lev, dl);
         mom -= *cx;
         hits += 1;
         counters[ORC_C_WALL_HITS] += 1;
     }
+    /* the position after the move is held with the cell it selects */
+    *y = dec_d(dl, *y);
     return mom;
 }
 
@@ -1147,12 +1277,12 @@ static int channel_cell(const orc_channel* ch, double y)
  * neighbour being on the particle's side of the centroid (ties to +), or on
  * the opposite side when that neighbour is a wall or holds fewer than two
  * particles; with neither neighbour usable the cell value is used. */
-void orc_channel_reconstruct(const orc_channel* ch, const int64_t* counts, const double* F,
-                             int cell, double y, double* out)
+static void channel_reconstruct(const orc_channel* ch, const int64_t* counts, const double* F,
+                                int cell, double y, double* out, orc_declog* dl)
 {
     double dy = ch->L / ch->ny;
     double yc = (cell + 0.5) * dy;
-    int s = (y >= yc) ? 1 : -1;
+    int s = dec_b(dl, y >= yc) ? 1 : -1;
     int nb = cell + s;
     if (nb < 0 || nb >= ch->ny || counts[nb] < 2) {
         nb = cell - s;
@@ -1166,14 +1296,29 @@ void orc_channel_reconstruct(const orc_channel* ch, const int64_t* counts, const
     }
 }
 
+void orc_channel_reconstruct(const orc_channel* ch, const int64_t* counts, const double* F,
+                             int cell, double y, double* out)
+{
+    channel_reconstruct(ch, counts, F, cell, y, out, NULL);
+}
+
 /* stable reorder of all particle arrays by cell index */
 static void sort_by_cell(const orc_channel* ch, int64_t n, double* y, double* cx, double* cy,
-                         double* cz, double* erot, int32_t* lev, uint32_t* pid, int64_t* off)
+                         double* cz, double* erot, int32_t* lev, uint32_t* pid, int64_t* off,
+                         orc_declog* dl)
 {
     int ny = ch->ny;
     int* cell = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
     int64_t* pos = (int64_t*)calloc(ny + 1, sizeof(int64_t));
-    for (int64_t j = 0; j < n; ++j) { cell[j] = channel_cell(ch, y[j]); pos[cell[j] + 1] += 1; }
+    for (int64_t j = 0; j < n; ++j) {
+        int c = (int)dec_i(dl, channel_cell(ch, y[j]));
+        if (c < 0 || c >= ny) {
+            if (dl) dl->overruns += 1;
+            c = channel_cell(ch, y[j]);
+        }
+        cell[j] = c;
+        pos[cell[j] + 1] += 1;
+    }
     for (int c = 0; c < ny; ++c) pos[c + 1] += pos[c];
     for (int c = 0; c <= ny; ++c) off[c] = pos[c];
     double* tmp = (double*)malloc(sizeof(double) * 5 * (n > 0 ? n : 1));
@@ -1191,11 +1336,11 @@ static void sort_by_cell(const orc_channel* ch, int64_t n, double* y, double* cx
     free(tmp); free(tl); free(tp); free(cell); free(pos);
 }
 
-int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t step0,
-                     int nsteps, const orc_channel* ch, double dt, int64_t n,
-                     double* y, double* cx, double* cy, double* cz, double* erot,
-                     int32_t* lev, uint32_t* pid, int64_t* cell_off, double* acc,
-                     uint32_t* flags, int64_t* counters)
+static int channel_step(const orc_species* sp, int form, uint64_t seed, int64_t step0,
+                        int nsteps, const orc_channel* ch, double dt, int64_t n,
+                        double* y, double* cx, double* cy, double* cz, double* erot,
+                        int32_t* lev, uint32_t* pid, int64_t* cell_off, double* acc,
+                        uint32_t* flags, int64_t* counters, orc_declog* dl)
 {
     double R = orc_R(sp);
     int ny = ch->ny;
@@ -1214,9 +1359,9 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
         double wall_mom = 0.0;
         for (int64_t j = 0; j < n; ++j)
             wall_mom += advect_channel(sp, form, seed, step, ch, dt, &y[j], &cx[j], &cy[j], &cz[j],
-                                       &erot[j], &lev[j], pid[j], flags, counters);
+                                       &erot[j], &lev[j], pid[j], flags, counters, dl);
         /* 2. sort */
-        sort_by_cell(ch, n, y, cx, cy, cz, erot, lev, pid, cell_off);
+        sort_by_cell(ch, n, y, cx, cy, cz, erot, lev, pid, cell_off, dl);
         /* 3. cell moments and coefficients */
         for (int c = 0; c < ny; ++c) {
             int64_t b = cell_off[c], e = cell_off[c + 1], N = e - b;
@@ -1253,7 +1398,8 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
                 ok[c] = 1;
                 continue;
             }
-            if (orc_cell_coeffs(sp, nd, dt, T_tr, T_rot, T_vib, &cc[c]) != 0) {
+            int bad = orc_cell_coeffs(sp, nd, dt, T_tr, T_rot, T_vib, &cc[c]) != 0;
+            if (dec_b(dl, bad)) {
                 *flags |= ORC_F_A_NONPOS;
                 status = -1;
                 continue;
@@ -1277,8 +1423,8 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
                 }
                 double f[NFIELD];
                 if (ch->reconstruct) {
-                    orc_channel_reconstruct(ch, counts, F, c, y[j], f);
-                    if (!(f[3] > 0.0) || !(f[4] > 0.0) || !(f[5] >= 0.0)) {
+                    channel_reconstruct(ch, counts, F, c, y[j], f, dl);
+                    if (dec_b(dl, !(f[3] > 0.0) || !(f[4] > 0.0) || !(f[5] >= 0.0))) {
                         counters[ORC_C_INTERP_FALLBACK] += 1;
                         memcpy(f, Fc, sizeof(f));
                     }
@@ -1287,8 +1433,8 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
                 }
                 double G[4], u5, u6, cv[3] = { cx[j], cy[j], cz[j] };
                 particle_draws(seed, pid[j], step, form, G, &u5, &u6);
-                orc_collide_particle(sp, form, &cc[c], f, f + 6, f[3], f[4], f[5], G, u5, u6,
-                                     cv, &erot[j], &lev[j], flags, counters);
+                collide_particle(sp, form, &cc[c], f, f + 6, f[3], f[4], f[5], G, u5, u6,
+                                 cv, &erot[j], &lev[j], flags, counters, dl);
                 cx[j] = cv[0]; cy[j] = cv[1]; cz[j] = cv[2];
             }
         }
@@ -1300,7 +1446,7 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
                           1.5 * R * cellT[3 * c], R * cellT[3 * c + 1], orc_e_vib(sp, cellT[3 * c + 2]),
                           Fc, fcs ? fcs[c].e_rot_tgt : cc[c].e_rot_tgt,
                           fcs ? fcs[c].e_vib_tgt : cc[c].e_vib_tgt, cx, cy, cz, erot, lev, flags,
-                          counters);
+                          counters, dl);
         }
         /* 6. time-average sums */
         if (acc) {
@@ -1320,6 +1466,27 @@ int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t ste
     }
     free(F); free(cellT); free(counts); free(cc); free(fcs); free(ok);
     return status;
+}
+
+int orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t step0,
+                     int nsteps, const orc_channel* ch, double dt, int64_t n,
+                     double* y, double* cx, double* cy, double* cz, double* erot,
+                     int32_t* lev, uint32_t* pid, int64_t* cell_off, double* acc,
+                     uint32_t* flags, int64_t* counters)
+{
+    return channel_step(sp, form, seed, step0, nsteps, ch, dt, n, y, cx, cy, cz, erot, lev, pid,
+                        cell_off, acc, flags, counters, NULL);
+}
+
+int orc_channel_step_frozen(const orc_species* sp, int form, uint64_t seed, int64_t step0,
+                            int nsteps, const orc_channel* ch, double dt, int64_t n,
+                            double* y, double* cx, double* cy, double* cz, double* erot,
+                            int32_t* lev, uint32_t* pid, int64_t* cell_off, double* acc,
+                            uint32_t* flags, int64_t* counters, orc_declog* dl)
+{
+    if (ch->method != 0) return -3;
+    return channel_step(sp, form, seed, step0, nsteps, ch, dt, n, y, cx, cy, cz, erot, lev, pid,
+                        cell_off, acc, flags, counters, dl);
 }
 
 /* ======================================================================== */
@@ -1978,7 +2145,7 @@ int orc_plane_step(const orc_species* sp, int form, uint64_t seed, int64_t step0
                           1.5 * R * cellT[3 * c], R * cellT[3 * c + 1], orc_e_vib(sp, cellT[3 * c + 2]),
                           &F[c * NFIELD], fcs ? fcs[c].e_rot_tgt : cc[c].e_rot_tgt,
                           fcs ? fcs[c].e_vib_tgt : cc[c].e_vib_tgt, cx, cy, cz, erot, lev,
-                          flags, counters);
+                          flags, counters, NULL);
         }
         /* 7. time-average sums */
         if (acc) {

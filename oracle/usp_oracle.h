@@ -193,6 +193,31 @@ int    orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t 
                         uint32_t* flags, int64_t* counters);
 void   orc_channel_reconstruct(const orc_channel* ch, const int64_t* counts, const double* F,
                                int cell, double y, double* out);
+/* Frozen-discrete runs (gradient checks by finite differences): a decision
+ * log records every discrete decision of a channel run in the order it is
+ * taken (mode 1: record, clearing the log) and replays it in a later run
+ * (mode 2: replay from the start; mode 0: off).  The decisions are the
+ * wall events of the flight (inside or not, which wall, the event time and
+ * its clamps), the
+ * cell of each particle, the reconstruction side and its fall-back, the
+ * Cholesky test and every branch of the positivity fix (bounds, clamps,
+ * root), the relaxation-temperature clamps, the two jump outcomes, the wall
+ * re-emission level, the rounded level deficit I_Delta and the two guards
+ * of the conservation scaling.  A replaying run takes the recorded outcome;
+ * stats: decisions of each kind recorded (yes/no, integer), replayed
+ * decisions that differ from the run's own, and replay requests past the
+ * end of the log.  orc_channel_step_frozen is orc_channel_step with a log
+ * (USP-FPM method only; returns -3 for the plain FPM method). */
+typedef struct orc_declog orc_declog;
+orc_declog* orc_declog_new(void);
+void   orc_declog_free(orc_declog* dl);
+void   orc_declog_set_mode(orc_declog* dl, int mode);
+void   orc_declog_stats(const orc_declog* dl, int64_t out[4]);
+int    orc_channel_step_frozen(const orc_species* sp, int form, uint64_t seed, int64_t step0,
+                               int nsteps, const orc_channel* ch, double dt, int64_t n,
+                               double* y, double* cx, double* cy, double* cz, double* erot,
+                               int32_t* lev, uint32_t* pid, int64_t* cell_off, double* acc,
+                               uint32_t* flags, int64_t* counters, orc_declog* dl);
 /* one diffuse re-emission (velocity, eps_rot, level) for tests of the wall law */
 void   orc_wall_reemit(const orc_species* sp, int form, uint64_t seed, uint32_t pid, uint32_t step,
                        int hit, double Tw, int into_positive_y, double out[4], int32_t* lev);

@@ -141,7 +141,8 @@ __global__ void ch_advect(long long n, int ny, double L, double dy, S Tw, double
       break;
     }
     const T wall = yn < T(0) ? T(0) : (T)L;
-    T t_hit = (wall - yy) / vy;
+    // gradient form: the time of a wall event is held with the event
+    T t_hit = held((wall - yy) / vy);
     t_hit = t_hit < T(0) ? T(0) : (t_hit > t_left ? t_left : t_hit);
     vx += (T)g * t_hit;
     mom += (double)vx;
@@ -158,6 +159,9 @@ __global__ void ch_advect(long long n, int ny, double L, double dy, S Tw, double
     atomicAdd(wallmom, mom);
     atomicAdd(&counters[C_WALL_HITS], (unsigned long long)hits);
   }
+  // gradient form: the position is held with the cell it selects (through
+  // the interpolated fields its derivative would feed a chaotic response)
+  yy = held(yy);
   y[j] = yy; cx[j] = vx; cy[j] = vy; cz[j] = vz; er[j] = e; lev[j] = l;
   int k = cell_index(yy, dy);
   k = k < 0 ? 0 : (k >= ny ? ny - 1 : k);
@@ -432,34 +436,112 @@ __global__ void ch_collide_fpm(int ny, const ChCellT<double>* __restrict__ cells
   if (fla) atomicOr(flags, fla);
 }
 
-// time-average sums of the post-step state, binned by its cell
-// (gradient form: block 0 holds the sums, blocks 1..3 their derivatives)
+// time-average sums of the post-step state, one warp per cell (the state is
+// in cell order), each sum reduced across the warp in a fixed order and added
+// by one lane, so that runs are reproducible bit for bit (gradient form:
+// block 0 holds the sums, blocks 1..3 their derivatives)
 template <typename T, typename S>
-__global__ void ch_sample(long long n, int ny, const int* __restrict__ keycell,
+__global__ void ch_sample(int ny, const long long* __restrict__ off,
                           const ChCellT<S>* __restrict__ cells, const T* __restrict__ cx,
                           const T* __restrict__ cy, const T* __restrict__ cz,
                           const T* __restrict__ er, const int* __restrict__ lev,
                           double* __restrict__ acc, const double* __restrict__ wallmom) {
-  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const size_t blk = (size_t)ny * kNAcc + 2;
-  if (j == 0) {
-    atomicAdd(&acc[(size_t)ny * kNAcc], 1.0);
-    atomicAdd(&acc[(size_t)ny * kNAcc + 1], *wallmom);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    acc[(size_t)ny * kNAcc] += 1.0;
+    acc[(size_t)ny * kNAcc + 1] += *wallmom;
   }
-  if (j >= n) return;
-  const int k = keycell[j];
-  const ChCellT<S>& cc = cells[k];
-  const S v0 = cc.Un[0] + cc.s * (S(cx[j]) - cc.Us[0]);
-  const S v1 = cc.Un[1] + cc.s * (S(cy[j]) - cc.Us[1]);
-  const S v2 = cc.Un[2] + cc.s * (S(cz[j]) - cc.Us[2]);
-  const S e = cc.r * S(er[j]);
-  double* a = acc + (size_t)k * kNAcc;
-  atomicAdd(&a[0], 1.0);
-  acc_add(&a[1], blk, v0); acc_add(&a[2], blk, v1); acc_add(&a[3], blk, v2);
-  acc_add(&a[4], blk, v0 * v0); acc_add(&a[5], blk, v1 * v1); acc_add(&a[6], blk, v2 * v2);
-  acc_add(&a[7], blk, v0 * v1); acc_add(&a[8], blk, v0 * v2); acc_add(&a[9], blk, v1 * v2);
-  acc_add(&a[10], blk, e);
-  atomicAdd(&a[11], (double)lev[j]);
+  for (int k = warp_global(); k < ny; k += warps_total()) {
+    const ChCellT<S>& cc = cells[k];
+    S q[10];
+    for (int i = 0; i < 10; ++i) q[i] = S(0.0);
+    long long sl = 0;
+    const long long b = off[k], e = off[k + 1];
+    for (long long j = b + lane; j < e; j += 32) {
+      const S v0 = cc.Un[0] + cc.s * (S(cx[j]) - cc.Us[0]);
+      const S v1 = cc.Un[1] + cc.s * (S(cy[j]) - cc.Us[1]);
+      const S v2 = cc.Un[2] + cc.s * (S(cz[j]) - cc.Us[2]);
+      q[0] += v0; q[1] += v1; q[2] += v2;
+      q[3] += v0 * v0; q[4] += v1 * v1; q[5] += v2 * v2;
+      q[6] += v0 * v1; q[7] += v0 * v2; q[8] += v1 * v2;
+      q[9] += cc.r * S(er[j]);
+      sl += lev[j];
+    }
+    for (int i = 0; i < 10; ++i) q[i] = wsum(q[i]);
+    for (int o = 16; o > 0; o >>= 1) sl += __shfl_xor_sync(0xffffffffu, sl, o);
+    if (lane == 0) {
+      double* a = acc + (size_t)k * kNAcc;
+      a[0] += (double)(e - b);
+      for (int i = 0; i < 10; ++i) acc_add(&a[1 + i], blk, q[i]);
+      a[11] += (double)sl;
+    }
+  }
+}
+
+// Time-averaged profiles of cell c from the pooled sums: values (b = 0) or
+// their derivatives with respect to parameter b - 1 (gradient form), in the
+// field order of usp_profiles.  Counts and levels carry no derivative.
+__device__ void ch_prof_cell(const double* __restrict__ acc, int ny, int c, int b, double R,
+                             double theta, double* P) {
+  const size_t blk = (size_t)ny * kNAcc + 2;
+  const double* A = acc + (size_t)c * kNAcc;
+  const double N = A[0], ns = acc[(size_t)ny * kNAcc];
+  for (int f = 0; f < USP_NPROF; ++f) P[f] = 0.0;
+  if (!(N > 0.0)) return;
+  const double U0 = A[1] / N, U1 = A[2] / N, U2 = A[3] / N;
+  if (b == 0) {
+    P[0] = ns > 0.0 ? N / ns : 0.0;
+    P[1] = U0; P[2] = U1; P[3] = U2;
+    P[4] = ((A[4] + A[5] + A[6]) / N - (U0 * U0 + U1 * U1 + U2 * U2)) / (3.0 * R);
+    P[5] = A[10] / (N * R);
+    const double eb = A[11] / N;
+    P[6] = eb > 0.0 ? theta / log1p(1.0 / eb) : 0.0;
+    return;
+  }
+  const double* D = A + (size_t)b * blk;
+  const double d0 = D[1] / N, d1 = D[2] / N, d2 = D[3] / N;
+  P[1] = d0; P[2] = d1; P[3] = d2;
+  P[4] = ((D[4] + D[5] + D[6]) / N - 2.0 * (U0 * d0 + U1 * d1 + U2 * d2)) / (3.0 * R);
+  P[5] = D[10] / (N * R);
+}
+
+__global__ void ch_profiles(int ny, int blocks, const double* __restrict__ acc, double R,
+                            double theta, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ny) return;
+  double P[USP_NPROF];
+  for (int b = 0; b < blocks; ++b) {
+    ch_prof_cell(acc, ny, c, b, R, theta, P);
+    for (int f = 0; f < USP_NPROF; ++f) out[((size_t)b * USP_NPROF + f) * ny + c] = P[f];
+  }
+}
+
+// grad[k] += sum over cells and fields of dL[f * ny + c] d prof[f][c] / d theta_k
+// (grad zeroed before the launch)
+__global__ void ch_backward(int ny, const double* __restrict__ acc, double R,
+                            const double* __restrict__ dL, double* __restrict__ grad) {
+  __shared__ double red[kND][256 / 32];
+  double g[kND] = {0.0, 0.0, 0.0};
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ny; c += gridDim.x * blockDim.x) {
+    double P[USP_NPROF];
+    for (int k = 0; k < kND; ++k) {
+      ch_prof_cell(acc, ny, c, k + 1, R, 0.0, P);
+      for (int f = 0; f < USP_NPROF; ++f) g[k] += dL[(size_t)f * ny + c] * P[f];
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < kND; ++k) {
+    double v = g[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[k][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kND) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) v += red[threadIdx.x][w];
+    atomicAdd(&grad[threadIdx.x], v);
+  }
 }
 
 // on-demand moments (USP_NMOM fields) of the current state by cell key:
@@ -554,6 +636,8 @@ struct ChannelCtx {
   long long* dstep;
   int sampling;
   double* fpmrec;           // the plain FPM method: kFpmRec per-cell constants (else null)
+  double* prof;             // time-averaged profiles (USP_NPROF x ny per block)
+  double* grad;             // the objective's gradient (3 doubles, gradient form)
 };
 
 namespace {
@@ -652,8 +736,8 @@ int ch_step_t(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
                                   nullptr);
   CHK(cudaGetLastError());
   if (h->sampling) {
-    ch_sample<T, S><<<nb, 256, 0, s>>>(n, h->ny, h->keycell, cells, cx, cy, cz, er, h->lv[b],
-                                       h->acc, h->wallmom);
+    ch_sample<T, S><<<wb, 128, 0, s>>>(h->ny, h->off, cells, cx, cy, cz, er, h->lv[b], h->acc,
+                                       h->wallmom);
     CHK(cudaGetLastError());
   }
   if (prof) prof(env.owner, 1, 0);
@@ -721,7 +805,10 @@ int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double
   h->macc = (double*)A(sizeof(double) * 21 * h->ny);
   h->mout = (double*)A(sizeof(double) * USP_NMOM * h->ny);
   h->dstep = (long long*)A(sizeof(long long));
+  h->prof = (double*)A(sizeof(double) * USP_NPROF * h->ny * h->blocks);
+  h->grad = (double*)A(sizeof(double) * kND);
   bool ok = h->keycell && h->bh && h->off && h->cells && h->prm && h->sums && h->acc &&
+            h->prof && h->grad &&
             (env.sp.method != 1 || h->fpmrec) &&
             h->wallmom && h->macc && h->mout && h->dstep;
   for (int k = 0; k < 2; ++k) {
@@ -880,6 +967,76 @@ int ch_get_particles(ChannelCtx* h, const ChEnv& env, double* y, double* cx, dou
   }
   return USP_OK;
 }
+
+int ch_profiles(ChannelCtx* h, const ChEnv& env, double* out, int out_is_device) {
+  cudaStream_t s = env.stream;
+  ch_profiles<<<(h->ny + 127) / 128, 128, 0, s>>>(h->ny, h->blocks, h->acc, env.sp.R,
+                                                   env.sp.theta_v, h->prof);
+  CHK(cudaGetLastError());
+  CHK(cudaMemcpyAsync(out, h->prof, sizeof(double) * USP_NPROF * h->ny * h->blocks,
+                      out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!out_is_device) CHK(cudaStreamSynchronize(s));
+  return USP_OK;
+}
+
+int ch_backward(ChannelCtx* h, const ChEnv& env, const double* dL, double* grad3,
+                int grad_is_device) {
+  if (h->blocks != 1 + kND) return USP_ENOTSUP;
+  cudaStream_t s = env.stream;
+  CHK(cudaMemsetAsync(h->grad, 0, sizeof(double) * kND, s));
+  const int nb = std::min(1024, (h->ny + 255) / 256);
+  ch_backward<<<nb, 256, 0, s>>>(h->ny, h->acc, env.sp.R, dL, h->grad);
+  CHK(cudaGetLastError());
+  CHK(cudaMemcpyAsync(grad3, h->grad, sizeof(double) * kND,
+                      grad_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!grad_is_device) CHK(cudaStreamSynchronize(s));
+  return USP_OK;
+}
+
+// The device buffers a step carries into the next one, in checkpoint order:
+// the particle state of the current buffer (y, c, eps, levels, ids, cell
+// keys), the per-cell records (pending conservation rescale, step moments),
+// the time-average sums and the device step counter.
+static int ch_segments(ChannelCtx* h, void** ptr, size_t* bytes) {
+  const size_t nn = (size_t)std::max<long long>(h->n, 1);
+  const bool grad = h->blocks > 1;
+  const size_t cell_bytes = grad ? sizeof(ChCellT<D3>) : sizeof(ChCellT<double>);
+  int k = 0;
+  for (int f = 0; f < 5; ++f) { ptr[k] = h->st[h->cur][f]; bytes[k++] = nn * h->es; }
+  ptr[k] = h->lv[h->cur]; bytes[k++] = nn * 4;
+  ptr[k] = h->pd[h->cur]; bytes[k++] = nn * 4;
+  ptr[k] = h->keycell; bytes[k++] = nn * 4;
+  ptr[k] = h->cells; bytes[k++] = cell_bytes * h->ny;
+  ptr[k] = h->acc; bytes[k++] = sizeof(double) * ((size_t)h->ny * kNAcc + 2) * h->blocks;
+  ptr[k] = h->dstep; bytes[k++] = sizeof(long long);
+  return k;
+}
+
+size_t ch_ckpt_bytes(ChannelCtx* h) {
+  void* p[16];
+  size_t b[16], t = 0;
+  const int k = ch_segments(h, p, b);
+  for (int i = 0; i < k; ++i) t += b[i];
+  return t;
+}
+
+int ch_ckpt_copy(ChannelCtx* h, const ChEnv& env, unsigned char* buf, int buf_is_device,
+                 int save) {
+  void* p[16];
+  size_t b[16];
+  const int k = ch_segments(h, p, b);
+  cudaMemcpyKind kind = buf_is_device ? cudaMemcpyDeviceToDevice
+                                      : (save ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+  size_t o = 0;
+  for (int i = 0; i < k; ++i) {
+    if (save) CHK(cudaMemcpyAsync(buf + o, p[i], b[i], kind, env.stream));
+    else CHK(cudaMemcpyAsync(p[i], buf + o, b[i], kind, env.stream));
+    o += b[i];
+  }
+  return USP_OK;
+}
+
+int ch_sampling(const ChannelCtx* h) { return h->sampling; }
 
 int ch_ncell(const ChannelCtx* h) { return h->ny; }
 int ch_parity(const ChannelCtx* h) { return h->cur; }

@@ -37,6 +37,16 @@ int ch_sample(ChannelCtx* ch, int on);
 int ch_read(ChannelCtx* ch, const ChEnv& env, double* h_acc, int reset);
 int ch_get_particles(ChannelCtx* ch, const ChEnv& env, double* y, double* cx, double* cy,
                      double* cz, double* erot, int32_t* lev, uint32_t* pid);
+// time-averaged profiles (and their derivatives in the gradient form) and the
+// device-side contraction of their derivatives with an objective's gradient
+int ch_profiles(ChannelCtx* ch, const ChEnv& env, double* out, int out_is_device);
+int ch_backward(ChannelCtx* ch, const ChEnv& env, const double* dL, double* grad3,
+                int grad_is_device);
+// checkpoint payload: size, and copy to (save = 1) or from (save = 0) buf
+size_t ch_ckpt_bytes(ChannelCtx* ch);
+int ch_ckpt_copy(ChannelCtx* ch, const ChEnv& env, unsigned char* buf, int buf_is_device,
+                 int save);
+int ch_sampling(const ChannelCtx* ch);
 int ch_ncell(const ChannelCtx* ch);
 // which of the two particle buffers holds the state (steps alternate them)
 int ch_parity(const ChannelCtx* ch);

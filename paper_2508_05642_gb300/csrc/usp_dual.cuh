@@ -152,4 +152,10 @@ using dual::value;
 __device__ inline double value(double a) { return a; }
 __device__ inline float value(float a) { return a; }
 
+// A quantity held at its value in the gradient form: its derivative is
+// dropped (the identity in the plain forms).
+__device__ inline D3 held(const D3& a) { return D3(a.v); }
+__device__ inline double held(double a) { return a; }
+__device__ inline float held(float a) { return a; }
+
 }  // namespace usp

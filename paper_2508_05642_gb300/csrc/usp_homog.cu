@@ -151,41 +151,61 @@ __device__ void b_row(int n, float p, float* T) {
   }
 }
 
-// Search of a table row: the number of leading entries <= u.  Rows are
-// non-decreasing (cumulative sums, +inf once the sum stops growing), so the
-// entries <= u of a group of four are its leading ones and their count is
-// the step of the sequential search through the group.  The caller holds the
-// row's first group (t0, loaded before the particle's draws so that its
-// latency hides behind them); the rest of the row is read only when u lies
-// beyond all four.
-__device__ __forceinline__ int count4(const float4& t, float u) {
-  return (u >= t.x) + (u >= t.y) + (u >= t.z) + (u >= t.w);
+// Guide tables (the indexed search of Chen & Asau): per row, one byte for
+// each of the 256 bins of the uniform's top eight bits.  A float uniform
+// (2 (x >> 9) + 1) 2^-24 lies in bin m = x >> 24, between
+// umin(m) = (2 (m << 15) + 1) 2^-24 and umax(m) = (2 ((m << 15) + 32767) + 1) 2^-24.
+// The byte holds k = the number of row entries <= umin(m), with bit 7 set when
+// no entry lies in (umin(m), umax(m)], so that every uniform of the bin gives
+// exactly k; otherwise the search continues from k.  The outcome is the row
+// search's, so still the sequential inversion's, bit for bit.  A row whose
+// P(0) underflowed (T[0] = -1) gets 0xff bytes: k = 127 sends the particle to
+// the sequential search.
+constexpr int kGB = 256;   // guide bytes per row
+
+__device__ void guide_row(const float* __restrict__ T, uint8_t* __restrict__ g) {
+  uint32_t* g4 = reinterpret_cast<uint32_t*>(g);
+  if (T[0] < 0.0f) {
+    for (int q = 0; q < kGB / 4; ++q) g4[q] = 0xffffffffu;
+    return;
+  }
+  int k = 0;
+  for (int q = 0; q < kGB / 4; ++q) {
+    uint32_t word = 0;
+    for (int b = 0; b < 4; ++b) {
+      const int m = 4 * q + b;
+      const float umin = (float)(2 * (m << 15) + 1) * 5.9604644775390625e-8f;
+      const float umax = (float)(2 * ((m << 15) + 32767) + 1) * 5.9604644775390625e-8f;
+      while (k < kJK && T[k] <= umin) ++k;
+      const bool exact = k >= kJK || T[k] > umax;
+      word |= (uint32_t)(k | (exact ? 0x80 : 0)) << (8 * b);
+    }
+    g4[q] = word;
+  }
 }
 
-__device__ __forceinline__ int row_search(const float* __restrict__ T, const float4& t0,
-                                          float u) {
-  int k = count4(t0, u);
-  if (k < 4) return k;
-  const float4* T4 = reinterpret_cast<const float4*>(T);
+// number of leading row entries <= u, u formed from the word x
+__device__ __forceinline__ int guided_search(const float* __restrict__ T,
+                                             const uint8_t* __restrict__ g, uint32_t x, float u) {
+  const unsigned gv = __ldg(g + (x >> 24));
+  int k = (int)(gv & 0x7fu);
+  if (!(gv & 0x80u)) {
 #pragma unroll 1
-  for (int q = 1; q < kJK / 4; ++q) {
-    const int c = count4(T4[q], u);
-    k += c;
-    if (c < 4) break;
+    while (k < kJK && T[k] <= u) ++k;
   }
   return k;
 }
 
-__device__ __forceinline__ int nb_tab(const float* __restrict__ T, const float4& t0, int r,
-                                      float p, float u, uint32_t& fl) {
+__device__ __forceinline__ int nb_tab(const float* __restrict__ T, const uint8_t* __restrict__ g,
+                                      int r, float p, float u, uint32_t x, uint32_t& fl) {
   if (r <= 0 || !(p < 1.0f)) return 0;
-  if (r > kJR || t0.x < 0.0f) return nb_inv(r, p, u, fl);
-  const int k = row_search(T, t0, u);
+  if (r > kJR) return nb_inv(r, p, u, fl);
+  const int k = guided_search(T, g, x, u);
   return k < kJK ? k : nb_inv(r, p, u, fl);
 }
 
-__device__ __forceinline__ int b_tab(const float* __restrict__ T, const float4& t0, int n,
-                                     float p, float u, uint32_t& fl) {
+__device__ __forceinline__ int b_tab(const float* __restrict__ T, const uint8_t* __restrict__ g,
+                                     int n, float p, float u, uint32_t x, uint32_t& fl) {
   if (n <= 0) return 0;
   if (p >= 1.0f) {
     if (p > 1.0f) fl |= F_PB_CLAMP;
@@ -193,14 +213,18 @@ __device__ __forceinline__ int b_tab(const float* __restrict__ T, const float4& 
   }
   if (!(p > 0.0f)) return 0;
   const bool flip = p > 0.5f;
-  int k;
-  if (n >= kJR || t0.x < 0.0f) {
-    k = binv(n, flip ? rn_sub(1.0f, p) : p, u, fl);
-  } else {
-    k = row_search(T, t0, u);    // T[n] = +inf ends the scan by k = n < kJK
-  }
+  int k = n < kJR ? guided_search(T, g, x, u) : kJK;   // T[n] = +inf: k <= n < kJK
+  if (k >= kJK) k = binv(n, flip ? rn_sub(1.0f, p) : p, u, fl);
   return flip ? n - k : k;
 }
+
+// the per-cell jump tables and their guides (FP32 form)
+struct JumpTabs {
+  const float* nb;
+  const float* b;
+  const uint8_t* gnb;
+  const uint8_t* gb;
+};
 
 // ---------------------------------------------------------------------------
 // One particle: pending rescale, velocity, rotation, vibration.
@@ -210,19 +234,8 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
                                             const PhiloxRoundKeys& rk, T& cx, T& cy, T& cz, T& er,
                                             int& lv,
                                             T* acc, int& accI, int& maxI, uint32_t& fl,
-                                            const float* __restrict__ tnb,
-                                            const float* __restrict__ tb) {
-  // the particle's jump-table rows (FP32 form): first groups loaded ahead
+                                            const JumpTabs& jt) {
   const int I = lv;
-  const float* rnb = tnb;
-  const float* rb = tb;
-  float4 t_nb = make_float4(0.f, 0.f, 0.f, 0.f), t_b = t_nb;
-  if constexpr (sizeof(T) == 4 && METHOD == 0) {
-    rnb += (size_t)(I < kJR ? I : 0) * kJK;
-    rb += (size_t)(I < kJR ? I : 0) * kJK;
-    t_nb = __ldg(reinterpret_cast<const float4*>(rnb));
-    t_b = __ldg(reinterpret_cast<const float4*>(rb));
-  }
   U4 w, w2;
   philox4x32_10_pair(pid, P.step, PTAG_NORMALS, PTAG_JUMPS, 0u, rk, w, w2);
   T g0, g1, g2, g3;
@@ -237,7 +250,7 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   cy = P.U[1] + r1;
   cz = P.U[2] + r2;
   // eps' = a + (sqrt(eps^n) alpha + sqrt(a) G)^2, eps^n = r eps*
-  const T root = sqrt(er) * P.ar + P.sqrt_a * g3;
+  const T root = sqrt_fast(er) * P.ar + P.sqrt_a * g3;
   er = P.a_rot + root * root;
   // I' = I + NB(I + 1, p_NB) - B(I, p_B)
   const T u5 = uniform_open<T>(w2.x), u6 = uniform_open<T>(w2.y);
@@ -247,8 +260,10 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   } else {
     int up, dn;
     if constexpr (sizeof(T) == 4) {
-      up = nb_tab(rnb, t_nb, I + 1, P.p_nb, u5, fl);
-      dn = b_tab(rb, t_b, I, P.p_b, u6, fl);
+      // the particle's rows: NB r = I + 1 is row I, binomial n = I is row I
+      const size_t row = (size_t)(I < kJR ? I : 0);
+      up = nb_tab(jt.nb + row * kJK, jt.gnb + row * kGB, I + 1, P.p_nb, u5, w2.x, fl);
+      dn = b_tab(jt.b + row * kJK, jt.gb + row * kGB, I, P.p_b, u6, w2.y, fl);
     } else {
       up = sample_nb<T>(I + 1, P.p_nb, u5, fl);
       dn = sample_b<T>(I, P.p_b, u6, fl);
@@ -358,14 +373,34 @@ __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Bounded wait on an mbarrier phase: gives up after ~2e9 SM cycles (about a
-// second) and reports false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase: gives up after `limit` SM cycles and
+// reports false.  The waits of the particle pass take the context's limit
+// (usp_set_wait_limit; by default kWaitCycles, about a second); the waits of
+// a block that is leaving after a timeout, for its own copies still in
+// flight, always take kWaitCycles.
+constexpr long long kWaitCycles = 2000000000ll;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > 2000000000ll) return false;
+    if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+
+// Check of the timeout path: one block waits, with the bounded wait of the
+// particle pass, on an mbarrier phase that nothing completes (no thread
+// arrives on it, no copy is aimed at it), records USP_F_WAIT_TIMEOUT when
+// the limit runs out and returns.
+__global__ void wait_check_kernel(long long limit, uint32_t* flags) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit);
+  if (!ok && threadIdx.x == 0) atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
 }
 
 constexpr int kTileMax = 1024;   // particles per staged tile
@@ -455,7 +490,7 @@ collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
                     T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
                     int* __restrict__ lev, CellSums* __restrict__ sums, uint32_t* flags,
                     unsigned long long* counters, const PhiloxRoundKeys rk,
-                    const float* __restrict__ tab_nb, const float* __restrict__ tab_b) {
+                    const JumpTabs tabs, long long wait_cycles) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_all[kWarps][kWS];
   __shared__ __align__(16) CollideParams<T> Pw[kWarps];   // the warp's current cell
@@ -502,7 +537,7 @@ collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
       __syncwarp();
       cell = tl.cell;
     }
-    const bool ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u);
+    const bool ok = mbar_wait_bounded(&bar[s], (phase >> s) & 1u, wait_cycles);
     if (__any_sync(0xffffffffu, !ok)) {
       if (lane == 0) atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
       break;
@@ -514,15 +549,15 @@ collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
       T* X = reinterpret_cast<T*>(b);
       int* Lv = reinterpret_cast<int*>(b + 4 * kWT * sizeof(T));
       const uint32_t pid0 = P.pid0 + (uint32_t)tl.start;
-      const float* tnb = tab_nb + (size_t)tl.cell * kJR * kJK;
-      const float* tb = tab_b + (size_t)tl.cell * kJR * kJK;
+      const size_t tc = (size_t)tl.cell * kJR;
+      const JumpTabs jt{tabs.nb + tc * kJK, tabs.b + tc * kJK, tabs.gnb + tc * kGB,
+                        tabs.gb + tc * kGB};
 #pragma unroll 1
       for (int k = lane; k < tl.count; k += 32) {
         T x = X[k], y = X[k + kWT], z = X[k + 2 * kWT], e = X[k + 3 * kWT];
         int l = Lv[k];
         uint32_t f1 = 0;
-        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb,
-                               tb);
+        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, jt);
         X[k] = x; X[k + kWT] = y; X[k + 2 * kWT] = z; X[k + 3 * kWT] = e;
         Lv[k] = l;
         npb += (f1 & F_PB_CLAMP) ? 1 : 0;
@@ -579,7 +614,7 @@ collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
     // loads still in flight after a timeout: wait for them (bounded) before
     // the block's shared memory is released
     for (int q = 0; q < kWS; ++q)
-      if (inflight & (1u << q)) (void)mbar_wait_bounded(&bar[q], (phase >> q) & 1u);
+      if (inflight & (1u << q)) (void)mbar_wait_bounded(&bar[q], (phase >> q) & 1u, kWaitCycles);
     bulk_wait_all();
   }
 }
@@ -638,7 +673,7 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
                T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
                int* __restrict__ lev, CellSums* __restrict__ sums, uint32_t* flags,
                unsigned long long* counters, const PhiloxRoundKeys rk,
-               const float* __restrict__ tab_nb, const float* __restrict__ tab_b) {
+               const JumpTabs tabs, long long wait_cycles) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[2], empty[2];
   __shared__ int done[2];
@@ -677,7 +712,7 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
       // t - 1 there and its store has read it
       bool ok = true;
       if (it >= 1) {
-        ok = mbar_wait_bounded(&empty[b ^ 1], (eph >> (b ^ 1)) & 1u);
+        ok = mbar_wait_bounded(&empty[b ^ 1], (eph >> (b ^ 1)) & 1u, wait_cycles);
         eph ^= 1u << (b ^ 1);
       }
       if (ok) {
@@ -689,7 +724,7 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
       }
     }
     const Tile tl = tiles[t];
-    const bool ok = mbar_wait_bounded(&full[b], (fph >> b) & 1u);
+    const bool ok = mbar_wait_bounded(&full[b], (fph >> b) & 1u, wait_cycles);
     if (__any_sync(0xffffffffu, !ok)) {
       if (lane == 0) atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
       break;
@@ -702,15 +737,15 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
       T* X = sb_x<T>(buf);
       int* Lv = sb_l<T>(buf);
       const uint32_t pid0 = P.pid0 + (uint32_t)tl.start;
-      const float* tnb = tab_nb + (size_t)tl.cell * kJR * kJK;
-      const float* tb = tab_b + (size_t)tl.cell * kJR * kJK;
+      const size_t tc = (size_t)tl.cell * kJR;
+      const JumpTabs jt{tabs.nb + tc * kJK, tabs.b + tc * kJK, tabs.gnb + tc * kGB,
+                        tabs.gb + tc * kGB};
 #pragma unroll 1
       for (int k = tid; k < tl.count; k += kBlock) {
         T x = X[k], y = X[k + kTileMax], z = X[k + 2 * kTileMax], e = X[k + 3 * kTileMax];
         int l = Lv[k];
         uint32_t f1 = 0;
-        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, tnb,
-                               tb);
+        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, jt);
         X[k] = x; X[k + kTileMax] = y; X[k + 2 * kTileMax] = z; X[k + 3 * kTileMax] = e;
         Lv[k] = l;
         npb += (f1 & F_PB_CLAMP) ? 1 : 0;
@@ -765,7 +800,7 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
     // loads still in flight after a timeout: wait for them (bounded) before
     // the block's shared memory is released
     for (int q = 0; q < 2; ++q)
-      if (inflight & (1u << q)) (void)mbar_wait_bounded(&full[q], (fph >> q) & 1u);
+      if (inflight & (1u << q)) (void)mbar_wait_bounded(&full[q], (fph >> q) & 1u, kWaitCycles);
   }
 }
 
@@ -775,7 +810,8 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
 // rows the cell's levels can reach.
 __global__ void jumptable_kernel(int c0, int c1, const CollideParams<float>* __restrict__ prm,
                                  const CellState* __restrict__ cells, float* __restrict__ tab_nb,
-                                 float* __restrict__ tab_b) {
+                                 float* __restrict__ tab_b, uint8_t* __restrict__ gd_nb,
+                                 uint8_t* __restrict__ gd_b) {
   const int c = c0 + blockIdx.x;
   const int j = threadIdx.x;
   if (c >= c1) return;
@@ -786,6 +822,7 @@ __global__ void jumptable_kernel(int c0, int c1, const CollideParams<float>* __r
     const int r = j + 1;
     if (r > rows || !(P.p_nb < 1.0f)) return;
     nb_row(r, P.p_nb, tab_nb + ((size_t)c * kJR + j) * kJK);
+    guide_row(tab_nb + ((size_t)c * kJR + j) * kJK, gd_nb + ((size_t)c * kJR + j) * kGB);
   } else {
     const int n = j - kJR;
     if (n < 1 || n > rows - 1) return;
@@ -793,6 +830,7 @@ __global__ void jumptable_kernel(int c0, int c1, const CollideParams<float>* __r
     if (!(p < 1.0f) || !(p > 0.0f)) return;
     if (p > 0.5f) p = rn_sub(1.0f, p);
     b_row(n, p, tab_b + ((size_t)c * kJR + n) * kJK);
+    guide_row(tab_b + ((size_t)c * kJR + n) * kJK, gd_b + ((size_t)c * kJR + n) * kGB);
   }
 }
 
@@ -1300,8 +1338,11 @@ struct usp_ctx {
   double* macc;             // moment accumulators
   double* mout;             // moment output (device)
   double* levsum;
+  long long wait_cycles;    // limit of the particle pass's waits (SM cycles)
   float* tab_nb;            // jump tables (FP32 form)
   float* tab_b;
+  uint8_t* gd_nb;           // their guide tables
+  uint8_t* gd_b;
   uint32_t* flags;
   unsigned long long* counters;
   std::vector<long long> h_uoff;
@@ -1535,20 +1576,19 @@ int launch_collide_m(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, v
   const CollideParams<T>* prm = (const CollideParams<T>*)c->prm;
   T* x = (T*)cx; T* y = (T*)cy; T* z = (T*)cz; T* e = (T*)er;
   const PhiloxRoundKeys rk = philox_round_keys(key0(c), key1(c));
-  const float* tn = c->tab_nb;
-  const float* tb = c->tab_b;
+  const JumpTabs tb{c->tab_nb, c->tab_b, c->gd_nb, c->gd_b};
   if (warp_tiles) {
     const Tile* tiles = c->wtiles + r.w0;
     const int ntiles = r.w1 - r.w0;
     if (minb == 2)
       collide_warp_kernel<T, 2, METHOD><<<grid, kBlock, smem, c->stream>>>(
-          tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
+          tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tb, c->wait_cycles);
     else if (minb == 3)
       collide_warp_kernel<T, 3, METHOD><<<grid, kBlock, smem, c->stream>>>(
-          tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
+          tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tb, c->wait_cycles);
     else
       collide_warp_kernel<T, 4, METHOD><<<grid, kBlock, smem, c->stream>>>(
-          tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
+          tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tb, c->wait_cycles);
     CK(cudaGetLastError());
     return USP_OK;
   }
@@ -1556,13 +1596,13 @@ int launch_collide_m(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, v
   const int ntiles = r.t1 - r.t0;
   if (minb == 2)
     collide_kernel<T, 2, METHOD><<<grid, kBlock, smem, c->stream>>>(
-        tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
+        tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tb, c->wait_cycles);
   else if (minb == 3)
     collide_kernel<T, 3, METHOD><<<grid, kBlock, smem, c->stream>>>(
-        tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
+        tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tb, c->wait_cycles);
   else
     collide_kernel<T, 4, METHOD><<<grid, kBlock, smem, c->stream>>>(
-        tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tn, tb);
+        tiles, ntiles, prm, x, y, z, e, lev, sums, flags, counters, rk, tb, c->wait_cycles);
   CK(cudaGetLastError());
   return USP_OK;
 }
@@ -1581,7 +1621,8 @@ int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, voi
 int launch_tables(usp_ctx* c, const CellRange& r) {
   if (c->precision != USP_FP32 || c->sp.method != 0 || r.c1 <= r.c0) return USP_OK;
   jumptable_kernel<<<r.c1 - r.c0, 2 * kJR, 0, c->stream>>>(
-      r.c0, r.c1, (const CollideParams<float>*)c->prm, c->cells, c->tab_nb, c->tab_b);
+      r.c0, r.c1, (const CollideParams<float>*)c->prm, c->cells, c->tab_nb, c->tab_b, c->gd_nb,
+      c->gd_b);
   CK(cudaGetLastError());
   return USP_OK;
 }
@@ -1678,7 +1719,13 @@ int init_params(usp_ctx* c) {
 // and kept (the largest request so far), so a call makes no allocation.
 void* staging(usp_ctx* c, size_t bytes) {
   if (c->stage && c->stage_bytes >= bytes) return c->stage;
-  if (c->stage) dev_release(c, c->stage);
+  if (c->stage) {
+    // queued copies and kernels may still read the old buffer, and a caller's
+    // free callback is not stream-ordered: let them finish first
+    cudaStreamSynchronize(c->stream);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    dev_release(c, c->stage);
+  }
   c->stage = dev_alloc(c, bytes);
   c->stage_bytes = c->stage ? bytes : 0;
   return c->stage;
@@ -1745,6 +1792,9 @@ int step_host_chunked(usp_ctx* c, const void* hx, const void* hy, const void* hz
   const char* src[5] = {(const char*)hx, (const char*)hy, (const char*)hz, (const char*)he,
                         (const char*)hl};
   const size_t sz[5] = {es, es, es, es, 4};
+  // after the first copy is queued, an error return first waits for the
+  // copies from the caller's buffers still in flight
+  auto body = [&]() -> int {
   // the staging buffer is free once the context stream has passed this point
   CK(cudaEventRecord(c->up_ev[0], c->stream));
   CK(cudaStreamWaitEvent(c->copy_stream, c->up_ev[0], 0));
@@ -1777,6 +1827,13 @@ int step_host_chunked(usp_ctx* c, const void* hx, const void* hy, const void* hz
       c->launches += kernels_per_step(c);
     }
     if ((rc = compute_moments<T>(c, nullptr, r))) return rc;
+  }
+  return USP_OK;
+  };
+  const int rc = body();
+  if (rc) {
+    cudaStreamSynchronize(c->copy_stream);
+    return rc;
   }
   c->step += nsteps;
   return USP_OK;
@@ -1948,18 +2005,12 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   c->device_bytes = 0;
   c->profiling = 0;
   c->ev_used = 0;
-  if (cfg->stream) {
-    c->stream = (cudaStream_t)cfg->stream;
-    c->own_stream = false;
-  } else {
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete c;
-      return USP_ECUDA;
-    }
-    c->own_stream = true;
-  }
+  // the stream is made after the allocations, so that a failing allocator
+  // callback is reported (USP_ENOMEM) before any CUDA call
+  c->stream = nullptr;
+  c->own_stream = false;
   auto fail = [&](int rc) {
-    cudaStreamSynchronize(c->stream);
+    if (c->stream) cudaStreamSynchronize(c->stream);
     dev_free_all(c);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1997,18 +2048,32 @@ int usp_init_homogeneous(usp_ctx** out, const usp_species* sp, const usp_config*
   c->macc = (double*)dev_alloc(c, sizeof(double) * kMomAcc * n_cells);
   c->mout = (double*)dev_alloc(c, sizeof(double) * USP_NMOM * n_cells);
   c->levsum = (double*)dev_alloc(c, sizeof(double) * n_cells);
+  c->wait_cycles = kWaitCycles;
   c->tab_nb = nullptr;
   c->tab_b = nullptr;
+  c->gd_nb = nullptr;
+  c->gd_b = nullptr;
   if (c->precision == USP_FP32) {
     c->tab_nb = (float*)dev_alloc(c, sizeof(float) * (size_t)n_cells * kJR * kJK);
     c->tab_b = (float*)dev_alloc(c, sizeof(float) * (size_t)n_cells * kJR * kJK);
-    if (!c->tab_nb || !c->tab_b) return fail(USP_ENOMEM);
+    c->gd_nb = (uint8_t*)dev_alloc(c, (size_t)n_cells * kJR * kGB);
+    c->gd_b = (uint8_t*)dev_alloc(c, (size_t)n_cells * kJR * kGB);
+    if (!c->tab_nb || !c->tab_b || !c->gd_nb || !c->gd_b) return fail(USP_ENOMEM);
   }
   c->flags = (uint32_t*)dev_alloc(c, 256);
   c->counters = (unsigned long long*)dev_alloc(c, 256);
   if (!c->cx || !c->cy || !c->cz || !c->er || !c->lev || !c->cells || !c->prm || !c->sums ||
       !c->uoff || !c->macc || !c->mout || !c->levsum || !c->flags || !c->counters)
     return fail(USP_ENOMEM);
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->stream = nullptr;
+      return fail(USP_ECUDA);
+    }
+    c->own_stream = true;
+  }
   if (cudaMemsetAsync(c->cx, 0, c->nstore * es, c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->cy, 0, c->nstore * es, c->stream) != cudaSuccess ||
       cudaMemsetAsync(c->cz, 0, c->nstore * es, c->stream) != cudaSuccess ||
@@ -2395,6 +2460,167 @@ int usp_step_host(usp_ctx* c, const void* hx, const void* hy, const void* hz, co
   return USP_OK;
 }
 
+int usp_profiles(usp_ctx* c, double* out, int out_is_device) {
+  if (!c || c->kind != 1 || !out) return USP_EINVAL;
+  return ch_profiles(c->ch, make_env(c), out, out_is_device);
+}
+
+int usp_backward(usp_ctx* c, const double* d_dL, double* grad3, int grad_is_device) {
+  if (!c || !d_dL || !grad3) return USP_EINVAL;
+  if (c->kind != 1 || c->precision != USP_FP64_TANGENT) return USP_ENOTSUP;
+  return ch_backward(c->ch, make_env(c), d_dL, grad3, grad_is_device);
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoints: a header that identifies the context, the status word and
+// counters, then the kind's own device buffers in a fixed order.
+// ---------------------------------------------------------------------------
+struct CkptHeader {
+  uint32_t magic, version;
+  int32_t kind, precision, method, sampling;
+  int64_t n, ncell, step;
+  uint64_t seed, payload;
+};
+constexpr uint32_t kCkptMagic = 0x43505355u;   // "USPC"
+constexpr size_t kCkptStatus = 4 + 8 * NCOUNTERS;
+
+// homogeneous contexts: particles (storage order), cell records, the
+// parameters and jump tables of the coming step, the cell sums
+int homog_segments(usp_ctx* c, void** ptr, size_t* bytes) {
+  const size_t es = c->precision == USP_FP32 ? 4 : 8;
+  const size_t pb = c->precision == USP_FP32 ? sizeof(CollideParams<float>)
+                                             : sizeof(CollideParams<double>);
+  int k = 0;
+  ptr[k] = c->cx; bytes[k++] = c->nstore * es;
+  ptr[k] = c->cy; bytes[k++] = c->nstore * es;
+  ptr[k] = c->cz; bytes[k++] = c->nstore * es;
+  ptr[k] = c->er; bytes[k++] = c->nstore * es;
+  ptr[k] = c->lev; bytes[k++] = c->nstore * 4;
+  ptr[k] = c->cells; bytes[k++] = sizeof(CellState) * c->ncell;
+  ptr[k] = c->prm; bytes[k++] = pb * c->ncell;
+  ptr[k] = c->sums; bytes[k++] = sizeof(CellSums) * c->ncell;
+  if (c->tab_nb) {
+    ptr[k] = c->tab_nb; bytes[k++] = sizeof(float) * (size_t)c->ncell * kJR * kJK;
+    ptr[k] = c->tab_b; bytes[k++] = sizeof(float) * (size_t)c->ncell * kJR * kJK;
+    ptr[k] = c->gd_nb; bytes[k++] = (size_t)c->ncell * kJR * kGB;
+    ptr[k] = c->gd_b; bytes[k++] = (size_t)c->ncell * kJR * kGB;
+  }
+  return k;
+}
+
+size_t ckpt_payload(usp_ctx* c) {
+  if (c->kind == 1) return ch_ckpt_bytes(c->ch);
+  void* p[16];
+  size_t b[16], t = 0;
+  const int k = homog_segments(c, p, b);
+  for (int i = 0; i < k; ++i) t += b[i];
+  return t;
+}
+
+CkptHeader ckpt_header(usp_ctx* c) {
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = kCkptMagic;
+  h.version = 1;
+  h.kind = c->kind;
+  h.precision = c->precision;
+  h.method = c->sp.method;
+  h.sampling = c->kind == 1 ? ch_sampling(c->ch) : 0;
+  h.n = c->kind == 1 ? ch_nparticles(c->ch) : c->nparticles;
+  h.ncell = c->kind == 1 ? ch_ncell(c->ch) : c->ncell;
+  h.step = c->step;
+  h.seed = c->cfg.seed;
+  h.payload = ckpt_payload(c);
+  return h;
+}
+
+int usp_checkpoint_bytes(usp_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return USP_EINVAL;
+  if (c->kind == 2) return USP_ENOTSUP;
+  *bytes = sizeof(CkptHeader) + kCkptStatus + ckpt_payload(c);
+  return USP_OK;
+}
+
+int usp_save(usp_ctx* c, void* buf, int buf_is_device) {
+  if (!c || !buf) return USP_EINVAL;
+  if (c->kind == 2) return USP_ENOTSUP;
+  const CkptHeader h = ckpt_header(c);
+  unsigned char* b = (unsigned char*)buf;
+  const cudaMemcpyKind d2b = buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (buf_is_device) {
+    CK(cudaMemcpyAsync(b, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    // the header lives on the host stack: complete its copy before returning
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    std::memcpy(b, &h, sizeof(h));
+  }
+  b += sizeof(h);
+  CK(cudaMemcpyAsync(b, c->flags, 4, d2b, c->stream));
+  CK(cudaMemcpyAsync(b + 4, c->counters, 8 * NCOUNTERS, d2b, c->stream));
+  b += kCkptStatus;
+  if (c->kind == 1) {
+    const int rc = ch_ckpt_copy(c->ch, make_env(c), b, buf_is_device, 1);
+    if (rc) return rc;
+  } else {
+    void* p[16];
+    size_t sz[16];
+    const int k = homog_segments(c, p, sz);
+    for (int i = 0; i < k; ++i) {
+      CK(cudaMemcpyAsync(b, p[i], sz[i], d2b, c->stream));
+      b += sz[i];
+    }
+  }
+  if (!buf_is_device) CK(cudaStreamSynchronize(c->stream));
+  return USP_OK;
+}
+
+int usp_load(usp_ctx* c, const void* buf, int buf_is_device) {
+  if (!c || !buf) return USP_EINVAL;
+  if (c->kind == 2) return USP_ENOTSUP;
+  CkptHeader h;
+  const unsigned char* b = (const unsigned char*)buf;
+  if (buf_is_device) {
+    CK(cudaMemcpyAsync(&h, b, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    std::memcpy(&h, b, sizeof(h));
+  }
+  const CkptHeader mine = ckpt_header(c);
+  if (h.magic != kCkptMagic || h.version != mine.version || h.kind != mine.kind ||
+      h.precision != mine.precision || h.method != mine.method || h.n != mine.n ||
+      h.ncell != mine.ncell || h.seed != mine.seed || h.payload != mine.payload)
+    return USP_EINVAL;
+  // a captured graph replays the step of the state it was captured with
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+  }
+  const cudaMemcpyKind b2d = buf_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  b += sizeof(h);
+  CK(cudaMemcpyAsync(c->flags, b, 4, b2d, c->stream));
+  CK(cudaMemcpyAsync(c->counters, b + 4, 8 * NCOUNTERS, b2d, c->stream));
+  b += kCkptStatus;
+  if (c->kind == 1) {
+    const int rc = ch_ckpt_copy(c->ch, make_env(c), const_cast<unsigned char*>(b),
+                                buf_is_device, 0);
+    if (rc) return rc;
+    ch_sample(c->ch, h.sampling);
+  } else {
+    void* p[16];
+    size_t sz[16];
+    const int k = homog_segments(c, p, sz);
+    for (int i = 0; i < k; ++i) {
+      CK(cudaMemcpyAsync(p[i], b, sz[i], b2d, c->stream));
+      b += sz[i];
+    }
+  }
+  c->step = h.step;
+  CK(cudaStreamSynchronize(c->stream));
+  return USP_OK;
+}
+
 int usp_status(usp_ctx* c, uint32_t* flags, int64_t* counters, int reset) {
   if (!c) return USP_EINVAL;
   uint32_t f = 0;
@@ -2410,8 +2636,29 @@ int usp_status(usp_ctx* c, uint32_t* flags, int64_t* counters, int reset) {
     CK(cudaMemsetAsync(c->counters, 0, 256, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
-  const uint32_t err = F_A_NONPOS | F_SAMPLER_UNDERFLOW | F_BOUNDS | F_CAPACITY;
+  const uint32_t err = F_A_NONPOS | F_SAMPLER_UNDERFLOW | F_BOUNDS | F_CAPACITY | F_WAIT_TIMEOUT;
   return (f & err) ? USP_EDEVICE : USP_OK;
+}
+
+int usp_set_wait_limit(usp_ctx* c, int64_t cycles) {
+  if (!c || cycles < 0) return USP_EINVAL;
+  if (c->kind != 0) return USP_ENOTSUP;
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->graph_exec) {  // the captured launches carry the old limit
+    cudaGraphExecDestroy(c->graph_exec);
+    cudaGraphDestroy(c->graph);
+    c->graph_exec = nullptr;
+  }
+  c->wait_cycles = cycles == 0 ? kWaitCycles : (long long)cycles;
+  return USP_OK;
+}
+
+int usp_wait_check(usp_ctx* c, int64_t cycles) {
+  if (!c || cycles <= 0 || cycles > kWaitCycles) return USP_EINVAL;
+  wait_check_kernel<<<1, 32, 0, c->stream>>>((long long)cycles, c->flags);
+  CK(cudaGetLastError());
+  c->launches += 1;
+  return USP_OK;
 }
 
 int usp_sync(usp_ctx* c) {

@@ -8,9 +8,15 @@
 // or hosts running under a hard device-memory budget.  usp_moments_noalloc
 // serves them: it computes the same per-cell moments as usp_moments, but its
 // working space (the FP64 per-cell accumulators) lives in the file-scope
-// device array below, of fixed size, reserved when the library is loaded on a
-// device and kept until the process exits.  The caller passes the inputs and
-// the output buffer.
+// device array below, of fixed size, kept on each device until the process
+// exits.  With CUDA's lazy module loading (the default), the array is
+// reserved on a device when the library's module is first loaded there,
+// which is at the first call on that device at the latest (that call also
+// looks up the array's address): a caller that must not see any reservation
+// inside its time loop makes one warm-up call at start-up, or sets
+// CUDA_MODULE_LOADING=EAGER.  The address looked up at a device's first call
+// is kept, so a cudaDeviceReset between calls is not supported.  The caller
+// passes the inputs and the output buffer.
 //
 // Every call shares that one array and leaves its last contents there: each
 // call clears it first on the caller's stream.  Two calls whose work overlaps
@@ -164,6 +170,9 @@ extern "C" int usp_moments_noalloc(const usp_species* sp, int n_cells, const int
   gas.R = kNaKB / sp->m;
   gas.theta_v = sp->theta_v;
   cudaStream_t st = (cudaStream_t)stream;
+  // an error left by the caller's earlier work is not this call's: report it
+  // without launching (and without clearing it)
+  if (cudaPeekAtLastError() != cudaSuccess) return USP_ECUDA;
   const int nacc = kNaAcc * n_cells;
   na_clear<<<(nacc + 255) / 256, 256, 0, st>>>(acc, nacc);
   if (cudaGetLastError() != cudaSuccess) return USP_ECUDA;

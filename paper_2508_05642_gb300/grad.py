@@ -1,13 +1,15 @@
 """Pathwise gradients of the channel's time-averaged profiles with respect to
 (Z_rot, omega, T_wall), behind a torch.autograd.Function.
 
-The derivatives come from the library's USP_FP64_TANGENT form: every kernel of
-the channel step runs on FP64 numbers carrying their derivatives with respect
-to the three parameters, under the same random numbers and with the same
-discrete outcomes as the plain FP64 run (levels, cell membership, wall hits,
-branches are held fixed).  With three parameters this forward (tangent)
-propagation gives the full Jacobian in one run, so the autograd backward is a
-contraction of the stored Jacobian with the incoming gradient.
+The library's USP_FP64_TANGENT form runs every kernel of the channel step on
+FP64 numbers carrying their derivatives with respect to the three parameters,
+under the same random numbers as the plain FP64 run; discrete outcomes and
+particle positions are held (usp.h, usp_backward).  The profiles, their
+derivatives and the contraction of those with an objective's gradient are
+formed on the device (usp_profiles, usp_backward); this module only marshals
+tensors and runs the steps, checkpointing the context (usp_save) every
+``checkpoint_every`` steps so that a long run can be resumed (usp_load) from
+its last checkpoint instead of from the start.
 """
 from __future__ import annotations
 
@@ -15,63 +17,117 @@ import numpy as np
 
 from . import usp
 
-KB = 1.380649e-23
-NACC = 12
+# fields of usp_profiles
+PROF_N, PROF_UX, PROF_UY, PROF_UZ, PROF_TTR, PROF_TROT, PROF_TVIB = range(usp.USP_NPROF)
 
 
-def profiles_from_sums(acc: np.ndarray, ny: int, m: float, blocks: int = 1):
-    """Time-averaged T_tr, T_rot and u_x per cell (3 x ny) from the pooled
-    sums of usp_channel_read, and, for the gradient form, their derivatives
-    (3 x ny x 3) with respect to (Z_rot, omega, T_wall)."""
-    R = KB / m
-    blk = ny * NACC + 2
-    A = acc[:blk][: ny * NACC].reshape(ny, NACC)
-    N = A[:, 0]
-    S1 = A[:, 1:4]
-    S2 = A[:, 4:7].sum(axis=1)
-    Se = A[:, 10]
-    U = S1 / N[:, None]
-    T_tr = (S2 / N - (U ** 2).sum(axis=1)) / (3 * R)
-    T_rot = Se / (N * R)
-    prof = np.stack([T_tr, T_rot, U[:, 0]])
-    if blocks == 1:
-        return prof, None
-    J = np.zeros((3, ny, 3))
-    for k in range(3):
-        D = acc[(k + 1) * blk:(k + 2) * blk][: ny * NACC].reshape(ny, NACC)
-        dS1 = D[:, 1:4]
-        dS2 = D[:, 4:7].sum(axis=1)
-        dSe = D[:, 10]
-        dU = dS1 / N[:, None]
-        J[0, :, k] = (dS2 / N - 2 * (U * dU).sum(axis=1)) / (3 * R)
-        J[1, :, k] = dSe / (N * R)
-        J[2, :, k] = dU[:, 0]
-    return prof, J
+class ChannelGradient:
+    """A gradient-form run of the channel: ``warmup`` steps, then ``sample``
+    steps whose post-step states are pooled into the time averages.
+    theta = (Z_rot, omega, T_wall)."""
 
+    def __init__(self, workload, dt: float, warmup: int, sample: int, seed: int = 1,
+                 checkpoint_every: int = 100, keep_checkpoints: bool = False,
+                 batches: int = 1):
+        self.w = workload
+        self.dt = float(dt)
+        self.warmup, self.sample = int(warmup), int(sample)
+        self.seed = seed
+        self.every = max(1, int(checkpoint_every))
+        self.keep = keep_checkpoints
+        self.batches = max(1, int(batches))
+        if self.sample % self.batches:
+            raise ValueError("sample must be a multiple of batches")
+        self.checkpoints = {}     # step -> host buffer (all of them when keep_checkpoints)
+        self.batch_blocks = {}    # end step of a batch -> usp_profiles blocks of that batch
+        self.ctx = None
+        self.theta = None
 
-def channel_profiles_and_jacobian(theta, workload, dt: float, warmup: int, sample: int,
-                                  seed: int = 1):
-    """Run the gradient form of the channel: `warmup` steps, then `sample`
-    steps averaged.  theta = (Z_rot, omega, T_wall)."""
-    sp = dict(workload.species)
-    sp["Z_rot"], sp["omega"] = float(theta[0]), float(theta[1])
-    ch = dict(workload.channel)
-    ch["T_wall"] = float(theta[2])
-    p = workload.particles
-    ctx = usp.usp_init_channel(sp, ch, dt, workload.y, p.cx, p.cy, p.cz, p.erot, p.lev,
-                               precision=usp.USP_FP64_TANGENT, seed=seed)
-    try:
-        if warmup:
-            usp.usp_step(ctx, warmup)
-        usp.usp_channel_sample(ctx, True)
-        usp.usp_step(ctx, sample)
-        acc = usp.usp_channel_read(ctx, blocks=4)
+    def _create(self, theta):
+        sp = dict(self.w.species)
+        sp["Z_rot"], sp["omega"] = float(theta[0]), float(theta[1])
+        ch = dict(self.w.channel)
+        ch["T_wall"] = float(theta[2])
+        p = self.w.particles
+        return usp.usp_init_channel(sp, ch, self.dt, self.w.y, p.cx, p.cy, p.cz, p.erot, p.lev,
+                                    precision=usp.USP_FP64_TANGENT, seed=self.seed)
+
+    def _advance(self, ctx, start: int):
+        """Steps start .. warmup + sample, sampling on from step warmup, a
+        checkpoint at every multiple of the checkpoint interval.  With
+        batches > 1 the sampling window is cut into equal batches: at the end
+        of each, its profiles (and derivatives) are kept and the sums restart
+        (batch means give the statistical error of a time average)."""
+        total = self.warmup + self.sample
+        blen = self.sample // self.batches
+        s = start
+        while s < total:
+            if s == self.warmup:
+                usp.usp_channel_sample(ctx, True)
+            nxt = min(total, (s // self.every + 1) * self.every)
+            if s < self.warmup:
+                nxt = min(nxt, self.warmup)
+            elif self.batches > 1:
+                nxt = min(nxt, self.warmup + ((s - self.warmup) // blen + 1) * blen)
+            usp.usp_step(ctx, nxt - s)
+            s = nxt
+            if self.batches > 1 and s > self.warmup and (s - self.warmup) % blen == 0:
+                self.batch_blocks[s] = usp.usp_profiles(ctx)
+                usp.usp_sample_read(ctx, reset=True)
+            if s % self.every == 0 and s < total:
+                buf = usp.usp_save(ctx)
+                if not self.keep:
+                    self.checkpoints.clear()
+                self.checkpoints[s] = buf
         flags, _ = usp.usp_status(ctx)
-    finally:
-        ctx.destroy()
-    if flags & usp.ERROR_FLAGS:
-        raise RuntimeError(f"channel run reported errors: flags {flags:#x}")
-    return profiles_from_sums(acc, ch["ny"], sp["m"], blocks=4)
+        if flags & usp.ERROR_FLAGS:
+            raise RuntimeError(f"channel run reported errors: flags {flags:#x}")
+
+    def run(self, theta):
+        """Run from the initial state; returns the profiles (USP_NPROF x ny)."""
+        self.release()
+        self.theta = np.asarray(theta, dtype=np.float64).reshape(3)
+        self.checkpoints = {}
+        self.batch_blocks = {}
+        self.ctx = self._create(self.theta)
+        self._advance(self.ctx, 0)
+        return self.profiles()
+
+    def resume(self, theta, step: int, checkpoint=None):
+        """Continue from the checkpoint taken after ``step`` steps (a fresh
+        context loads it) to the end of the run; returns the profiles."""
+        self.release()
+        self.theta = np.asarray(theta, dtype=np.float64).reshape(3)
+        buf = self.checkpoints[step] if checkpoint is None else checkpoint
+        self.batch_blocks = {k: v for k, v in self.batch_blocks.items() if k <= step}
+        self.ctx = self._create(self.theta)
+        usp.usp_load(self.ctx, buf)
+        self._advance(self.ctx, step)
+        return self.profiles()
+
+    def profiles(self):
+        return usp.usp_profiles(self.ctx)[0]
+
+    def jacobian(self):
+        """d profiles / d theta: (USP_NPROF, ny, 3)."""
+        blocks = usp.usp_profiles(self.ctx)
+        return np.moveaxis(blocks[1:], 0, -1)
+
+    def batch_results(self):
+        """Per batch (ascending end step): profiles (USP_NPROF, ny) and their
+        Jacobian (USP_NPROF, ny, 3)."""
+        return [(self.batch_blocks[k][0], np.moveaxis(self.batch_blocks[k][1:], 0, -1))
+                for k in sorted(self.batch_blocks)]
+
+    def backward(self, d_dL: int) -> np.ndarray:
+        """Gradient (3,) of an objective whose dL/dprofiles sits in device
+        memory at d_dL (USP_NPROF x ny doubles)."""
+        return usp.usp_backward(self.ctx, d_dL)
+
+    def release(self):
+        if self.ctx is not None:
+            self.ctx.destroy()
+            self.ctx = None
 
 
 def channel_profiles_fn():
@@ -79,21 +135,23 @@ def channel_profiles_fn():
     import torch
 
     class ChannelProfiles(torch.autograd.Function):
-        """profiles(theta) -> (3, ny): time-averaged T_tr, T_rot, u_x per cell
-        of the force-driven channel, differentiable in theta = (Z_rot, omega,
-        T_wall) (0-dim or 1-dim FP64 tensor of 3)."""
+        """profiles(theta) -> (USP_NPROF, ny) time-averaged profiles of the
+        force-driven channel (usp_profiles field order), differentiable in
+        theta = (Z_rot, omega, T_wall) (FP64 tensor of 3).  ``runner`` is a
+        ChannelGradient; its context stays alive for the backward pass."""
 
         @staticmethod
-        def forward(ctx, theta, workload, dt, warmup, sample, seed):
-            th = theta.detach().cpu().double().numpy().reshape(3)
-            prof, J = channel_profiles_and_jacobian(th, workload, dt, warmup, sample, seed)
-            ctx.save_for_backward(torch.from_numpy(J))
+        def forward(ctx, theta, runner):
+            prof = runner.run(theta.detach().cpu().double().numpy())
+            ctx.runner = runner
             return torch.from_numpy(prof).to(theta.device)
 
         @staticmethod
         def backward(ctx, grad_out):
-            (J,) = ctx.saved_tensors
-            g = torch.einsum("fc,fck->k", grad_out.detach().cpu().double(), J)
-            return g.to(grad_out.device), None, None, None, None, None
+            dev = torch.device("cuda", torch.cuda.current_device())
+            dL = grad_out.detach().to(device=dev, dtype=torch.float64).contiguous()
+            torch.cuda.synchronize(dev)
+            g = ctx.runner.backward(dL.data_ptr())
+            return torch.from_numpy(g).to(grad_out.device), None
 
     return ChannelProfiles

@@ -184,33 +184,52 @@ def homogeneous_single(seed: int = 1, N: int = 20000, n: float = 1e23,
                     np.array([[T_tr, T_rot, T_vib]]), dt_over_tau_c, p, seed, steps)
 
 
-def batched_instances(seed: int = 1, n_inst: int = 4096, nmin: float = 1e3, nmax: float = 2e5,
-                      n: float = 1e23, Ttr_range=(2000.0, 20000.0), Tint_range=(300.0, 3000.0),
-                      Z_rot: float = 5.0, Z_vib: float = 50.0, dt_over_tau_c: float = 0.5,
-                      steps: int = 500, scale: float = 1.0) -> Workload:
-    """``n_inst`` independent single-cell instances.  ``scale`` < 1 shrinks
-    every particle count (for quick tests) while keeping the log-uniform mix."""
-    sp = n2_vhs_relaxation_species(Z_rot, Z_vib)
+def batched_parameters(seed: int = 1, n_inst: int = 4096, nmin: float = 1e3, nmax: float = 2e5,
+                       Ttr_range=(2000.0, 20000.0), Tint_range=(300.0, 3000.0),
+                       scale: float = 1.0):
+    """Per-instance particle counts (log-uniform in [nmin, nmax], times
+    ``scale``, at least 2) and initial temperatures (n_inst, 3) of the batched
+    workload, drawn before any particle."""
     rng = np.random.default_rng([seed, 0xBA7C])
     counts = np.floor(np.exp(rng.uniform(np.log(nmin), np.log(nmax), n_inst)) * scale).astype(np.int64)
     counts = np.maximum(counts, 2)
     Ttr = rng.uniform(*Ttr_range, n_inst)
     Trot = rng.uniform(*Tint_range, n_inst)
     Tvib = rng.uniform(*Tint_range, n_inst)
-    off = np.zeros(n_inst + 1, dtype=np.int64)
+    return counts, np.stack([Ttr, Trot, Tvib], axis=1)
+
+
+def batched_instances(seed: int = 1, n_inst: int = 4096, nmin: float = 1e3, nmax: float = 2e5,
+                      n: float = 1e23, Ttr_range=(2000.0, 20000.0), Tint_range=(300.0, 3000.0),
+                      Z_rot: float = 5.0, Z_vib: float = 50.0, dt_over_tau_c: float = 0.5,
+                      steps: int = 500, scale: float = 1.0, select=None) -> Workload:
+    """``n_inst`` independent single-cell instances.  ``scale`` < 1 shrinks
+    every particle count (for quick tests) while keeping the log-uniform mix.
+    ``select`` (instance indices, ascending) builds only those instances of
+    the same population: each instance's particles come from a stream of its
+    own, so a subset equals the corresponding part of the whole."""
+    sp = n2_vhs_relaxation_species(Z_rot, Z_vib)
+    all_counts, all_T = batched_parameters(seed, n_inst, nmin, nmax, Ttr_range, Tint_range, scale)
+    idx = np.arange(n_inst) if select is None else np.asarray(select, dtype=np.int64)
+    counts, T = all_counts[idx], all_T[idx]
+    k = len(idx)
+    off = np.zeros(k + 1, dtype=np.int64)
     off[1:] = np.cumsum(counts)
     Ntot = int(off[-1])
     cx = np.empty(Ntot); cy = np.empty(Ntot); cz = np.empty(Ntot)
     er = np.empty(Ntot); lev = np.empty(Ntot, dtype=np.int32)
-    for i in range(n_inst):
-        b, e = off[i], off[i + 1]
+    for j, i in enumerate(idx):
+        b, e = off[j], off[j + 1]
+        rng = np.random.default_rng([seed, 0xBA7C, int(i)])
         p = equilibrium_particles(rng, int(e - b), sp["m"], sp["theta_v"],
-                                  T_tr=Ttr[i], T_rot=Trot[i], T_vib=Tvib[i])
+                                  T_tr=T[j, 0], T_rot=T[j, 1], T_vib=T[j, 2])
         cx[b:e] = p.cx; cy[b:e] = p.cy; cz[b:e] = p.cz; er[b:e] = p.erot; lev[b:e] = p.lev
-    return Workload("batched homogeneous N2 relaxation, %d instances, N log-uniform [%d, %d]"
-                    % (n_inst, int(nmin * scale), int(nmax * scale)), sp, off,
-                    np.full(n_inst, n), np.stack([Ttr, Trot, Tvib], axis=1), dt_over_tau_c,
-                    Particles(cx, cy, cz, er, lev), seed, steps)
+    name = "batched homogeneous N2 relaxation, %d instances, N log-uniform [%d, %d]" % (
+        n_inst, int(nmin * scale), int(nmax * scale))
+    if select is not None:
+        name += " (%d of them)" % k
+    return Workload(name, sp, off, np.full(k, n), T, dt_over_tau_c,
+                    Particles(cx, cy, cz, er, lev), seed, steps, {"instances": idx})
 
 
 @dataclass

@@ -42,10 +42,13 @@ EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogene
             "usp_info", "usp_tuning", "usp_set_variant", "usp_launch_count", "usp_profile_enable", "usp_profile_read",
             "usp_moments_noalloc", "usp_init_channel", "usp_channel_sample",
             "usp_channel_read", "usp_channel_get_particles", "usp_init_plane", "usp_plane_leaves", "usp_plane_count",
-            "usp_plane_get_particles", "usp_sample", "usp_sample_read", "usp_destroy"]
+            "usp_plane_get_particles", "usp_sample", "usp_sample_read", "usp_profiles",
+            "usp_backward", "usp_checkpoint_bytes", "usp_save", "usp_load", "usp_set_wait_limit",
+            "usp_wait_check", "usp_destroy"]
 USP_METHOD_USP_FPM, USP_METHOD_FPM = 0, 1
 USP_NSURF = 180
 USP_NOALLOC_MAX_CELLS = 8192
+USP_NPROF = 7
 
 
 class usp_species(C.Structure):
@@ -150,6 +153,13 @@ def lib():
                                                   _I32, _U32]
             L.usp_sample.argtypes = [_CTX, C.c_int]
             L.usp_sample_read.argtypes = [_CTX, _D, C.c_int]
+            L.usp_profiles.argtypes = [_CTX, C.c_void_p, C.c_int]
+            L.usp_backward.argtypes = [_CTX, C.c_void_p, C.c_void_p, C.c_int]
+            L.usp_checkpoint_bytes.argtypes = [_CTX, C.POINTER(C.c_size_t)]
+            L.usp_save.argtypes = [_CTX, C.c_void_p, C.c_int]
+            L.usp_load.argtypes = [_CTX, C.c_void_p, C.c_int]
+            L.usp_set_wait_limit.argtypes = [_CTX, C.c_int64]
+            L.usp_wait_check.argtypes = [_CTX, C.c_int64]
             L.usp_destroy.argtypes = [_CTX]
             L.usp_destroy.restype = None
             _lib = L
@@ -412,6 +422,59 @@ def usp_sample_read(ctx: Context, reset: bool = False) -> np.ndarray:
     return out
 
 
+def usp_profiles(ctx: Context, out=None, out_is_device=False):
+    """Time-averaged channel profiles (USP_NPROF x ny; in the USP_FP64_TANGENT
+    form 4 x USP_NPROF x ny: values, then derivatives w.r.t. Z_rot, omega,
+    T_wall).  Host numpy unless a device pointer (int) is given."""
+    blocks = 4 if ctx.precision == USP_FP64_TANGENT else 1
+    if out_is_device:
+        _check(lib().usp_profiles(ctx.h, C.c_void_p(out), 1), "usp_profiles")
+        return None
+    o = np.zeros((blocks, USP_NPROF, ctx.n_cells), dtype=np.float64)
+    _check(lib().usp_profiles(ctx.h, o.ctypes.data_as(C.c_void_p), 0), "usp_profiles")
+    return o if blocks > 1 else o[0]
+
+
+def usp_backward(ctx: Context, d_dL: int, grad3=None, grad_is_device=False):
+    """Gradient (3,) of an objective w.r.t. (Z_rot, omega, T_wall) from
+    dL/dprofiles held in device memory at ``d_dL`` (USP_NPROF x ny doubles).
+    With grad_is_device, ``grad3`` is a device pointer written asynchronously."""
+    if grad_is_device:
+        _check(lib().usp_backward(ctx.h, C.c_void_p(d_dL), C.c_void_p(grad3), 1), "usp_backward")
+        return None
+    g = np.zeros(3)
+    _check(lib().usp_backward(ctx.h, C.c_void_p(d_dL), g.ctypes.data_as(C.c_void_p), 0),
+           "usp_backward")
+    return g
+
+
+def usp_checkpoint_bytes(ctx: Context) -> int:
+    n = C.c_size_t(0)
+    _check(lib().usp_checkpoint_bytes(ctx.h, C.byref(n)), "usp_checkpoint_bytes")
+    return int(n.value)
+
+
+def usp_save(ctx: Context, buf=None, buf_is_device=False):
+    """Checkpoint into ``buf`` (a host numpy uint8 array of
+    usp_checkpoint_bytes, allocated when None; or a device pointer with
+    buf_is_device).  Returns the host array (or None)."""
+    if buf_is_device:
+        _check(lib().usp_save(ctx.h, C.c_void_p(buf), 1), "usp_save")
+        return None
+    if buf is None:
+        buf = np.zeros(usp_checkpoint_bytes(ctx), dtype=np.uint8)
+    _check(lib().usp_save(ctx.h, buf.ctypes.data_as(C.c_void_p), 0), "usp_save")
+    return buf
+
+
+def usp_load(ctx: Context, buf, buf_is_device=False):
+    if buf_is_device:
+        _check(lib().usp_load(ctx.h, C.c_void_p(buf), 1), "usp_load")
+        return
+    b = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().usp_load(ctx.h, b.ctypes.data_as(C.c_void_p), 0), "usp_load")
+
+
 def usp_step(ctx: Context, nsteps: int):
     _check(lib().usp_step(ctx.h, nsteps), "usp_step")
 
@@ -465,6 +528,16 @@ def usp_status(ctx: Context, reset=False):
     if rc not in (USP_OK, USP_EDEVICE):
         _check(rc, "usp_status")
     return f.value, cnt
+
+
+def usp_set_wait_limit(ctx: Context, cycles: int):
+    """Wait limit (SM cycles) of the homogeneous particle pass; 0 = default."""
+    _check(lib().usp_set_wait_limit(ctx.h, int(cycles)), "usp_set_wait_limit")
+
+
+def usp_wait_check(ctx: Context, cycles: int):
+    """Enqueue a bounded wait on a barrier nothing completes (timeout check)."""
+    _check(lib().usp_wait_check(ctx.h, int(cycles)), "usp_wait_check")
 
 
 def usp_sync(ctx: Context):

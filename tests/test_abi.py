@@ -88,3 +88,77 @@ def test_plane_leaves_on_the_host_match_the_oracle(levels, r2, r3, r):
         usp.usp_plane_leaves(dict(bad, T_wall=500.0, n_inf=1e21, T_inf=200.0, U_inf=0.0,
                                   bc=(0, 0, 1, 0), inflow=(1, 0, 0, 1), F_num=1.0, depth=1.0,
                                   reconstruct=1))
+
+
+class _CountingAllocator:
+    """Allocator callbacks that hand out distinct fake addresses (never
+    dereferenced: the library fails before any device work) and return NULL
+    at the ``fail_at``-th request; they count what is outstanding."""
+
+    def __init__(self, fail_at):
+        self.fail_at = fail_at
+        self.calls = 0
+        self.live = set()
+
+        @usp.ALLOC_FN
+        def _alloc(nbytes, user):
+            self.calls += 1
+            if self.calls == self.fail_at:
+                return None
+            p = 0x7f0000000000 + 0x100000 * self.calls
+            self.live.add(p)
+            return p
+
+        @usp.FREE_FN
+        def _free(ptr, user):
+            self.live.discard(ptr)
+
+        self.fns = (_alloc, _free, None)
+
+
+@pytest.mark.parametrize("precision", [usp.USP_FP32, usp.USP_FP64])
+def test_failing_allocator_returns_enomem_and_frees_everything(precision):
+    """A caller allocator that fails at any one request: context creation
+    returns USP_ENOMEM before any CUDA call, having released through the free
+    callback everything it had taken."""
+    w = I.batched_instances(seed=2, n_inst=3, nmin=20, nmax=50, steps=1)
+    dt = np.full(w.n_cells, 1e-9)
+    p = w.particles
+    probe = _CountingAllocator(fail_at=1)
+    with pytest.raises(usp.USPError) as e:
+        usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, dt, p.cx, p.cy, p.cz, p.erot,
+                                 p.lev, precision=precision, allocator=probe.fns)
+    assert e.value.code == usp.USP_ENOMEM and not probe.live
+    n_alloc = 0
+    k = 1
+    while True:
+        a = _CountingAllocator(fail_at=k)
+        try:
+            usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, dt, p.cx, p.cy, p.cz,
+                                     p.erot, p.lev, precision=precision, allocator=a.fns)
+        except usp.USPError as err:
+            if err.code != usp.USP_ENOMEM:
+                raise
+            assert not a.live, (k, len(a.live))
+            n_alloc = max(n_alloc, a.calls)
+            k += 1
+            if k > n_alloc:
+                break
+            continue
+        raise AssertionError("context created on fake device memory")
+    assert n_alloc >= 10
+
+
+@pytest.mark.skipif(usp.lib().usp_select_device(0) == 0, reason="a GPU is present")
+def test_allocator_memory_released_when_the_device_is_missing():
+    """Every allocation succeeds, the first CUDA call fails (no device): the
+    context is not created (USP_ECUDA) and nothing is left allocated."""
+    w = I.batched_instances(seed=2, n_inst=3, nmin=20, nmax=50, steps=1)
+    dt = np.full(w.n_cells, 1e-9)
+    p = w.particles
+    a = _CountingAllocator(fail_at=-1)
+    with pytest.raises(usp.USPError) as e:
+        usp.usp_init_homogeneous(w.species, w.offsets, w.ndens, dt, p.cx, p.cy, p.cz, p.erot,
+                                 p.lev, precision=usp.USP_FP32, allocator=a.fns)
+    assert e.value.code in (usp.USP_ECUDA, usp.USP_EINVAL)
+    assert a.calls >= 10 and not a.live

@@ -93,40 +93,51 @@ def test_channel_graph_and_eager_agree():
 
 
 def test_fp32_poiseuille_matches_oracle_profile():
-    """Developed force-driven Poiseuille flow: the FP32 GPU run's time-averaged
+    """Developed force-driven Poiseuille flow: the FP32 GPU runs' time-averaged
     velocity profile agrees with the FP64 oracle's within the statistical
-    scatter, and both balance the body force with wall friction."""
+    scatter, and both balance the body force with wall friction.  Different
+    seeds are different realizations: the centreline velocity of one
+    5,000-step average scatters by about 3.5 % between seeds, so the test
+    compares means over six library seeds and three oracle seeds (standard
+    error of the difference about 2.3 %) at 8 %."""
     w = I.channel_poiseuille(ny=32, ppc=100, steps=0)
     sp = O.species(**w.species)
     ch = O.channel(**w.channel)
     dto = w.dt_over_tau_c * O.tau_c(sp, w.n, 300.0)
+    dtg = w.dt_over_tau_c * usp.usp_tau_c(w.species, w.n, 300.0)
     p = w.particles
-    st = O.ChannelState.from_arrays(w.y, p.cx, p.cy, p.cz, p.erot, p.lev)
-    O.channel_step(sp, 0, 11, 0, 2000, ch, dto, st)
-    acc = np.zeros(ch.ny * O.NACC + 2)
-    O.channel_step(sp, 0, 11, 2000, 5000, ch, dto, st, acc)
-    ctx = usp.usp_init_channel(w.species, w.channel,
-                               w.dt_over_tau_c * usp.usp_tau_c(w.species, w.n, 300.0), w.y, p.cx,
-                               p.cy, p.cz, p.erot, p.lev, precision=usp.USP_FP32, seed=12)
-    usp.usp_step(ctx, 2000)
-    usp.usp_channel_sample(ctx, True)
-    usp.usp_step(ctx, 5000)
-    gacc = usp.usp_channel_read(ctx)
-    flags, cnt = usp.usp_status(ctx)
-    # clamps of relaxation temperatures occur where the sparse vibrational
-    # excitation (mean level ~1e-5 at 300 K) makes the cell T_vib jump; only
-    # error bits fail the run
-    assert flags & usp.ERROR_FLAGS == 0
+    n = len(w.y)
+    force = n * ch.g * dto
 
     def profile(a):
         A = a[: ch.ny * O.NACC].reshape(ch.ny, O.NACC)
         return A[:, 1] / A[:, 0]
 
-    uo, ug = profile(acc), profile(gacc)
+    uo = []
+    for seed in (11, 21, 31):
+        st = O.ChannelState.from_arrays(w.y, p.cx, p.cy, p.cz, p.erot, p.lev)
+        O.channel_step(sp, 0, seed, 0, 2000, ch, dto, st)
+        acc = np.zeros(ch.ny * O.NACC + 2)
+        O.channel_step(sp, 0, seed, 2000, 5000, ch, dto, st, acc)
+        assert acc[-1] / 5000 == pytest.approx(force, rel=0.03)
+        uo.append(profile(acc))
+    ug = []
+    for seed in (12, 13, 14, 15, 16, 17):
+        ctx = usp.usp_init_channel(w.species, w.channel, dtg, w.y, p.cx, p.cy, p.cz, p.erot,
+                                   p.lev, precision=usp.USP_FP32, seed=seed)
+        usp.usp_step(ctx, 2000)
+        usp.usp_channel_sample(ctx, True)
+        usp.usp_step(ctx, 5000)
+        gacc = usp.usp_channel_read(ctx)
+        flags, cnt = usp.usp_status(ctx)
+        ctx.destroy()
+        # clamps of relaxation temperatures occur where the sparse vibrational
+        # excitation (mean level ~1e-5 at 300 K) makes the cell T_vib jump;
+        # only error bits fail the run
+        assert flags & usp.ERROR_FLAGS == 0
+        assert gacc[-1] / 5000 == pytest.approx(force, rel=0.03)
+        ug.append(profile(gacc))
+    uo, ug = np.mean(uo, axis=0), np.mean(ug, axis=0)
     mid = slice(ch.ny // 2 - 4, ch.ny // 2 + 4)
-    assert ug[mid].mean() == pytest.approx(uo[mid].mean(), rel=0.06)
+    assert ug[mid].mean() == pytest.approx(uo[mid].mean(), rel=0.08)
     assert np.abs(ug - uo).max() < 0.15 * uo.max()
-    n = len(w.y)
-    force = n * ch.g * dto
-    assert gacc[-1] / 5000 == pytest.approx(force, rel=0.03)
-    assert acc[-1] / 5000 == pytest.approx(force, rel=0.03)

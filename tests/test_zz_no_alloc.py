@@ -13,6 +13,7 @@ process.
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2508_05642_gb300 import inputs as I
 from paper_2508_05642_gb300 import usp
 
@@ -46,13 +47,29 @@ def test_noalloc_moments_match_context_moments_twice():
     doff = d(w.offsets.astype(np.int64))
     out = torch.empty((usp.USP_NMOM, w.n_cells), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream().cuda_stream
-    for _ in range(2):
+    # the oracle's moments of the same particles, cell by cell
+    orc = O.moments(O.species(**w.species), w.offsets, O.State.from_arrays(cx, cy, cz, er, lv))
+    for k in range(2):
         out.fill_(np.nan)
+        torch.cuda.synchronize()
+        if k == 1:
+            free0 = torch.cuda.mem_get_info()[0]
+            alloc0 = torch.cuda.memory_allocated()
         usp.usp_moments_noalloc(w.species, w.n_cells, doff.data_ptr(), dcx.data_ptr(),
                                 dcy.data_ptr(), dcz.data_ptr(), der.data_ptr(), dlv.data_ptr(),
                                 out.data_ptr(), stream)
         torch.cuda.synchronize()
-        _close(out.cpu().numpy(), ref)
+        if k == 1:
+            # the second call took no device memory from the driver or torch
+            assert torch.cuda.mem_get_info()[0] == free0
+            assert torch.cuda.memory_allocated() == alloc0
+        got = out.cpu().numpy()
+        _close(got, ref)
+        # per cell, against the oracle (1e-5 relative to each cell's value,
+        # with a floor of 1e-9 of the field's scale for values near zero)
+        for f in range(orc.shape[0]):
+            scale = max(np.abs(orc[f]).max(), 1e-300)
+            assert np.all(np.abs(got[f] - orc[f]) <= 1e-5 * np.abs(orc[f]) + 1e-9 * scale), f
 
 
 def test_noalloc_rejects_more_cells_than_its_scratch_holds():
