@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink particle counts (debug only; the default is the full workload)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--late-steps", type=int, default=20,
+                    help="steps timed from step 250 on (0: skip)")
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--fpm-steps", type=int, default=100,
                     help="steps of the plain FPM method (Sec. 2.C) on the same workload, FP32")
@@ -360,6 +362,23 @@ def run_ours(args, rank, world, local):
     achieved = alg_bytes / (collide_ms / 1e3) / 1e9
     flags, counters = usp.usp_status(ctx)
 
+    # ---- a late window of the 500-step run: the cost grows as the levels
+    # heat up, so the rate of steps 250-270 is reported beside the early one
+    late = None
+    if args.late_steps > 0:
+        done = args.warmup + 2 * args.steps
+        start = max(done, 250)
+        usp.usp_step(ctx, start - done)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        usp.usp_step(ctx, args.late_steps)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        lms = max_over_ranks(g0.elapsed_time(g1))
+        late = {"steps": f"{start}-{start + args.late_steps}",
+                "value": total_particles * args.late_steps / (lms / 1e3), "unit": UNIT,
+                "ms_per_step": lms / args.late_steps}
+
     # ---- end to end through the C ABI on pinned host buffers ---------------
     e2e = None
     if args.e2e_steps > 0:
@@ -513,6 +532,7 @@ def run_ours(args, rank, world, local):
                              "autotune": {"warp_tiles": warp_tiles, "blocks_per_sm": minb,
                                           "ms_block_tiled_2_3_4": [float(x) for x in tune_ms[:3]],
                                           "ms_warp_tiled_2_3_4": [float(x) for x in tune_ms[3:]]}},
+                "late_window": late,
                 "e2e": e2e, "cpu_baseline": cpu, "fp64_plain": fp64, "fpm_method": fpm,
                 "poiseuille_channel": chan,
                 "cylinder_plane": cyl, "cylinder_plane_refined": cyl_ref,

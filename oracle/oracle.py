@@ -214,6 +214,7 @@ def _bind(L):
                                    C.POINTER(Channel), C.c_double, C.c_int64, _D, _D, _D, _D, _D,
                                    _I32, _U32, _I64, _D, _U32, _I64]
     L.orc_channel_step.restype = C.c_int
+    L.orc_particle_draws.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, _D, _D, _D]
     L.orc_channel_step_frozen.argtypes = L.orc_channel_step.argtypes + [C.c_void_p]
     L.orc_channel_step_frozen.restype = C.c_int
     L.orc_declog_new.restype = C.c_void_p
@@ -265,6 +266,15 @@ def philox(ctr, key) -> tuple:
     out = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_p(c, C.c_uint32), _p(k, C.c_uint32), _p(out, C.c_uint32))
     return tuple(int(x) for x in out)
+
+
+def particle_draws(seed, pid, step, form):
+    """(G[4], u5, u6): one particle's collision draws."""
+    G = np.zeros(4)
+    u5, u6 = C.c_double(), C.c_double()
+    lib().orc_particle_draws(C.c_uint64(seed), pid, step, form, _p(G, C.c_double),
+                             C.byref(u5), C.byref(u6))
+    return G, u5.value, u6.value
 
 
 def uniform(x: int, form: int) -> float:

@@ -841,21 +841,38 @@ static void conserve_cell(const orc_species* sp, uint64_t seed, uint32_t cell, u
     }
 }
 
-/* Collision-stream draws of one particle: counter (pid, step, tag, 0).
- * Tag 0 -> four normals (two Box-Muller pairs), tag 1 -> the two uniforms of
- * the jump samplers. */
+/* Collision-stream draws of one particle: four normals (two Box-Muller
+ * pairs of a radius and an angle uniform) and the two uniforms of the jump
+ * samplers, from the one Philox block with counter (pid, step, 0, 0), in
+ * both forms.  A uniform takes 23 bits of a word, (2 (x >> 9) + 1) 2^-24
+ * (orc_uniform form 1, exact in float), so the block carries all six: the
+ * radius uniforms from words 0 and 1, the jump uniforms from words 2 and 3,
+ * and the two angle uniforms (2a + 1) 2^-19 from the 18-bit
+ * a = (low 9 bits of word 0) << 9 | (low 9 bits of word 1), then of words 2
+ * and 3.  The reading is the project's (the paper names no generator). */
 #define PTAG_NORMALS 0u
-#define PTAG_JUMPS 1u
+static double angle_uniform18(uint32_t wa, uint32_t wb)
+{
+    uint32_t a = ((wa & 0x1FFu) << 9) | (wb & 0x1FFu);
+    return (2.0 * (double)a + 1.0) * 0x1p-19;
+}
+
 static void particle_draws(uint64_t seed, uint32_t pid, uint32_t step, int form,
                            double G[4], double* u5, double* u6)
 {
     uint32_t w[4];
+    (void)form;
     philox_words(pid, step, PTAG_NORMALS, 0u, seed, w);
-    box_muller(orc_uniform(w[0], form), orc_uniform(w[1], form), &G[0], &G[1]);
-    box_muller(orc_uniform(w[2], form), orc_uniform(w[3], form), &G[2], &G[3]);
-    philox_words(pid, step, PTAG_JUMPS, 0u, seed, w);
-    *u5 = orc_uniform(w[0], form);
-    *u6 = orc_uniform(w[1], form);
+    box_muller(orc_uniform(w[0], 1), angle_uniform18(w[0], w[1]), &G[0], &G[1]);
+    box_muller(orc_uniform(w[1], 1), angle_uniform18(w[2], w[3]), &G[2], &G[3]);
+    *u5 = orc_uniform(w[2], 1);
+    *u6 = orc_uniform(w[3], 1);
+}
+
+void orc_particle_draws(uint64_t seed, uint32_t pid, uint32_t step, int form,
+                        double G[4], double* u5, double* u6)
+{
+    particle_draws(seed, pid, step, form, G, u5, u6);
 }
 
 /* ======================================================================== */

@@ -193,6 +193,12 @@ int    orc_channel_step(const orc_species* sp, int form, uint64_t seed, int64_t 
                         uint32_t* flags, int64_t* counters);
 void   orc_channel_reconstruct(const orc_channel* ch, const int64_t* counts, const double* F,
                                int cell, double y, double* out);
+/* The collision draws of one particle and step (four standard normals and
+ * the two jump-sampler uniforms), as every step uses them (the same in both
+ * forms). */
+void   orc_particle_draws(uint64_t seed, uint32_t pid, uint32_t step, int form,
+                          double G[4], double* u5, double* u6);
+
 /* Frozen-discrete runs (gradient checks by finite differences): a decision
  * log records every discrete decision of a channel run in the order it is
  * taken (mode 1: record, clearing the log) and replays it in a later run

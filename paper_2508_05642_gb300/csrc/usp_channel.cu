@@ -48,6 +48,13 @@ __device__ __forceinline__ void box_muller(D3 ua, D3 ub, D3& ga, D3& gb) {
   ga = D3(a);
   gb = D3(b);
 }
+__device__ __forceinline__ void particle_draws(uint32_t pid, uint32_t step,
+                                               const PhiloxRoundKeys& rk, D3& g0, D3& g1, D3& g2,
+                                               D3& g3, uint32_t& j5, uint32_t& j6) {
+  double a0, a1, a2, a3;
+  particle_draws(pid, step, rk, a0, a1, a2, a3, j5, j6);
+  g0 = D3(a0); g1 = D3(a1); g2 = D3(a2); g3 = D3(a3);
+}
 template <>
 __device__ __forceinline__ int sample_nb<D3>(int r, D3 p, D3 u, uint32_t& fl) {
   return sample_nb<double>(r, p.v, u.v, fl);

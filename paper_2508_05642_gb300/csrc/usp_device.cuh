@@ -171,6 +171,61 @@ __device__ __forceinline__ void box_muller(double ua, double ub, double& ga, dou
 }
 
 // ---------------------------------------------------------------------------
+// The collision draws of one particle and step: four standard normals
+// g0..g3 (two Box-Muller pairs) and the two words j5, j6 whose uniforms
+// drive the jump samplers, all from one Philox block, counter
+// (pid, step, 0, 0).  A uniform takes 23 bits of a word,
+// (2 (x >> 9) + 1) 2^-24, exact in float and double, so one block carries
+// all six: the top 23 bits of words 0 and 1 are the two radius uniforms, those
+// of words 2 and 3 the jump uniforms (j5 = word 2, j6 = word 3), and the low
+// 9 bits of words 0 and 1, then of words 2 and 3, form the two angle uniforms
+// of 18 bits, (2 a + 1) 2^-19 with a = (lo9(word) << 9) | lo9(next word).
+// The FP32 and FP64 forms thus draw identical values.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t angle_bits18(uint32_t wa, uint32_t wb) {
+  return ((wa & 0x1ffu) << 9) | (wb & 0x1ffu);
+}
+__device__ __forceinline__ float angle_uniform18(uint32_t wa, uint32_t wb) {
+  // 1 + a 2^-18 minus 1 - 2^-19: exactly (2 a + 1) 2^-19 (Sterbenz)
+  return __fsub_rn(__int_as_float((int)(0x3f800000u | (angle_bits18(wa, wb) << 5))),
+                   0.99999809265136718750f);
+}
+__device__ __forceinline__ double angle_uniform18_d(uint32_t wa, uint32_t wb) {
+  return (2.0 * (double)angle_bits18(wa, wb) + 1.0) * 1.9073486328125e-06;   // 2^-19
+}
+// the 23-bit uniform of a word in double (equal to uniform_open<float>)
+__device__ __forceinline__ double uniform23_d(uint32_t x) {
+  return (2.0 * (double)(x >> 9) + 1.0) * 5.9604644775390625e-08;             // 2^-24
+}
+
+// the jump-sampler uniform of a word, in the working type
+template <typename T>
+__device__ __forceinline__ T jump_uniform(uint32_t x) { return T(uniform23_d(x)); }
+template <>
+__device__ __forceinline__ float jump_uniform<float>(uint32_t x) { return uniform_open<float>(x); }
+
+__device__ __forceinline__ void particle_draws(uint32_t pid, uint32_t step,
+                                               const PhiloxRoundKeys& rk, float& g0, float& g1,
+                                               float& g2, float& g3, uint32_t& j5, uint32_t& j6) {
+  const U4 w = philox4x32_10(pid, step, PTAG_NORMALS, 0u, rk);
+  box_muller(uniform_open<float>(w.x), angle_uniform18(w.x, w.y), g0, g1);
+  box_muller(uniform_open<float>(w.y), angle_uniform18(w.z, w.w), g2, g3);
+  j5 = w.z;
+  j6 = w.w;
+}
+
+__device__ __forceinline__ void particle_draws(uint32_t pid, uint32_t step,
+                                               const PhiloxRoundKeys& rk, double& g0, double& g1,
+                                               double& g2, double& g3, uint32_t& j5,
+                                               uint32_t& j6) {
+  const U4 w = philox4x32_10(pid, step, PTAG_NORMALS, 0u, rk);
+  box_muller(uniform23_d(w.x), angle_uniform18_d(w.x, w.y), g0, g1);
+  box_muller(uniform23_d(w.y), angle_uniform18_d(w.z, w.w), g2, g3);
+  j5 = w.z;
+  j6 = w.w;
+}
+
+// ---------------------------------------------------------------------------
 // Jump samplers of Eq. update_evib: sequential inversion with one uniform,
 // pmf stepped by its ratio recursion, P(0) by square-and-multiply; a binomial
 // with p > 1/2 is drawn as n - B(n, 1 - p).  Every operation is an explicit

@@ -163,27 +163,6 @@ __device__ void b_row(int n, float p, float* T) {
 // the sequential search.
 constexpr int kGB = 256;   // guide bytes per row
 
-__device__ void guide_row(const float* __restrict__ T, uint8_t* __restrict__ g) {
-  uint32_t* g4 = reinterpret_cast<uint32_t*>(g);
-  if (T[0] < 0.0f) {
-    for (int q = 0; q < kGB / 4; ++q) g4[q] = 0xffffffffu;
-    return;
-  }
-  int k = 0;
-  for (int q = 0; q < kGB / 4; ++q) {
-    uint32_t word = 0;
-    for (int b = 0; b < 4; ++b) {
-      const int m = 4 * q + b;
-      const float umin = (float)(2 * (m << 15) + 1) * 5.9604644775390625e-8f;
-      const float umax = (float)(2 * ((m << 15) + 32767) + 1) * 5.9604644775390625e-8f;
-      while (k < kJK && T[k] <= umin) ++k;
-      const bool exact = k >= kJK || T[k] > umax;
-      word |= (uint32_t)(k | (exact ? 0x80 : 0)) << (8 * b);
-    }
-    g4[q] = word;
-  }
-}
-
 // number of leading row entries <= u, u formed from the word x
 __device__ __forceinline__ int guided_search(const float* __restrict__ T,
                                              const uint8_t* __restrict__ g, uint32_t x, float u) {
@@ -236,11 +215,9 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
                                             T* acc, int& accI, int& maxI, uint32_t& fl,
                                             const JumpTabs& jt) {
   const int I = lv;
-  U4 w, w2;
-  philox4x32_10_pair(pid, P.step, PTAG_NORMALS, PTAG_JUMPS, 0u, rk, w, w2);
   T g0, g1, g2, g3;
-  box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
-  box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
+  uint32_t j5, j6;
+  particle_draws(pid, P.step, rk, g0, g1, g2, g3, j5, j6);
   // c^n - U = s (c* - U*);  C' = alpha C^n + sqrt(1 - alpha^2) L G
   const T d0 = cx - P.Us[0], d1 = cy - P.Us[1], d2 = cz - P.Us[2];
   const T r0 = P.as * d0 + P.Lp[0] * g0;
@@ -253,7 +230,7 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   const T root = sqrt_fast(er) * P.ar + P.sqrt_a * g3;
   er = P.a_rot + root * root;
   // I' = I + NB(I + 1, p_NB) - B(I, p_B)
-  const T u5 = uniform_open<T>(w2.x), u6 = uniform_open<T>(w2.y);
+  const T u5 = jump_uniform<T>(j5), u6 = jump_uniform<T>(j6);
   if constexpr (METHOD == 1) {
     // plain FPM method: Gillespie's direct method (Sec. 2.C)
     lv = gillespie<T>(I, P.p_nb, P.p_b, pid, P.step, rk, fl);
@@ -262,8 +239,8 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
     if constexpr (sizeof(T) == 4) {
       // the particle's rows: NB r = I + 1 is row I, binomial n = I is row I
       const size_t row = (size_t)(I < kJR ? I : 0);
-      up = nb_tab(jt.nb + row * kJK, jt.gnb + row * kGB, I + 1, P.p_nb, u5, w2.x, fl);
-      dn = b_tab(jt.b + row * kJK, jt.gb + row * kGB, I, P.p_b, u6, w2.y, fl);
+      up = nb_tab(jt.nb + row * kJK, jt.gnb + row * kGB, I + 1, P.p_nb, u5, j5, fl);
+      dn = b_tab(jt.b + row * kJK, jt.gb + row * kGB, I, P.p_b, u6, j6, fl);
     } else {
       up = sample_nb<T>(I + 1, P.p_nb, u5, fl);
       dn = sample_b<T>(I, P.p_b, u6, fl);
@@ -805,32 +782,72 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
 }
 
 
-// Jump-table rows of every cell for the coming step (FP32 form): thread j <
-// kJR builds the NB row r = j + 1, thread kJR + n the binomial row n, for the
-// rows the cell's levels can reach.
-__global__ void jumptable_kernel(int c0, int c1, const CollideParams<float>* __restrict__ prm,
-                                 const CellState* __restrict__ cells, float* __restrict__ tab_nb,
-                                 float* __restrict__ tab_b, uint8_t* __restrict__ gd_nb,
-                                 uint8_t* __restrict__ gd_b) {
+// Jump-table rows of every cell for the coming step (FP32 form), one block of
+// kJT threads per cell: thread j < kJR builds the NB row r = j + 1, thread
+// kJR + n the binomial row n, for the rows the cell's levels can reach; then
+// every thread builds a quarter (64 bins) of one row's guide.
+constexpr int kJT = 8 * kJR;
+
+__device__ __forceinline__ bool nb_row_used(int j, int rows, float p_nb) {
+  return j + 1 <= rows && p_nb < 1.0f;
+}
+__device__ __forceinline__ bool b_row_used(int n, int rows, float p_b) {
+  return n >= 1 && n <= rows - 1 && p_b < 1.0f && p_b > 0.0f;
+}
+
+// bins [q kGB/4, (q + 1) kGB/4) of the guide of row T (the guide tables above)
+__device__ void guide_quarter(const float* __restrict__ T, uint8_t* __restrict__ g, int q) {
+  uint32_t* g4 = reinterpret_cast<uint32_t*>(g);
+  constexpr int kQ = kGB / 4;
+  if (T[0] < 0.0f) {
+    for (int w = q * kQ / 4; w < (q + 1) * kQ / 4; ++w) g4[w] = 0xffffffffu;
+    return;
+  }
+  int k = 0;
+  const float u0 = (float)(2 * ((q * kQ) << 15) + 1) * 5.9604644775390625e-8f;
+  while (k < kJK && T[k] <= u0) ++k;
+  for (int w = q * kQ / 4; w < (q + 1) * kQ / 4; ++w) {
+    uint32_t word = 0;
+    for (int b = 0; b < 4; ++b) {
+      const int m = 4 * w + b;
+      const float umin = (float)(2 * (m << 15) + 1) * 5.9604644775390625e-8f;
+      const float umax = (float)(2 * ((m << 15) + 32767) + 1) * 5.9604644775390625e-8f;
+      while (k < kJK && T[k] <= umin) ++k;
+      const bool exact = k >= kJK || T[k] > umax;
+      word |= (uint32_t)(k | (exact ? 0x80 : 0)) << (8 * b);
+    }
+    g4[w] = word;
+  }
+}
+
+__global__ void __launch_bounds__(kJT)
+jumptable_kernel(int c0, int c1, const CollideParams<float>* __restrict__ prm,
+                 const CellState* __restrict__ cells, float* __restrict__ tab_nb,
+                 float* __restrict__ tab_b, uint8_t* __restrict__ gd_nb,
+                 uint8_t* __restrict__ gd_b) {
   const int c = c0 + blockIdx.x;
   const int j = threadIdx.x;
-  if (c >= c1) return;
+  if (c >= c1) return;                       // uniform over the block
   const CollideParams<float>& P = prm[c];
-  if (!P.active) return;
+  if (!P.active) return;                     // uniform over the block
   const int rows = min(kJR, cells[c].maxI + 1);
+  float pb = P.p_b;
+  if (pb > 0.5f && pb < 1.0f) pb = rn_sub(1.0f, pb);
   if (j < kJR) {
-    const int r = j + 1;
-    if (r > rows || !(P.p_nb < 1.0f)) return;
-    nb_row(r, P.p_nb, tab_nb + ((size_t)c * kJR + j) * kJK);
-    guide_row(tab_nb + ((size_t)c * kJR + j) * kJK, gd_nb + ((size_t)c * kJR + j) * kGB);
-  } else {
+    if (nb_row_used(j, rows, P.p_nb)) nb_row(j + 1, P.p_nb, tab_nb + ((size_t)c * kJR + j) * kJK);
+  } else if (j < 2 * kJR) {
     const int n = j - kJR;
-    if (n < 1 || n > rows - 1) return;
-    float p = P.p_b;
-    if (!(p < 1.0f) || !(p > 0.0f)) return;
-    if (p > 0.5f) p = rn_sub(1.0f, p);
-    b_row(n, p, tab_b + ((size_t)c * kJR + n) * kJK);
-    guide_row(tab_b + ((size_t)c * kJR + n) * kJK, gd_b + ((size_t)c * kJR + n) * kGB);
+    if (b_row_used(n, rows, P.p_b)) b_row(n, pb, tab_b + ((size_t)c * kJR + n) * kJK);
+  }
+  __syncthreads();
+  const int row = j >> 2, q = j & 3;         // 2 kJR rows, four quarters each
+  if (row < kJR) {
+    if (nb_row_used(row, rows, P.p_nb))
+      guide_quarter(tab_nb + ((size_t)c * kJR + row) * kJK, gd_nb + ((size_t)c * kJR + row) * kGB, q);
+  } else {
+    const int n = row - kJR;
+    if (b_row_used(n, rows, P.p_b))
+      guide_quarter(tab_b + ((size_t)c * kJR + n) * kJK, gd_b + ((size_t)c * kJR + n) * kGB, q);
   }
 }
 
@@ -1620,7 +1637,7 @@ int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, voi
 // jump tables for the coming step (FP32 form only)
 int launch_tables(usp_ctx* c, const CellRange& r) {
   if (c->precision != USP_FP32 || c->sp.method != 0 || r.c1 <= r.c0) return USP_OK;
-  jumptable_kernel<<<r.c1 - r.c0, 2 * kJR, 0, c->stream>>>(
+  jumptable_kernel<<<r.c1 - r.c0, kJT, 0, c->stream>>>(
       r.c0, r.c1, (const CollideParams<float>*)c->prm, c->cells, c->tab_nb, c->tab_b, c->gd_nb,
       c->gd_b);
   CK(cudaGetLastError());

@@ -232,11 +232,9 @@ __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx
   }
   if (cl) { t.fl |= F_TREL_CLAMP; ++t.ncl; }
   // draws
-  U4 w, w2;
-  philox4x32_10_pair(id, step, PTAG_NORMALS, PTAG_JUMPS, 0u, rk, w, w2);
   T g0, g1, g2, g3;
-  box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
-  box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
+  uint32_t j5, j6;
+  particle_draws(id, step, rk, g0, g1, g2, g3, j5, j6);
   // Eq. update_ci about the interpolated bulk velocity
   const T a2 = alpha * alpha, sq = sqrt(T(1) - a2);
   const T v0 = f[0] + alpha * (vx - f[0]) + sq * (L[0] * g0);
@@ -258,8 +256,8 @@ __device__ __forceinline__ int collide_particle_t(const P_& P, const T* f, T& vx
   }
   const T p_b = (T(1) + eb) * (T(1) - a2);
   uint32_t f1 = 0;
-  const int up = sample_nb<T>(I + 1, p_nb, uniform_open<T>(w2.x), f1);
-  const int dn = sample_b<T>(I, p_b, uniform_open<T>(w2.y), f1);
+  const int up = sample_nb<T>(I + 1, p_nb, jump_uniform<T>(j5), f1);
+  const int dn = sample_b<T>(I, p_b, jump_uniform<T>(j6), f1);
   if (f1 & F_PB_CLAMP) ++t.npb;
   t.fl |= f1;
   return I + up - dn;
@@ -688,10 +686,9 @@ __device__ __forceinline__ int fpm_particle(const T* U, T a, const T* Lp, T a_ro
                                             T lam_up, T lam_dn, T& v0, T& v1, T& v2, T& en,
                                             int l0, uint32_t id, uint32_t step,
                                             const PhiloxRoundKeys& rk, uint32_t& fl) {
-  const U4 w = philox4x32_10(id, step, PTAG_NORMALS, 0u, rk);
   T g0, g1, g2, g3;
-  box_muller(uniform_open<T>(w.x), uniform_open<T>(w.y), g0, g1);
-  box_muller(uniform_open<T>(w.z), uniform_open<T>(w.w), g2, g3);
+  uint32_t j5, j6;   // unused: Gillespie's method draws from its own stream
+  particle_draws(id, step, rk, g0, g1, g2, g3, j5, j6);
   const T d0 = v0 - U[0], d1 = v1 - U[1], d2 = v2 - U[2];
   v0 = U[0] + a * d0 + Lp[0] * g0;
   v1 = U[1] + a * d1 + (Lp[1] * g0 + Lp[2] * g1);

@@ -42,6 +42,26 @@ def _pair(w, steps, precision, sample_last=0, use_graph=True):
     return dict(sp=sp, ch=ch, st=st, g=g, acc=acc, gacc=gacc, gfl=gfl, gcnt=gcnt, ctx=ctx)
 
 
+def test_fp64_channel_full_size_100_steps_matches_oracle():
+    """The Poiseuille workload at its full size (64 cells x 200 particles)
+    over its first 100 steps, the last 20 sampled: same particles in the same
+    cell order, same levels, values within FP64 rounding, same time-average
+    sums.  (The runs stay one realization for about 500 steps: their velocity
+    difference grows tenfold per 100 steps from rounding size.)"""
+    w = I.channel_poiseuille(ny=64, ppc=200, steps=0)
+    r = _pair(w, 100, usp.USP_FP64, sample_last=20)
+    st, (gy, gx, gyv, gz, ge, gl, gp) = r["st"], r["g"]
+    R = O.R(r["sp"])
+    vth = math.sqrt(R * 300.0)
+    assert np.array_equal(gp, st.pid) and np.array_equal(gl, st.lev)
+    assert np.max(np.abs(gy - st.y)) < 1e-9 * r["ch"].L
+    for a, b in ((gx, st.cx), (gyv, st.cy), (gz, st.cz)):
+        assert np.max(np.abs(a - b)) < 1e-8 * vth
+    assert np.max(np.abs(ge - st.erot)) < 1e-8 * R * 300.0
+    np.testing.assert_allclose(r["gacc"], r["acc"], rtol=1e-9, atol=1e-6)
+    assert r["gcnt"][usp.C_WALL_HITS] > 0 and r["gfl"] & usp.ERROR_FLAGS == 0
+
+
 def test_fp64_channel_matches_oracle_step_by_step():
     w = I.channel_poiseuille(ny=16, ppc=100, steps=0)
     r = _pair(w, 30, usp.USP_FP64, sample_last=10)

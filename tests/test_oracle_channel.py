@@ -92,12 +92,17 @@ def test_momentum_bookkeeping_is_exact():
 
 
 def test_closed_box_keeps_wall_equilibrium():
-    """No force, gas at the wall temperature: it stays at T_w, at rest."""
+    """No force, gas at the wall temperature: it stays at T_w, at rest.  One
+    run's mean temperature over the box scatters by 1.4 % between seeds (16
+    cells of 100 particles, 100 averaged steps), so eight seeds are pooled."""
     w = I.channel_poiseuille(ny=16, ppc=100, g=0.0, steps=0)
-    sp, ch, dt, st = _setup(w)
-    acc = np.zeros(ch.ny * O.NACC + 2)
-    O.channel_step(sp, 0, 6, 0, 100, ch, dt, st)
-    O.channel_step(sp, 0, 6, 100, 100, ch, dt, st, acc)
+    acc = None
+    for seed in range(1, 9):
+        sp, ch, dt, st = _setup(w)
+        a1 = np.zeros(ch.ny * O.NACC + 2)
+        O.channel_step(sp, 0, seed, 0, 100, ch, dt, st)
+        O.channel_step(sp, 0, seed, 100, 100, ch, dt, st, a1)
+        acc = a1 if acc is None else acc + a1
     R = O.R(sp)
     a = acc[: ch.ny * O.NACC].reshape(ch.ny, O.NACC)
     N = a[:, 0]

@@ -591,3 +591,26 @@ def test_moments_match_brute_force_definitions():
                                               for i in range(3)])
         qv = [sum(C[k, i] * lev[k] for k in range(N)) / N * R * sp.theta_v for i in range(3)]
         np.testing.assert_allclose(m[19:22, ci], qv, rtol=1e-15, atol=1e-300)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_collision_draws_are_independent_normals_and_uniforms(form):
+    """The four normals and two jump uniforms of a particle's step (one
+    Philox block: 23-bit radius and jump uniforms, 18-bit angles; the same in
+    both forms): each normal passes a KS test against N(0, 1), each uniform
+    against U(0, 1), and the six are uncorrelated over 40,000 particles."""
+    n = 40000
+    D = np.array([np.concatenate([g, [a, b]]) for g, a, b in
+                  (O.particle_draws(7, pid, 3, form) for pid in range(n))])
+    for k in range(4):
+        assert stats.kstest(D[:, k], "norm").pvalue > 1e-3, k
+    for k in (4, 5):
+        assert stats.kstest(D[:, k], "uniform").pvalue > 1e-3, k
+    Z = np.column_stack([D[:, :4], stats.norm.ppf(D[:, 4:])])
+    C = np.corrcoef(Z.T)
+    assert np.abs(C - np.eye(6)).max() < 5.0 / math.sqrt(n)
+    # float-exact uniforms, the same draws in both forms
+    assert np.all(np.float32(D[:, 4]) == D[:, 4]) and np.all(np.float32(D[:, 5]) == D[:, 5])
+    other = O.particle_draws(7, 123, 3, 1 - form)
+    mine = O.particle_draws(7, 123, 3, form)
+    assert np.array_equal(other[0], mine[0]) and other[1:] == mine[1:]
