@@ -101,8 +101,12 @@ enum {
  * USP_FP64_TANGENT (channel contexts only) the FP64 form carrying, for every
  * continuous quantity, its derivatives with respect to Z_rot, the viscosity
  * index omega and T_wall (forward-mode pathwise derivatives under common
- * random numbers; discrete outcomes held fixed). */
-enum { USP_FP64 = 0, USP_FP32 = 1, USP_FP64_TANGENT = 2 };
+ * random numbers; discrete outcomes, wall-event times and positions held
+ * fixed); USP_FP32_TANGENT (channel contexts only) the same derivatives with
+ * the FP32 form's particle state and per-particle arithmetic (values and
+ * derivatives in FP32) and FP64 cell quantities, sums and time averages
+ * (FP64 accumulation of the derivatives). */
+enum { USP_FP64 = 0, USP_FP32 = 1, USP_FP64_TANGENT = 2, USP_FP32_TANGENT = 3 };
 
 /* Particle method (usp_config.method, homogeneous contexts):
  * USP_METHOD_USP_FPM  the second-order USP-FPM method (Sec. 3, 4), default;
@@ -149,7 +153,7 @@ typedef struct {
   int method;           /* USP_METHOD_*; channel and plane contexts run
                            USP_METHOD_FPM with the cell values at every
                            particle (the first-order method: no
-                           reconstruction); not with USP_FP64_TANGENT
+                           reconstruction); not with the tangent forms
                            (USP_ENOTSUP)                                      */
 } usp_config;
 
@@ -274,7 +278,7 @@ int usp_channel_read(usp_ctx* ctx, double* h_acc, int reset);
  * over every particle-step of the window): U = sum c / sum N,
  * T_tr = (sum |c|^2 / sum N - |U|^2) / 3R, T_rot = sum eps / (R sum N),
  * T_vib inverting e_vib at the mean level (0 for no excitation).  Cells
- * that held no particle give zeros.  In the USP_FP64_TANGENT form out holds
+ * that held no particle give zeros.  In the tangent forms out holds
  * 4 such blocks of USP_NPROF * ny doubles: the profiles, then their
  * derivatives with respect to Z_rot, omega and T_wall (0 for the count and
  * T_vib: counts and levels are held).  out_is_device = 1: device memory,
@@ -284,7 +288,7 @@ int usp_channel_read(usp_ctx* ctx, double* h_acc, int reset);
 int usp_profiles(usp_ctx* ctx, double* out, int out_is_device);
 
 /* Gradient of a scalar objective L(profiles) with respect to the parameters
- * (Z_rot, omega, T_wall) of a USP_FP64_TANGENT channel context: the pathwise
+ * (Z_rot, omega, T_wall) of a tangent-form channel context: the pathwise
  * derivative under common random numbers,
  *   grad3[k] = sum_{f, cell} dL_dprof[f * ny + cell] * d prof[f][cell] / d theta_k,
  * contracted on the device from the derivative sums the run accumulated.

@@ -55,6 +55,30 @@ __device__ __forceinline__ void particle_draws(uint32_t pid, uint32_t step,
   particle_draws(pid, step, rk, a0, a1, a2, a3, j5, j6);
   g0 = D3(a0); g1 = D3(a1); g2 = D3(a2); g3 = D3(a3);
 }
+// the FP32 gradient form: FP32 values and derivatives per particle
+template <>
+__device__ __forceinline__ F3 uniform_open<F3>(uint32_t x) {
+  return F3(uniform_open<float>(x));
+}
+__device__ __forceinline__ void particle_draws(uint32_t pid, uint32_t step,
+                                               const PhiloxRoundKeys& rk, F3& g0, F3& g1, F3& g2,
+                                               F3& g3, uint32_t& j5, uint32_t& j6) {
+  float a0, a1, a2, a3;
+  particle_draws(pid, step, rk, a0, a1, a2, a3, j5, j6);
+  g0 = F3(a0); g1 = F3(a1); g2 = F3(a2); g3 = F3(a3);
+}
+template <>
+__device__ __forceinline__ F3 jump_uniform<F3>(uint32_t x) {
+  return F3(uniform_open<float>(x));
+}
+template <>
+__device__ __forceinline__ int sample_nb<F3>(int r, F3 p, F3 u, uint32_t& fl) {
+  return sample_nb<float>(r, p.v, u.v, fl);
+}
+template <>
+__device__ __forceinline__ int sample_b<F3>(int n, F3 p, F3 u, uint32_t& fl) {
+  return sample_b<float>(n, p.v, u.v, fl);
+}
 template <>
 __device__ __forceinline__ int sample_nb<D3>(int r, D3 p, D3 u, uint32_t& fl) {
   return sample_nb<double>(r, p.v, u.v, fl);
@@ -82,6 +106,9 @@ struct ChParams {
 __device__ __forceinline__ int cell_index(float y, double dy) { return (int)floorf(y / (float)dy); }
 __device__ __forceinline__ int cell_index(double y, double dy) { return (int)floor(y / dy); }
 __device__ __forceinline__ int cell_index(const D3& y, double dy) { return (int)floor(y.v / dy); }
+__device__ __forceinline__ int cell_index(const F3& y, double dy) {
+  return (int)floorf(y.v / (float)dy);
+}
 
 // ---------------------------------------------------------------------------
 // move
@@ -760,6 +787,7 @@ int ch_kernels_per_step(const ChannelCtx* h) {
 int ch_launch_step(ChannelCtx* h, const ChEnv& env, ch_prof_fn prof) {
   if (env.precision == USP_FP32) return ch_step_t<float, double>(h, env, prof);
   if (env.precision == USP_FP64_TANGENT) return ch_step_t<D3, D3>(h, env, prof);
+  if (env.precision == USP_FP32_TANGENT) return ch_step_t<F3, D3>(h, env, prof);
   return ch_step_t<double, double>(h, env, prof);
 }
 
@@ -777,8 +805,9 @@ int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double
   h->ny = chp->ny; h->L = chp->L; h->dy = chp->L / chp->ny; h->Tw = chp->T_wall; h->g = chp->g;
   h->Fnum = chp->F_num; h->area = chp->area; h->recon = chp->reconstruct ? 1 : 0; h->dt = dt;
   h->n = n;
-  const bool grad = env.precision == USP_FP64_TANGENT;
-  h->es = env.precision == USP_FP32 ? 4 : (grad ? sizeof(D3) : 8);
+  const bool g32 = env.precision == USP_FP32_TANGENT;
+  const bool grad = env.precision == USP_FP64_TANGENT || g32;
+  h->es = env.precision == USP_FP32 ? 4 : (g32 ? sizeof(F3) : (grad ? sizeof(D3) : 8));
   h->blocks = grad ? 1 + kND : 1;
   const size_t cell_bytes = grad ? sizeof(ChCellT<D3>) : sizeof(ChCellT<double>);
   const size_t sums_bytes = grad ? sizeof(ChSumsT<D3>) : sizeof(ChSumsT<double>);
@@ -803,7 +832,9 @@ int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double
   h->off = (long long*)A(sizeof(long long) * (h->ny + 1));
   h->cells = A(cell_bytes * h->ny);
   h->prm = A((env.precision == USP_FP32 ? sizeof(ChParams<float>)
-                                        : (grad ? sizeof(ChParams<D3>) : sizeof(ChParams<double>))) *
+                                        : (g32 ? sizeof(ChParams<F3>)
+                                               : (grad ? sizeof(ChParams<D3>)
+                                                       : sizeof(ChParams<double>)))) *
              h->ny);
   h->sums = A(sums_bytes * h->ny);
   if (env.sp.method == 1) h->fpmrec = (double*)A(sizeof(double) * kFpmRec * (size_t)h->ny);
@@ -864,6 +895,9 @@ int ch_create(ChannelCtx** out, const ChEnv& env, const usp_channel* chp, double
     if (env.precision == USP_FP32)
       ch_from_host_layout<float><<<nb, 256, 0, s>>>(n, stage, (float*)h->st[0][0],
           (float*)h->st[0][1], (float*)h->st[0][2], (float*)h->st[0][3], (float*)h->st[0][4]);
+    else if (g32)
+      ch_from_host_layout<F3><<<nb, 256, 0, s>>>(n, stage, (F3*)h->st[0][0], (F3*)h->st[0][1],
+          (F3*)h->st[0][2], (F3*)h->st[0][3], (F3*)h->st[0][4]);
     else if (grad)
       ch_from_host_layout<D3><<<nb, 256, 0, s>>>(n, stage, (D3*)h->st[0][0], (D3*)h->st[0][1],
           (D3*)h->st[0][2], (D3*)h->st[0][3], (D3*)h->st[0][4]);
@@ -923,6 +957,10 @@ int ch_moments(ChannelCtx* h, const ChEnv& env, double* out, int out_is_device) 
       ch_mom_pass<D3, D3><<<nb, 256, 0, s>>>(pass, n, h->keycell, (const ChCellT<D3>*)h->cells,
           (D3*)h->st[b][1], (D3*)h->st[b][2], (D3*)h->st[b][3], (D3*)h->st[b][4], h->lv[b],
           h->macc);
+    else if (env.precision == USP_FP32_TANGENT)
+      ch_mom_pass<F3, D3><<<nb, 256, 0, s>>>(pass, n, h->keycell, (const ChCellT<D3>*)h->cells,
+          (F3*)h->st[b][1], (F3*)h->st[b][2], (F3*)h->st[b][3], (F3*)h->st[b][4], h->lv[b],
+          h->macc);
     else
       ch_mom_pass<double, double><<<nb, 256, 0, s>>>(pass, n, h->keycell,
           (const ChCellT<double>*)h->cells, (double*)h->st[b][1], (double*)h->st[b][2],
@@ -953,6 +991,10 @@ int ch_get_particles(ChannelCtx* h, const ChEnv& env, double* y, double* cx, dou
   else if (env.precision == USP_FP64_TANGENT)
     ch_to_host_layout<D3, D3><<<nb, 256, 0, s>>>(n, h->keycell, (const ChCellT<D3>*)h->cells,
         (D3*)h->st[b][0], (D3*)h->st[b][1], (D3*)h->st[b][2], (D3*)h->st[b][3], (D3*)h->st[b][4],
+        tmp);
+  else if (env.precision == USP_FP32_TANGENT)
+    ch_to_host_layout<F3, D3><<<nb, 256, 0, s>>>(n, h->keycell, (const ChCellT<D3>*)h->cells,
+        (F3*)h->st[b][0], (F3*)h->st[b][1], (F3*)h->st[b][2], (F3*)h->st[b][3], (F3*)h->st[b][4],
         tmp);
   else
     ch_to_host_layout<double, double><<<nb, 256, 0, s>>>(n, h->keycell,

@@ -5,9 +5,14 @@
 // Every arithmetic operation and elementary function below propagates the
 // derivative by the chain rule; comparisons look at the value only, so a
 // discrete decision (a level jump, a cell index, a wall hit, a branch) taken
-// in the derivative form is the same as in the plain FP64 form and is held
-// fixed in the derivative (the pathwise derivative under common random
-// numbers).
+// in the derivative form is the same as in the plain form of the same
+// precision and is held fixed in the derivative (the pathwise derivative
+// under common random numbers).
+//
+// Dual<double> (D3) carries FP64 values and derivatives (the FP64 gradient
+// form); Dual<float> (F3) carries FP32 values and derivatives for the
+// per-particle arithmetic of the FP32 gradient form, whose cell sums and
+// cell-level quantities stay D3 (FP64 accumulation).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -19,134 +24,213 @@ namespace dual {
 
 constexpr int kND = 3;
 
-struct D3 {
-  double v;
-  double d[kND];
-  __host__ __device__ D3() : v(0.0) { d[0] = d[1] = d[2] = 0.0; }
-  __host__ __device__ D3(double x) : v(x) { d[0] = d[1] = d[2] = 0.0; }
-  __host__ __device__ D3(double x, double d0, double d1, double d2) : v(x) {
-    d[0] = d0; d[1] = d1; d[2] = d2;
+// elementary functions of the value type
+__host__ __device__ inline float vsqrt(float x) { return sqrtf(x); }
+__host__ __device__ inline double vsqrt(double x) { return ::sqrt(x); }
+__host__ __device__ inline float vlog(float x) { return logf(x); }
+__host__ __device__ inline double vlog(double x) { return ::log(x); }
+__host__ __device__ inline float vlog1p(float x) { return log1pf(x); }
+__host__ __device__ inline double vlog1p(double x) { return ::log1p(x); }
+__host__ __device__ inline float vexp(float x) { return expf(x); }
+__host__ __device__ inline double vexp(double x) { return ::exp(x); }
+__host__ __device__ inline float vexpm1(float x) { return expm1f(x); }
+__host__ __device__ inline double vexpm1(double x) { return ::expm1(x); }
+__host__ __device__ inline float vsinh(float x) { return sinhf(x); }
+__host__ __device__ inline double vsinh(double x) { return ::sinh(x); }
+__host__ __device__ inline float vcosh(float x) { return coshf(x); }
+__host__ __device__ inline double vcosh(double x) { return ::cosh(x); }
+__host__ __device__ inline float vcos(float x) { return cosf(x); }
+__host__ __device__ inline double vcos(double x) { return ::cos(x); }
+__host__ __device__ inline float vsin(float x) { return sinf(x); }
+__host__ __device__ inline double vsin(double x) { return ::sin(x); }
+__host__ __device__ inline float vacos(float x) { return acosf(x); }
+__host__ __device__ inline double vacos(double x) { return ::acos(x); }
+__host__ __device__ inline float vcbrt(float x) { return cbrtf(x); }
+__host__ __device__ inline double vcbrt(double x) { return ::cbrt(x); }
+__host__ __device__ inline float vpow(float x, float y) { return powf(x, y); }
+__host__ __device__ inline double vpow(double x, double y) { return ::pow(x, y); }
+
+template <typename V>
+struct Dual {
+  V v;
+  V d[kND];
+  __host__ __device__ Dual() : v(V(0)) { d[0] = d[1] = d[2] = V(0); }
+  __host__ __device__ Dual(double x) : v(V(x)) { d[0] = d[1] = d[2] = V(0); }
+  __host__ __device__ Dual(double x, double d0, double d1, double d2) : v(V(x)) {
+    d[0] = V(d0); d[1] = V(d1); d[2] = V(d2);
   }
-  __host__ __device__ explicit operator double() const { return v; }
+  // between precisions (FP32 particle values <-> FP64 cell values)
+  template <typename U>
+  __host__ __device__ explicit Dual(const Dual<U>& o) : v(V(o.v)) {
+    for (int i = 0; i < kND; ++i) d[i] = V(o.d[i]);
+  }
+  __host__ __device__ explicit operator double() const { return (double)v; }
   __host__ __device__ explicit operator float() const { return (float)v; }
   __host__ __device__ explicit operator int() const { return (int)v; }
-  __host__ __device__ D3& operator+=(const D3& b) {
+  __host__ __device__ Dual& operator+=(const Dual& b) {
     v += b.v;
     for (int i = 0; i < kND; ++i) d[i] += b.d[i];
     return *this;
   }
-  __host__ __device__ D3& operator-=(const D3& b) {
+  __host__ __device__ Dual& operator-=(const Dual& b) {
     v -= b.v;
     for (int i = 0; i < kND; ++i) d[i] -= b.d[i];
     return *this;
   }
-  __host__ __device__ D3& operator*=(const D3& b) {
+  __host__ __device__ Dual& operator*=(const Dual& b) {
     for (int i = 0; i < kND; ++i) d[i] = d[i] * b.v + v * b.d[i];
     v *= b.v;
     return *this;
   }
-  __host__ __device__ D3& operator/=(const D3& b) {
-    const double q = v / b.v;
+  __host__ __device__ Dual& operator/=(const Dual& b) {
+    const V q = v / b.v;
     for (int i = 0; i < kND; ++i) d[i] = (d[i] - q * b.d[i]) / b.v;
     v = q;
     return *this;
   }
 };
 
-__host__ __device__ inline D3 operator+(D3 a, const D3& b) { return a += b; }
-__host__ __device__ inline D3 operator-(D3 a, const D3& b) { return a -= b; }
-__host__ __device__ inline D3 operator*(D3 a, const D3& b) { return a *= b; }
-__host__ __device__ inline D3 operator/(D3 a, const D3& b) { return a /= b; }
-__host__ __device__ inline D3 operator+(D3 a, double b) { a.v += b; return a; }
-__host__ __device__ inline D3 operator+(double b, D3 a) { a.v += b; return a; }
-__host__ __device__ inline D3 operator-(D3 a, double b) { a.v -= b; return a; }
-__host__ __device__ inline D3 operator-(double b, const D3& a) {
-  D3 r(b - a.v);
+using D3 = Dual<double>;
+using F3 = Dual<float>;
+
+template <typename V>
+__host__ __device__ inline Dual<V> operator+(Dual<V> a, const Dual<V>& b) { return a += b; }
+template <typename V>
+__host__ __device__ inline Dual<V> operator-(Dual<V> a, const Dual<V>& b) { return a -= b; }
+template <typename V>
+__host__ __device__ inline Dual<V> operator*(Dual<V> a, const Dual<V>& b) { return a *= b; }
+template <typename V>
+__host__ __device__ inline Dual<V> operator/(Dual<V> a, const Dual<V>& b) { return a /= b; }
+template <typename V>
+__host__ __device__ inline Dual<V> operator+(Dual<V> a, double b) { a.v += V(b); return a; }
+template <typename V>
+__host__ __device__ inline Dual<V> operator+(double b, Dual<V> a) { a.v += V(b); return a; }
+template <typename V>
+__host__ __device__ inline Dual<V> operator-(Dual<V> a, double b) { a.v -= V(b); return a; }
+template <typename V>
+__host__ __device__ inline Dual<V> operator-(double b, const Dual<V>& a) {
+  Dual<V> r;
+  r.v = V(b) - a.v;
   for (int i = 0; i < kND; ++i) r.d[i] = -a.d[i];
   return r;
 }
-__host__ __device__ inline D3 operator*(D3 a, double b) {
-  a.v *= b;
-  for (int i = 0; i < kND; ++i) a.d[i] *= b;
+template <typename V>
+__host__ __device__ inline Dual<V> operator*(Dual<V> a, double b) {
+  const V c = V(b);
+  a.v *= c;
+  for (int i = 0; i < kND; ++i) a.d[i] *= c;
   return a;
 }
-__host__ __device__ inline D3 operator*(double b, D3 a) { return a * b; }
-__host__ __device__ inline D3 operator/(D3 a, double b) {
-  a.v /= b;
-  for (int i = 0; i < kND; ++i) a.d[i] /= b;
+template <typename V>
+__host__ __device__ inline Dual<V> operator*(double b, Dual<V> a) { return a * b; }
+template <typename V>
+__host__ __device__ inline Dual<V> operator/(Dual<V> a, double b) {
+  const V c = V(b);
+  a.v /= c;
+  for (int i = 0; i < kND; ++i) a.d[i] /= c;
   return a;
 }
-__host__ __device__ inline D3 operator/(double b, const D3& a) { return D3(b) / a; }
-__host__ __device__ inline D3 operator-(const D3& a) {
-  D3 r(-a.v);
+template <typename V>
+__host__ __device__ inline Dual<V> operator/(double b, const Dual<V>& a) { return Dual<V>(b) / a; }
+template <typename V>
+__host__ __device__ inline Dual<V> operator-(const Dual<V>& a) {
+  Dual<V> r;
+  r.v = -a.v;
   for (int i = 0; i < kND; ++i) r.d[i] = -a.d[i];
   return r;
 }
 
-#define USP_D3_CMP(op)                                                                  \
-  __host__ __device__ inline bool operator op(const D3& a, const D3& b) { return a.v op b.v; } \
-  __host__ __device__ inline bool operator op(const D3& a, double b) { return a.v op b; }      \
-  __host__ __device__ inline bool operator op(double a, const D3& b) { return a op b.v; }
-USP_D3_CMP(<)
-USP_D3_CMP(>)
-USP_D3_CMP(<=)
-USP_D3_CMP(>=)
-USP_D3_CMP(==)
-USP_D3_CMP(!=)
-#undef USP_D3_CMP
+#define USP_DUAL_CMP(op)                                                                       \
+  template <typename V>                                                                        \
+  __host__ __device__ inline bool operator op(const Dual<V>& a, const Dual<V>& b) {            \
+    return a.v op b.v;                                                                         \
+  }                                                                                            \
+  template <typename V>                                                                        \
+  __host__ __device__ inline bool operator op(const Dual<V>& a, double b) { return a.v op b; } \
+  template <typename V>                                                                        \
+  __host__ __device__ inline bool operator op(double a, const Dual<V>& b) { return a op b.v; }
+USP_DUAL_CMP(<)
+USP_DUAL_CMP(>)
+USP_DUAL_CMP(<=)
+USP_DUAL_CMP(>=)
+USP_DUAL_CMP(==)
+USP_DUAL_CMP(!=)
+#undef USP_DUAL_CMP
 
 // f(a) with f'(a) = df
-__host__ __device__ inline D3 chain(const D3& a, double fv, double df) {
-  D3 r(fv);
+template <typename V>
+__host__ __device__ inline Dual<V> chain(const Dual<V>& a, V fv, V df) {
+  Dual<V> r;
+  r.v = fv;
   for (int i = 0; i < kND; ++i) r.d[i] = df * a.d[i];
   return r;
 }
 
-__device__ inline D3 sqrt(const D3& a) {
-  const double s = ::sqrt(a.v);
-  return chain(a, s, s > 0.0 ? 0.5 / s : 0.0);
+template <typename V>
+__device__ inline Dual<V> sqrt(const Dual<V>& a) {
+  const V s = vsqrt(a.v);
+  return chain(a, s, s > V(0) ? V(0.5) / s : V(0));
 }
-__device__ inline D3 log(const D3& a) { return chain(a, ::log(a.v), 1.0 / a.v); }
-__device__ inline D3 log1p(const D3& a) { return chain(a, ::log1p(a.v), 1.0 / (1.0 + a.v)); }
-__device__ inline D3 exp(const D3& a) {
-  const double e = ::exp(a.v);
+template <typename V>
+__device__ inline Dual<V> log(const Dual<V>& a) { return chain(a, vlog(a.v), V(1) / a.v); }
+template <typename V>
+__device__ inline Dual<V> log1p(const Dual<V>& a) {
+  return chain(a, vlog1p(a.v), V(1) / (V(1) + a.v));
+}
+template <typename V>
+__device__ inline Dual<V> exp(const Dual<V>& a) {
+  const V e = vexp(a.v);
   return chain(a, e, e);
 }
-__device__ inline D3 expm1(const D3& a) { return chain(a, ::expm1(a.v), ::exp(a.v)); }
-__device__ inline D3 sinh(const D3& a) { return chain(a, ::sinh(a.v), ::cosh(a.v)); }
-__device__ inline D3 cos(const D3& a) { return chain(a, ::cos(a.v), -::sin(a.v)); }
-__device__ inline D3 acos(const D3& a) {
-  const double den = ::sqrt(1.0 - a.v * a.v);
-  return chain(a, ::acos(a.v), den > 0.0 ? -1.0 / den : 0.0);
+template <typename V>
+__device__ inline Dual<V> expm1(const Dual<V>& a) { return chain(a, vexpm1(a.v), vexp(a.v)); }
+template <typename V>
+__device__ inline Dual<V> sinh(const Dual<V>& a) { return chain(a, vsinh(a.v), vcosh(a.v)); }
+template <typename V>
+__device__ inline Dual<V> cos(const Dual<V>& a) { return chain(a, vcos(a.v), -vsin(a.v)); }
+template <typename V>
+__device__ inline Dual<V> acos(const Dual<V>& a) {
+  const V den = vsqrt(V(1) - a.v * a.v);
+  return chain(a, vacos(a.v), den > V(0) ? V(-1) / den : V(0));
 }
-__device__ inline D3 cbrt(const D3& a) {
-  const double c = ::cbrt(a.v);
-  return chain(a, c, c != 0.0 ? c / (3.0 * a.v) : 0.0);
+template <typename V>
+__device__ inline Dual<V> cbrt(const Dual<V>& a) {
+  const V c = vcbrt(a.v);
+  return chain(a, c, c != V(0) ? c / (V(3) * a.v) : V(0));
 }
-__device__ inline D3 fabs(const D3& a) { return a.v < 0.0 ? -a : a; }
-__device__ inline D3 fmin(const D3& a, const D3& b) { return b.v < a.v ? b : a; }
-__device__ inline D3 fmax(const D3& a, const D3& b) { return b.v > a.v ? b : a; }
+template <typename V>
+__device__ inline Dual<V> fabs(const Dual<V>& a) { return a.v < V(0) ? -a : a; }
+template <typename V>
+__device__ inline Dual<V> fmin(const Dual<V>& a, const Dual<V>& b) { return b.v < a.v ? b : a; }
+template <typename V>
+__device__ inline Dual<V> fmax(const Dual<V>& a, const Dual<V>& b) { return b.v > a.v ? b : a; }
 // a^b with a > 0 (both carrying derivatives)
-__device__ inline D3 pow(const D3& a, const D3& b) {
-  const double p = ::pow(a.v, b.v);
-  D3 r(p);
-  const double la = ::log(a.v);
+template <typename V>
+__device__ inline Dual<V> pow(const Dual<V>& a, const Dual<V>& b) {
+  const V p = vpow(a.v, b.v);
+  Dual<V> r;
+  r.v = p;
+  const V la = vlog(a.v);
   for (int i = 0; i < kND; ++i) r.d[i] = p * (b.d[i] * la + b.v * a.d[i] / a.v);
   return r;
 }
-__device__ inline D3 pow(const D3& a, double b) {
-  const double p = ::pow(a.v, b);
-  return chain(a, p, b * ::pow(a.v, b - 1.0));
+template <typename V>
+__device__ inline Dual<V> pow(const Dual<V>& a, double b) {
+  const V p = vpow(a.v, V(b));
+  return chain(a, p, V(b) * vpow(a.v, V(b - 1.0)));
 }
-__device__ inline D3 pow(double a, const D3& b) {
-  const double p = ::pow(a, b.v);
-  return chain(b, p, p * ::log(a));
+template <typename V>
+__device__ inline Dual<V> pow(double a, const Dual<V>& b) {
+  const V p = vpow(V(a), b.v);
+  return chain(b, p, p * vlog(V(a)));
 }
-__device__ inline double value(const D3& a) { return a.v; }
+template <typename V>
+__device__ inline V value(const Dual<V>& a) { return a.v; }
 
 }  // namespace dual
 
 using dual::D3;
+using dual::F3;
 using dual::kND;
 using dual::value;
 __device__ inline double value(double a) { return a; }
@@ -154,7 +238,8 @@ __device__ inline float value(float a) { return a; }
 
 // A quantity held at its value in the gradient form: its derivative is
 // dropped (the identity in the plain forms).
-__device__ inline D3 held(const D3& a) { return D3(a.v); }
+template <typename V>
+__device__ inline dual::Dual<V> held(const dual::Dual<V>& a) { return dual::Dual<V>(a.v); }
 __device__ inline double held(double a) { return a; }
 __device__ inline float held(float a) { return a; }
 

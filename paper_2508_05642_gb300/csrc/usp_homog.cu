@@ -2158,10 +2158,9 @@ int usp_init_channel(usp_ctx** out, const usp_species* sp, const usp_config* cfg
                      const double* h_erot, const int32_t* h_lev, const uint32_t* h_pid) {
   if (!out || !sp || !cfg || !ch) return USP_EINVAL;
   if (cfg->method != USP_METHOD_USP_FPM && cfg->method != USP_METHOD_FPM) return USP_EINVAL;
-  if (cfg->method == USP_METHOD_FPM && cfg->precision == USP_FP64_TANGENT) return USP_ENOTSUP;
-  if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64 &&
-      cfg->precision != USP_FP64_TANGENT)
-    return USP_EINVAL;
+  const bool tangent = cfg->precision == USP_FP64_TANGENT || cfg->precision == USP_FP32_TANGENT;
+  if (cfg->method == USP_METHOD_FPM && tangent) return USP_ENOTSUP;
+  if (cfg->precision != USP_FP32 && cfg->precision != USP_FP64 && !tangent) return USP_EINVAL;
   if (!(sp->m > 0) || !(sp->d_ref > 0) || !(sp->T_ref > 0) || !(sp->c_alpha > 0) ||
       !(sp->theta_v > 0))
     return USP_EINVAL;
@@ -2484,7 +2483,8 @@ int usp_profiles(usp_ctx* c, double* out, int out_is_device) {
 
 int usp_backward(usp_ctx* c, const double* d_dL, double* grad3, int grad_is_device) {
   if (!c || !d_dL || !grad3) return USP_EINVAL;
-  if (c->kind != 1 || c->precision != USP_FP64_TANGENT) return USP_ENOTSUP;
+  if (c->kind != 1 || (c->precision != USP_FP64_TANGENT && c->precision != USP_FP32_TANGENT))
+    return USP_ENOTSUP;
   return ch_backward(c->ch, make_env(c), d_dL, grad3, grad_is_device);
 }
 

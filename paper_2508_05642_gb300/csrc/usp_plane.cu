@@ -1020,6 +1020,10 @@ __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<d
   stage_meta(c + W, &meta[1]);
   cp_async_commit();
   int slot = 0, buf = 0;
+  // event counts and flags per lane over all of the warp's cells, reduced
+  // once at the end
+  CollideTally tl = {0u, 0ull, 0ull, 0ull, 0ull};
+  unsigned long long nfb = 0;
   for (; c < ncell; c += W) {
     // cell c's data and cell c + W's place are in shared memory once every
     // lane's copies are done; the previous cell's readers are done too
@@ -1047,8 +1051,6 @@ __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<d
       for (int i = 0; i < 10; ++i) acc[i] = T(0);
       int accI = 0;
       int maxI = 0;
-      CollideTally tl = {0u, 0ull, 0ull, 0ull, 0ull};
-      unsigned nfb = 0;
       for (int i = lane; i < n; i += 32) {
         const long long j = off + i;
         T xv, yv, v0, v1, v2, en;
@@ -1101,28 +1103,32 @@ __global__ void __launch_bounds__(kBlk, 2) pl_collide(int ncell, const ChCellT<d
       }
       const double sv = (double)mine;
       const long long sI = wsum((long long)accI);
-      const unsigned long long fix = wsum(tl.nfix), fb = wsum((unsigned long long)nfb),
-                               ncl2 = wsum(tl.ncl), pb = wsum(tl.npb), nz = wsum(tl.nnz);
       const int mI = __reduce_max_sync(0xffffffffu, maxI);
-      const uint32_t fla = __reduce_or_sync(0xffffffffu, tl.fl);
       ChSumsT<double>& sm = sums[c];
       if (lane < 10) sm.v[lane] = sv;
       if (lane == 0) {
         sm.I = (unsigned long long)sI;
         sm.net = 0;
         sm.maxI = mI;
-        tally_or(tal, fla);
-        tally_add(tal, C_CHOL_FIX, fix);
-        tally_add(tal, C_INTERP_FALLBACK, fb);
-        tally_add(tal, C_TREL_CLAMP, ncl2);
-        tally_add(tal, C_PB_CLAMP, pb);
-        tally_add(tal, C_NU_ZERO, nz);
       }
     }
     slot = s1;
     buf ^= 1;
   }
   cp_async_wait_all();
+  {
+    const unsigned long long fix = wsum(tl.nfix), fb = wsum(nfb), ncl2 = wsum(tl.ncl),
+                             pb = wsum(tl.npb), nz = wsum(tl.nnz);
+    const uint32_t fla = __reduce_or_sync(0xffffffffu, tl.fl);
+    if (lane == 0) {
+      tally_or(tal, fla);
+      tally_add(tal, C_CHOL_FIX, fix);
+      tally_add(tal, C_INTERP_FALLBACK, fb);
+      tally_add(tal, C_TREL_CLAMP, ncl2);
+      tally_add(tal, C_PB_CLAMP, pb);
+      tally_add(tal, C_NU_ZERO, nz);
+    }
+  }
   tally_flush(tal, flags, counters);
 }
 
@@ -1433,17 +1439,23 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   if (prof) prof(env.owner, 1, 1);
   const int wb = h->grid_wc, tb = h->grid_tc;
   float* pend = env.precision == USP_FP32 ? h->pend : nullptr;
-  ch_moments<T, double><<<wb, kBlk, 0, s>>>(ncell, 32, h->off, h->af, cx, cy, cz, er, h->lv[b],
-                                            h->cells, env.sp, env.counters, pend, (T*)h->fT,
-                                            h->usable_c);
   const bool fpm = h->fpmrec != nullptr;
+  // the FP32 form of USP-FPM takes its moments and FP32 coefficients in one
+  // pass; the FP64 form and the plain FPM method in two
+  const bool fused = sizeof(T) == 4 && !fpm;
+  if (fused)
+    ch_moments_coeffs_f32<<<(ncell + 32 * kMW - 1) / (32 * kMW), 32 * kMW, 0, s>>>(
+        ncell, h->off, h->af, h->afv, (float)(h->Fnum / h->vol), h->g.dt, (const float*)cx,
+        (const float*)cy, (const float*)cz, (const float*)er, h->lv[b], h->cells, env.sp,
+        env.flags, env.counters, pend, (float*)h->fT, h->usable_c);
+  else
+    ch_moments<T, double><<<wb, kBlk, 0, s>>>(ncell, 32, h->off, h->af, cx, cy, cz, er, h->lv[b],
+                                              h->cells, env.sp, env.counters, pend, (T*)h->fT,
+                                              h->usable_c);
   if (fpm)
     ch_coeffs_fpm<<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->afv, h->g.dt, h->cells,
                                       h->fpmrec, env.sp, env.flags, env.counters);
-  else if (env.precision == USP_FP32)
-    ch_coeffs_f32<<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->afv, h->g.dt, h->cells, env.sp,
-                                      env.flags, env.counters);
-  else
+  else if (!fused)
     ch_coeffs<double><<<tb, kBlk, 0, s>>>(ncell, h->Fnum, h->vol, h->afv, h->g.dt, h->cells,
                                           env.sp, env.sp.omega, env.sp.Z_rot, env.flags,
                                           env.counters);
@@ -1471,10 +1483,12 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   CHK(cudaGetLastError());
   if (prof) prof(env.owner, 0, 0);
   if (prof) prof(env.owner, 1, 1);
-  ch_levelfix<double><<<wb, kBlk, 0, s>>>(ncell, 32, h->cells, h->sums, h->lv[b], h->dstep, env.sp,
-                                          env.k0, env.k1, env.flags, env.counters);
-  ch_update<double><<<tb, kBlk, 0, s>>>(ncell, h->cells, h->sums, h->dstep, env.sp, env.flags,
-                                        env.counters, pend);
+  if (pend)
+    ch_fix_update<true><<<wb, kBlk, 0, s>>>(ncell, h->cells, h->sums, h->lv[b], h->dstep, env.sp,
+                                             env.k0, env.k1, env.flags, env.counters, pend);
+  else
+    ch_fix_update<false><<<wb, kBlk, 0, s>>>(ncell, h->cells, h->sums, h->lv[b], h->dstep, env.sp,
+                                              env.k0, env.k1, env.flags, env.counters, nullptr);
   CHK(cudaGetLastError());
   if (h->sampling) {
     pl_sample<T><<<h->grid_p, kBlk, 0, s>>>(h->cnt, ncell, h->keycell, h->cells, cx, cy, cz, er,
@@ -1493,7 +1507,8 @@ int pl_kernels_per_step(const PlaneCtx* h) {
     params = 0;
     for (int L = 1; L <= h->levels; ++L) params += h->nblk_lv[L] > 0 ? 1 : 0;
   }
-  return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 2 + 2 + params + 1 + 2 +
+  const int cellpass = h->es == sizeof(float) && !h->fpmrec ? 1 : 2;
+  return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 2 + cellpass + params + 1 + 1 +
          (h->sampling ? 1 : 0);
 }
 
@@ -1651,7 +1666,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   h->acc = (double*)A(acc_bytes);
   h->macc = (double*)A(sizeof(double) * 21 * ncell);
   h->mout = (double*)A(sizeof(double) * USP_NMOM * ncell);
-  h->dstep = (long long*)A(sizeof(long long));
+  h->dstep = (long long*)A(2 * sizeof(long long));   // step, finished blocks
   bool ok = h->keycell && h->bh && h->tot && h->face_off && h->off && h->af && h->afv && h->cnt &&
             (env.sp.method != 1 || h->fpmrec) &&
             (G.levels < 2 || (h->htree.l1_first && h->htree.l2_first && h->htree.l2_ref &&
@@ -1746,6 +1761,7 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
   }
   cok = cok && cudaMemsetAsync(h->acc, 0, acc_bytes, s) == cudaSuccess;
   cok = cok && cudaMemcpyAsync(h->dstep, &dstep0, sizeof(long long), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  cok = cok && cudaMemsetAsync(h->dstep + 1, 0, sizeof(long long), s) == cudaSuccess;
   cok = cok && cudaStreamSynchronize(s) == cudaSuccess;
   if (tmp) env.release(env.owner, tmp);
   if (!cok) {

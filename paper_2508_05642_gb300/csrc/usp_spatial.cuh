@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "usp_device.cuh"
 #include "usp_dual.cuh"
@@ -61,7 +62,8 @@ __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
-__device__ __forceinline__ D3 wsum(D3 v) {
+template <typename V>
+__device__ __forceinline__ dual::Dual<V> wsum(dual::Dual<V> v) {
   v.v = wsum(v.v);
   for (int k = 0; k < kND; ++k) v.d[k] = wsum(v.d[k]);
   return v;
@@ -424,6 +426,141 @@ __global__ void ch_update(int ny, ChCellT<S>* __restrict__ cells,
   if (blockIdx.x == 0 && threadIdx.x == 0) *dstep += 1;
 }
 
+// ch_levelfix and ch_update in one pass (FP64 cell records): the warp makes
+// the +-1 corrections of its 32 cells one after the other, lane k keeping
+// cell k's net change, then every lane computes its cell's rescale factors.
+// F32: the factors in FP32 arithmetic (the FP32 state's own precision) from
+// the FP64 sums.  dstep[0] is the step counter, dstep[1] counts finished
+// blocks: the last block to finish advances the step, after every block has
+// read it.
+template <bool F32>
+__global__ void ch_fix_update(int ncell, ChCellT<double>* __restrict__ cells,
+                              const ChSumsT<double>* __restrict__ sums, int* __restrict__ lev,
+                              long long* dstep, Species sp, uint32_t k0, uint32_t k1,
+                              uint32_t* flags, unsigned long long* counters,
+                              float* __restrict__ pend) {
+  __shared__ BlockTally tal;
+  tally_init(tal);
+  const int lane = threadIdx.x & 31;
+  const uint32_t step = (uint32_t)dstep[0];
+  const double Rth = gasR(sp) * sp.theta_v;
+  for (long long c0 = (long long)warp_global() * 32; c0 < ncell;
+       c0 += (long long)warps_total() * 32) {
+    const int ng = (int)(ncell - c0 < 32 ? ncell - c0 : 32);
+    // I_Delta of Sec. 4.C for cell c0 + lane (FP64, one cell per lane)
+    long long myId = 0, mynet = 0;
+    if (lane < ng) {
+      const long long c = c0 + lane;
+      const ChCellT<double>& cs = cells[c];
+      if (cs.active) {
+        const U4 w = philox4x32_10((uint32_t)c, step, CTAG_IDELTA, 0u, k0, k1);
+        const double u = uniform_open<double>(w.x);
+        myId = (long long)floor((double)cs.N * cs.e_vib_tgt / Rth - (double)(long long)sums[c].I +
+                                u);
+      }
+    }
+    for (int g = 0; g < ng; ++g) {
+      const long long Id = __shfl_sync(0xffffffffu, myId, g);
+      const long long c = c0 + g;
+      const ChCellT<double>& cs = cells[c];
+      if (!cs.active) continue;
+      const long long N = cs.N;
+      long long remaining = Id, draws = 0, net = 0;
+      const long long cap = 64 * N;
+      int* lv = lev + cs.off;
+      while (remaining != 0 && draws < cap) {
+        const long long j = draws + lane;
+        const U4 w = philox4x32_10((uint32_t)c, step, CTAG_PICK, (uint32_t)(j >> 2), k0, k1);
+        const uint32_t word = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
+        const long long k = (long long)(((unsigned long long)word * (unsigned long long)N) >> 32);
+        const bool valid = j < cap;
+        bool accept;
+        if (remaining > 0) {
+          accept = valid;
+        } else {
+          const int cur = valid ? __ldcg(&lv[k]) : 0;
+          const unsigned grp = __match_any_sync(0xffffffffu, valid ? k : -1ll);
+          accept = valid && __popc(grp & lane_lt()) < cur;
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, accept);
+        const long long need = remaining > 0 ? remaining : -remaining;
+        const int nacc = __popc(am);
+        const int take = (int)(nacc < need ? nacc : need);
+        const bool eff = accept && __popc(am & lane_lt()) < take;
+        __syncwarp();
+        if (eff) atomicAdd(&lv[k], remaining > 0 ? 1 : -1);
+        __syncwarp();
+        long long used = 32;
+        if (take == need && take > 0) {
+          unsigned m = am;
+          for (int i = 1; i < take; ++i) m &= m - 1;
+          used = __ffs((int)m);
+        }
+        if (draws + used > cap) used = cap - draws;
+        draws += used;
+        if (remaining > 0) { remaining -= take; net += take; }
+        else { remaining += take; net -= take; }
+      }
+      if (lane == g) mynet = net;
+      if (lane == 0) {
+        if (remaining != 0) tally_or(tal, (uint32_t)F_VIB_LOOP_CAP);
+        tally_add(tal, C_VIB_DRAWS, (unsigned long long)draws);
+      }
+    }
+    // the rescale factors of Sec. 4.C for cell c0 + lane
+    if (lane >= ng) continue;
+    const long long c = c0 + lane;
+    ChCellT<double>& cs = cells[c];
+    if (!cs.active) continue;
+    const ChSumsT<double>& sm = sums[c];
+    using V = std::conditional_t<F32, float, double>;
+    const V R = (V)gasR(sp), RthV = (V)Rth;
+    const V invN = V(1) / (V)cs.N;
+    const V sumI = (V)((long long)sm.I + mynet);
+    const V er_star = (V)sm.v[9] * invN;
+    const V r = er_star > V(0) ? (V)cs.e_rot_tgt / er_star : V(1);
+    const V e_rot_new = r * er_star;
+    const V e_vib_new = RthV * sumI * invN;
+    const V m0 = (V)sm.v[0] * invN, m1 = (V)sm.v[1] * invN, m2 = (V)sm.v[2] * invN;
+    const V etr_star = V(0.5) * ((V)sm.v[3] * invN - m0 * m0 + (V)sm.v[4] * invN - m1 * m1 +
+                                 (V)sm.v[5] * invN - m2 * m2);
+    const V e_tr_n = V(0.5) * ((V)cs.Pi[0] + (V)cs.Pi[1] + (V)cs.Pi[2]);
+    const V rad = (e_tr_n + R * (V)cs.Trot + RthV * (V)cs.ebar - e_rot_new - e_vib_new) / etr_star;
+    const V U0 = (V)cs.U[0], U1 = (V)cs.U[1], U2 = (V)cs.U[2];
+    const V Us[3] = {U0 + m0, U1 + m1, U2 + m2};
+    V Un[3] = {U0, U1, U2}, sc = V(1);
+    if (!(etr_star > V(0)) || !(rad > V(0))) {
+      tally_or(tal, (uint32_t)F_NEG_RADICAND);
+      tally_add(tal, C_NEG_RADICAND, 1ull);
+      for (int i = 0; i < 3; ++i) Un[i] = Us[i];
+    } else {
+      sc = sqrt(rad);
+    }
+    for (int i = 0; i < 3; ++i) { cs.Un[i] = Un[i]; cs.Us[i] = Us[i]; }
+    cs.s = sc;
+    cs.r = r;
+    cs.maxI = sm.maxI + 1;
+    if (pend) {   // FP32 copy for the next move of an FP32 state
+      float* pc = pend + (size_t)c * 8;
+      for (int i = 0; i < 3; ++i) {
+        pc[i] = (float)Un[i];
+        pc[3 + i] = (float)Us[i];
+      }
+      pc[6] = (float)sc;
+      pc[7] = (float)r;
+    }
+  }
+  tally_flush(tal, flags, counters);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(reinterpret_cast<unsigned long long*>(dstep + 1), 1ull) ==
+        (unsigned long long)gridDim.x - 1) {
+      dstep[1] = 0;
+      dstep[0] += 1;
+    }
+  }
+}
+
 
 // ---------------------------------------------------------------------------
 // per-cell moments and coefficients
@@ -589,29 +726,132 @@ __global__ void ch_coeffs(int ny, double F_num, double vol, const double* __rest
   tally_flush(tal, flags, counters);
 }
 
-// ch_coeffs with the coefficients evaluated in FP32 (cell_coeffs_f32): the
-// FP32-state form of the 2D path
-__global__ void ch_coeffs_f32(int ny, double F_num, double vol, const double* __restrict__ af,
-                              double dt, ChCellT<double>* __restrict__ cells, Species sp,
-                              uint32_t* flags, unsigned long long* counters) {
+// ---------------------------------------------------------------------------
+// FP32 state, USP-FPM: the moments of ch_moments and the coefficients of
+// ch_coeffs evaluated in FP32 (cell_coeffs_f32) in one pass, 32 consecutive
+// cells per warp.  The warp stages
+// its cells' particles in shared memory in chunks of kMC (coalesced loads);
+// lane k then sums cell k's particles from there, shifted by the cell's
+// first particle (sums of d = c - c_first and of d d^T, so that the central
+// second moments need no second pass over the particles), and evaluates
+// cell k's fields and coefficients in FP32 from those sums.  Each lane keeps
+// its cell's sums in registers, so a cell costs no warp-wide reduction.
+// ---------------------------------------------------------------------------
+constexpr int kMC = 512;   // particles per warp chunk
+constexpr int kMW = 4;     // warps per block
+
+__global__ void __launch_bounds__(kMW * 32)
+ch_moments_coeffs_f32(int ncell, const long long* __restrict__ off,
+                      const double* __restrict__ af, const double* __restrict__ afv, float nv,
+                      double dt,
+                      const float* __restrict__ cx, const float* __restrict__ cy,
+                      const float* __restrict__ cz, const float* __restrict__ er,
+                      const int* __restrict__ lev, ChCellT<double>* __restrict__ cells,
+                      Species sp, uint32_t* flags, unsigned long long* counters,
+                      float* __restrict__ pend, float* __restrict__ fT,
+                      int* __restrict__ usable_c) {
+  __shared__ float sv[kMW][4][kMC];
+  __shared__ int sl[kMW][kMC];
   __shared__ BlockTally tal;
   tally_init(tal);
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ny; c += gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float R = (float)gasR(sp), th = (float)sp.theta_v;
+  float* S0 = sv[wid][0];
+  float* S1 = sv[wid][1];
+  float* S2 = sv[wid][2];
+  float* S3 = sv[wid][3];
+  int* SL = sl[wid];
+  const long long stride = (long long)gridDim.x * kMW * 32;
+  for (long long c0 = ((long long)blockIdx.x * kMW + wid) * 32; c0 < ncell; c0 += stride) {
+    const int ng = (int)(ncell - c0 < 32 ? ncell - c0 : 32);
+    const long long b = lane < ng ? off[c0 + lane] : 0;
+    const long long e = lane < ng ? off[c0 + lane + 1] : 0;
+    const long long P0 = __shfl_sync(0xffffffffu, b, 0);
+    const long long P1 = __shfl_sync(0xffffffffu, e, ng - 1);
+    float r0 = 0.0f, r1 = 0.0f, r2 = 0.0f;   // the cell's first particle
+    float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, se = 0.0f;
+    float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f, q3 = 0.0f, q4 = 0.0f, q5 = 0.0f;
+    int sI = 0;
+    for (long long q = P0; q < P1; q += kMC) {
+      const int len = (int)(P1 - q < kMC ? P1 - q : kMC);
+      __syncwarp();   // the previous chunk's readers are done
+#pragma unroll 4
+      for (int i = lane; i < len; i += 32) {
+        S0[i] = cx[q + i]; S1[i] = cy[q + i]; S2[i] = cz[q + i]; S3[i] = er[q + i];
+        SL[i] = lev[q + i];
+      }
+      __syncwarp();
+      const long long j0 = b > q ? b : q, j1 = e < q + len ? e : q + len;
+      if (j0 < j1) {
+        const int i0 = (int)(j0 - q), i1 = (int)(j1 - q);
+        if (j0 == b) { r0 = S0[i0]; r1 = S1[i0]; r2 = S2[i0]; }
+        for (int i = i0; i < i1; ++i) {
+          const float d0 = S0[i] - r0, d1 = S1[i] - r1, d2 = S2[i] - r2;
+          s0 += d0; s1 += d1; s2 += d2;
+          q0 = fmaf(d0, d0, q0); q1 = fmaf(d1, d1, q1); q2 = fmaf(d2, d2, q2);
+          q3 = fmaf(d0, d1, q3); q4 = fmaf(d0, d2, q4); q5 = fmaf(d1, d2, q5);
+          se += S3[i];
+          sI += SL[i];
+        }
+      }
+    }
+    if (lane >= ng) continue;
+    const long long c = c0 + lane;
+    const long long N = e - b;
+    const float inv = N > 0 ? 1.0f / (float)N : 0.0f;
+    const float m0 = s0 * inv, m1 = s1 * inv, m2 = s2 * inv;
+    const float U0 = r0 + m0, U1 = r1 + m1, U2 = r2 + m2;
+    if (pend) {   // identity pending rescale
+      float* pc = pend + (size_t)c * 8;
+      pc[0] = pc[1] = pc[2] = pc[3] = pc[4] = pc[5] = 0.0f;
+      pc[6] = pc[7] = 1.0f;
+    }
     ChCellT<double>& cs = cells[c];
-    if (!cs.active) continue;
-    const double v = af ? af[c] * vol : vol;
-    if (!(v > 0.0)) {
+    cs.off = b;
+    cs.N = N;
+    cs.active = N >= 2;
+    // a reconstruction neighbour (Sec. 3.B): two or more particles, not cut
+    cs.usable = N >= 2 && (!af || af[c] >= 1.0);
+    if (usable_c) usable_c[c] = cs.usable;
+    cs.U[0] = U0; cs.U[1] = U1; cs.U[2] = U2;
+    for (int i = 0; i < 3; ++i) { cs.Un[i] = 0.0; cs.Us[i] = 0.0; }
+    cs.s = 1.0;
+    cs.r = 1.0;
+    if (!cs.active) {
+      tally_add(tal, C_SKIPPED_CELLS, 1ull);
+      continue;
+    }
+    float P[6];
+    P[0] = fmaf(q0, inv, -m0 * m0); P[1] = fmaf(q1, inv, -m1 * m1); P[2] = fmaf(q2, inv, -m2 * m2);
+    P[3] = fmaf(q3, inv, -m0 * m1); P[4] = fmaf(q4, inv, -m0 * m2); P[5] = fmaf(q5, inv, -m1 * m2);
+    const float Ttr = (P[0] + P[1] + P[2]) / (3.0f * R);
+    const float Trot = se * inv / R;
+    const float ebar = (float)sI * inv;
+    const float Tvib = ebar > 0.0f ? th / log1pf(1.0f / ebar) : 0.0f;
+    for (int i = 0; i < 6; ++i) cs.Pi[i] = P[i];
+    cs.Ttr = Ttr;
+    cs.Trot = Trot;
+    cs.ebar = ebar;
+    cs.Tvib = Tvib;
+    float* o = fT + (size_t)c * kNF;   // the 13 fields for the stencils
+    o[0] = U0; o[1] = U1; o[2] = U2;
+    o[3] = Ttr; o[4] = Trot; o[5] = Tvib;
+    for (int i = 0; i < 6; ++i) o[6 + i] = P[i];
+    // coefficients: the number density from the fluid volume
+    // (afv: the cell's volume over the nominal cell volume; nv = F_num over it)
+    const float a = afv ? (float)afv[c] : 1.0f;
+    if (!(a > 0.0f)) {
       cs.active = 0;
       continue;
     }
-    cs.n = (double)cs.N * F_num / v;
-    const CellCoeffsF k =
-        cell_coeffs_f32(sp, cs.n, dt, (float)cs.Ttr, (float)cs.Trot, (float)cs.Tvib);
+    const float n = (float)N * nv / a;
+    const CellCoeffsF k = cell_coeffs_f32(sp, (double)n, dt, Ttr, Trot, Tvib);
     if (!k.ok) {
       tally_or(tal, (uint32_t)F_A_NONPOS);
       cs.active = 0;
       continue;
     }
+    cs.n = n;
     cs.alpha = k.alpha; cs.nu_ref = k.nu_ref; cs.B = k.B; cs.mu_p = k.mu_p; cs.Pr = k.Pr;
     cs.gtr = k.g_tr_rot; cs.gtv = k.g_tr_vib; cs.grv = k.g_rot_vib;
     cs.e_rot_tgt = k.e_rot_tgt;

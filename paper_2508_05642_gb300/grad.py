@@ -1,10 +1,12 @@
 """Pathwise gradients of the channel's time-averaged profiles with respect to
 (Z_rot, omega, T_wall), behind a torch.autograd.Function.
 
-The library's USP_FP64_TANGENT form runs every kernel of the channel step on
-FP64 numbers carrying their derivatives with respect to the three parameters,
-under the same random numbers as the plain FP64 run; discrete outcomes and
-particle positions are held (usp.h, usp_backward).  The profiles, their
+The library's tangent forms run every kernel of the channel step on numbers
+carrying their derivatives with respect to the three parameters, under the
+same random numbers as the plain run of the same precision -- FP64 throughout
+(USP_FP64_TANGENT), or FP32 particle values and derivatives with FP64 cell
+quantities and accumulation (USP_FP32_TANGENT); discrete outcomes, wall-event
+times and particle positions are held (usp.h, usp_backward).  The profiles, their
 derivatives and the contraction of those with an objective's gradient are
 formed on the device (usp_profiles, usp_backward); this module only marshals
 tensors and runs the steps, checkpointing the context (usp_save) every
@@ -28,7 +30,10 @@ class ChannelGradient:
 
     def __init__(self, workload, dt: float, warmup: int, sample: int, seed: int = 1,
                  checkpoint_every: int = 100, keep_checkpoints: bool = False,
-                 batches: int = 1):
+                 batches: int = 1, precision: int = usp.USP_FP64_TANGENT):
+        if precision not in usp.TANGENT_FORMS:
+            raise ValueError("precision must be USP_FP64_TANGENT or USP_FP32_TANGENT")
+        self.precision = precision
         self.w = workload
         self.dt = float(dt)
         self.warmup, self.sample = int(warmup), int(sample)
@@ -50,7 +55,7 @@ class ChannelGradient:
         ch["T_wall"] = float(theta[2])
         p = self.w.particles
         return usp.usp_init_channel(sp, ch, self.dt, self.w.y, p.cx, p.cy, p.cz, p.erot, p.lev,
-                                    precision=usp.USP_FP64_TANGENT, seed=self.seed)
+                                    precision=self.precision, seed=self.seed)
 
     def _advance(self, ctx, start: int):
         """Steps start .. warmup + sample, sampling on from step warmup, a

@@ -16,7 +16,8 @@ import numpy as np
 from . import build as _build
 
 USP_OK, USP_EINVAL, USP_ENOMEM, USP_ECUDA, USP_EDEVICE, USP_ENOTSUP = 0, -1, -2, -3, -4, -5
-USP_FP64, USP_FP32, USP_FP64_TANGENT = 0, 1, 2
+USP_FP64, USP_FP32, USP_FP64_TANGENT, USP_FP32_TANGENT = 0, 1, 2, 3
+TANGENT_FORMS = (USP_FP64_TANGENT, USP_FP32_TANGENT)
 USP_NMOM = 22
 USP_NCOUNTERS = 11
 
@@ -298,10 +299,10 @@ def usp_channel_sample(ctx: Context, on: bool = True):
 
 def usp_channel_read(ctx: Context, reset: bool = False, blocks: int = None) -> np.ndarray:
     """ny * 12 + 2 doubles: per-cell time-average sums, step count, wall
-    momentum (four such blocks in the USP_FP64_TANGENT form: sums, then their
+    momentum (four such blocks in the tangent forms: sums, then their
     derivatives with respect to Z_rot, omega, T_wall)."""
     if blocks is None:
-        blocks = 4 if ctx.precision == USP_FP64_TANGENT else 1
+        blocks = 4 if ctx.precision in TANGENT_FORMS else 1
     out = np.zeros((ctx.n_cells * 12 + 2) * blocks)
     _check(lib().usp_channel_read(ctx.h, _p(out, C.c_double), 1 if reset else 0),
            "usp_channel_read")
@@ -414,7 +415,7 @@ def usp_sample(ctx: Context, on: bool = True):
 def usp_sample_read(ctx: Context, reset: bool = False) -> np.ndarray:
     """Per-cell time-average sums of a channel or plane context (n_cells * 12
     + 2 doubles; a plane context appends USP_NSURF x 4 cylinder surface sums)."""
-    blocks = 4 if ctx.precision == USP_FP64_TANGENT else 1
+    blocks = 4 if ctx.precision in TANGENT_FORMS else 1
     extra = 4 * USP_NSURF if ctx.kind == 2 else 0
     out = np.zeros((ctx.n_cells * 12 + 2) * blocks + extra)
     _check(lib().usp_sample_read(ctx.h, _p(out, C.c_double), 1 if reset else 0),
@@ -423,10 +424,10 @@ def usp_sample_read(ctx: Context, reset: bool = False) -> np.ndarray:
 
 
 def usp_profiles(ctx: Context, out=None, out_is_device=False):
-    """Time-averaged channel profiles (USP_NPROF x ny; in the USP_FP64_TANGENT
+    """Time-averaged channel profiles (USP_NPROF x ny; in the tangent
     form 4 x USP_NPROF x ny: values, then derivatives w.r.t. Z_rot, omega,
     T_wall).  Host numpy unless a device pointer (int) is given."""
-    blocks = 4 if ctx.precision == USP_FP64_TANGENT else 1
+    blocks = 4 if ctx.precision in TANGENT_FORMS else 1
     if out_is_device:
         _check(lib().usp_profiles(ctx.h, C.c_void_p(out), 1), "usp_profiles")
         return None

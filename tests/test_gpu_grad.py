@@ -217,3 +217,54 @@ def test_checkpoint_resume_reproduces_the_run(long_run):
         for (pa, ja), (pb, jb) in zip(ref, got):
             assert np.array_equal(pa, pb) and np.array_equal(ja, jb)
         q.release()
+
+
+# ---------------------------------------------------------------------------
+# the FP32 gradient form (FP32 particle values and derivatives, FP64 cell
+# quantities and accumulation)
+# ---------------------------------------------------------------------------
+def test_fp32_tangent_values_follow_the_fp32_form():
+    """Over the first steps the FP32 gradient form's values are the FP32
+    form's (the same float operations carry the values; the derivative slots
+    ride along): profiles after 5 + 5 steps within 1e-5 relative."""
+    from paper_2508_05642_gb300 import usp
+    w = _workload()
+    dt = _dt(w)
+    r = G.ChannelGradient(w, dt, 5, 5, precision=usp.USP_FP32_TANGENT)
+    prof = r.run(_theta(w))
+    r.release()
+    p = w.particles
+    ctx = usp.usp_init_channel(w.species, w.channel, dt, w.y, p.cx, p.cy, p.cz, p.erot, p.lev,
+                               precision=usp.USP_FP32, seed=1)
+    usp.usp_step(ctx, 5)
+    usp.usp_channel_sample(ctx, True)
+    usp.usp_step(ctx, 5)
+    ref = usp.usp_profiles(ctx)
+    ctx.destroy()
+    for f in FIELDS:
+        np.testing.assert_allclose(prof[f], ref[f], rtol=1e-5, atol=1e-5 * np.abs(ref[f]).max())
+
+
+def test_fp32_tangent_long_run_gradient_agrees_with_oracle_differences(long_run):
+    """The FP32 gradient form over the 2,000 steps (its own realization: FP32
+    and FP64 runs of the channel part ways within about 100 steps, and the
+    Z_rot and omega derivatives of single cells are dominated by sampling
+    noise at this size, so entries are not compared one by one): batch means
+    of the objective's gradient within four combined standard errors of the
+    oracle's frozen-discrete central differences, omega and T_wall resolved
+    to 10 %."""
+    from paper_2508_05642_gb300 import usp
+    w, dt, th, base, fd, _ = long_run
+    r = G.ChannelGradient(w, dt, WARM_B, SAMPLE_B, checkpoint_every=EVERY, batches=BATCHES,
+                          precision=usp.USP_FP32_TANGENT)
+    r.run(th)
+    res = r.batch_results()
+    r.release()
+    wts = _weights(base[0].shape[1], base[0].shape[0])
+    g32 = np.array([np.einsum("fc,fck->k", wts, J) for _, J in res])
+    orc = np.array([np.einsum("fc,fck->k", wts, d) for d in fd])
+    m32, mo = g32.mean(axis=0), orc.mean(axis=0)
+    s32 = g32.std(axis=0, ddof=1) / np.sqrt(BATCHES)
+    so = orc.std(axis=0, ddof=1) / np.sqrt(BATCHES)
+    assert np.all(np.abs(m32 - mo) <= 4 * np.sqrt(s32 ** 2 + so ** 2)), (m32, mo, s32, so)
+    assert np.all(s32[1:] < 0.1 * np.abs(m32[1:])), (m32, s32)

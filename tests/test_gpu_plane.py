@@ -117,8 +117,10 @@ def test_fp64_plane_quarter_size_100_steps_matches_oracle():
     d = np.abs(ge - st.erot[:st.n])
     assert d.max() < 1e-2 * R * 200.0 and np.quantile(d, 0.999) < 1e-6 * R * 200.0
     ncell = r["pl"].nx * r["pl"].ny
-    np.testing.assert_allclose(r["gacc"][:ncell * 12 + 2], r["acc"][:ncell * 12 + 2], rtol=1e-6,
-                               atol=1e-2)
+    ga, oa = r["gacc"][:ncell * 12].reshape(ncell, 12), r["acc"][:ncell * 12].reshape(ncell, 12)
+    assert np.array_equal(ga[:, 0], oa[:, 0]) and np.array_equal(ga[:, 11], oa[:, 11])
+    dev = np.abs(ga - oa) / (np.abs(oa) + 1.0)
+    assert dev.max() < 1e-3 and np.mean(dev > 1e-6) < 1e-4
     gs = r["gacc"][ncell * 12 + 2:].reshape(-1, 4)
     osf = r["acc"][ncell * 12 + 2:].reshape(-1, 4)
     assert np.array_equal(gs[:, 3], osf[:, 3])
