@@ -66,6 +66,22 @@ struct PlGeom {
   int bcbits;         // 2 bits per side (USP_BC_*): left, right, bottom, top
 };
 
+// The geometry's coordinates in the working precision, converted once on
+// the host (an FP32 state would otherwise convert them per particle on the
+// narrow FP64 pipe); for T = double the same values as PlGeom's.
+template <typename T>
+struct PlGeomT {
+  T x0, x1, y0, y1, dx, dy, cxc, cyc, cr, dt;
+  T RTw, Tw, theta, Rth;   // R T_wall, T_wall, Theta_v, R Theta_v
+  T idx, idy;              // 1 / dx, 1 / dy
+};
+template <typename T>
+PlGeomT<T> geom_t(const PlGeom& g, const Species& sp) {
+  return {(T)g.x0, (T)g.x1, (T)g.y0, (T)g.y1, (T)g.dx, (T)g.dy, (T)g.cxc, (T)g.cyc, (T)g.cr,
+          (T)g.dt, (T)(sp.R * g.Tw), (T)g.Tw, (T)sp.theta_v, (T)(sp.R * sp.theta_v),
+          (T)(1.0 / g.dx), (T)(1.0 / g.dy)};
+}
+
 // Refined grid (levels 2, 3), in device memory: per level-1 cell its first
 // cell, per level-2 child its first cell (-1: the level-1 cell is not split)
 // and whether it is split again; per cell its level and integer coordinates
@@ -115,18 +131,18 @@ __device__ __forceinline__ int grid_threads() { return gridDim.x * blockDim.x; }
 // (round-to-nearest operations: the FP64 form places points exactly as the
 // plain definition does)
 template <typename T, bool AMR>
-__device__ __forceinline__ int plane_cell(const PlGeom& g, const PlTree* __restrict__ tr, T x,
-                                          T y) {
-  int i = (int)floor((x - (T)g.x0) / (T)g.dx);
-  int j = (int)floor((y - (T)g.y0) / (T)g.dy);
+__device__ __forceinline__ int plane_cell(const PlGeom& g, const PlGeomT<T>& gt,
+                                          const PlTree* __restrict__ tr, T x, T y) {
+  int i = (int)floor((x - gt.x0) / gt.dx);
+  int j = (int)floor((y - gt.y0) / gt.dy);
   i = i < 0 ? 0 : (i >= g.nx ? g.nx - 1 : i);
   j = j < 0 ? 0 : (j >= g.ny ? g.ny - 1 : j);
   const int c = j * g.nx + i;
   if (!AMR) return c;
   const int first = tr->l2_first[4 * c];
   if (first < 0) return tr->l1_first[c];
-  const T ux = rn_div(rn_sub(x, rn_add((T)g.x0, rn_mul((T)i, (T)g.dx))), rn_mul(T(0.5), (T)g.dx));
-  const T uy = rn_div(rn_sub(y, rn_add((T)g.y0, rn_mul((T)j, (T)g.dy))), rn_mul(T(0.5), (T)g.dy));
+  const T ux = rn_div(rn_sub(x, rn_add(gt.x0, rn_mul((T)i, gt.dx))), rn_mul(T(0.5), gt.dx));
+  const T uy = rn_div(rn_sub(y, rn_add(gt.y0, rn_mul((T)j, gt.dy))), rn_mul(T(0.5), gt.dy));
   const int ci = ux >= T(1) ? 1 : 0, cj = uy >= T(1) ? 1 : 0;
   const int k = 2 * cj + ci;
   const int l = tr->l2_first[4 * c + k];
@@ -139,28 +155,29 @@ __device__ __forceinline__ int plane_cell(const PlGeom& g, const PlTree* __restr
 // normal speed, Maxwellian in-plane tangential and z components,
 // exponential eps_rot, geometric level.  Draws (pid, step, 2, hit) and
 // (pid, step, 3, hit).
+// (The arithmetic is in the working precision T: the FP32 state's wall
+// events and inflow stay off the FP64 pipe.)
 template <typename T>
-__device__ void plane_emit(const Species& sp, double Tw, double nx, double ny, uint32_t pid,
-                           uint32_t step, int hit, uint32_t k0, uint32_t k1, T& vx, T& vy, T& vz,
-                           T& e, int& l) {
-  const double R = gasR(sp);
+__device__ void plane_emit(const PlGeomT<T>& gt, T nx, T ny, uint32_t pid, uint32_t step, int hit,
+                           uint32_t k0, uint32_t k1, T& vx, T& vy, T& vz, T& e, int& l) {
+  const T RTw = gt.RTw;
   const U4 w = philox4x32_10(pid, step, PTAG_WALL_A, (uint32_t)hit, k0, k1);
   const U4 v = philox4x32_10(pid, step, PTAG_WALL_B, (uint32_t)hit, k0, k1);
-  const double u0 = (double)uniform_open<T>(w.x);
-  const double u1 = (double)uniform_open<T>(w.y);
-  const double u2 = (double)uniform_open<T>(w.z);
-  const double u3 = (double)uniform_open<T>(w.w);
-  const double u4 = (double)uniform_open<T>(v.x);
-  const double vn = sqrt(-2.0 * R * Tw * log(u0));
-  double g1, g2;
+  const T u0 = uniform_open<T>(w.x);
+  const T u1 = uniform_open<T>(w.y);
+  const T u2 = uniform_open<T>(w.z);
+  const T u3 = uniform_open<T>(w.w);
+  const T u4 = uniform_open<T>(v.x);
+  const T vn = sqrt(T(-2) * RTw * log(u0));
+  T g1, g2;
   box_muller(u1, u2, g1, g2);
-  const double st = sqrt(R * Tw);
-  const double tx = -ny, ty = nx;
-  vx = (T)(vn * nx + st * g1 * tx);
-  vy = (T)(vn * ny + st * g1 * ty);
-  vz = (T)(st * g2);
-  e = (T)(-R * Tw * log(u3));
-  l = (int)floor(-log(u4) * Tw / sp.theta_v);
+  const T st = sqrt(RTw);
+  const T tx = -ny, ty = nx;
+  vx = vn * nx + st * g1 * tx;
+  vy = vn * ny + st * g1 * ty;
+  vz = st * g2;
+  e = -RTw * log(u3);
+  l = (int)floor(-log(u4) * gt.Tw / gt.theta);
 }
 
 // Flight over t_left with events, earliest first: cylinder (diffuse; a
@@ -170,17 +187,17 @@ __device__ void plane_emit(const Species& sp, double Tw, double nx, double ny, u
 // continues for the rest of the time.  Returns false when the particle left
 // through an open side.  hits counts the events met (at most 16).
 template <typename T>
-__device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint32_t step,
+__device__ bool plane_fly(const PlGeom& g, const PlGeomT<T>& gt, uint32_t pid, uint32_t step,
                           uint32_t k0, uint32_t k1, T t_left, T& x, T& y, T& vx, T& vy, T& vz,
                           T& e, int& l, int& hits, uint32_t& fl, double* surf) {
   for (;;) {
     int ev = -1;
     T te = t_left;
-    if (g.cr > 0.0) {
-      const T dx = x - (T)g.cxc, dy = y - (T)g.cyc;
+    if (gt.cr > T(0)) {
+      const T dx = x - gt.cxc, dy = y - gt.cyc;
       const T a = vx * vx + vy * vy;
       const T b = dx * vx + dy * vy;
-      const T c = dx * dx + dy * dy - (T)g.cr * (T)g.cr;
+      const T c = dx * dx + dy * dy - gt.cr * gt.cr;
       if (c > T(0) && b < T(0) && a > T(0)) {
         const T disc = b * b - a * c;
         if (disc >= T(0)) {
@@ -195,19 +212,19 @@ __device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint
       }
     }
     if (vx < T(0)) {
-      const T t = ((T)g.x0 - x) / vx;
+      const T t = (gt.x0 - x) / vx;
       if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 1; }
     }
     if (vx > T(0)) {
-      const T t = ((T)g.x1 - x) / vx;
+      const T t = (gt.x1 - x) / vx;
       if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 2; }
     }
     if (vy < T(0)) {
-      const T t = ((T)g.y0 - y) / vy;
+      const T t = (gt.y0 - y) / vy;
       if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 3; }
     }
     if (vy > T(0)) {
-      const T t = ((T)g.y1 - y) / vy;
+      const T t = (gt.y1 - y) / vy;
       if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 4; }
     }
     if (ev < 0) {
@@ -225,16 +242,16 @@ __device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint
     T nx = T(0), ny = T(0);
     int kind;
     if (ev == 0) {
-      nx = (x - (T)g.cxc) / (T)g.cr;
-      ny = (y - (T)g.cyc) / (T)g.cr;
+      nx = (x - gt.cxc) / gt.cr;
+      ny = (y - gt.cyc) / gt.cr;
       kind = USP_BC_DIFFUSE;
     } else {
       const int side = ev - 1;
       kind = (g.bcbits >> (2 * side)) & 3;
-      if (side == 0) { nx = T(1); x = (T)g.x0; }
-      if (side == 1) { nx = T(-1); x = (T)g.x1; }
-      if (side == 2) { ny = T(1); y = (T)g.y0; }
-      if (side == 3) { ny = T(-1); y = (T)g.y1; }
+      if (side == 0) { nx = T(1); x = gt.x0; }
+      if (side == 1) { nx = T(-1); x = gt.x1; }
+      if (side == 2) { ny = T(1); y = gt.y0; }
+      if (side == 3) { ny = T(-1); y = gt.y1; }
     }
     if (kind == USP_BC_OPEN) return false;
     if (kind == USP_BC_SPECULAR) {
@@ -242,13 +259,13 @@ __device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint
       vx -= T(2) * vn * nx;
       vy -= T(2) * vn * ny;
     } else {
-      const T Rth = (T)(gasR(sp) * sp.theta_v);
+      const T Rth = gt.Rth;
       const T in_x = vx, in_y = vy;
       const T in_e = T(0.5) * (vx * vx + vy * vy + vz * vz) + e + Rth * (T)l;
-      plane_emit<T>(sp, g.Tw, (double)nx, (double)ny, pid, step, hits, k0, k1, vx, vy, vz, e, l);
+      plane_emit<T>(gt, nx, ny, pid, step, hits, k0, k1, vx, vy, vz, e, l);
       if (surf && ev == 0) {
         // surface tally of this wall event (bin of the polar angle)
-        const double phi = atan2((double)(y - (T)g.cyc), (double)(x - (T)g.cxc));
+        const double phi = atan2((double)(y - gt.cyc), (double)(x - gt.cxc));
         int b = (int)floor((phi + kPi) / (2.0 * kPi) * kNSurf);
         b = b < 0 ? 0 : (b > kNSurf - 1 ? kNSurf - 1 : b);
         const T out_e = T(0.5) * (vx * vx + vy * vy + vz * vz) + e + Rth * (T)l;
@@ -263,7 +280,8 @@ __device__ bool plane_fly(const PlGeom& g, const Species& sp, uint32_t pid, uint
 }
 
 template <typename T, bool AMR>
-__global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, const PlTree* __restrict__ tr,
+__global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, PlGeomT<T> gt,
+                                                     const PlTree* __restrict__ tr,
                                                      const PlCount* __restrict__ cnt,
                           const int* __restrict__ keycell, const ChCellT<double>* __restrict__ cells,
                           const float* __restrict__ pend,
@@ -283,14 +301,15 @@ __global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, const PlTree* __r
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
        j += grid_threads()) {
     // pending conservation rescale of the previous step (FP32 state: its
-    // FP32 copy, so no FP64 conversion per particle)
+    // FP32 copy, two 16-byte loads, so no FP64 conversion per particle)
     T vx, vy, vz, e;
     if constexpr (sizeof(T) == 4) {
-      const float* pc = pend + (size_t)keycell[j] * 8;
-      vx = pc[0] + pc[6] * (cx[j] - pc[3]);
-      vy = pc[1] + pc[6] * (cy[j] - pc[4]);
-      vz = pc[2] + pc[6] * (cz[j] - pc[5]);
-      e = pc[7] * er[j];
+      const float4* pc = reinterpret_cast<const float4*>(pend + (size_t)keycell[j] * 8);
+      const float4 p0 = pc[0], p1 = pc[1];   // Un(3), Us(3), s, r
+      vx = p0.x + p1.z * (cx[j] - p0.w);
+      vy = p0.y + p1.z * (cy[j] - p1.x);
+      vz = p0.z + p1.z * (cz[j] - p1.y);
+      e = p1.w * er[j];
     } else {
       const ChCellT<double>& cc = cells[keycell[j]];
       vx = (T)cc.Un[0] + (T)cc.s * (cx[j] - (T)cc.Us[0]);
@@ -301,12 +320,12 @@ __global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, const PlTree* __r
     int l = lev[j];
     T px = x[j], py = y[j];
     int hits = 0;
-    const bool keep = plane_fly<T>(g, sp, pid[j], step, k0, k1, (T)g.dt, px, py, vx, vy, vz, e,
-                                   l, hits, fl, surf);
+    const bool keep = plane_fly<T>(g, gt, pid[j], step, k0, k1, gt.dt, px, py, vx, vy, vz, e, l,
+                                   hits, fl, surf);
     nhit += hits;
     nout += keep ? 0 : 1;
     x[j] = px; y[j] = py; cx[j] = vx; cy[j] = vy; cz[j] = vz; er[j] = e; lev[j] = l;
-    keyout[j] = keep ? plane_cell<T, AMR>(g, tr, px, py) : g.ncell;
+    keyout[j] = keep ? plane_cell<T, AMR>(g, gt, tr, px, py) : g.ncell;
     idxout[j] = (int)j;
   }
   fl = __reduce_or_sync(0xffffffffu, fl);
@@ -408,41 +427,42 @@ __global__ void pl_inflow(PlInflow f, PlCount* __restrict__ cnt, int* __restrict
 // accepted if u3 <= exp(2 s w).  Double precision on uniforms of the
 // working precision.
 template <typename T>
-__device__ double inflow_speed(double RT, double u_n, uint32_t pid, uint32_t step, uint32_t k0,
-                               uint32_t k1, uint32_t& fl) {
-  const double sc = sqrt(2.0 * RT);
-  const double s = u_n / sc;
-  const double p1 = 1.0 / (1.0 + s * sqrt(kPi));
+__device__ T inflow_speed(T RT, T u_n, uint32_t pid, uint32_t step, uint32_t k0, uint32_t k1,
+                          uint32_t& fl) {
+  const T sc = sqrt(T(2) * RT);
+  const T s = u_n / sc;
+  const T p1 = T(1) / (T(1) + s * sqrt(T(kPi)));
   for (int k = 0; k < kInflowTries; ++k) {
     const U4 r = philox4x32_10(pid, step, PTAG_INFLOW_V, (uint32_t)k, k0, k1);
-    const double u0 = (double)uniform_open<T>(r.x), u1 = (double)uniform_open<T>(r.y);
-    const double u2 = (double)uniform_open<T>(r.z), u3 = (double)uniform_open<T>(r.w);
-    if (s < 0.0) {
-      const double wn = sqrt(-log(u1));
-      if (u3 <= exp(2.0 * s * wn)) return wn * sc;
+    const T u0 = uniform_open<T>(r.x), u1 = uniform_open<T>(r.y);
+    const T u2 = uniform_open<T>(r.z), u3 = uniform_open<T>(r.w);
+    if (s < T(0)) {
+      const T wn = sqrt(-log(u1));
+      if (u3 <= exp(T(2) * s * wn)) return wn * sc;
       continue;
     }
-    double t;
+    T t;
     if (u0 < p1) {
       t = sqrt(-log(u1));
-      if (u2 < 0.5) t = -t;
+      if (u2 < T(0.5)) t = -t;
     } else {
-      double g1, g2;
+      T g1, g2;
       box_muller(u1, u2, g1, g2);
-      t = g1 / sqrt(2.0);
+      t = g1 / sqrt(T(2));
     }
-    const double wn = s + t;
-    if (!(wn > 0.0)) continue;
+    const T wn = s + t;
+    if (!(wn > T(0))) continue;
     if (u3 * (fabs(t) + s) <= wn) return wn * sc;
   }
   fl |= F_INFLOW_CAP;
-  return (s > 0.0 ? s : 0.5 * sqrt(kPi)) * sc;
+  return (s > T(0) ? s : T(0.5) * sqrt(T(kPi))) * sc;
 }
 
 // one thread per entering particle (grid-stride over the step's count); its
 // face by binary search of the face offsets
 template <typename T, bool AMR>
-__global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, const PlTree* __restrict__ tr,
+__global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, PlGeomT<T> gt,
+                                                     const PlTree* __restrict__ tr,
                                                      PlInflow f, const PlCount* __restrict__ cnt,
                           const int* __restrict__ face_off, T* __restrict__ x, T* __restrict__ y,
                           T* __restrict__ cx, T* __restrict__ cy, T* __restrict__ cz,
@@ -456,7 +476,10 @@ __global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, const PlTree* __r
   const long long ninj = cnt->ninj;
   const uint32_t step = (uint32_t)*dstep;
   const long long n = cnt->n;
-  const double st = sqrt(f.RT);
+  // the freestream in the working precision
+  struct { T RT, U, Tinf, u_n[4]; } fin = {(T)f.RT, (T)f.U, (T)f.T,
+                                          {(T)f.u_n[0], (T)f.u_n[1], (T)f.u_n[2], (T)f.u_n[3]}};
+  const T st = sqrt(fin.RT);
   uint32_t fl = 0;
   unsigned long long nhit = 0, nout = 0;
   for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < ninj;
@@ -470,39 +493,38 @@ __global__ void __launch_bounds__(kBlk, 3) pl_inject(PlGeom g, const PlTree* __r
     const int q = lo;
     int side, k;
     face_of(f, q, side, k);
-    const double nxs = side == 0 ? 1.0 : (side == 1 ? -1.0 : 0.0);
-    const double nys = side == 2 ? 1.0 : (side == 3 ? -1.0 : 0.0);
+    const T nxs = side == 0 ? T(1) : (side == 1 ? T(-1) : T(0));
+    const T nys = side == 2 ? T(1) : (side == 3 ? T(-1) : T(0));
     const uint32_t id = cnt->pid0 + (uint32_t)m;
     const U4 a = philox4x32_10(id, step, PTAG_INFLOW_P, 0u, k0, k1);
     const U4 bb = philox4x32_10(id, step, PTAG_INFLOW_T, 0u, k0, k1);
-    const double u_pos = (double)uniform_open<T>(a.x), u_t = (double)uniform_open<T>(a.y);
-    double g1, g2;
-    box_muller((double)uniform_open<T>(bb.x), (double)uniform_open<T>(bb.y), g1, g2);
-    const double vn = inflow_speed<T>(f.RT, pick4(f.u_n, side), id, step, k0, k1, fl);
-    double px, py, vx, vy;
+    const T u_pos = uniform_open<T>(a.x), u_t = uniform_open<T>(a.y);
+    T g1, g2;
+    box_muller(uniform_open<T>(bb.x), uniform_open<T>(bb.y), g1, g2);
+    const T vn = inflow_speed<T>(fin.RT, pick4(fin.u_n, side), id, step, k0, k1, fl);
+    T X, Y, VX, VY;
     if (side < 2) {
-      px = side == 0 ? g.x0 : g.x1;
-      py = g.y0 + (k + u_pos) * g.dy;
-      vx = vn * nxs;
-      vy = st * g1;
+      X = side == 0 ? gt.x0 : gt.x1;
+      Y = gt.y0 + ((T)k + u_pos) * gt.dy;
+      VX = vn * nxs;
+      VY = st * g1;
     } else {
-      px = g.x0 + (k + u_pos) * g.dx;
-      py = side == 2 ? g.y0 : g.y1;
-      vx = f.U + st * g1;
-      vy = vn * nys;
+      X = gt.x0 + ((T)k + u_pos) * gt.dx;
+      Y = side == 2 ? gt.y0 : gt.y1;
+      VX = fin.U + st * g1;
+      VY = vn * nys;
     }
-    const double vz = st * g2;
-    const double e = -f.RT * log((double)uniform_open<T>(a.z));
-    const int l0 = (int)floor(-log((double)uniform_open<T>(a.w)) * f.T / sp.theta_v);
-    T X = (T)px, Y = (T)py, VX = (T)vx, VY = (T)vy, VZ = (T)vz, E = (T)e;
+    T VZ = st * g2;
+    T E = -fin.RT * log(uniform_open<T>(a.z));
+    const int l0 = (int)floor(-log(uniform_open<T>(a.w)) * fin.Tinf / gt.theta);
     int L = l0, hits = 0;
-    const bool keep = plane_fly<T>(g, sp, id, step, k0, k1, (T)(u_t * g.dt), X, Y, VX, VY, VZ,
-                                   E, L, hits, fl, surf);
+    const bool keep = plane_fly<T>(g, gt, id, step, k0, k1, u_t * gt.dt, X, Y, VX, VY, VZ, E, L,
+                                   hits, fl, surf);
     nhit += hits;
     nout += keep ? 0 : 1;
     const long long j = n + m;
     x[j] = X; y[j] = Y; cx[j] = VX; cy[j] = VY; cz[j] = VZ; er[j] = E; lev[j] = L; pid[j] = id;
-    keyout[j] = keep ? plane_cell<T, AMR>(g, tr, X, Y) : g.ncell;
+    keyout[j] = keep ? plane_cell<T, AMR>(g, gt, tr, X, Y) : g.ncell;
     idxout[j] = (int)j;
   }
   fl = __reduce_or_sync(0xffffffffu, fl);
@@ -686,86 +708,112 @@ __global__ void pl_gather(PlCount* __restrict__ cnt, int ncell,
 // the centroid the x and y neighbour used (that side's if usable, else the
 // opposite one, else none) and the quadrant's diagonal when usable
 // ---------------------------------------------------------------------------
+// cells per block of the uniform grid's stencil pass (its static shared
+// memory stays under 48 KB)
 template <typename T>
-__global__ void pl_params(PlGeom g, int recon, const ChCellT<double>* __restrict__ cells,
-                          const T* __restrict__ fT, const int* __restrict__ usable_c,
-                          PlParams<T>* __restrict__ prm, Species sp,
-                          const double* __restrict__ fpm) {
+constexpr int kStencilBlock = sizeof(T) == 4 ? 64 : 32;
+
+template <typename T>
+__global__ void __launch_bounds__(kStencilBlock<T>)
+pl_params(PlGeom g, PlGeomT<T> gt, int recon, const ChCellT<double>* __restrict__ cells,
+          const T* __restrict__ fT, const int* __restrict__ usable_c,
+          PlParams<T>* __restrict__ prm, Species sp, const double* __restrict__ fpm) {
   // a thread builds its cell's record in shared memory; the block then copies
-  // its kParamBlock records out as consecutive 8-byte words (coalesced), where
-  // one thread storing a ~0.5 KB record would scatter every store
-  __shared__ PlParams<T> buf[kParamBlock];
-  const int c0 = blockIdx.x * kParamBlock;
+  // its records out as consecutive 8-byte words (coalesced), where one thread
+  // storing a ~0.5 KB record would scatter every store.  The fields and
+  // usable flags of the block's cells and their neighbours (three runs of
+  // kSpan consecutive cells: the rows below, at and above) are staged first,
+  // with coalesced loads.
+  constexpr int kB = kStencilBlock<T>;
+  constexpr int kSpan = kB + 2;
+  __shared__ PlParams<T> buf[kB];
+  __shared__ T sf[3][kSpan][kNF];
+  __shared__ int su[3][kSpan];
+  const int c0 = blockIdx.x * kB;
   const int c = c0 + threadIdx.x;
-  const int nb = min(kParamBlock, g.ncell - c0);
+  const int nb = min(kB, g.ncell - c0);
+  // cell of run r (row offset r - 1), place m: c0 - 1 + (r - 1) nx + m
+  for (int e = threadIdx.x; e < 3 * kSpan * kNF; e += kB) {
+    const int r = e / (kSpan * kNF), m = (e / kNF) % kSpan, k = e % kNF;
+    const int cc = c0 - 1 + (r - 1) * g.nx + m;
+    sf[r][m][k] = cc >= 0 && cc < g.ncell ? fT[(size_t)cc * kNF + k] : T(0);
+  }
+  for (int e = threadIdx.x; e < 3 * kSpan; e += kB) {
+    const int r = e / kSpan, m = e % kSpan;
+    const int cc = c0 - 1 + (r - 1) * g.nx + m;
+    su[r][m] = cc >= 0 && cc < g.ncell ? usable_c[cc] : 0;
+  }
+  __syncthreads();
   if (c < g.ncell) {
-  const ChCellT<double>& cs = cells[c];
-  PlParams<T>& P = buf[threadIdx.x];
-  P.active = cs.active;
-  P.pad = 0;
-  P.alpha = (T)cs.alpha; P.nu_ref = (T)cs.nu_ref; P.B = (T)cs.B; P.mu_p = (T)cs.mu_p;
-  P.Pr = (T)cs.Pr; P.gtr = (T)cs.gtr; P.gtv = (T)cs.gtv; P.grv = (T)cs.grv;
-  P.R = (T)gasR(sp); P.theta = (T)sp.theta_v; P.dt = (T)g.dt;
-  const int i = c % g.nx, j = c / g.nx;
-  P.xc = (T)(g.x0 + (i + 0.5) * g.dx);
-  P.yc = (T)(g.y0 + (j + 0.5) * g.dy);
-  const T* f = fT + (size_t)c * kNF;
-  for (int k = 0; k < kNF; ++k) P.F[k] = f[k];
-  if (fpm) {
-    // the plain FPM method: cell values, its per-cell constants
-    for (int k = 0; k < kNF; ++k) { P.gx[0][k] = P.gx[1][k] = P.gy[0][k] = P.gy[1][k] = T(0); }
-    const double* r = fpm + (size_t)c * kFpmRec;
-    P.fpm.as = (T)r[0];
-    for (int k = 0; k < 6; ++k) P.fpm.Lp[k] = (T)r[1 + k];
-    P.fpm.a_rot = (T)r[7]; P.fpm.sqrt_a = (T)r[8];
-    P.fpm.lam_up = (T)r[9]; P.fpm.lam_dn = (T)r[10];
-  } else {
-  auto usable = [&](int ii, int jj) {
-    return recon && ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && usable_c[jj * g.nx + ii];
-  };
-  // slopes in the working precision from the cell values, times 1/offset
-  const T idx = (T)(1.0 / g.dx), idy = (T)(1.0 / g.dy);
-  int ix[2], jy[2];
-  for (int sd = 0; sd < 2; ++sd) {
-    const int sg = sd ? 1 : -1;
-    ix[sd] = usable(i + sg, j) ? i + sg : (usable(i - sg, j) ? i - sg : -1);
-    jy[sd] = usable(i, j + sg) ? j + sg : (usable(i, j - sg) ? j - sg : -1);
-    if (ix[sd] >= 0) {
-      const T* fn = fT + (size_t)(j * g.nx + ix[sd]) * kNF;
-      const T ih = ix[sd] > i ? idx : -idx;
-      for (int k = 0; k < kNF; ++k) P.gx[sd][k] = (fn[k] - f[k]) * ih;
+    const ChCellT<double>& cs = cells[c];
+    PlParams<T>& P = buf[threadIdx.x];
+    P.active = cs.active;
+    P.pad = 0;
+    P.alpha = (T)cs.alpha; P.nu_ref = (T)cs.nu_ref; P.B = (T)cs.B; P.mu_p = (T)cs.mu_p;
+    P.Pr = (T)cs.Pr; P.gtr = (T)cs.gtr; P.gtv = (T)cs.gtv; P.grv = (T)cs.grv;
+    P.R = (T)gasR(sp); P.theta = gt.theta; P.dt = gt.dt;
+    const int i = c % g.nx, j = c / g.nx;
+    P.xc = (T)(g.x0 + (i + 0.5) * g.dx);
+    P.yc = (T)(g.y0 + (j + 0.5) * g.dy);
+    // neighbour (i + di, j + dj): run dj + 1, place threadIdx.x + 1 + di
+    const int m0 = threadIdx.x + 1;
+    const T* f = sf[1][m0];
+    for (int k = 0; k < kNF; ++k) P.F[k] = f[k];
+    if (fpm) {
+      // the plain FPM method: cell values, its per-cell constants
+      for (int k = 0; k < kNF; ++k) { P.gx[0][k] = P.gx[1][k] = P.gy[0][k] = P.gy[1][k] = T(0); }
+      const double* r = fpm + (size_t)c * kFpmRec;
+      P.fpm.as = (T)r[0];
+      for (int k = 0; k < 6; ++k) P.fpm.Lp[k] = (T)r[1 + k];
+      P.fpm.a_rot = (T)r[7]; P.fpm.sqrt_a = (T)r[8];
+      P.fpm.lam_up = (T)r[9]; P.fpm.lam_dn = (T)r[10];
     } else {
-      for (int k = 0; k < kNF; ++k) P.gx[sd][k] = T(0);
+      auto usable = [&](int di, int dj) {
+        const int ii = i + di, jj = j + dj;
+        return recon && ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && su[dj + 1][m0 + di];
+      };
+      auto field = [&](int di, int dj) { return sf[dj + 1][m0 + di]; };
+      // slopes in the working precision from the cell values, times 1/offset
+      int ox[2], oy[2];   // the x and y neighbour of each side (offset; 0: none)
+      for (int sd = 0; sd < 2; ++sd) {
+        const int sg = sd ? 1 : -1;
+        ox[sd] = usable(sg, 0) ? sg : (usable(-sg, 0) ? -sg : 0);
+        oy[sd] = usable(0, sg) ? sg : (usable(0, -sg) ? -sg : 0);
+        if (ox[sd] != 0) {
+          const T* fn = field(ox[sd], 0);
+          const T ih = ox[sd] > 0 ? gt.idx : -gt.idx;
+          for (int k = 0; k < kNF; ++k) P.gx[sd][k] = (fn[k] - f[k]) * ih;
+        } else {
+          for (int k = 0; k < kNF; ++k) P.gx[sd][k] = T(0);
+        }
+        if (oy[sd] != 0) {
+          const T* fn = field(0, oy[sd]);
+          const T ih = oy[sd] > 0 ? gt.idy : -gt.idy;
+          for (int k = 0; k < kNF; ++k) P.gy[sd][k] = (fn[k] - f[k]) * ih;
+        } else {
+          for (int k = 0; k < kNF; ++k) P.gy[sd][k] = T(0);
+        }
+      }
+      for (int q = 0; q < 4; ++q) {
+        const int sx = q & 1, sy = q >> 1;
+        if (ox[sx] != 0 && oy[sy] != 0 && usable(ox[sx], oy[sy])) {
+          const T* fd = field(ox[sx], oy[sy]);
+          const T* fx = field(ox[sx], 0);
+          const T* fy = field(0, oy[sy]);
+          const T ih = ((ox[sx] > 0) == (oy[sy] > 0) ? T(1) : T(-1)) * gt.idx * gt.idy;
+          for (int k = 0; k < kNF; ++k) P.gxy[q][k] = (fd[k] - fx[k] - fy[k] + f[k]) * ih;
+        } else {
+          for (int k = 0; k < kNF; ++k) P.gxy[q][k] = T(0);
+        }
+      }
     }
-    if (jy[sd] >= 0) {
-      const T* fn = fT + (size_t)(jy[sd] * g.nx + i) * kNF;
-      const T ih = jy[sd] > j ? idy : -idy;
-      for (int k = 0; k < kNF; ++k) P.gy[sd][k] = (fn[k] - f[k]) * ih;
-    } else {
-      for (int k = 0; k < kNF; ++k) P.gy[sd][k] = T(0);
-    }
-  }
-  for (int q = 0; q < 4; ++q) {
-    const int sx = q & 1, sy = q >> 1;
-    const bool d = ix[sx] >= 0 && jy[sy] >= 0 && usable(ix[sx], jy[sy]);
-    if (d) {
-      const T* fd = fT + (size_t)(jy[sy] * g.nx + ix[sx]) * kNF;
-      const T* fx = fT + (size_t)(j * g.nx + ix[sx]) * kNF;
-      const T* fy = fT + (size_t)(jy[sy] * g.nx + i) * kNF;
-      const T ih = ((ix[sx] > i) == (jy[sy] > j) ? T(1) : T(-1)) * idx * idy;
-      for (int k = 0; k < kNF; ++k) P.gxy[q][k] = (fd[k] - fx[k] - fy[k] + f[k]) * ih;
-    } else {
-      for (int k = 0; k < kNF; ++k) P.gxy[q][k] = T(0);
-    }
-  }
-  }
   }
   __syncthreads();
   static_assert(sizeof(PlParams<T>) % 8 == 0, "records copied as 8-byte words");
   const int words = nb * (int)(sizeof(PlParams<T>) / 8);
   const unsigned long long* src = reinterpret_cast<const unsigned long long*>(buf);
   unsigned long long* dst = reinterpret_cast<unsigned long long*>(prm + c0);
-  for (int w = threadIdx.x; w < words; w += kParamBlock) dst[w] = src[w];
+  for (int w = threadIdx.x; w < words; w += kB) dst[w] = src[w];
 }
 
 // ---------------------------------------------------------------------------
@@ -1406,14 +1454,15 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   double* surf = h->sampling ? h->acc + (size_t)ncell * kNAcc + 2 : nullptr;
   // the uniform grid takes the point location without the refined-grid branch
   const bool amr = h->levels >= 2;
+  const PlGeomT<T> gt = geom_t<T>(h->g, env.sp);
   (amr ? pl_advect<T, true> : pl_advect<T, false>)<<<h->grid_p, kBlk, 0, s>>>(
-      h->g, h->tree, h->cnt, h->keycell, h->cells, h->pend, x, y, cx, cy, cz, er, h->lv[a], h->pd[a],
+      h->g, gt, h->tree, h->cnt, h->keycell, h->cells, h->pend, x, y, cx, cy, cz, er, h->lv[a], h->pd[a],
       h->kbuf[0], h->ibuf[0], h->dstep, env.sp, env.k0, env.k1, env.flags, env.counters, surf);
   pl_inflow<<<1, 1024, 0, s>>>(h->inf, h->cnt, h->face_off, h->cap, h->dstep, env.k0, env.k1,
                                env.flags, env.counters);
   if (h->inf.nfaces > 0)
     (amr ? pl_inject<T, true> : pl_inject<T, false>)<<<h->grid_inj, kBlk, 0, s>>>(
-        h->g, h->tree, h->inf, h->cnt, h->face_off, x, y, cx, cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0],
+        h->g, gt, h->tree, h->inf, h->cnt, h->face_off, x, y, cx, cy, cz, er, h->lv[a], h->pd[a], h->kbuf[0],
         h->ibuf[0], h->dstep, env.sp, env.k0, env.k1, env.flags, env.counters, surf);
   CHK(cudaGetLastError());
   int src = 0;
@@ -1460,9 +1509,9 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
                                           env.sp, env.sp.omega, env.sp.Z_rot, env.flags,
                                           env.counters);
   if (fpm || h->levels < 2)
-    pl_params<T><<<(ncell + kParamBlock - 1) / kParamBlock, kParamBlock, 0, s>>>(
-        h->g, fpm ? 0 : h->recon, h->cells, (const T*)h->fT, h->usable_c, (PlParams<T>*)h->prm,
-        env.sp, h->fpmrec);
+    pl_params<T><<<(ncell + kStencilBlock<T> - 1) / kStencilBlock<T>, kStencilBlock<T>, 0, s>>>(
+        h->g, gt, fpm ? 0 : h->recon, h->cells, (const T*)h->fT, h->usable_c,
+        (PlParams<T>*)h->prm, env.sp, h->fpmrec);
   else
     for (int L = 1; L <= h->levels; ++L)
       if (h->nblk_lv[L] > 0)
