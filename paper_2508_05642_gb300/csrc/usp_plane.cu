@@ -17,18 +17,18 @@
 //                  Maxwellian tangential components, uniform entry point
 //                  and entry time, flight for the rest of the step
 //   radix passes   stable LSD radix sort of (cell key, index) over the moved
-//                  and the new particles, 8-bit digits, removed ones last
-//   pl_offsets     cell segment starts; the new live count is the start of
-//                  the removed particles' segment
-//   pl_gather      live state permuted into cell order (other buffer)
-//   ch_moments, ch_coeffs   per-cell moments and coefficients (Sec. 2.A,
-//                  3.A), cut cells with their fluid volume
+//                  and the new particles, 9-bit digits, removed ones last
+//   pl_gather      live state permuted into cell order (other buffer), the
+//                  cell segment starts and the new live count
+//   ch_moments_coeffs_f32 (FP32 USP-FPM; else ch_moments, ch_coeffs or
+//                  ch_coeffs_fpm)  per-cell moments and coefficients (Sec.
+//                  2.A, 3.A), cut cells with their fluid volume
 //   pl_params      per cell the reconstruction stencil of Sec. 3.B: for each
 //                  side of the centroid the neighbour used along x and y and
 //                  whether the quadrant's diagonal neighbour is usable
 //   pl_collide     per particle: bilinear fields of its quadrant, collision
 //                  of Sec. 4.D; per-cell sums
-//   ch_levelfix, ch_update  conservation of Sec. 4.C (rescale kept pending)
+//   ch_fix_update  conservation of Sec. 4.C (rescale kept pending)
 //   pl_sample      (while sampling) time-average sums of the post-step state
 #include <cuda_runtime.h>
 
@@ -283,12 +283,12 @@ template <typename T, bool AMR>
 __global__ void __launch_bounds__(kBlk, 3) pl_advect(PlGeom g, PlGeomT<T> gt,
                                                      const PlTree* __restrict__ tr,
                                                      const PlCount* __restrict__ cnt,
-                          const int* __restrict__ keycell, const ChCellT<double>* __restrict__ cells,
+                          const int* keycell, const ChCellT<double>* __restrict__ cells,
                           const float* __restrict__ pend,
                           T* __restrict__ x, T* __restrict__ y, T* __restrict__ cx,
                           T* __restrict__ cy, T* __restrict__ cz, T* __restrict__ er,
                           int* __restrict__ lev, const uint32_t* __restrict__ pid,
-                          int* __restrict__ keyout, int* __restrict__ idxout,
+                          int* keyout, int* __restrict__ idxout,
                           const long long* __restrict__ dstep, Species sp, uint32_t k0,
                           uint32_t k1, uint32_t* flags, unsigned long long* counters,
                           double* surf) {
@@ -662,45 +662,44 @@ __global__ void pl_scatter(const int* __restrict__ kin, const int* __restrict__ 
   }
 }
 
-// cell segment starts from the sorted keys (keys in [0, ncell], ncell =
-// removed particles)
-__global__ void pl_offsets(const PlCount* __restrict__ cnt, int ncell,
-                           const int* __restrict__ key, long long* __restrict__ off) {
+// The live state permuted into cell order (other buffer), and the cell
+// segment starts from the sorted keys (keys in [0, ncell], ncell = removed
+// particles, which are not copied): where the key changes between j - 1 and
+// j, the cells in between start at j.  The new live count is the start of
+// the removed particles' segment.  The sorted keys stay where the sort left
+// them and serve as the particles' cells from here on.
+template <typename T>
+__global__ void pl_gather(PlCount* __restrict__ cnt, int ncell, long long* __restrict__ off,
+                          const int* __restrict__ idx, const int* __restrict__ ksorted,
+                          const T* __restrict__ x0, const T* __restrict__ y0,
+                          const T* __restrict__ vx0, const T* __restrict__ vy0,
+                          const T* __restrict__ vz0, const T* __restrict__ e0,
+                          const int* __restrict__ l0, const uint32_t* __restrict__ p0,
+                          T* __restrict__ x1, T* __restrict__ y1, T* __restrict__ vx1,
+                          T* __restrict__ vy1, T* __restrict__ vz1, T* __restrict__ e1,
+                          int* __restrict__ l1, uint32_t* __restrict__ p1) {
   const long long n = cnt->ntot;
   const long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (n == 0) {
     for (long long c = j0; c <= ncell; c += grid_threads()) off[c] = 0;
+    if (j0 == 0) cnt->n = 0;
     return;
   }
   for (long long j = j0; j < n; j += grid_threads()) {
-    const int k = key[j];
-    const int prev = j > 0 ? key[j - 1] : -1;
+    const int k = ksorted[j];
+    const int prev = j > 0 ? ksorted[j - 1] : -1;
     for (int c = prev + 1; c <= k; ++c) off[c] = j;
-    if (j == n - 1)
+    if (k == ncell && prev < ncell) cnt->n = j;
+    if (j == n - 1 && k < ncell) {
       for (int c = k + 1; c <= ncell; ++c) off[c] = n;
+      cnt->n = n;
+    }
+    if (k < ncell) {
+      const int s = idx[j];
+      x1[j] = x0[s]; y1[j] = y0[s]; vx1[j] = vx0[s]; vy1[j] = vy0[s]; vz1[j] = vz0[s];
+      e1[j] = e0[s]; l1[j] = l0[s]; p1[j] = p0[s];
+    }
   }
-}
-
-template <typename T>
-__global__ void pl_gather(PlCount* __restrict__ cnt, int ncell,
-                          const long long* __restrict__ off, const int* __restrict__ idx,
-                          const int* __restrict__ ksorted, const T* __restrict__ x0,
-                          const T* __restrict__ y0, const T* __restrict__ vx0,
-                          const T* __restrict__ vy0, const T* __restrict__ vz0,
-                          const T* __restrict__ e0, const int* __restrict__ l0,
-                          const uint32_t* __restrict__ p0, T* __restrict__ x1,
-                          T* __restrict__ y1, T* __restrict__ vx1, T* __restrict__ vy1,
-                          T* __restrict__ vz1, T* __restrict__ e1, int* __restrict__ l1,
-                          uint32_t* __restrict__ p1, int* __restrict__ keycell) {
-  const long long n = off[ncell];
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-       j += grid_threads()) {
-    const int s = idx[j];
-    x1[j] = x0[s]; y1[j] = y0[s]; vx1[j] = vx0[s]; vy1[j] = vy0[s]; vz1[j] = vz0[s];
-    e1[j] = e0[s]; l1[j] = l0[s]; p1[j] = p0[s];
-    keycell[j] = ksorted[j];
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) cnt->n = n;
 }
 
 // ---------------------------------------------------------------------------
@@ -1474,12 +1473,11 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
     CHK(cudaGetLastError());
     src ^= 1;
   }
-  pl_offsets<<<h->grid_p, kBlk, 0, s>>>(h->cnt, ncell, h->kbuf[src], h->off);
+  // the sorted keys end in kbuf[passes & 1], which keycell names
   pl_gather<T><<<h->grid_p, kBlk, 0, s>>>(h->cnt, ncell, h->off, h->ibuf[src], h->kbuf[src], x, y,
                                           cx, cy, cz, er, h->lv[a], h->pd[a], (T*)h->st[b][0],
                                           (T*)h->st[b][1], (T*)h->st[b][2], (T*)h->st[b][3],
-                                          (T*)h->st[b][4], (T*)h->st[b][5], h->lv[b], h->pd[b],
-                                          h->keycell);
+                                          (T*)h->st[b][4], (T*)h->st[b][5], h->lv[b], h->pd[b]);
   CHK(cudaGetLastError());
   h->cur = b;
   x = (T*)h->st[b][0]; y = (T*)h->st[b][1]; cx = (T*)h->st[b][2]; cy = (T*)h->st[b][3];
@@ -1557,7 +1555,7 @@ int pl_kernels_per_step(const PlaneCtx* h) {
     for (int L = 1; L <= h->levels; ++L) params += h->nblk_lv[L] > 0 ? 1 : 0;
   }
   const int cellpass = h->es == sizeof(float) && !h->fpmrec ? 1 : 2;
-  return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 2 + cellpass + params + 1 + 1 +
+  return 2 + (h->inf.nfaces > 0 ? 1 : 0) + 3 * h->passes + 1 + cellpass + params + 1 + 1 +
          (h->sampling ? 1 : 0);
 }
 
@@ -1666,7 +1664,9 @@ int pl_create(PlaneCtx** out, const ChEnv& env, const usp_plane* pp, double dt,
     h->kbuf[k] = (int*)A(nn * 4);
     h->ibuf[k] = (int*)A(nn * 4);
   }
-  h->keycell = (int*)A(nn * 4);
+  // the particles' cells: the sorted keys, where the last radix pass leaves them
+  h->keycell = h->kbuf[h->passes & 1];
+
   h->bh = (int*)A((size_t)h->nblk * kNB * 4);
   h->tot = (int*)A(kNB * 4);
   h->face_off = (int*)A(sizeof(int) * (f.nfaces + 1));
