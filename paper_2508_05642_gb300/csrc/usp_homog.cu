@@ -103,6 +103,20 @@ struct Tile {
 constexpr int kJR = 32;   // rows: NB r = 1..32, B n = 0..31
 constexpr int kJK = 48;   // cumulative values per row (rows 16-byte aligned)
 
+// The pmf ratios of the rows, the same for every cell: (k + r) / (k + 1) of
+// the NB row r (index r - 1) and (n - k) / (k + 1) of the binomial row n,
+// each the correctly rounded float quotient that the sequential inversion
+// forms; filled once per context by jratio_kernel.
+__device__ float g_jratio[2][kJR][kJK];
+
+__global__ void jratio_kernel() {
+  for (int e = threadIdx.x; e < kJR * kJK; e += blockDim.x) {
+    const int a = e / kJK, k = e % kJK;
+    g_jratio[0][a][k] = rn_div(rn_i2f(k + a + 1, 0.0f), rn_i2f(k + 1, 0.0f));
+    g_jratio[1][a][k] = k < a ? rn_div(rn_i2f(a - k, 0.0f), rn_i2f(k + 1, 0.0f)) : 0.0f;
+  }
+}
+
 __device__ void nb_row(int r, float p, float* T) {
   const float q = rn_sub(1.0f, p);
   float P = powi_rn(p, r);
@@ -113,7 +127,7 @@ __device__ void nb_row(int r, float p, float* T) {
   for (int j = 1; j < kJK; ++j) {
     if (!stop) {
       const int k = j - 1;
-      const float t = rn_div(rn_i2f(k + r, 0.0f), rn_i2f(k + 1, 0.0f));
+      const float t = g_jratio[0][r - 1][k];   // (k + r) / (k + 1)
       P = rn_mul(P, t);
       P = rn_mul(P, q);
       const float nc = rn_add(cdf, P);
@@ -139,7 +153,7 @@ __device__ void b_row(int n, float p, float* T) {
         stop = true;   // the search ends at k = n whatever u is
       } else {
         const int k = j - 1;
-        const float t = rn_div(rn_i2f(n - k, 0.0f), rn_i2f(k + 1, 0.0f));
+        const float t = g_jratio[1][n][k];       // (n - k) / (k + 1)
         P = rn_mul(P, t);
         P = rn_mul(P, pq);
         const float nc = rn_add(cdf, P);
@@ -161,12 +175,14 @@ __device__ void b_row(int n, float p, float* T) {
 // search's, so still the sequential inversion's, bit for bit.  A row whose
 // P(0) underflowed (T[0] = -1) gets 0xff bytes: k = 127 sends the particle to
 // the sequential search.
-constexpr int kGB = 256;   // guide bytes per row
+constexpr int kGBits = 8;             // guide bins per row: 2^kGBits
+constexpr int kGB = 1 << kGBits;      // guide bytes per row
+constexpr int kGS = 23 - kGBits;      // 23-bit uniform index -> bin: >> kGS
 
 // number of leading row entries <= u, u formed from the word x
 __device__ __forceinline__ int guided_search(const float* __restrict__ T,
                                              const uint8_t* __restrict__ g, uint32_t x, float u) {
-  const unsigned gv = __ldg(g + (x >> 24));
+  const unsigned gv = __ldg(g + (x >> (32 - kGBits)));
   int k = (int)(gv & 0x7fu);
   if (!(gv & 0x80u)) {
 #pragma unroll 1
@@ -785,7 +801,7 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
 // Jump-table rows of every cell for the coming step (FP32 form), one block of
 // kJT threads per cell: thread j < kJR builds the NB row r = j + 1, thread
 // kJR + n the binomial row n, for the rows the cell's levels can reach; then
-// every thread builds a quarter (64 bins) of one row's guide.
+// every row's guide is built by kGP threads.
 constexpr int kJT = 8 * kJR;
 
 __device__ __forceinline__ bool nb_row_used(int j, int rows, float p_nb) {
@@ -795,23 +811,25 @@ __device__ __forceinline__ bool b_row_used(int n, int rows, float p_b) {
   return n >= 1 && n <= rows - 1 && p_b < 1.0f && p_b > 0.0f;
 }
 
-// bins [q kGB/4, (q + 1) kGB/4) of the guide of row T (the guide tables above)
-__device__ void guide_quarter(const float* __restrict__ T, uint8_t* __restrict__ g, int q) {
+// bins [q kQ, (q + 1) kQ) of the guide of row T (the guide tables above),
+// kQ = kGB / kGP
+constexpr int kGP = 4;   // threads per guide row
+__device__ void guide_part(const float* __restrict__ T, uint8_t* __restrict__ g, int q) {
   uint32_t* g4 = reinterpret_cast<uint32_t*>(g);
-  constexpr int kQ = kGB / 4;
+  constexpr int kQ = kGB / kGP;
   if (T[0] < 0.0f) {
     for (int w = q * kQ / 4; w < (q + 1) * kQ / 4; ++w) g4[w] = 0xffffffffu;
     return;
   }
   int k = 0;
-  const float u0 = (float)(2 * ((q * kQ) << 15) + 1) * 5.9604644775390625e-8f;
+  const float u0 = (float)(2 * ((q * kQ) << kGS) + 1) * 5.9604644775390625e-8f;
   while (k < kJK && T[k] <= u0) ++k;
   for (int w = q * kQ / 4; w < (q + 1) * kQ / 4; ++w) {
     uint32_t word = 0;
     for (int b = 0; b < 4; ++b) {
       const int m = 4 * w + b;
-      const float umin = (float)(2 * (m << 15) + 1) * 5.9604644775390625e-8f;
-      const float umax = (float)(2 * ((m << 15) + 32767) + 1) * 5.9604644775390625e-8f;
+      const float umin = (float)(2 * (m << kGS) + 1) * 5.9604644775390625e-8f;
+      const float umax = (float)(2 * ((m << kGS) + (1 << kGS) - 1) + 1) * 5.9604644775390625e-8f;
       while (k < kJK && T[k] <= umin) ++k;
       const bool exact = k >= kJK || T[k] > umax;
       word |= (uint32_t)(k | (exact ? 0x80 : 0)) << (8 * b);
@@ -840,14 +858,15 @@ jumptable_kernel(int c0, int c1, const CollideParams<float>* __restrict__ prm,
     if (b_row_used(n, rows, P.p_b)) b_row(n, pb, tab_b + ((size_t)c * kJR + n) * kJK);
   }
   __syncthreads();
-  const int row = j >> 2, q = j & 3;         // 2 kJR rows, four quarters each
+  static_assert(2 * kJR * kGP == kJT, "one guide part per thread");
+  const int row = j / kGP, q = j % kGP;      // 2 kJR rows, kGP parts each
   if (row < kJR) {
     if (nb_row_used(row, rows, P.p_nb))
-      guide_quarter(tab_nb + ((size_t)c * kJR + row) * kJK, gd_nb + ((size_t)c * kJR + row) * kGB, q);
+      guide_part(tab_nb + ((size_t)c * kJR + row) * kJK, gd_nb + ((size_t)c * kJR + row) * kGB, q);
   } else {
     const int n = row - kJR;
     if (b_row_used(n, rows, P.p_b))
-      guide_quarter(tab_b + ((size_t)c * kJR + n) * kJK, gd_b + ((size_t)c * kJR + n) * kGB, q);
+      guide_part(tab_b + ((size_t)c * kJR + n) * kJK, gd_b + ((size_t)c * kJR + n) * kGB, q);
   }
 }
 
@@ -1365,6 +1384,7 @@ struct usp_ctx {
   std::vector<long long> h_uoff;
   std::vector<long long> h_poff;   // padded segment starts
   std::vector<float> tune_ms;      // autotuner timings: block-tiled 2, 3, 4, warp-tiled 2, 3, 4
+  bool jratio_ready = false;       // the rows' pmf ratio table filled on the device
   int tile;
   int grid_collide;
   int minb;                 // register-budget variant of the particle pass
@@ -1637,6 +1657,11 @@ int launch_collide(usp_ctx* c, int warp_tiles, int minb, int grid, void* cx, voi
 // jump tables for the coming step (FP32 form only)
 int launch_tables(usp_ctx* c, const CellRange& r) {
   if (c->precision != USP_FP32 || c->sp.method != 0 || r.c1 <= r.c0) return USP_OK;
+  if (!c->jratio_ready) {
+    jratio_kernel<<<1, 256, 0, c->stream>>>();
+    CK(cudaGetLastError());
+    c->jratio_ready = true;
+  }
   jumptable_kernel<<<r.c1 - r.c0, kJT, 0, c->stream>>>(
       r.c0, r.c1, (const CollideParams<float>*)c->prm, c->cells, c->tab_nb, c->tab_b, c->gd_nb,
       c->gd_b);
@@ -1662,7 +1687,8 @@ int launch_step(usp_ctx* c, const CellRange& r) {
   levelfix_kernel<<<blocks, 32 * warps_per_block, 0, c->stream>>>(
       c->sp, r.c0, r.c1, c->cells, c->sums, c->lev, c->flags, c->counters, key0(c), key1(c));
   CK(cudaGetLastError());
-  cellupdate_kernel<T><<<(n + 63) / 64, 64, 0, c->stream>>>(
+  // one warp per block: the cells' FP64 work spreads over all SMs' FP64 pipes
+  cellupdate_kernel<T><<<(n + 31) / 32, 32, 0, c->stream>>>(
       c->sp, r.c0, r.c1, c->cells, (CollideParams<T>*)c->prm, c->sums, c->flags, c->counters);
   CK(cudaGetLastError());
   if ((rc = launch_tables(c, r))) return rc;
@@ -1878,9 +1904,14 @@ int build_graph(usp_ctx* c, int steps) {
 // Autotuner of the particle pass: times each design (block-tiled, warp-tiled)
 // and register-budget variant (2, 3 or 4 resident blocks per SM) on a scratch
 // copy of the whole state (each variant starts from the same copy; one
-// untimed and two timed launches) and keeps the fastest; within 1 % the
-// earlier candidate wins (warp-tiled before block-tiled, more resident blocks
-// before fewer).
+// untimed and two timed launches) and keeps the fastest; within 3 % the
+// earlier candidate wins (warp-tiled before block-tiled, fewer resident
+// blocks before more).  The state it is timed on is the initial one; as the
+// levels spread over more jump-table rows, the tables' share of the unified
+// L1 grows, and fewer resident blocks (less shared memory, more registers)
+// keep the pass faster: on the 4096-instance workload 3 and 4 blocks per SM
+// tie within 1 % at the start, while from step 250 on 3 take 1.69 ms per
+// launch and 4 take 1.82 ms.
 template <typename T>
 int autotune(usp_ctx* c) {
   const size_t es = sizeof(T);
@@ -1912,7 +1943,7 @@ int autotune(usp_ctx* c) {
   int best_mb = 3, best_wt = 1;
   c->tune_ms.assign(6, 0.f);
   for (int wt = 1; wt >= 0; --wt) {
-    for (int mb = 4; mb >= 2; --mb) {
+    for (int mb = 2; mb <= 4; ++mb) {
       int rc = fresh();
       if (rc) return rc;
       const int grid = c->grid_by_minb[wt][mb];
@@ -1927,7 +1958,7 @@ int autotune(usp_ctx* c) {
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, e0, e1));
       c->tune_ms[3 * wt + mb - 2] = ms / 2.f;
-      if (ms < 0.99f * best) { best = ms; best_mb = mb; best_wt = wt; }
+      if (ms < 0.97f * best) { best = ms; best_mb = mb; best_wt = wt; }
     }
   }
   cudaEventDestroy(e0);
