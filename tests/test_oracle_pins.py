@@ -191,6 +191,30 @@ def test_targets_conserve_energy_and_T1_residual():
         assert c.t1_iters < 50
 
 
+@pytest.mark.parametrize("delta", [1e-2, 1e-4, 1e-6])
+def test_T1_iteration_near_equilibrium_stops_at_the_secant_rounding(delta):
+    """Near equilibrium (T_vib just below T_tr) the secant of c_v,vib(T_1)
+    cancels in its numerator; the iteration still stops within a few passes,
+    and the value it returns is the secant between T_check and T_vib within
+    that secant's rounding (4 eps (|e(T_check)| + |e(T_vib)|) / |T_check -
+    T_vib| plus the tolerance), and within the second-order midpoint bound of
+    c_v,vib at (T_check + T_vib) / 2."""
+    sp = _sp()
+    T = 8000.0
+    for T_rot in (T, 0.9 * T):
+        c = _coeffs(sp, T, T_rot, T * (1.0 - delta))
+        assert c.t1_iters < 10, c.t1_iters
+        ec, ev = O.e_vib(sp, c.T_check), O.e_vib(sp, T * (1.0 - delta))
+        dT = c.T_check - T * (1.0 - delta)
+        if abs(dT) <= 1e-9 * T:
+            continue
+        sec = (ec - ev) / dT
+        noise = 4 * 2.0 ** -52 * (abs(ec) + abs(ev)) / abs(dT)
+        assert abs(c.cv_T1 - sec) <= 2 * noise + 1e-14 * abs(sec)
+        mid = O.cv_vib(sp, 0.5 * (c.T_check + T * (1.0 - delta)))
+        assert c.cv_T1 == pytest.approx(mid, rel=max(1e-12, 10 * (dT / T) ** 2) + noise / mid)
+
+
 def _taylor_second_order(sp, c, T_tr, T_rot, T_vib, dt):
     """Second-order Taylor expansions of the energy relaxations from the
     moment production terms: Eqs. analytic_etr, and the e_rot / e_vib ones
