@@ -814,7 +814,7 @@ __device__ __forceinline__ bool b_row_used(int n, int rows, float p_b) {
 // bins [q kQ, (q + 1) kQ) of the guide of row T (the guide tables above),
 // kQ = kGB / kGP
 constexpr int kGP = 4;   // threads per guide row
-__device__ void guide_part(const float* __restrict__ T, uint8_t* __restrict__ g, int q) {
+__device__ void guide_part(const float* T, uint8_t* __restrict__ g, int q) {
   uint32_t* g4 = reinterpret_cast<uint32_t*>(g);
   constexpr int kQ = kGB / kGP;
   if (T[0] < 0.0f) {
@@ -848,25 +848,32 @@ jumptable_kernel(int c0, int c1, const CollideParams<float>* __restrict__ prm,
   if (c >= c1) return;                       // uniform over the block
   const CollideParams<float>& P = prm[c];
   if (!P.active) return;                     // uniform over the block
+  // the rows are built in shared memory, copied out coalesced, and the
+  // guides read them there
+  __shared__ float rs[2][kJR][kJK];
   const int rows = min(kJR, cells[c].maxI + 1);
   float pb = P.p_b;
   if (pb > 0.5f && pb < 1.0f) pb = rn_sub(1.0f, pb);
   if (j < kJR) {
-    if (nb_row_used(j, rows, P.p_nb)) nb_row(j + 1, P.p_nb, tab_nb + ((size_t)c * kJR + j) * kJK);
+    if (nb_row_used(j, rows, P.p_nb)) nb_row(j + 1, P.p_nb, rs[0][j]);
   } else if (j < 2 * kJR) {
     const int n = j - kJR;
-    if (b_row_used(n, rows, P.p_b)) b_row(n, pb, tab_b + ((size_t)c * kJR + n) * kJK);
+    if (b_row_used(n, rows, P.p_b)) b_row(n, pb, rs[1][n]);
   }
   __syncthreads();
+  for (int e = j; e < 2 * kJR * kJK; e += kJT) {
+    const int t = e / (kJR * kJK), row = (e / kJK) % kJR, k = e % kJK;
+    if (t == 0 ? nb_row_used(row, rows, P.p_nb) : b_row_used(row, rows, P.p_b))
+      (t == 0 ? tab_nb : tab_b)[((size_t)c * kJR + row) * kJK + k] = rs[t][row][k];
+  }
   static_assert(2 * kJR * kGP == kJT, "one guide part per thread");
   const int row = j / kGP, q = j % kGP;      // 2 kJR rows, kGP parts each
   if (row < kJR) {
     if (nb_row_used(row, rows, P.p_nb))
-      guide_part(tab_nb + ((size_t)c * kJR + row) * kJK, gd_nb + ((size_t)c * kJR + row) * kGB, q);
+      guide_part(rs[0][row], gd_nb + ((size_t)c * kJR + row) * kGB, q);
   } else {
     const int n = row - kJR;
-    if (b_row_used(n, rows, P.p_b))
-      guide_part(tab_b + ((size_t)c * kJR + n) * kJK, gd_b + ((size_t)c * kJR + n) * kGB, q);
+    if (b_row_used(n, rows, P.p_b)) guide_part(rs[1][n], gd_b + ((size_t)c * kJR + n) * kGB, q);
   }
 }
 
