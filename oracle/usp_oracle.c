@@ -262,8 +262,12 @@ void orc_collision_numbers(const orc_species* sp, double T_tr, double* Zrot, dou
  *                             + gamma_tr-vib/2 (T_vib - T_tr).
  * The paper gives no solver for this implicit pair.  Reading: fixed-point
  * iteration on c_v,vib(T_1), started at c_v,vib(T_tr), until the relative
- * change is below 1e-14 (at most 50 passes); when T_check is within 1e-9 of
- * T_vib the secant is replaced by the derivative c_v,vib(T_vib).
+ * change is below 1e-14 or below the rounding of the secant itself,
+ * 4 eps (|e_vib(T_check)| + |e_vib(T_vib)|) / |T_check - T_vib| with
+ * eps = 2^-52 (near equilibrium the secant's numerator cancels, and the
+ * rounded map can settle into a cycle of that size instead of a fixed
+ * point), at most 50 passes; when T_check is within 1e-9 of T_vib the secant
+ * is replaced by the derivative c_v,vib(T_vib).
  * For dt >= 2 mu / (p Pr) the ratio A is negative (behind a strong shock at
  * a time step set by the freestream); reading: alpha is then the real cube
  * root, in (-1, 0), which keeps alpha^3 = A for the heat flux and
@@ -304,15 +308,18 @@ int orc_cell_coeffs(const orc_species* sp, double n, double dt,
         double gtv = 2.0 * o->g_v * c_tr * x / den;
         /* e_tr(Tc) - e_tr(T_tr) = c_tr (Tc - T_tr) */
         Tc = T_tr + (0.5 * gtr * (T_rot - T_tr) + 0.5 * gtv * (T_vib - T_tr)) / c_tr;
-        double xn;
+        double xn, noise = 0.0;
         double scale = fabs(Tc) > fabs(T_vib) ? fabs(Tc) : fabs(T_vib);
-        if (fabs(Tc - T_vib) <= 1e-9 * scale)
+        if (fabs(Tc - T_vib) <= 1e-9 * scale) {
             xn = orc_cv_vib(sp, T_vib);
-        else
-            xn = (orc_e_vib(sp, Tc) - orc_e_vib(sp, T_vib)) / (Tc - T_vib);
+        } else {
+            double ec = orc_e_vib(sp, Tc), ev = orc_e_vib(sp, T_vib);
+            xn = (ec - ev) / (Tc - T_vib);
+            noise = 4.0 * 0x1p-52 * (fabs(ec) + fabs(ev)) / fabs(Tc - T_vib);
+        }
         double change = fabs(xn - x);
         x = xn;
-        if (change <= 1e-14 * fabs(xn)) break;
+        if (change <= 1e-14 * fabs(xn) || change <= noise) break;
     }
     o->t1_iters = it > 50 ? 50 : it;
     o->cv_T1 = x;

@@ -441,8 +441,9 @@ __device__ __forceinline__ void collision_numbers(const Species& s, const S& Ttr
 // Per-cell coefficients of Sec. 3.A: alpha = A^(1/3) (the real cube root,
 // negative when dt >= 2 mu / (p Pr)), nu, the gamma
 // coefficients with the implicit c_v,vib(T_1) (fixed point started at
-// c_v,vib(T_tr), relative tolerance 1e-14, at most 50 passes), and the
-// second-order energy targets.
+// c_v,vib(T_tr), relative tolerance 1e-14 or the secant's own rounding,
+// whichever is larger, at most 50 passes), and the second-order energy
+// targets.
 template <typename S>
 struct CellCoeffsT {
   S mu_p, Pr, A, B, alpha, nu_ref;
@@ -494,11 +495,19 @@ __device__ inline CellCoeffsT<S> cell_coeffs_t(const Species& s, const S& omega,
     const S idn = 1.0 / (ctr + gr * crot + gv * x);
     const S Tc = Ttr + (gr * crot * (Trot - Ttr) + gv * x * (Tvib - Ttr)) * idn;
     const S scale = fmax(fabs(Tc), fabs(Tvib));
-    const S xn = (fabs(Tc - Tvib) <= 1e-9 * scale) ? cv_vib_T<S>(s, Tvib)
-                                                    : (e_vib_T<S>(s, Tc) - evT) / (Tc - Tvib);
+    S xn;
+    double noise = 0.0;   // rounding of the secant (its numerator cancels near equilibrium)
+    if (fabs(Tc - Tvib) <= 1e-9 * scale) {
+      xn = cv_vib_T<S>(s, Tvib);
+    } else {
+      const S ec = e_vib_T<S>(s, Tc);
+      xn = (ec - evT) / (Tc - Tvib);
+      noise = 4.0 * 0x1p-52 * (::fabs((double)ec) + ::fabs((double)evT)) /
+              ::fabs((double)(Tc - Tvib));
+    }
     const S ch = fabs(xn - x);
     x = xn;
-    if (ch <= 1e-14 * fabs(xn)) break;
+    if (ch <= 1e-14 * fabs(xn) || ch <= noise) break;
   }
   const S idn = 1.0 / (ctr + gr * crot + gv * x);
   c.g_tr_rot = 2.0 * gr * ctr * crot * idn;
@@ -637,11 +646,17 @@ __device__ inline CellCoeffsF cell_coeffs_f32(const Species& s, double n, double
     const float idn = 1.0f / (ctr + gr * crot + gv * x);
     const float Tc = Ttr + (gr * crot * (Trot - Ttr) + gv * x * (Tvib - Ttr)) * idn;
     const float scale = fmaxf(fabsf(Tc), fabsf(Tvib));
-    const float xn = (fabsf(Tc - Tvib) <= 2e-3f * scale) ? cv(Tvib)
-                                                          : (evib(Tc) - evT) / (Tc - Tvib);
+    float xn, noise = 0.0f;   // rounding of the secant
+    if (fabsf(Tc - Tvib) <= 2e-3f * scale) {
+      xn = cv(Tvib);
+    } else {
+      const float ec = evib(Tc);
+      xn = (ec - evT) / (Tc - Tvib);
+      noise = 4.0f * 0x1p-23f * (fabsf(ec) + fabsf(evT)) / fabsf(Tc - Tvib);
+    }
     const float ch = fabsf(xn - x);
     x = xn;
-    if (ch <= 1e-6f * fabsf(xn)) break;
+    if (ch <= 1e-6f * fabsf(xn) || ch <= noise) break;
   }
   const float idn = 1.0f / (ctr + gr * crot + gv * x);
   c.g_tr_rot = 2.0f * gr * ctr * crot * idn;

@@ -215,6 +215,50 @@ def test_T1_iteration_near_equilibrium_stops_at_the_secant_rounding(delta):
         assert c.cv_T1 == pytest.approx(mid, rel=max(1e-12, 10 * (dT / T) ** 2) + noise / mid)
 
 
+def test_T1_iteration_never_cycles_near_equilibrium():
+    """4,000 seeded states near equilibrium (T_vib = T_tr (1 -+ d), d log-uniform
+    in [1e-9, 1e-1], T_rot within 1e-3 of T_tr): the rounded fixed-point map
+    of c_v,vib(T_1) can settle into a cycle whose step exceeds the 1e-14
+    relative tolerance (with that tolerance alone about 0.15 % of such states
+    ran all 50 passes); stopping at the secant's rounding ends every one within
+    a few passes, at the secant between T_check and T_vib within that rounding."""
+    sp = _sp()
+    rng = np.random.default_rng(7)
+    for _ in range(4000):
+        T = rng.uniform(2000.0, 20000.0)
+        d = 10.0 ** rng.uniform(-9, -1) * rng.choice([-1.0, 1.0])
+        Tv = T * (1.0 - d)
+        c = _coeffs(sp, T, T * (1.0 + rng.normal(0.0, 1e-3)), Tv)
+        assert c.t1_iters <= 6, (T, d, c.t1_iters)
+        dT = c.T_check - Tv
+        if abs(dT) > 1e-9 * max(abs(c.T_check), abs(Tv)):
+            ec, ev = O.e_vib(sp, c.T_check), O.e_vib(sp, Tv)
+            noise = 4 * 2.0 ** -52 * (abs(ec) + abs(ev)) / abs(dT)
+            assert abs(c.cv_T1 - (ec - ev) / dT) <= 3 * noise + 1e-14 * abs(c.cv_T1)
+
+
+def test_T1_cycle_pin_catches_the_tolerance_alone():
+    """The pin above discriminates: a copy of the oracle that stops on the
+    relative tolerance alone runs all 50 passes on some of the same states."""
+    import ctypes as C
+    src = O.source()
+    old = "if (change <= 1e-14 * fabs(xn) || change <= noise) break;"
+    assert old in src
+    L = O.load_variant(src.replace(old, "if (change <= 1e-14 * fabs(xn)) break;"), "plant_t1_tol")
+    sp = _sp()
+    rng = np.random.default_rng(7)
+    worst = 0
+    for _ in range(4000):
+        T = rng.uniform(2000.0, 20000.0)
+        d = 10.0 ** rng.uniform(-9, -1) * rng.choice([-1.0, 1.0])
+        Tr = T * (1.0 + rng.normal(0.0, 1e-3))
+        dt = 0.5 * O.tau_c(sp, 1e23, T)
+        cc = O.Coeffs()
+        assert L.orc_cell_coeffs(C.byref(sp), 1e23, dt, T, Tr, T * (1.0 - d), C.byref(cc)) == 0
+        worst = max(worst, cc.t1_iters)
+    assert worst == 50
+
+
 def _taylor_second_order(sp, c, T_tr, T_rot, T_vib, dt):
     """Second-order Taylor expansions of the energy relaxations from the
     moment production terms: Eqs. analytic_etr, and the e_rot / e_vib ones
