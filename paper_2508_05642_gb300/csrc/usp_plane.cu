@@ -74,12 +74,14 @@ struct PlGeomT {
   T x0, x1, y0, y1, dx, dy, cxc, cyc, cr, dt;
   T RTw, Tw, theta, Rth;   // R T_wall, T_wall, Theta_v, R Theta_v
   T idx, idy;              // 1 / dx, 1 / dy
+  T margin;                // 1e-5 of the domain's larger side
 };
 template <typename T>
 PlGeomT<T> geom_t(const PlGeom& g, const Species& sp) {
   return {(T)g.x0, (T)g.x1, (T)g.y0, (T)g.y1, (T)g.dx, (T)g.dy, (T)g.cxc, (T)g.cyc, (T)g.cr,
           (T)g.dt, (T)(sp.R * g.Tw), (T)g.Tw, (T)sp.theta_v, (T)(sp.R * sp.theta_v),
-          (T)(1.0 / g.dx), (T)(1.0 / g.dy)};
+          (T)(1.0 / g.dx), (T)(1.0 / g.dy),
+          (T)(1e-5 * std::max(g.x1 - g.x0, g.y1 - g.y0))};
 }
 
 // Refined grid (levels 2, 3), in device memory: per level-1 cell its first
@@ -211,19 +213,31 @@ __device__ bool plane_fly(const PlGeom& g, const PlGeomT<T>& gt, uint32_t pid, u
         ev = 0;
       }
     }
-    if (vx < T(0)) {
+    // a side's time is formed only when the side may be met by te: in FP32
+    // a particle whose straight move stops short of the side by more than a
+    // margin far above rounding cannot reach it (the FP64 form always forms
+    // the time)
+    auto may = [&](T pos, T v, T side, bool lower) {
+      if constexpr (sizeof(T) == 4) {
+        const T end = pos + v * te;
+        return lower ? end <= side + gt.margin : end >= side - gt.margin;
+      } else {
+        return true;
+      }
+    };
+    if (vx < T(0) && may(x, vx, gt.x0, true)) {
       const T t = (gt.x0 - x) / vx;
       if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 1; }
     }
-    if (vx > T(0)) {
+    if (vx > T(0) && may(x, vx, gt.x1, false)) {
       const T t = (gt.x1 - x) / vx;
       if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 2; }
     }
-    if (vy < T(0)) {
+    if (vy < T(0) && may(y, vy, gt.y0, true)) {
       const T t = (gt.y0 - y) / vy;
       if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 3; }
     }
-    if (vy > T(0)) {
+    if (vy > T(0) && may(y, vy, gt.y1, false)) {
       const T t = (gt.y1 - y) / vy;
       if (t <= te && (ev < 0 || t < te)) { te = t < T(0) ? T(0) : t; ev = 4; }
     }
