@@ -567,27 +567,37 @@ __global__ void pl_hist(const int* __restrict__ key, const PlCount* __restrict__
   __syncthreads();
   const long long n = cnt->ntot;
   const long long b = (long long)blockIdx.x * kChunk;
-  if (b < n) {
+  if (b >= n) return;   // uniform over the block: no keys, a column no one reads
+  {
+    // every key of the thread loaded first (the loads in flight together)
+    int kk[kRPT];
+#pragma unroll
     for (int r = 0; r < kRPT; ++r) {
       const long long i = b + (long long)r * kRB + threadIdx.x;
-      if (i < n) atomicAdd(&h[(key[i] >> shift) & (kNB - 1)], 1);
+      kk[r] = i < n ? key[i] : -1;
     }
+#pragma unroll
+    for (int r = 0; r < kRPT; ++r)
+      if (kk[r] >= 0) atomicAdd(&h[(kk[r] >> shift) & (kNB - 1)], 1);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < kNB; d += kRB) bh[(size_t)d * nblk + blockIdx.x] = h[d];
 }
 
-// one block per digit: exclusive scan over the blocks, digit total
-__global__ void pl_scan_digits(int* __restrict__ bh, int nblk, int* __restrict__ tot) {
+// one block per digit: exclusive scan over the blocks that hold keys (the
+// rest of the storage's blocks are empty and read by no one), digit total
+__global__ void pl_scan_digits(int* __restrict__ bh, int nblk, const PlCount* __restrict__ cnt,
+                               int* __restrict__ tot) {
   __shared__ int ws[kRB / 32];
   __shared__ int carry;
   const int d = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
   int* row = bh + (size_t)d * nblk;
+  const int nb = (int)min((long long)nblk, (cnt->ntot + kChunk - 1) / kChunk);
   if (t == 0) carry = 0;
   __syncthreads();
-  for (int b0 = 0; b0 < nblk; b0 += kRB) {
+  for (int b0 = 0; b0 < nb; b0 += kRB) {
     const int b = b0 + t;
-    const int c = b < nblk ? row[b] : 0;
+    const int c = b < nb ? row[b] : 0;
     int v = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -598,7 +608,7 @@ __global__ void pl_scan_digits(int* __restrict__ bh, int nblk, int* __restrict__
     __syncthreads();
     int pre = 0;
     for (int k = 0; k < w; ++k) pre += ws[k];
-    if (b < nblk) row[b] = carry + pre + v - c;
+    if (b < nb) row[b] = carry + pre + v - c;
     __syncthreads();
     if (t == 0) {
       int sum = 0;
@@ -647,32 +657,45 @@ __global__ void pl_scatter(const int* __restrict__ kin, const int* __restrict__ 
     pre += loc[q];
   }
   __syncthreads();
-  for (int r = 0; r < kRPT; ++r) {
-    for (int q = 0; q < kRB / 32; ++q)
-      for (int d = t; d < kNB; d += kRB) cntw[q][d] = 0;
-    __syncthreads();
+  // per round of kRB keys: each warp's count of every digit it holds (set by
+  // the digit's first lane, cleared by it after use, so only the touched
+  // entries change), the position from the digit's run and the counts of
+  // the earlier warps, then the run advanced by each warp's count.  The keys
+  // and indices of a round are loaded two rounds ahead.
+  for (int q = 0; q < kRB / 32; ++q)
+    for (int d = t; d < kNB; d += kRB) cntw[q][d] = 0;
+  auto load = [&](int r, int& k_, int& i_) {
     const long long i = b + (long long)r * kRB + t;
-    const bool valid = i < n;
-    const int kk = valid ? kin[i] : 0;
-    const int d = valid ? ((kk >> shift) & (kNB - 1)) : kNB;
+    if (r < kRPT && i < n) { k_ = kin[i]; i_ = iin[i]; }
+  };
+  int k0 = 0, i0 = 0, k1 = 0, i1 = 0;
+  load(0, k0, i0);
+  load(1, k1, i1);
+  __syncthreads();
+  for (int r = 0; r < kRPT; ++r) {
+    int k2 = 0, i2 = 0;
+    load(r + 2, k2, i2);
+    const bool valid = b + (long long)r * kRB + t < n;
+    const int d = valid ? ((k0 >> shift) & (kNB - 1)) : kNB;
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & lane_lt());
-    if (valid && rank == 0) cntw[w][d] = __popc(peers);
+    const bool lead = valid && rank == 0;
+    if (lead) cntw[w][d] = __popc(peers);
     __syncthreads();
     if (valid) {
       int p = 0;
       for (int q = 0; q < w; ++q) p += cntw[q][d];
       const int pos = run[d] + p + rank;
-      kout[pos] = kk;
-      iout[pos] = iin[i];
+      kout[pos] = k0;
+      iout[pos] = i0;
     }
     __syncthreads();
-    for (int dd = t; dd < kNB; dd += kRB) {
-      int sum = 0;
-      for (int q = 0; q < kRB / 32; ++q) sum += cntw[q][dd];
-      run[dd] += sum;
+    if (lead) {
+      atomicAdd(&run[d], cntw[w][d]);
+      cntw[w][d] = 0;
     }
-    __syncthreads();
+    __syncwarp();
+    k0 = k1; i0 = i1; k1 = k2; i1 = i2;
   }
 }
 
@@ -1481,7 +1504,7 @@ int pl_step_t(PlaneCtx* h, const ChEnv& env, ch_prof_fn prof) {
   int src = 0;
   for (int p = 0; p < h->passes; ++p) {
     pl_hist<<<h->nblk, kRB, 0, s>>>(h->kbuf[src], h->cnt, kDig * p, h->bh, h->nblk);
-    pl_scan_digits<<<kNB, kRB, 0, s>>>(h->bh, h->nblk, h->tot);
+    pl_scan_digits<<<kNB, kRB, 0, s>>>(h->bh, h->nblk, h->cnt, h->tot);
     pl_scatter<<<h->nblk, kRB, 0, s>>>(h->kbuf[src], h->ibuf[src], h->kbuf[src ^ 1],
                                        h->ibuf[src ^ 1], h->cnt, kDig * p, h->bh, h->tot, h->nblk);
     CHK(cudaGetLastError());
