@@ -440,7 +440,7 @@ int usp_info(usp_ctx* ctx, int64_t* n_particles, int* n_cells, int* precision, i
 
 /* Particle-pass variant of a homogeneous context: its design (*warp_tiles =
  * 1: every warp pipelines its own tiles of <= 128 particles; 0: a block
- * stages tiles of <= 1024 particles shared by its 256 threads), the resident
+ * stages tiles of <= 1536 particles shared by its 256 threads), the resident
  * blocks per SM its register budget targets (2, 3 or 4), and the autotuner's
  * milliseconds per launch of each variant on the whole state, ordered
  * block-tiled 2, 3, 4 then warp-tiled 2, 3, 4 (zeros when the tuner did not

@@ -396,7 +396,7 @@ __global__ void wait_check_kernel(long long limit, uint32_t* flags) {
   if (!ok && threadIdx.x == 0) atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
 }
 
-constexpr int kTileMax = 1024;   // particles per staged tile
+constexpr int kTileMax = 1536;   // particles per staged tile
 
 // One staging buffer: x, y, z, eps (kTileMax T each) then levels (kTileMax int).
 template <typename T>
