@@ -397,6 +397,7 @@ __global__ void wait_check_kernel(long long limit, uint32_t* flags) {
 }
 
 constexpr int kTileMax = 1536;   // particles per staged tile
+constexpr int kBS = 2;           // staging buffers of the block-tiled pass
 
 // One staging buffer: x, y, z, eps (kTileMax T each) then levels (kTileMax int).
 template <typename T>
@@ -617,7 +618,7 @@ collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
 // of the tile list (tiles of one cell are adjacent, so a block meets few cell
 // boundaries); each tile (<= kTileMax particles of one cell) and its cell's
 // CollideParams are brought into shared memory by bulk copies while the
-// previous tile is being processed (two buffers), updated in place, and
+// previous tile is being processed (kBS buffers), updated in place, and
 // written back by bulk copies.  The block's warps share each tile but never
 // wait for one another: a warp that finishes its part of a tile counts itself
 // done; the last one issues the tile's bulk store and, once the store has
@@ -668,26 +669,30 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
                unsigned long long* counters, const PhiloxRoundKeys rk,
                const JumpTabs tabs, long long wait_cycles) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[2], empty[2];
-  __shared__ int done[2];
+  __shared__ __align__(8) uint64_t full[kBS], empty[kBS];
+  __shared__ int done[kBS];
   const int tid = threadIdx.x, lane = tid & 31;
   const int G = gridDim.x;
   const int t_begin = (int)(((long long)ntiles * blockIdx.x) / G);
   const int t_end = (int)(((long long)ntiles * (blockIdx.x + 1)) / G);
   if (t_begin >= t_end) return;
   if (tid == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
-    mbar_init(&empty[0], 1);
-    mbar_init(&empty[1], 1);
-    done[0] = done[1] = 0;
+    for (int q = 0; q < kBS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+      done[q] = 0;
+    }
     mbar_init_fence();
   }
   __syncthreads();
   uint32_t inflight = 0;   // thread 0: buffers with a load in flight
   if (tid == 0) {
-    stage_load_p<T>(tiles[t_begin], prm, smem, &full[0], cx, cy, cz, er, lev);
-    inflight = 1u;
+    // the first kBS - 1 tiles
+    for (int q = 0; q < kBS - 1 && t_begin + q < t_end; ++q) {
+      stage_load_p<T>(tiles[t_begin + q], prm, smem + q * bstage_bytes<T>(), &full[q], cx, cy, cz,
+                      er, lev);
+      inflight |= 1u << q;
+    }
   }
   uint32_t fph = 0, eph = 0;   // parities of the next full / empty completion per buffer
   T acc[10];
@@ -697,21 +702,22 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
   uint32_t fl = 0;
   int npb = 0;
   int it = 0;
-  for (int t = t_begin; t < t_end; ++t, ++it) {
-    const int b = it & 1;
+  int b = 0;   // buffer of tile t: it % kBS
+  for (int t = t_begin; t < t_end; ++t, ++it, b = b == kBS - 1 ? 0 : b + 1) {
     unsigned char* buf = smem + b * bstage_bytes<T>();
-    if (tid == 0 && t + 1 < t_end) {
-      // the other buffer takes tile t + 1 once every warp is done with tile
-      // t - 1 there and its store has read it
+    const int bn = b == 0 ? kBS - 1 : b - 1;   // the buffer of tile t - 1
+    if (tid == 0 && t + kBS - 1 < t_end) {
+      // tile t - 1's buffer takes tile t + kBS - 1 once every warp is done
+      // with tile t - 1 there and its store has read it
       bool ok = true;
       if (it >= 1) {
-        ok = mbar_wait_bounded(&empty[b ^ 1], (eph >> (b ^ 1)) & 1u, wait_cycles);
-        eph ^= 1u << (b ^ 1);
+        ok = mbar_wait_bounded(&empty[bn], (eph >> bn) & 1u, wait_cycles);
+        eph ^= 1u << bn;
       }
       if (ok) {
-        stage_load_p<T>(tiles[t + 1], prm, smem + (b ^ 1) * bstage_bytes<T>(), &full[b ^ 1], cx,
-                        cy, cz, er, lev);
-        inflight |= 1u << (b ^ 1);
+        stage_load_p<T>(tiles[t + kBS - 1], prm, smem + bn * bstage_bytes<T>(), &full[bn], cx, cy,
+                        cz, er, lev);
+        inflight |= 1u << bn;
       } else {
         atomicOr(flags, (uint32_t)F_WAIT_TIMEOUT);
       }
@@ -792,7 +798,7 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
   if (tid == 0) {
     // loads still in flight after a timeout: wait for them (bounded) before
     // the block's shared memory is released
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < kBS; ++q)
       if (inflight & (1u << q)) (void)mbar_wait_bounded(&full[q], (fph >> q) & 1u, kWaitCycles);
   }
 }
@@ -1595,7 +1601,7 @@ void* collide_variant(int warp_tiles, int minb, int method) {
 
 template <typename T>
 size_t collide_smem(int warp_tiles) {
-  return warp_tiles ? wsmem_bytes<T>() : 2 * bstage_bytes<T>();
+  return warp_tiles ? wsmem_bytes<T>() : kBS * bstage_bytes<T>();
 }
 
 // A run of consecutive cells [c0, c1) and its tiles in either tile list.
