@@ -152,15 +152,19 @@ __device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
 // relative error near 2^-22 elsewhere: far below the 2^-24 resolution of the
 // uniforms' effect on the normals' distribution), and evaluates the angle on
 // (-pi, pi), where the hardware sine/cosine has an absolute error below 2^-21:
-// cos(2 pi u) = -cos(2 pi u - pi), sin(2 pi u) = -sin(2 pi u - pi).
-__device__ __forceinline__ void box_muller(float ua, float ub, float& ga, float& gb) {
+// cos(2 pi u) = -cos(2 pi u - pi), sin(2 pi u) = -sin(2 pi u - pi).  The
+// centred form takes uc = u_b - 1/2 directly.
+__device__ __forceinline__ void box_muller_centred(float ua, float uc, float& ga, float& gb) {
   float l2;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l2) : "f"(ua));
   const float rad = sqrt_fast(fmaxf(-1.38629436111989061883f * l2, 0.0f));
   float s, c;
-  __sincosf(6.28318530717958647692f * (ub - 0.5f), &s, &c);
+  __sincosf(6.28318530717958647692f * uc, &s, &c);
   ga = -rad * c;
   gb = -rad * s;
+}
+__device__ __forceinline__ void box_muller(float ua, float ub, float& ga, float& gb) {
+  box_muller_centred(ua, ub - 0.5f, ga, gb);
 }
 __device__ __forceinline__ void box_muller(double ua, double ub, double& ga, double& gb) {
   const double rad = sqrt(-2.0 * log(ua));
@@ -185,10 +189,12 @@ __device__ __forceinline__ void box_muller(double ua, double ub, double& ga, dou
 __device__ __forceinline__ uint32_t angle_bits18(uint32_t wa, uint32_t wb) {
   return ((wa & 0x1ffu) << 9) | (wb & 0x1ffu);
 }
-__device__ __forceinline__ float angle_uniform18(uint32_t wa, uint32_t wb) {
-  // 1 + a 2^-18 minus 1 - 2^-19: exactly (2 a + 1) 2^-19 (Sterbenz)
+// the angle uniform minus 1/2: 1 + a 2^-18 minus 3/2 - 2^-19 is exactly
+// (2 a + 1) 2^-19 - 1/2 (Sterbenz), the value that (2 a + 1) 2^-19 - 1/2
+// rounds to as well, in one subtraction
+__device__ __forceinline__ float angle_centred18(uint32_t wa, uint32_t wb) {
   return __fsub_rn(__int_as_float((int)(0x3f800000u | (angle_bits18(wa, wb) << 5))),
-                   0.99999809265136718750f);
+                   1.49999809265136718750f);
 }
 __device__ __forceinline__ double angle_uniform18_d(uint32_t wa, uint32_t wb) {
   return (2.0 * (double)angle_bits18(wa, wb) + 1.0) * 1.9073486328125e-06;   // 2^-19
@@ -208,8 +214,8 @@ __device__ __forceinline__ void particle_draws(uint32_t pid, uint32_t step,
                                                const PhiloxRoundKeys& rk, float& g0, float& g1,
                                                float& g2, float& g3, uint32_t& j5, uint32_t& j6) {
   const U4 w = philox4x32_10(pid, step, PTAG_NORMALS, 0u, rk);
-  box_muller(uniform_open<float>(w.x), angle_uniform18(w.x, w.y), g0, g1);
-  box_muller(uniform_open<float>(w.y), angle_uniform18(w.z, w.w), g2, g3);
+  box_muller_centred(uniform_open<float>(w.x), angle_centred18(w.x, w.y), g0, g1);
+  box_muller_centred(uniform_open<float>(w.y), angle_centred18(w.z, w.w), g2, g3);
   j5 = w.z;
   j6 = w.w;
 }

@@ -179,10 +179,15 @@ constexpr int kGBits = 8;             // guide bins per row: 2^kGBits
 constexpr int kGB = 1 << kGBits;      // guide bytes per row
 constexpr int kGS = 23 - kGBits;      // 23-bit uniform index -> bin: >> kGS
 
-// number of leading row entries <= u, u formed from the word x
-__device__ __forceinline__ int guided_search(const float* __restrict__ T,
-                                             const uint8_t* __restrict__ g, uint32_t x, float u) {
-  const unsigned gv = __ldg(g + (x >> (32 - kGBits)));
+// the guide byte of the word x's bin in the guide g of a row
+__device__ __forceinline__ unsigned guide_byte(const uint8_t* __restrict__ g, uint32_t x) {
+  return __ldg(g + (x >> (32 - kGBits)));
+}
+
+// number of leading row entries <= u, from the guide byte gv of u's bin: an
+// exact bin inside the row (bit 7 set, k < kJK) answers on one comparison
+__device__ __forceinline__ int guided_search(const float* __restrict__ T, unsigned gv, float u) {
+  if (gv - 0x80u < (unsigned)kJK) return (int)(gv - 0x80u);
   int k = (int)(gv & 0x7fu);
   if (!(gv & 0x80u)) {
 #pragma unroll 1
@@ -191,24 +196,28 @@ __device__ __forceinline__ int guided_search(const float* __restrict__ T,
   return k;
 }
 
-__device__ __forceinline__ int nb_tab(const float* __restrict__ T, const uint8_t* __restrict__ g,
-                                      int r, float p, float u, uint32_t x, uint32_t& fl) {
+__device__ __forceinline__ int nb_tab(const float* __restrict__ T, unsigned gv, int r, float p,
+                                      float u, uint32_t& fl) {
   if (r <= 0 || !(p < 1.0f)) return 0;
   if (r > kJR) return nb_inv(r, p, u, fl);
-  const int k = guided_search(T, g, x, u);
+  const int k = guided_search(T, gv, u);
   return k < kJK ? k : nb_inv(r, p, u, fl);
 }
 
-__device__ __forceinline__ int b_tab(const float* __restrict__ T, const uint8_t* __restrict__ g,
-                                     int n, float p, float u, uint32_t x, uint32_t& fl) {
+// npb counts the draws clamped at p_B > 1
+__device__ __forceinline__ int b_tab(const float* __restrict__ T, unsigned gv, int n, float p,
+                                     float u, uint32_t& fl, int& npb) {
   if (n <= 0) return 0;
   if (p >= 1.0f) {
-    if (p > 1.0f) fl |= F_PB_CLAMP;
+    if (p > 1.0f) {
+      fl |= F_PB_CLAMP;
+      ++npb;
+    }
     return n;
   }
   if (!(p > 0.0f)) return 0;
   const bool flip = p > 0.5f;
-  int k = n < kJR ? guided_search(T, g, x, u) : kJK;   // T[n] = +inf: k <= n < kJK
+  int k = n < kJR ? guided_search(T, gv, u) : kJK;   // T[n] = +inf: k <= n < kJK
   if (k >= kJK) k = binv(n, flip ? rn_sub(1.0f, p) : p, u, fl);
   return flip ? n - k : k;
 }
@@ -222,18 +231,31 @@ struct JumpTabs {
 };
 
 // ---------------------------------------------------------------------------
-// One particle: pending rescale, velocity, rotation, vibration.
+// One particle: pending rescale, velocity, rotation, vibration.  Flags go
+// into fl, draws clamped at p_B > 1 are counted in npb.
 // ---------------------------------------------------------------------------
 template <typename T, int METHOD>
 __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t pid,
                                             const PhiloxRoundKeys& rk, T& cx, T& cy, T& cz, T& er,
                                             int& lv,
-                                            T* acc, int& accI, int& maxI, uint32_t& fl,
+                                            T* acc, int& accI, int& maxI, uint32_t& fl, int& npb,
                                             const JumpTabs& jt) {
-  const int I = lv;
+  // levels are non-negative; a negative one (invalid input) is taken as 0,
+  // which also keeps the particle's table row in range
+  const int I = max(lv, 0);
   T g0, g1, g2, g3;
   uint32_t j5, j6;
   particle_draws(pid, P.step, rk, g0, g1, g2, g3, j5, j6);
+  // FP32 form: the guide bytes of the particle's two rows (NB r = I + 1 is
+  // row I, binomial n = I is row I) are loaded here, so that their latency
+  // passes under the arithmetic below
+  size_t row = 0;
+  unsigned gv5 = 0, gv6 = 0;
+  if constexpr (sizeof(T) == 4 && METHOD == 0) {
+    row = (size_t)(I < kJR ? I : 0);
+    gv5 = guide_byte(jt.gnb + row * kGB, j5);
+    gv6 = guide_byte(jt.gb + row * kGB, j6);
+  }
   // c^n - U = s (c* - U*);  C' = alpha C^n + sqrt(1 - alpha^2) L G
   const T d0 = cx - P.Us[0], d1 = cy - P.Us[1], d2 = cz - P.Us[2];
   const T r0 = P.as * d0 + P.Lp[0] * g0;
@@ -249,17 +271,21 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   const T u5 = jump_uniform<T>(j5), u6 = jump_uniform<T>(j6);
   if constexpr (METHOD == 1) {
     // plain FPM method: Gillespie's direct method (Sec. 2.C)
-    lv = gillespie<T>(I, P.p_nb, P.p_b, pid, P.step, rk, fl);
+    uint32_t f1 = 0;
+    lv = gillespie<T>(I, P.p_nb, P.p_b, pid, P.step, rk, f1);
+    npb += (f1 & F_PB_CLAMP) ? 1 : 0;
+    fl |= f1;
   } else {
     int up, dn;
     if constexpr (sizeof(T) == 4) {
-      // the particle's rows: NB r = I + 1 is row I, binomial n = I is row I
-      const size_t row = (size_t)(I < kJR ? I : 0);
-      up = nb_tab(jt.nb + row * kJK, jt.gnb + row * kGB, I + 1, P.p_nb, u5, j5, fl);
-      dn = b_tab(jt.b + row * kJK, jt.gb + row * kGB, I, P.p_b, u6, j6, fl);
+      up = nb_tab(jt.nb + row * kJK, gv5, I + 1, P.p_nb, u5, fl);
+      dn = b_tab(jt.b + row * kJK, gv6, I, P.p_b, u6, fl, npb);
     } else {
-      up = sample_nb<T>(I + 1, P.p_nb, u5, fl);
-      dn = sample_b<T>(I, P.p_b, u6, fl);
+      uint32_t f1 = 0;
+      up = sample_nb<T>(I + 1, P.p_nb, u5, f1);
+      dn = sample_b<T>(I, P.p_b, u6, f1);
+      npb += (f1 & F_PB_CLAMP) ? 1 : 0;
+      fl |= f1;
     }
     lv = I + up - dn;
   }
@@ -550,12 +576,10 @@ collide_warp_kernel(const Tile* __restrict__ tiles, int ntiles,
       for (int k = lane; k < tl.count; k += 32) {
         T x = X[k], y = X[k + kWT], z = X[k + 2 * kWT], e = X[k + 3 * kWT];
         int l = Lv[k];
-        uint32_t f1 = 0;
-        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, jt);
+        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, fl, npb,
+                               jt);
         X[k] = x; X[k + kWT] = y; X[k + 2 * kWT] = z; X[k + 3 * kWT] = e;
         Lv[k] = l;
-        npb += (f1 & F_PB_CLAMP) ? 1 : 0;
-        fl |= f1;
       }
       // results in shared memory -> visible to the bulk-copy engine
       fence_async_smem();
@@ -743,12 +767,10 @@ collide_kernel(const Tile* __restrict__ tiles, int ntiles,
       for (int k = tid; k < tl.count; k += kBlock) {
         T x = X[k], y = X[k + kTileMax], z = X[k + 2 * kTileMax], e = X[k + 3 * kTileMax];
         int l = Lv[k];
-        uint32_t f1 = 0;
-        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, f1, jt);
+        collide_one<T, METHOD>(P, pid0 + (uint32_t)k, rk, x, y, z, e, l, acc, accI, maxI, fl, npb,
+                               jt);
         X[k] = x; X[k + kTileMax] = y; X[k + 2 * kTileMax] = z; X[k + 3 * kTileMax] = e;
         Lv[k] = l;
-        npb += (f1 & F_PB_CLAMP) ? 1 : 0;
-        fl |= f1;
       }
     }
     // this warp's results -> visible to the bulk-copy engine; count it done
