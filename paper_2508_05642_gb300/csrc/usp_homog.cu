@@ -169,12 +169,17 @@ __device__ void b_row(int n, float p, float* T) {
 // each of the 256 bins of the uniform's top eight bits.  A float uniform
 // (2 (x >> 9) + 1) 2^-24 lies in bin m = x >> 24, between
 // umin(m) = (2 (m << 15) + 1) 2^-24 and umax(m) = (2 ((m << 15) + 32767) + 1) 2^-24.
-// The byte holds k = the number of row entries <= umin(m), with bit 7 set when
-// no entry lies in (umin(m), umax(m)], so that every uniform of the bin gives
-// exactly k; otherwise the search continues from k.  The outcome is the row
-// search's, so still the sequential inversion's, bit for bit.  A row whose
-// P(0) underflowed (T[0] = -1) gets 0xff bytes: k = 127 sends the particle to
-// the sequential search.
+// With k = the number of row entries <= umin(m): when no entry lies in
+// (umin(m), umax(m)], every uniform of the bin gives k, and the byte holds
+// bit 7 and the sampler's outcome for that k (k; n - k for a binomial row
+// taken at 1 - p_B, p_B > 1/2); otherwise it holds k, from which the search
+// continues.  An outcome k = kJK (past the row) or a row whose P(0)
+// underflowed (0xff bytes) sends the particle to the sequential search.  The
+// rows a cell's parameters make trivial hold their outcome in every byte:
+// 0 for an NB row at p_NB >= 1 and for the binomial rows n = 0 and p_B <= 0,
+// n at p_B = 1, and 0x7f (the general path, which flags the clamp) at
+// p_B > 1.  The outcome is the row search's, so still the sequential
+// inversion's, bit for bit.
 constexpr int kGBits = 8;             // guide bins per row: 2^kGBits
 constexpr int kGB = 1 << kGBits;      // guide bytes per row
 constexpr int kGS = 23 - kGBits;      // 23-bit uniform index -> bin: >> kGS
@@ -183,11 +188,11 @@ constexpr int kGS = 23 - kGBits;      // 23-bit uniform index -> bin: >> kGS
 __device__ __forceinline__ unsigned guide_byte(const uint8_t* __restrict__ g, uint32_t x) {
   return __ldg(g + (x >> (32 - kGBits)));
 }
+// the outcome an exact guide byte holds (>= kJK: none)
+__device__ __forceinline__ unsigned guide_outcome(unsigned gv) { return gv - 0x80u; }
 
-// number of leading row entries <= u, from the guide byte gv of u's bin: an
-// exact bin inside the row (bit 7 set, k < kJK) answers on one comparison
+// number of leading row entries <= u for a guide byte without an outcome
 __device__ __forceinline__ int guided_search(const float* __restrict__ T, unsigned gv, float u) {
-  if (gv - 0x80u < (unsigned)kJK) return (int)(gv - 0x80u);
   int k = (int)(gv & 0x7fu);
   if (!(gv & 0x80u)) {
 #pragma unroll 1
@@ -196,10 +201,12 @@ __device__ __forceinline__ int guided_search(const float* __restrict__ T, unsign
   return k;
 }
 
+// The general path of the two samplers (the guide byte of u's bin gv)
 __device__ __forceinline__ int nb_tab(const float* __restrict__ T, unsigned gv, int r, float p,
                                       float u, uint32_t& fl) {
   if (r <= 0 || !(p < 1.0f)) return 0;
   if (r > kJR) return nb_inv(r, p, u, fl);
+  if (guide_outcome(gv) < (unsigned)kJK) return (int)guide_outcome(gv);
   const int k = guided_search(T, gv, u);
   return k < kJK ? k : nb_inv(r, p, u, fl);
 }
@@ -217,8 +224,12 @@ __device__ __forceinline__ int b_tab(const float* __restrict__ T, unsigned gv, i
   }
   if (!(p > 0.0f)) return 0;
   const bool flip = p > 0.5f;
-  int k = n < kJR ? guided_search(T, gv, u) : kJK;   // T[n] = +inf: k <= n < kJK
-  if (k >= kJK) k = binv(n, flip ? rn_sub(1.0f, p) : p, u, fl);
+  if (n < kJR) {
+    if (guide_outcome(gv) < (unsigned)kJK) return (int)guide_outcome(gv);
+    const int k = guided_search(T, gv, u);   // T[n] = +inf: k <= n < kJK
+    if (k < kJK) return flip ? n - k : k;
+  }
+  const int k = binv(n, flip ? rn_sub(1.0f, p) : p, u, fl);
   return flip ? n - k : k;
 }
 
@@ -278,8 +289,16 @@ __device__ __forceinline__ void collide_one(const CollideParams<T>& P, uint32_t 
   } else {
     int up, dn;
     if constexpr (sizeof(T) == 4) {
-      up = nb_tab(jt.nb + row * kJK, gv5, I + 1, P.p_nb, u5, fl);
-      dn = b_tab(jt.b + row * kJK, gv6, I, P.p_b, u6, fl, npb);
+      // both guide bytes hold their outcome (every cell case included):
+      // one test decides the jump
+      const unsigned o5 = guide_outcome(gv5), o6 = guide_outcome(gv6);
+      if ((I < kJR) & (o5 < (unsigned)kJK) & (o6 < (unsigned)kJK)) {
+        up = (int)o5;
+        dn = (int)o6;
+      } else {
+        up = nb_tab(jt.nb + row * kJK, gv5, I + 1, P.p_nb, u5, fl);
+        dn = b_tab(jt.b + row * kJK, gv6, I, P.p_b, u6, fl, npb);
+      }
     } else {
       uint32_t f1 = 0;
       up = sample_nb<T>(I + 1, P.p_nb, u5, f1);
@@ -840,13 +859,20 @@ __device__ __forceinline__ bool b_row_used(int n, int rows, float p_b) {
 }
 
 // bins [q kQ, (q + 1) kQ) of the guide of row T (the guide tables above),
-// kQ = kGB / kGP
+// kQ = kGB / kGP; nflip = n for a binomial row taken at 1 - p_B (exact bytes
+// hold n - k), else -1
 constexpr int kGP = 4;   // threads per guide row
-__device__ void guide_part(const float* T, uint8_t* __restrict__ g, int q) {
+__device__ void guide_fill(uint8_t* __restrict__ g, int q, uint32_t byte) {
+  uint32_t* g4 = reinterpret_cast<uint32_t*>(g);
+  constexpr int kQ = kGB / kGP;
+  const uint32_t word = byte * 0x01010101u;
+  for (int w = q * kQ / 4; w < (q + 1) * kQ / 4; ++w) g4[w] = word;
+}
+__device__ void guide_part(const float* T, uint8_t* __restrict__ g, int q, int nflip) {
   uint32_t* g4 = reinterpret_cast<uint32_t*>(g);
   constexpr int kQ = kGB / kGP;
   if (T[0] < 0.0f) {
-    for (int w = q * kQ / 4; w < (q + 1) * kQ / 4; ++w) g4[w] = 0xffffffffu;
+    guide_fill(g, q, 0xffu);
     return;
   }
   int k = 0;
@@ -860,7 +886,8 @@ __device__ void guide_part(const float* T, uint8_t* __restrict__ g, int q) {
       const float umax = (float)(2 * ((m << kGS) + (1 << kGS) - 1) + 1) * 5.9604644775390625e-8f;
       while (k < kJK && T[k] <= umin) ++k;
       const bool exact = k >= kJK || T[k] > umax;
-      word |= (uint32_t)(k | (exact ? 0x80 : 0)) << (8 * b);
+      const int o = exact && k < kJK && nflip >= 0 ? nflip - k : k;
+      word |= (uint32_t)(o | (exact ? 0x80 : 0)) << (8 * b);
     }
     g4[w] = word;
   }
@@ -897,11 +924,21 @@ jumptable_kernel(int c0, int c1, const CollideParams<float>* __restrict__ prm,
   static_assert(2 * kJR * kGP == kJT, "one guide part per thread");
   const int row = j / kGP, q = j % kGP;      // 2 kJR rows, kGP parts each
   if (row < kJR) {
+    uint8_t* g = gd_nb + ((size_t)c * kJR + row) * kGB;
     if (nb_row_used(row, rows, P.p_nb))
-      guide_part(rs[0][row], gd_nb + ((size_t)c * kJR + row) * kGB, q);
+      guide_part(rs[0][row], g, q, -1);
+    else if (row < rows)
+      guide_fill(g, q, 0x80u);              // p_NB >= 1: no jump up
   } else {
     const int n = row - kJR;
-    if (b_row_used(n, rows, P.p_b)) guide_part(rs[1][n], gd_b + ((size_t)c * kJR + n) * kGB, q);
+    uint8_t* g = gd_b + ((size_t)c * kJR + n) * kGB;
+    const float p = P.p_b;
+    if (b_row_used(n, rows, p))
+      guide_part(rs[1][n], g, q, p > 0.5f ? n : -1);
+    else if (n < rows)
+      // n = 0 or p_B <= 0: no jump down; p_B = 1: n; p_B > 1: the general
+      // path, which flags the clamp
+      guide_fill(g, q, n >= 1 && p >= 1.0f ? (p > 1.0f ? 0x7fu : 0x80u | (uint32_t)n) : 0x80u);
   }
 }
 

@@ -259,6 +259,32 @@ def test_pb_clamp_flag_matches_oracle():
     assert np.mean(r["gs"][4] != r["ost"].lev) < 1e-5
 
 
+@pytest.mark.parametrize("f, lo, hi", [(0.3, 0.5, 1.0), (0.97, 1.0, 10.0)])
+def test_fp32_flipped_and_clamped_binomial_match_oracle(f, lo, hi):
+    """FP32 table path at p_B above 1/2 (the binomial row taken at 1 - p_B,
+    outcome n - k, Sec. 3.A.2) and above 1 (clamped to n and counted): the
+    levels equal the oracle's float-decision levels and the clamp counts
+    agree.  The time step sets 1 - alpha^2 (alpha -> 0 as Pr dt -> 2 mu/p);
+    p_B = (1 + ebar)(1 - alpha^2) at the equilibrium ebar of 6000 K."""
+    T = 6000.0
+    w = I.homogeneous_single(N=30000, T_tr=T, T_rot=T, T_vib=T, steps=1)
+    sp = O.species(**w.species)
+    n = float(w.ndens[0])
+    mu_p = O.mu(sp, T) / (n * 1.380649e-23 * T)
+    w.dt_over_tau_c = f * 2 * mu_p / O.prandtl(sp, T) / O.tau_c(sp, n, T)
+    cc = O.cell_coeffs(sp, n, w.dt_over_tau_c * O.tau_c(sp, n, T), T, T, T)
+    p_b = (1.0 + 1.0 / math.expm1(sp.theta_v / T)) * (1.0 - cc.alpha ** 2)
+    assert lo < p_b < hi
+    r = _run_pair(w, 1, usp.USP_FP32)
+    assert np.mean(r["gs"][4] != r["ost"].lev) < 1e-5
+    assert r["gcnt"][usp.C_PB_CLAMP] == r["ocnt"][O.C_PB_CLAMP]
+    if hi > 1.0 + 1e-9 and lo >= 1.0:
+        assert r["gfl"] & usp.F_PB_CLAMP and r["ocnt"][O.C_PB_CLAMP] > 0
+    else:
+        assert r["ocnt"][O.C_PB_CLAMP] == 0
+    _check_moments(r["om"], r["gm"], r["sp"])
+
+
 def test_torch_allocator_path():
     torch = pytest.importorskip("torch")
     w = I.batched_instances(seed=14, n_inst=4, nmin=500, nmax=2000, steps=0)
