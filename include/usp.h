@@ -431,6 +431,19 @@ int usp_set_wait_limit(usp_ctx* ctx, int64_t cycles);
  * USP_EINVAL for cycles out of range. */
 int usp_wait_check(usp_ctx* ctx, int64_t cycles);
 
+/* The guide of one jump-table row as the FP32 form builds it (Chen & Asau's
+ * indexed search over the row of Eq. update_evib's inversion; host code, no
+ * GPU).  row: 48 float cumulative values, non-decreasing, +inf after the
+ * last one (row[0] = -1 marks an underflowed P(0)).  guide: 256 bytes out,
+ * one per bin of a 23-bit uniform's top eight bits; with k the number of row
+ * entries <= the bin's smallest uniform: bit 7 and the outcome (k, or
+ * n_flip - k for a binomial row taken at 1 - p_B when n_flip >= 0) when no
+ * entry lies inside the bin; else k (the search continues from there).
+ * n_flip: -1, or the binomial n (0 .. 31), whose row ends at n
+ * (row[n_flip] = +inf).  USP_EINVAL for NULL pointers, n_flip out of range
+ * or a flipped row that does not end at n. */
+int usp_guide_row(const float* row, int n_flip, uint8_t* guide);
+
 /* Wait for all work of the context. */
 int usp_sync(usp_ctx* ctx);
 

@@ -192,6 +192,7 @@ __device__ __forceinline__ unsigned guide_byte(const uint8_t* __restrict__ g, ui
 __device__ __forceinline__ unsigned guide_outcome(unsigned gv) { return gv - 0x80u; }
 
 // number of leading row entries <= u for a guide byte without an outcome
+// below kJK (an exact byte here sends the particle to the sequential search)
 __device__ __forceinline__ int guided_search(const float* __restrict__ T, unsigned gv, float u) {
   int k = (int)(gv & 0x7fu);
   if (!(gv & 0x80u)) {
@@ -860,34 +861,52 @@ __device__ __forceinline__ bool b_row_used(int n, int rows, float p_b) {
 
 // bins [q kQ, (q + 1) kQ) of the guide of row T (the guide tables above),
 // kQ = kGB / kGP; nflip = n for a binomial row taken at 1 - p_B (exact bytes
-// hold n - k), else -1
+// hold n - k), else -1.  The bounds of bin m are exact floats formed by one
+// fused multiply-add each: umin(m) = m 2^-kGBits + 2^-24 and
+// umax(m) = (m + 1) 2^-kGBits - 2^-24.  Four bins that no row entry reaches
+// (the next entry above umin lies above the fourth bin's umax) are exact at
+// the same count and written as one word.
 constexpr int kGP = 4;   // threads per guide row
-__device__ void guide_fill(uint8_t* __restrict__ g, int q, uint32_t byte) {
+constexpr int kGQ = kGB / kGP;   // bins per guide part
+__host__ __device__ inline void guide_fill(uint8_t* __restrict__ g, int q, uint32_t byte) {
   uint32_t* g4 = reinterpret_cast<uint32_t*>(g);
-  constexpr int kQ = kGB / kGP;
   const uint32_t word = byte * 0x01010101u;
-  for (int w = q * kQ / 4; w < (q + 1) * kQ / 4; ++w) g4[w] = word;
+  for (int w = q * kGQ / 4; w < (q + 1) * kGQ / 4; ++w) g4[w] = word;
 }
-__device__ void guide_part(const float* T, uint8_t* __restrict__ g, int q, int nflip) {
+__host__ __device__ inline float guide_umin(int m) {
+  return fmaf((float)m, 1.0f / (float)kGB, 5.9604644775390625e-8f);
+}
+__host__ __device__ inline float guide_umax(int m) {
+  return fmaf((float)(m + 1), 1.0f / (float)kGB, -5.9604644775390625e-8f);
+}
+__host__ __device__ inline void guide_part(const float* T, uint8_t* __restrict__ g, int q,
+                                           int nflip) {
   uint32_t* g4 = reinterpret_cast<uint32_t*>(g);
-  constexpr int kQ = kGB / kGP;
   if (T[0] < 0.0f) {
     guide_fill(g, q, 0xffu);
     return;
   }
+  const float inf = INFINITY;
   int k = 0;
-  const float u0 = (float)(2 * ((q * kQ) << kGS) + 1) * 5.9604644775390625e-8f;
+  const float u0 = guide_umin(q * kGQ);
   while (k < kJK && T[k] <= u0) ++k;
-  for (int w = q * kQ / 4; w < (q + 1) * kQ / 4; ++w) {
-    uint32_t word = 0;
-    for (int b = 0; b < 4; ++b) {
-      const int m = 4 * w + b;
-      const float umin = (float)(2 * (m << kGS) + 1) * 5.9604644775390625e-8f;
-      const float umax = (float)(2 * ((m << kGS) + (1 << kGS) - 1) + 1) * 5.9604644775390625e-8f;
-      while (k < kJK && T[k] <= umin) ++k;
-      const bool exact = k >= kJK || T[k] > umax;
-      const int o = exact && k < kJK && nflip >= 0 ? nflip - k : k;
-      word |= (uint32_t)(o | (exact ? 0x80 : 0)) << (8 * b);
+  float tk = k < kJK ? T[k] : inf;   // the first entry above the current umin
+  for (int w = q * kGQ / 4; w < (q + 1) * kGQ / 4; ++w) {
+    uint32_t word;
+    if (tk > guide_umax(4 * w + 3)) {
+      const int o = k < kJK && nflip >= 0 ? nflip - k : k;
+      word = (uint32_t)(o | 0x80) * 0x01010101u;
+    } else {
+      word = 0;
+      for (int b = 0; b < 4; ++b) {
+        const int m = 4 * w + b;
+        const float umin = guide_umin(m), umax = guide_umax(m);
+        while (k < kJK && T[k] <= umin) ++k;
+        const bool exact = k >= kJK || T[k] > umax;
+        const int o = exact && k < kJK && nflip >= 0 ? nflip - k : k;
+        word |= (uint32_t)(o | (exact ? 0x80 : 0)) << (8 * b);
+      }
+      tk = k < kJK ? T[k] : inf;
     }
     g4[w] = word;
   }
@@ -1081,7 +1100,8 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 // acceptance of draw j is decided exactly as in the one-at-a-time loop: a
 // decrement on particle k is accepted iff fewer than lev[k] earlier accepted
 // decrements in the round hit k.  The net level change goes to sums[c].net.
-__global__ void levelfix_kernel(Species sp, int c0, int c1, const CellState* __restrict__ cells,
+__global__ void __launch_bounds__(128, 8)
+levelfix_kernel(Species sp, int c0, int c1, const CellState* __restrict__ cells,
                                 CellSums* __restrict__ sums, int* __restrict__ lev,
                                 uint32_t* flags, unsigned long long* counters, uint32_t k0,
                                 uint32_t k1) {
@@ -1104,41 +1124,90 @@ __global__ void levelfix_kernel(Species sp, int c0, int c1, const CellState* __r
   const long long cap = 64 * N;
   long long net = 0;
   int* lv = lev + cs.off;
+  const bool down = remaining < 0;   // decrements need the current level
+  // Draw j picks particle k = floor(word_j N / 2^32), word j % 4 of the
+  // Philox block (c, step, CTAG_PICK, j / 4), and the draws are decided one
+  // after another.  The warp takes them 128 at a time: lane l computes the
+  // block of draws 4 l .. 4 l + 3 and the lanes exchange words so that
+  // sub-batch s holds draws 32 s + lane; the levels of all four sub-batches
+  // are read before the first is decided, so their latencies overlap.  A
+  // sub-batch is cut short only where the correction completes (or at the
+  // cap), which ends the loop, so every round starts on a multiple of 128.
+  // A level read before an earlier sub-batch's decrements is read again when
+  // that sub-batch decremented its particle (every level of the later
+  // sub-batches, after more than two decrements).
+  constexpr int kSub = 4;
   while (remaining != 0 && draws < cap) {
-    const long long j = draws + lane;
-    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_PICK, (uint32_t)(j >> 2), k0, k1);
-    const uint32_t word = (j & 3) == 0 ? w.x : (j & 3) == 1 ? w.y : (j & 3) == 2 ? w.z : w.w;
-    const long long k = (long long)(((unsigned long long)word * (unsigned long long)N) >> 32);
-    const bool valid = j < cap;
-    bool accept;
-    if (remaining > 0) {
-      accept = valid;
-    } else {
-      const int cur = valid ? __ldcg(&lv[k]) : 0;
-      const unsigned grp = __match_any_sync(0xffffffffu, valid ? k : -1ll);
-      const int rank = __popc(grp & lanemask_lt());
-      accept = valid && rank < cur;
+    const U4 w = philox4x32_10((uint32_t)c, step, CTAG_PICK, (uint32_t)((draws >> 2) + lane),
+                               k0, k1);
+    long long kk[kSub];
+    bool vd[kSub];
+    int cur[kSub];
+#pragma unroll
+    for (int s = 0; s < kSub; ++s) {
+      const int src = 8 * s + (lane >> 2);
+      const uint32_t x = __shfl_sync(0xffffffffu, w.x, src), y = __shfl_sync(0xffffffffu, w.y, src);
+      const uint32_t z = __shfl_sync(0xffffffffu, w.z, src), v = __shfl_sync(0xffffffffu, w.w, src);
+      const int q = lane & 3;
+      const uint32_t word = q == 0 ? x : q == 1 ? y : q == 2 ? z : v;
+      kk[s] = (long long)(((unsigned long long)word * (unsigned long long)N) >> 32);
+      vd[s] = draws + 32 * s + lane < cap;
+      cur[s] = down && vd[s] ? __ldcg(&lv[kk[s]]) : 0;
     }
-    const unsigned am = __ballot_sync(0xffffffffu, accept);
-    const long long need = remaining > 0 ? remaining : -remaining;
-    const int nacc = __popc(am);
-    const int take = (int)(nacc < need ? nacc : need);
-    const int order = __popc(am & lanemask_lt());
-    const bool eff = accept && order < take;
-    __syncwarp();
-    if (eff) atomicAdd(&lv[k], remaining > 0 ? 1 : -1);
-    __syncwarp();
-    long long used = 32;
-    if (take == need && take > 0) {
-      // the loop stops at the take-th accepted draw
-      unsigned m = am;
-      for (int i = 1; i < take; ++i) m &= m - 1;
-      used = __ffs((int)m);  // lane index + 1
+#pragma unroll
+    for (int s = 0; s < kSub; ++s) {
+      if (remaining == 0 || draws >= cap) break;
+      const long long k = kk[s];
+      const bool valid = vd[s];
+      bool accept;
+      if (!down) {
+        accept = valid;
+      } else {
+        const unsigned grp = __match_any_sync(0xffffffffu, valid ? k : -1ll);
+        const int rank = __popc(grp & lanemask_lt());
+        accept = valid && rank < cur[s];
+      }
+      const unsigned am = __ballot_sync(0xffffffffu, accept);
+      const long long need = remaining > 0 ? remaining : -remaining;
+      const int nacc = __popc(am);
+      const int take = (int)(nacc < need ? nacc : need);
+      const int order = __popc(am & lanemask_lt());
+      const bool eff = accept && order < take;
+      __syncwarp();
+      if (eff) atomicAdd(&lv[k], down ? -1 : 1);
+      __syncwarp();
+      long long used = 32;
+      if (take == need && take > 0) {
+        // the loop stops at the take-th accepted draw
+        unsigned m = am;
+        for (int i = 1; i < take; ++i) m &= m - 1;
+        used = __ffs((int)m);  // lane index + 1
+      }
+      if (draws + used > cap) used = cap - draws;
+      draws += used;
+      if (!down) { remaining -= take; net += take; }
+      else { remaining += take; net -= take; }
+      if (down && remaining != 0 && s + 1 < kSub) {
+        unsigned em = __ballot_sync(0xffffffffu, eff);
+        if (em) {
+          bool st[kSub];
+#pragma unroll
+          for (int t = 0; t < kSub; ++t) st[t] = __popc(em) > 2;
+          if (__popc(em) <= 2) {
+            while (em) {
+              const int l = __ffs((int)em) - 1;
+              em &= em - 1;
+              const long long kd = __shfl_sync(0xffffffffu, k, l);
+#pragma unroll
+              for (int t = s + 1; t < kSub; ++t) st[t] |= kk[t] == kd;
+            }
+          }
+#pragma unroll
+          for (int t = s + 1; t < kSub; ++t)
+            if (st[t] && vd[t]) cur[t] = __ldcg(&lv[kk[t]]);
+        }
+      }
     }
-    if (draws + used > cap) used = cap - draws;
-    draws += used;
-    if (remaining > 0) { remaining -= take; net += take; }
-    else { remaining += take; net -= take; }
   }
   if (lane != 0) return;
   if (remaining != 0) atomicOr(flags, (uint32_t)F_VIB_LOOP_CAP);
@@ -2758,6 +2827,15 @@ int usp_status(usp_ctx* c, uint32_t* flags, int64_t* counters, int reset) {
   }
   const uint32_t err = F_A_NONPOS | F_SAMPLER_UNDERFLOW | F_BOUNDS | F_CAPACITY | F_WAIT_TIMEOUT;
   return (f & err) ? USP_EDEVICE : USP_OK;
+}
+
+int usp_guide_row(const float* row, int n_flip, uint8_t* guide) {
+  if (!row || !guide || n_flip < -1 || n_flip >= kJR) return USP_EINVAL;
+  if (n_flip >= 0 && !(row[n_flip] == INFINITY)) return USP_EINVAL;
+  uint32_t w[kGB / 4];
+  for (int q = 0; q < kGP; ++q) guide_part(row, reinterpret_cast<uint8_t*>(w), q, n_flip);
+  std::memcpy(guide, w, kGB);
+  return USP_OK;
 }
 
 int usp_set_wait_limit(usp_ctx* c, int64_t cycles) {

@@ -45,7 +45,7 @@ EXPORTED = ["usp_select_device", "usp_tau_c", "usp_strerror", "usp_init_homogene
             "usp_channel_read", "usp_channel_get_particles", "usp_init_plane", "usp_plane_leaves", "usp_plane_count",
             "usp_plane_get_particles", "usp_sample", "usp_sample_read", "usp_profiles",
             "usp_backward", "usp_checkpoint_bytes", "usp_save", "usp_load", "usp_set_wait_limit",
-            "usp_wait_check", "usp_destroy"]
+            "usp_wait_check", "usp_guide_row", "usp_destroy"]
 USP_METHOD_USP_FPM, USP_METHOD_FPM = 0, 1
 USP_NSURF = 180
 USP_NOALLOC_MAX_CELLS = 8192
@@ -161,6 +161,7 @@ def lib():
             L.usp_load.argtypes = [_CTX, C.c_void_p, C.c_int]
             L.usp_set_wait_limit.argtypes = [_CTX, C.c_int64]
             L.usp_wait_check.argtypes = [_CTX, C.c_int64]
+            L.usp_guide_row.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
             L.usp_destroy.argtypes = [_CTX]
             L.usp_destroy.restype = None
             _lib = L
@@ -529,6 +530,17 @@ def usp_status(ctx: Context, reset=False):
     if rc not in (USP_OK, USP_EDEVICE):
         _check(rc, "usp_status")
     return f.value, cnt
+
+
+def usp_guide_row(row, n_flip: int = -1) -> np.ndarray:
+    """The 256-byte guide of one 48-value jump-table row (host code)."""
+    r = np.ascontiguousarray(row, dtype=np.float32)
+    if r.shape != (48,):
+        raise ValueError("a jump-table row holds 48 values")
+    g = np.zeros(256, dtype=np.uint8)
+    _check(lib().usp_guide_row(r.ctypes.data_as(C.c_void_p), int(n_flip), g.ctypes.data_as(C.c_void_p)),
+           "usp_guide_row")
+    return g
 
 
 def usp_set_wait_limit(ctx: Context, cycles: int):
