@@ -233,6 +233,9 @@ double usp_tau_c(const usp_species* sp, double n, double T);
  *   h_ndens:   number density n of each cell [1/m^3] (constant in time).
  *   h_dt:      time step of each cell [s]; must satisfy 2 mu/p > Pr dt.
  *   h_cx, h_cy, h_cz, h_erot (double) and h_lev (int32): the particles.
+ *              Levels are >= 0; they are not checked here (nor in the
+ *              host-buffer step), and the collision takes a negative level
+ *              as 0.
  * Particle ids (the Philox counter word 0) are the positions in these
  * arrays.  Returns USP_EINVAL for inconsistent sizes or a total above 2^31.
  * Synchronises the stream. */
